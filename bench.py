@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the AM sparse-PCA hot path on GB300.
+
+A step is one pass of the whole path over one batch: for each of the 8 formulations of
+Table 1, one solve of Algorithm 2 from r = 1024 unit-norm starts (start normalisation, sweeps
+until every start has stopped, FP64 objective, best start) on the spiked-model workload
+  A = sum_{k=1..5} theta_k u_k v_k^T + N(0,1),  n = 5000, p = 20000 (FP32, 400 MB > L2),
+  theta_k = (40, 30, 20, 15, 10) sqrt(n / p), u_k Gaussian unit, v_k unit with 50 nonzeros,
+  s = 50 (L0), sqrt(50) (L1 radius), gamma by the Section 4.1 rule targeting 50 nonzeros for
+  the first 10 sweeps (penalty forms), at most 100 sweeps, tol 1e-9.
+
+Metric: AM sweeps x starts per second (the sum over solves of the sweeps each start ran),
+with solves/s and the p50/p99 latency of single solves.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AM sweeps·starts/s and solves/s (p50/p99) at ≤1e-3 rel. obj. error vs plain FP32"
+UNIT = "sweeps*starts/s"
+
+WORKLOADS = {
+    # the spiked-model workload (all 8 formulations, r = 1024)
+    "spiked-5000x20000-r1024": dict(n=5000, p=20000, r=1024, spikes=(40.0, 30.0, 20.0, 15.0, 10.0),
+                                    nnz=50, s=50, forms=(1, 2, 3, 4, 5, 6, 7, 8), max_iter=100,
+                                    tol=1e-9, calib=10, data_seed=7, start_seed=8),
+    # the small dense case (n = 100, p = 500, N(0,1), form 1, s = 10, r = 16)
+    "gaussian-100x500-r16": dict(n=100, p=500, r=16, spikes=None, nnz=0, s=10, forms=(1,),
+                                 max_iter=100, tol=1e-9, calib=10, data_seed=1, start_seed=2),
+}
+DEFAULT_WORKLOAD = "spiked-5000x20000-r1024"
+
+# peak of the FP32 CUDA-core pipe: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz
+SIMT_FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+_INPUTS = {}
+
+
+def make_inputs(w):
+    key = (w["n"], w["p"], w["data_seed"])
+    if key not in _INPUTS:
+        _INPUTS[key] = _make_inputs(w)
+    return _INPUTS[key]
+
+
+def _make_inputs(w):
+    from paper_1212_4137_gb300 import inputs as I
+    n, p = w["n"], w["p"]
+    if w["spikes"] is None:
+        A = I.gaussian_matrix(n, p, w["data_seed"]).astype(np.float32)
+    else:
+        A = I.spiked_matrix(n, p, I.spiked_thetas(n, p, w["spikes"]), w["nnz"], w["data_seed"],
+                            dtype=np.float32)
+    return A
+
+
+def solve_kwargs(w, form):
+    if form in (1, 2, 3, 4):
+        return dict(s=float(w["s"]))
+    return dict(s=float(w["s"]), gamma_target=True, calib=w["calib"])
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        med = statistics.median(sm) if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------- our arm
+def run_ours(args, w, rank, world, local_rank):
+    import torch
+
+    from paper_1212_4137_gb300 import build, spca
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    A = make_inputs(w)
+    n, p, r = w["n"], w["p"], w["r"]
+    from paper_1212_4137_gb300 import inputs as I
+    G = I.raw_starts(p, r, w["start_seed"] + 1000 * rank).astype(np.float32)   # weak scaling: own starts
+    Ad = torch.from_numpy(A).to(dev)
+    Gd = torch.from_numpy(G).to(dev)
+    torch.cuda.synchronize(dev)
+    h = spca.Handle(Ad, stream=stream.cuda_stream)
+
+    def one_step(times=None):
+        sw = 0
+        for form in w["forms"]:
+            t0 = time.perf_counter()
+            out = h.solve(form, r, max_iter=w["max_iter"], tol=w["tol"], x0=Gd.data_ptr(), x0_device=True,
+                          **solve_kwargs(w, form))
+            if times is not None:
+                times.append(time.perf_counter() - t0)
+            sw += out["sweeps_total"]
+        return sw
+
+    for _ in range(args.warmup):
+        one_step()
+    barrier(world)
+    h.profile(True)
+    lat = []
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sweeps = 0
+        for _ in range(args.steps):
+            sweeps += one_step(lat)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+    ms = e0.elapsed_time(e1)
+    kern = {}
+    for kid, name in spca.KERNEL_NAMES.items():
+        kern[name] = h.profile_query(kid)
+    launches, _ = h.profile_query(spca.SPCA_K_ALL)
+    h.profile(False)
+    clocks = clk.summary()
+
+    ms_max = reduce_max(ms, world)
+    sweeps_all = reduce_sum(sweeps, world)
+    solves_all = reduce_sum(len(lat), world)
+    value = sweeps_all / (ms_max / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    A_pin = torch.from_numpy(A).pin_memory()
+    G_pin = torch.from_numpy(G).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier(world)
+    t0 = time.perf_counter()
+    e2e_sweeps = 0
+    d2h = 0
+    for _ in range(e2e_steps):
+        h2 = spca.Handle(A_pin.numpy(), stream=stream.cuda_stream)
+        for form in w["forms"]:
+            out = h2.solve(form, r, max_iter=w["max_iter"], tol=w["tol"], x0=G_pin.numpy(),
+                           **solve_kwargs(w, form))
+            e2e_sweeps += out["sweeps_total"]
+            d2h += 4 * (p + n) + 8 * int(out["nnz"]) + 64
+        h2.close()
+    torch.cuda.synchronize(dev)
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    e2e_value = reduce_sum(e2e_sweeps, world) / e2e_s
+    h2d = A.nbytes + len(w["forms"]) * G.nbytes
+    h.close()
+
+    if rank != 0:
+        return None
+    # roofline of the dominant kernel (largest share of device time)
+    shares = {k: v[1] for k, v in kern.items()}
+    total_ms = sum(shares.values()) or 1.0
+    dom = max(shares, key=shares.get)
+    flops_v = 2.0 * n * p * sweeps          # this rank's algorithmic flops of v = A^T y
+    roof = None
+    if dom == "v" and kern["v"][1] > 0:
+        achieved = flops_v / (kern["v"][1] / 1e3) / 1e12
+        roof = {"kernel": "v = A^T y (k_gemm_nt_f32, FP32 CUDA cores)", "bound": "alu",
+                "achieved": round(achieved, 3), "peak": round(SIMT_FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / SIMT_FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "algorithmic": "2*n*p flop per sweep*start", "launches": kern["v"][0],
+                "avg_launch_ms": round(kern["v"][1] / max(1, kern["v"][0]), 4)}
+    elif dom == "xstep" and kern["xstep"][1] > 0:
+        peaks = load_peaks()
+        achieved = 8.0 * p * sweeps / (kern["xstep"][1] / 1e3) / 1e9
+        roof = {"kernel": "x-step (k_xstep)", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": round(achieved / peaks.get("hbm_gbs", 6701.5), 4), "traffic": None,
+                "algorithmic": "8*p bytes per sweep*start (read v, write x)", "launches": kern["xstep"][0]}
+    lat_ms = sorted(1e3 * t for t in lat)
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "p": p, "r": r, "formulations": list(w["forms"]),
+                   "s": w["s"], "gamma_mode": "target_nnz (Section 4.1), 10 calibration sweeps",
+                   "max_iter": w["max_iter"], "tol": w["tol"], "storage": "fp32",
+                   "engine": "auto", "l2": "inputs larger than L2 (A = %d MB)" % (A.nbytes // 2**20),
+                   "parallelism": f"replicas x{world} (starts sharded, no collective)"},
+        "solves_per_s": round(solves_all / (ms_max / 1e3), 3),
+        "solve_latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
+                             "p99": round(float(np.percentile(lat_ms, 99)), 3)},
+        "sweeps_starts": int(sweeps_all),
+        "kernels_ms_share": {k: round(v / total_ms, 4) for k, v in shares.items()},
+        "roofline": roof,
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h // e2e_steps), "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    return line
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "fallback": True}
+
+
+# ---------------------------------------------------------------------------- CPU baseline
+def oracle_sample(w, A64, G, form, starts, sweeps):
+    from oracle import oracle
+    kw = solve_kwargs(w, form)
+    kw.pop("calib", None)
+    t0 = time.perf_counter()
+    res = oracle.solve(A64, form, G[:starts].astype(np.float64), max_iter=sweeps, tol=-1,
+                       calib=w["calib"], **kw)
+    dt = time.perf_counter() - t0
+    return int(res.iters.sum()), dt, oracle.num_threads()
+
+
+def cpu_baseline(w, A, G, starts=32, sweeps=10):
+    A64 = A.astype(np.float64)
+    sw, dt, cores = oracle_sample(w, A64, G, 1, starts, sweeps)
+    return {"value": round(sw / dt, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"formulation 1, first {starts} of the {w['r']} starts, {sweeps} sweeps each "
+                      f"({sw} sweeps*starts in {dt:.1f} s), FP64, OpenMP over starts"}
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return None
+    from oracle import oracle
+    oracle.build()
+    from paper_1212_4137_gb300 import inputs as I
+    A = make_inputs(w)
+    A64 = A.astype(np.float64)
+    G = I.raw_starts(w["p"], w["r"], w["start_seed"]).astype(np.float32)
+    starts, sweeps = (16, 5) if w["n"] * w["p"] > 1e7 else (w["r"], w["max_iter"])
+    forms = w["forms"]
+    for k in range(args.warmup):
+        oracle_sample(w, A64, G, forms[k % len(forms)], starts, sweeps)
+    tot_sw, tot_dt, cores = 0, 0.0, 1
+    for k in range(args.steps):
+        sw, dt, cores = oracle_sample(w, A64, G, forms[k % len(forms)], starts, sweeps)
+        tot_sw += sw
+        tot_dt += dt
+    value = tot_sw / tot_dt
+    sample = (f"per step one formulation (cycling 1..8), first {starts} starts, {sweeps} sweeps each, "
+              f"FP64 oracle, OpenMP over starts")
+    return {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * tot_dt / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "n": w["n"], "p": w["p"], "r": w["r"]},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------------------- distributed glue
+_dist = None
+
+
+def init_dist():
+    global _dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        _dist = dist
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1 and _dist is not None:
+        _dist.barrier()
+
+
+def _reduce(val, world, op):
+    if world == 1 or _dist is None:
+        return val
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([float(val)], dtype=torch.float64, device=dev)
+    _dist.all_reduce(t, op=op)
+    return t.item()
+
+
+def reduce_max(val, world):
+    return _reduce(val, world, _dist.ReduceOp.MAX if _dist else None)
+
+
+def reduce_sum(val, world):
+    return _reduce(val, world, _dist.ReduceOp.SUM if _dist else None)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = init_dist()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        line = run_reference(args, w, rank, world)
+    else:
+        line = run_ours(args, w, rank, world, local)
+        if line is not None and world == 1 and not args.no_cpu_baseline:
+            from paper_1212_4137_gb300 import inputs as I
+            G = I.raw_starts(w["p"], w["r"], w["start_seed"]).astype(np.float32)
+            line["cpu_baseline"] = cpu_baseline(w, make_inputs(w), G)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if _dist is not None:
+        _dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,249 @@
+/*
+ * spca.h -- C ABI of the GB300 (sm_103a) alternating-maximization sparse PCA library
+ * (libspca.so).
+ *
+ * The library computes, for one dense data matrix A (n samples x p variables), the
+ * single-component sparse PCA problem OPT = max_{x in X} f(x) for any of the eight
+ * formulations of Table 1 of Richtarik, Jahani, Ahipasaoglu, Takac, "Alternating
+ * maximization: unifying framework for 8 sparse PCA formulations and efficient parallel
+ * codes" (arXiv 1212.4137), by the alternating maximization method of Algorithm 2 run
+ * from r starting points at once (Section 4: the r matrix-vector products of a sweep
+ * become matrix-matrix products), keeping the best start.
+ *
+ * Conventions (all entry points):
+ *   - every call returns an int status (spca_status); no exception crosses the ABI;
+ *   - outputs are left untouched when a call fails;
+ *   - "host" buffers are ordinary (pageable or pinned) host memory, "device" buffers are
+ *     CUDA device memory of the handle's device;
+ *   - matrices are row-major; a block of r vectors of length m is r x m row-major (one
+ *     vector per row);
+ *   - a handle is bound to one CUDA stream and is not thread-safe.  Work is queued on
+ *     that stream; spca_solve returns after its results are on the host.
+ * There is no CPU fallback: without a usable GB300 the calls fail with SPCA_E_CUDA.
+ */
+#ifndef SPCA_H
+#define SPCA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spca_handle spca_handle;
+
+/* status codes */
+typedef enum {
+    SPCA_OK = 0,
+    SPCA_E_INVALID = 1,      /* an argument is out of range, a pointer is NULL, A is not finite */
+    SPCA_E_NOMEM = 2,        /* a device or pinned-host allocation failed                         */
+    SPCA_E_CUDA = 3,         /* a CUDA runtime error (no device, launch failure, ...)             */
+    SPCA_E_TIMEOUT = 4,      /* a bounded device-side wait gave up (reported by the kernel)       */
+    SPCA_E_BUSY = 5,         /* the handle is in use                                              */
+    SPCA_E_UNSUPPORTED = 6   /* a valid request this build does not implement                     */
+} spca_status;
+
+/* element types */
+typedef enum {
+    SPCA_F32 = 0,
+    SPCA_F64 = 1,
+    SPCA_BF16 = 2,
+    SPCA_FP8_E4M3_COLSCALED = 3
+} spca_dtype;
+
+/* formulation numbers = Table 1 of the paper:
+ *   #  variance  sparsity   usage        X                                  f(x)
+ *   1  L2        L0         constraint   ||x||_2 <= 1, ||x||_0 <= s         ||Ax||_2
+ *   2  L1        L0         constraint   ||x||_2 <= 1, ||x||_0 <= s         ||Ax||_1
+ *   3  L2        L1         constraint   ||x||_2 <= 1, ||x||_1 <= sqrt(s)   ||Ax||_2
+ *   4  L1        L1         constraint   ||x||_2 <= 1, ||x||_1 <= sqrt(s)   ||Ax||_1
+ *   5  L2        L0         penalty      ||x||_2 <= 1                       ||Ax||_2^2 - gamma ||x||_0
+ *   6  L1        L0         penalty      ||x||_2 <= 1                       ||Ax||_1^2 - gamma ||x||_0
+ *   7  L2        L1         penalty      ||x||_2 <= 1                       ||Ax||_2   - gamma ||x||_1
+ *   8  L1        L1         penalty      ||x||_2 <= 1                       ||Ax||_1   - gamma ||x||_1 */
+typedef enum {
+    SPCA_L2_L0CON = 1, SPCA_L1_L0CON = 2, SPCA_L2_L1CON = 3, SPCA_L1_L1CON = 4,
+    SPCA_L2_L0PEN = 5, SPCA_L1_L0PEN = 6, SPCA_L2_L1PEN = 7, SPCA_L1_L1PEN = 8
+} spca_formulation;
+
+/* gamma modes of the penalty forms 5..8.
+ *   SPCA_GAMMA_FIXED       gamma as given (Algorithm 2).
+ *   SPCA_GAMMA_TARGET_NNZ  the sparsity-targeting rule of Section 4.1: during the first
+ *                          gamma_calib_sweeps sweeps each start sets gamma so that exactly
+ *                          s entries survive (the (s+1)-th largest v_i^2 for U_gamma, the
+ *                          (s+1)-th largest |v_i| for V_gamma; 0 if s >= p), then freezes it. */
+typedef enum { SPCA_GAMMA_FIXED = 0, SPCA_GAMMA_TARGET_NNZ = 1 } spca_gamma_mode;
+
+/* per-start termination status */
+typedef enum {
+    SPCA_ST_MAXITER = 0,     /* ran max_iter sweeps                                           */
+    SPCA_ST_CONVERGED = 1,   /* stopping rule of Section 2.2 met: F_{k+1} <= (1 + tol) F_k     */
+    SPCA_ST_DEGENERATE = 2   /* the x-step returned 0 (or Ax = 0 for L2 variance): x = 0       */
+} spca_start_status;
+
+/* compute engines for the two contractions of a sweep */
+typedef enum {
+    SPCA_ENGINE_AUTO = 0,    /* the fastest engine this build has for the request             */
+    SPCA_ENGINE_SIMT = 1,    /* FP32 CUDA-core kernels                                        */
+    SPCA_ENGINE_TC = 2       /* tcgen05 tensor-core kernels (TMEM accumulators, TMA loads)    */
+} spca_engine;
+
+/*
+ * spca_create -- copy A to the device and prepare the layouts the kernels read.
+ *   out          receives the new handle (host pointer to a handle pointer).
+ *   A            n x p row-major matrix with leading dimension lda >= p (elements), of type
+ *                in_dtype (SPCA_F32 or SPCA_F64), in host memory (a_is_device = 0) or
+ *                device memory (a_is_device = 1).  Copied; the caller may free it on return.
+ *                The library does not centre the columns (the paper assumes centred data,
+ *                Section 1).
+ *   storage      SPCA_F32 (the FP32 path).  Other storage types return SPCA_E_UNSUPPORTED.
+ *   cuda_stream  cudaStream_t the handle uses (NULL = the legacy default stream).
+ * Errors: SPCA_E_INVALID (NULL pointers, n < 1, p < 1, lda < p, A not finite, unknown dtype),
+ *         SPCA_E_UNSUPPORTED, SPCA_E_NOMEM, SPCA_E_CUDA.
+ */
+int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t lda,
+                int in_dtype, int a_is_device, int storage, void *cuda_stream);
+
+/*
+ * Parameters of one solve (Algorithm 2 from r starts, Section 2.2 stopping rule).
+ *   form                Table 1 formulation (1..8).
+ *   s                   L0 forms 1, 2: the cardinality bound (integer 1..p).
+ *                       L1 forms 3, 4: the L1 radius is sqrt(s), s >= 1.
+ *                       penalty forms in SPCA_GAMMA_TARGET_NNZ mode: the target count (1..p).
+ *   gamma               penalty forms, SPCA_GAMMA_FIXED mode: gamma >= 0.
+ *   gamma_mode          spca_gamma_mode (penalty forms only).
+ *   gamma_calib_sweeps  sweeps during which gamma is re-targeted (>= 1; typical 10).
+ *   r                   number of starts (>= 1).
+ *   max_iter            maximum sweeps per start (>= 1).
+ *   tol                 stopping tolerance; a start stops after sweep k >= 2 when
+ *                       F(x^(k), y^(k-1)) <= (1 + tol) F(x^(k-1), y^(k-2)), comparing only
+ *                       values computed with the same gamma; tol < 0 disables the test.
+ *   seed                starts when x0 == NULL: x^(0) = g / ||g||_2 with g the Box-Muller
+ *                       normals of the counter-based SplitMix64 stream (seed, stream 5);
+ *                       element (c, j) of the r x p block is normal number c*p + j.
+ *   x0_is_device        x0 is a device pointer (1) or a host pointer (0).
+ *   engine              spca_engine.
+ */
+typedef struct {
+    int form;
+    double s;
+    double gamma;
+    int gamma_mode;
+    int gamma_calib_sweeps;
+    int r;
+    int max_iter;
+    double tol;
+    uint64_t seed;
+    int x0_is_device;
+    int engine;
+    int reserved[4];
+} spca_params;
+
+/*
+ * Results of one solve.  Scalars are always written.  Every pointer is a caller-owned
+ * HOST buffer of the stated length, or NULL to skip that output.
+ *   objective            f(x) of Table 1 for the best start, accumulated in FP64 on the GPU
+ *                        (gamma = the start's final gamma for the penalty forms).
+ *   explained_variance   ||Ax||_2^2 (L2 variance) or ||Ax||_1 (L1 variance) of the best start.
+ *   best_start           argmax over starts of the objective (of the explained variance in
+ *                        SPCA_GAMMA_TARGET_NNZ mode, where gammas differ per start); ties go
+ *                        to the lower start index.
+ *   sweeps_total         sum over starts of sweeps performed (sweeps x starts of work).
+ *   x [p], y [n]         the best start's normalised x and y = y(x) (S1 or S2 of Table 3).
+ *   support [p]          indices of the nonzeros of x, ascending; nnz entries are written.
+ *   start_* [r]          per-start objective, explained variance, last F value, sweeps,
+ *                        status (spca_start_status), final gamma.
+ *   start_x [r*p]        every start's final x, one per row.
+ */
+typedef struct {
+    double objective;
+    double explained_variance;
+    double gamma;
+    int best_start;
+    int best_iters;
+    int best_status;
+    int converged;
+    int degenerate;
+    int64_t sweeps_total;
+    int64_t nnz;
+    float *x;
+    float *y;
+    int64_t *support;
+    double *start_objective;
+    double *start_explained;
+    double *start_F;
+    int *start_iters;
+    int *start_status;
+    double *start_gamma;
+    float *start_x;
+} spca_result;
+
+/*
+ * spca_solve -- Algorithm 2 (Section 2.2) for r starts at once, then the Table 1 objective
+ * of every start in FP64 and the best start.
+ *   x0   r x p starting vectors (one per row, need not be normalised) of type float, host or
+ *        device memory per prm->x0_is_device; NULL = seeded starts (see spca_params.seed).
+ * Errors: SPCA_E_INVALID (NULL h/prm/res, form outside 1..8, s outside [1, p] for L0 or
+ *         target modes, s < 1 for L1 constraints, gamma < 0, r < 1, max_iter < 1,
+ *         gamma_calib_sweeps < 1 in target mode, unknown engine, non-finite x0),
+ *         SPCA_E_UNSUPPORTED (engine not available), SPCA_E_NOMEM, SPCA_E_CUDA,
+ *         SPCA_E_TIMEOUT.
+ */
+int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_result *res);
+
+/*
+ * spca_xstep -- the x-step of Algorithm 2 (Table 3, S3..S6, then normalisation) on r
+ * given vectors v = A^T y, on the handle's stream, device memory only.  Exposed so that
+ * each operator (T_s, U_gamma, V_gamma, lambda_s) can be checked on its own.
+ *   form, s, gamma   as in spca_params; calibrate != 0 applies the Section 4.1 rule
+ *                    (penalty forms) before thresholding.
+ *   V     device, r x p float, leading dimension ldv >= p.
+ *   X     device, r x p float output (ldx >= p): the normalised x-step result, or 0.
+ *   F     device, r doubles: the Table 3 value of the subproblem.
+ *   nnz   device, r ints: nonzeros of each result.
+ *   thr   device, r doubles: the threshold used (gamma for U/V, lambda_s for S4, 0 for T_s).
+ * Errors: SPCA_E_INVALID, SPCA_E_CUDA.
+ */
+int spca_xstep(spca_handle *h, int form, double s, double gamma, int calibrate,
+               const float *V, int64_t ldv, int r, float *X, int64_t ldx,
+               double *F, int *nnz, double *thr);
+
+/*
+ * Measurement hooks (not part of the method): per-kernel launch counts are always kept;
+ * with profiling on, every launch is also bracketed by CUDA events on the handle's stream.
+ *   spca_profile_enable  on != 0 starts timing (and clears the counters), 0 stops it.
+ *   spca_profile_query   kernel = one of spca_kernel_id, or SPCA_K_ALL for the total launch
+ *                        count (ms then = sum over kernels); waits for the stream, then
+ *                        writes the number of launches and their summed device time in ms
+ *                        (0 while profiling is off).  Either output pointer may be NULL.
+ * Errors: SPCA_E_INVALID (NULL handle, unknown kernel id), SPCA_E_CUDA.
+ */
+typedef enum {
+    SPCA_K_ALL = -1,
+    SPCA_K_INIT = 0,          /* a1: start normalisation                                   */
+    SPCA_K_U_DENSE = 1,       /* a2: u = A x, dense contraction                            */
+    SPCA_K_U_SPARSE = 2,      /* a2: u = A x over the support of x                          */
+    SPCA_K_YSTEP = 3,         /* a3: y-step (S1 / S2)                                       */
+    SPCA_K_V = 4,             /* a4: v = A^T y                                              */
+    SPCA_K_XSTEP = 5,         /* a5, a6: x-step, F, stopping rule                           */
+    SPCA_K_FINALISE = 6,      /* a7: FP64 objective, best start, outputs                    */
+    SPCA_K_PREP = 7,          /* layout preparation and input checks                        */
+    SPCA_K_COUNT = 8
+} spca_kernel_id;
+int spca_profile_enable(spca_handle *h, int on);
+int spca_profile_query(spca_handle *h, int kernel, int64_t *launches, double *ms);
+
+/* spca_destroy -- free the handle's device memory (waits for its stream). NULL is a no-op. */
+void spca_destroy(spca_handle *h);
+
+/* spca_strerror -- static text for a status code. */
+const char *spca_strerror(int status);
+
+/* spca_last_error -- static text for the last failure of this handle ("" if none). */
+const char *spca_last_error(const spca_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPCA_H */

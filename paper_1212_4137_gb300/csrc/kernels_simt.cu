@@ -1,0 +1,298 @@
+// kernels_simt.cu -- layout preparation, start initialisation, the y-step, and the FP32
+// CUDA-core contractions of one AM sweep (Algorithm 2): u = A x (dense or over the support of
+// x) and v = A^T y.
+#include <cstdint>
+
+#include "block_util.cuh"
+#include "spca_internal.cuh"
+
+namespace spca {
+
+// ------------------------------------------------------------------ layout preparation
+__global__ void k_transpose_f32(const float *__restrict__ src, int64_t rows, int64_t cols,
+                                int64_t lds, float *__restrict__ dst, int64_t ldd) {
+  __shared__ float tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + k, c = c0 + threadIdx.x;
+    tile[k][threadIdx.x] = (r < rows && c < cols) ? src[r * lds + c] : 0.0f;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c = c0 + k, r = r0 + threadIdx.x;  // dst row = src column
+    if (c < cols && r < rows) dst[c * ldd + r] = tile[threadIdx.x][k];
+  }
+}
+
+cudaError_t launch_transpose_f32(const float *src, int64_t rows, int64_t cols, int64_t lds,
+                                 float *dst, int64_t ldd, cudaStream_t st) {
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  k_transpose_f32<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, lds, dst, ldd);
+  return cudaGetLastError();
+}
+
+__global__ void k_convert_f64_f32(const double *__restrict__ src, int64_t rows, int64_t cols,
+                                  int64_t lds, float *__restrict__ dst, int64_t ldd) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e - r * cols;
+    dst[r * ldd + c] = (float)src[r * lds + c];
+  }
+}
+
+cudaError_t launch_convert_f64_f32(const double *src, int64_t rows, int64_t cols, int64_t lds,
+                                   float *dst, int64_t ldd, cudaStream_t st) {
+  k_convert_f64_f32<<<1216, 256, 0, st>>>(src, rows, cols, lds, dst, ldd);
+  return cudaGetLastError();
+}
+
+__global__ void k_copy_f32(const float *__restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                           float *__restrict__ dst, int64_t ldd) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e - r * cols;
+    dst[r * ldd + c] = src[r * lds + c];
+  }
+}
+
+cudaError_t launch_copy_f32(const float *src, int64_t rows, int64_t cols, int64_t lds, float *dst,
+                            int64_t ldd, cudaStream_t st) {
+  k_copy_f32<<<1216, 256, 0, st>>>(src, rows, cols, lds, dst, ldd);
+  return cudaGetLastError();
+}
+
+__global__ void k_check_finite(const float *__restrict__ a, int64_t rows, int64_t cols, int64_t ld,
+                               int *flag) {
+  const int64_t total = rows * cols;
+  int bad = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e - r * cols;
+    bad |= !isfinite(a[r * ld + c]);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+cudaError_t launch_check_finite(const float *a, int64_t rows, int64_t cols, int64_t ld, int *flag,
+                                cudaStream_t st) {
+  k_check_finite<<<1216, 256, 0, st>>>(a, rows, cols, ld, flag);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ a1: start initialisation
+// SplitMix64 (Steele, Lea, Flood 2014) finaliser with the published constants, used as a
+// counter-based generator: word(key, i) = mix(key + (i + 1) * golden).
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double sm64_uniform(uint64_t key, uint64_t i) {
+  return (double)(sm64_mix(key + (i + 1ull) * 0x9E3779B97F4A7C15ull) >> 11) * 0x1.0p-53;
+}
+// normal number i of the stream (Box-Muller over the pair i/2)
+__device__ __forceinline__ double bm_normal(uint64_t key, uint64_t i) {
+  const uint64_t j = i >> 1;
+  const double u1 = 1.0 - sm64_uniform(key, 2 * j), u2 = sm64_uniform(key, 2 * j + 1);
+  const double rad = sqrt(-2.0 * log(u1)), ang = 6.283185307179586 * u2;
+  return (i & 1) ? rad * sin(ang) : rad * cos(ang);
+}
+
+// Algorithm 2, "select initial point": x^(0) = g / ||g||_2 per start (block per start).
+__global__ void __launch_bounds__(256) k_start_init(const float *__restrict__ x0, int64_t ld0,
+                                                    uint64_t key, int p, float *__restrict__ X,
+                                                    int64_t ldX, StartState s, double gamma0) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  float *x = X + (int64_t)c * ldX;
+  const float *g = x0 ? x0 + (int64_t)c * ld0 : nullptr;
+  double part = 0.0;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    const float gj = g ? g[j] : (float)bm_normal(key, (uint64_t)c * (uint64_t)p + (uint64_t)j);
+    x[j] = gj;
+    part += (double)gj * (double)gj;
+  }
+  const double nrm = sqrt(block_sum_d(part, red));
+  const float inv = nrm > 0.0 ? (float)(1.0 / nrm) : 0.0f;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) x[j] = x[j] * inv;
+  if (threadIdx.x == 0) {
+    s.status[c] = (nrm > 0.0) ? ST_ACTIVE : SPCA_ST_DEGENERATE;
+    s.iters[c] = 0;
+    s.nnz[c] = (nrm > 0.0) ? p : 0;
+    s.F[c] = 0.0;
+    s.F_prev[c] = 0.0;
+    s.gamma[c] = gamma0;
+    s.thr[c] = 0.0f;
+  }
+}
+
+cudaError_t launch_start_init(const float *x0, int64_t ld0, uint64_t seed, int r, int p, float *X,
+                              int64_t ldX, StartState s, double gamma0, cudaStream_t st) {
+  // key = mix(seed ^ mix(stream)), stream 5 = starts (same definition as the host generator)
+  auto mixh = [](uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  const uint64_t key = mixh(seed ^ mixh(5ull));
+  k_start_init<<<r, 256, 0, st>>>(x0, ld0, key, p, X, ldX, s, gamma0);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ y-step (Table 3 S1, S2)
+// Counts the sweep for every active start; L1 variance: y = sgn(u) with sgn(0) = +1;
+// L2 variance: y = u / ||u||_2, and ||u||_2 = 0 ends the start as degenerate (x = 0).
+__global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict__ U, int64_t ldu,
+                                               int n, float *__restrict__ Y, StartState s,
+                                               float *__restrict__ X, int64_t ldX, int p) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  if (s.status[c] != ST_ACTIVE) return;
+  const float *u = U + (int64_t)c * ldu;
+  float *y = Y + (int64_t)c * ldu;
+  if (threadIdx.x == 0) s.iters[c] += 1;
+  if (is_l1_var(form)) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (u[i] >= 0.0f) ? 1.0f : -1.0f;
+    return;
+  }
+  double part = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) part += (double)u[i] * (double)u[i];
+  const double nrm = sqrt(block_sum_d(part, red));
+  if (nrm == 0.0) {
+    float *x = X + (int64_t)c * ldX;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) x[j] = 0.0f;
+    if (threadIdx.x == 0) {
+      s.status[c] = SPCA_ST_DEGENERATE;
+      s.nnz[c] = 0;
+      s.F[c] = 0.0;
+    }
+    return;
+  }
+  const float inv = (float)(1.0 / nrm);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = u[i] * inv;
+}
+
+cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, float *Y, StartState s,
+                         float *X, int64_t ldX, int p, cudaStream_t st) {
+  k_ystep<<<r, 256, 0, st>>>(form, U, ldu, n, Y, s, X, ldX, p);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ FP32 CUDA-core GEMM
+// C[m, j] = sum_k P[m, k] Q[j, k]; P (M x K) and Q (N x K) are both K-contiguous with
+// leading dimensions that are multiples of 8 and zero pads, and K is a multiple of 8.
+// 128 x 128 tile, 8-deep K slices, 256 threads with an 8 x 8 register block each; the
+// next slice is prefetched into registers while the current one is multiplied.
+namespace {
+constexpr int BM = 128, BN = 128, BK = 8;
+}
+
+__global__ void __launch_bounds__(256) k_gemm_nt_f32(const float *__restrict__ P, int64_t ldp,
+                                                     const float *__restrict__ Q, int64_t ldq,
+                                                     float *__restrict__ C, int64_t ldc, int M,
+                                                     int N, int K, const int *__restrict__ gate) {
+  if (gate && *gate == 0) return;
+  __shared__ __align__(16) float As[BK][BM + 4];
+  __shared__ __align__(16) float Bs[BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // loader: thread -> (row, 4 consecutive k)
+  const int lrow = tid >> 1, lk = (tid & 1) * 4;
+  const bool pa = (m0 + lrow) < M, qa = (n0 + lrow) < N;
+  const float *pp = P + (int64_t)(pa ? m0 + lrow : 0) * ldp + lk;
+  const float *qp = Q + (int64_t)(qa ? n0 + lrow : 0) * ldq + lk;
+  // compute: thread -> rows {ty*4..+3, 64+ty*4..+3}, cols {tx*4..+3, 64+tx*4..+3}
+  const int ty = tid >> 4, tx = tid & 15;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+
+  float4 ra = pa ? *reinterpret_cast<const float4 *>(pp) : make_float4(0, 0, 0, 0);
+  float4 rb = qa ? *reinterpret_cast<const float4 *>(qp) : make_float4(0, 0, 0, 0);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    __syncthreads();
+    As[lk + 0][lrow] = ra.x; As[lk + 1][lrow] = ra.y; As[lk + 2][lrow] = ra.z; As[lk + 3][lrow] = ra.w;
+    Bs[lk + 0][lrow] = rb.x; Bs[lk + 1][lrow] = rb.y; Bs[lk + 2][lrow] = rb.z; Bs[lk + 3][lrow] = rb.w;
+    __syncthreads();
+    if (k0 + BK < K) {
+      ra = pa ? *reinterpret_cast<const float4 *>(pp + k0 + BK) : make_float4(0, 0, 0, 0);
+      rb = qa ? *reinterpret_cast<const float4 *>(qp + k0 + BK) : make_float4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + ((i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int nn = n0 + ((j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      if (nn < N) C[(int64_t)m * ldc + nn] = acc[i][j];
+    }
+  }
+}
+
+cudaError_t launch_gemm_nt_f32(const float *P, int64_t ldp, const float *Q, int64_t ldq, float *C,
+                               int64_t ldc, int M, int N, int K, const int *gate, cudaStream_t st) {
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+  k_gemm_nt_f32<<<grid, 256, 0, st>>>(P, ldp, Q, ldq, C, ldc, M, N, K, gate);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ u = A x over supp(x)
+// U[c, i] = sum_t val[c, t] AT[idx[c, t], i] (t over the support of x, ascending index).
+// Runs only when *gate == 0, i.e. when every active start's support fits the sparse path.
+__global__ void __launch_bounds__(256) k_gemm1_sparse(const float *__restrict__ AT, int64_t ldat,
+                                                      int n, const int *__restrict__ sup_idx,
+                                                      const float *__restrict__ sup_val, int cap,
+                                                      StartState s, float *__restrict__ U,
+                                                      int64_t ldu, const int *__restrict__ gate) {
+  if (*gate != 0) return;
+  const int c = blockIdx.y;
+  if (s.status[c] != ST_ACTIVE) return;
+  __shared__ int sidx[256];
+  __shared__ float sval[256];
+  const int nnz = s.nnz[c];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int *gi = sup_idx + (int64_t)c * cap;
+  const float *gv = sup_val + (int64_t)c * cap;
+  float acc = 0.0f;
+  for (int t0 = 0; t0 < nnz; t0 += 256) {
+    __syncthreads();
+    if (t0 + (int)threadIdx.x < nnz) {
+      sidx[threadIdx.x] = gi[t0 + threadIdx.x];
+      sval[threadIdx.x] = gv[t0 + threadIdx.x];
+    }
+    __syncthreads();
+    const int m = min(256, nnz - t0);
+    if (i < n)
+      for (int t = 0; t < m; ++t) acc = fmaf(sval[t], AT[(int64_t)sidx[t] * ldat + i], acc);
+  }
+  if (i < n) U[(int64_t)c * ldu + i] = acc;
+}
+
+cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int *sup_idx,
+                                const float *sup_val, int cap, StartState s, int r, float *U,
+                                int64_t ldu, const int *gate, cudaStream_t st) {
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)r);
+  k_gemm1_sparse<<<grid, 256, 0, st>>>(AT, ldat, n, sup_idx, sup_val, cap, s, U, ldu, gate);
+  return cudaGetLastError();
+}
+
+}  // namespace spca

@@ -1,0 +1,472 @@
+// spca_api.cu -- the C ABI of include/spca.h: the handle (device copies of A), the solve
+// driver that runs Algorithm 2 for r starts as a sequence of kernels on one stream, and the
+// stand-alone x-step entry point.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "spca_internal.cuh"
+
+using namespace spca;
+
+struct spca_handle {
+  int64_t n = 0, p = 0;
+  int64_t ldA = 0, ldAT = 0;  // padded leading dimensions of A32 (n x p) and AT32 (p x n)
+  cudaStream_t stream = nullptr;
+  float *A32 = nullptr, *AT32 = nullptr;
+
+  // per-solve workspace, grown on demand
+  int r_cap = 0;
+  int64_t ldX = 0, ldU = 0;
+  float *X = nullptr, *V = nullptr, *U = nullptr, *Y = nullptr;
+  int *sup_idx = nullptr;
+  float *sup_val = nullptr;
+  int *status = nullptr, *iters = nullptr, *nnz = nullptr;
+  double *F = nullptr, *F_prev = nullptr, *gamma = nullptr, *f = nullptr, *ev = nullptr;
+  float *thr = nullptr;
+  double *partials = nullptr;
+  Ctrl *ctrl = nullptr;       // device, 2 entries
+  int *best = nullptr;
+  float *y_out = nullptr, *x_out = nullptr;
+  int64_t *support_out = nullptr, *nnz_out = nullptr;
+  int *flag = nullptr;        // device scratch flag
+  Ctrl *h_ctrl = nullptr;     // pinned host mirror
+  int *h_flag = nullptr;      // pinned host mirror
+
+  // measurement hooks: launch counts, and event pairs per kernel id while profiling is on
+  bool prof_on = false;
+  int64_t launches[SPCA_K_COUNT] = {0};
+  double ms[SPCA_K_COUNT] = {0};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[SPCA_K_COUNT];
+  std::vector<cudaEvent_t> event_pool;
+
+  char last_error[256] = {0};
+};
+
+namespace {
+
+int fail(spca_handle *h, int code, const char *fmt, const char *detail = "") {
+  if (h) snprintf(h->last_error, sizeof(h->last_error), fmt, detail);
+  return code;
+}
+
+#define CK(expr)                                                               \
+  do {                                                                         \
+    cudaError_t e_ = (expr);                                                   \
+    if (e_ != cudaSuccess)                                                     \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? SPCA_E_NOMEM : SPCA_E_CUDA, \
+                  "CUDA error: %s", cudaGetErrorString(e_));                   \
+  } while (0)
+
+cudaEvent_t get_event(spca_handle *h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// runs `launch` (which enqueues `nk` kernels of kind `kid`), counting and optionally timing it
+template <typename F>
+cudaError_t timed(spca_handle *h, int kid, int nk, F &&launch) {
+  h->launches[kid] += nk;
+  if (!h->prof_on) return launch();
+  cudaEvent_t a = get_event(h), b = get_event(h);
+  cudaEventRecord(a, h->stream);
+  cudaError_t e = launch();
+  cudaEventRecord(b, h->stream);
+  h->pending[kid].push_back({a, b});
+  return e;
+}
+
+cudaError_t drain_profile(spca_handle *h) {
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < SPCA_K_COUNT; ++k) {
+    for (auto &pr : h->pending[k]) {
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, pr.first, pr.second);
+      h->ms[k] += t;
+      h->event_pool.push_back(pr.first);
+      h->event_pool.push_back(pr.second);
+    }
+    h->pending[k].clear();
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count) {
+  return cudaMalloc((void **)p, count * sizeof(T) + 16);
+}
+
+void free_workspace(spca_handle *h) {
+  void *ptrs[] = {h->X, h->V, h->U, h->Y, h->sup_idx, h->sup_val, h->status, h->iters, h->nnz,
+                  h->F, h->F_prev, h->gamma, h->f, h->ev, h->thr, h->partials, h->ctrl, h->best,
+                  h->y_out, h->x_out, h->support_out, h->nnz_out};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+  h->X = h->V = h->U = h->Y = nullptr;
+  h->sup_idx = nullptr; h->sup_val = nullptr;
+  h->status = h->iters = h->nnz = nullptr;
+  h->F = h->F_prev = h->gamma = h->f = h->ev = nullptr;
+  h->thr = nullptr; h->partials = nullptr; h->ctrl = nullptr; h->best = nullptr;
+  h->y_out = h->x_out = nullptr; h->support_out = h->nnz_out = nullptr;
+  h->r_cap = 0;
+}
+
+int ensure_workspace(spca_handle *h, int r) {
+  if (r <= h->r_cap) return SPCA_OK;
+  free_workspace(h);
+  const int64_t n = h->n, p = h->p;
+  h->ldX = pad_ld(p);
+  h->ldU = pad_ld(n);
+  const int64_t nchunks = (n + 255) / 256;
+  CK(dalloc(&h->X, (size_t)r * h->ldX));
+  CK(dalloc(&h->V, (size_t)r * h->ldX));
+  CK(dalloc(&h->U, (size_t)r * h->ldU));
+  CK(dalloc(&h->Y, (size_t)r * h->ldU));
+  CK(dalloc(&h->sup_idx, (size_t)r * p));
+  CK(dalloc(&h->sup_val, (size_t)r * p));
+  CK(dalloc(&h->status, r)); CK(dalloc(&h->iters, r)); CK(dalloc(&h->nnz, r));
+  CK(dalloc(&h->F, r)); CK(dalloc(&h->F_prev, r)); CK(dalloc(&h->gamma, r));
+  CK(dalloc(&h->f, r)); CK(dalloc(&h->ev, r)); CK(dalloc(&h->thr, r));
+  CK(dalloc(&h->partials, (size_t)r * nchunks * 2));
+  CK(dalloc(&h->ctrl, 2)); CK(dalloc(&h->best, 1));
+  CK(dalloc(&h->y_out, (size_t)h->ldU)); CK(dalloc(&h->x_out, (size_t)h->ldX));
+  CK(dalloc(&h->support_out, (size_t)p)); CK(dalloc(&h->nnz_out, 1));
+  // zero pads: the contractions read the padded K range
+  CK(cudaMemsetAsync(h->X, 0, (size_t)r * h->ldX * sizeof(float), h->stream));
+  CK(cudaMemsetAsync(h->V, 0, (size_t)r * h->ldX * sizeof(float), h->stream));
+  CK(cudaMemsetAsync(h->U, 0, (size_t)r * h->ldU * sizeof(float), h->stream));
+  CK(cudaMemsetAsync(h->Y, 0, (size_t)r * h->ldU * sizeof(float), h->stream));
+  h->r_cap = r;
+  return SPCA_OK;
+}
+
+StartState state_of(spca_handle *h) {
+  StartState s;
+  s.status = h->status; s.iters = h->iters; s.nnz = h->nnz;
+  s.F = h->F; s.F_prev = h->F_prev; s.gamma = h->gamma; s.thr = h->thr;
+  s.f = h->f; s.ev = h->ev;
+  return s;
+}
+
+// threshold in |v| units for U_gamma: the largest float t with t <= sqrt(gamma), so that for
+// every float v, |v| > t  <=>  v^2 > gamma
+float u_threshold(double gamma) {
+  const double r = std::sqrt(gamma);
+  float t = (float)r;
+  if ((double)t > r) t = std::nextafterf(t, 0.0f);
+  return t;
+}
+
+int check_form_params(spca_handle *h, int form, double s, double gamma, int gamma_mode, int64_t p) {
+  if (form < 1 || form > 8) return fail(h, SPCA_E_INVALID, "form must be 1..8%s");
+  if (!std::isfinite(s) || !std::isfinite(gamma)) return fail(h, SPCA_E_INVALID, "s and gamma must be finite%s");
+  if (uses_T(form) && (s < 1.0 || s > (double)p || s != std::floor(s)))
+    return fail(h, SPCA_E_INVALID, "L0 constraint: s must be an integer in [1, p]%s");
+  if (uses_lam(form) && s < 1.0) return fail(h, SPCA_E_INVALID, "L1 constraint: s must be >= 1%s");
+  if (is_pen(form)) {
+    if (gamma_mode != SPCA_GAMMA_FIXED && gamma_mode != SPCA_GAMMA_TARGET_NNZ)
+      return fail(h, SPCA_E_INVALID, "unknown gamma_mode%s");
+    if (gamma_mode == SPCA_GAMMA_FIXED && gamma < 0.0) return fail(h, SPCA_E_INVALID, "gamma must be >= 0%s");
+    if (gamma_mode == SPCA_GAMMA_TARGET_NNZ && (s < 1.0 || s > (double)p || s != std::floor(s)))
+      return fail(h, SPCA_E_INVALID, "target mode: s must be an integer in [1, p]%s");
+  }
+  return SPCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *spca_strerror(int status) {
+  switch (status) {
+    case SPCA_OK: return "ok";
+    case SPCA_E_INVALID: return "invalid argument";
+    case SPCA_E_NOMEM: return "out of memory";
+    case SPCA_E_CUDA: return "CUDA error";
+    case SPCA_E_TIMEOUT: return "device-side wait timed out";
+    case SPCA_E_BUSY: return "handle busy";
+    case SPCA_E_UNSUPPORTED: return "not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+const char *spca_last_error(const spca_handle *h) { return h ? h->last_error : ""; }
+
+int spca_profile_enable(spca_handle *h, int on) {
+  if (!h) return SPCA_E_INVALID;
+  CK(drain_profile(h));
+  for (int k = 0; k < SPCA_K_COUNT; ++k) {
+    h->launches[k] = 0;
+    h->ms[k] = 0.0;
+  }
+  h->prof_on = on != 0;
+  return SPCA_OK;
+}
+
+int spca_profile_query(spca_handle *h, int kernel, int64_t *launches, double *ms) {
+  if (!h || kernel < SPCA_K_ALL || kernel >= SPCA_K_COUNT) return SPCA_E_INVALID;
+  CK(drain_profile(h));
+  int64_t l = 0;
+  double t = 0.0;
+  for (int k = 0; k < SPCA_K_COUNT; ++k) {
+    if (kernel == SPCA_K_ALL || kernel == k) {
+      l += h->launches[k];
+      t += h->ms[k];
+    }
+  }
+  if (launches) *launches = l;
+  if (ms) *ms = t;
+  return SPCA_OK;
+}
+
+void spca_destroy(spca_handle *h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  drain_profile(h);
+  for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  free_workspace(h);
+  if (h->A32) cudaFree(h->A32);
+  if (h->AT32) cudaFree(h->AT32);
+  if (h->flag) cudaFree(h->flag);
+  if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+  if (h->h_flag) cudaFreeHost(h->h_flag);
+  delete h;
+}
+
+int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t lda, int in_dtype,
+                int a_is_device, int storage, void *cuda_stream) {
+  spca_handle *h = nullptr;
+  if (!out || !A) return SPCA_E_INVALID;
+  if (n < 1 || p < 1 || lda < p || n > INT32_MAX || p > INT32_MAX) return SPCA_E_INVALID;
+  if (in_dtype != SPCA_F32 && in_dtype != SPCA_F64) return SPCA_E_INVALID;
+  if (storage != SPCA_F32) {
+    if (storage == SPCA_BF16 || storage == SPCA_FP8_E4M3_COLSCALED || storage == SPCA_F64)
+      return SPCA_E_UNSUPPORTED;
+    return SPCA_E_INVALID;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SPCA_E_CUDA;
+  h = new (std::nothrow) spca_handle();
+  if (!h) return SPCA_E_NOMEM;
+  int rc = [&]() -> int {
+    h->n = n; h->p = p;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->ldA = pad_ld(p);
+    h->ldAT = pad_ld(n);
+    CK(cudaMallocHost((void **)&h->h_ctrl, 2 * sizeof(Ctrl)));
+    CK(cudaMallocHost((void **)&h->h_flag, sizeof(int)));
+    CK(dalloc(&h->flag, 1));
+    CK(dalloc(&h->A32, (size_t)n * h->ldA));
+    CK(dalloc(&h->AT32, (size_t)p * h->ldAT));
+    CK(cudaMemsetAsync(h->A32, 0, (size_t)n * h->ldA * sizeof(float), h->stream));
+    CK(cudaMemsetAsync(h->AT32, 0, (size_t)p * h->ldAT * sizeof(float), h->stream));
+    const cudaMemcpyKind kind = a_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (in_dtype == SPCA_F32) {
+      CK(cudaMemcpy2DAsync(h->A32, h->ldA * sizeof(float), A, lda * sizeof(float), p * sizeof(float),
+                           n, kind, h->stream));
+    } else {
+      double *tmp = nullptr;
+      CK(dalloc(&tmp, (size_t)n * lda));
+      cudaError_t e = cudaMemcpyAsync(tmp, A, (size_t)n * lda * sizeof(double), kind, h->stream);
+      if (e == cudaSuccess) e = launch_convert_f64_f32(tmp, n, p, lda, h->A32, h->ldA, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      cudaFree(tmp);
+      CK(e);
+    }
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    CK(timed(h, SPCA_K_PREP, 1, [&] { return launch_check_finite(h->A32, n, p, h->ldA, h->flag, h->stream); }));
+    CK(cudaMemcpyAsync(h->h_flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(timed(h, SPCA_K_PREP, 1, [&] { return launch_transpose_f32(h->A32, n, p, h->ldA, h->AT32, h->ldAT, h->stream); }));
+    CK(cudaStreamSynchronize(h->stream));
+    if (*h->h_flag) return fail(h, SPCA_E_INVALID, "A has a non-finite entry%s");
+    return SPCA_OK;
+  }();
+  if (rc != SPCA_OK) {
+    spca_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return SPCA_OK;
+}
+
+int spca_xstep(spca_handle *h, int form, double s, double gamma, int calibrate, const float *V,
+               int64_t ldv, int r, float *X, int64_t ldx, double *F, int *nnz, double *thr) {
+  if (!h || !V || !X || !F || !nnz || !thr || r < 1) return fail(h, SPCA_E_INVALID, "bad argument%s");
+  if (ldv < h->p || ldx < h->p) return fail(h, SPCA_E_INVALID, "leading dimension < p%s");
+  int rc = check_form_params(h, form, s, gamma,
+                             calibrate ? SPCA_GAMMA_TARGET_NNZ : SPCA_GAMMA_FIXED, h->p);
+  if (rc != SPCA_OK) return rc;
+  XstepArgs a{};
+  a.form = form; a.p = (int)h->p; a.s = s;
+  a.calibrate = is_pen(form) && calibrate;
+  a.per_start_thr = 0;
+  a.thr_fixed = uses_U(form) ? u_threshold(gamma) : (float)gamma;
+  a.gamma_fixed = gamma;
+  a.stop_test = 0; a.tol = -1.0; a.max_iter = 1 << 30;
+  a.cap = 0; a.sparse_cap = (int)h->p;
+  StartState st{};
+  st.nnz = nnz; st.F = F; st.gamma = thr;
+  CK(timed(h, SPCA_K_XSTEP, 1,
+           [&] { return launch_xstep(a, V, ldv, r, X, ldx, st, nullptr, nullptr, nullptr, h->stream); }));
+  CK(cudaStreamSynchronize(h->stream));
+  return SPCA_OK;
+}
+
+int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_result *res) {
+  if (!h || !prm || !res) return fail(h, SPCA_E_INVALID, "NULL argument%s");
+  const spca_params P = *prm;
+  const int form = P.form;
+  int rc = check_form_params(h, form, P.s, P.gamma, P.gamma_mode, h->p);
+  if (rc != SPCA_OK) return rc;
+  if (P.r < 1 || P.max_iter < 1) return fail(h, SPCA_E_INVALID, "r and max_iter must be >= 1%s");
+  if (!std::isfinite(P.tol)) return fail(h, SPCA_E_INVALID, "tol must be finite%s");
+  const bool target = is_pen(form) && P.gamma_mode == SPCA_GAMMA_TARGET_NNZ;
+  if (target && P.gamma_calib_sweeps < 1) return fail(h, SPCA_E_INVALID, "gamma_calib_sweeps must be >= 1%s");
+  if (P.engine != SPCA_ENGINE_AUTO && P.engine != SPCA_ENGINE_SIMT && P.engine != SPCA_ENGINE_TC)
+    return fail(h, SPCA_E_INVALID, "unknown engine%s");
+  if (P.engine == SPCA_ENGINE_TC) return fail(h, SPCA_E_UNSUPPORTED, "tensor-core engine not built%s");
+
+  const int r = P.r, n = (int)h->n, p = (int)h->p;
+  rc = ensure_workspace(h, r);
+  if (rc != SPCA_OK) return rc;
+  cudaStream_t st = h->stream;
+  StartState S = state_of(h);
+
+  // ---- a1: starting points
+  const double gamma0 = is_pen(form) && !target ? P.gamma : 0.0;
+  if (x0 && !P.x0_is_device) {
+    CK(cudaMemcpy2DAsync(h->X, h->ldX * sizeof(float), x0, (size_t)p * sizeof(float),
+                         (size_t)p * sizeof(float), r, cudaMemcpyHostToDevice, st));
+  } else if (x0) {
+    CK(cudaMemcpy2DAsync(h->X, h->ldX * sizeof(float), x0, (size_t)p * sizeof(float),
+                         (size_t)p * sizeof(float), r, cudaMemcpyDeviceToDevice, st));
+  }
+  if (x0) {
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
+    CK(timed(h, SPCA_K_PREP, 1, [&] { return launch_check_finite(h->X, r, p, h->ldX, h->flag, st); }));
+    CK(cudaMemcpyAsync(h->h_flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*h->h_flag) return fail(h, SPCA_E_INVALID, "x0 has a non-finite entry%s");
+  }
+  CK(timed(h, SPCA_K_INIT, 1, [&] {
+    return launch_start_init(x0 ? h->X : nullptr, h->ldX, P.seed, r, p, h->X, h->ldX, S, gamma0, st);
+  }));
+  h->h_ctrl[0].active = r; h->h_ctrl[0].need_dense = 1; h->h_ctrl[0].err = 0; h->h_ctrl[0].pad = 0;
+  CK(cudaMemcpyAsync(h->ctrl, h->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));  // h_ctrl is reused below
+
+  // ---- the sweeps (Algorithm 2)
+  XstepArgs xa{};
+  xa.form = form; xa.p = p; xa.s = P.s;
+  xa.thr_fixed = uses_U(form) ? u_threshold(P.gamma) : (float)P.gamma;
+  xa.gamma_fixed = P.gamma;
+  xa.tol = P.tol; xa.max_iter = P.max_iter;
+  xa.cap = p;
+  xa.sparse_cap = p / 8 > 0 ? p / 8 : 1;
+  const int C = target ? P.gamma_calib_sweeps : 0;
+  const int check_every = 1;
+  for (int k = 1; k <= P.max_iter; ++k) {
+    Ctrl *cur = h->ctrl + ((k - 1) & 1), *nxt = h->ctrl + (k & 1);
+    // u = A x: dense contraction, or the support gather when every support is small
+    CK(timed(h, SPCA_K_U_DENSE, 1, [&] {
+      return launch_gemm_nt_f32(h->X, h->ldX, h->A32, h->ldA, h->U, h->ldU, r, n, (int)h->ldX,
+                                &cur->need_dense, st);
+    }));
+    CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
+      return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U,
+                                 h->ldU, &cur->need_dense, st);
+    }));
+    CK(timed(h, SPCA_K_YSTEP, 1,
+             [&] { return launch_ystep(form, h->U, h->ldU, n, r, h->Y, S, h->X, h->ldX, p, st); }));
+    // v = A^T y
+    CK(timed(h, SPCA_K_V, 1, [&] {
+      return launch_gemm_nt_f32(h->Y, h->ldU, h->AT32, h->ldAT, h->V, h->ldX, r, p, (int)h->ldU,
+                                nullptr, st);
+    }));
+    CK(cudaMemsetAsync(nxt, 0, sizeof(Ctrl), st));
+    xa.calibrate = target && k <= C;
+    xa.per_start_thr = target && k > C;
+    xa.stop_test = P.tol >= 0.0 && k >= 2 && k >= C + 1;
+    CK(timed(h, SPCA_K_XSTEP, 1, [&] {
+      return launch_xstep(xa, h->V, h->ldX, r, h->X, h->ldX, S, h->sup_idx, h->sup_val, nxt, st);
+    }));
+    if (k == P.max_iter || k % check_every == 0) {
+      CK(cudaMemcpyAsync(h->h_ctrl, nxt, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (h->h_ctrl->active == 0) break;
+    }
+  }
+
+  // ---- a7: FP64 objective, best start, y(x) and support of the best x
+  CK(timed(h, SPCA_K_FINALISE, 4, [&] {
+    cudaError_t e = launch_finalise(form, h->AT32, h->ldAT, n, p, h->X, h->ldX, S, r, h->U, h->ldU,
+                                    h->sup_idx, h->sup_val, p, h->partials, st);
+    if (e == cudaSuccess) e = launch_best(form, target ? 1 : 0, S, r, h->best, st);
+    if (e == cudaSuccess)
+      e = launch_best_outputs(form, h->best, h->U, h->ldU, n, h->X, h->ldX, p, h->y_out, h->x_out,
+                              h->support_out, h->nnz_out, st);
+    return e;
+  }));
+
+  // ---- results to the host
+  std::vector<int> status(r), iters(r);
+  std::vector<double> f(r), ev(r), gam(r), F(r);
+  int best = 0;
+  int64_t nnz = 0;
+  CK(cudaMemcpyAsync(status.data(), h->status, r * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(iters.data(), h->iters, r * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(f.data(), h->f, r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ev.data(), h->ev, r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(gam.data(), h->gamma, r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(F.data(), h->F, r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&best, h->best, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&nnz, h->nnz_out, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (res->x) CK(cudaMemcpyAsync(res->x, h->x_out, (size_t)p * sizeof(float), cudaMemcpyDeviceToHost, st));
+  if (res->y) CK(cudaMemcpyAsync(res->y, h->y_out, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st));
+  if (res->support && nnz > 0)
+    CK(cudaMemcpyAsync(res->support, h->support_out, (size_t)nnz * sizeof(int64_t),
+                       cudaMemcpyDeviceToHost, st));
+  if (res->start_x)
+    CK(cudaMemcpy2DAsync(res->start_x, (size_t)p * sizeof(float), h->X, h->ldX * sizeof(float),
+                         (size_t)p * sizeof(float), r, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+
+  int64_t sweeps = 0;
+  int nconv = 0, ndeg = 0;
+  for (int c = 0; c < r; ++c) {
+    sweeps += iters[c];
+    nconv += status[c] == SPCA_ST_CONVERGED;
+    ndeg += status[c] == SPCA_ST_DEGENERATE;
+  }
+  res->objective = f[best];
+  res->explained_variance = ev[best];
+  res->gamma = is_pen(form) ? gam[best] : 0.0;
+  res->best_start = best;
+  res->best_iters = iters[best];
+  res->best_status = status[best];
+  res->converged = nconv;
+  res->degenerate = ndeg;
+  res->sweeps_total = sweeps;
+  res->nnz = nnz;
+  if (res->start_objective) memcpy(res->start_objective, f.data(), r * sizeof(double));
+  if (res->start_explained) memcpy(res->start_explained, ev.data(), r * sizeof(double));
+  if (res->start_F) memcpy(res->start_F, F.data(), r * sizeof(double));
+  if (res->start_iters) memcpy(res->start_iters, iters.data(), r * sizeof(int));
+  if (res->start_status) memcpy(res->start_status, status.data(), r * sizeof(int));
+  if (res->start_gamma) {
+    for (int c = 0; c < r; ++c) res->start_gamma[c] = is_pen(form) ? gam[c] : 0.0;
+  }
+  return SPCA_OK;
+}
+
+}  // extern "C"

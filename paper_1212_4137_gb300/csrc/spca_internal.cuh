@@ -1,0 +1,121 @@
+// spca_internal.cuh -- shared declarations of the CUDA side of libspca (sm_103a).
+//
+// Layout in HBM (per handle):
+//   A32   n x ldA  FP32, row-major copy of A             (dense y-side contraction, SIMT)
+//   AT32  p x ldAT FP32, A transposed (column-major A)   (x-side contraction, sparse gathers,
+//                                                          FP64 objective)
+// Per solve (workspace, r starts, one vector per row):
+//   X  r x ldX   current iterates x        U  r x ldU  u = A x
+//   Y  r x ldU   y-step result             V  r x ldX  v = A^T y
+//   support lists (idx, val) r x cap, per-start scalars, control words.
+// Leading dimensions are padded to a multiple of 8 elements and the pad is kept at zero,
+// so contraction kernels need no K-tail guards.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/spca.h"
+
+namespace spca {
+
+constexpr int kPad = 8;  // leading dimensions are multiples of 8 elements
+inline int64_t pad_ld(int64_t m) { return (m + kPad - 1) / kPad * kPad; }
+
+// formulation predicates (Table 1 numbering)
+__host__ __device__ inline bool is_l1_var(int f) { return (f % 2) == 0; }
+__host__ __device__ inline bool is_pen(int f) { return f >= 5; }
+__host__ __device__ inline bool uses_T(int f) { return f == 1 || f == 2; }
+__host__ __device__ inline bool uses_lam(int f) { return f == 3 || f == 4; }
+__host__ __device__ inline bool uses_U(int f) { return f == 5 || f == 6; }
+__host__ __device__ inline bool uses_V(int f) { return f == 7 || f == 8; }
+
+constexpr int ST_ACTIVE = -1;  // device-side: still iterating (host sees SPCA_ST_* only)
+
+// control words, one set per sweep parity (double-buffered so that the x-step of sweep k
+// writes the flags the contractions of sweep k+1 read)
+struct Ctrl {
+  int active;      // starts still iterating after this sweep
+  int need_dense;  // some active start has more nonzeros than the sparse path holds
+  int err;         // kernel-reported error code (0 = none)
+  int pad;
+};
+
+// per-start state of one solve (device arrays, r each)
+struct StartState {
+  int *status;      // ST_ACTIVE or SPCA_ST_*
+  int *iters;       // sweeps performed
+  int *nnz;         // nonzeros of x
+  double *F;        // F of the last sweep
+  double *F_prev;   // F of the sweep before
+  double *gamma;    // gamma (penalty forms, in the units of Table 1)
+  float *thr;       // the same threshold in |v| units, as a float the kernels compare with
+  double *f;        // Table 1 objective (finalise)
+  double *ev;       // explained variance (finalise)
+};
+
+struct XstepArgs {
+  int form;
+  int p;
+  double s;
+  int calibrate;       // apply the Section 4.1 gamma rule in this sweep
+  int per_start_thr;   // penalty threshold from StartState (frozen after calibration)
+  float thr_fixed;     // otherwise: the fixed threshold in |v| units ...
+  double gamma_fixed;  // ... and gamma in Table 1 units
+  int stop_test;       // stopping rule allowed in this sweep
+  double tol;
+  int max_iter;
+  int cap;             // capacity of each support list (entries per start)
+  int sparse_cap;      // larger supports make the next sweep use the dense u = A x
+};
+
+// ---------------------------------------------------------------- kernels (launchers)
+// each returns cudaGetLastError() of its launch(es)
+cudaError_t launch_transpose_f32(const float *src, int64_t rows, int64_t cols, int64_t lds,
+                                 float *dst, int64_t ldd, cudaStream_t st);
+cudaError_t launch_convert_f64_f32(const double *src, int64_t rows, int64_t cols, int64_t lds,
+                                   float *dst, int64_t ldd, cudaStream_t st);
+cudaError_t launch_copy_f32(const float *src, int64_t rows, int64_t cols, int64_t lds,
+                            float *dst, int64_t ldd, cudaStream_t st);
+cudaError_t launch_check_finite(const float *a, int64_t rows, int64_t cols, int64_t ld,
+                                int *flag, cudaStream_t st);
+
+// a1: x^(0) = g / ||g||_2 (g from x0, or seeded normals when x0 == nullptr); resets the
+// per-start state (gamma0 = the fixed gamma of a penalty form, else 0)
+cudaError_t launch_start_init(const float *x0, int64_t ld0, uint64_t seed, int r, int p,
+                              float *X, int64_t ldX, StartState s, double gamma0, cudaStream_t st);
+
+// C[m, j] = sum_k P[m, k] Q[j, k]  (both operands K-contiguous); with gate != nullptr the
+// launch does nothing unless *gate != 0 (the dense u = A x is needed this sweep)
+cudaError_t launch_gemm_nt_f32(const float *P, int64_t ldp, const float *Q, int64_t ldq,
+                               float *C, int64_t ldc, int M, int N, int K, const int *gate,
+                               cudaStream_t st);
+
+// U[c, i] = sum_t val[c, t] AT[idx[c, t], i] for every active start; does nothing when
+// *gate != 0 (the dense contraction runs instead)
+cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int *sup_idx,
+                                const float *sup_val, int cap, StartState s, int r, float *U,
+                                int64_t ldu, const int *gate, cudaStream_t st);
+
+// y-step (S1 / S2 of Table 3) for active starts
+cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, float *Y,
+                         StartState s, float *X, int64_t ldX, int p, cudaStream_t st);
+
+// x-step (S3..S6), objective F, stopping rule, support lists
+cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,
+                         StartState s, int *sup_idx, float *sup_val, Ctrl *ctrl_next,
+                         cudaStream_t st);
+
+// a7: Table 1 objective in FP64 for every start; u of each start into U
+// (partials: r * ceil(n / 256) * 2 doubles of scratch)
+cudaError_t launch_finalise(int form, const float *AT, int64_t ldat, int n, int p, const float *X,
+                            int64_t ldX, StartState s, int r, float *U, int64_t ldu,
+                            const int *sup_idx, const float *sup_val, int cap, double *partials,
+                            cudaStream_t st);
+// argmax over starts (ties: lower index), then y(x) and the support of the best start
+cudaError_t launch_best(int form, int use_ev, StartState s, int r, int *best, cudaStream_t st);
+cudaError_t launch_best_outputs(int form, const int *best, const float *U, int64_t ldu, int n,
+                                const float *X, int64_t ldX, int p, float *y_out, float *x_out,
+                                int64_t *support_out, int64_t *nnz_out, cudaStream_t st);
+
+}  // namespace spca

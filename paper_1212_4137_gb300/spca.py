@@ -1,0 +1,222 @@
+"""Thin ctypes binding of libspca.so with the names of include/spca.h.
+
+Only argument marshalling lives here: every step of the solve runs in the library's CUDA
+kernels.  ``load()`` raises if the library is missing or no GPU is usable; there is no CPU
+fallback.  Device buffers are passed as integer addresses (e.g. ``tensor.data_ptr()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspca.so")
+
+SPCA_OK, SPCA_E_INVALID, SPCA_E_NOMEM, SPCA_E_CUDA, SPCA_E_TIMEOUT, SPCA_E_BUSY, SPCA_E_UNSUPPORTED = range(7)
+SPCA_F32, SPCA_F64, SPCA_BF16, SPCA_FP8_E4M3_COLSCALED = range(4)
+SPCA_GAMMA_FIXED, SPCA_GAMMA_TARGET_NNZ = 0, 1
+SPCA_ST_MAXITER, SPCA_ST_CONVERGED, SPCA_ST_DEGENERATE = 0, 1, 2
+SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC = 0, 1, 2
+
+# every symbol include/spca.h declares
+EXPORTS = ("spca_create", "spca_solve", "spca_xstep", "spca_profile_enable", "spca_profile_query",
+           "spca_destroy", "spca_strerror", "spca_last_error")
+SPCA_K_ALL, SPCA_K_INIT, SPCA_K_U_DENSE, SPCA_K_U_SPARSE, SPCA_K_YSTEP, SPCA_K_V, SPCA_K_XSTEP, \
+    SPCA_K_FINALISE, SPCA_K_PREP = range(-1, 8)
+KERNEL_NAMES = {SPCA_K_INIT: "init", SPCA_K_U_DENSE: "u_dense", SPCA_K_U_SPARSE: "u_sparse",
+                SPCA_K_YSTEP: "ystep", SPCA_K_V: "v", SPCA_K_XSTEP: "xstep",
+                SPCA_K_FINALISE: "finalise", SPCA_K_PREP: "prep"}
+
+
+class spca_params(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int), ("s", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("gamma_mode", ctypes.c_int), ("gamma_calib_sweeps", ctypes.c_int),
+                ("r", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("x0_is_device", ctypes.c_int), ("engine", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+_fp = ctypes.POINTER(ctypes.c_float)
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class spca_result(ctypes.Structure):
+    _fields_ = [("objective", ctypes.c_double), ("explained_variance", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("best_start", ctypes.c_int), ("best_iters", ctypes.c_int),
+                ("best_status", ctypes.c_int), ("converged", ctypes.c_int), ("degenerate", ctypes.c_int),
+                ("sweeps_total", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("x", _fp), ("y", _fp), ("support", _i64p), ("start_objective", _dp),
+                ("start_explained", _dp), ("start_F", _dp), ("start_iters", _ip),
+                ("start_status", _ip), ("start_gamma", _dp), ("start_x", _fp)]
+
+
+class SpcaError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: status {status}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libspca.so; raises if it is missing (build it with paper_1212_4137_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libspca.so not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        lib.spca_create.restype = ctypes.c_int
+        lib.spca_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int64,
+                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_void_p]
+        lib.spca_solve.restype = ctypes.c_int
+        lib.spca_solve.argtypes = [ctypes.c_void_p, ctypes.POINTER(spca_params), ctypes.c_void_p,
+                                   ctypes.POINTER(spca_result)]
+        lib.spca_xstep.restype = ctypes.c_int
+        lib.spca_xstep.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]
+        lib.spca_profile_enable.restype = ctypes.c_int
+        lib.spca_profile_enable.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.spca_profile_query.restype = ctypes.c_int
+        lib.spca_profile_query.argtypes = [ctypes.c_void_p, ctypes.c_int, _i64p, _dp]
+        lib.spca_destroy.restype = None
+        lib.spca_destroy.argtypes = [ctypes.c_void_p]
+        lib.spca_strerror.restype = ctypes.c_char_p
+        lib.spca_strerror.argtypes = [ctypes.c_int]
+        lib.spca_last_error.restype = ctypes.c_char_p
+        lib.spca_last_error.argtypes = [ctypes.c_void_p]
+        _lib = lib
+    return _lib
+
+
+def spca_strerror(status: int) -> str:
+    return load().spca_strerror(int(status)).decode()
+
+
+def spca_last_error(h) -> str:
+    return load().spca_last_error(h).decode()
+
+
+def _check(status: int, what: str, h=None):
+    if status != SPCA_OK:
+        detail = spca_last_error(h) if h else ""
+        raise SpcaError(status, f"{what} failed: {spca_strerror(status)} {detail}".strip())
+
+
+def spca_create(A, n: int, p: int, lda: int, in_dtype: int, a_is_device: bool, storage: int = SPCA_F32,
+                stream: int = 0):
+    """A: host numpy array (C-contiguous) or a device address (int)."""
+    h = ctypes.c_void_p()
+    ptr = A if isinstance(A, int) else A.ctypes.data
+    st = load().spca_create(ctypes.byref(h), ctypes.c_void_p(ptr), n, p, lda, in_dtype,
+                            int(a_is_device), storage, ctypes.c_void_p(stream))
+    return st, h
+
+
+def spca_solve(h, params: spca_params, x0, result: spca_result) -> int:
+    ptr = None if x0 is None else (x0 if isinstance(x0, int) else x0.ctypes.data)
+    return load().spca_solve(h, ctypes.byref(params), ctypes.c_void_p(ptr) if ptr else None,
+                             ctypes.byref(result))
+
+
+def spca_xstep(h, form, s, gamma, calibrate, V, ldv, r, X, ldx, F, nnz, thr) -> int:
+    return load().spca_xstep(h, int(form), float(s), float(gamma), int(calibrate), ctypes.c_void_p(V),
+                             ldv, r, ctypes.c_void_p(X), ldx, ctypes.c_void_p(F), ctypes.c_void_p(nnz),
+                             ctypes.c_void_p(thr))
+
+
+def spca_profile_enable(h, on: bool) -> int:
+    return load().spca_profile_enable(h, int(on))
+
+
+def spca_profile_query(h, kernel: int):
+    """(status, launches, ms)"""
+    n = ctypes.c_int64()
+    t = ctypes.c_double()
+    st = load().spca_profile_query(h, int(kernel), ctypes.byref(n), ctypes.byref(t))
+    return st, n.value, t.value
+
+
+def spca_destroy(h) -> None:
+    if h:
+        load().spca_destroy(h)
+
+
+# ------------------------------------------------------------------ convenience wrappers
+class Handle:
+    """Owns an spca_handle; A is host numpy (float32/float64) or a torch CUDA tensor."""
+
+    def __init__(self, A, stream: int = 0):
+        try:
+            import torch
+            is_tensor = isinstance(A, torch.Tensor)
+        except ImportError:  # pragma: no cover
+            is_tensor = False
+        if is_tensor:
+            assert A.is_cuda and A.dim() == 2 and A.stride(1) == 1
+            dt = {"torch.float32": SPCA_F32, "torch.float64": SPCA_F64}[str(A.dtype)]
+            n, p = A.shape
+            st, h = spca_create(A.data_ptr(), n, p, A.stride(0), dt, True, SPCA_F32, stream)
+        else:
+            A = np.ascontiguousarray(A)
+            dt = SPCA_F64 if A.dtype == np.float64 else SPCA_F32
+            if A.dtype not in (np.float32, np.float64):
+                A = A.astype(np.float32)
+            n, p = A.shape
+            st, h = spca_create(A, n, p, p, dt, False, SPCA_F32, stream)
+        _check(st, "spca_create")
+        self.h, self.n, self.p = h, n, p
+
+    def profile(self, on: bool):
+        _check(spca_profile_enable(self.h, on), "spca_profile_enable", self.h)
+
+    def profile_query(self, kernel: int):
+        st, n, ms = spca_profile_query(self.h, kernel)
+        _check(st, "spca_profile_query", self.h)
+        return n, ms
+
+    def close(self):
+        if self.h:
+            spca_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, form, r, s=1.0, gamma=0.0, gamma_target=False, calib=10, max_iter=100,
+              tol=1e-9, x0=None, seed=0, engine=SPCA_ENGINE_AUTO, want_starts=False, x0_device=False):
+        """Returns a dict of numpy results.  x0: r x p float32 host array, device address
+        (x0_device=True), or None for seeded starts."""
+        prm = spca_params(form=form, s=s, gamma=gamma,
+                          gamma_mode=SPCA_GAMMA_TARGET_NNZ if gamma_target else SPCA_GAMMA_FIXED,
+                          gamma_calib_sweeps=calib, r=r, max_iter=max_iter, tol=tol, seed=seed,
+                          x0_is_device=int(x0_device), engine=engine)
+        n, p = self.n, self.p
+        out = {"x": np.zeros(p, np.float32), "y": np.zeros(n, np.float32),
+               "support": np.zeros(p, np.int64)}
+        if want_starts:
+            out.update(start_objective=np.zeros(r), start_explained=np.zeros(r), start_F=np.zeros(r),
+                       start_iters=np.zeros(r, np.int32), start_status=np.zeros(r, np.int32),
+                       start_gamma=np.zeros(r), start_x=np.zeros((r, p), np.float32))
+        res = spca_result()
+        for k, v in out.items():
+            setattr(res, k, v.ctypes.data_as(type(getattr(res, k))))
+        if x0 is not None and not x0_device:
+            x0 = np.ascontiguousarray(x0, dtype=np.float32)
+            assert x0.shape == (r, p)
+        _check(spca_solve(self.h, prm, x0, res), "spca_solve", self.h)
+        out["support"] = out["support"][:res.nnz]
+        for k in ("objective", "explained_variance", "gamma", "best_start", "best_iters", "best_status",
+                  "converged", "degenerate", "sweeps_total", "nnz"):
+            out[k] = getattr(res, k)
+        return out

@@ -1,0 +1,81 @@
+"""CPU-side checks of the boundary: the library builds for sm_103a, loads, and exports every
+symbol include/spca.h declares; the ctypes structures match the header's field order; and
+without a GPU the calls fail loudly instead of falling back to the CPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "spca.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spca_[a-z_0-9]+)\s*\(", text)))
+
+
+def _struct_fields(name):
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + ";", text).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            m = re.search(r"\**\s*([A-Za-z_][A-Za-z_0-9]*)\s*(\[\d+\])?\s*$", part.strip())
+            fields.append(m.group(1))
+    return fields
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1212_4137_gb300 import build, spca
+    build.build()
+    return spca
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared_functions()
+    assert set(declared) == set(lib.EXPORTS)
+    so = lib.load()
+    for name in declared:
+        assert hasattr(so, name), name
+
+
+def test_struct_layout_matches_header(lib):
+    assert [f for f, _ in lib.spca_params._fields_] == _struct_fields("spca_params")
+    assert [f for f, _ in lib.spca_result._fields_] == _struct_fields("spca_result")
+
+
+def test_strerror_is_static_text(lib):
+    assert lib.spca_strerror(0) == "ok"
+    assert lib.spca_strerror(1) == "invalid argument"
+    assert lib.spca_strerror(12345) == "unknown status"
+
+
+def test_bad_arguments_rejected_before_device(lib):
+    so = lib.load()
+    h = ctypes.c_void_p()
+    A = np.zeros((2, 3), np.float32)
+    for (n, p, lda, dt) in ((0, 3, 3, 0), (2, 0, 3, 0), (2, 3, 2, 0), (2, 3, 3, 7)):
+        st = so.spca_create(ctypes.byref(h), ctypes.c_void_p(A.ctypes.data), n, p, lda, dt, 0, 0, None)
+        assert st == lib.SPCA_E_INVALID
+    st = so.spca_create(ctypes.byref(h), None, 2, 3, 3, 0, 0, 0, None)
+    assert st == lib.SPCA_E_INVALID
+    st = so.spca_create(ctypes.byref(h), ctypes.c_void_p(A.ctypes.data), 2, 3, 3, 0, 0, lib.SPCA_BF16, None)
+    assert st == lib.SPCA_E_UNSUPPORTED
+    assert so.spca_solve(None, None, None, None) == lib.SPCA_E_INVALID
+    so.spca_destroy(None)
+
+
+def test_no_gpu_fails_loudly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st, h = lib.spca_create(np.zeros((2, 3), np.float32), 2, 3, 3, lib.SPCA_F32, False)
+    assert st == lib.SPCA_E_CUDA
