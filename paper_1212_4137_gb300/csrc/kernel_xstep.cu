@@ -99,17 +99,17 @@ __device__ double lambda_s_bisect(const float *__restrict__ v, int p, double s, 
   int kc = 0;
   double s1 = 0.0, s2 = 0.0;
   {
-    float f1 = 0.0f, f2 = 0.0f;
+    double d1 = 0.0, d2 = 0.0;
     for (int i = threadIdx.x; i < p; i += blockDim.x) {
       const float a = fabsf(v[i]);
       if (__float_as_uint(a) > lo) {
         ++kc;
-        f1 += a;
-        f2 = fmaf(a, a, f2);
+        d1 += (double)a;
+        d2 = fma((double)a, (double)a, d2);
       }
     }
-    s1 = block_sum_d((double)f1, sh.red_d);
-    s2 = block_sum_d((double)f2, sh.red_d);
+    s1 = block_sum_d(d1, sh.red_d);
+    s2 = block_sum_d(d2, sh.red_d);
     kc = block_sum_i(kc, sh.red_i);
   }
   const double k = (double)kc;

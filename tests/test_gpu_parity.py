@@ -109,8 +109,11 @@ def test_small_dense_case_form1(lib, oracle):
     out = h.solve(1, 16, s=10, max_iter=100, tol=1e-9, x0=G.astype(np.float32), want_starts=True)
     ref = _oracle_solve(oracle, A, 1, G.astype(np.float32).astype(np.float64), dict(s=10), 100, 1e-9)
     _compare_solve(oracle, A, out, ref, 1)
-    assert out["best_start"] == ref.best
-    assert np.array_equal(out["support"], np.flatnonzero(ref.X[ref.best]))
+    # several starts may reach the same stationary point: the GPU's best start must be one
+    # whose oracle objective is the maximum, and its support must be that start's support
+    b = out["best_start"]
+    assert abs(ref.f[b] - ref.f[ref.best]) <= OBJ_RTOL * ref.f[ref.best]
+    assert np.array_equal(out["support"], np.flatnonzero(ref.X[b]))
     h.close()
 
 
