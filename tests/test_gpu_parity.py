@@ -70,21 +70,24 @@ def test_xstep_matches_oracle(lib, oracle, form, p):
 
 
 # ------------------------------------------------------------------ whole solves
-def _compare_solve(oracle, A64, out, ref, form, tol_frac=0.95):
+def _compare_solve(oracle, A64, out, ref, form, tol_frac=0.95, x_atol=X_ATOL):
+    """Per-start comparison of a whole solve.  At least tol_frac of the starts must match the
+    oracle outright (objective within OBJ_RTOL, x within x_atol).  A start that does not
+    match and that stopped by the stopping rule must be a fixed point of the FP64 map at FP32
+    resolution (it converged to another stationary point); a start still moving at max_iter
+    only counts against tol_frac (single sweeps are checked on their own elsewhere)."""
     r = ref.X.shape[0]
     gx = out["start_x"].astype(np.float64)
     match = 0
     for c in range(r):
         fo, fg = ref.f[c], out["start_objective"][c]
-        same = (abs(fg - fo) <= OBJ_RTOL * max(1.0, abs(fo)) and np.abs(gx[c] - ref.X[c]).max() <= X_ATOL)
+        same = (abs(fg - fo) <= OBJ_RTOL * max(1.0, abs(fo)) and np.abs(gx[c] - ref.X[c]).max() <= x_atol)
         if same:
             match += 1
             continue
-        # a different stationary point: the GPU's x must be a fixed point of the FP64 map
-        one = oracle.solve(A64, form, gx[c:c + 1], max_iter=1, tol=-1, **ref.kw)
-        if ref.kw.get("gamma_target"):
-            pytest.skip("per-start gammas differ between the two runs")
-        assert np.abs(one.X[0] - gx[c]).max() <= 10 * X_ATOL, ("not stationary", c)
+        if out["start_status"][c] == 1 and not ref.kw.get("gamma_target"):
+            one = oracle.solve(A64, form, gx[c:c + 1], max_iter=1, tol=-1, **ref.kw)
+            assert np.abs(one.X[0] - gx[c]).max() <= 10 * X_ATOL, ("not stationary", c)
     assert match >= tol_frac * r, (match, r)
     bo, bg = ref.f[ref.best], out["objective"]
     assert abs(bg - bo) <= OBJ_RTOL * max(1.0, abs(bo)), (bg, bo)
@@ -108,7 +111,11 @@ def test_small_dense_case_form1(lib, oracle):
     h = lib.Handle(A)
     out = h.solve(1, 16, s=10, max_iter=100, tol=1e-9, x0=G.astype(np.float32), want_starts=True)
     ref = _oracle_solve(oracle, A, 1, G.astype(np.float32).astype(np.float64), dict(s=10), 100, 1e-9)
-    _compare_solve(oracle, A, out, ref, 1)
+    # tol = 1e-9 is below the FP32 resolution of F (~1e-7): the FP32 path stops when F stops
+    # rising at its precision, a few sweeps before the FP64 oracle; F converges quadratically in
+    # x, so x then agrees to ~1e-4..1e-3 while the objective agrees to ~1e-7.  The x <= 1e-4
+    # bar is checked on fixed sweep counts (test_spiked_all_forms_fixed_sweeps).
+    _compare_solve(oracle, A, out, ref, 1, x_atol=1e-3)
     # several starts may reach the same stationary point: the GPU's best start must be one
     # whose oracle objective is the maximum, and its support must be that start's support
     b = out["best_start"]
@@ -149,6 +156,64 @@ def test_spiked_all_forms_fixed_sweeps(lib, oracle, spiked, form, target):
     assert np.all(out["start_status"] == ref.status)
     _compare_solve(oracle, A64, out, ref, form)
     h.close()
+
+
+def _near_tie(A64, form, xk, s, gamma, gap=1e-4):
+    """True if the hard selection of this sweep (top-s for T_s and the gamma-targeting
+    rule, v_i^2 > gamma for a fixed gamma) has a boundary gap below `gap` (relative)."""
+    if form in (3, 4, 7, 8) and gamma is None:
+        return False                       # soft thresholds are continuous in v
+    if form in (7, 8):
+        return False
+    u = A64 @ xk
+    y = np.where(u >= 0, 1.0, -1.0) if form % 2 == 0 else u / np.linalg.norm(u)
+    a = np.sort(np.abs(A64.T @ y))[::-1]
+    if gamma is not None:
+        return bool(np.min(np.abs(a * a - gamma)) <= gap * gamma)
+    return bool((a[s - 1] - a[s]) <= gap * a[s - 1])
+
+
+@pytest.mark.parametrize("form", range(1, 9))
+def test_single_sweep_parity(lib, oracle, spiked, form):
+    """One sweep of the GPU from its own iterate x^(k) against one FP64 oracle sweep from the
+    same x^(k): isolates the arithmetic of a sweep from trajectory drift.  Penalty forms run
+    in gamma-targeting mode (C = 5): sweeps k+1 <= C re-target, later ones use the start's
+    frozen gamma."""
+    A = spiked
+    A64 = A.astype(np.float64)
+    n, p = A.shape
+    r, C = 40, 5
+    G = I.raw_starts(p, r, 19).astype(np.float32)
+    kw = _kw(form, 12 if form != 3 else 12.0, 0.0, True)
+    if form >= 5:
+        kw["calib"] = C
+    h = lib.Handle(A)
+    worst = 0.0
+    for k in (0, 3, 6, 15):
+        if k == 0:
+            Xk = G.astype(np.float64) / np.linalg.norm(G.astype(np.float64), axis=1, keepdims=True)
+            stat = np.full(r, lib.SPCA_ST_MAXITER)
+        else:
+            o = h.solve(form, r, max_iter=k, tol=-1, x0=G, want_starts=True, **kw)
+            Xk, stat = o["start_x"].astype(np.float64), o["start_status"]
+        o1 = h.solve(form, r, max_iter=k + 1, tol=-1, x0=G, want_starts=True, **kw)
+        for c in range(r):
+            if stat[c] == lib.SPCA_ST_DEGENERATE or o1["start_status"][c] == lib.SPCA_ST_DEGENERATE:
+                continue
+            okw = dict(kw)
+            if form >= 5 and k + 1 > C:
+                okw = dict(gamma=float(o1["start_gamma"][c]))
+            elif form >= 5:
+                okw["calib"] = 1
+            ref = oracle.solve(A64, form, Xk[c:c + 1], max_iter=1, tol=-1, **okw)
+            assert abs(o1["start_F"][c] - ref.F[0]) <= OBJ_RTOL * max(1.0, abs(ref.F[0])), (k, c)
+            if _near_tie(A64, form, Xk[c], 12, okw.get("gamma") if "gamma" in okw else None):
+                continue   # the selection boundary is within FP32 noise: either choice is correct
+            err = np.abs(o1["start_x"][c] - ref.X[0]).max()
+            worst = max(worst, err)
+            assert err <= X_ATOL, (form, k, c, err)
+    h.close()
+    print(f"form {form}: worst single-sweep |dx|_inf = {worst:.2e}")
 
 
 @pytest.mark.parametrize("form", [1, 4, 5, 8])
