@@ -209,6 +209,22 @@ int spca_xstep(spca_handle *h, int form, double s, double gamma, int calibrate,
                double *F, int *nnz, double *thr);
 
 /*
+ * spca_products -- the linear algebra of one sweep of Algorithm 2 for r given iterates, on
+ * the handle's stream, device memory only: u = A x (dense contraction), the y-step (S1 for
+ * L2 variance, S2 with sgn(0) = +1 for L1 variance, chosen by `form`), and v = A^T y.
+ * Exposed so that the contractions of each engine can be checked on their own.
+ *   form    Table 1 formulation (only its variance norm matters here).
+ *   engine  spca_engine.
+ *   X       device, r x p float iterates (ldx >= p).
+ *   U       device, r x n float output u = A x (ldu >= n).
+ *   V       device, r x p float output v = A^T y (ldv >= p); unspecified for a row whose
+ *           u is 0 under L2 variance.
+ * Errors: SPCA_E_INVALID, SPCA_E_UNSUPPORTED (engine), SPCA_E_NOMEM, SPCA_E_CUDA, SPCA_E_TIMEOUT.
+ */
+int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t ldx, int r,
+                  float *U, int64_t ldu, float *V, int64_t ldv);
+
+/*
  * Measurement hooks (not part of the method): per-kernel launch counts are always kept;
  * with profiling on, every launch is also bracketed by CUDA events on the handle's stream.
  *   spca_profile_enable  on != 0 starts timing (and clears the counters), 0 stops it.

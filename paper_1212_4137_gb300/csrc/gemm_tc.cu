@@ -1,0 +1,319 @@
+// gemm_tc.cu -- the two contractions of an AM sweep (u = A x, v = A^T y; Algorithm 2) on the
+// 5th-generation tensor cores (tcgen05, sm_103a): TMA loads into 128B-swizzled shared memory,
+// one elected thread issues tcgen05.mma with the accumulator in TMEM, four epilogue warps read
+// TMEM back with tcgen05.ld and store the result transposed (one start per output row).
+//
+// FP32 accuracy from BF16 tensor cores: every FP32 operand is stored as three BF16 planes
+// (hi = bf16(a), mid = bf16(a - hi), lo = a - hi - mid; hi + mid + lo == a exactly, since
+// each plane holds the next 8 significant bits).  A product sum a.b is then the sum over
+// plane pairs (i, j) of a_i . b_j, each term exact in the FP32 accumulator; the pairs with
+// i + j <= 2 carry everything above the 2^-24 relative level of FP32 (6 products for two
+// general operands, 3 when b is +-1 and has a single plane).
+//
+//   D[m, c] = sum_{(i,j) in pairs} sum_k P_i[m, k] Q_j[c, k]      out[c * ldo + m] = D[m, c]
+//
+// P (M x K) and Q (N x K) are K-contiguous BF16 planes; plane i of P starts at row i * M_alloc.
+// Tile 128 (M) x BN (N) x 64 (K); STAGES-deep TMA -> MMA pipeline over mbarriers.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "spca_internal.cuh"
+
+namespace spca {
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;                 // 64 bf16 = 128 B rows: one 128B swizzle atom wide
+constexpr int TC_THREADS = 192;           // warp 0 TMA + TMEM alloc, warp 1 MMA, warps 2-5 epilogue
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;   // bounded waits: 2 s, then error + exit
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for the phase with the given parity; false (and *err set) after TC_WAIT_NS
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > TC_WAIT_NS) {
+      *abort_flag = 1;
+      if (err) atomicExch(err, SPCA_E_TIMEOUT);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row core groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                      // descriptor version (tcgen05)
+  d |= (uint64_t)2 << 61;                      // swizzle: 128B
+  return d;
+}
+// instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, M = 128, N = BN
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+      "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+}  // namespace
+
+template <int BN, int NA, int NB, int STAGES>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int M, int N,
+              int kblocks, TcPairs pairs, float *__restrict__ out, int64_t ldo, const int *__restrict__ gate,
+              int *err) {
+  constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;       // 16 KB per P plane tile
+  constexpr uint32_t B_BYTES = BN * TC_BK * 2;          // 32 KB (BN = 256) per Q plane tile
+  constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
+  constexpr uint32_t TMEM_COLS = BN;                    // FP32 accumulator: BN columns x 128 lanes
+
+  extern __shared__ __align__(1024) uint8_t dsmem[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  if (gate && *gate == 0) return;   // uniform over the grid: the contraction is not needed
+
+  uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&accum_bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    for (int kb = 0; kb < kblocks; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, err, &abort_flag)) break;
+      const uint32_t fb = smem_u32(&full_bar[s]);
+      mbar_expect_tx(fb, STAGE_BYTES);
+      uint8_t *st = tiles + (size_t)s * STAGE_BYTES;
+#pragma unroll
+      for (int a = 0; a < NA; ++a) tma_load_3d(smem_u32(st + a * A_BYTES), &tmP, kb * TC_BK, m0, a, fb);
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        tma_load_3d(smem_u32(st + NA * A_BYTES + b * B_BYTES), &tmQ, kb * TC_BK, n0, b, fb);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
+    bool ok = true;
+    for (int kb = 0; kb < kblocks && ok; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(smem_u32(&full_bar[s]), ph, err, &abort_flag)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = smem_u32(tiles + (size_t)s * STAGE_BYTES);
+      for (int q = 0; q < pairs.n; ++q) {
+        const uint32_t a_base = st + pairs.a[q] * A_BYTES;
+        const uint32_t b_base = st + NA * A_BYTES + pairs.b[q] * B_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          mma_bf16(tmem, sw128_desc(a_base + kk * 32), sw128_desc(b_base + kk * 32), idesc,
+                   (kb | q | kk) != 0 ? 1u : 0u);
+        }
+      }
+      mma_commit(smem_u32(&empty_bar[s]));   // frees the stage once these MMAs have read it
+    }
+    if (ok) mma_commit(smem_u32(&accum_bar));  // accumulator complete
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------------- epilogue (TMEM -> HBM)
+    const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
+    if (mbar_wait(smem_u32(&accum_bar), 0, err, &abort_flag)) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = m0 + quad * 32 + lane;
+#pragma unroll 1
+      for (int cb = 0; cb < BN / 32; ++cb) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 32), v);
+        if (row < M) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + cb * 32 + j;
+            if (col < N) out[(int64_t)col * ldo + row] = v[j];
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------- planes
+// dst plane t (t < nplanes) of element e: the t-th BF16 piece of src (hi, mid, lo)
+__global__ void k_split_planes(const float *__restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                               __nv_bfloat16 *__restrict__ dst, int64_t ldd, int64_t plane_stride,
+                               int nplanes, const int *__restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e - r * cols;
+    float a = src[r * lds + c];
+    const int64_t o = r * ldd + c;
+    for (int t = 0; t < nplanes; ++t) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(a);
+      dst[o + t * plane_stride] = h;
+      a -= __bfloat162float(h);
+    }
+  }
+}
+
+cudaError_t launch_split_planes(const float *src, int64_t rows, int64_t cols, int64_t lds, void *dst,
+                                int64_t ldd, int64_t plane_stride, int nplanes, const int *gate,
+                                cudaStream_t st) {
+  k_split_planes<<<2 * 1216, 256, 0, st>>>(src, rows, cols, lds, static_cast<__nv_bfloat16 *>(dst), ldd,
+                                          plane_stride, nplanes, gate);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------- host side
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+}  // namespace
+
+// 3-D map over `planes` BF16 planes of `rows` x `ld` (K-contiguous), box 64 x box_rows x 1
+cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int64_t ld, int planes,
+                           int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * (cuuint64_t)rows};
+  cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+namespace {
+template <int BN, int NA, int NB, int STAGES>
+cudaError_t launch_tc_impl(const CUtensorMap &P, const CUtensorMap &Q, int M, int N, int K, TcPairs pairs,
+                           float *out, int64_t ldo, const int *gate, int *err, cudaStream_t st) {
+  constexpr int STAGE_BYTES = NA * TC_BM * TC_BK * 2 + NB * BN * TC_BK * 2;
+  constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  auto kern = k_gemm_tc<BN, NA, NB, STAGES>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + BN - 1) / BN));
+  const int kblocks = (K + TC_BK - 1) / TC_BK;
+  kern<<<grid, TC_THREADS, SMEM, st>>>(P, Q, M, N, kblocks, pairs, out, ldo, gate, err);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_gemm_tc(const CUtensorMap &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
+                           TcPairs pairs, float *out, int64_t ldo, const int *gate, int *err, cudaStream_t st) {
+  if (na == 3 && nb == 1)
+    return launch_tc_impl<256, 3, 1, 2>(P, Q, M, N, K, pairs, out, ldo, gate, err, st);
+  if (na == 3 && nb == 3)
+    return launch_tc_impl<128, 3, 3, 2>(P, Q, M, N, K, pairs, out, ldo, gate, err, st);
+  return cudaErrorInvalidValue;
+}
+
+int tc_box_rows(int nb) { return nb == 1 ? 256 : 128; }
+
+}  // namespace spca

@@ -1,6 +1,8 @@
 // kernels_simt.cu -- layout preparation, start initialisation, the y-step, and the FP32
 // CUDA-core contractions of one AM sweep (Algorithm 2): u = A x (dense or over the support of
 // x) and v = A^T y.
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 #include "block_util.cuh"
@@ -144,17 +146,25 @@ cudaError_t launch_start_init(const float *x0, int64_t ld0, uint64_t seed, int r
 // ------------------------------------------------------------------ y-step (Table 3 S1, S2)
 // Counts the sweep for every active start; L1 variance: y = sgn(u) with sgn(0) = +1;
 // L2 variance: y = u / ||u||_2, and ||u||_2 = 0 ends the start as degenerate (x = 0).
+// y goes to Y (FP32) and/or to BF16 planes (hi, mid, lo; a single exact plane for +-1).
 __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict__ U, int64_t ldu,
-                                               int n, float *__restrict__ Y, StartState s,
-                                               float *__restrict__ X, int64_t ldX, int p) {
+                                               int n, float *__restrict__ Y,
+                                               __nv_bfloat16 *__restrict__ Ypl, int64_t pstride,
+                                               StartState s, float *__restrict__ X, int64_t ldX,
+                                               int p) {
   __shared__ double red[32];
   const int c = blockIdx.x;
   if (s.status[c] != ST_ACTIVE) return;
   const float *u = U + (int64_t)c * ldu;
-  float *y = Y + (int64_t)c * ldu;
+  float *y = Y ? Y + (int64_t)c * ldu : nullptr;
+  __nv_bfloat16 *yp = Ypl ? Ypl + (int64_t)c * ldu : nullptr;
   if (threadIdx.x == 0) s.iters[c] += 1;
   if (is_l1_var(form)) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (u[i] >= 0.0f) ? 1.0f : -1.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float yi = (u[i] >= 0.0f) ? 1.0f : -1.0f;
+      if (y) y[i] = yi;
+      if (yp) yp[i] = __float2bfloat16_rn(yi);
+    }
     return;
   }
   double part = 0.0;
@@ -171,12 +181,25 @@ __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict
     return;
   }
   const float inv = (float)(1.0 / nrm);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = u[i] * inv;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float yi = u[i] * inv;
+    if (y) y[i] = yi;
+    if (yp) {
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(yi);
+        yp[i + t * pstride] = h;
+        yi -= __bfloat162float(h);
+      }
+    }
+  }
 }
 
-cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, float *Y, StartState s,
-                         float *X, int64_t ldX, int p, cudaStream_t st) {
-  k_ystep<<<r, 256, 0, st>>>(form, U, ldu, n, Y, s, X, ldX, p);
+cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, float *Y, void *Ypl,
+                         int64_t plane_stride, StartState s, float *X, int64_t ldX, int p,
+                         cudaStream_t st) {
+  k_ystep<<<r, 256, 0, st>>>(form, U, ldu, n, Y, static_cast<__nv_bfloat16 *>(Ypl), plane_stride, s,
+                             X, ldX, p);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
-// spca_api.cu -- the C ABI of include/spca.h: the handle (device copies of A), the solve
-// driver that runs Algorithm 2 for r starts as a sequence of kernels on one stream, and the
-// stand-alone x-step entry point.
+// spca_api.cu -- the C ABI of include/spca.h: the handle (device copies of A in the layouts
+// the kernels read), the solve driver that runs Algorithm 2 for r starts as a sequence of
+// kernels on one stream, and the step-level entry points (x-step, sweep products).
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,14 +13,19 @@ using namespace spca;
 
 struct spca_handle {
   int64_t n = 0, p = 0;
-  int64_t ldA = 0, ldAT = 0;  // padded leading dimensions of A32 (n x p) and AT32 (p x n)
+  int64_t ldA = 0, ldAT = 0;  // padded leading dimensions of A (n x p) and A^T (p x n)
   cudaStream_t stream = nullptr;
-  float *A32 = nullptr, *AT32 = nullptr;
+  float *A32 = nullptr, *AT32 = nullptr;   // FP32 copies
+  bool tc_ok = false;                      // the device has tcgen05 tensor cores (sm_100+)
+  void *Apl = nullptr, *ATpl = nullptr;    // 3 BF16 planes each (hi, mid, lo)
+  CUtensorMap tmA{}, tmAT{};               // P-operand maps of the planes (128-row boxes)
 
   // per-solve workspace, grown on demand
   int r_cap = 0;
   int64_t ldX = 0, ldU = 0;
   float *X = nullptr, *V = nullptr, *U = nullptr, *Y = nullptr;
+  void *Xpl = nullptr, *Ypl = nullptr;     // 3 BF16 planes each (tensor-core engine)
+  CUtensorMap tmX3{}, tmY1{}, tmY3{};      // Q-operand maps: X planes, y = +-1, y planes
   int *sup_idx = nullptr;
   float *sup_val = nullptr;
   int *status = nullptr, *iters = nullptr, *nnz = nullptr;
@@ -32,8 +37,9 @@ struct spca_handle {
   float *y_out = nullptr, *x_out = nullptr;
   int64_t *support_out = nullptr, *nnz_out = nullptr;
   int *flag = nullptr;        // device scratch flag
+  int *dev_err = nullptr;     // device error word written by kernels (SPCA_E_TIMEOUT)
   Ctrl *h_ctrl = nullptr;     // pinned host mirror
-  int *h_flag = nullptr;      // pinned host mirror
+  int *h_flag = nullptr;      // pinned host mirror (2 ints)
 
   // measurement hooks: launch counts, and event pairs per kernel id while profiling is on
   bool prof_on = false;
@@ -52,12 +58,18 @@ int fail(spca_handle *h, int code, const char *fmt, const char *detail = "") {
   return code;
 }
 
-#define CK(expr)                                                               \
-  do {                                                                         \
-    cudaError_t e_ = (expr);                                                   \
-    if (e_ != cudaSuccess)                                                     \
-      return fail(h, e_ == cudaErrorMemoryAllocation ? SPCA_E_NOMEM : SPCA_E_CUDA, \
-                  "CUDA error: %s", cudaGetErrorString(e_));                   \
+#define CK(expr)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (expr);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? SPCA_E_NOMEM : SPCA_E_CUDA,   \
+                  "CUDA error: %s", cudaGetErrorString(e_));                         \
+  } while (0)
+
+#define RC(expr)                  \
+  do {                            \
+    int rc_ = (expr);             \
+    if (rc_ != SPCA_OK) return rc_; \
   } while (0)
 
 cudaEvent_t get_event(spca_handle *h) {
@@ -72,8 +84,8 @@ cudaEvent_t get_event(spca_handle *h) {
 }
 
 // runs `launch` (which enqueues `nk` kernels of kind `kid`), counting and optionally timing it
-template <typename F>
-cudaError_t timed(spca_handle *h, int kid, int nk, F &&launch) {
+template <typename Fn>
+cudaError_t timed(spca_handle *h, int kid, int nk, Fn &&launch) {
   h->launches[kid] += nk;
   if (!h->prof_on) return launch();
   cudaEvent_t a = get_event(h), b = get_event(h);
@@ -101,17 +113,18 @@ cudaError_t drain_profile(spca_handle *h) {
 }
 
 template <typename T>
-cudaError_t dalloc(T **p, size_t count) {
-  return cudaMalloc((void **)p, count * sizeof(T) + 16);
+cudaError_t dalloc(T **p, size_t count, size_t elem = sizeof(T)) {
+  return cudaMalloc((void **)p, count * elem + 16);
 }
 
 void free_workspace(spca_handle *h) {
-  void *ptrs[] = {h->X, h->V, h->U, h->Y, h->sup_idx, h->sup_val, h->status, h->iters, h->nnz,
-                  h->F, h->F_prev, h->gamma, h->f, h->ev, h->thr, h->partials, h->ctrl, h->best,
+  void *ptrs[] = {h->X, h->V, h->U, h->Y, h->Xpl, h->Ypl, h->sup_idx, h->sup_val, h->status, h->iters,
+                  h->nnz, h->F, h->F_prev, h->gamma, h->f, h->ev, h->thr, h->partials, h->ctrl, h->best,
                   h->y_out, h->x_out, h->support_out, h->nnz_out};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   h->X = h->V = h->U = h->Y = nullptr;
+  h->Xpl = h->Ypl = nullptr;
   h->sup_idx = nullptr; h->sup_val = nullptr;
   h->status = h->iters = h->nnz = nullptr;
   h->F = h->F_prev = h->gamma = h->f = h->ev = nullptr;
@@ -145,6 +158,15 @@ int ensure_workspace(spca_handle *h, int r) {
   CK(cudaMemsetAsync(h->V, 0, (size_t)r * h->ldX * sizeof(float), h->stream));
   CK(cudaMemsetAsync(h->U, 0, (size_t)r * h->ldU * sizeof(float), h->stream));
   CK(cudaMemsetAsync(h->Y, 0, (size_t)r * h->ldU * sizeof(float), h->stream));
+  if (h->tc_ok) {
+    CK(dalloc(&h->Xpl, (size_t)3 * r * h->ldX, 2));
+    CK(dalloc(&h->Ypl, (size_t)3 * r * h->ldU, 2));
+    CK(cudaMemsetAsync(h->Xpl, 0, (size_t)3 * r * h->ldX * 2, h->stream));
+    CK(cudaMemsetAsync(h->Ypl, 0, (size_t)3 * r * h->ldU * 2, h->stream));
+    CK(make_plane_map(&h->tmX3, h->Xpl, r, h->ldX, 3, tc_box_rows(3)));
+    CK(make_plane_map(&h->tmY1, h->Ypl, r, h->ldU, 1, tc_box_rows(1)));
+    CK(make_plane_map(&h->tmY3, h->Ypl, r, h->ldU, 3, tc_box_rows(3)));
+  }
   h->r_cap = r;
   return SPCA_OK;
 }
@@ -178,6 +200,86 @@ int check_form_params(spca_handle *h, int form, double s, double gamma, int gamm
     if (gamma_mode == SPCA_GAMMA_FIXED && gamma < 0.0) return fail(h, SPCA_E_INVALID, "gamma must be >= 0%s");
     if (gamma_mode == SPCA_GAMMA_TARGET_NNZ && (s < 1.0 || s > (double)p || s != std::floor(s)))
       return fail(h, SPCA_E_INVALID, "target mode: s must be an integer in [1, p]%s");
+  }
+  return SPCA_OK;
+}
+
+int resolve_engine(spca_handle *h, int engine, int *out) {
+  if (engine != SPCA_ENGINE_AUTO && engine != SPCA_ENGINE_SIMT && engine != SPCA_ENGINE_TC)
+    return fail(h, SPCA_E_INVALID, "unknown engine%s");
+  if (engine == SPCA_ENGINE_TC && !h->tc_ok)
+    return fail(h, SPCA_E_UNSUPPORTED, "tensor-core engine needs an sm_100+ device%s");
+  *out = engine == SPCA_ENGINE_AUTO ? (h->tc_ok ? SPCA_ENGINE_TC : SPCA_ENGINE_SIMT) : engine;
+  return SPCA_OK;
+}
+
+// plane products of the two contractions (smaller terms first): with three planes on both
+// sides every pair with i + j <= 2; with y = +-1 (one exact plane) the three pairs (i, 0)
+TcPairs pairs_general() {
+  TcPairs q{};
+  const unsigned char a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
+  q.n = 6;
+  for (int i = 0; i < 6; ++i) { q.a[i] = a[i]; q.b[i] = b[i]; }
+  return q;
+}
+TcPairs pairs_sign() {
+  TcPairs q{};
+  q.n = 3;
+  q.a[0] = 2; q.a[1] = 1; q.a[2] = 0;
+  return q;
+}
+
+// u = A x for every row of h->X: dense contraction (gated: runs only if *gate != 0)
+int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate) {
+  const int n = (int)h->n, p = (int)h->p;
+  cudaStream_t st = h->stream;
+  if (engine == SPCA_ENGINE_TC) {
+    CK(timed(h, SPCA_K_U_DENSE, 2, [&] {
+      cudaError_t e = launch_split_planes(h->X, r, p, h->ldX, h->Xpl, h->ldX, (int64_t)h->r_cap * h->ldX, 3,
+                                          gate, st);
+      if (e != cudaSuccess) return e;
+      return launch_gemm_tc(h->tmA, 3, h->tmX3, 3, n, r, p, pairs_general(), h->U, h->ldU, gate, h->dev_err, st);
+    }));
+  } else {
+    CK(timed(h, SPCA_K_U_DENSE, 1, [&] {
+      return launch_gemm_nt_f32(h->X, h->ldX, h->A32, h->ldA, h->U, h->ldU, r, n, (int)h->ldX, gate, st);
+    }));
+  }
+  return SPCA_OK;
+}
+
+// y-step and v = A^T y for every active row
+int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S) {
+  const int n = (int)h->n, p = (int)h->p;
+  cudaStream_t st = h->stream;
+  const bool tc = engine == SPCA_ENGINE_TC;
+  const int64_t ypstride = (int64_t)h->r_cap * h->ldU;
+  CK(timed(h, SPCA_K_YSTEP, 1, [&] {
+    return launch_ystep(form, h->U, h->ldU, n, r, tc ? nullptr : h->Y, tc ? h->Ypl : nullptr, ypstride, S,
+                        h->X, h->ldX, p, st);
+  }));
+  if (tc) {
+    const bool l1 = is_l1_var(form);
+    CK(timed(h, SPCA_K_V, 1, [&] {
+      return launch_gemm_tc(h->tmAT, 3, l1 ? h->tmY1 : h->tmY3, l1 ? 1 : 3, p, r, n,
+                            l1 ? pairs_sign() : pairs_general(), h->V, h->ldX, nullptr, h->dev_err, st);
+    }));
+  } else {
+    CK(timed(h, SPCA_K_V, 1, [&] {
+      return launch_gemm_nt_f32(h->Y, h->ldU, h->AT32, h->ldAT, h->V, h->ldX, r, p, (int)h->ldU, nullptr, st);
+    }));
+  }
+  return SPCA_OK;
+}
+
+int read_dev_err(spca_handle *h) {
+  CK(cudaMemcpyAsync(h->h_flag + 1, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->h_flag[1] != 0) {
+    const int code = h->h_flag[1];
+    h->h_flag[1] = 0;
+    cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream);
+    return fail(h, code, "a device-side wait timed out%s");
   }
   return SPCA_OK;
 }
@@ -234,9 +336,9 @@ void spca_destroy(spca_handle *h) {
   drain_profile(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   free_workspace(h);
-  if (h->A32) cudaFree(h->A32);
-  if (h->AT32) cudaFree(h->AT32);
-  if (h->flag) cudaFree(h->flag);
+  void *ptrs[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->flag, h->dev_err};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
   if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
   if (h->h_flag) cudaFreeHost(h->h_flag);
   delete h;
@@ -253,8 +355,9 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
       return SPCA_E_UNSUPPORTED;
     return SPCA_E_INVALID;
   }
-  int ndev = 0;
+  int ndev = 0, dev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SPCA_E_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPCA_E_CUDA;
   h = new (std::nothrow) spca_handle();
   if (!h) return SPCA_E_NOMEM;
   int rc = [&]() -> int {
@@ -262,17 +365,23 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     h->stream = (cudaStream_t)cuda_stream;
     h->ldA = pad_ld(p);
     h->ldAT = pad_ld(n);
+    int major = 0;
+    CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+    h->tc_ok = major >= 10;
     CK(cudaMallocHost((void **)&h->h_ctrl, 2 * sizeof(Ctrl)));
-    CK(cudaMallocHost((void **)&h->h_flag, sizeof(int)));
+    CK(cudaMallocHost((void **)&h->h_flag, 2 * sizeof(int)));
+    h->h_flag[0] = h->h_flag[1] = 0;
     CK(dalloc(&h->flag, 1));
+    CK(dalloc(&h->dev_err, 1));
+    CK(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
     CK(dalloc(&h->A32, (size_t)n * h->ldA));
     CK(dalloc(&h->AT32, (size_t)p * h->ldAT));
     CK(cudaMemsetAsync(h->A32, 0, (size_t)n * h->ldA * sizeof(float), h->stream));
     CK(cudaMemsetAsync(h->AT32, 0, (size_t)p * h->ldAT * sizeof(float), h->stream));
     const cudaMemcpyKind kind = a_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (in_dtype == SPCA_F32) {
-      CK(cudaMemcpy2DAsync(h->A32, h->ldA * sizeof(float), A, lda * sizeof(float), p * sizeof(float),
-                           n, kind, h->stream));
+      CK(cudaMemcpy2DAsync(h->A32, h->ldA * sizeof(float), A, lda * sizeof(float), p * sizeof(float), n, kind,
+                           h->stream));
     } else {
       double *tmp = nullptr;
       CK(dalloc(&tmp, (size_t)n * lda));
@@ -285,7 +394,21 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     CK(timed(h, SPCA_K_PREP, 1, [&] { return launch_check_finite(h->A32, n, p, h->ldA, h->flag, h->stream); }));
     CK(cudaMemcpyAsync(h->h_flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CK(timed(h, SPCA_K_PREP, 1, [&] { return launch_transpose_f32(h->A32, n, p, h->ldA, h->AT32, h->ldAT, h->stream); }));
+    CK(timed(h, SPCA_K_PREP, 1,
+             [&] { return launch_transpose_f32(h->A32, n, p, h->ldA, h->AT32, h->ldAT, h->stream); }));
+    if (h->tc_ok) {
+      CK(dalloc(&h->Apl, (size_t)3 * n * h->ldA, 2));
+      CK(dalloc(&h->ATpl, (size_t)3 * p * h->ldAT, 2));
+      CK(timed(h, SPCA_K_PREP, 2, [&] {
+        cudaError_t e = launch_split_planes(h->A32, n, h->ldA, h->ldA, h->Apl, h->ldA, n * h->ldA, 3, nullptr,
+                                            h->stream);
+        if (e != cudaSuccess) return e;
+        return launch_split_planes(h->AT32, p, h->ldAT, h->ldAT, h->ATpl, h->ldAT, p * h->ldAT, 3, nullptr,
+                                   h->stream);
+      }));
+      CK(make_plane_map(&h->tmA, h->Apl, n, h->ldA, 3, 128));
+      CK(make_plane_map(&h->tmAT, h->ATpl, p, h->ldAT, 3, 128));
+    }
     CK(cudaStreamSynchronize(h->stream));
     if (*h->h_flag) return fail(h, SPCA_E_INVALID, "A has a non-finite entry%s");
     return SPCA_OK;
@@ -298,13 +421,11 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
   return SPCA_OK;
 }
 
-int spca_xstep(spca_handle *h, int form, double s, double gamma, int calibrate, const float *V,
-               int64_t ldv, int r, float *X, int64_t ldx, double *F, int *nnz, double *thr) {
+int spca_xstep(spca_handle *h, int form, double s, double gamma, int calibrate, const float *V, int64_t ldv,
+               int r, float *X, int64_t ldx, double *F, int *nnz, double *thr) {
   if (!h || !V || !X || !F || !nnz || !thr || r < 1) return fail(h, SPCA_E_INVALID, "bad argument%s");
   if (ldv < h->p || ldx < h->p) return fail(h, SPCA_E_INVALID, "leading dimension < p%s");
-  int rc = check_form_params(h, form, s, gamma,
-                             calibrate ? SPCA_GAMMA_TARGET_NNZ : SPCA_GAMMA_FIXED, h->p);
-  if (rc != SPCA_OK) return rc;
+  RC(check_form_params(h, form, s, gamma, calibrate ? SPCA_GAMMA_TARGET_NNZ : SPCA_GAMMA_FIXED, h->p));
   XstepArgs a{};
   a.form = form; a.p = (int)h->p; a.s = s;
   a.calibrate = is_pen(form) && calibrate;
@@ -321,36 +442,52 @@ int spca_xstep(spca_handle *h, int form, double s, double gamma, int calibrate, 
   return SPCA_OK;
 }
 
+int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t ldx, int r, float *U,
+                  int64_t ldu, float *V, int64_t ldv) {
+  if (!h || !X || !U || !V || r < 1) return fail(h, SPCA_E_INVALID, "bad argument%s");
+  if (form < 1 || form > 8) return fail(h, SPCA_E_INVALID, "form must be 1..8%s");
+  if (ldx < h->p || ldv < h->p || ldu < h->n) return fail(h, SPCA_E_INVALID, "leading dimension too small%s");
+  int eng;
+  RC(resolve_engine(h, engine, &eng));
+  RC(ensure_workspace(h, r));
+  const int n = (int)h->n, p = (int)h->p;
+  cudaStream_t st = h->stream;
+  CK(cudaMemcpy2DAsync(h->X, h->ldX * sizeof(float), X, ldx * sizeof(float), (size_t)p * sizeof(float), r,
+                       cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(h->status, 0xFF, (size_t)r * sizeof(int), st));   // every row active (-1)
+  CK(cudaMemsetAsync(h->iters, 0, (size_t)r * sizeof(int), st));
+  RC(sweep_u_dense(h, eng, r, nullptr));
+  RC(sweep_y_v(h, eng, form, r, state_of(h)));
+  CK(cudaMemcpy2DAsync(U, ldu * sizeof(float), h->U, h->ldU * sizeof(float), (size_t)n * sizeof(float), r,
+                       cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpy2DAsync(V, ldv * sizeof(float), h->V, h->ldX * sizeof(float), (size_t)p * sizeof(float), r,
+                       cudaMemcpyDeviceToDevice, st));
+  RC(read_dev_err(h));
+  return SPCA_OK;
+}
+
 int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_result *res) {
   if (!h || !prm || !res) return fail(h, SPCA_E_INVALID, "NULL argument%s");
   const spca_params P = *prm;
   const int form = P.form;
-  int rc = check_form_params(h, form, P.s, P.gamma, P.gamma_mode, h->p);
-  if (rc != SPCA_OK) return rc;
+  RC(check_form_params(h, form, P.s, P.gamma, P.gamma_mode, h->p));
   if (P.r < 1 || P.max_iter < 1) return fail(h, SPCA_E_INVALID, "r and max_iter must be >= 1%s");
   if (!std::isfinite(P.tol)) return fail(h, SPCA_E_INVALID, "tol must be finite%s");
   const bool target = is_pen(form) && P.gamma_mode == SPCA_GAMMA_TARGET_NNZ;
   if (target && P.gamma_calib_sweeps < 1) return fail(h, SPCA_E_INVALID, "gamma_calib_sweeps must be >= 1%s");
-  if (P.engine != SPCA_ENGINE_AUTO && P.engine != SPCA_ENGINE_SIMT && P.engine != SPCA_ENGINE_TC)
-    return fail(h, SPCA_E_INVALID, "unknown engine%s");
-  if (P.engine == SPCA_ENGINE_TC) return fail(h, SPCA_E_UNSUPPORTED, "tensor-core engine not built%s");
+  int engine;
+  RC(resolve_engine(h, P.engine, &engine));
 
   const int r = P.r, n = (int)h->n, p = (int)h->p;
-  rc = ensure_workspace(h, r);
-  if (rc != SPCA_OK) return rc;
+  RC(ensure_workspace(h, r));
   cudaStream_t st = h->stream;
   StartState S = state_of(h);
 
   // ---- a1: starting points
   const double gamma0 = is_pen(form) && !target ? P.gamma : 0.0;
-  if (x0 && !P.x0_is_device) {
-    CK(cudaMemcpy2DAsync(h->X, h->ldX * sizeof(float), x0, (size_t)p * sizeof(float),
-                         (size_t)p * sizeof(float), r, cudaMemcpyHostToDevice, st));
-  } else if (x0) {
-    CK(cudaMemcpy2DAsync(h->X, h->ldX * sizeof(float), x0, (size_t)p * sizeof(float),
-                         (size_t)p * sizeof(float), r, cudaMemcpyDeviceToDevice, st));
-  }
   if (x0) {
+    CK(cudaMemcpy2DAsync(h->X, h->ldX * sizeof(float), x0, (size_t)p * sizeof(float), (size_t)p * sizeof(float),
+                         r, P.x0_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
     CK(timed(h, SPCA_K_PREP, 1, [&] { return launch_check_finite(h->X, r, p, h->ldX, h->flag, st); }));
     CK(cudaMemcpyAsync(h->h_flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -377,21 +514,13 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   for (int k = 1; k <= P.max_iter; ++k) {
     Ctrl *cur = h->ctrl + ((k - 1) & 1), *nxt = h->ctrl + (k & 1);
     // u = A x: dense contraction, or the support gather when every support is small
-    CK(timed(h, SPCA_K_U_DENSE, 1, [&] {
-      return launch_gemm_nt_f32(h->X, h->ldX, h->A32, h->ldA, h->U, h->ldU, r, n, (int)h->ldX,
-                                &cur->need_dense, st);
-    }));
+    RC(sweep_u_dense(h, engine, r, &cur->need_dense));
     CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
-      return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U,
-                                 h->ldU, &cur->need_dense, st);
+      return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
+                                 &cur->need_dense, st);
     }));
-    CK(timed(h, SPCA_K_YSTEP, 1,
-             [&] { return launch_ystep(form, h->U, h->ldU, n, r, h->Y, S, h->X, h->ldX, p, st); }));
-    // v = A^T y
-    CK(timed(h, SPCA_K_V, 1, [&] {
-      return launch_gemm_nt_f32(h->Y, h->ldU, h->AT32, h->ldAT, h->V, h->ldX, r, p, (int)h->ldU,
-                                nullptr, st);
-    }));
+    // y-step, v = A^T y
+    RC(sweep_y_v(h, engine, form, r, S));
     CK(cudaMemsetAsync(nxt, 0, sizeof(Ctrl), st));
     xa.calibrate = target && k <= C;
     xa.per_start_thr = target && k > C;
@@ -405,11 +534,12 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
       if (h->h_ctrl->active == 0) break;
     }
   }
+  RC(read_dev_err(h));
 
   // ---- a7: FP64 objective, best start, y(x) and support of the best x
   CK(timed(h, SPCA_K_FINALISE, 4, [&] {
-    cudaError_t e = launch_finalise(form, h->AT32, h->ldAT, n, p, h->X, h->ldX, S, r, h->U, h->ldU,
-                                    h->sup_idx, h->sup_val, p, h->partials, st);
+    cudaError_t e = launch_finalise(form, h->AT32, h->ldAT, n, p, h->X, h->ldX, S, r, h->U, h->ldU, h->sup_idx,
+                                    h->sup_val, p, h->partials, st);
     if (e == cudaSuccess) e = launch_best(form, target ? 1 : 0, S, r, h->best, st);
     if (e == cudaSuccess)
       e = launch_best_outputs(form, h->best, h->U, h->ldU, n, h->X, h->ldX, p, h->y_out, h->x_out,
@@ -434,8 +564,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   if (res->x) CK(cudaMemcpyAsync(res->x, h->x_out, (size_t)p * sizeof(float), cudaMemcpyDeviceToHost, st));
   if (res->y) CK(cudaMemcpyAsync(res->y, h->y_out, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, st));
   if (res->support && nnz > 0)
-    CK(cudaMemcpyAsync(res->support, h->support_out, (size_t)nnz * sizeof(int64_t),
-                       cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(res->support, h->support_out, (size_t)nnz * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   if (res->start_x)
     CK(cudaMemcpy2DAsync(res->start_x, (size_t)p * sizeof(float), h->X, h->ldX * sizeof(float),
                          (size_t)p * sizeof(float), r, cudaMemcpyDeviceToHost, st));

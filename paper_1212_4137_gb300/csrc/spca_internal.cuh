@@ -12,8 +12,10 @@
 // so contraction kernels need no K-tail guards.
 #pragma once
 
-#include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 #include "../../include/spca.h"
 
@@ -97,9 +99,31 @@ cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int 
                                 const float *sup_val, int cap, StartState s, int r, float *U,
                                 int64_t ldu, const int *gate, cudaStream_t st);
 
-// y-step (S1 / S2 of Table 3) for active starts
+// y-step (S1 / S2 of Table 3) for active starts.  Writes Y as FP32 (Y != nullptr) and/or as
+// BF16 planes (Ypl != nullptr: 1 plane of +-1 for L1 variance, 3 planes hi/mid/lo for L2
+// variance, plane t at Ypl + t * plane_stride)
 cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, float *Y,
-                         StartState s, float *X, int64_t ldX, int p, cudaStream_t st);
+                         void *Ypl, int64_t plane_stride, StartState s, float *X, int64_t ldX,
+                         int p, cudaStream_t st);
+
+// ---------------------------------------------------------------- tcgen05 engine
+struct TcPairs {      // plane products summed into one accumulator: P plane a[q] x Q plane b[q]
+  int n;
+  unsigned char a[8], b[8];
+};
+// 3-D TMA map over `planes` BF16 planes of rows x ld (K-contiguous), box 64 x box_rows
+cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int64_t ld, int planes,
+                           int box_rows);
+int tc_box_rows(int nb);   // Q-operand box height for nb planes (the tile's N)
+// out[c * ldo + m] = sum_q sum_k P_{a_q}[m, k] Q_{b_q}[c, k], m < M, c < N; with gate != nullptr
+// nothing runs unless *gate != 0; a timed-out wait sets *err = SPCA_E_TIMEOUT
+cudaError_t launch_gemm_tc(const CUtensorMap &P, int na, const CUtensorMap &Q, int nb, int M, int N,
+                           int K, TcPairs pairs, float *out, int64_t ldo, const int *gate, int *err,
+                           cudaStream_t st);
+// BF16 planes of an FP32 matrix (plane t at dst + t * plane_stride elements); gated like above
+cudaError_t launch_split_planes(const float *src, int64_t rows, int64_t cols, int64_t lds, void *dst,
+                                int64_t ldd, int64_t plane_stride, int nplanes, const int *gate,
+                                cudaStream_t st);
 
 // x-step (S3..S6), objective F, stopping rule, support lists
 cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,

@@ -21,7 +21,8 @@ SPCA_ST_MAXITER, SPCA_ST_CONVERGED, SPCA_ST_DEGENERATE = 0, 1, 2
 SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC = 0, 1, 2
 
 # every symbol include/spca.h declares
-EXPORTS = ("spca_create", "spca_solve", "spca_xstep", "spca_profile_enable", "spca_profile_query",
+EXPORTS = ("spca_create", "spca_solve", "spca_xstep", "spca_products", "spca_profile_enable",
+           "spca_profile_query",
            "spca_destroy", "spca_strerror", "spca_last_error")
 SPCA_K_ALL, SPCA_K_INIT, SPCA_K_U_DENSE, SPCA_K_U_SPARSE, SPCA_K_YSTEP, SPCA_K_V, SPCA_K_XSTEP, \
     SPCA_K_FINALISE, SPCA_K_PREP = range(-1, 8)
@@ -82,6 +83,10 @@ def load(path: str = LIB_PATH):
                                    ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                    ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]
+        lib.spca_products.restype = ctypes.c_int
+        lib.spca_products.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                      ctypes.c_void_p, ctypes.c_int64]
         lib.spca_profile_enable.restype = ctypes.c_int
         lib.spca_profile_enable.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.spca_profile_query.restype = ctypes.c_int
@@ -130,6 +135,11 @@ def spca_xstep(h, form, s, gamma, calibrate, V, ldv, r, X, ldx, F, nnz, thr) -> 
     return load().spca_xstep(h, int(form), float(s), float(gamma), int(calibrate), ctypes.c_void_p(V),
                              ldv, r, ctypes.c_void_p(X), ldx, ctypes.c_void_p(F), ctypes.c_void_p(nnz),
                              ctypes.c_void_p(thr))
+
+
+def spca_products(h, form, engine, X, ldx, r, U, ldu, V, ldv) -> int:
+    return load().spca_products(h, int(form), int(engine), ctypes.c_void_p(X), ldx, r, ctypes.c_void_p(U), ldu,
+                                ctypes.c_void_p(V), ldv)
 
 
 def spca_profile_enable(h, on: bool) -> int:

@@ -26,6 +26,13 @@ def lib():
     return spca
 
 
+ENGINES = ("simt", "tc")
+
+
+def _engine(lib, name):
+    return {"simt": lib.SPCA_ENGINE_SIMT, "tc": lib.SPCA_ENGINE_TC}[name]
+
+
 def _kw(form, s, gamma, target):
     if form in (1, 2, 3, 4):
         return dict(s=s)
@@ -93,23 +100,21 @@ def _compare_solve(oracle, A64, out, ref, form, tol_frac=0.95, x_atol=X_ATOL):
     assert abs(bg - bo) <= OBJ_RTOL * max(1.0, abs(bo)), (bg, bo)
 
 
-class _Ref:
-    pass
-
-
 def _oracle_solve(oracle, A64, form, G, kw, max_iter, tol):
     res = oracle.solve(A64, form, G, max_iter=max_iter, tol=tol, **kw)
     res.kw = kw
     return res
 
 
-def test_small_dense_case_form1(lib, oracle):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_small_dense_case_form1(lib, oracle, engine):
     """n = 100, p = 500, A_ij ~ N(0,1) (FP64, uploaded and stored as FP32), L0-constrained
     L2 variance, s = 10, 16 unit-norm Gaussian starts, 100 sweeps or relative change < 1e-9."""
     A = I.gaussian_matrix(100, 500, 1)
     G = I.raw_starts(500, 16, 2)
     h = lib.Handle(A)
-    out = h.solve(1, 16, s=10, max_iter=100, tol=1e-9, x0=G.astype(np.float32), want_starts=True)
+    out = h.solve(1, 16, s=10, max_iter=100, tol=1e-9, x0=G.astype(np.float32), want_starts=True,
+                  engine=_engine(lib, engine))
     ref = _oracle_solve(oracle, A, 1, G.astype(np.float32).astype(np.float64), dict(s=10), 100, 1e-9)
     # tol = 1e-9 is below the FP32 resolution of F (~1e-7): the FP32 path stops when F stops
     # rising at its precision, a few sweeps before the FP64 oracle; F converges quadratically in
@@ -134,9 +139,10 @@ def spiked():
     return A
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("form", range(1, 9))
 @pytest.mark.parametrize("target", [False, True])
-def test_spiked_all_forms_fixed_sweeps(lib, oracle, spiked, form, target):
+def test_spiked_all_forms_fixed_sweeps(lib, oracle, spiked, form, target, engine):
     if target and form < 5:
         pytest.skip("gamma targeting applies to the penalty forms")
     A = spiked
@@ -150,7 +156,7 @@ def test_spiked_all_forms_fixed_sweeps(lib, oracle, spiked, form, target):
     if target:
         kw["calib"] = 5
     h = lib.Handle(A)
-    out = h.solve(form, r, max_iter=25, tol=-1, x0=G, want_starts=True, **kw)
+    out = h.solve(form, r, max_iter=25, tol=-1, x0=G, want_starts=True, engine=_engine(lib, engine), **kw)
     ref = _oracle_solve(oracle, A64, form, G.astype(np.float64), kw, 25, -1)
     assert np.all(out["start_iters"] == ref.iters)
     assert np.all(out["start_status"] == ref.status)
@@ -173,8 +179,9 @@ def _near_tie(A64, form, xk, s, gamma, gap=1e-4):
     return bool((a[s - 1] - a[s]) <= gap * a[s - 1])
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("form", range(1, 9))
-def test_single_sweep_parity(lib, oracle, spiked, form):
+def test_single_sweep_parity(lib, oracle, spiked, form, engine):
     """One sweep of the GPU from its own iterate x^(k) against one FP64 oracle sweep from the
     same x^(k): isolates the arithmetic of a sweep from trajectory drift.  Penalty forms run
     in gamma-targeting mode (C = 5): sweeps k+1 <= C re-target, later ones use the start's
@@ -194,9 +201,9 @@ def test_single_sweep_parity(lib, oracle, spiked, form):
             Xk = G.astype(np.float64) / np.linalg.norm(G.astype(np.float64), axis=1, keepdims=True)
             stat = np.full(r, lib.SPCA_ST_MAXITER)
         else:
-            o = h.solve(form, r, max_iter=k, tol=-1, x0=G, want_starts=True, **kw)
+            o = h.solve(form, r, max_iter=k, tol=-1, x0=G, want_starts=True, engine=_engine(lib, engine), **kw)
             Xk, stat = o["start_x"].astype(np.float64), o["start_status"]
-        o1 = h.solve(form, r, max_iter=k + 1, tol=-1, x0=G, want_starts=True, **kw)
+        o1 = h.solve(form, r, max_iter=k + 1, tol=-1, x0=G, want_starts=True, engine=_engine(lib, engine), **kw)
         for c in range(r):
             if stat[c] == lib.SPCA_ST_DEGENERATE or o1["start_status"][c] == lib.SPCA_ST_DEGENERATE:
                 continue
@@ -206,25 +213,26 @@ def test_single_sweep_parity(lib, oracle, spiked, form):
             elif form >= 5:
                 okw["calib"] = 1
             ref = oracle.solve(A64, form, Xk[c:c + 1], max_iter=1, tol=-1, **okw)
-            assert abs(o1["start_F"][c] - ref.F[0]) <= OBJ_RTOL * max(1.0, abs(ref.F[0])), (k, c)
             if _near_tie(A64, form, Xk[c], 12, okw.get("gamma") if "gamma" in okw else None):
                 continue   # the selection boundary is within FP32 noise: either choice is correct
+            assert abs(o1["start_F"][c] - ref.F[0]) <= OBJ_RTOL * max(1.0, abs(ref.F[0])), (k, c)
             err = np.abs(o1["start_x"][c] - ref.X[0]).max()
             worst = max(worst, err)
             assert err <= X_ATOL, (form, k, c, err)
     h.close()
-    print(f"form {form}: worst single-sweep |dx|_inf = {worst:.2e}")
+    print(f"{engine} form {form}: worst single-sweep |dx|_inf = {worst:.2e}")
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("form", [1, 4, 5, 8])
-def test_spiked_stopping_rule(lib, oracle, spiked, form):
+def test_spiked_stopping_rule(lib, oracle, spiked, form, engine):
     A = spiked
     A64 = A.astype(np.float64)
     r = 24
     G = I.raw_starts(A.shape[1], r, 13).astype(np.float32)
     kw = _kw(form, 12, {5: 0.5, 8: 2.0}.get(form, 0.0), False)
     h = lib.Handle(A)
-    out = h.solve(form, r, max_iter=200, tol=1e-6, x0=G, want_starts=True, **kw)
+    out = h.solve(form, r, max_iter=200, tol=1e-6, x0=G, want_starts=True, engine=_engine(lib, engine), **kw)
     ref = _oracle_solve(oracle, A64, form, G.astype(np.float64), kw, 200, 1e-6)
     bo = ref.f[ref.best]
     assert abs(out["objective"] - bo) <= OBJ_RTOL * max(1.0, abs(bo))

@@ -1,0 +1,79 @@
+"""Step-level parity of the two contractions of a sweep (u = A x, y-step, v = A^T y) for both
+engines (FP32 CUDA cores; tcgen05 tensor cores on three BF16 planes per FP32 operand) against
+FP64, on shapes that span several tiles and ragged tails.  The tensor-core engine sums every
+plane product above the 2^-24 relative level, so both engines must agree with FP64 to FP32
+accumulation accuracy."""
+import numpy as np
+import pytest
+
+from paper_1212_4137_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(7, 9, 3), (300, 1003, 40), (129, 257, 300), (1000, 3000, 257), (2500, 700, 520)]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1212_4137_gb300 import build, spca
+    build.build()
+    spca.load()
+    return spca
+
+
+def _run(lib, h, form, engine, X):
+    import torch
+    r, p = X.shape
+    n = h.n
+    Xd = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
+    Ud = torch.zeros((r, n + 1), dtype=torch.float32, device="cuda")
+    Vd = torch.zeros((r, p + 5), dtype=torch.float32, device="cuda")
+    st = lib.spca_products(h.h, form, engine, Xd.data_ptr(), p, r, Ud.data_ptr(), n + 1, Vd.data_ptr(), p + 5)
+    assert st == 0, lib.spca_last_error(h.h)
+    torch.cuda.synchronize()
+    return Ud[:, :n].cpu().numpy().astype(np.float64), Vd[:, :p].cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("engine", ["simt", "tc"])
+@pytest.mark.parametrize("form", [1, 2])
+def test_products_match_fp64(lib, shape, engine, form):
+    n, p, r = shape
+    A = I.gaussian_matrix(n, p, 500 + n).astype(np.float32)
+    A64 = A.astype(np.float64)
+    rng = np.random.default_rng(n + p)
+    X = rng.standard_normal((r, p)).astype(np.float32)
+    X[:, rng.uniform(size=p) < 0.5] = 0.0            # sparse-ish iterates as after an x-step
+    X[0] = 0.0
+    X[0, p // 2] = 1.0
+    eng = {"simt": lib.SPCA_ENGINE_SIMT, "tc": lib.SPCA_ENGINE_TC}[engine]
+    h = lib.Handle(A)
+    U, V = _run(lib, h, form, eng, X)
+    h.close()
+    U_ref = X.astype(np.float64) @ A64.T                      # r x n
+    scale_u = np.abs(X.astype(np.float64)) @ np.abs(A64).T    # bound of the rounding error
+    assert np.all(np.abs(U - U_ref) <= 2e-6 * scale_u + 1e-30), np.max(np.abs(U - U_ref) / (scale_u + 1e-30))
+    # y from the GPU's own u (same sign / scale decisions), then v in FP64
+    if form % 2 == 0:
+        Yr = np.where(U >= 0, 1.0, -1.0)
+    else:
+        Yr = U / np.linalg.norm(U, axis=1, keepdims=True)
+    V_ref = Yr @ A64
+    scale_v = np.abs(Yr) @ np.abs(A64)
+    err = np.abs(V - V_ref) / (scale_v + 1e-30)
+    assert err.max() <= 2e-6, err.max()
+
+
+def test_engines_agree_on_spiked(lib):
+    n, p, r = 600, 2100, 130
+    A = I.spiked_matrix(n, p, I.spiked_thetas(n, p), 20, 501, dtype=np.float32)
+    G = I.raw_starts(p, r, 502).astype(np.float32)
+    h = lib.Handle(A)
+    for form in (1, 2):
+        Us, Vs = _run(lib, h, form, lib.SPCA_ENGINE_SIMT, G)
+        Ut, Vt = _run(lib, h, form, lib.SPCA_ENGINE_TC, G)
+        assert np.abs(Us - Ut).max() <= 1e-5 * np.abs(Us).max()
+        assert np.abs(Vs - Vt).max() <= 1e-5 * np.abs(Vs).max()
+    h.close()
