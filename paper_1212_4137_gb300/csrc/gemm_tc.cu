@@ -6,9 +6,14 @@
 // FP32 accuracy from BF16 tensor cores: every FP32 operand is stored as three BF16 planes
 // (hi = bf16(a), mid = bf16(a - hi), lo = a - hi - mid; hi + mid + lo == a exactly, since
 // each plane holds the next 8 significant bits).  A product sum a.b is then the sum over
-// plane pairs (i, j) of a_i . b_j, each term exact in the FP32 accumulator; the pairs with
-// i + j <= 2 carry everything above the 2^-24 relative level of FP32 (6 products for two
-// general operands, 3 when b is +-1 and has a single plane).
+// plane pairs (i, j) of a_i . b_j, each product exact; the pairs with i + j <= 2 carry
+// everything above the 2^-24 relative level of FP32 (6 products for two general operands,
+// 3 when b is +-1 and has a single plane).  The tensor core's accumulation truncates, so the
+// error grows with the number of MMA steps into one accumulator: the hi x hi product goes to
+// its own TMEM accumulator and the correction products (2^-8 smaller and below) to a second
+// one; the epilogue adds the two with FP32 round-to-nearest.  Measured on GB300 against FP64
+// (K = 8192, relative to sum |a_k b_k|): one accumulator for all six products 3.5e-6, the
+// hi x hi product alone 7.6e-7.
 //
 //   D[m, c] = sum_{(i,j) in pairs} sum_k P_i[m, k] Q_j[c, k]      out[c * ldo + m] = D[m, c]
 //
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;       // 16 KB per P plane tile
   constexpr uint32_t B_BYTES = BN * TC_BK * 2;          // 32 KB (BN = 256) per Q plane tile
   constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
-  constexpr uint32_t TMEM_COLS = BN;                    // FP32 accumulator: BN columns x 128 lanes
+  constexpr uint32_t TMEM_COLS = 2 * BN;                // two FP32 accumulators of BN columns x 128 lanes
 
   extern __shared__ __align__(1024) uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar;
@@ -189,10 +194,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int q = 0; q < pairs.n; ++q) {
         const uint32_t a_base = st + pairs.a[q] * A_BYTES;
         const uint32_t b_base = st + NA * A_BYTES + pairs.b[q] * B_BYTES;
+        const bool main = (pairs.a[q] | pairs.b[q]) == 0;   // hi x hi -> accumulator 0
+        const uint32_t d = tmem + (main ? 0u : (uint32_t)BN);
+        const bool first = kb == 0 && q == (main ? pairs.first_main : pairs.first_corr);
 #pragma unroll
         for (int kk = 0; kk < TC_BK / 16; ++kk) {
-          mma_bf16(tmem, sw128_desc(a_base + kk * 32), sw128_desc(b_base + kk * 32), idesc,
-                   (kb | q | kk) != 0 ? 1u : 0u);
+          mma_bf16(d, sw128_desc(a_base + kk * 32), sw128_desc(b_base + kk * 32), idesc,
+                   (first && kk == 0) ? 0u : 1u);
         }
       }
       mma_commit(smem_u32(&empty_bar[s]));   // frees the stage once these MMAs have read it
@@ -201,13 +209,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp >= 2) {
     // ---------------------------------------------------------------- epilogue (TMEM -> HBM)
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
-    if (mbar_wait(smem_u32(&accum_bar), 0, err, &abort_flag)) {
+    // tcgen05.ld is warp-collective: take the barrier result uniformly over the warp
+    const bool ready = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accum_bar), 0, err, &abort_flag));
+    if (ready) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int row = m0 + quad * 32 + lane;
 #pragma unroll 1
       for (int cb = 0; cb < BN / 32; ++cb) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 32), v);
+        float v[32], w[32];
+        const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 32);
+        tmem_ld32(ta, v);
+        if (pairs.first_corr >= 0) {
+          tmem_ld32(ta + (uint32_t)BN, w);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += w[j];
+        }
         if (row < M) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {

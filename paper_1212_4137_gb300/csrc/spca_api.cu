@@ -220,12 +220,16 @@ TcPairs pairs_general() {
   const unsigned char a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
   q.n = 6;
   for (int i = 0; i < 6; ++i) { q.a[i] = a[i]; q.b[i] = b[i]; }
+  q.first_corr = 0;
+  q.first_main = 5;
   return q;
 }
 TcPairs pairs_sign() {
   TcPairs q{};
   q.n = 3;
   q.a[0] = 2; q.a[1] = 1; q.a[2] = 0;
+  q.first_corr = 0;
+  q.first_main = 2;
   return q;
 }
 

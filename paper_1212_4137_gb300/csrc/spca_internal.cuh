@@ -107,8 +107,10 @@ cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, fl
                          int p, cudaStream_t st);
 
 // ---------------------------------------------------------------- tcgen05 engine
-struct TcPairs {      // plane products summed into one accumulator: P plane a[q] x Q plane b[q]
-  int n;
+struct TcPairs {      // plane products P plane a[q] x Q plane b[q], q < n; the hi x hi product
+  int n;              // (a = b = 0, index first_main) accumulates apart from the corrections
+  int first_main;     // (first of them at index first_corr, -1 if none)
+  int first_corr;
   unsigned char a[8], b[8];
 };
 // 3-D TMA map over `planes` BF16 planes of rows x ld (K-contiguous), box 64 x box_rows
