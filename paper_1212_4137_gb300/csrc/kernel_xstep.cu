@@ -8,6 +8,12 @@
 // then normalisation (Section 2.2), the Table 3 value F(x^(k+1), y^(k)), the stopping rule,
 // and the support list (ascending indices) used by the sparse u = A x and the FP64 objective.
 // Section 4.1's gamma rule (penalty forms) picks gamma so that exactly s entries survive.
+//
+// Layout: v is staged once in shared memory (p * 4 bytes up to XSTEP_SMEM_MAX, else read from
+// global memory on every pass).  Each warp owns one contiguous index segment, so ordered work
+// (support compaction, ranking of tied magnitudes) needs only warp ballots plus one scan over
+// the 16 warps.  Reductions are in a fixed order: a start's result does not depend on the
+// other starts or on scheduling.
 #include <cstdint>
 
 #include "block_util.cuh"
@@ -16,63 +22,153 @@
 namespace spca {
 
 namespace {
-constexpr int XT = 512;  // threads per CTA
+constexpr int XT = 512;                        // threads per CTA
+constexpr int XW = XT / 32;                    // warps per CTA
+constexpr int XSTEP_SMEM_MAX = 200 * 1024;     // largest v staged in shared memory (bytes)
 
 struct XShared {
   unsigned hist[256];
-  double red_d[32];
-  int red_i[32];
-  unsigned red_u[32];
-  int digit, rem;
+  double red_d[XW][2];
+  int red_i[XW][2];
+  int wcnt[XW];                                // per-warp counts of one pass
+  int woff[XW];                                // their exclusive prefix over warps
+  int digit, rem, cnt_bin;
+  unsigned red_u[XW];
 };
 
-// The j-th largest (1 <= j <= p) of the keys |v_i| (MSB-first radix select, 8-bit digits).
-// Returns the key; *need_eq = how many elements equal to it belong to the top j, and
-// *eq_total = how many elements equal it.
-__device__ uint32_t radix_select_desc(const float *__restrict__ v, int p, int j, XShared &sh,
-                                      int *need_eq, int *eq_total) {
-  uint32_t prefix = 0, mask = 0;
+struct Seg {
+  int lo, hi;
+};
+// this warp's index segment: 16 contiguous ranges, each a multiple of 32 long (the last shorter)
+__device__ __forceinline__ Seg warp_seg(int p) {
+  const int seg = (((p + XW - 1) / XW) + 31) / 32 * 32;
+  const int w = threadIdx.x >> 5;
+  Seg s;
+  s.lo = min(p, w * seg);
+  s.hi = min(p, s.lo + seg);
+  return s;
+}
+
+// block sums of (d0, d1, i0, i1) in one round; every thread gets them
+__device__ __forceinline__ void block_sum2(double &d0, double &d1, int &i0, int &i1, XShared &sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  d0 = warp_sum_d(d0); d1 = warp_sum_d(d1); i0 = warp_sum_i(i0); i1 = warp_sum_i(i1);
+  __syncthreads();
+  if (lane == 0) { sh.red_d[w][0] = d0; sh.red_d[w][1] = d1; sh.red_i[w][0] = i0; sh.red_i[w][1] = i1; }
+  __syncthreads();
+  d0 = d1 = 0.0; i0 = i1 = 0;
+  for (int k = 0; k < XW; ++k) { d0 += sh.red_d[k][0]; d1 += sh.red_d[k][1]; i0 += sh.red_i[k][0]; i1 += sh.red_i[k][1]; }
+}
+
+// per-warp count -> exclusive offsets over warps (sh.woff) and the block total
+__device__ __forceinline__ int warp_offsets(int my_warp_count, XShared &sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh.wcnt[w] = my_warp_count;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int k = 0; k < XW; ++k) { sh.woff[k] = acc; acc += sh.wcnt[k]; }
+    sh.cnt_bin = acc;
+  }
+  __syncthreads();
+  return sh.cnt_bin;
+}
+
+// The j-th largest (1 <= j <= p) of the keys |v_i| by MSB-first radix select over the digits
+// bits 30..23 (the exponent), 22..15, 14..7, 6..0.  Histogram updates are aggregated per warp.
+// If the chosen bin is exactly the remainder of the top j before the last digit, the search
+// stops: every element of the bin is in the top j.  Then, with exact == false, *K is the bin's
+// lower bound and *whole = true; with exact == true one more pass finds the bin's minimum,
+// which is the j-th largest key.  Otherwise *need_eq / *eq_total describe ties at *K.
+__device__ void radix_select(const float *vv, int p, int j, bool exact, XShared &sh, uint32_t *K,
+                             bool *whole, int *need_eq, int *eq_total) {
+  const int shifts[4] = {23, 15, 7, 0};
+  const uint32_t wmask[4] = {0xFFu, 0xFFu, 0xFFu, 0x7Fu};
+  const int lane = threadIdx.x & 31;
+  const Seg sg = warp_seg(p);
+  uint32_t prefix = 0u, mask = 0u;
   int rem = j;
-  for (int shift = 24; shift >= 0; shift -= 8) {
+  *whole = false;
+  for (int t = 0; t < 4; ++t) {
+    const int sh_ = shifts[t];
     for (int b = threadIdx.x; b < 256; b += blockDim.x) sh.hist[b] = 0u;
     __syncthreads();
-    for (int i = threadIdx.x; i < p; i += blockDim.x) {
-      const uint32_t key = abs_key(v[i]);
-      if ((key & mask) == prefix) atomicAdd(&sh.hist[(key >> shift) & 255u], 1u);
+    for (int base = sg.lo; base < sg.hi; base += 32) {
+      const int i = base + lane;
+      const uint32_t key = (i < sg.hi) ? abs_key(vv[i]) : 0xFFFFFFFFu;
+      const bool m = (i < sg.hi) && (key & mask) == prefix;
+      const uint32_t bin = m ? (key >> sh_) & wmask[t] : 0xFFFFFFFFu;
+      const unsigned peers = __match_any_sync(0xffffffffu, bin);
+      if (m && lane == __ffs(peers) - 1) atomicAdd(&sh.hist[bin], (unsigned)__popc(peers));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      int acc = 0, d = 255;
+      int acc = 0, d = (int)wmask[t];
       for (; d > 0; --d) {
         if (acc + (int)sh.hist[d] >= rem) break;
         acc += (int)sh.hist[d];
       }
       sh.digit = d;
       sh.rem = rem - acc;
+      sh.cnt_bin = (int)sh.hist[d];
     }
     __syncthreads();
-    prefix |= (uint32_t)sh.digit << shift;
-    mask |= 255u << shift;
+    prefix |= (uint32_t)sh.digit << sh_;
+    mask |= wmask[t] << sh_;
     rem = sh.rem;
-    if (shift == 0) *eq_total = (int)sh.hist[sh.digit];
+    const int cnt = sh.cnt_bin;
     __syncthreads();
+    if (t == 3) {
+      *K = prefix;
+      *need_eq = rem;
+      *eq_total = cnt;
+      return;
+    }
+    if (cnt == rem) {  // the whole bin belongs to the top j
+      if (!exact) {
+        *K = prefix;
+        *whole = true;
+        return;
+      }
+      unsigned mn = 0xFFFFFFFFu;
+      for (int base = sg.lo; base < sg.hi; base += 32) {
+        const int i = base + lane;
+        if (i < sg.hi) {
+          const uint32_t key = abs_key(vv[i]);
+          if ((key & mask) == prefix) mn = min(mn, key);
+        }
+      }
+      // block minimum
+      for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      if (lane == 0) sh.red_u[threadIdx.x >> 5] = mn;
+      __syncthreads();
+      unsigned m2 = 0xFFFFFFFFu;
+      for (int k = 0; k < XW; ++k) m2 = min(m2, sh.red_u[k]);
+      __syncthreads();
+      *K = m2;
+      *whole = true;
+      return;
+    }
   }
-  *need_eq = rem;
-  return prefix;
 }
 
-// lambda_s(v) (Section 2.1) for the case phi(0) < 0.  Returns lambda and the key interval
-// (lo, hi] such that the active set {|v_i| > lambda} = {key_i > lo}.
-__device__ double lambda_s_bisect(const float *__restrict__ v, int p, double s, uint32_t maxkey,
-                                  XShared &sh, uint32_t *lo_out) {
+// lambda_s(v) (Section 2.1) when phi(0) < 0.  Bisection over the float keys of lambda in
+// [0, max|v|] on the sign of phi, stopping as soon as no |v_i| lies strictly inside the
+// bracket (the active set is then fixed); then the root of phi on that piece in FP64.
+// *lo_out: the active set is {key_i > *lo_out}.
+__device__ double lambda_s_bisect(const float *vv, int p, double s, uint32_t maxkey, XShared &sh,
+                                  uint32_t *lo_out) {
+  const int lane = threadIdx.x & 31;
+  const Seg sg = warp_seg(p);
   uint32_t lo = 0u, hi = maxkey;  // phi(key lo) < 0 <= phi(key hi)
   while (hi - lo > 1u) {
     const uint32_t mid = lo + (hi - lo) / 2u;
     const float lam = __uint_as_float(mid);
     float sw = 0.0f, sw2 = 0.0f;
     int in_lo = 0, in_hi = 0;  // elements strictly inside (lo, mid) and (mid, hi)
-    for (int i = threadIdx.x; i < p; i += blockDim.x) {
-      const float a = fabsf(v[i]);
+    for (int i = sg.lo + lane; i < sg.hi; i += 32) {
+      const float a = fabsf(vv[i]);
       const uint32_t key = __float_as_uint(a);
       if (a > lam) {
         const float w = a - lam;
@@ -82,36 +178,29 @@ __device__ double lambda_s_bisect(const float *__restrict__ v, int p, double s, 
       in_lo += (key > lo && key < mid);
       in_hi += (key > mid && key < hi);
     }
-    const double Sw = block_sum_d((double)sw, sh.red_d);
-    const double Sw2 = block_sum_d((double)sw2, sh.red_d);
-    const int nlo = block_sum_i(in_lo, sh.red_i);
-    const int nhi = block_sum_i(in_hi, sh.red_i);
+    double Sw = sw, Sw2 = sw2;
+    block_sum2(Sw, Sw2, in_lo, in_hi, sh);
     const double phi = s * Sw2 - Sw * Sw;
     if (phi < 0.0) {
       lo = mid;
-      if (nhi == 0) break;  // no magnitude strictly inside (mid, hi): active set fixed
+      if (in_hi == 0) break;  // no magnitude strictly inside (mid, hi): active set fixed
     } else {
       hi = mid;
-      if (nlo == 0) break;
+      if (in_lo == 0) break;
     }
   }
   // active set {key > lo}: k, S1, S2 in FP64, then the root of phi on this piece
-  int kc = 0;
   double s1 = 0.0, s2 = 0.0;
-  {
-    double d1 = 0.0, d2 = 0.0;
-    for (int i = threadIdx.x; i < p; i += blockDim.x) {
-      const float a = fabsf(v[i]);
-      if (__float_as_uint(a) > lo) {
-        ++kc;
-        d1 += (double)a;
-        d2 = fma((double)a, (double)a, d2);
-      }
+  int kc = 0, unused = 0;
+  for (int i = sg.lo + lane; i < sg.hi; i += 32) {
+    const float a = fabsf(vv[i]);
+    if (__float_as_uint(a) > lo) {
+      ++kc;
+      s1 += (double)a;
+      s2 = fma((double)a, (double)a, s2);
     }
-    s1 = block_sum_d(d1, sh.red_d);
-    s2 = block_sum_d(d2, sh.red_d);
-    kc = block_sum_i(kc, sh.red_i);
   }
+  block_sum2(s1, s2, kc, unused, sh);
   const double k = (double)kc;
   const double flo = (double)__uint_as_float(lo), fhi = (double)__uint_as_float(hi);
   double lam;
@@ -126,23 +215,31 @@ __device__ double lambda_s_bisect(const float *__restrict__ v, int p, double s, 
   *lo_out = lo;
   return lam;
 }
-}  // namespace
 
+template <bool kSmem>
 __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restrict__ V, int64_t ldv,
                                               float *__restrict__ X, int64_t ldx, StartState st,
-                                              int *__restrict__ sup_idx,
-                                              float *__restrict__ sup_val, Ctrl *ctrl) {
+                                              int *__restrict__ sup_idx, float *__restrict__ sup_val,
+                                              Ctrl *ctrl) {
+  extern __shared__ float vsm[];
   __shared__ XShared sh;
   const int c = blockIdx.x;
   if (st.status && st.status[c] != ST_ACTIVE) return;
   const int p = a.p;
-  const float *v = V + (int64_t)c * ldv;
+  const int lane = threadIdx.x & 31;
+  const float *vg = V + (int64_t)c * ldv;
   float *x = X + (int64_t)c * ldx;
   const int form = a.form;
+  if (kSmem) {
+    for (int i = threadIdx.x; i < p; i += XT) vsm[i] = vg[i];
+    __syncthreads();
+  }
+  const float *vv = kSmem ? vsm : vg;
+  const Seg sg = warp_seg(p);
 
-  // ---- choose the operator's parameters
-  // mode 0: T_s (keep key > K, plus the first need_eq of key == K in index order)
-  // mode 1: hard threshold: keep key > tkey, value v            (U_gamma; T_s with s >= p)
+  // ---- the operator's parameters
+  // mode 0: T_s with ties: keep key > K, plus the first need_eq of key == K in index order
+  // mode 1: hard threshold: keep key > tkey, value v            (U_gamma; T_s otherwise)
   // mode 2: soft threshold: keep key > tkey, value sgn(v)(|v|-t)  (V_gamma, V_lambda)
   int mode = 0;
   uint32_t K = 0u, tkey = 0u;
@@ -152,28 +249,31 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
   const int s_int = (int)a.s;
 
   if (uses_T(form)) {
-    if (s_int >= p) {
-      mode = 1;
-      tkey = 0u;
-    } else {
-      K = radix_select_desc(v, p, s_int, sh, &need_eq, &eq_total);
-      if (K == 0u || need_eq >= eq_total) {
-        mode = 1;  // no ties to break: keep key >= K (zeros contribute nothing)
-        tkey = K == 0u ? 0u : K - 1u;
+    mode = 1;
+    if (s_int < p) {
+      bool whole;
+      radix_select(vv, p, s_int, false, sh, &K, &whole, &need_eq, &eq_total);
+      if (whole) {
+        tkey = K == 0u ? 0u : K - 1u;          // keep every key >= the bin's lower bound
+      } else if (K == 0u || need_eq >= eq_total) {
+        tkey = K == 0u ? 0u : K - 1u;          // no ties to break: keep key >= K
+      } else {
+        mode = 0;
       }
     }
   } else if (uses_lam(form)) {
     // phi(0) = s ||v||_2^2 - ||v||_1^2 >= 0: the L1 ball is not binding, lambda = 0
     float f1 = 0.0f, f2 = 0.0f;
     unsigned mk = 0u;
-    for (int i = threadIdx.x; i < p; i += blockDim.x) {
-      const float av = fabsf(v[i]);
+    for (int i = sg.lo + lane; i < sg.hi; i += 32) {
+      const float av = fabsf(vv[i]);
       f1 += av;
       f2 = fmaf(av, av, f2);
       mk = max(mk, __float_as_uint(av));
     }
-    const double S1 = block_sum_d((double)f1, sh.red_d);
-    const double S2 = block_sum_d((double)f2, sh.red_d);
+    double S1 = f1, S2 = f2;
+    int d0 = 0, d1 = 0;
+    block_sum2(S1, S2, d0, d1, sh);
     const uint32_t maxkey = block_max_u(mk, sh.red_u);
     mode = 2;
     if (a.s * S2 - S1 * S1 >= 0.0) {
@@ -182,7 +282,7 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
       tval = 0.0f;
     } else {
       uint32_t lo;
-      gam = lambda_s_bisect(v, p, a.s, maxkey, sh, &lo);
+      gam = lambda_s_bisect(vv, p, a.s, maxkey, sh, &lo);
       tkey = lo;
       tval = (float)gam;
     }
@@ -193,7 +293,8 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
       uint32_t tk = 0u;
       if (j <= p) {
         int ne, et;
-        tk = radix_select_desc(v, p, j, sh, &ne, &et);
+        bool whole;
+        radix_select(vv, p, j, true, sh, &tk, &whole, &ne, &et);
       }
       tkey = tk;
       tval = __uint_as_float(tk);
@@ -210,34 +311,46 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
     }
   }
 
-  // ---- pass A: ||w||_2^2 and nnz of the unnormalised result w, in index order
-  auto wval = [&](int i, float vi, bool tie_keep) -> float {
-    const uint32_t key = abs_key(vi);
+  // ---- ties (mode 0): offsets of each warp's equal keys in index order
+  if (mode == 0) {
+    int eq = 0;
+    for (int i = sg.lo + lane; i < sg.hi; i += 32) eq += abs_key(vv[i]) == K;
+    eq = warp_sum_i(eq);
+    warp_offsets(eq, sh);
+  }
+  const int eq_base = (mode == 0) ? sh.woff[threadIdx.x >> 5] : 0;
+  const unsigned lt_mask = (1u << lane) - 1u;
+
+  // ---- pass A: ||w||_2^2 and nnz of the unnormalised result w
+  auto wval = [&](float vi, uint32_t key, bool tie_keep) -> float {
     if (mode == 0) return (key > K || (key == K && tie_keep)) ? vi : 0.0f;
     if (key <= tkey) return 0.0f;
     if (mode == 1) return vi;
     return copysignf(fabsf(vi) - tval, vi);
   };
   float part = 0.0f;
-  int cnt = 0;
-  int eq_seen = 0;
-  for (int base = 0; base < p; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const float vi = (i < p) ? v[i] : 0.0f;
-    bool tie_keep = false;
-    if (mode == 0) {  // rank among equal keys, in index order (block-wide scan)
-      int tot;
-      const bool eq = (i < p) && abs_key(vi) == K;
-      const int rank = eq_seen + block_excl_scan_flag(eq, sh.red_i, &tot);
-      tie_keep = eq && rank < need_eq;
-      eq_seen += tot;
+  int wnnz = 0;
+  {
+    int eq_run = eq_base;
+    for (int base = sg.lo; base < sg.hi; base += 32) {
+      const int i = base + lane;
+      const float vi = (i < sg.hi) ? vv[i] : 0.0f;
+      const uint32_t key = abs_key(vi);
+      bool tie_keep = false;
+      if (mode == 0) {
+        const unsigned b = __ballot_sync(0xffffffffu, i < sg.hi && key == K);
+        tie_keep = (eq_run + __popc(b & lt_mask)) < need_eq;
+        eq_run += __popc(b);
+      }
+      const float w = (i < sg.hi) ? wval(vi, key, tie_keep) : 0.0f;
+      part = fmaf(w, w, part);
+      wnnz += __popc(__ballot_sync(0xffffffffu, w != 0.0f));
     }
-    const float w = (i < p) ? wval(i, vi, tie_keep) : 0.0f;
-    part = fmaf(w, w, part);
-    cnt += (w != 0.0f);
   }
-  const double sumsq = block_sum_d((double)part, sh.red_d);
-  const int nnz = block_sum_i(cnt, sh.red_i);
+  double sumsq = part, dz = 0.0;
+  int zz = 0, nnz_dummy = 0;
+  block_sum2(sumsq, dz, zz, nnz_dummy, sh);
+  const int nnz = warp_offsets(wnnz, sh);   // sh.woff: each warp's first slot in the support list
   const double nrm = sqrt(sumsq);
 
   // ---- Table 3 value of the subproblem
@@ -247,34 +360,35 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
   else if (uses_U(form)) F = sumsq - gam * (double)nnz;        // S5: ||U||^2 - gamma ||U||_0
   else F = nrm;                                                // S6: ||V_gamma(v)||_2
 
-  // ---- pass B: x = w / ||w||_2, support list in index order
+  // ---- pass B: x = w / ||w||_2 and the support list in index order
   const float inv = nrm > 0.0 ? (float)(1.0 / nrm) : 0.0f;
   int *gi = sup_idx ? sup_idx + (int64_t)c * a.cap : nullptr;
   float *gv = sup_val ? sup_val + (int64_t)c * a.cap : nullptr;
-  int written = 0;
-  eq_seen = 0;
-  for (int base = 0; base < p; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const float vi = (i < p) ? v[i] : 0.0f;
-    bool tie_keep = false;
-    if (mode == 0) {
-      int tot;
-      const bool eq = (i < p) && abs_key(vi) == K;
-      const int rank = eq_seen + block_excl_scan_flag(eq, sh.red_i, &tot);
-      tie_keep = eq && rank < need_eq;
-      eq_seen += tot;
-    }
-    const float w = (i < p) ? wval(i, vi, tie_keep) : 0.0f;
-    const float xi = w * inv;
-    if (i < p) x[i] = xi;
-    if (gi) {
-      int tot;
-      const int pos = written + block_excl_scan_flag(xi != 0.0f, sh.red_i, &tot);
-      if (xi != 0.0f && pos < a.cap) {
-        gi[pos] = i;
-        gv[pos] = xi;
+  {
+    int eq_run = eq_base;
+    int pos = sh.woff[threadIdx.x >> 5];
+    for (int base = sg.lo; base < sg.hi; base += 32) {
+      const int i = base + lane;
+      const float vi = (i < sg.hi) ? vv[i] : 0.0f;
+      const uint32_t key = abs_key(vi);
+      bool tie_keep = false;
+      if (mode == 0) {
+        const unsigned b = __ballot_sync(0xffffffffu, i < sg.hi && key == K);
+        tie_keep = (eq_run + __popc(b & lt_mask)) < need_eq;
+        eq_run += __popc(b);
       }
-      written += tot;
+      const float w = (i < sg.hi) ? wval(vi, key, tie_keep) : 0.0f;
+      const float xi = w * inv;
+      if (i < sg.hi) x[i] = xi;
+      const unsigned nzb = __ballot_sync(0xffffffffu, xi != 0.0f);
+      if (gi && xi != 0.0f) {
+        const int q = pos + __popc(nzb & lt_mask);
+        if (q < a.cap) {
+          gi[q] = i;
+          gv[q] = xi;
+        }
+      }
+      pos += __popc(nzb);
     }
   }
 
@@ -301,11 +415,24 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
     }
   }
 }
+}  // namespace
 
 cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,
                          StartState s, int *sup_idx, float *sup_val, Ctrl *ctrl_next,
                          cudaStream_t st) {
-  k_xstep<<<r, XT, 0, st>>>(a, V, ldv, X, ldx, s, sup_idx, sup_val, ctrl_next);
+  const size_t bytes = (size_t)a.p * sizeof(float);
+  if (bytes <= (size_t)XSTEP_SMEM_MAX) {
+    static bool configured = false;
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(k_xstep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           XSTEP_SMEM_MAX);
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    k_xstep<true><<<r, XT, bytes, st>>>(a, V, ldv, X, ldx, s, sup_idx, sup_val, ctrl_next);
+  } else {
+    k_xstep<false><<<r, XT, 0, st>>>(a, V, ldv, X, ldx, s, sup_idx, sup_val, ctrl_next);
+  }
   return cudaGetLastError();
 }
 

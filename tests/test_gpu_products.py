@@ -23,6 +23,16 @@ def lib():
     return spca
 
 
+def _bound(engine, K):
+    """Error bound relative to sum_k |a_k b_k|.  FP32 FMA chains (CUDA cores) round to nearest:
+    2e-6 covers K up to a few thousand.  The tensor core's FP32 accumulator truncates once per
+    MMA step (K/16 steps for the hi x hi accumulator), losing less than one ulp (2^-23
+    relative) each time, and on a sum whose terms share one sign these losses add up."""
+    if engine == "simt":
+        return 2e-6
+    return max(2e-6, (K / 16.0) * 2.0 ** -23)
+
+
 def _run(lib, h, form, engine, X):
     import torch
     r, p = X.shape
@@ -54,7 +64,8 @@ def test_products_match_fp64(lib, shape, engine, form):
     h.close()
     U_ref = X.astype(np.float64) @ A64.T                      # r x n
     scale_u = np.abs(X.astype(np.float64)) @ np.abs(A64).T    # bound of the rounding error
-    assert np.all(np.abs(U - U_ref) <= 2e-6 * scale_u + 1e-30), np.max(np.abs(U - U_ref) / (scale_u + 1e-30))
+    err_u = np.abs(U - U_ref) / (scale_u + 1e-30)
+    assert err_u.max() <= _bound(engine, p), err_u.max()
     # y from the GPU's own u (same sign / scale decisions), then v in FP64
     if form % 2 == 0:
         Yr = np.where(U >= 0, 1.0, -1.0)
@@ -63,7 +74,7 @@ def test_products_match_fp64(lib, shape, engine, form):
     V_ref = Yr @ A64
     scale_v = np.abs(Yr) @ np.abs(A64)
     err = np.abs(V - V_ref) / (scale_v + 1e-30)
-    assert err.max() <= 2e-6, err.max()
+    assert err.max() <= _bound(engine, n), err.max()
 
 
 def test_engines_agree_on_spiked(lib):
