@@ -41,6 +41,18 @@ __device__ __forceinline__ double block_sum_d(double v, double *red) {
   return t;
 }
 
+// FP32 sum over the block in a fixed order; every thread gets the total
+__device__ __forceinline__ float block_sum_f(float v, float *red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum_f(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float t = 0.0f;
+  for (int k = 0; k < nw; ++k) t += red[k];
+  return t;
+}
+
 __device__ __forceinline__ int block_sum_i(int v, int *red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   v = warp_sum_i(v);

@@ -129,7 +129,7 @@ template <int BN, int NA, int NB, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int M, int N,
               int kblocks, TcPairs pairs, float *__restrict__ out, int64_t ldo, const int *__restrict__ gate,
-              int *err) {
+              const int *__restrict__ n_dev, const int *__restrict__ col_map, int *err) {
   constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;       // 16 KB per P plane tile
   constexpr uint32_t B_BYTES = BN * TC_BK * 2;          // 32 KB (BN = 256) per Q plane tile
   constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
@@ -141,6 +141,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ volatile int abort_flag;
 
   if (gate && *gate == 0) return;   // uniform over the grid: the contraction is not needed
+  if (n_dev) N = *n_dev;            // columns (active starts) known only on the device
+  if ((int)blockIdx.y * BN >= N) return;
 
   uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int col = n0 + cb * 32 + j;
-            if (col < N) out[(int64_t)col * ldo + row] = v[j];
+            if (col < N) out[(int64_t)(col_map ? col_map[col] : col) * ldo + row] = v[j];
           }
         }
       }
@@ -246,13 +248,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // dst plane t (t < nplanes) of element e: the t-th BF16 piece of src (hi, mid, lo)
 __global__ void k_split_planes(const float *__restrict__ src, int64_t rows, int64_t cols, int64_t lds,
                                __nv_bfloat16 *__restrict__ dst, int64_t ldd, int64_t plane_stride,
-                               int nplanes, const int *__restrict__ gate) {
+                               int nplanes, const int *__restrict__ gate, const int *__restrict__ rows_dev,
+                               const int *__restrict__ row_map) {
   if (gate && *gate == 0) return;
+  if (rows_dev) rows = *rows_dev;
   const int64_t total = rows * cols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / cols, c = e - r * cols;
-    float a = src[r * lds + c];
+    float a = src[(row_map ? (int64_t)row_map[r] : r) * lds + c];
     const int64_t o = r * ldd + c;
     for (int t = 0; t < nplanes; ++t) {
       const __nv_bfloat16 h = __float2bfloat16_rn(a);
@@ -264,9 +268,9 @@ __global__ void k_split_planes(const float *__restrict__ src, int64_t rows, int6
 
 cudaError_t launch_split_planes(const float *src, int64_t rows, int64_t cols, int64_t lds, void *dst,
                                 int64_t ldd, int64_t plane_stride, int nplanes, const int *gate,
-                                cudaStream_t st) {
+                                const int *rows_dev, const int *row_map, cudaStream_t st) {
   k_split_planes<<<2 * 1216, 256, 0, st>>>(src, rows, cols, lds, static_cast<__nv_bfloat16 *>(dst), ldd,
-                                          plane_stride, nplanes, gate);
+                                          plane_stride, nplanes, gate, rows_dev, row_map);
   return cudaGetLastError();
 }
 
@@ -304,7 +308,8 @@ cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int
 namespace {
 template <int BN, int NA, int NB, int STAGES>
 cudaError_t launch_tc_impl(const CUtensorMap &P, const CUtensorMap &Q, int M, int N, int K, TcPairs pairs,
-                           float *out, int64_t ldo, const int *gate, int *err, cudaStream_t st) {
+                           float *out, int64_t ldo, const int *gate, const int *n_dev, const int *col_map,
+                           int *err, cudaStream_t st) {
   constexpr int STAGE_BYTES = NA * TC_BM * TC_BK * 2 + NB * BN * TC_BK * 2;
   constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
   auto kern = k_gemm_tc<BN, NA, NB, STAGES>;
@@ -316,17 +321,18 @@ cudaError_t launch_tc_impl(const CUtensorMap &P, const CUtensorMap &Q, int M, in
   }
   dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + BN - 1) / BN));
   const int kblocks = (K + TC_BK - 1) / TC_BK;
-  kern<<<grid, TC_THREADS, SMEM, st>>>(P, Q, M, N, kblocks, pairs, out, ldo, gate, err);
+  kern<<<grid, TC_THREADS, SMEM, st>>>(P, Q, M, N, kblocks, pairs, out, ldo, gate, n_dev, col_map, err);
   return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t launch_gemm_tc(const CUtensorMap &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
-                           TcPairs pairs, float *out, int64_t ldo, const int *gate, int *err, cudaStream_t st) {
+                           TcPairs pairs, float *out, int64_t ldo, const int *gate, const int *n_dev,
+                           const int *col_map, int *err, cudaStream_t st) {
   if (na == 3 && nb == 1)
-    return launch_tc_impl<256, 3, 1, 2>(P, Q, M, N, K, pairs, out, ldo, gate, err, st);
+    return launch_tc_impl<256, 3, 1, 2>(P, Q, M, N, K, pairs, out, ldo, gate, n_dev, col_map, err, st);
   if (na == 3 && nb == 3)
-    return launch_tc_impl<128, 3, 3, 2>(P, Q, M, N, K, pairs, out, ldo, gate, err, st);
+    return launch_tc_impl<128, 3, 3, 2>(P, Q, M, N, K, pairs, out, ldo, gate, n_dev, col_map, err, st);
   return cudaErrorInvalidValue;
 }
 

@@ -29,6 +29,7 @@ constexpr int XSTEP_SMEM_MAX = 200 * 1024;     // largest v staged in shared mem
 struct XShared {
   unsigned hist[256];
   double red_d[XW][2];
+  float red_f[XW][2];
   int red_i[XW][2];
   int wcnt[XW];                                // per-warp counts of one pass
   int woff[XW];                                // their exclusive prefix over warps
@@ -49,15 +50,40 @@ __device__ __forceinline__ Seg warp_seg(int p) {
   return s;
 }
 
-// block sums of (d0, d1, i0, i1) in one round; every thread gets them
-__device__ __forceinline__ void block_sum2(double &d0, double &d1, int &i0, int &i1, XShared &sh) {
+// block sums of (f0, f1, i0, i1) in one round, FP32 in a fixed order; every thread gets them.
+// (GB300's FP64 pipe is ~1/64 of FP32: FP64 stays out of the per-pass reductions.)
+__device__ __forceinline__ void block_sum2f(float &f0, float &f1, int &i0, int &i1, XShared &sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  d0 = warp_sum_d(d0); d1 = warp_sum_d(d1); i0 = warp_sum_i(i0); i1 = warp_sum_i(i1);
+  f0 = warp_sum_f(f0); f1 = warp_sum_f(f1); i0 = warp_sum_i(i0); i1 = warp_sum_i(i1);
   __syncthreads();
-  if (lane == 0) { sh.red_d[w][0] = d0; sh.red_d[w][1] = d1; sh.red_i[w][0] = i0; sh.red_i[w][1] = i1; }
+  if (lane == 0) { sh.red_f[w][0] = f0; sh.red_f[w][1] = f1; sh.red_i[w][0] = i0; sh.red_i[w][1] = i1; }
   __syncthreads();
-  d0 = d1 = 0.0; i0 = i1 = 0;
-  for (int k = 0; k < XW; ++k) { d0 += sh.red_d[k][0]; d1 += sh.red_d[k][1]; i0 += sh.red_i[k][0]; i1 += sh.red_i[k][1]; }
+  f0 = f1 = 0.0f; i0 = i1 = 0;
+  for (int k = 0; k < XW; ++k) { f0 += sh.red_f[k][0]; f1 += sh.red_f[k][1]; i0 += sh.red_i[k][0]; i1 += sh.red_i[k][1]; }
+}
+
+// block sums of two FP64 values (each thread's value already accurate); the warp partials are
+// combined by one thread, so the FP64 work is ~5 adds per thread
+__device__ __forceinline__ void block_sum2d(double &d0, double &d1, XShared &sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  d0 = warp_sum_d(d0); d1 = warp_sum_d(d1);
+  __syncthreads();
+  if (lane == 0) { sh.red_d[w][0] = d0; sh.red_d[w][1] = d1; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < XW; ++k) { a += sh.red_d[k][0]; b += sh.red_d[k][1]; }
+    sh.red_d[0][0] = a; sh.red_d[0][1] = b;
+  }
+  __syncthreads();
+  d0 = sh.red_d[0][0]; d1 = sh.red_d[0][1];
+}
+
+// compensated (Neumaier) FP32 accumulation: s + c carries the sum to ~2^-40 relative
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+  const float t = s + x;
+  c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+  s = t;
 }
 
 // per-warp count -> exclusive offsets over warps (sh.woff) and the block total
@@ -178,10 +204,9 @@ __device__ double lambda_s_bisect(const float *vv, int p, double s, uint32_t max
       in_lo += (key > lo && key < mid);
       in_hi += (key > mid && key < hi);
     }
-    double Sw = sw, Sw2 = sw2;
-    block_sum2(Sw, Sw2, in_lo, in_hi, sh);
-    const double phi = s * Sw2 - Sw * Sw;
-    if (phi < 0.0) {
+    block_sum2f(sw, sw2, in_lo, in_hi, sh);
+    const float phi = (float)s * sw2 - sw * sw;
+    if (phi < 0.0f) {
       lo = mid;
       if (in_hi == 0) break;  // no magnitude strictly inside (mid, hi): active set fixed
     } else {
@@ -189,18 +214,23 @@ __device__ double lambda_s_bisect(const float *vv, int p, double s, uint32_t max
       if (in_lo == 0) break;
     }
   }
-  // active set {key > lo}: k, S1, S2 in FP64, then the root of phi on this piece
-  double s1 = 0.0, s2 = 0.0;
+  // active set {key > lo}: k, S1, S2 (compensated per thread, FP64 across threads), then the
+  // root of phi on this piece in FP64
+  float a1 = 0.0f, c1 = 0.0f, a2 = 0.0f, c2 = 0.0f, fz = 0.0f;
   int kc = 0, unused = 0;
   for (int i = sg.lo + lane; i < sg.hi; i += 32) {
     const float a = fabsf(vv[i]);
     if (__float_as_uint(a) > lo) {
       ++kc;
-      s1 += (double)a;
-      s2 = fma((double)a, (double)a, s2);
+      kahan_add(a1, c1, a);
+      const float aa = a * a;
+      kahan_add(a2, c2, aa);
+      kahan_add(a2, c2, fmaf(a, a, -aa));   // exact square: aa + the FMA residual
     }
   }
-  block_sum2(s1, s2, kc, unused, sh);
+  double s1 = (double)a1 + (double)c1, s2 = (double)a2 + (double)c2;
+  block_sum2d(s1, s2, sh);
+  block_sum2f(fz, fz, kc, unused, sh);
   const double k = (double)kc;
   const double flo = (double)__uint_as_float(lo), fhi = (double)__uint_as_float(hi);
   double lam;
@@ -271,12 +301,11 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
       f2 = fmaf(av, av, f2);
       mk = max(mk, __float_as_uint(av));
     }
-    double S1 = f1, S2 = f2;
     int d0 = 0, d1 = 0;
-    block_sum2(S1, S2, d0, d1, sh);
+    block_sum2f(f1, f2, d0, d1, sh);
     const uint32_t maxkey = block_max_u(mk, sh.red_u);
     mode = 2;
-    if (a.s * S2 - S1 * S1 >= 0.0) {
+    if ((float)a.s * f2 - f1 * f1 >= 0.0f) {
       gam = 0.0;
       tkey = 0u;
       tval = 0.0f;
@@ -347,9 +376,10 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
       wnnz += __popc(__ballot_sync(0xffffffffu, w != 0.0f));
     }
   }
-  double sumsq = part, dz = 0.0;
+  float fz = 0.0f;
   int zz = 0, nnz_dummy = 0;
-  block_sum2(sumsq, dz, zz, nnz_dummy, sh);
+  block_sum2f(part, fz, zz, nnz_dummy, sh);
+  const double sumsq = (double)part;
   const int nnz = warp_offsets(wnnz, sh);   // sh.woff: each warp's first slot in the support list
   const double nrm = sqrt(sumsq);
 
@@ -408,10 +438,8 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
       }
       st.F_prev[c] = F;
       st.status[c] = status;
-      if (status == ST_ACTIVE && ctrl) {
-        atomicAdd(&ctrl->active, 1);
-        if (nnz > a.sparse_cap) atomicOr(&ctrl->need_dense, 1);
-      }
+      // (the active count and list for the next sweep are built after this kernel)
+      if (status == ST_ACTIVE && ctrl && nnz > a.sparse_cap) atomicOr(&ctrl->need_dense, 1);
     }
   }
 }

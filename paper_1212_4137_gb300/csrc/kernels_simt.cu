@@ -106,17 +106,17 @@ __device__ __forceinline__ double bm_normal(uint64_t key, uint64_t i) {
 __global__ void __launch_bounds__(256) k_start_init(const float *__restrict__ x0, int64_t ld0,
                                                     uint64_t key, int p, float *__restrict__ X,
                                                     int64_t ldX, StartState s, double gamma0) {
-  __shared__ double red[32];
+  __shared__ float redf[32];
   const int c = blockIdx.x;
   float *x = X + (int64_t)c * ldX;
   const float *g = x0 ? x0 + (int64_t)c * ld0 : nullptr;
-  double part = 0.0;
+  float part = 0.0f;
   for (int j = threadIdx.x; j < p; j += blockDim.x) {
     const float gj = g ? g[j] : (float)bm_normal(key, (uint64_t)c * (uint64_t)p + (uint64_t)j);
     x[j] = gj;
-    part += (double)gj * (double)gj;
+    part = fmaf(gj, gj, part);
   }
-  const double nrm = sqrt(block_sum_d(part, red));
+  const double nrm = sqrt((double)block_sum_f(part, redf));
   const float inv = nrm > 0.0 ? (float)(1.0 / nrm) : 0.0f;
   for (int j = threadIdx.x; j < p; j += blockDim.x) x[j] = x[j] * inv;
   if (threadIdx.x == 0) {
@@ -150,14 +150,14 @@ cudaError_t launch_start_init(const float *x0, int64_t ld0, uint64_t seed, int r
 __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict__ U, int64_t ldu,
                                                int n, float *__restrict__ Y,
                                                __nv_bfloat16 *__restrict__ Ypl, int64_t pstride,
-                                               StartState s, float *__restrict__ X, int64_t ldX,
-                                               int p) {
-  __shared__ double red[32];
+                                               const int *__restrict__ rank, StartState s,
+                                               float *__restrict__ X, int64_t ldX, int p) {
+  __shared__ float redf[32];
   const int c = blockIdx.x;
   if (s.status[c] != ST_ACTIVE) return;
   const float *u = U + (int64_t)c * ldu;
   float *y = Y ? Y + (int64_t)c * ldu : nullptr;
-  __nv_bfloat16 *yp = Ypl ? Ypl + (int64_t)c * ldu : nullptr;
+  __nv_bfloat16 *yp = Ypl ? Ypl + (int64_t)(rank ? rank[c] : c) * ldu : nullptr;
   if (threadIdx.x == 0) s.iters[c] += 1;
   if (is_l1_var(form)) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -167,9 +167,9 @@ __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict
     }
     return;
   }
-  double part = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) part += (double)u[i] * (double)u[i];
-  const double nrm = sqrt(block_sum_d(part, red));
+  float part = 0.0f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) part = fmaf(u[i], u[i], part);
+  const double nrm = sqrt((double)block_sum_f(part, redf));
   if (nrm == 0.0) {
     float *x = X + (int64_t)c * ldX;
     for (int j = threadIdx.x; j < p; j += blockDim.x) x[j] = 0.0f;
@@ -196,10 +196,36 @@ __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict
 }
 
 cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, float *Y, void *Ypl,
-                         int64_t plane_stride, StartState s, float *X, int64_t ldX, int p,
-                         cudaStream_t st) {
-  k_ystep<<<r, 256, 0, st>>>(form, U, ldu, n, Y, static_cast<__nv_bfloat16 *>(Ypl), plane_stride, s,
-                             X, ldX, p);
+                         int64_t plane_stride, const int *rank, StartState s, float *X, int64_t ldX,
+                         int p, cudaStream_t st) {
+  k_ystep<<<r, 256, 0, st>>>(form, U, ldu, n, Y, static_cast<__nv_bfloat16 *>(Ypl), plane_stride, rank,
+                             s, X, ldX, p);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ active-start list
+// one CTA: ordered compaction of the flags status[c] == ST_ACTIVE over r starts
+__global__ void __launch_bounds__(1024) k_active_list(const int *__restrict__ status, int r,
+                                                      int *__restrict__ act, int *__restrict__ rank,
+                                                      int *__restrict__ count) {
+  __shared__ int red[32];
+  int base_pos = 0;
+  for (int base = 0; base < r; base += blockDim.x) {
+    const int c = base + threadIdx.x;
+    const bool on = c < r && status[c] == ST_ACTIVE;
+    int tot;
+    const int pos = base_pos + block_excl_scan_flag(on, red, &tot);
+    if (on) {
+      act[pos] = c;
+      rank[c] = pos;
+    }
+    base_pos += tot;
+  }
+  if (threadIdx.x == 0) *count = base_pos;
+}
+
+cudaError_t launch_active_list(const int *status, int r, int *act, int *rank, int *count, cudaStream_t st) {
+  k_active_list<<<1, 1024, 0, st>>>(status, r, act, rank, count);
   return cudaGetLastError();
 }
 

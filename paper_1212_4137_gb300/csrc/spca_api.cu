@@ -28,6 +28,7 @@ struct spca_handle {
   CUtensorMap tmX3{}, tmY1{}, tmY3{};      // Q-operand maps: X planes, y = +-1, y planes
   int *sup_idx = nullptr;
   float *sup_val = nullptr;
+  int *act = nullptr, *rank = nullptr;     // ordered list of the active starts and its inverse
   int *status = nullptr, *iters = nullptr, *nnz = nullptr;
   double *F = nullptr, *F_prev = nullptr, *gamma = nullptr, *f = nullptr, *ev = nullptr;
   float *thr = nullptr;
@@ -118,14 +119,15 @@ cudaError_t dalloc(T **p, size_t count, size_t elem = sizeof(T)) {
 }
 
 void free_workspace(spca_handle *h) {
-  void *ptrs[] = {h->X, h->V, h->U, h->Y, h->Xpl, h->Ypl, h->sup_idx, h->sup_val, h->status, h->iters,
-                  h->nnz, h->F, h->F_prev, h->gamma, h->f, h->ev, h->thr, h->partials, h->ctrl, h->best,
-                  h->y_out, h->x_out, h->support_out, h->nnz_out};
+  void *ptrs[] = {h->X, h->V, h->U, h->Y, h->Xpl, h->Ypl, h->sup_idx, h->sup_val, h->act, h->rank,
+                  h->status, h->iters, h->nnz, h->F, h->F_prev, h->gamma, h->f, h->ev, h->thr,
+                  h->partials, h->ctrl, h->best, h->y_out, h->x_out, h->support_out, h->nnz_out};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   h->X = h->V = h->U = h->Y = nullptr;
   h->Xpl = h->Ypl = nullptr;
   h->sup_idx = nullptr; h->sup_val = nullptr;
+  h->act = h->rank = nullptr;
   h->status = h->iters = h->nnz = nullptr;
   h->F = h->F_prev = h->gamma = h->f = h->ev = nullptr;
   h->thr = nullptr; h->partials = nullptr; h->ctrl = nullptr; h->best = nullptr;
@@ -146,6 +148,7 @@ int ensure_workspace(spca_handle *h, int r) {
   CK(dalloc(&h->Y, (size_t)r * h->ldU));
   CK(dalloc(&h->sup_idx, (size_t)r * p));
   CK(dalloc(&h->sup_val, (size_t)r * p));
+  CK(dalloc(&h->act, r)); CK(dalloc(&h->rank, r));
   CK(dalloc(&h->status, r)); CK(dalloc(&h->iters, r)); CK(dalloc(&h->nnz, r));
   CK(dalloc(&h->F, r)); CK(dalloc(&h->F_prev, r)); CK(dalloc(&h->gamma, r));
   CK(dalloc(&h->f, r)); CK(dalloc(&h->ev, r)); CK(dalloc(&h->thr, r));
@@ -233,16 +236,18 @@ TcPairs pairs_sign() {
   return q;
 }
 
-// u = A x for every row of h->X: dense contraction (gated: runs only if *gate != 0)
-int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate) {
+// u = A x for every active row of h->X: dense contraction (gated: runs only if *gate != 0).  The
+// tensor-core engine packs the active starts (h->act, count *nact) into consecutive plane rows.
+int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int *nact) {
   const int n = (int)h->n, p = (int)h->p;
   cudaStream_t st = h->stream;
   if (engine == SPCA_ENGINE_TC) {
     CK(timed(h, SPCA_K_U_DENSE, 2, [&] {
       cudaError_t e = launch_split_planes(h->X, r, p, h->ldX, h->Xpl, h->ldX, (int64_t)h->r_cap * h->ldX, 3,
-                                          gate, st);
+                                          gate, nact, h->act, st);
       if (e != cudaSuccess) return e;
-      return launch_gemm_tc(h->tmA, 3, h->tmX3, 3, n, r, p, pairs_general(), h->U, h->ldU, gate, h->dev_err, st);
+      return launch_gemm_tc(h->tmA, 3, h->tmX3, 3, n, r, p, pairs_general(), h->U, h->ldU, gate, nact, h->act,
+                            h->dev_err, st);
     }));
   } else {
     CK(timed(h, SPCA_K_U_DENSE, 1, [&] {
@@ -252,21 +257,22 @@ int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate) {
   return SPCA_OK;
 }
 
-// y-step and v = A^T y for every active row
-int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S) {
+// y-step and v = A^T y for every active row (tensor-core engine: packed active rows, see above)
+int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const int *nact) {
   const int n = (int)h->n, p = (int)h->p;
   cudaStream_t st = h->stream;
   const bool tc = engine == SPCA_ENGINE_TC;
   const int64_t ypstride = (int64_t)h->r_cap * h->ldU;
   CK(timed(h, SPCA_K_YSTEP, 1, [&] {
-    return launch_ystep(form, h->U, h->ldU, n, r, tc ? nullptr : h->Y, tc ? h->Ypl : nullptr, ypstride, S,
-                        h->X, h->ldX, p, st);
+    return launch_ystep(form, h->U, h->ldU, n, r, tc ? nullptr : h->Y, tc ? h->Ypl : nullptr, ypstride,
+                        tc ? h->rank : nullptr, S, h->X, h->ldX, p, st);
   }));
   if (tc) {
     const bool l1 = is_l1_var(form);
     CK(timed(h, SPCA_K_V, 1, [&] {
       return launch_gemm_tc(h->tmAT, 3, l1 ? h->tmY1 : h->tmY3, l1 ? 1 : 3, p, r, n,
-                            l1 ? pairs_sign() : pairs_general(), h->V, h->ldX, nullptr, h->dev_err, st);
+                            l1 ? pairs_sign() : pairs_general(), h->V, h->ldX, nullptr, nact, h->act,
+                            h->dev_err, st);
     }));
   } else {
     CK(timed(h, SPCA_K_V, 1, [&] {
@@ -405,10 +411,10 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
       CK(dalloc(&h->ATpl, (size_t)3 * p * h->ldAT, 2));
       CK(timed(h, SPCA_K_PREP, 2, [&] {
         cudaError_t e = launch_split_planes(h->A32, n, h->ldA, h->ldA, h->Apl, h->ldA, n * h->ldA, 3, nullptr,
-                                            h->stream);
+                                            nullptr, nullptr, h->stream);
         if (e != cudaSuccess) return e;
         return launch_split_planes(h->AT32, p, h->ldAT, h->ldAT, h->ATpl, h->ldAT, p * h->ldAT, 3, nullptr,
-                                   h->stream);
+                                   nullptr, nullptr, h->stream);
       }));
       CK(make_plane_map(&h->tmA, h->Apl, n, h->ldA, 3, 128));
       CK(make_plane_map(&h->tmAT, h->ATpl, p, h->ldAT, 3, 128));
@@ -460,8 +466,9 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
                        cudaMemcpyDeviceToDevice, st));
   CK(cudaMemsetAsync(h->status, 0xFF, (size_t)r * sizeof(int), st));   // every row active (-1)
   CK(cudaMemsetAsync(h->iters, 0, (size_t)r * sizeof(int), st));
-  RC(sweep_u_dense(h, eng, r, nullptr));
-  RC(sweep_y_v(h, eng, form, r, state_of(h)));
+  CK(launch_active_list(h->status, r, h->act, h->rank, &h->ctrl[0].active, st));
+  RC(sweep_u_dense(h, eng, r, nullptr, &h->ctrl[0].active));
+  RC(sweep_y_v(h, eng, form, r, state_of(h), &h->ctrl[0].active));
   CK(cudaMemcpy2DAsync(U, ldu * sizeof(float), h->U, h->ldU * sizeof(float), (size_t)n * sizeof(float), r,
                        cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpy2DAsync(V, ldv * sizeof(float), h->V, h->ldX * sizeof(float), (size_t)p * sizeof(float), r,
@@ -503,6 +510,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   }));
   h->h_ctrl[0].active = r; h->h_ctrl[0].need_dense = 1; h->h_ctrl[0].err = 0; h->h_ctrl[0].pad = 0;
   CK(cudaMemcpyAsync(h->ctrl, h->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+  CK(timed(h, SPCA_K_XSTEP, 1, [&] { return launch_active_list(h->status, r, h->act, h->rank, &h->ctrl[0].active, st); }));
   CK(cudaStreamSynchronize(st));  // h_ctrl is reused below
 
   // ---- the sweeps (Algorithm 2)
@@ -518,19 +526,21 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   for (int k = 1; k <= P.max_iter; ++k) {
     Ctrl *cur = h->ctrl + ((k - 1) & 1), *nxt = h->ctrl + (k & 1);
     // u = A x: dense contraction, or the support gather when every support is small
-    RC(sweep_u_dense(h, engine, r, &cur->need_dense));
+    RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active));
     CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
       return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
                                  &cur->need_dense, st);
     }));
     // y-step, v = A^T y
-    RC(sweep_y_v(h, engine, form, r, S));
+    RC(sweep_y_v(h, engine, form, r, S, &cur->active));
     CK(cudaMemsetAsync(nxt, 0, sizeof(Ctrl), st));
     xa.calibrate = target && k <= C;
     xa.per_start_thr = target && k > C;
     xa.stop_test = P.tol >= 0.0 && k >= 2 && k >= C + 1;
-    CK(timed(h, SPCA_K_XSTEP, 1, [&] {
-      return launch_xstep(xa, h->V, h->ldX, r, h->X, h->ldX, S, h->sup_idx, h->sup_val, nxt, st);
+    CK(timed(h, SPCA_K_XSTEP, 2, [&] {
+      cudaError_t e = launch_xstep(xa, h->V, h->ldX, r, h->X, h->ldX, S, h->sup_idx, h->sup_val, nxt, st);
+      if (e != cudaSuccess) return e;
+      return launch_active_list(h->status, r, h->act, h->rank, &nxt->active, st);   // for the next sweep
     }));
     if (k == P.max_iter || k % check_every == 0) {
       CK(cudaMemcpyAsync(h->h_ctrl, nxt, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));

@@ -99,12 +99,12 @@ cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int 
                                 const float *sup_val, int cap, StartState s, int r, float *U,
                                 int64_t ldu, const int *gate, cudaStream_t st);
 
-// y-step (S1 / S2 of Table 3) for active starts.  Writes Y as FP32 (Y != nullptr) and/or as
-// BF16 planes (Ypl != nullptr: 1 plane of +-1 for L1 variance, 3 planes hi/mid/lo for L2
-// variance, plane t at Ypl + t * plane_stride)
+// y-step (S1 / S2 of Table 3) for active starts.  Writes Y as FP32 (Y != nullptr, row c) and/or
+// as BF16 planes (Ypl != nullptr, row rank[c] when rank is given, else c: 1 plane of +-1 for L1
+// variance, 3 planes hi/mid/lo for L2 variance, plane t at Ypl + t * plane_stride)
 cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, float *Y,
-                         void *Ypl, int64_t plane_stride, StartState s, float *X, int64_t ldX,
-                         int p, cudaStream_t st);
+                         void *Ypl, int64_t plane_stride, const int *rank, StartState s, float *X,
+                         int64_t ldX, int p, cudaStream_t st);
 
 // ---------------------------------------------------------------- tcgen05 engine
 struct TcPairs {      // plane products P plane a[q] x Q plane b[q], q < n; the hi x hi product
@@ -117,15 +117,21 @@ struct TcPairs {      // plane products P plane a[q] x Q plane b[q], q < n; the 
 cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int64_t ld, int planes,
                            int box_rows);
 int tc_box_rows(int nb);   // Q-operand box height for nb planes (the tile's N)
-// out[c * ldo + m] = sum_q sum_k P_{a_q}[m, k] Q_{b_q}[c, k], m < M, c < N; with gate != nullptr
-// nothing runs unless *gate != 0; a timed-out wait sets *err = SPCA_E_TIMEOUT
+// out[map(c) * ldo + m] = sum_q sum_k P_{a_q}[m, k] Q_{b_q}[c, k], m < M, c < N (N = *n_dev when
+// n_dev != nullptr; map = col_map when given, else the identity); with gate != nullptr nothing
+// runs unless *gate != 0; a timed-out wait sets *err = SPCA_E_TIMEOUT
 cudaError_t launch_gemm_tc(const CUtensorMap &P, int na, const CUtensorMap &Q, int nb, int M, int N,
-                           int K, TcPairs pairs, float *out, int64_t ldo, const int *gate, int *err,
-                           cudaStream_t st);
-// BF16 planes of an FP32 matrix (plane t at dst + t * plane_stride elements); gated like above
+                           int K, TcPairs pairs, float *out, int64_t ldo, const int *gate,
+                           const int *n_dev, const int *col_map, int *err, cudaStream_t st);
+// BF16 planes of an FP32 matrix (plane t at dst + t * plane_stride elements): destination row r
+// comes from source row row_map[r] (identity when null), r < rows (*rows_dev when given); gated
 cudaError_t launch_split_planes(const float *src, int64_t rows, int64_t cols, int64_t lds, void *dst,
                                 int64_t ldd, int64_t plane_stride, int nplanes, const int *gate,
-                                cudaStream_t st);
+                                const int *rows_dev, const int *row_map, cudaStream_t st);
+// ordered list of the active starts (status == ST_ACTIVE): act[k] = c and rank[c] = k for the
+// k-th active start; the count goes to *count
+cudaError_t launch_active_list(const int *status, int r, int *act, int *rank, int *count,
+                               cudaStream_t st);
 
 // x-step (S3..S6), objective F, stopping rule, support lists
 cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,
