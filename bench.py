@@ -158,11 +158,12 @@ def run_ours(args, w, rank, world, local_rank):
             if times is not None:
                 times.append(time.perf_counter() - t0)
                 l1, m1 = h.profile_query(spca.SPCA_K_V)
-                # tensor-pipe flops of v = A^T y: every launch contracts all r columns with
-                # 3 (L1 variance, y = +-1) or 6 (L2 variance) BF16 plane products
+                # algorithmic tensor-pipe flops of v = A^T y: each sweep of each active start
+                # contracts one column with 3 (L1 variance, y = +-1) or 6 (L2 variance) BF16
+                # plane products (frozen starts are not contracted)
                 vstats["launches"] += l1 - l0
                 vstats["ms"] += m1 - m0
-                vstats["tensor_flop"] += (l1 - l0) * 2.0 * n * p * r * (3 if form % 2 == 0 else 6)
+                vstats["tensor_flop"] += out["sweeps_total"] * 2.0 * n * p * (3 if form % 2 == 0 else 6)
             sw += out["sweeps_total"]
         return sw
 
@@ -233,7 +234,7 @@ def run_ours(args, w, rank, world, local_rank):
                 "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
-                "per_launch": "2*n*p*r*(3 plane products for L1 variance, 6 for L2 variance) tensor flop",
+                "per_unit": "2*n*p*(3 plane products for L1 variance, 6 for L2 variance) BF16 flop per sweep*start (active starts only)",
                 "launches": vstats["launches"], "avg_launch_ms": round(vstats["ms"] / max(1, vstats["launches"]), 4),
                 "fp32_equivalent_algorithmic_tflops": round(alg, 1)}
     elif dom == "xstep" and kern["xstep"][1] > 0:
