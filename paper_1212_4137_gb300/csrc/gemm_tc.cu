@@ -18,7 +18,8 @@
 //   D[m, c] = sum_{(i,j) in pairs} sum_k P_i[m, k] Q_j[c, k]      out[c * ldo + m] = D[m, c]
 //
 // P (M x K) and Q (N x K) are K-contiguous BF16 planes; plane i of P starts at row i * M_alloc.
-// Tile 128 (M) x BN (N) x 64 (K); STAGES-deep TMA -> MMA pipeline over mbarriers.
+// Tile 128 (M) x BN (N) x 32 (K) in 64B-swizzled rows; STAGES-deep TMA -> MMA pipeline (5 stages
+// with one Q plane, 4 with three) so that several loads are in flight while the MMAs run.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -32,7 +33,7 @@ namespace spca {
 namespace {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BK = 64;                 // 64 bf16 = 128 B rows: one 128B swizzle atom wide
+constexpr int TC_BK = 32;                 // 32 bf16 = 64 B rows: one 64B swizzle atom wide
 constexpr int TC_THREADS = 192;           // warp 0 TMA + TMEM alloc, warp 1 MMA, warps 2-5 epilogue
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;   // bounded waits: 2 s, then error + exit
 
@@ -81,14 +82,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
       ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
-// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row core groups 1024 B apart
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// shared-memory matrix descriptor: K-major, 64B swizzle, 8-row core groups 512 B apart
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
   d |= (uint64_t)1 << 16;                      // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)(512 >> 4) << 32;             // stride byte offset: 8 rows x 64 B
   d |= (uint64_t)1 << 46;                      // descriptor version (tcgen05)
-  d |= (uint64_t)2 << 61;                      // swizzle: 128B
+  d |= (uint64_t)4 << 61;                      // swizzle: 64B
   return d;
 }
 // instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, M = 128, N = BN
@@ -130,8 +131,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int M, int N,
               int kblocks, TcPairs pairs, float *__restrict__ out, int64_t ldo, const int *__restrict__ gate,
               const int *__restrict__ n_dev, const int *__restrict__ col_map, int *err) {
-  constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;       // 16 KB per P plane tile
-  constexpr uint32_t B_BYTES = BN * TC_BK * 2;          // 32 KB (BN = 256) per Q plane tile
+  constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;       // 8 KB per P plane tile
+  constexpr uint32_t B_BYTES = BN * TC_BK * 2;          // 16 KB (BN = 256) per Q plane tile
   constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
   constexpr uint32_t TMEM_COLS = 2 * BN;                // two FP32 accumulators of BN columns x 128 lanes
 
@@ -142,11 +143,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (gate && *gate == 0) return;   // uniform over the grid: the contraction is not needed
   if (n_dev) N = *n_dev;            // columns (active starts) known only on the device
-  if ((int)blockIdx.y * BN >= N) return;
+  if ((int)blockIdx.x * BN >= N) return;
 
   uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;   // N fastest: CTAs sharing a P tile run together
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const bool first = kb == 0 && q == (main ? pairs.first_main : pairs.first_corr);
 #pragma unroll
         for (int kk = 0; kk < TC_BK / 16; ++kk) {
-          mma_bf16(d, sw128_desc(a_base + kk * 32), sw128_desc(b_base + kk * 32), idesc,
+          mma_bf16(d, sw64_desc(a_base + kk * 32), sw64_desc(b_base + kk * 32), idesc,
                    (first && kk == 0) ? 0u : 1u);
         }
       }
@@ -300,7 +301,7 @@ cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int
   cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -319,7 +320,7 @@ cudaError_t launch_tc_impl(const CUtensorMap &P, const CUtensorMap &Q, int M, in
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + BN - 1) / BN));
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + TC_BM - 1) / TC_BM));
   const int kblocks = (K + TC_BK - 1) / TC_BK;
   kern<<<grid, TC_THREADS, SMEM, st>>>(P, Q, M, N, kblocks, pairs, out, ldo, gate, n_dev, col_map, err);
   return cudaGetLastError();
@@ -330,9 +331,9 @@ cudaError_t launch_gemm_tc(const CUtensorMap &P, int na, const CUtensorMap &Q, i
                            TcPairs pairs, float *out, int64_t ldo, const int *gate, const int *n_dev,
                            const int *col_map, int *err, cudaStream_t st) {
   if (na == 3 && nb == 1)
-    return launch_tc_impl<256, 3, 1, 2>(P, Q, M, N, K, pairs, out, ldo, gate, n_dev, col_map, err, st);
+    return launch_tc_impl<256, 3, 1, 5>(P, Q, M, N, K, pairs, out, ldo, gate, n_dev, col_map, err, st);
   if (na == 3 && nb == 3)
-    return launch_tc_impl<128, 3, 3, 2>(P, Q, M, N, K, pairs, out, ldo, gate, n_dev, col_map, err, st);
+    return launch_tc_impl<128, 3, 3, 4>(P, Q, M, N, K, pairs, out, ldo, gate, n_dev, col_map, err, st);
   return cudaErrorInvalidValue;
 }
 
