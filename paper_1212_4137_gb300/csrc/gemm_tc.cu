@@ -18,8 +18,12 @@
 //   D[m, c] = sum_{(i,j) in pairs} sum_k P_i[m, k] Q_j[c, k]      out[c * ldo + m] = D[m, c]
 //
 // P (M x K) and Q (N x K) are K-contiguous BF16 planes; plane i of P starts at row i * M_alloc.
-// Tile 128 (M) x BN (N) x 32 (K) in 64B-swizzled rows; STAGES-deep TMA -> MMA pipeline (5 stages
-// with one Q plane, 4 with three) so that several loads are in flight while the MMAs run.
+// Tile 128 (M) x BN (N) x 64 (K); 2-stage TMA -> MMA pipeline over mbarriers.  The operand
+// delivery from L2, not the MMAs, bounds this contraction (measured: the time is the same with
+// 1, 2 or 3 plane products per stage), and the three P planes are its largest stream.  So the
+// C CTAs (C = 1, 2, 4) that compute adjacent N tiles of one M tile form a thread-block cluster:
+// each loads 1/C of the P tile and multicasts it to all C, and each CTA's MMA commit frees the
+// stage in every CTA of the cluster.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -33,7 +37,7 @@ namespace spca {
 namespace {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BK = 32;                 // 32 bf16 = 64 B rows: one 64B swizzle atom wide
+constexpr int TC_BK = 64;                 // 64 bf16 = 128 B rows: one 128B swizzle atom wide
 constexpr int TC_THREADS = 192;           // warp 0 TMA + TMEM alloc, warp 1 MMA, warps 2-5 epilogue
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;   // bounded waits: 2 s, then error + exit
 
@@ -82,15 +86,44 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
       ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
-// shared-memory matrix descriptor: K-major, 64B swizzle, 8-row core groups 512 B apart
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row core groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
   d |= (uint64_t)1 << 16;                      // leading byte offset (unused for this layout)
-  d |= (uint64_t)(512 >> 4) << 32;             // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
   d |= (uint64_t)1 << 46;                      // descriptor version (tcgen05)
-  d |= (uint64_t)4 << 61;                      // swizzle: 64B
+  d |= (uint64_t)2 << 61;                      // swizzle: 128B
   return d;
+}
+// multicast variant: the box lands at the same offset in every CTA of ctaMask, and the
+// complete_tx goes to the barrier at the same offset in each of them
+__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
+                                               uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3, %4}], [%5], %6;"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+      ::"r"(bar), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 // instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, M = 128, N = BN
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -131,8 +164,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int M, int N,
               int kblocks, TcPairs pairs, float *__restrict__ out, int64_t ldo, const int *__restrict__ gate,
               const int *__restrict__ n_dev, const int *__restrict__ col_map, int *err) {
-  constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;       // 8 KB per P plane tile
-  constexpr uint32_t B_BYTES = BN * TC_BK * 2;          // 16 KB (BN = 256) per Q plane tile
+  constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;       // 16 KB per P plane tile
+  constexpr uint32_t B_BYTES = BN * TC_BK * 2;          // 32 KB (BN = 256) per Q plane tile
   constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
   constexpr uint32_t TMEM_COLS = 2 * BN;                // two FP32 accumulators of BN columns x 128 lanes
 
@@ -141,18 +174,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
+  const uint32_t crank = cluster_rank(), csize = cluster_size();
   if (gate && *gate == 0) return;   // uniform over the grid: the contraction is not needed
   if (n_dev) N = *n_dev;            // columns (active starts) known only on the device
-  if ((int)blockIdx.x * BN >= N) return;
+  if ((int)(blockIdx.x - crank) * BN >= N) return;   // uniform over the cluster
 
   uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;   // N fastest: CTAs sharing a P tile run together
+  const uint16_t cmask = (uint16_t)((1u << csize) - 1u);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), csize);         // one MMA commit from every CTA
     }
     mbar_init(smem_u32(&accum_bar), 1);
     abort_flag = 0;
@@ -167,10 +202,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  cluster_sync_all();               // every CTA's barriers exist before any multicast reaches them
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------------- TMA producer
+    const int rows_per = TC_BM / (int)csize;                    // this CTA's slice of the P tile
+    const uint32_t slice = (uint32_t)(crank * rows_per) * (TC_BK * 2);
     for (int kb = 0; kb < kblocks; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
@@ -179,7 +217,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_expect_tx(fb, STAGE_BYTES);
       uint8_t *st = tiles + (size_t)s * STAGE_BYTES;
 #pragma unroll
-      for (int a = 0; a < NA; ++a) tma_load_3d(smem_u32(st + a * A_BYTES), &tmP, kb * TC_BK, m0, a, fb);
+      for (int a = 0; a < NA; ++a) {
+        if (csize == 1)
+          tma_load_3d(smem_u32(st + a * A_BYTES), &tmP, kb * TC_BK, m0, a, fb);
+        else
+          tma_load_3d_mc(smem_u32(st + a * A_BYTES) + slice, &tmP, kb * TC_BK, m0 + (int)crank * rows_per, a, fb,
+                         cmask);
+      }
 #pragma unroll
       for (int b = 0; b < NB; ++b)
         tma_load_3d(smem_u32(st + NA * A_BYTES + b * B_BYTES), &tmQ, kb * TC_BK, n0, b, fb);
@@ -202,11 +246,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const bool first = kb == 0 && q == (main ? pairs.first_main : pairs.first_corr);
 #pragma unroll
         for (int kk = 0; kk < TC_BK / 16; ++kk) {
-          mma_bf16(d, sw64_desc(a_base + kk * 32), sw64_desc(b_base + kk * 32), idesc,
+          mma_bf16(d, sw128_desc(a_base + kk * 32), sw128_desc(b_base + kk * 32), idesc,
                    (first && kk == 0) ? 0u : 1u);
         }
       }
-      mma_commit(smem_u32(&empty_bar[s]));   // frees the stage once these MMAs have read it
+      // frees the stage (in every CTA of the cluster) once these MMAs have read it
+      if (csize == 1)
+        mma_commit(smem_u32(&empty_bar[s]));
+      else
+        mma_commit_mc(smem_u32(&empty_bar[s]), cmask);
     }
     if (ok) mma_commit(smem_u32(&accum_bar));  // accumulator complete
   } else if (warp >= 2) {
@@ -243,6 +291,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
+  // no CTA leaves while a peer may still multicast into it or arrive on its barriers
+  cluster_sync_all();
 }
 
 // ---------------------------------------------------------------------- planes
@@ -301,14 +351,22 @@ cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int
   cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld, int planes) {
+  for (int i = 0; i < 3; ++i) {
+    cudaError_t e = make_plane_map(&maps->m[i], base, rows, ld, planes, TC_BM >> i);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 namespace {
 template <int BN, int NA, int NB, int STAGES>
-cudaError_t launch_tc_impl(const CUtensorMap &P, const CUtensorMap &Q, int M, int N, int K, TcPairs pairs,
+cudaError_t launch_tc_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, int K, TcPairs pairs,
                            float *out, int64_t ldo, const int *gate, const int *n_dev, const int *col_map,
                            int *err, cudaStream_t st) {
   constexpr int STAGE_BYTES = NA * TC_BM * TC_BK * 2 + NB * BN * TC_BK * 2;
@@ -320,20 +378,36 @@ cudaError_t launch_tc_impl(const CUtensorMap &P, const CUtensorMap &Q, int M, in
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + TC_BM - 1) / TC_BM));
+  // cluster of C CTAs over adjacent N tiles (C = 1, 2, 4: at most the number of N tiles)
+  const int ntn = (N + BN - 1) / BN;
+  int lg = 0;
+  while (lg < 2 && (2 << lg) <= ntn) ++lg;
+  const int C = 1 << lg;
+  dim3 grid((unsigned)((ntn + C - 1) / C * C), (unsigned)((M + TC_BM - 1) / TC_BM));
   const int kblocks = (K + TC_BK - 1) / TC_BK;
-  kern<<<grid, TC_THREADS, SMEM, st>>>(P, Q, M, N, kblocks, pairs, out, ldo, gate, n_dev, col_map, err);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, P.m[lg], Q, M, N, kblocks, pairs, out, ldo, gate, n_dev, col_map, err);
 }
 }  // namespace
 
-cudaError_t launch_gemm_tc(const CUtensorMap &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
+cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
                            TcPairs pairs, float *out, int64_t ldo, const int *gate, const int *n_dev,
                            const int *col_map, int *err, cudaStream_t st) {
   if (na == 3 && nb == 1)
-    return launch_tc_impl<256, 3, 1, 5>(P, Q, M, N, K, pairs, out, ldo, gate, n_dev, col_map, err, st);
+    return launch_tc_impl<256, 3, 1, 2>(P, Q, M, N, K, pairs, out, ldo, gate, n_dev, col_map, err, st);
   if (na == 3 && nb == 3)
-    return launch_tc_impl<128, 3, 3, 4>(P, Q, M, N, K, pairs, out, ldo, gate, n_dev, col_map, err, st);
+    return launch_tc_impl<128, 3, 3, 2>(P, Q, M, N, K, pairs, out, ldo, gate, n_dev, col_map, err, st);
   return cudaErrorInvalidValue;
 }
 

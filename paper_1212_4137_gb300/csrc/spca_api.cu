@@ -18,7 +18,7 @@ struct spca_handle {
   float *A32 = nullptr, *AT32 = nullptr;   // FP32 copies
   bool tc_ok = false;                      // the device has tcgen05 tensor cores (sm_100+)
   void *Apl = nullptr, *ATpl = nullptr;    // 3 BF16 planes each (hi, mid, lo)
-  CUtensorMap tmA{}, tmAT{};               // P-operand maps of the planes (128-row boxes)
+  PMaps pmA{}, pmAT{};                     // P-operand maps of the planes (per cluster size)
 
   // per-solve workspace, grown on demand
   int r_cap = 0;
@@ -238,7 +238,7 @@ TcPairs pairs_sign() {
 
 // u = A x for every active row of h->X: dense contraction (gated: runs only if *gate != 0).  The
 // tensor-core engine packs the active starts (h->act, count *nact) into consecutive plane rows.
-int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int *nact) {
+int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int *nact, int nhost) {
   const int n = (int)h->n, p = (int)h->p;
   cudaStream_t st = h->stream;
   if (engine == SPCA_ENGINE_TC) {
@@ -246,7 +246,7 @@ int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int 
       cudaError_t e = launch_split_planes(h->X, r, p, h->ldX, h->Xpl, h->ldX, (int64_t)h->r_cap * h->ldX, 3,
                                           gate, nact, h->act, st);
       if (e != cudaSuccess) return e;
-      return launch_gemm_tc(h->tmA, 3, h->tmX3, 3, n, r, p, pairs_general(), h->U, h->ldU, gate, nact, h->act,
+      return launch_gemm_tc(h->pmA, 3, h->tmX3, 3, n, nhost, p, pairs_general(), h->U, h->ldU, gate, nact, h->act,
                             h->dev_err, st);
     }));
   } else {
@@ -258,7 +258,7 @@ int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int 
 }
 
 // y-step and v = A^T y for every active row (tensor-core engine: packed active rows, see above)
-int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const int *nact) {
+int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const int *nact, int nhost) {
   const int n = (int)h->n, p = (int)h->p;
   cudaStream_t st = h->stream;
   const bool tc = engine == SPCA_ENGINE_TC;
@@ -270,7 +270,7 @@ int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const i
   if (tc) {
     const bool l1 = is_l1_var(form);
     CK(timed(h, SPCA_K_V, 1, [&] {
-      return launch_gemm_tc(h->tmAT, 3, l1 ? h->tmY1 : h->tmY3, l1 ? 1 : 3, p, r, n,
+      return launch_gemm_tc(h->pmAT, 3, l1 ? h->tmY1 : h->tmY3, l1 ? 1 : 3, p, nhost, n,
                             l1 ? pairs_sign() : pairs_general(), h->V, h->ldX, nullptr, nact, h->act,
                             h->dev_err, st);
     }));
@@ -416,8 +416,8 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
         return launch_split_planes(h->AT32, p, h->ldAT, h->ldAT, h->ATpl, h->ldAT, p * h->ldAT, 3, nullptr,
                                    nullptr, nullptr, h->stream);
       }));
-      CK(make_plane_map(&h->tmA, h->Apl, n, h->ldA, 3, 128));
-      CK(make_plane_map(&h->tmAT, h->ATpl, p, h->ldAT, 3, 128));
+      CK(make_p_maps(&h->pmA, h->Apl, n, h->ldA, 3));
+      CK(make_p_maps(&h->pmAT, h->ATpl, p, h->ldAT, 3));
     }
     CK(cudaStreamSynchronize(h->stream));
     if (*h->h_flag) return fail(h, SPCA_E_INVALID, "A has a non-finite entry%s");
@@ -467,8 +467,8 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
   CK(cudaMemsetAsync(h->status, 0xFF, (size_t)r * sizeof(int), st));   // every row active (-1)
   CK(cudaMemsetAsync(h->iters, 0, (size_t)r * sizeof(int), st));
   CK(launch_active_list(h->status, r, h->act, h->rank, &h->ctrl[0].active, st));
-  RC(sweep_u_dense(h, eng, r, nullptr, &h->ctrl[0].active));
-  RC(sweep_y_v(h, eng, form, r, state_of(h), &h->ctrl[0].active));
+  RC(sweep_u_dense(h, eng, r, nullptr, &h->ctrl[0].active, r));
+  RC(sweep_y_v(h, eng, form, r, state_of(h), &h->ctrl[0].active, r));
   CK(cudaMemcpy2DAsync(U, ldu * sizeof(float), h->U, h->ldU * sizeof(float), (size_t)n * sizeof(float), r,
                        cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpy2DAsync(V, ldv * sizeof(float), h->V, h->ldX * sizeof(float), (size_t)p * sizeof(float), r,
@@ -511,7 +511,9 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   h->h_ctrl[0].active = r; h->h_ctrl[0].need_dense = 1; h->h_ctrl[0].err = 0; h->h_ctrl[0].pad = 0;
   CK(cudaMemcpyAsync(h->ctrl, h->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
   CK(timed(h, SPCA_K_XSTEP, 1, [&] { return launch_active_list(h->status, r, h->act, h->rank, &h->ctrl[0].active, st); }));
+  CK(cudaMemcpyAsync(h->h_ctrl + 1, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));  // h_ctrl is reused below
+  int nhost = h->h_ctrl[1].active;  // active starts as the host knows them (sizes the launches)
 
   // ---- the sweeps (Algorithm 2)
   XstepArgs xa{};
@@ -526,13 +528,13 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   for (int k = 1; k <= P.max_iter; ++k) {
     Ctrl *cur = h->ctrl + ((k - 1) & 1), *nxt = h->ctrl + (k & 1);
     // u = A x: dense contraction, or the support gather when every support is small
-    RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active));
+    RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, nhost));
     CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
       return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
                                  &cur->need_dense, st);
     }));
     // y-step, v = A^T y
-    RC(sweep_y_v(h, engine, form, r, S, &cur->active));
+    RC(sweep_y_v(h, engine, form, r, S, &cur->active, nhost));
     CK(cudaMemsetAsync(nxt, 0, sizeof(Ctrl), st));
     xa.calibrate = target && k <= C;
     xa.per_start_thr = target && k > C;
@@ -546,6 +548,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
       CK(cudaMemcpyAsync(h->h_ctrl, nxt, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if (h->h_ctrl->active == 0) break;
+      nhost = h->h_ctrl->active;   // counts only fall: any earlier value stays an upper bound
     }
   }
   RC(read_dev_err(h));

@@ -117,12 +117,19 @@ struct TcPairs {      // plane products P plane a[q] x Q plane b[q], q < n; the 
 cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int64_t ld, int planes,
                            int box_rows);
 int tc_box_rows(int nb);   // Q-operand box height for nb planes (the tile's N)
-// out[map(c) * ldo + m] = sum_q sum_k P_{a_q}[m, k] Q_{b_q}[c, k], m < M, c < N (N = *n_dev when
-// n_dev != nullptr; map = col_map when given, else the identity); with gate != nullptr nothing
-// runs unless *gate != 0; a timed-out wait sets *err = SPCA_E_TIMEOUT
-cudaError_t launch_gemm_tc(const CUtensorMap &P, int na, const CUtensorMap &Q, int nb, int M, int N,
-                           int K, TcPairs pairs, float *out, int64_t ldo, const int *gate,
-                           const int *n_dev, const int *col_map, int *err, cudaStream_t st);
+// P-operand maps with 128-, 64- and 32-row boxes (the slice one CTA of a 1-, 2- or 4-CTA
+// cluster loads and multicasts)
+struct PMaps {
+  CUtensorMap m[3];
+};
+cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld, int planes);
+// out[map(c) * ldo + m] = sum_q sum_k P_{a_q}[m, k] Q_{b_q}[c, k], m < M, c < N.  N bounds the
+// columns for the launch; with n_dev != nullptr the kernel uses *n_dev (<= N) instead; map =
+// col_map when given, else the identity.  With gate != nullptr nothing runs unless *gate != 0;
+// a timed-out wait sets *err = SPCA_E_TIMEOUT
+cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
+                           TcPairs pairs, float *out, int64_t ldo, const int *gate, const int *n_dev,
+                           const int *col_map, int *err, cudaStream_t st);
 // BF16 planes of an FP32 matrix (plane t at dst + t * plane_stride elements): destination row r
 // comes from source row row_map[r] (identity when null), r < rows (*rows_dev when given); gated
 cudaError_t launch_split_planes(const float *src, int64_t rows, int64_t cols, int64_t lds, void *dst,
