@@ -1,6 +1,7 @@
 // spca_api.cu -- the C ABI of include/spca.h: the handle (device copies of A in the layouts
 // the kernels read), the solve driver that runs Algorithm 2 for r starts as a sequence of
 // kernels on one stream, and the step-level entry points (x-step, sweep products).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -29,6 +30,13 @@ struct spca_handle {
   int *sup_idx = nullptr;
   float *sup_val = nullptr;
   int *act = nullptr, *rank = nullptr;     // ordered list of the active starts and its inverse
+  // union of the active supports (tensor-core engine): marks, positions, columns, and the
+  // compact operands of u = A x over it (kcap columns at most)
+  int kcap = 0;
+  int *mark = nullptr, *colpos = nullptr, *collist = nullptr;
+  void *AS = nullptr, *XS = nullptr;
+  PMaps pmAS{};
+  CUtensorMap tmXS3{};
   int *status = nullptr, *iters = nullptr, *nnz = nullptr;
   double *F = nullptr, *F_prev = nullptr, *gamma = nullptr, *f = nullptr, *ev = nullptr;
   float *thr = nullptr;
@@ -121,9 +129,12 @@ cudaError_t dalloc(T **p, size_t count, size_t elem = sizeof(T)) {
 void free_workspace(spca_handle *h) {
   void *ptrs[] = {h->X, h->V, h->U, h->Y, h->Xpl, h->Ypl, h->sup_idx, h->sup_val, h->act, h->rank,
                   h->status, h->iters, h->nnz, h->F, h->F_prev, h->gamma, h->f, h->ev, h->thr,
-                  h->partials, h->ctrl, h->best, h->y_out, h->x_out, h->support_out, h->nnz_out};
+                  h->partials, h->ctrl, h->best, h->y_out, h->x_out, h->support_out, h->nnz_out,
+                  h->mark, h->colpos, h->collist, h->AS, h->XS};
   for (void *q : ptrs)
     if (q) cudaFree(q);
+  h->mark = h->colpos = h->collist = nullptr;
+  h->AS = h->XS = nullptr;
   h->X = h->V = h->U = h->Y = nullptr;
   h->Xpl = h->Ypl = nullptr;
   h->sup_idx = nullptr; h->sup_val = nullptr;
@@ -169,6 +180,12 @@ int ensure_workspace(spca_handle *h, int r) {
     CK(make_plane_map(&h->tmX3, h->Xpl, r, h->ldX, 3, tc_box_rows(3)));
     CK(make_plane_map(&h->tmY1, h->Ypl, r, h->ldU, 1, tc_box_rows(1)));
     CK(make_plane_map(&h->tmY3, h->Ypl, r, h->ldU, 3, tc_box_rows(3)));
+    h->kcap = (int)std::min<int64_t>(1024, (p + 63) / 64 * 64);
+    CK(dalloc(&h->mark, (size_t)p)); CK(dalloc(&h->colpos, (size_t)p)); CK(dalloc(&h->collist, (size_t)h->kcap));
+    CK(dalloc(&h->AS, (size_t)3 * n * h->kcap, 2));
+    CK(dalloc(&h->XS, (size_t)3 * r * h->kcap, 2));
+    CK(make_p_maps(&h->pmAS, h->AS, n, h->kcap, 3));
+    CK(make_plane_map(&h->tmXS3, h->XS, r, h->kcap, 3, tc_box_rows(3)));
   }
   h->r_cap = r;
   return SPCA_OK;
@@ -254,6 +271,23 @@ int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int 
       return launch_gemm_nt_f32(h->X, h->ldX, h->A32, h->ldA, h->U, h->ldU, r, n, (int)h->ldX, gate, st);
     }));
   }
+  return SPCA_OK;
+}
+
+// u = A x for every active row over the union S of the active supports (|S| = K <= h->kcap):
+// compact BF16 operands, then the tensor-core contraction over K
+int sweep_u_union(spca_handle *h, StartState S, const int *nact, int nhost, int K) {
+  const int n = (int)h->n, p = (int)h->p;
+  const int kpad = (K + 63) / 64 * 64;
+  CK(timed(h, SPCA_K_U_SPARSE, 3, [&] {
+    cudaError_t e = launch_union_operands(h->ATpl, h->ldAT, (int64_t)p * h->ldAT, n, h->collist, K, kpad, h->AS,
+                                          h->kcap, (int64_t)n * h->kcap, h->sup_idx, h->sup_val, p, S, h->act,
+                                          nact, nhost, h->colpos, h->XS, h->kcap, (int64_t)h->r_cap * h->kcap,
+                                          h->stream);
+    if (e != cudaSuccess) return e;
+    return launch_gemm_tc(h->pmAS, 3, h->tmXS3, 3, n, nhost, K, pairs_general(), h->U, h->ldU, nullptr, nact,
+                          h->act, h->dev_err, h->stream);
+  }));
   return SPCA_OK;
 }
 
@@ -508,12 +542,14 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   CK(timed(h, SPCA_K_INIT, 1, [&] {
     return launch_start_init(x0 ? h->X : nullptr, h->ldX, P.seed, r, p, h->X, h->ldX, S, gamma0, st);
   }));
-  h->h_ctrl[0].active = r; h->h_ctrl[0].need_dense = 1; h->h_ctrl[0].err = 0; h->h_ctrl[0].pad = 0;
+  h->h_ctrl[0].active = r; h->h_ctrl[0].need_dense = 1; h->h_ctrl[0].err = 0; h->h_ctrl[0].kunion = 0;
   CK(cudaMemcpyAsync(h->ctrl, h->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
   CK(timed(h, SPCA_K_XSTEP, 1, [&] { return launch_active_list(h->status, r, h->act, h->rank, &h->ctrl[0].active, st); }));
   CK(cudaMemcpyAsync(h->h_ctrl + 1, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));  // h_ctrl is reused below
   int nhost = h->h_ctrl[1].active;  // active starts as the host knows them (sizes the launches)
+  bool need_dense_host = true;      // the previous sweep's control word, as the host read it
+  int kunion_host = 0;
 
   // ---- the sweeps (Algorithm 2)
   XstepArgs xa{};
@@ -527,12 +563,19 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   const int check_every = 1;
   for (int k = 1; k <= P.max_iter; ++k) {
     Ctrl *cur = h->ctrl + ((k - 1) & 1), *nxt = h->ctrl + (k & 1);
-    // u = A x: dense contraction, or the support gather when every support is small
-    RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, nhost));
-    CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
-      return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
-                                 &cur->need_dense, st);
-    }));
+    // u = A x: over the union of the supports when it is small (tensor cores), else the dense
+    // contraction, or the per-start support gather when every support is small
+    const bool use_union = engine == SPCA_ENGINE_TC && k > 1 && !need_dense_host && kunion_host > 0 &&
+                           kunion_host <= h->kcap;
+    if (use_union) {
+      RC(sweep_u_union(h, S, &cur->active, nhost, kunion_host));
+    } else {
+      RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, nhost));
+      CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
+        return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
+                                   &cur->need_dense, st);
+      }));
+    }
     // y-step, v = A^T y
     RC(sweep_y_v(h, engine, form, r, S, &cur->active, nhost));
     CK(cudaMemsetAsync(nxt, 0, sizeof(Ctrl), st));
@@ -544,11 +587,18 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
       if (e != cudaSuccess) return e;
       return launch_active_list(h->status, r, h->act, h->rank, &nxt->active, st);   // for the next sweep
     }));
+    if (engine == SPCA_ENGINE_TC) {
+      CK(timed(h, SPCA_K_U_SPARSE, 2, [&] {
+        return launch_union(h->sup_idx, p, S, r, p, h->mark, h->colpos, h->collist, h->kcap, &nxt->kunion, st);
+      }));
+    }
     if (k == P.max_iter || k % check_every == 0) {
       CK(cudaMemcpyAsync(h->h_ctrl, nxt, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if (h->h_ctrl->active == 0) break;
       nhost = h->h_ctrl->active;   // counts only fall: any earlier value stays an upper bound
+      need_dense_host = h->h_ctrl->need_dense != 0;
+      kunion_host = h->h_ctrl->kunion;
     }
   }
   RC(read_dev_err(h));

@@ -40,7 +40,7 @@ struct Ctrl {
   int active;      // starts still iterating after this sweep
   int need_dense;  // some active start has more nonzeros than the sparse path holds
   int err;         // kernel-reported error code (0 = none)
-  int pad;
+  int kunion;      // size of the union of the active starts' supports
 };
 
 // per-start state of one solve (device arrays, r each)
@@ -135,6 +135,17 @@ cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb,
 cudaError_t launch_split_planes(const float *src, int64_t rows, int64_t cols, int64_t lds, void *dst,
                                 int64_t ldd, int64_t plane_stride, int nplanes, const int *gate,
                                 const int *rows_dev, const int *row_map, cudaStream_t st);
+// union S of the active starts' supports: colpos[j] = position of column j in S (or -1),
+// collist[k] = the k-th column of S (k < kcap), *kunion = |S|.  mark: p ints of scratch
+cudaError_t launch_union(const int *sup_idx, int cap, StartState s, int r, int p, int *mark, int *colpos,
+                         int *collist, int kcap, int *kunion, cudaStream_t st);
+// operands of u = A x over S (K = |S| <= kpad): AS planes n x kpad (row i: A[i, S], zero past K)
+// from the A^T planes, and XS planes (row k: the k-th active x at the positions of S)
+cudaError_t launch_union_operands(const void *ATpl, int64_t ldat, int64_t at_pstride, int n, const int *collist,
+                                  int K, int kpad, void *AS, int64_t ldas, int64_t as_pstride, const int *sup_idx,
+                                  const float *sup_val, int cap, StartState s, const int *act, const int *nact,
+                                  int nhost, const int *colpos, void *XS, int64_t ldxs, int64_t xs_pstride,
+                                  cudaStream_t st);
 // ordered list of the active starts (status == ST_ACTIVE): act[k] = c and rank[c] = k for the
 // k-th active start; the count goes to *count
 cudaError_t launch_active_list(const int *status, int r, int *act, int *rank, int *count,
