@@ -162,8 +162,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 template <int BN, int NA, int NB, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int M, int N,
-              int kblocks, TcPairs pairs, float *__restrict__ out, int64_t ldo, const int *__restrict__ gate,
-              const int *__restrict__ n_dev, const int *__restrict__ col_map, int *err) {
+              int kblocks, const int *__restrict__ k_dev, TcPairs pairs, float *__restrict__ out, int64_t ldo,
+              const int *__restrict__ gate, const int *__restrict__ n_dev, const int *__restrict__ col_map,
+              int *err) {
   constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;       // 16 KB per P plane tile
   constexpr uint32_t B_BYTES = BN * TC_BK * 2;          // 32 KB (BN = 256) per Q plane tile
   constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
@@ -177,6 +178,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t crank = cluster_rank(), csize = cluster_size();
   if (gate && *gate == 0) return;   // uniform over the grid: the contraction is not needed
   if (n_dev) N = *n_dev;            // columns (active starts) known only on the device
+  if (k_dev) kblocks = (*k_dev + TC_BK - 1) / TC_BK;   // contraction length known only on the device
+  if (kblocks <= 0) return;
   if ((int)(blockIdx.x - crank) * BN >= N) return;   // uniform over the cluster
 
   uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
@@ -366,7 +369,7 @@ cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld,
 
 namespace {
 template <int BN, int NA, int NB, int STAGES>
-cudaError_t launch_tc_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, int K, TcPairs pairs,
+cudaError_t launch_tc_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, int K, const int *k_dev, TcPairs pairs,
                            float *out, int64_t ldo, const int *gate, const int *n_dev, const int *col_map,
                            int *err, cudaStream_t st) {
   constexpr int STAGE_BYTES = NA * TC_BM * TC_BK * 2 + NB * BN * TC_BK * 2;
@@ -397,17 +400,18 @@ cudaError_t launch_tc_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, i
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, P.m[lg], Q, M, N, kblocks, pairs, out, ldo, gate, n_dev, col_map, err);
+  return cudaLaunchKernelEx(&cfg, kern, P.m[lg], Q, M, N, kblocks, k_dev, pairs, out, ldo, gate, n_dev, col_map,
+                            err);
 }
 }  // namespace
 
 cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
-                           TcPairs pairs, float *out, int64_t ldo, const int *gate, const int *n_dev,
-                           const int *col_map, int *err, cudaStream_t st) {
+                           const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const int *gate,
+                           const int *n_dev, const int *col_map, int *err, cudaStream_t st) {
   if (na == 3 && nb == 1)
-    return launch_tc_impl<256, 3, 1, 2>(P, Q, M, N, K, pairs, out, ldo, gate, n_dev, col_map, err, st);
+    return launch_tc_impl<256, 3, 1, 2>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
   if (na == 3 && nb == 3)
-    return launch_tc_impl<128, 3, 3, 2>(P, Q, M, N, K, pairs, out, ldo, gate, n_dev, col_map, err, st);
+    return launch_tc_impl<128, 3, 3, 2>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
   return cudaErrorInvalidValue;
 }
 

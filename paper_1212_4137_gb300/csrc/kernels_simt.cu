@@ -207,7 +207,7 @@ cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, fl
 // one CTA: ordered compaction of the flags status[c] == ST_ACTIVE over r starts
 __global__ void __launch_bounds__(1024) k_active_list(const int *__restrict__ status, int r,
                                                       int *__restrict__ act, int *__restrict__ rank,
-                                                      int *__restrict__ count) {
+                                                      Ctrl *__restrict__ ctrl) {
   __shared__ int red[32];
   int base_pos = 0;
   for (int base = 0; base < r; base += blockDim.x) {
@@ -221,11 +221,14 @@ __global__ void __launch_bounds__(1024) k_active_list(const int *__restrict__ st
     }
     base_pos += tot;
   }
-  if (threadIdx.x == 0) *count = base_pos;
+  if (threadIdx.x == 0) {
+    ctrl->active = base_pos;
+    ctrl->use_gather = (ctrl->need_dense == 0 && base_pos > 0) ? 1 : 0;
+  }
 }
 
-cudaError_t launch_active_list(const int *status, int r, int *act, int *rank, int *count, cudaStream_t st) {
-  k_active_list<<<1, 1024, 0, st>>>(status, r, act, rank, count);
+cudaError_t launch_active_list(const int *status, int r, int *act, int *rank, Ctrl *c, cudaStream_t st) {
+  k_active_list<<<1, 1024, 0, st>>>(status, r, act, rank, c);
   return cudaGetLastError();
 }
 
@@ -306,13 +309,13 @@ cudaError_t launch_gemm_nt_f32(const float *P, int64_t ldp, const float *Q, int6
 
 // ------------------------------------------------------------------ u = A x over supp(x)
 // U[c, i] = sum_t val[c, t] AT[idx[c, t], i] (t over the support of x, ascending index).
-// Runs only when *gate == 0, i.e. when every active start's support fits the sparse path.
+// Runs only when *gate != 0 (the control word chose this path for the sweep).
 __global__ void __launch_bounds__(256) k_gemm1_sparse(const float *__restrict__ AT, int64_t ldat,
                                                       int n, const int *__restrict__ sup_idx,
                                                       const float *__restrict__ sup_val, int cap,
                                                       StartState s, float *__restrict__ U,
                                                       int64_t ldu, const int *__restrict__ gate) {
-  if (*gate != 0) return;
+  if (*gate == 0) return;
   const int c = blockIdx.y;
   if (s.status[c] != ST_ACTIVE) return;
   __shared__ int sidx[256];

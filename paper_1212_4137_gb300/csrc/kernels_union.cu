@@ -1,8 +1,9 @@
 // kernels_union.cu -- u = A x (Algorithm 2) when the active starts' supports share few columns.
 // After an x-step every x is sparse, and on structured data the starts converge onto a few
 // supports, so the union S of the active supports is small.  Then:
-//   1. one mark byte per column of A for every support entry, and an ordered compaction of
-//      the marks into S (column -> position, position -> column, K' = |S|);
+//   1. one mark per column of A for every support entry, and an ordered compaction of the
+//      marks into S (column -> position, position -> column, K' = |S|), which also decides on
+//      the device whether the next sweep takes this path;
 //   2. the columns of A in S gathered into BF16 planes with the support position contiguous
 //      (n x K' per plane, zero-padded to a multiple of 64), from the rows of A^T;
 //   3. each active x scattered into the same K' positions (three BF16 planes);
@@ -26,41 +27,71 @@ __global__ void __launch_bounds__(256) k_union_mark(const int *__restrict__ sup_
   for (int t = threadIdx.x; t < nnz; t += blockDim.x) mark[gi[t]] = 1;
 }
 
-// one CTA: positions of the marked columns in index order
+// one CTA: each thread owns a contiguous segment of columns; one block scan of the per-thread
+// counts gives every marked column its position in index order
 __global__ void __launch_bounds__(1024) k_union_scan(const int *__restrict__ mark, int p, int *__restrict__ colpos,
-                                                     int *__restrict__ collist, int kcap, int *__restrict__ kunion) {
+                                                     int *__restrict__ collist, int kcap, Ctrl *__restrict__ ctrl) {
   __shared__ int red[32];
-  int base_pos = 0;
-  for (int base = 0; base < p; base += blockDim.x) {
-    const int j = base + threadIdx.x;
-    const bool on = j < p && mark[j] != 0;
-    int tot;
-    const int pos = base_pos + block_excl_scan_flag(on, red, &tot);
-    if (j < p) colpos[j] = on ? pos : -1;
-    if (on && pos < kcap) collist[pos] = j;
-    base_pos += tot;
+  __shared__ int total_s;
+  const int seg = (p + blockDim.x - 1) / blockDim.x;
+  const int lo = min(p, (int)threadIdx.x * seg), hi = min(p, lo + seg);
+  int cnt = 0;
+  for (int j = lo; j < hi; ++j) cnt += mark[j] != 0;
+  // exclusive scan of cnt over the block (warp shuffles, then the warp totals)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
   }
-  if (threadIdx.x == 0) *kunion = base_pos;
+  if (lane == 31) red[w] = incl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int k = 0; k < nw; ++k) { const int t = red[k]; red[k] = acc; acc += t; }
+    total_s = acc;
+  }
+  __syncthreads();
+  int pos = red[w] + incl - cnt;
+  for (int j = lo; j < hi; ++j) {
+    if (mark[j] != 0) {
+      colpos[j] = pos;
+      if (pos < kcap) collist[pos] = j;
+      ++pos;
+    } else {
+      colpos[j] = -1;
+    }
+  }
+  if (threadIdx.x == 0) {
+    const int K = total_s;
+    ctrl->kunion = K;
+    const int use = (ctrl->need_dense == 0 && ctrl->active > 0 && K > 0 && K <= kcap) ? 1 : 0;
+    ctrl->use_union = use;
+    if (use) ctrl->use_gather = 0;
+  }
 }
 
 cudaError_t launch_union(const int *sup_idx, int cap, StartState s, int r, int p, int *mark, int *colpos,
-                         int *collist, int kcap, int *kunion, cudaStream_t st) {
+                         int *collist, int kcap, Ctrl *c, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(mark, 0, (size_t)p * sizeof(int), st);
   if (e != cudaSuccess) return e;
   k_union_mark<<<r, 256, 0, st>>>(sup_idx, cap, s, mark);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_union_scan<<<1, 1024, 0, st>>>(mark, p, colpos, collist, kcap, kunion);
+  k_union_scan<<<1, 1024, 0, st>>>(mark, p, colpos, collist, kcap, c);
   return cudaGetLastError();
 }
 
-// AS[t][i * ldas + k] = plane t of A[i, collist[k]] (= A^T[collist[k], i]) for k < K', 0 for
+// AS[t][i * kcap + k] = plane t of A[i, collist[k]] (= A^T[collist[k], i]) for k < K', 0 for
 // K' <= k < kpad; 32 x 32 tiles transposed through shared memory (coalesced on both sides)
 __global__ void __launch_bounds__(256) k_gather_cols(const __nv_bfloat16 *__restrict__ ATpl, int64_t ldat,
                                                      int64_t at_pstride, int n, const int *__restrict__ collist,
-                                                     int K, int kpad, __nv_bfloat16 *__restrict__ AS,
-                                                     int64_t ldas, int64_t as_pstride) {
+                                                     int kcap, __nv_bfloat16 *__restrict__ AS, int64_t as_pstride,
+                                                     const Ctrl *__restrict__ ctrl) {
   __shared__ __nv_bfloat16 tile[32][34];
+  if (ctrl->use_union == 0) return;
+  const int K = ctrl->kunion, kpad = min(kcap, (K + 63) / 64 * 64);
   const int k0 = blockIdx.x * 32, i0 = blockIdx.y * 32, pl = blockIdx.z;
   if (k0 >= kpad) return;
   const __nv_bfloat16 *src = ATpl + pl * at_pstride;
@@ -75,20 +106,22 @@ __global__ void __launch_bounds__(256) k_gather_cols(const __nv_bfloat16 *__rest
   __syncthreads();
   for (int ii = ty; ii < 32; ii += 8) {
     const int i = i0 + ii, k = k0 + tx;
-    if (i < n && k < kpad) dst[(int64_t)i * ldas + k] = tile[tx][ii];
+    if (i < n && k < kpad) dst[(int64_t)i * kcap + k] = tile[tx][ii];
   }
 }
 
-// XS[t][k * ldxs + colpos[j]] = plane t of x_j for the k-th active start (rows zeroed first)
+// XS[t][k * kcap + colpos[j]] = plane t of x_j for the k-th active start (rows zeroed first)
 __global__ void __launch_bounds__(256) k_scatter_x(const int *__restrict__ sup_idx, const float *__restrict__ sup_val,
                                                    int cap, StartState s, const int *__restrict__ act,
-                                                   const int *__restrict__ nact, const int *__restrict__ colpos,
-                                                   int kpad, __nv_bfloat16 *__restrict__ XS, int64_t ldxs,
-                                                   int64_t xs_pstride) {
+                                                   const int *__restrict__ colpos, int kcap,
+                                                   __nv_bfloat16 *__restrict__ XS, int64_t xs_pstride,
+                                                   const Ctrl *__restrict__ ctrl) {
+  if (ctrl->use_union == 0) return;
   const int k = blockIdx.x;
-  if (k >= *nact) return;
+  if (k >= ctrl->active) return;
+  const int kpad = min(kcap, (ctrl->kunion + 63) / 64 * 64);
   const int c = act[k];
-  __nv_bfloat16 *row = XS + (int64_t)k * ldxs;
+  __nv_bfloat16 *row = XS + (int64_t)k * kcap;
   for (int q = threadIdx.x; q < kpad; q += blockDim.x) {
     row[q] = __float2bfloat16_rn(0.0f);
     row[q + xs_pstride] = __float2bfloat16_rn(0.0f);
@@ -100,8 +133,8 @@ __global__ void __launch_bounds__(256) k_scatter_x(const int *__restrict__ sup_i
   const float *gv = sup_val + (int64_t)c * cap;
   for (int t = threadIdx.x; t < nnz; t += blockDim.x) {
     const int pos = colpos[gi[t]];
-    if (pos < 0 || pos >= kpad) continue;   // not in the union's first kpad columns (cannot happen
-                                            // when the union path is chosen)
+    if (pos < 0 || pos >= kpad) continue;   // outside the union's first kpad columns (cannot
+                                            // happen when use_union is set)
     float a = gv[t];
     for (int pl = 0; pl < 3; ++pl) {
       const __nv_bfloat16 h = __float2bfloat16_rn(a);
@@ -112,17 +145,17 @@ __global__ void __launch_bounds__(256) k_scatter_x(const int *__restrict__ sup_i
 }
 
 cudaError_t launch_union_operands(const void *ATpl, int64_t ldat, int64_t at_pstride, int n, const int *collist,
-                                  int K, int kpad, void *AS, int64_t ldas, int64_t as_pstride, const int *sup_idx,
-                                  const float *sup_val, int cap, StartState s, const int *act, const int *nact,
-                                  int nhost, const int *colpos, void *XS, int64_t ldxs, int64_t xs_pstride,
+                                  int kcap, void *AS, int64_t as_pstride, const int *sup_idx,
+                                  const float *sup_val, int cap, StartState s, const int *act, int nhost,
+                                  const int *colpos, void *XS, int64_t xs_pstride, const Ctrl *c,
                                   cudaStream_t st) {
-  dim3 g1((unsigned)((kpad + 31) / 32), (unsigned)((n + 31) / 32), 3);
-  k_gather_cols<<<g1, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(ATpl), ldat, at_pstride, n, collist, K,
-                                    kpad, static_cast<__nv_bfloat16 *>(AS), ldas, as_pstride);
+  dim3 g1((unsigned)((kcap + 31) / 32), (unsigned)((n + 31) / 32), 3);
+  k_gather_cols<<<g1, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(ATpl), ldat, at_pstride, n, collist, kcap,
+                                    static_cast<__nv_bfloat16 *>(AS), as_pstride, c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_scatter_x<<<nhost, 256, 0, st>>>(sup_idx, sup_val, cap, s, act, nact, colpos, kpad,
-                                      static_cast<__nv_bfloat16 *>(XS), ldxs, xs_pstride);
+  k_scatter_x<<<nhost > 0 ? nhost : 1, 256, 0, st>>>(sup_idx, sup_val, cap, s, act, colpos, kcap,
+                                                      static_cast<__nv_bfloat16 *>(XS), xs_pstride, c);
   return cudaGetLastError();
 }
 

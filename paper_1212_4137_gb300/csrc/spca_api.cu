@@ -263,8 +263,8 @@ int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int 
       cudaError_t e = launch_split_planes(h->X, r, p, h->ldX, h->Xpl, h->ldX, (int64_t)h->r_cap * h->ldX, 3,
                                           gate, nact, h->act, st);
       if (e != cudaSuccess) return e;
-      return launch_gemm_tc(h->pmA, 3, h->tmX3, 3, n, nhost, p, pairs_general(), h->U, h->ldU, gate, nact, h->act,
-                            h->dev_err, st);
+      return launch_gemm_tc(h->pmA, 3, h->tmX3, 3, n, nhost, p, nullptr, pairs_general(), h->U, h->ldU, gate, nact,
+                            h->act, h->dev_err, st);
     }));
   } else {
     CK(timed(h, SPCA_K_U_DENSE, 1, [&] {
@@ -274,19 +274,17 @@ int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int 
   return SPCA_OK;
 }
 
-// u = A x for every active row over the union S of the active supports (|S| = K <= h->kcap):
-// compact BF16 operands, then the tensor-core contraction over K
-int sweep_u_union(spca_handle *h, StartState S, const int *nact, int nhost, int K) {
+// u = A x for every active row over the union S of the active supports, when the control word
+// c chose it (|S| <= h->kcap): compact BF16 operands, then the tensor-core contraction over |S|
+int sweep_u_union(spca_handle *h, StartState S, const Ctrl *c, int nhost) {
   const int n = (int)h->n, p = (int)h->p;
-  const int kpad = (K + 63) / 64 * 64;
   CK(timed(h, SPCA_K_U_SPARSE, 3, [&] {
-    cudaError_t e = launch_union_operands(h->ATpl, h->ldAT, (int64_t)p * h->ldAT, n, h->collist, K, kpad, h->AS,
-                                          h->kcap, (int64_t)n * h->kcap, h->sup_idx, h->sup_val, p, S, h->act,
-                                          nact, nhost, h->colpos, h->XS, h->kcap, (int64_t)h->r_cap * h->kcap,
-                                          h->stream);
+    cudaError_t e = launch_union_operands(h->ATpl, h->ldAT, (int64_t)p * h->ldAT, n, h->collist, h->kcap, h->AS,
+                                          (int64_t)n * h->kcap, h->sup_idx, h->sup_val, p, S, h->act, nhost,
+                                          h->colpos, h->XS, (int64_t)h->r_cap * h->kcap, c, h->stream);
     if (e != cudaSuccess) return e;
-    return launch_gemm_tc(h->pmAS, 3, h->tmXS3, 3, n, nhost, K, pairs_general(), h->U, h->ldU, nullptr, nact,
-                          h->act, h->dev_err, h->stream);
+    return launch_gemm_tc(h->pmAS, 3, h->tmXS3, 3, n, nhost, h->kcap, &c->kunion, pairs_general(), h->U, h->ldU,
+                          &c->use_union, &c->active, h->act, h->dev_err, h->stream);
   }));
   return SPCA_OK;
 }
@@ -304,7 +302,7 @@ int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const i
   if (tc) {
     const bool l1 = is_l1_var(form);
     CK(timed(h, SPCA_K_V, 1, [&] {
-      return launch_gemm_tc(h->pmAT, 3, l1 ? h->tmY1 : h->tmY3, l1 ? 1 : 3, p, nhost, n,
+      return launch_gemm_tc(h->pmAT, 3, l1 ? h->tmY1 : h->tmY3, l1 ? 1 : 3, p, nhost, n, nullptr,
                             l1 ? pairs_sign() : pairs_general(), h->V, h->ldX, nullptr, nact, h->act,
                             h->dev_err, st);
     }));
@@ -500,7 +498,8 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
                        cudaMemcpyDeviceToDevice, st));
   CK(cudaMemsetAsync(h->status, 0xFF, (size_t)r * sizeof(int), st));   // every row active (-1)
   CK(cudaMemsetAsync(h->iters, 0, (size_t)r * sizeof(int), st));
-  CK(launch_active_list(h->status, r, h->act, h->rank, &h->ctrl[0].active, st));
+  CK(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), st));
+  CK(launch_active_list(h->status, r, h->act, h->rank, &h->ctrl[0], st));
   RC(sweep_u_dense(h, eng, r, nullptr, &h->ctrl[0].active, r));
   RC(sweep_y_v(h, eng, form, r, state_of(h), &h->ctrl[0].active, r));
   CK(cudaMemcpy2DAsync(U, ldu * sizeof(float), h->U, h->ldU * sizeof(float), (size_t)n * sizeof(float), r,
@@ -542,14 +541,14 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   CK(timed(h, SPCA_K_INIT, 1, [&] {
     return launch_start_init(x0 ? h->X : nullptr, h->ldX, P.seed, r, p, h->X, h->ldX, S, gamma0, st);
   }));
-  h->h_ctrl[0].active = r; h->h_ctrl[0].need_dense = 1; h->h_ctrl[0].err = 0; h->h_ctrl[0].kunion = 0;
+  memset(&h->h_ctrl[0], 0, sizeof(Ctrl));
+  h->h_ctrl[0].active = r;
+  h->h_ctrl[0].need_dense = 1;      // x^(0) is dense: the first sweep's u = A x is the dense one
   CK(cudaMemcpyAsync(h->ctrl, h->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
-  CK(timed(h, SPCA_K_XSTEP, 1, [&] { return launch_active_list(h->status, r, h->act, h->rank, &h->ctrl[0].active, st); }));
+  CK(timed(h, SPCA_K_XSTEP, 1, [&] { return launch_active_list(h->status, r, h->act, h->rank, &h->ctrl[0], st); }));
   CK(cudaMemcpyAsync(h->h_ctrl + 1, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));  // h_ctrl is reused below
   int nhost = h->h_ctrl[1].active;  // active starts as the host knows them (sizes the launches)
-  bool need_dense_host = true;      // the previous sweep's control word, as the host read it
-  int kunion_host = 0;
 
   // ---- the sweeps (Algorithm 2)
   XstepArgs xa{};
@@ -560,22 +559,19 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   xa.cap = p;
   xa.sparse_cap = p / 8 > 0 ? p / 8 : 1;
   const int C = target ? P.gamma_calib_sweeps : 0;
-  const int check_every = 1;
+  // the host queues this many sweeps before it reads the active count back; every path decision
+  // inside a sweep is taken on the device from the control word
+  const int check_every = 4;
   for (int k = 1; k <= P.max_iter; ++k) {
     Ctrl *cur = h->ctrl + ((k - 1) & 1), *nxt = h->ctrl + (k & 1);
     // u = A x: over the union of the supports when it is small (tensor cores), else the dense
     // contraction, or the per-start support gather when every support is small
-    const bool use_union = engine == SPCA_ENGINE_TC && k > 1 && !need_dense_host && kunion_host > 0 &&
-                           kunion_host <= h->kcap;
-    if (use_union) {
-      RC(sweep_u_union(h, S, &cur->active, nhost, kunion_host));
-    } else {
-      RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, nhost));
-      CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
-        return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
-                                   &cur->need_dense, st);
-      }));
-    }
+    RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, nhost));
+    if (engine == SPCA_ENGINE_TC) RC(sweep_u_union(h, S, cur, nhost));
+    CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
+      return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
+                                 &cur->use_gather, st);
+    }));
     // y-step, v = A^T y
     RC(sweep_y_v(h, engine, form, r, S, &cur->active, nhost));
     CK(cudaMemsetAsync(nxt, 0, sizeof(Ctrl), st));
@@ -585,11 +581,11 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     CK(timed(h, SPCA_K_XSTEP, 2, [&] {
       cudaError_t e = launch_xstep(xa, h->V, h->ldX, r, h->X, h->ldX, S, h->sup_idx, h->sup_val, nxt, st);
       if (e != cudaSuccess) return e;
-      return launch_active_list(h->status, r, h->act, h->rank, &nxt->active, st);   // for the next sweep
+      return launch_active_list(h->status, r, h->act, h->rank, nxt, st);   // for the next sweep
     }));
     if (engine == SPCA_ENGINE_TC) {
       CK(timed(h, SPCA_K_U_SPARSE, 2, [&] {
-        return launch_union(h->sup_idx, p, S, r, p, h->mark, h->colpos, h->collist, h->kcap, &nxt->kunion, st);
+        return launch_union(h->sup_idx, p, S, r, p, h->mark, h->colpos, h->collist, h->kcap, nxt, st);
       }));
     }
     if (k == P.max_iter || k % check_every == 0) {
@@ -597,8 +593,6 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
       CK(cudaStreamSynchronize(st));
       if (h->h_ctrl->active == 0) break;
       nhost = h->h_ctrl->active;   // counts only fall: any earlier value stays an upper bound
-      need_dense_host = h->h_ctrl->need_dense != 0;
-      kunion_host = h->h_ctrl->kunion;
     }
   }
   RC(read_dev_err(h));

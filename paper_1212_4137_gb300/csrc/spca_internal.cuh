@@ -36,11 +36,17 @@ constexpr int ST_ACTIVE = -1;  // device-side: still iterating (host sees SPCA_S
 
 // control words, one set per sweep parity (double-buffered so that the x-step of sweep k
 // writes the flags the contractions of sweep k+1 read)
+// Every path decision of the next sweep's u = A x is made on the device, so the host can queue
+// sweeps ahead without reading anything back: exactly one of need_dense, use_union and
+// use_gather is set for the next sweep.
 struct Ctrl {
   int active;      // starts still iterating after this sweep
-  int need_dense;  // some active start has more nonzeros than the sparse path holds
-  int err;         // kernel-reported error code (0 = none)
+  int need_dense;  // some active start has more nonzeros than the sparse paths hold: dense u
+  int use_union;   // u over the union of the supports (tensor cores)
+  int use_gather;  // u by the per-start support gather
   int kunion;      // size of the union of the active starts' supports
+  int err;         // kernel-reported error code (0 = none)
+  int pad[2];
 };
 
 // per-start state of one solve (device arrays, r each)
@@ -93,8 +99,8 @@ cudaError_t launch_gemm_nt_f32(const float *P, int64_t ldp, const float *Q, int6
                                float *C, int64_t ldc, int M, int N, int K, const int *gate,
                                cudaStream_t st);
 
-// U[c, i] = sum_t val[c, t] AT[idx[c, t], i] for every active start; does nothing when
-// *gate != 0 (the dense contraction runs instead)
+// U[c, i] = sum_t val[c, t] AT[idx[c, t], i] for every active start; runs only when
+// *gate != 0 (the control word chose the per-start gather)
 cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int *sup_idx,
                                 const float *sup_val, int cap, StartState s, int r, float *U,
                                 int64_t ldu, const int *gate, cudaStream_t st);
@@ -127,8 +133,9 @@ cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld,
 // columns for the launch; with n_dev != nullptr the kernel uses *n_dev (<= N) instead; map =
 // col_map when given, else the identity.  With gate != nullptr nothing runs unless *gate != 0;
 // a timed-out wait sets *err = SPCA_E_TIMEOUT
+// (K from *k_dev when k_dev != nullptr, K being then only an upper bound)
 cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
-                           TcPairs pairs, float *out, int64_t ldo, const int *gate, const int *n_dev,
+                           const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const int *gate, const int *n_dev,
                            const int *col_map, int *err, cudaStream_t st);
 // BF16 planes of an FP32 matrix (plane t at dst + t * plane_stride elements): destination row r
 // comes from source row row_map[r] (identity when null), r < rows (*rows_dev when given); gated
@@ -136,20 +143,23 @@ cudaError_t launch_split_planes(const float *src, int64_t rows, int64_t cols, in
                                 int64_t ldd, int64_t plane_stride, int nplanes, const int *gate,
                                 const int *rows_dev, const int *row_map, cudaStream_t st);
 // union S of the active starts' supports: colpos[j] = position of column j in S (or -1),
-// collist[k] = the k-th column of S (k < kcap), *kunion = |S|.  mark: p ints of scratch
+// collist[k] = the k-th column of S (k < kcap), c->kunion = |S|; then c->use_union (S fits in
+// kcap columns and no start needs the dense path) and, if set, c->use_gather = 0.
+// mark: p ints of scratch
 cudaError_t launch_union(const int *sup_idx, int cap, StartState s, int r, int p, int *mark, int *colpos,
-                         int *collist, int kcap, int *kunion, cudaStream_t st);
-// operands of u = A x over S (K = |S| <= kpad): AS planes n x kpad (row i: A[i, S], zero past K)
-// from the A^T planes, and XS planes (row k: the k-th active x at the positions of S)
+                         int *collist, int kcap, Ctrl *c, cudaStream_t st);
+// operands of u = A x over S when c->use_union: AS planes n x kcap (row i: A[i, S], zero past
+// |S| up to the next multiple of 64) from the A^T planes, and XS planes (row k: the k-th active
+// x at the positions of S)
 cudaError_t launch_union_operands(const void *ATpl, int64_t ldat, int64_t at_pstride, int n, const int *collist,
-                                  int K, int kpad, void *AS, int64_t ldas, int64_t as_pstride, const int *sup_idx,
-                                  const float *sup_val, int cap, StartState s, const int *act, const int *nact,
-                                  int nhost, const int *colpos, void *XS, int64_t ldxs, int64_t xs_pstride,
+                                  int kcap, void *AS, int64_t as_pstride, const int *sup_idx,
+                                  const float *sup_val, int cap, StartState s, const int *act, int nhost,
+                                  const int *colpos, void *XS, int64_t xs_pstride, const Ctrl *c,
                                   cudaStream_t st);
 // ordered list of the active starts (status == ST_ACTIVE): act[k] = c and rank[c] = k for the
-// k-th active start; the count goes to *count
-cudaError_t launch_active_list(const int *status, int r, int *act, int *rank, int *count,
-                               cudaStream_t st);
+// k-th active start; c->active = the count, c->use_gather = !c->need_dense (the union step,
+// when it runs afterwards, may take the sweep over)
+cudaError_t launch_active_list(const int *status, int r, int *act, int *rank, Ctrl *c, cudaStream_t st);
 
 // x-step (S3..S6), objective F, stopping rule, support lists
 cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,
