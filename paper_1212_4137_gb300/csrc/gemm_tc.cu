@@ -37,7 +37,13 @@ namespace spca {
 namespace {
 
 constexpr int TC_BM = 128;
-constexpr int TC_BK = 64;                 // 64 bf16 = 128 B rows: one 128B swizzle atom wide
+// K-block width of the configuration with three Q planes: 64 (128 B rows, 128B swizzle, 2
+// stages) or 32 (64 B rows, 64B swizzle, 4 stages); one Q plane always uses 64
+#ifndef SPCA_TC_BK_NB3
+#define SPCA_TC_BK_NB3 64
+#endif
+constexpr int TC_BK_NB3 = SPCA_TC_BK_NB3;
+constexpr int TC_STAGES_NB3 = TC_BK_NB3 == 64 ? 2 : 4;
 constexpr int TC_THREADS = 192;           // warp 0 TMA + TMEM alloc, warp 1 MMA, warps 2-5 epilogue
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;   // bounded waits: 2 s, then error + exit
 
@@ -86,14 +92,16 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
       ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
-// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row core groups 1024 B apart
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// shared-memory matrix descriptor: K-major rows of BK bf16 (BK = 64: 128B swizzle; BK = 32:
+// 64B swizzle), 8-row core groups 8 * 2 * BK bytes apart
+template <int BK>
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
   uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
-  d |= (uint64_t)1 << 16;                      // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1 << 46;                      // descriptor version (tcgen05)
-  d |= (uint64_t)2 << 61;                      // swizzle: 128B
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);             // start address
+  d |= (uint64_t)1 << 16;                                // leading byte offset (unused here)
+  d |= (uint64_t)((8 * 2 * BK) >> 4) << 32;             // stride byte offset: 8 rows
+  d |= (uint64_t)1 << 46;                                // descriptor version (tcgen05)
+  d |= (uint64_t)(BK == 64 ? 2 : 4) << 61;               // swizzle: 128B or 64B
   return d;
 }
 // multicast variant: the box lands at the same offset in every CTA of ctaMask, and the
@@ -159,7 +167,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 }  // namespace
 
-template <int BN, int NA, int NB, int STAGES>
+template <int BN, int NA, int NB, int STAGES, int TC_BK>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int M, int N,
               int kblocks, const int *__restrict__ k_dev, TcPairs pairs, float *__restrict__ out, int64_t ldo,
@@ -249,7 +257,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const bool first = kb == 0 && q == (main ? pairs.first_main : pairs.first_corr);
 #pragma unroll
         for (int kk = 0; kk < TC_BK / 16; ++kk) {
-          mma_bf16(d, sw128_desc(a_base + kk * 32), sw128_desc(b_base + kk * 32), idesc,
+          mma_bf16(d, sw_desc<TC_BK>(a_base + kk * 32), sw_desc<TC_BK>(b_base + kk * 32), idesc,
                    (first && kk == 0) ? 0u : 1u);
         }
       }
@@ -344,37 +352,40 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 }  // namespace
 
-// 3-D map over `planes` BF16 planes of `rows` x `ld` (K-contiguous), box 64 x box_rows x 1
+// 3-D map over `planes` BF16 planes of `rows` x `ld` (K-contiguous), box bk x box_rows x 1
 cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int64_t ld, int planes,
-                           int box_rows) {
+                           int box_rows, int bk) {
   auto enc = get_encode();
   if (!enc) return cudaErrorNotSupported;
   cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * (cuuint64_t)rows};
-  cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld, int planes) {
   for (int i = 0; i < 3; ++i) {
-    cudaError_t e = make_plane_map(&maps->m[i], base, rows, ld, planes, TC_BM >> i);
+    cudaError_t e = make_plane_map(&maps->m[i], base, rows, ld, planes, TC_BM >> i, 64);
+    if (e != cudaSuccess) return e;
+    e = make_plane_map(&maps->m32[i], base, rows, ld, planes, TC_BM >> i, 32);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
 namespace {
-template <int BN, int NA, int NB, int STAGES>
+template <int BN, int NA, int NB, int STAGES, int TC_BK>
 cudaError_t launch_tc_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, int K, const int *k_dev, TcPairs pairs,
                            float *out, int64_t ldo, const int *gate, const int *n_dev, const int *col_map,
                            int *err, cudaStream_t st) {
   constexpr int STAGE_BYTES = NA * TC_BM * TC_BK * 2 + NB * BN * TC_BK * 2;
   constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
-  auto kern = k_gemm_tc<BN, NA, NB, STAGES>;
+  auto kern = k_gemm_tc<BN, NA, NB, STAGES, TC_BK>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
@@ -400,7 +411,8 @@ cudaError_t launch_tc_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, i
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, P.m[lg], Q, M, N, kblocks, k_dev, pairs, out, ldo, gate, n_dev, col_map,
+  return cudaLaunchKernelEx(&cfg, kern, TC_BK == 64 ? P.m[lg] : P.m32[lg], Q, M, N, kblocks, k_dev, pairs, out, ldo,
+                            gate, n_dev, col_map,
                             err);
 }
 }  // namespace
@@ -409,12 +421,14 @@ cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb,
                            const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const int *gate,
                            const int *n_dev, const int *col_map, int *err, cudaStream_t st) {
   if (na == 3 && nb == 1)
-    return launch_tc_impl<256, 3, 1, 2>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
+    return launch_tc_impl<256, 3, 1, 2, 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
   if (na == 3 && nb == 3)
-    return launch_tc_impl<128, 3, 3, 2>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
+    return launch_tc_impl<128, 3, 3, TC_STAGES_NB3, TC_BK_NB3>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
+                                                               col_map, err, st);
   return cudaErrorInvalidValue;
 }
 
 int tc_box_rows(int nb) { return nb == 1 ? 256 : 128; }
+int tc_bk(int nb) { return nb == 1 ? 64 : TC_BK_NB3; }
 
 }  // namespace spca

@@ -177,15 +177,15 @@ int ensure_workspace(spca_handle *h, int r) {
     CK(dalloc(&h->Ypl, (size_t)3 * r * h->ldU, 2));
     CK(cudaMemsetAsync(h->Xpl, 0, (size_t)3 * r * h->ldX * 2, h->stream));
     CK(cudaMemsetAsync(h->Ypl, 0, (size_t)3 * r * h->ldU * 2, h->stream));
-    CK(make_plane_map(&h->tmX3, h->Xpl, r, h->ldX, 3, tc_box_rows(3)));
-    CK(make_plane_map(&h->tmY1, h->Ypl, r, h->ldU, 1, tc_box_rows(1)));
-    CK(make_plane_map(&h->tmY3, h->Ypl, r, h->ldU, 3, tc_box_rows(3)));
+    CK(make_plane_map(&h->tmX3, h->Xpl, r, h->ldX, 3, tc_box_rows(3), tc_bk(3)));
+    CK(make_plane_map(&h->tmY1, h->Ypl, r, h->ldU, 1, tc_box_rows(1), tc_bk(1)));
+    CK(make_plane_map(&h->tmY3, h->Ypl, r, h->ldU, 3, tc_box_rows(3), tc_bk(3)));
     h->kcap = (int)std::min<int64_t>(1024, (p + 63) / 64 * 64);
     CK(dalloc(&h->mark, (size_t)p)); CK(dalloc(&h->colpos, (size_t)p)); CK(dalloc(&h->collist, (size_t)h->kcap));
     CK(dalloc(&h->AS, (size_t)3 * n * h->kcap, 2));
     CK(dalloc(&h->XS, (size_t)3 * r * h->kcap, 2));
     CK(make_p_maps(&h->pmAS, h->AS, n, h->kcap, 3));
-    CK(make_plane_map(&h->tmXS3, h->XS, r, h->kcap, 3, tc_box_rows(3)));
+    CK(make_plane_map(&h->tmXS3, h->XS, r, h->kcap, 3, tc_box_rows(3), tc_bk(3)));
   }
   h->r_cap = r;
   return SPCA_OK;

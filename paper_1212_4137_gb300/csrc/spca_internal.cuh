@@ -121,12 +121,14 @@ struct TcPairs {      // plane products P plane a[q] x Q plane b[q], q < n; the 
 };
 // 3-D TMA map over `planes` BF16 planes of rows x ld (K-contiguous), box 64 x box_rows
 cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int64_t ld, int planes,
-                           int box_rows);
+                           int box_rows, int bk);
 int tc_box_rows(int nb);   // Q-operand box height for nb planes (the tile's N)
+int tc_bk(int nb);         // K-block width of the contraction with nb Q planes
 // P-operand maps with 128-, 64- and 32-row boxes (the slice one CTA of a 1-, 2- or 4-CTA
 // cluster loads and multicasts)
 struct PMaps {
-  CUtensorMap m[3];
+  CUtensorMap m[3];     // 64-wide K blocks
+  CUtensorMap m32[3];   // 32-wide K blocks
 };
 cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld, int planes);
 // out[map(c) * ldo + m] = sum_q sum_k P_{a_q}[m, k] Q_{b_q}[c, k], m < M, c < N.  N bounds the
