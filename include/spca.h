@@ -249,6 +249,36 @@ typedef enum {
 int spca_profile_enable(spca_handle *h, int on);
 int spca_profile_query(spca_handle *h, int kernel, int64_t *launches, double *ms);
 
+/*
+ * spca_objective_noalloc -- the objective f(x) of Table 1 and the explained variance
+ * (||Ax||_2^2 for L2 variance, ||Ax||_1 for L1 variance) of r given vectors x, with u = A x
+ * accumulated in FP64: the values spca_solve reports per start (start_objective,
+ * start_explained).  The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- code running inside someone else's CUDA graph capture,
+ * under an allocator that owns the whole device, or in a latency-critical loop where an
+ * allocation's implicit synchronisation is not acceptable.  It needs no handle and allocates
+ * nothing: its scratch is a fixed array in the library's device memory (4 MiB, held on every
+ * GPU that loads the library until the process exits).
+ *   form, gamma  Table 1 formulation (1..8) and the penalty weight (>= 0; ignored by 1..4).
+ *   A            device, n x p float, row-major, leading dimension lda >= p.
+ *   X            device, r x p float, one vector per row, leading dimension ldx >= p.
+ *   f, ev        device, r doubles each (outputs).
+ *   cuda_stream  cudaStream_t the kernels are queued on (NULL = the legacy default stream);
+ *                the call returns once they are queued.
+ * Limits: r * ceil(n / 256) <= SPCA_NOALLOC_MAX_PARTIALS, else SPCA_E_INVALID and nothing runs.
+ * The first call on a device looks up the scratch's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call shares the
+ * one scratch array: calls whose kernels overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller.  The scratch keeps the last call's contents; each
+ * call writes every entry it reads.
+ * Errors: SPCA_E_INVALID (form, sizes, leading dimensions, NULL pointers, gamma, limit),
+ *         SPCA_E_CUDA.
+ */
+#define SPCA_NOALLOC_MAX_PARTIALS 262144
+int spca_objective_noalloc(int form, double gamma, const float *A, int64_t n, int64_t p, int64_t lda,
+                           const float *X, int64_t ldx, int r, double *f, double *ev,
+                           void *cuda_stream);
+
 /* spca_destroy -- free the handle's device memory (waits for its stream). NULL is a no-op. */
 void spca_destroy(spca_handle *h);
 

@@ -22,7 +22,7 @@ SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC = 0, 1, 2
 
 # every symbol include/spca.h declares
 EXPORTS = ("spca_create", "spca_solve", "spca_xstep", "spca_products", "spca_profile_enable",
-           "spca_profile_query",
+           "spca_profile_query", "spca_objective_noalloc",
            "spca_destroy", "spca_strerror", "spca_last_error")
 SPCA_K_ALL, SPCA_K_INIT, SPCA_K_U_DENSE, SPCA_K_U_SPARSE, SPCA_K_YSTEP, SPCA_K_V, SPCA_K_XSTEP, \
     SPCA_K_FINALISE, SPCA_K_PREP = range(-1, 8)
@@ -87,6 +87,10 @@ def load(path: str = LIB_PATH):
         lib.spca_products.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                       ctypes.c_void_p, ctypes.c_int64]
+        lib.spca_objective_noalloc.restype = ctypes.c_int
+        lib.spca_objective_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64,
+                                               ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.spca_profile_enable.restype = ctypes.c_int
         lib.spca_profile_enable.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.spca_profile_query.restype = ctypes.c_int
@@ -140,6 +144,13 @@ def spca_xstep(h, form, s, gamma, calibrate, V, ldv, r, X, ldx, F, nnz, thr) -> 
 def spca_products(h, form, engine, X, ldx, r, U, ldu, V, ldv) -> int:
     return load().spca_products(h, int(form), int(engine), ctypes.c_void_p(X), ldx, r, ctypes.c_void_p(U), ldu,
                                 ctypes.c_void_p(V), ldv)
+
+
+def spca_objective_noalloc(form, gamma, A, n, p, lda, X, ldx, r, f, ev, stream=0) -> int:
+    """All pointers are device addresses (ints)."""
+    return load().spca_objective_noalloc(int(form), float(gamma), ctypes.c_void_p(A), n, p, lda,
+                                         ctypes.c_void_p(X), ldx, int(r), ctypes.c_void_p(f),
+                                         ctypes.c_void_p(ev), ctypes.c_void_p(stream))
 
 
 def spca_profile_enable(h, on: bool) -> int:
