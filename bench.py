@@ -197,9 +197,10 @@ def run_ours(args, w, rank, world, local_rank):
     value = sweeps_all / (ms_max / 1e3)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    A_pin = torch.from_numpy(A).pin_memory()
-    G_pin = torch.from_numpy(G).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
+    if e2e_steps:
+        A_pin = torch.from_numpy(A).pin_memory()
+        G_pin = torch.from_numpy(G).pin_memory()
     barrier(world)
     t0 = time.perf_counter()
     e2e_sweeps = 0
@@ -214,7 +215,7 @@ def run_ours(args, w, rank, world, local_rank):
         h2.close()
     torch.cuda.synchronize(dev)
     e2e_s = reduce_max(time.perf_counter() - t0, world)
-    e2e_value = reduce_sum(e2e_sweeps, world) / e2e_s
+    e2e_value = reduce_sum(e2e_sweeps, world) / e2e_s if e2e_steps else 0.0
     h2d = A.nbytes + len(w["forms"]) * G.nbytes
     h.close()
 
@@ -259,8 +260,8 @@ def run_ours(args, w, rank, world, local_rank):
         "sweeps_starts": int(sweeps_all),
         "kernels_ms_share": {k: round(v / total_ms, 4) for k, v in shares.items()},
         "roofline": roof,
-        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h // e2e_steps), "steps": e2e_steps},
+        "e2e": ({"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                 "d2h_bytes_per_step": int(d2h // e2e_steps), "steps": e2e_steps} if e2e_steps else None),
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
@@ -377,9 +378,14 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # for profiler captures: a subset of the formulations, no end-to-end pass
+    ap.add_argument("--forms", type=str, default=None, help="comma-separated formulations (default: all 8)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     rank, world, local = init_dist()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.forms:
+        w["forms"] = tuple(int(t) for t in args.forms.split(","))
     if args.impl == "reference":
         line = run_reference(args, w, rank, world)
     else:

@@ -129,15 +129,32 @@ __device__ void radix_select(const float *vv, int p, int j, bool exact, XShared 
       if (m && lane == __ffs(peers) - 1) atomicAdd(&sh.hist[bin], (unsigned)__popc(peers));
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int acc = 0, d = (int)wmask[t];
-      for (; d > 0; --d) {
-        if (acc + (int)sh.hist[d] >= rem) break;
-        acc += (int)sh.hist[d];
+    if (threadIdx.x < 32) {
+      // warp 0 finds the bin holding the rem-th largest: lane l owns the bins
+      // [top - l*per, top - l*per - per + 1] (descending), scans the lane sums from the top,
+      // and the owning lane walks its own bins
+      const int nb = (int)wmask[t] + 1, per = nb / 32, top = nb - 1 - lane * per;
+      int lsum = 0;
+      for (int q = 0; q < per; ++q) lsum += (int)sh.hist[top - q];
+      int incl = lsum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
       }
-      sh.digit = d;
-      sh.rem = rem - acc;
-      sh.cnt_bin = (int)sh.hist[d];
+      const int excl = incl - lsum;
+      const bool mine = excl < rem && rem <= incl;
+      const unsigned who = __ballot_sync(0xffffffffu, mine);
+      if (mine && lane == __ffs(who) - 1) {
+        int acc = excl, d = top;
+        for (int q = 0; q < per - 1; ++q, --d) {
+          if (acc + (int)sh.hist[d] >= rem) break;
+          acc += (int)sh.hist[d];
+        }
+        sh.digit = d;
+        sh.rem = rem - acc;
+        sh.cnt_bin = (int)sh.hist[d];
+      }
     }
     __syncthreads();
     prefix |= (uint32_t)sh.digit << sh_;

@@ -27,41 +27,41 @@ __global__ void __launch_bounds__(256) k_union_mark(const int *__restrict__ sup_
   for (int t = threadIdx.x; t < nnz; t += blockDim.x) mark[gi[t]] = 1;
 }
 
-// one CTA: each thread owns a contiguous segment of columns; one block scan of the per-thread
-// counts gives every marked column its position in index order
+// one CTA of 32 warps: warp w owns a contiguous segment of the columns and walks it 32 at a
+// time (coalesced), counting marks with ballots; one scan over the 32 warp counts then gives
+// every marked column its position in index order
 __global__ void __launch_bounds__(1024) k_union_scan(const int *__restrict__ mark, int p, int *__restrict__ colpos,
                                                      int *__restrict__ collist, int kcap, Ctrl *__restrict__ ctrl) {
-  __shared__ int red[32];
+  __shared__ int woff[32];
   __shared__ int total_s;
-  const int seg = (p + blockDim.x - 1) / blockDim.x;
-  const int lo = min(p, (int)threadIdx.x * seg), hi = min(p, lo + seg);
-  int cnt = 0;
-  for (int j = lo; j < hi; ++j) cnt += mark[j] != 0;
-  // exclusive scan of cnt over the block (warp shuffles, then the warp totals)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
+  const int seg = ((p + nw - 1) / nw + 31) / 32 * 32;
+  const int lo = min(p, w * seg), hi = min(p, lo + seg);
+  int cnt = 0;
+  for (int base = lo; base < hi; base += 32) {
+    const int j = base + lane;
+    cnt += __popc(__ballot_sync(0xffffffffu, j < hi && mark[j] != 0));
   }
-  if (lane == 31) red[w] = incl;
+  if (lane == 0) woff[w] = cnt;
   __syncthreads();
   if (threadIdx.x == 0) {
     int acc = 0;
-    for (int k = 0; k < nw; ++k) { const int t = red[k]; red[k] = acc; acc += t; }
+    for (int k = 0; k < nw; ++k) { const int t = woff[k]; woff[k] = acc; acc += t; }
     total_s = acc;
   }
   __syncthreads();
-  int pos = red[w] + incl - cnt;
-  for (int j = lo; j < hi; ++j) {
-    if (mark[j] != 0) {
-      colpos[j] = pos;
-      if (pos < kcap) collist[pos] = j;
-      ++pos;
-    } else {
-      colpos[j] = -1;
+  int pos = woff[w];
+  const unsigned lt = (1u << lane) - 1u;
+  for (int base = lo; base < hi; base += 32) {
+    const int j = base + lane;
+    const bool on = j < hi && mark[j] != 0;
+    const unsigned b = __ballot_sync(0xffffffffu, on);
+    if (j < hi) {
+      const int q = pos + __popc(b & lt);
+      colpos[j] = on ? q : -1;
+      if (on && q < kcap) collist[q] = j;
     }
+    pos += __popc(b);
   }
   if (threadIdx.x == 0) {
     const int K = total_s;
@@ -84,7 +84,8 @@ cudaError_t launch_union(const int *sup_idx, int cap, StartState s, int r, int p
 }
 
 // AS[t][i * kcap + k] = plane t of A[i, collist[k]] (= A^T[collist[k], i]) for k < K', 0 for
-// K' <= k < kpad; 32 x 32 tiles transposed through shared memory (coalesced on both sides)
+// K' <= k < kpad; 32 x 32 tiles transposed through shared memory (coalesced on both sides),
+// visited by a grid-stride loop so that a gated-off launch costs only a few early exits
 __global__ void __launch_bounds__(256) k_gather_cols(const __nv_bfloat16 *__restrict__ ATpl, int64_t ldat,
                                                      int64_t at_pstride, int n, const int *__restrict__ collist,
                                                      int kcap, __nv_bfloat16 *__restrict__ AS, int64_t as_pstride,
@@ -92,21 +93,26 @@ __global__ void __launch_bounds__(256) k_gather_cols(const __nv_bfloat16 *__rest
   __shared__ __nv_bfloat16 tile[32][34];
   if (ctrl->use_union == 0) return;
   const int K = ctrl->kunion, kpad = min(kcap, (K + 63) / 64 * 64);
-  const int k0 = blockIdx.x * 32, i0 = blockIdx.y * 32, pl = blockIdx.z;
-  if (k0 >= kpad) return;
-  const __nv_bfloat16 *src = ATpl + pl * at_pstride;
-  __nv_bfloat16 *dst = AS + pl * as_pstride;
+  const int tk = (kpad + 31) / 32, ti = (n + 31) / 32;
+  const int ntiles = tk * ti * 3;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
-  for (int kk = ty; kk < 32; kk += 8) {
-    const int k = k0 + kk, i = i0 + tx;
-    __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
-    if (k < K && i < n) v = src[(int64_t)collist[k] * ldat + i];
-    tile[kk][tx] = v;
-  }
-  __syncthreads();
-  for (int ii = ty; ii < 32; ii += 8) {
-    const int i = i0 + ii, k = k0 + tx;
-    if (i < n && k < kpad) dst[(int64_t)i * kcap + k] = tile[tx][ii];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int pl = t / (tk * ti), rem = t - pl * tk * ti;
+    const int k0 = (rem % tk) * 32, i0 = (rem / tk) * 32;
+    const __nv_bfloat16 *src = ATpl + pl * at_pstride;
+    __nv_bfloat16 *dst = AS + pl * as_pstride;
+    __syncthreads();
+    for (int kk = ty; kk < 32; kk += 8) {
+      const int k = k0 + kk, i = i0 + tx;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
+      if (k < K && i < n) v = src[(int64_t)collist[k] * ldat + i];
+      tile[kk][tx] = v;
+    }
+    __syncthreads();
+    for (int ii = ty; ii < 32; ii += 8) {
+      const int i = i0 + ii, k = k0 + tx;
+      if (i < n && k < kpad) dst[(int64_t)i * kcap + k] = tile[tx][ii];
+    }
   }
 }
 
@@ -149,8 +155,7 @@ cudaError_t launch_union_operands(const void *ATpl, int64_t ldat, int64_t at_pst
                                   const float *sup_val, int cap, StartState s, const int *act, int nhost,
                                   const int *colpos, void *XS, int64_t xs_pstride, const Ctrl *c,
                                   cudaStream_t st) {
-  dim3 g1((unsigned)((kcap + 31) / 32), (unsigned)((n + 31) / 32), 3);
-  k_gather_cols<<<g1, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(ATpl), ldat, at_pstride, n, collist, kcap,
+  k_gather_cols<<<608, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(ATpl), ldat, at_pstride, n, collist, kcap,
                                     static_cast<__nv_bfloat16 *>(AS), as_pstride, c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

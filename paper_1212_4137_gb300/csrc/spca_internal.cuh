@@ -128,7 +128,6 @@ int tc_bk(int nb);         // K-block width of the contraction with nb Q planes
 // cluster loads and multicasts)
 struct PMaps {
   CUtensorMap m[3];     // 64-wide K blocks
-  CUtensorMap m32[3];   // 32-wide K blocks
 };
 cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld, int planes);
 // out[map(c) * ldo + m] = sum_q sum_k P_{a_q}[m, k] Q_{b_q}[c, k], m < M, c < N.  N bounds the
