@@ -94,6 +94,25 @@ __device__ __forceinline__ int block_excl_scan_flag(bool flag, int *red, int *to
   return off + in_warp;
 }
 
+// Compensated dot product in FP32 pairs (Ogita, Rump, Oishi 2005, "Dot2"): each product is
+// split exactly into its rounded value and its error (one FMA), the running sum is kept as an
+// unevaluated pair hi + lo with Knuth's two-sum, and the errors are collected in lo.  The result
+// is as accurate as an FP32 sum carried in twice the precision, on the FP32 pipe (GB300 runs FP64
+// at a small fraction of the FP32 rate).  The _rn intrinsics are never fused or reassociated.
+struct F32Pair {
+  float hi = 0.0f, lo = 0.0f;
+};
+__device__ __forceinline__ void f32pair_fma(F32Pair &s, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(s.hi, p);
+  const float bv = __fsub_rn(t, s.hi);
+  const float te = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+  s.hi = t;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(te, pe));
+}
+__device__ __forceinline__ double f32pair_value(const F32Pair &s) { return (double)s.hi + (double)s.lo; }
+
 // order-preserving key of |v|: the IEEE bits without the sign (monotone for |v| >= 0)
 __device__ __forceinline__ uint32_t abs_key(float v) { return __float_as_uint(v) & 0x7fffffffu; }
 

@@ -614,35 +614,57 @@ cudaError_t launch_tc2_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, 
 }
 }  // namespace
 
+// N width of the CTA-pair tile: 256 (512 TMEM columns: the hi x hi and the correction
+// accumulators of 256 columns each) or 128; each CTA of a pair loads BN / 2 rows of Q, and the
+// single-CTA tile used for a lone M tile is BN / 2 wide so that both read the same Q boxes
+#ifndef SPCA_TC_PAIR_BN
+#define SPCA_TC_PAIR_BN 256
+#endif
+constexpr int TC_PAIR_BN = SPCA_TC_PAIR_BN;
+static_assert(TC_PAIR_BN == 128 || TC_PAIR_BN == 256, "pair tile width");
+
 namespace {
-// the single-CTA kernel with its cluster multicast of P: 128 x 64 tiles
+// pipeline stages that fit in shared memory (227 KB per CTA, less 1 KB of alignment slack and
+// 1 KB of barriers): 3 P planes of 128 x 64 plus nb Q planes of (BN / 2) x 64, all BF16 -- the
+// same per CTA for the pair tile and for the single-CTA tile
+constexpr int tc_stages(int nb) {
+  return (230400 / (3 * TC_BM * 64 * 2 + nb * (TC_PAIR_BN / 2) * 64 * 2)) > 4
+             ? 4
+             : 230400 / (3 * TC_BM * 64 * 2 + nb * (TC_PAIR_BN / 2) * 64 * 2);
+}
+
+// the single-CTA kernel with its cluster multicast of P: 128 x (BN / 2) tiles
 cudaError_t launch_gemm_tc_single(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
                                   const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const int *gate,
                                   const int *n_dev, const int *col_map, int *err, cudaStream_t st) {
+  constexpr int BN1 = TC_PAIR_BN / 2;
   if (na == 3 && nb == 1)
-    return launch_tc_impl<64, 3, 1, 4, 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
+    return launch_tc_impl<BN1, 3, 1, tc_stages(1), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
+                                                           col_map, err, st);
   if (na == 3 && nb == 3)
-    return launch_tc_impl<64, 3, 3, 3, 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
+    return launch_tc_impl<BN1, 3, 3, tc_stages(3), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
+                                                           col_map, err, st);
   return cudaErrorInvalidValue;
 }
 }  // namespace
 
-// CTA pairs (256 x 128 tiles) when there are at least two M tiles; one M tile runs on single CTAs
+// CTA pairs (256 x BN tiles) when there are at least two M tiles; one M tile runs on single CTAs
 cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
                            const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const int *gate,
                            const int *n_dev, const int *col_map, int *err, cudaStream_t st) {
   if (M <= TC_BM)
     return launch_gemm_tc_single(P, na, Q, nb, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
   if (na == 3 && nb == 1)
-    return launch_tc2_impl<128, 3, 1, 4>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
+    return launch_tc2_impl<TC_PAIR_BN, 3, 1, tc_stages(1)>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
+                                                             col_map, err, st);
   if (na == 3 && nb == 3)
-    return launch_tc2_impl<128, 3, 3, 3>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
+    return launch_tc2_impl<TC_PAIR_BN, 3, 3, tc_stages(3)>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
+                                                             col_map, err, st);
   return cudaErrorInvalidValue;
 }
 
-// Q-operand boxes are 64 rows: each CTA of a pair loads half of a 128-wide N tile, a single CTA
-// a whole 64-wide one
-int tc_box_rows(int nb) { (void)nb; return 64; }
+// Q-operand boxes: BN / 2 rows (half of a pair tile, or a whole single-CTA tile)
+int tc_box_rows(int nb) { (void)nb; return TC_PAIR_BN / 2; }
 int tc_bk(int nb) { (void)nb; return 64; }
 
 }  // namespace spca

@@ -1,6 +1,7 @@
 // kernel_finalise.cu -- after the sweeps: the Table 1 objective f(x) of every start with
-// u = A x accumulated in FP64 (the only FP64 arithmetic of the path), the explained variance
-// (Section 4.1), the best start (ties: lower index), and y(x) and the support of the best x.
+// u = A x accumulated as a compensated FP32-pair dot product (about twice FP32's precision) and
+// the norms of u summed in FP64, the explained variance (Section 4.1), the best start (ties:
+// lower index), and y(x) and the support of the best x.
 #include <cstdint>
 
 #include "block_util.cuh"
@@ -12,8 +13,8 @@ namespace {
 constexpr int FT = 256;
 }
 
-// grid (ceil(n / FT), r): u_i = sum_t x_{j_t} A[i, j_t] over the support, products and sums
-// in FP64; per-CTA partial sums of |u_i| and u_i^2 go to partials (fixed order later).
+// grid (ceil(n / FT), r): u_i = sum_t x_{j_t} A[i, j_t] over the support (compensated FP32
+// pairs); per-CTA FP64 partial sums of |u_i| and u_i^2 go to partials (fixed order later).
 __global__ void __launch_bounds__(FT) k_fin_partial(const float *__restrict__ AT, int64_t ldat, int n,
                                                     const int *__restrict__ sup_idx,
                                                     const float *__restrict__ sup_val, int cap,
@@ -27,7 +28,7 @@ __global__ void __launch_bounds__(FT) k_fin_partial(const float *__restrict__ AT
   const int nnz = st.nnz[c];
   const int *gi = sup_idx + (int64_t)c * cap;
   const float *gv = sup_val + (int64_t)c * cap;
-  double acc = 0.0;
+  F32Pair acc2;
   for (int t0 = 0; t0 < nnz; t0 += FT) {
     __syncthreads();
     if (t0 + (int)threadIdx.x < nnz) {
@@ -37,8 +38,9 @@ __global__ void __launch_bounds__(FT) k_fin_partial(const float *__restrict__ AT
     __syncthreads();
     const int m = min(FT, nnz - t0);
     if (i < n)
-      for (int t = 0; t < m; ++t) acc = fma((double)sval[t], (double)AT[(int64_t)sidx[t] * ldat + i], acc);
+      for (int t = 0; t < m; ++t) f32pair_fma(acc2, sval[t], AT[(int64_t)sidx[t] * ldat + i]);
   }
+  const double acc = f32pair_value(acc2);
   if (i < n) U[(int64_t)c * ldu + i] = (float)acc;
   const double l1 = block_sum_d(i < n ? fabs(acc) : 0.0, red);
   const double l2 = block_sum_d(i < n ? acc * acc : 0.0, red);
