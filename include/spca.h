@@ -226,8 +226,11 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
 
 /*
  * Measurement hooks (not part of the method): per-kernel launch counts are always kept;
- * with profiling on, every launch is also bracketed by CUDA events on the handle's stream.
- *   spca_profile_enable  on != 0 starts timing (and clears the counters), 0 stops it.
+ * with profiling on, the launches of the selected kernel ids are also bracketed by CUDA
+ * events on the handle's stream (each pair costs a few microseconds of host and device time).
+ *   spca_profile_enable  mask = bit (1 << id) per spca_kernel_id to time, SPCA_PROFILE_ALL for
+ *                        every kernel, 0 to stop; clears the counters.  A mask outside
+ *                        0..SPCA_PROFILE_ALL is SPCA_E_INVALID.
  *   spca_profile_query   kernel = one of spca_kernel_id, or SPCA_K_ALL for the total launch
  *                        count (ms then = sum over kernels); waits for the stream, then
  *                        writes the number of launches and their summed device time in ms
@@ -246,7 +249,8 @@ typedef enum {
     SPCA_K_PREP = 7,          /* layout preparation and input checks                        */
     SPCA_K_COUNT = 8
 } spca_kernel_id;
-int spca_profile_enable(spca_handle *h, int on);
+#define SPCA_PROFILE_ALL ((1 << SPCA_K_COUNT) - 1)
+int spca_profile_enable(spca_handle *h, int mask);
 int spca_profile_query(spca_handle *h, int kernel, int64_t *launches, double *ms);
 
 /*

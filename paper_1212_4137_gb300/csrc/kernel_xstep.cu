@@ -197,14 +197,15 @@ __device__ void radix_select(const float *vv, int p, int j, bool exact, XShared 
 }
 
 // lambda_s(v) (Section 2.1) when phi(0) < 0.  Bisection over the float keys of lambda in
-// [0, max|v|] on the sign of phi, stopping as soon as no |v_i| lies strictly inside the
-// bracket (the active set is then fixed); then the root of phi on that piece in FP64.
+// [lo0, max|v|] (phi(lo0) < 0 is known: lo0 = 0, or a lower bound checked by the caller) on
+// the sign of phi, stopping as soon as no |v_i| lies strictly inside the bracket (the active
+// set is then fixed); then the root of phi on that piece in FP64.
 // *lo_out: the active set is {key_i > *lo_out}.
-__device__ double lambda_s_bisect(const float *vv, int p, double s, uint32_t maxkey, XShared &sh,
+__device__ double lambda_s_bisect(const float *vv, int p, double s, uint32_t lo0, uint32_t maxkey, XShared &sh,
                                   uint32_t *lo_out) {
   const int lane = threadIdx.x & 31;
   const Seg sg = warp_seg(p);
-  uint32_t lo = 0u, hi = maxkey;  // phi(key lo) < 0 <= phi(key hi)
+  uint32_t lo = lo0, hi = maxkey;  // phi(key lo) < 0 <= phi(key hi)
   while (hi - lo > 1u) {
     const uint32_t mid = lo + (hi - lo) / 2u;
     const float lam = __uint_as_float(mid);
@@ -263,116 +264,43 @@ __device__ double lambda_s_bisect(const float *vv, int p, double s, uint32_t max
   return lam;
 }
 
-template <bool kSmem>
-__global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restrict__ V, int64_t ldv,
-                                              float *__restrict__ X, int64_t ldx, StartState st,
-                                              int *__restrict__ sup_idx, float *__restrict__ sup_val,
-                                              Ctrl *ctrl) {
-  extern __shared__ float vsm[];
-  __shared__ XShared sh;
-  const int c = blockIdx.x;
-  if (st.status && st.status[c] != ST_ACTIVE) return;
-  const int p = a.p;
-  const int lane = threadIdx.x & 31;
-  const float *vg = V + (int64_t)c * ldv;
-  float *x = X + (int64_t)c * ldx;
-  const int form = a.form;
-  if (kSmem) {
-    for (int i = threadIdx.x; i < p; i += XT) vsm[i] = vg[i];
-    __syncthreads();
-  }
-  const float *vv = kSmem ? vsm : vg;
-  const Seg sg = warp_seg(p);
-
-  // ---- the operator's parameters
-  // mode 0: T_s with ties: keep key > K, plus the first need_eq of key == K in index order
-  // mode 1: hard threshold: keep key > tkey, value v            (U_gamma; T_s otherwise)
-  // mode 2: soft threshold: keep key > tkey, value sgn(v)(|v|-t)  (V_gamma, V_lambda)
-  int mode = 0;
+// ---------------------------------------------------------------- the operator, then x
+// mode 0: T_s with ties: keep key > K, plus the first need_eq of key == K in index order
+// mode 1: hard threshold: keep key > tkey, value v            (U_gamma; T_s otherwise)
+// mode 2: soft threshold: keep key > tkey, value sgn(v)(|v|-t)  (V_gamma, V_lambda)
+struct XOp {
+  int mode = 1;
   uint32_t K = 0u, tkey = 0u;
-  int need_eq = 0, eq_total = 0;
-  float tval = 0.0f;     // threshold value subtracted in mode 2
-  double gam = 0.0;      // gamma in Table 1 units (penalties) or lambda_s (S4)
-  const int s_int = (int)a.s;
+  int need_eq = 0;
+  float tval = 0.0f;    // threshold value subtracted in mode 2
+  double gam = 0.0;     // gamma in Table 1 units (penalties) or lambda_s (S4)
+  float tnext = 0.0f;   // the threshold (|v| units) that seeds the next sweep's candidate filter
+};
 
-  if (uses_T(form)) {
-    mode = 1;
-    if (s_int < p) {
-      bool whole;
-      radix_select(vv, p, s_int, false, sh, &K, &whole, &need_eq, &eq_total);
-      if (whole) {
-        tkey = K == 0u ? 0u : K - 1u;          // keep every key >= the bin's lower bound
-      } else if (K == 0u || need_eq >= eq_total) {
-        tkey = K == 0u ? 0u : K - 1u;          // no ties to break: keep key >= K
-      } else {
-        mode = 0;
-      }
-    }
-  } else if (uses_lam(form)) {
-    // phi(0) = s ||v||_2^2 - ||v||_1^2 >= 0: the L1 ball is not binding, lambda = 0
-    float f1 = 0.0f, f2 = 0.0f;
-    unsigned mk = 0u;
-    for (int i = sg.lo + lane; i < sg.hi; i += 32) {
-      const float av = fabsf(vv[i]);
-      f1 += av;
-      f2 = fmaf(av, av, f2);
-      mk = max(mk, __float_as_uint(av));
-    }
-    int d0 = 0, d1 = 0;
-    block_sum2f(f1, f2, d0, d1, sh);
-    const uint32_t maxkey = block_max_u(mk, sh.red_u);
-    mode = 2;
-    if ((float)a.s * f2 - f1 * f1 >= 0.0f) {
-      gam = 0.0;
-      tkey = 0u;
-      tval = 0.0f;
-    } else {
-      uint32_t lo;
-      gam = lambda_s_bisect(vv, p, a.s, maxkey, sh, &lo);
-      tkey = lo;
-      tval = (float)gam;
-    }
-  } else {  // penalties
-    mode = uses_U(form) ? 1 : 2;
-    if (a.calibrate) {
-      const int j = s_int + 1;
-      uint32_t tk = 0u;
-      if (j <= p) {
-        int ne, et;
-        bool whole;
-        radix_select(vv, p, j, true, sh, &tk, &whole, &ne, &et);
-      }
-      tkey = tk;
-      tval = __uint_as_float(tk);
-      gam = uses_U(form) ? (double)tval * (double)tval : (double)tval;
-      if (threadIdx.x == 0 && st.thr) st.thr[c] = tval;
-    } else if (a.per_start_thr) {
-      tval = st.thr[c];
-      gam = st.gamma[c];
-      tkey = __float_as_uint(tval);
-    } else {
-      tval = a.thr_fixed;
-      gam = a.gamma_fixed;
-      tkey = __float_as_uint(tval);
-    }
-  }
+// Pass A (||w||_2^2 and nnz of the unnormalised result w), the Table 3 value, pass B (x = w /
+// ||w||_2 and the support list in index order) and the per-start outputs, over vv[0 .. len):
+// element i is entry map[i] of v and x (map == nullptr: entry i).
+__device__ void xstep_finish(const XstepArgs &a, int c, const float *vv, int len, const int *map, const XOp &op,
+                             float *x, StartState st, int *sup_idx, float *sup_val, Ctrl *ctrl, XShared &sh) {
+  const int lane = threadIdx.x & 31;
+  const int form = a.form;
+  const Seg sg = warp_seg(len);
 
   // ---- ties (mode 0): offsets of each warp's equal keys in index order
-  if (mode == 0) {
+  if (op.mode == 0) {
     int eq = 0;
-    for (int i = sg.lo + lane; i < sg.hi; i += 32) eq += abs_key(vv[i]) == K;
+    for (int i = sg.lo + lane; i < sg.hi; i += 32) eq += abs_key(vv[i]) == op.K;
     eq = warp_sum_i(eq);
     warp_offsets(eq, sh);
   }
-  const int eq_base = (mode == 0) ? sh.woff[threadIdx.x >> 5] : 0;
+  const int eq_base = (op.mode == 0) ? sh.woff[threadIdx.x >> 5] : 0;
   const unsigned lt_mask = (1u << lane) - 1u;
 
-  // ---- pass A: ||w||_2^2 and nnz of the unnormalised result w
   auto wval = [&](float vi, uint32_t key, bool tie_keep) -> float {
-    if (mode == 0) return (key > K || (key == K && tie_keep)) ? vi : 0.0f;
-    if (key <= tkey) return 0.0f;
-    if (mode == 1) return vi;
-    return copysignf(fabsf(vi) - tval, vi);
+    if (op.mode == 0) return (key > op.K || (key == op.K && tie_keep)) ? vi : 0.0f;
+    if (key <= op.tkey) return 0.0f;
+    if (op.mode == 1) return vi;
+    return copysignf(fabsf(vi) - op.tval, vi);
   };
   float part = 0.0f;
   int wnnz = 0;
@@ -383,9 +311,9 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
       const float vi = (i < sg.hi) ? vv[i] : 0.0f;
       const uint32_t key = abs_key(vi);
       bool tie_keep = false;
-      if (mode == 0) {
-        const unsigned b = __ballot_sync(0xffffffffu, i < sg.hi && key == K);
-        tie_keep = (eq_run + __popc(b & lt_mask)) < need_eq;
+      if (op.mode == 0) {
+        const unsigned b = __ballot_sync(0xffffffffu, i < sg.hi && key == op.K);
+        tie_keep = (eq_run + __popc(b & lt_mask)) < op.need_eq;
         eq_run += __popc(b);
       }
       const float w = (i < sg.hi) ? wval(vi, key, tie_keep) : 0.0f;
@@ -403,11 +331,11 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
   // ---- Table 3 value of the subproblem
   double F;
   if (uses_T(form)) F = nrm;                                   // S3: ||T_s(v)||_2
-  else if (uses_lam(form)) F = gam * sqrt(a.s) + nrm;          // S4: lambda sqrt(s) + ||V||_2
-  else if (uses_U(form)) F = sumsq - gam * (double)nnz;        // S5: ||U||^2 - gamma ||U||_0
+  else if (uses_lam(form)) F = op.gam * sqrt(a.s) + nrm;       // S4: lambda sqrt(s) + ||V||_2
+  else if (uses_U(form)) F = sumsq - op.gam * (double)nnz;     // S5: ||U||^2 - gamma ||U||_0
   else F = nrm;                                                // S6: ||V_gamma(v)||_2
 
-  // ---- pass B: x = w / ||w||_2 and the support list in index order
+  // ---- pass B
   const float inv = nrm > 0.0 ? (float)(1.0 / nrm) : 0.0f;
   int *gi = sup_idx ? sup_idx + (int64_t)c * a.cap : nullptr;
   float *gv = sup_val ? sup_val + (int64_t)c * a.cap : nullptr;
@@ -419,19 +347,20 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
       const float vi = (i < sg.hi) ? vv[i] : 0.0f;
       const uint32_t key = abs_key(vi);
       bool tie_keep = false;
-      if (mode == 0) {
-        const unsigned b = __ballot_sync(0xffffffffu, i < sg.hi && key == K);
-        tie_keep = (eq_run + __popc(b & lt_mask)) < need_eq;
+      if (op.mode == 0) {
+        const unsigned b = __ballot_sync(0xffffffffu, i < sg.hi && key == op.K);
+        tie_keep = (eq_run + __popc(b & lt_mask)) < op.need_eq;
         eq_run += __popc(b);
       }
       const float w = (i < sg.hi) ? wval(vi, key, tie_keep) : 0.0f;
       const float xi = w * inv;
-      if (i < sg.hi) x[i] = xi;
+      const int j = (i < sg.hi) ? (map ? map[i] : i) : 0;
+      if (i < sg.hi) x[j] = xi;
       const unsigned nzb = __ballot_sync(0xffffffffu, xi != 0.0f);
       if (gi && xi != 0.0f) {
         const int q = pos + __popc(nzb & lt_mask);
         if (q < a.cap) {
-          gi[q] = i;
+          gi[q] = j;
           gv[q] = xi;
         }
       }
@@ -443,7 +372,8 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
   if (threadIdx.x == 0) {
     if (st.F) st.F[c] = F;
     if (st.nnz) st.nnz[c] = nnz;
-    if (st.gamma) st.gamma[c] = gam;
+    if (st.gamma) st.gamma[c] = op.gam;
+    if (st.tprev) st.tprev[c] = op.tnext;
     if (st.status) {
       int status = ST_ACTIVE;
       if (nrm == 0.0) {
@@ -460,11 +390,307 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
     }
   }
 }
+
+// ---------------------------------------------------------------- full x-step
+// Every pass over all p entries of v (staged in shared memory when it fits).  Starts that the
+// candidate kernel below already finished in this sweep are skipped.
+template <bool kSmem>
+__global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restrict__ V, int64_t ldv,
+                                              float *__restrict__ X, int64_t ldx, StartState st,
+                                              int *__restrict__ sup_idx, float *__restrict__ sup_val,
+                                              Ctrl *ctrl) {
+  extern __shared__ float vsm[];
+  __shared__ XShared sh;
+  const int c = blockIdx.x;
+  if (st.status && st.status[c] != ST_ACTIVE) return;
+  if (st.xfast && st.xfast[c]) return;
+  const int p = a.p;
+  const int lane = threadIdx.x & 31;
+  const float *vg = V + (int64_t)c * ldv;
+  float *x = X + (int64_t)c * ldx;
+  const int form = a.form;
+  if (kSmem) {
+    for (int i = threadIdx.x; i < p; i += XT) vsm[i] = vg[i];
+    __syncthreads();
+  }
+  const float *vv = kSmem ? vsm : vg;
+  const Seg sg = warp_seg(p);
+
+  XOp op;
+  const int s_int = (int)a.s;
+  if (uses_T(form)) {
+    op.mode = 1;
+    if (s_int < p) {
+      bool whole;
+      int eq_total;
+      radix_select(vv, p, s_int, false, sh, &op.K, &whole, &op.need_eq, &eq_total);
+      op.tnext = __uint_as_float(op.K);
+      if (whole) {
+        op.tkey = op.K == 0u ? 0u : op.K - 1u;   // keep every key >= the bin's lower bound
+      } else if (op.K == 0u || op.need_eq >= eq_total) {
+        op.tkey = op.K == 0u ? 0u : op.K - 1u;   // no ties to break: keep key >= K
+      } else {
+        op.mode = 0;
+      }
+    }
+  } else if (uses_lam(form)) {
+    // phi(0) = s ||v||_2^2 - ||v||_1^2 >= 0: the L1 ball is not binding, lambda = 0
+    float f1 = 0.0f, f2 = 0.0f;
+    unsigned mk = 0u;
+    for (int i = sg.lo + lane; i < sg.hi; i += 32) {
+      const float av = fabsf(vv[i]);
+      f1 += av;
+      f2 = fmaf(av, av, f2);
+      mk = max(mk, __float_as_uint(av));
+    }
+    int d0 = 0, d1 = 0;
+    block_sum2f(f1, f2, d0, d1, sh);
+    const uint32_t maxkey = block_max_u(mk, sh.red_u);
+    op.mode = 2;
+    if ((float)a.s * f2 - f1 * f1 < 0.0f) {
+      uint32_t lo;
+      op.gam = lambda_s_bisect(vv, p, a.s, 0u, maxkey, sh, &lo);
+      op.tkey = lo;
+      op.tval = (float)op.gam;
+      op.tnext = op.tval;
+    }
+  } else {  // penalties
+    op.mode = uses_U(form) ? 1 : 2;
+    if (a.calibrate) {
+      const int j = s_int + 1;
+      uint32_t tk = 0u;
+      if (j <= p) {
+        int ne, et;
+        bool whole;
+        radix_select(vv, p, j, true, sh, &tk, &whole, &ne, &et);
+      }
+      op.tkey = tk;
+      op.tval = __uint_as_float(tk);
+      op.gam = uses_U(form) ? (double)op.tval * (double)op.tval : (double)op.tval;
+      op.tnext = op.tval;
+      if (threadIdx.x == 0 && st.thr) st.thr[c] = op.tval;
+    } else if (a.per_start_thr) {
+      op.tval = st.thr[c];
+      op.gam = st.gamma[c];
+      op.tkey = __float_as_uint(op.tval);
+    } else {
+      op.tval = a.thr_fixed;
+      op.gam = a.gamma_fixed;
+      op.tkey = __float_as_uint(op.tval);
+    }
+  }
+  xstep_finish(a, c, vv, p, nullptr, op, x, st, sup_idx, sup_val, ctrl, sh);
+}
+
+// ---------------------------------------------------------------- candidate x-step
+// Near convergence v moves little between sweeps, and every operator keeps only entries above a
+// threshold (the s-th or (s+1)-th largest |v_i|, lambda_s, or the penalty's fixed threshold).
+// One coalesced pass keeps the entries above a guess G -- the fixed threshold itself, or
+// kGuess times last sweep's -- in per-warp lists (index order), zeroes x, and sums |v| and v^2
+// for the lambda test; the operator then runs on the candidates in shared memory.  G is valid
+// when the operator's threshold lies above it: at least s (or s + 1) candidates for the
+// selections, phi(G) < 0 for lambda_s (phi increases through its root); then the candidates
+// hold every surviving entry and the result is the full pass's.  Otherwise, or when a warp's
+// list overflows, the start is left to k_xstep (xfast[c] = 0).
+constexpr int kCandW = 64;               // candidates per warp
+constexpr int kCand = kCandW * XW;       // per start
+constexpr float kGuess = 0.85f;
+
+__global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a, const float *__restrict__ V, int64_t ldv,
+                                                   float *__restrict__ X, int64_t ldx, StartState st,
+                                                   int *__restrict__ sup_idx, float *__restrict__ sup_val,
+                                                   Ctrl *ctrl) {
+  __shared__ XShared sh;
+  __shared__ float wval_s[kCand];
+  __shared__ int widx_s[kCand];
+  __shared__ float cval[kCand];
+  __shared__ int cidx[kCand];
+  __shared__ int fail_s;
+  const int c = blockIdx.x;
+  if (st.status[c] != ST_ACTIVE) return;
+  const int p = a.p, form = a.form;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int s_int = (int)a.s;
+
+  // ---- the guess (uniform over the CTA)
+  bool exact = false;   // G is the threshold itself (penalty forms after calibration / fixed)
+  float G = 0.0f;
+  if (is_pen(form) && !a.calibrate) {
+    exact = true;
+    G = a.per_start_thr ? st.thr[c] : a.thr_fixed;
+  } else {
+    G = kGuess * st.tprev[c];
+  }
+  const int need = uses_T(form) ? s_int : (is_pen(form) && a.calibrate ? s_int + 1 : 1);
+  if ((!exact && !(G > 0.0f)) || need > p || (uses_T(form) && s_int >= p)) {
+    if (threadIdx.x == 0) st.xfast[c] = 0;
+    return;
+  }
+  const uint32_t Gk = __float_as_uint(G);
+
+  // ---- one pass: candidates (key > Gk) into this warp's list, x = 0, sums for lambda_s
+  const float *vg = V + (int64_t)c * ldv;
+  float *x = X + (int64_t)c * ldx;
+  const int seg = ((p + XW - 1) / XW + 127) / 128 * 128;
+  const int lo = min(p, w * seg), hi = min(p, lo + seg);
+  float *wv = wval_s + w * kCandW;
+  int *wi = widx_s + w * kCandW;
+  int wc = 0;
+  bool over = false;
+  float f1 = 0.0f, f2 = 0.0f;
+  for (int base = lo; base < hi && !over; base += 128) {
+    const int i0 = base + 4 * lane;
+    float e[4];
+    if (i0 + 3 < hi) {
+      const float4 t = *reinterpret_cast<const float4 *>(vg + i0);
+      e[0] = t.x; e[1] = t.y; e[2] = t.z; e[3] = t.w;
+      *reinterpret_cast<float4 *>(x + i0) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        e[q] = (i0 + q < hi) ? vg[i0 + q] : 0.0f;
+        if (i0 + q < hi) x[i0 + q] = 0.0f;
+      }
+    }
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float av = fabsf(e[q]);
+      cnt += (i0 + q < hi && __float_as_uint(av) > Gk) ? 1 : 0;
+      f1 += av;
+      f2 = fmaf(av, av, f2);
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    if (wc + tot > kCandW) {
+      over = true;
+    } else {
+      int q2 = wc + incl - cnt;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (i0 + q < hi && abs_key(e[q]) > Gk) {
+          wv[q2] = e[q];
+          wi[q2] = i0 + q;
+          ++q2;
+        }
+      }
+      wc += tot;
+    }
+  }
+  if (threadIdx.x == 0) fail_s = 0;
+  __syncthreads();
+  if (lane == 0 && over) fail_s = 1;
+  int d0 = 0, d1 = 0;
+  block_sum2f(f1, f2, d0, d1, sh);   // (its barriers also publish fail_s)
+  if (fail_s) {
+    if (threadIdx.x == 0) st.xfast[c] = 0;
+    return;
+  }
+  // ---- the warp lists, concatenated in warp order, are the candidates in index order
+  const int ncand = warp_offsets(lane == 0 ? wc : 0, sh);
+  {
+    const int off = sh.woff[w];
+    for (int t = lane; t < wc; t += 32) {
+      cval[off + t] = wv[t];
+      cidx[off + t] = wi[t];
+    }
+  }
+  __syncthreads();
+
+  // ---- the operator on the candidates, with the check that G lies below its threshold
+  XOp op;
+  bool ok = ncand >= need;
+  if (ok && uses_T(form)) {
+    bool whole;
+    int eq_total;
+    radix_select(cval, ncand, s_int, false, sh, &op.K, &whole, &op.need_eq, &eq_total);
+    op.tnext = __uint_as_float(op.K);
+    op.mode = 1;
+    if (whole) {
+      op.tkey = op.K == 0u ? 0u : op.K - 1u;
+    } else if (op.K == 0u || op.need_eq >= eq_total) {
+      op.tkey = op.K == 0u ? 0u : op.K - 1u;
+    } else {
+      op.mode = 0;
+    }
+  } else if (ok && uses_lam(form)) {
+    // lambda = 0 (phi(0) >= 0) keeps every entry: left to the full pass
+    ok = (float)a.s * f2 - f1 * f1 < 0.0f;
+    if (ok) {
+      float sw = 0.0f, sw2 = 0.0f;
+      unsigned mk = 0u;
+      const Seg sgc = warp_seg(ncand);
+      for (int i = sgc.lo + lane; i < sgc.hi; i += 32) {
+        const float av = fabsf(cval[i]);
+        const float wv2 = av - G;
+        sw += wv2;
+        sw2 = fmaf(wv2, wv2, sw2);
+        mk = max(mk, __float_as_uint(av));
+      }
+      int e0 = 0, e1 = 0;
+      block_sum2f(sw, sw2, e0, e1, sh);
+      const uint32_t maxkey = block_max_u(mk, sh.red_u);
+      ok = (float)a.s * sw2 - sw * sw < 0.0f;   // phi(G) < 0: lambda_s > G
+      if (ok) {
+        uint32_t lok;
+        op.mode = 2;
+        op.gam = lambda_s_bisect(cval, ncand, a.s, Gk, maxkey, sh, &lok);
+        op.tkey = lok;
+        op.tval = (float)op.gam;
+        op.tnext = op.tval;
+      }
+    }
+  } else if (ok) {  // penalties
+    op.mode = uses_U(form) ? 1 : 2;
+    if (a.calibrate) {
+      uint32_t tk;
+      int ne, et;
+      bool whole;
+      radix_select(cval, ncand, s_int + 1, true, sh, &tk, &whole, &ne, &et);
+      op.tkey = tk;
+      op.tval = __uint_as_float(tk);
+      op.gam = uses_U(form) ? (double)op.tval * (double)op.tval : (double)op.tval;
+      op.tnext = op.tval;
+      if (threadIdx.x == 0) st.thr[c] = op.tval;
+    } else if (a.per_start_thr) {
+      op.tval = st.thr[c];
+      op.gam = st.gamma[c];
+      op.tkey = __float_as_uint(op.tval);
+      op.tnext = st.tprev[c];
+    } else {
+      op.tval = a.thr_fixed;
+      op.gam = a.gamma_fixed;
+      op.tkey = __float_as_uint(op.tval);
+      op.tnext = st.tprev[c];
+    }
+  }
+  if (!ok) {   // uniform: every input of ok is a block-wide value
+    if (threadIdx.x == 0) st.xfast[c] = 0;
+    return;
+  }
+  xstep_finish(a, c, cval, ncand, cidx, op, x, st, sup_idx, sup_val, ctrl, sh);
+  if (threadIdx.x == 0) st.xfast[c] = 1;
+}
 }  // namespace
 
 cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,
                          StartState s, int *sup_idx, float *sup_val, Ctrl *ctrl_next,
                          cudaStream_t st) {
+  // the candidate kernel needs the per-start thresholds of the last sweep and 16-byte rows
+  const bool cand = s.status && s.tprev && s.xfast && s.thr && ldv % 4 == 0 && ldx % 4 == 0 &&
+                    (reinterpret_cast<uintptr_t>(V) & 15u) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
+  if (cand) {
+    k_xstep_cand<<<r, XT, 0, st>>>(a, V, ldv, X, ldx, s, sup_idx, sup_val, ctrl_next);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  } else {
+    s.xfast = nullptr;
+  }
   const size_t bytes = (size_t)a.p * sizeof(float);
   if (bytes <= (size_t)XSTEP_SMEM_MAX) {
     static bool configured = false;

@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(256) k_start_init(const float *__restrict__ x0
     s.F_prev[c] = 0.0;
     s.gamma[c] = gamma0;
     s.thr[c] = 0.0f;
+    if (s.tprev) s.tprev[c] = 0.0f;
   }
 }
 
@@ -205,11 +206,13 @@ cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, fl
 
 // ------------------------------------------------------------------ active-start list
 // one CTA: ordered compaction of the flags status[c] == ST_ACTIVE over r starts
-__global__ void __launch_bounds__(1024) k_active_list(const int *__restrict__ status, int r,
-                                                      int *__restrict__ act, int *__restrict__ rank,
+__global__ void __launch_bounds__(1024) k_active_list(const int *__restrict__ status, const int *__restrict__ nnz,
+                                                      int r, int *__restrict__ act, int *__restrict__ rank,
                                                       Ctrl *__restrict__ ctrl) {
   __shared__ int red[32];
+  __shared__ long long red_l[32];
   int base_pos = 0;
+  long long nz = 0;
   for (int base = 0; base < r; base += blockDim.x) {
     const int c = base + threadIdx.x;
     const bool on = c < r && status[c] == ST_ACTIVE;
@@ -218,17 +221,26 @@ __global__ void __launch_bounds__(1024) k_active_list(const int *__restrict__ st
     if (on) {
       act[pos] = c;
       rank[c] = pos;
+      if (nnz) nz += nnz[c];
     }
     base_pos += tot;
   }
+  // sum of the active support sizes (a bound on the size of their union)
+  for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(0xffffffffu, nz, o);
+  if ((threadIdx.x & 31) == 0) red_l[threadIdx.x >> 5] = nz;
+  __syncthreads();
   if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red_l[k];
     ctrl->active = base_pos;
     ctrl->use_gather = (ctrl->need_dense == 0 && base_pos > 0) ? 1 : 0;
+    ctrl->sum_nnz = (int)(t < 0x7fffffffLL ? t : 0x7fffffffLL);
   }
 }
 
-cudaError_t launch_active_list(const int *status, int r, int *act, int *rank, Ctrl *c, cudaStream_t st) {
-  k_active_list<<<1, 1024, 0, st>>>(status, r, act, rank, c);
+cudaError_t launch_active_list(const int *status, const int *nnz, int r, int *act, int *rank, Ctrl *c,
+                               cudaStream_t st) {
+  k_active_list<<<1, 1024, 0, st>>>(status, nnz, r, act, rank, c);
   return cudaGetLastError();
 }
 
@@ -321,10 +333,19 @@ __global__ void __launch_bounds__(256) k_gemm1_sparse(const float *__restrict__ 
   __shared__ int sidx[256];
   __shared__ float sval[256];
   const int nnz = s.nnz[c];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // four consecutive rows per thread, read as one 16-byte vector (ldat is a multiple of 8, so
+  // the rows up to the padded width are in bounds); eight columns' loads are issued before
+  // their FMAs, which still run in support order
+  const int i4 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
   const int *gi = sup_idx + (int64_t)c * cap;
   const float *gv = sup_val + (int64_t)c * cap;
-  float acc = 0.0f;
+  float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  auto step = [&](float xv, float4 a) {
+    acc.x = fmaf(xv, a.x, acc.x);
+    acc.y = fmaf(xv, a.y, acc.y);
+    acc.z = fmaf(xv, a.z, acc.z);
+    acc.w = fmaf(xv, a.w, acc.w);
+  };
   for (int t0 = 0; t0 < nnz; t0 += 256) {
     __syncthreads();
     if (t0 + (int)threadIdx.x < nnz) {
@@ -333,16 +354,31 @@ __global__ void __launch_bounds__(256) k_gemm1_sparse(const float *__restrict__ 
     }
     __syncthreads();
     const int m = min(256, nnz - t0);
-    if (i < n)
-      for (int t = 0; t < m; ++t) acc = fmaf(sval[t], AT[(int64_t)sidx[t] * ldat + i], acc);
+    if (i4 < n) {
+      const float *base = AT + i4;
+      int t = 0;
+      for (; t + 8 <= m; t += 8) {
+        float4 a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = __ldg(reinterpret_cast<const float4 *>(base + (int64_t)sidx[t + q] * ldat));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) step(sval[t + q], a[q]);
+      }
+      for (; t < m; ++t) step(sval[t], __ldg(reinterpret_cast<const float4 *>(base + (int64_t)sidx[t] * ldat)));
+    }
   }
-  if (i < n) U[(int64_t)c * ldu + i] = acc;
+  float *u = U + (int64_t)c * ldu;
+  if (i4 < n) u[i4] = acc.x;
+  if (i4 + 1 < n) u[i4 + 1] = acc.y;
+  if (i4 + 2 < n) u[i4 + 2] = acc.z;
+  if (i4 + 3 < n) u[i4 + 3] = acc.w;
 }
 
 cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int *sup_idx,
                                 const float *sup_val, int cap, StartState s, int r, float *U,
                                 int64_t ldu, const int *gate, cudaStream_t st) {
-  dim3 grid((unsigned)((n + 255) / 256), (unsigned)r);
+  if (ldat % 4 != 0 || (reinterpret_cast<uintptr_t>(AT) & 15u) != 0) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((n + 1023) / 1024), (unsigned)r);
   k_gemm1_sparse<<<grid, 256, 0, st>>>(AT, ldat, n, sup_idx, sup_val, cap, s, U, ldu, gate);
   return cudaGetLastError();
 }

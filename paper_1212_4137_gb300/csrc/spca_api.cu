@@ -39,7 +39,8 @@ struct spca_handle {
   CUtensorMap tmXS3{};
   int *status = nullptr, *iters = nullptr, *nnz = nullptr;
   double *F = nullptr, *F_prev = nullptr, *gamma = nullptr, *f = nullptr, *ev = nullptr;
-  float *thr = nullptr;
+  float *thr = nullptr, *tprev = nullptr;
+  int *xfast = nullptr;
   double *partials = nullptr;
   Ctrl *ctrl = nullptr;       // device, 2 entries
   int *best = nullptr;
@@ -51,7 +52,7 @@ struct spca_handle {
   int *h_flag = nullptr;      // pinned host mirror (2 ints)
 
   // measurement hooks: launch counts, and event pairs per kernel id while profiling is on
-  bool prof_on = false;
+  unsigned prof_mask = 0u;   // bit k: kernel id k is timed
   int64_t launches[SPCA_K_COUNT] = {0};
   double ms[SPCA_K_COUNT] = {0};
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[SPCA_K_COUNT];
@@ -96,7 +97,7 @@ cudaEvent_t get_event(spca_handle *h) {
 template <typename Fn>
 cudaError_t timed(spca_handle *h, int kid, int nk, Fn &&launch) {
   h->launches[kid] += nk;
-  if (!h->prof_on) return launch();
+  if (!(h->prof_mask & (1u << kid))) return launch();
   cudaEvent_t a = get_event(h), b = get_event(h);
   cudaEventRecord(a, h->stream);
   cudaError_t e = launch();
@@ -128,7 +129,7 @@ cudaError_t dalloc(T **p, size_t count, size_t elem = sizeof(T)) {
 
 void free_workspace(spca_handle *h) {
   void *ptrs[] = {h->X, h->V, h->U, h->Y, h->Xpl, h->Ypl, h->sup_idx, h->sup_val, h->act, h->rank,
-                  h->status, h->iters, h->nnz, h->F, h->F_prev, h->gamma, h->f, h->ev, h->thr,
+                  h->status, h->iters, h->nnz, h->F, h->F_prev, h->gamma, h->f, h->ev, h->thr, h->tprev, h->xfast,
                   h->partials, h->ctrl, h->best, h->y_out, h->x_out, h->support_out, h->nnz_out,
                   h->mark, h->colpos, h->collist, h->AS, h->XS};
   for (void *q : ptrs)
@@ -141,10 +142,14 @@ void free_workspace(spca_handle *h) {
   h->act = h->rank = nullptr;
   h->status = h->iters = h->nnz = nullptr;
   h->F = h->F_prev = h->gamma = h->f = h->ev = nullptr;
-  h->thr = nullptr; h->partials = nullptr; h->ctrl = nullptr; h->best = nullptr;
+  h->thr = h->tprev = nullptr; h->xfast = nullptr; h->partials = nullptr; h->ctrl = nullptr; h->best = nullptr;
   h->y_out = h->x_out = nullptr; h->support_out = h->nnz_out = nullptr;
   h->r_cap = 0;
 }
+
+// the union of the active supports is tried while the sum of their sizes is at most this many
+// times the union capacity (overlapping supports can still fit)
+constexpr int kUnionTry = 16;
 
 int ensure_workspace(spca_handle *h, int r) {
   if (r <= h->r_cap) return SPCA_OK;
@@ -163,6 +168,7 @@ int ensure_workspace(spca_handle *h, int r) {
   CK(dalloc(&h->status, r)); CK(dalloc(&h->iters, r)); CK(dalloc(&h->nnz, r));
   CK(dalloc(&h->F, r)); CK(dalloc(&h->F_prev, r)); CK(dalloc(&h->gamma, r));
   CK(dalloc(&h->f, r)); CK(dalloc(&h->ev, r)); CK(dalloc(&h->thr, r));
+  CK(dalloc(&h->tprev, r)); CK(dalloc(&h->xfast, r));
   CK(dalloc(&h->partials, (size_t)r * nchunks * 2));
   CK(dalloc(&h->ctrl, 2)); CK(dalloc(&h->best, 1));
   CK(dalloc(&h->y_out, (size_t)h->ldU)); CK(dalloc(&h->x_out, (size_t)h->ldX));
@@ -196,6 +202,7 @@ StartState state_of(spca_handle *h) {
   s.status = h->status; s.iters = h->iters; s.nnz = h->nnz;
   s.F = h->F; s.F_prev = h->F_prev; s.gamma = h->gamma; s.thr = h->thr;
   s.f = h->f; s.ev = h->ev;
+  s.tprev = h->tprev; s.xfast = h->xfast;
   return s;
 }
 
@@ -345,14 +352,14 @@ const char *spca_strerror(int status) {
 
 const char *spca_last_error(const spca_handle *h) { return h ? h->last_error : ""; }
 
-int spca_profile_enable(spca_handle *h, int on) {
-  if (!h) return SPCA_E_INVALID;
+int spca_profile_enable(spca_handle *h, int mask) {
+  if (!h || mask < 0 || mask > SPCA_PROFILE_ALL) return SPCA_E_INVALID;
   CK(drain_profile(h));
   for (int k = 0; k < SPCA_K_COUNT; ++k) {
     h->launches[k] = 0;
     h->ms[k] = 0.0;
   }
-  h->prof_on = on != 0;
+  h->prof_mask = (unsigned)mask;
   return SPCA_OK;
 }
 
@@ -499,7 +506,7 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
   CK(cudaMemsetAsync(h->status, 0xFF, (size_t)r * sizeof(int), st));   // every row active (-1)
   CK(cudaMemsetAsync(h->iters, 0, (size_t)r * sizeof(int), st));
   CK(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), st));
-  CK(launch_active_list(h->status, r, h->act, h->rank, &h->ctrl[0], st));
+  CK(launch_active_list(h->status, nullptr, r, h->act, h->rank, &h->ctrl[0], st));
   RC(sweep_u_dense(h, eng, r, nullptr, &h->ctrl[0].active, r));
   RC(sweep_y_v(h, eng, form, r, state_of(h), &h->ctrl[0].active, r));
   CK(cudaMemcpy2DAsync(U, ldu * sizeof(float), h->U, h->ldU * sizeof(float), (size_t)n * sizeof(float), r,
@@ -545,7 +552,8 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   h->h_ctrl[0].active = r;
   h->h_ctrl[0].need_dense = 1;      // x^(0) is dense: the first sweep's u = A x is the dense one
   CK(cudaMemcpyAsync(h->ctrl, h->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
-  CK(timed(h, SPCA_K_XSTEP, 1, [&] { return launch_active_list(h->status, r, h->act, h->rank, &h->ctrl[0], st); }));
+  CK(timed(h, SPCA_K_XSTEP, 1,
+           [&] { return launch_active_list(h->status, nullptr, r, h->act, h->rank, &h->ctrl[0], st); }));
   CK(cudaMemcpyAsync(h->h_ctrl + 1, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));  // h_ctrl is reused below
   int nhost = h->h_ctrl[1].active;  // active starts as the host knows them (sizes the launches)
@@ -562,12 +570,16 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   // the host queues this many sweeps before it reads the active count back; every path decision
   // inside a sweep is taken on the device from the control word
   const int check_every = 4;
+  // the union of the active supports is built only while the sum of their sizes (read back
+  // with the active count; dense before the first read) could let it fit the union operands
+  int64_t sum_nnz = (int64_t)nhost * p;
+  bool union_built = false;
   for (int k = 1; k <= P.max_iter; ++k) {
     Ctrl *cur = h->ctrl + ((k - 1) & 1), *nxt = h->ctrl + (k & 1);
     // u = A x: over the union of the supports when it is small (tensor cores), else the dense
     // contraction, or the per-start support gather when every support is small
     RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, nhost));
-    if (engine == SPCA_ENGINE_TC) RC(sweep_u_union(h, S, cur, nhost));
+    if (union_built) RC(sweep_u_union(h, S, cur, nhost));
     CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
       return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
                                  &cur->use_gather, st);
@@ -578,12 +590,13 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     xa.calibrate = target && k <= C;
     xa.per_start_thr = target && k > C;
     xa.stop_test = P.tol >= 0.0 && k >= 2 && k >= C + 1;
-    CK(timed(h, SPCA_K_XSTEP, 2, [&] {
+    CK(timed(h, SPCA_K_XSTEP, 3, [&] {   // candidate x-step, full x-step, active list
       cudaError_t e = launch_xstep(xa, h->V, h->ldX, r, h->X, h->ldX, S, h->sup_idx, h->sup_val, nxt, st);
       if (e != cudaSuccess) return e;
-      return launch_active_list(h->status, r, h->act, h->rank, nxt, st);   // for the next sweep
+      return launch_active_list(h->status, h->nnz, r, h->act, h->rank, nxt, st);   // for the next sweep
     }));
-    if (engine == SPCA_ENGINE_TC) {
+    union_built = engine == SPCA_ENGINE_TC && sum_nnz <= (int64_t)kUnionTry * h->kcap;
+    if (union_built) {
       CK(timed(h, SPCA_K_U_SPARSE, 2, [&] {
         return launch_union(h->sup_idx, p, S, r, p, h->mark, h->colpos, h->collist, h->kcap, nxt, st);
       }));
@@ -593,6 +606,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
       CK(cudaStreamSynchronize(st));
       if (h->h_ctrl->active == 0) break;
       nhost = h->h_ctrl->active;   // counts only fall: any earlier value stays an upper bound
+      sum_nnz = h->h_ctrl->sum_nnz;
     }
   }
   RC(read_dev_err(h));

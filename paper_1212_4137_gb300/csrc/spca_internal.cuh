@@ -46,7 +46,8 @@ struct Ctrl {
   int use_gather;  // u by the per-start support gather
   int kunion;      // size of the union of the active starts' supports
   int err;         // kernel-reported error code (0 = none)
-  int pad[2];
+  int sum_nnz;     // sum of the active starts' support sizes (bounds the union; saturates)
+  int pad;
 };
 
 // per-start state of one solve (device arrays, r each)
@@ -60,6 +61,9 @@ struct StartState {
   float *thr;       // the same threshold in |v| units, as a float the kernels compare with
   double *f;        // Table 1 objective (finalise)
   double *ev;       // explained variance (finalise)
+  float *tprev;     // last sweep's x-step threshold in |v| units (0: none); seeds the
+                    // candidate filter of the next x-step
+  int *xfast;       // 1 when the candidate x-step finished the start in this sweep
 };
 
 struct XstepArgs {
@@ -160,7 +164,8 @@ cudaError_t launch_union_operands(const void *ATpl, int64_t ldat, int64_t at_pst
 // ordered list of the active starts (status == ST_ACTIVE): act[k] = c and rank[c] = k for the
 // k-th active start; c->active = the count, c->use_gather = !c->need_dense (the union step,
 // when it runs afterwards, may take the sweep over)
-cudaError_t launch_active_list(const int *status, int r, int *act, int *rank, Ctrl *c, cudaStream_t st);
+cudaError_t launch_active_list(const int *status, const int *nnz, int r, int *act, int *rank, Ctrl *c,
+                               cudaStream_t st);
 
 // x-step (S3..S6), objective F, stopping rule, support lists
 cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,

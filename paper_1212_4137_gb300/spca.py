@@ -153,8 +153,11 @@ def spca_objective_noalloc(form, gamma, A, n, p, lda, X, ldx, r, f, ev, stream=0
                                          ctypes.c_void_p(ev), ctypes.c_void_p(stream))
 
 
-def spca_profile_enable(h, on: bool) -> int:
-    return load().spca_profile_enable(h, int(on))
+SPCA_PROFILE_ALL = (1 << 8) - 1
+
+
+def spca_profile_enable(h, mask: int) -> int:
+    return load().spca_profile_enable(h, int(mask))
 
 
 def spca_profile_query(h, kernel: int):
@@ -195,8 +198,12 @@ class Handle:
         _check(st, "spca_create")
         self.h, self.n, self.p = h, n, p
 
-    def profile(self, on: bool):
-        _check(spca_profile_enable(self.h, on), "spca_profile_enable", self.h)
+    def profile(self, on: bool, kernels=None):
+        """Time every kernel (on=True), only the given kernel ids, or nothing (on=False)."""
+        mask = 0
+        if on:
+            mask = SPCA_PROFILE_ALL if kernels is None else sum(1 << int(k) for k in set(kernels))
+        _check(spca_profile_enable(self.h, mask), "spca_profile_enable", self.h)
 
     def profile_query(self, kernel: int):
         st, n, ms = spca_profile_query(self.h, kernel)

@@ -52,6 +52,28 @@ def test_struct_layout_matches_header(lib):
     assert [f for f, _ in lib.spca_result._fields_] == _struct_fields("spca_result")
 
 
+def _enum_values(names):
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for name in names:
+        m = re.search(r"\b" + name + r"\s*=\s*(-?\d+)", text)
+        out[name] = int(m.group(1))
+    return out
+
+
+def test_constants_match_header(lib):
+    kids = ("SPCA_K_ALL", "SPCA_K_INIT", "SPCA_K_U_DENSE", "SPCA_K_U_SPARSE", "SPCA_K_YSTEP", "SPCA_K_V",
+            "SPCA_K_XSTEP", "SPCA_K_FINALISE", "SPCA_K_PREP", "SPCA_K_COUNT")
+    vals = _enum_values(kids)
+    for name in kids[:-1]:
+        assert getattr(lib, name) == vals[name], name
+    assert lib.SPCA_PROFILE_ALL == (1 << vals["SPCA_K_COUNT"]) - 1
+    text = open(HEADER).read()
+    assert "#define SPCA_PROFILE_ALL ((1 << SPCA_K_COUNT) - 1)" in text
+    m = re.search(r"#define SPCA_NOALLOC_MAX_PARTIALS (\d+)", text)
+    assert m and int(m.group(1)) == 262144
+
+
 def test_strerror_is_static_text(lib):
     assert lib.spca_strerror(0) == "ok"
     assert lib.spca_strerror(1) == "invalid argument"
@@ -70,6 +92,7 @@ def test_bad_arguments_rejected_before_device(lib):
     st = so.spca_create(ctypes.byref(h), ctypes.c_void_p(A.ctypes.data), 2, 3, 3, 0, 0, lib.SPCA_BF16, None)
     assert st == lib.SPCA_E_UNSUPPORTED
     assert so.spca_solve(None, None, None, None) == lib.SPCA_E_INVALID
+    assert so.spca_profile_enable(None, 1) == lib.SPCA_E_INVALID
     so.spca_destroy(None)
 
 
