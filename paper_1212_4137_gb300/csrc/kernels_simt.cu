@@ -211,8 +211,10 @@ __global__ void __launch_bounds__(1024) k_active_list(const int *__restrict__ st
                                                       Ctrl *__restrict__ ctrl) {
   __shared__ int red[32];
   __shared__ long long red_l[32];
+  __shared__ int red_m[32];
   int base_pos = 0;
   long long nz = 0;
+  int mz = 0;
   for (int base = 0; base < r; base += blockDim.x) {
     const int c = base + threadIdx.x;
     const bool on = c < r && status[c] == ST_ACTIVE;
@@ -221,17 +223,31 @@ __global__ void __launch_bounds__(1024) k_active_list(const int *__restrict__ st
     if (on) {
       act[pos] = c;
       rank[c] = pos;
-      if (nnz) nz += nnz[c];
+      if (nnz) {
+        nz += nnz[c];
+        mz = max(mz, nnz[c]);
+      }
     }
     base_pos += tot;
   }
   // sum of the active support sizes (a bound on the size of their union)
-  for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(0xffffffffu, nz, o);
-  if ((threadIdx.x & 31) == 0) red_l[threadIdx.x >> 5] = nz;
+  for (int o = 16; o > 0; o >>= 1) {
+    nz += __shfl_xor_sync(0xffffffffu, nz, o);
+    mz = max(mz, __shfl_xor_sync(0xffffffffu, mz, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_l[threadIdx.x >> 5] = nz;
+    red_m[threadIdx.x >> 5] = mz;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     long long t = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red_l[k];
+    int m = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      t += red_l[k];
+      m = max(m, red_m[k]);
+    }
+    ctrl->max_nnz = m;
     ctrl->active = base_pos;
     ctrl->use_gather = (ctrl->need_dense == 0 && base_pos > 0) ? 1 : 0;
     ctrl->sum_nnz = (int)(t < 0x7fffffffLL ? t : 0x7fffffffLL);

@@ -574,11 +574,18 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   // with the active count; dense before the first read) could let it fit the union operands
   int64_t sum_nnz = (int64_t)nhost * p;
   bool union_built = false;
+  // the dense u = A x is a faster path for large supports, never a required one (the gather
+  // takes any support): the host queues it only while some active support may come near
+  // sparse_cap (T_s keeps at most s entries; otherwise read back with the active count), and the
+  // x-step of the sweep before requests it only then
+  const int sparse_cap = xa.sparse_cap;
+  int64_t max_nnz = uses_T(form) ? std::min<int64_t>((int64_t)P.s, p) : p;
+  bool dense_queued = true;   // x^(0) is dense
   for (int k = 1; k <= P.max_iter; ++k) {
     Ctrl *cur = h->ctrl + ((k - 1) & 1), *nxt = h->ctrl + (k & 1);
     // u = A x: over the union of the supports when it is small (tensor cores), else the dense
     // contraction, or the per-start support gather when every support is small
-    RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, nhost));
+    if (dense_queued) RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, nhost));
     if (union_built) RC(sweep_u_union(h, S, cur, nhost));
     CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
       return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
@@ -590,6 +597,8 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     xa.calibrate = target && k <= C;
     xa.per_start_thr = target && k > C;
     xa.stop_test = P.tol >= 0.0 && k >= 2 && k >= C + 1;
+    dense_queued = max_nnz > sparse_cap / 2;
+    xa.sparse_cap = dense_queued ? sparse_cap : p;   // p: the gather for every support
     CK(timed(h, SPCA_K_XSTEP, 3, [&] {   // candidate x-step, full x-step, active list
       cudaError_t e = launch_xstep(xa, h->V, h->ldX, r, h->X, h->ldX, S, h->sup_idx, h->sup_val, nxt, st);
       if (e != cudaSuccess) return e;
@@ -607,6 +616,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
       if (h->h_ctrl->active == 0) break;
       nhost = h->h_ctrl->active;   // counts only fall: any earlier value stays an upper bound
       sum_nnz = h->h_ctrl->sum_nnz;
+      max_nnz = h->h_ctrl->max_nnz;
     }
   }
   RC(read_dev_err(h));

@@ -47,7 +47,7 @@ struct Ctrl {
   int kunion;      // size of the union of the active starts' supports
   int err;         // kernel-reported error code (0 = none)
   int sum_nnz;     // sum of the active starts' support sizes (bounds the union; saturates)
-  int pad;
+  int max_nnz;     // largest active support
 };
 
 // per-start state of one solve (device arrays, r each)
