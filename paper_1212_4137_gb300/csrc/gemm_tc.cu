@@ -300,13 +300,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------- CTA-pair variant
-// A cluster of two CTAs along M computes a 256 x BN tile with tcgen05 .cta_group::2: each CTA
-// loads its own 128 rows of the P planes and its half (BN/2 rows) of the Q planes to the same
-// shared-memory offsets; the leader (cluster rank 0) issues the MMAs with M = 256, which read
-// both CTAs' shared memory, and each CTA's TMEM receives its own 128 rows of D.  The peer's
-// loads complete on the leader's full barrier; the leader's commits free the stage and signal
-// the accumulator in both CTAs.  Per SM this doubles the MMA work per loaded byte of Q and per
-// pipeline stage compared with the single-CTA tile.
+// A cluster of two CTAs computes 256 x BN tiles with tcgen05 .cta_group::2: each CTA loads its
+// own 128 rows of the P planes and its half (BN/2 rows) of the Q planes to the same shared-memory
+// offsets; the leader (cluster rank 0) issues the MMAs with M = 256, which read both CTAs' shared
+// memory, and each CTA's TMEM receives its own 128 rows of D.  The peer's loads complete on the
+// leader's full barrier; the leader's commits free the stage and signal the accumulator in both
+// CTAs.  Per SM this doubles the MMA work per loaded byte of Q and per pipeline stage compared
+// with the single-CTA tile.
+//
+// Persistent stream-K schedule: the grid is S resident pairs ("slots"); the T tiles x KB K-blocks
+// of the product are numbered tile-major (M pair fastest within an N column of tiles, so that
+// slots running at the same time share P rows in L2), and slot j takes the units
+// [j W / S, (j + 1) W / S), W = T KB -- an equal share whatever T is, so no wave runs part-empty.
+// A slot walks its range as segments, one per tile it touches; a segment is a whole tile (its
+// epilogue writes the output), the first K-blocks of a tile (the slot then owns the tile), or a
+// later part of one (the slot's first segment: it writes the partial to its workspace slot and
+// publishes a flag).  An owner's part is the last segment of its range, so by then the later
+// parts, which other slots compute first, are mostly done: it waits for their flags (bounded),
+// adds them in slot order and writes the tile.  The TMEM accumulators are reused from segment to
+// segment: the epilogue of both CTAs releases them before the leader's next MMA.
 __device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
                                                  uint32_t bar_cluster) {
   asm volatile(
@@ -334,13 +346,32 @@ __device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
   return r;
 }
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// the four epilogue warps (128 threads) only
+__device__ __forceinline__ void epilogue_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+struct SkRange {   // slot j's share of the W units: [u0, u1)
+  long long W;
+  int S;
+  __device__ long long start(int j) const { return (long long)j * W / S; }
+};
 
 template <int BN, int NA, int NB, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc2(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int M, int N,
-               int ntn, int kblocks, const int *__restrict__ k_dev, TcPairs pairs, float *__restrict__ out,
-               int64_t ldo, const int *__restrict__ gate, const int *__restrict__ n_dev,
-               const int *__restrict__ col_map, int *err) {
+               int kblocks, const int *__restrict__ k_dev, TcPairs pairs, float *__restrict__ out, int64_t ldo,
+               const int *__restrict__ gate, const int *__restrict__ n_dev, const int *__restrict__ col_map,
+               int *err, float *__restrict__ ws, int *__restrict__ flags, int epoch) {
   constexpr int BK = 64;
   constexpr uint32_t A_BYTES = TC_BM * BK * 2;          // this CTA's 128 rows of one P plane
   constexpr uint32_t B_BYTES = (BN / 2) * BK * 2;       // this CTA's half of one Q plane
@@ -348,24 +379,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr uint32_t TMEM_COLS = 2 * BN;
 
   extern __shared__ __align__(1024) uint8_t dsmem[];
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar;
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar, tmem_empty_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
-  // a 1-D grid of pairs (cluster dims 2 x 1 x 1), N tiles fastest: consecutive pairs share the
-  // P rows and so read them from L2
-  const uint32_t rank = cluster_rank();   // 0: leader (even M tile), 1: peer
-  const int pair_id = (int)(blockIdx.x >> 1);
-  const int tn = pair_id % ntn, tm = 2 * (pair_id / ntn) + (int)rank;
+  const uint32_t rank = cluster_rank();   // 0: leader (even M tile of the pair), 1: peer
+  const int slot = (int)(blockIdx.x >> 1), S = (int)(gridDim.x >> 1);
   if (gate && *gate == 0) return;         // uniform over the grid
   if (n_dev) N = *n_dev;
-  if (k_dev) kblocks = (*k_dev + BK - 1) / BK;
-  if (kblocks <= 0) return;
-  if (tn * BN >= N) return;               // both CTAs of a pair share tn
+  const int KB = k_dev ? (*k_dev + BK - 1) / BK : kblocks;
+  const int pm = ((M + TC_BM - 1) / TC_BM + 1) / 2;   // pairs of 128-row tiles along M
+  const int ntn = (N + BN - 1) / BN;
+  SkRange R{(long long)pm * ntn * (KB > 0 ? KB : 0), S};
+  if (R.W <= 0) return;
+  const long long u0 = R.start(slot), u1 = R.start(slot + 1);
+  if (u0 >= u1) return;                   // an empty share (uniform over the pair)
 
   uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = tm * TC_BM, n0 = tn * BN;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -373,6 +404,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     mbar_init(smem_u32(&accum_bar), 1);
+    mbar_init(smem_u32(&tmem_empty_bar), 8);   // 4 epilogue warps in each CTA of the pair
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -389,55 +421,115 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
+  // segment iteration shared by the three roles: tile t, K-blocks [kb0, kb1)
+  auto next_seg = [&](long long &u, long long &t, int &kb0, int &kb1) {
+    t = u / KB;
+    kb0 = (int)(u - t * KB);
+    const long long e = (t + 1) * KB < u1 ? (t + 1) * KB : u1;
+    kb1 = (int)(e - t * KB);
+    u = e;
+  };
+
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------------- TMA producer (both CTAs)
-    for (int kb = 0; kb < kblocks; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, err, &abort_flag)) break;
-      const uint32_t own = smem_u32(&full_bar[s]);
-      const uint32_t fb = rank == 0 ? own : map_to_rank(own, 0);   // the leader's full barrier
-      if (rank == 0) mbar_expect_tx(own, 2 * STAGE_BYTES);         // both CTAs' bytes
-      uint8_t *st = tiles + (size_t)s * STAGE_BYTES;
+    uint32_t it = 0;
+    bool ok = true;
+    for (long long u = u0; u < u1 && ok;) {
+      long long t;
+      int kb0, kb1;
+      next_seg(u, t, kb0, kb1);
+      const int m0 = (2 * (int)(t % pm) + (int)rank) * TC_BM, n0 = (int)(t / pm) * BN;
+      for (int kb = kb0; kb < kb1; ++kb, ++it) {
+        const int s = (int)(it % STAGES);
+        const uint32_t ph = (it / STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, err, &abort_flag)) { ok = false; break; }
+        const uint32_t own = smem_u32(&full_bar[s]);
+        const uint32_t fb = rank == 0 ? own : map_to_rank(own, 0);   // the leader's full barrier
+        if (rank == 0) mbar_expect_tx(own, 2 * STAGE_BYTES);         // both CTAs' bytes
+        uint8_t *st = tiles + (size_t)s * STAGE_BYTES;
 #pragma unroll
-      for (int a = 0; a < NA; ++a) tma_load_3d_pair(smem_u32(st + a * A_BYTES), &tmP, kb * BK, m0, a, fb);
+        for (int a = 0; a < NA; ++a) tma_load_3d_pair(smem_u32(st + a * A_BYTES), &tmP, kb * BK, m0, a, fb);
 #pragma unroll
-      for (int b = 0; b < NB; ++b)
-        tma_load_3d_pair(smem_u32(st + NA * A_BYTES + b * B_BYTES), &tmQ, kb * BK, n0 + (int)rank * (BN / 2), b,
-                         fb);
+        for (int b = 0; b < NB; ++b)
+          tma_load_3d_pair(smem_u32(st + NA * A_BYTES + b * B_BYTES), &tmQ, kb * BK, n0 + (int)rank * (BN / 2), b,
+                           fb);
+      }
     }
   } else if (warp == 1 && lane == 0 && rank == 0) {
     // ---------------------------------------------------------------- MMA issuer (leader)
     constexpr uint32_t idesc = idesc_bf16(2 * TC_BM, BN);
+    uint32_t it = 0, seg = 0;
     bool ok = true;
-    for (int kb = 0; kb < kblocks && ok; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!mbar_wait(smem_u32(&full_bar[s]), ph, err, &abort_flag)) { ok = false; break; }
+    for (long long u = u0; u < u1 && ok; ++seg) {
+      long long t;
+      int kb0, kb1;
+      next_seg(u, t, kb0, kb1);
+      // the epilogues of both CTAs have read the previous segment's accumulators
+      if (seg > 0 && !mbar_wait(smem_u32(&tmem_empty_bar), (seg - 1) & 1u, err, &abort_flag)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = smem_u32(tiles + (size_t)s * STAGE_BYTES);
-      for (int q = 0; q < pairs.n; ++q) {
-        const uint32_t a_base = st + pairs.a[q] * A_BYTES;
-        const uint32_t b_base = st + NA * A_BYTES + pairs.b[q] * B_BYTES;
-        const bool main = (pairs.a[q] | pairs.b[q]) == 0;
-        const uint32_t d = tmem + (main ? 0u : (uint32_t)BN);
-        const bool first = kb == 0 && q == (main ? pairs.first_main : pairs.first_corr);
+      for (int kb = kb0; kb < kb1; ++kb, ++it) {
+        const int s = (int)(it % STAGES);
+        const uint32_t ph = (it / STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&full_bar[s]), ph, err, &abort_flag)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = smem_u32(tiles + (size_t)s * STAGE_BYTES);
+        for (int q = 0; q < pairs.n; ++q) {
+          const uint32_t a_base = st + pairs.a[q] * A_BYTES;
+          const uint32_t b_base = st + NA * A_BYTES + pairs.b[q] * B_BYTES;
+          const bool main = (pairs.a[q] | pairs.b[q]) == 0;
+          const uint32_t d = tmem + (main ? 0u : (uint32_t)BN);
+          const bool first = kb == kb0 && q == (main ? pairs.first_main : pairs.first_corr);
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          mma_bf16_pair(d, sw_desc<BK>(a_base + kk * 32), sw_desc<BK>(b_base + kk * 32), idesc,
-                        (first && kk == 0) ? 0u : 1u);
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            mma_bf16_pair(d, sw_desc<BK>(a_base + kk * 32), sw_desc<BK>(b_base + kk * 32), idesc,
+                          (first && kk == 0) ? 0u : 1u);
+          }
         }
+        mma_commit_pair(smem_u32(&empty_bar[s]));   // frees stage s in both CTAs
       }
-      mma_commit_pair(smem_u32(&empty_bar[s]));   // frees stage s in both CTAs
+      if (ok) mma_commit_pair(smem_u32(&accum_bar));
     }
-    if (ok) mma_commit_pair(smem_u32(&accum_bar));
   } else if (warp >= 2) {
     // ---------------------------------------------------------------- epilogue (own 128 rows)
     const int quad = warp & 3;
-    const bool ready = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accum_bar), 0, err, &abort_flag));
-    if (ready) {
+    const uint32_t tmem_empty_leader = map_to_rank(smem_u32(&tmem_empty_bar), 0);
+    uint32_t seg = 0;
+    bool ok = true;
+    for (long long u = u0; u < u1 && ok; ++seg) {
+      long long t;
+      int kb0, kb1;
+      next_seg(u, t, kb0, kb1);
+      const bool owner = kb0 == 0 && kb1 < KB, contrib = kb0 > 0;
+      const int m0 = (2 * (int)(t % pm) + (int)rank) * TC_BM, n0 = (int)(t / pm) * BN;
+      ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accum_bar), seg & 1u, err, &abort_flag));
+      if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int row = m0 + quad * 32 + lane;
+      // an owner first waits for the later parts of its tile (slots slot+1, slot+2, ...)
+      int jlast = slot;
+      if (owner) {
+        const long long tend = (t + 1) * KB;
+        while (jlast + 1 < S && R.start(jlast + 1) < tend) ++jlast;
+        if (lane == 0) {
+          for (int j = slot + 1; j <= jlast && ok; ++j) {
+            if (R.start(j) >= R.start(j + 1)) continue;   // empty share: no part
+            const int *fl = flags + (j * 2 + (int)rank);
+            if (ld_acquire(fl) == epoch) continue;
+            const uint64_t t0 = globaltimer();
+            while (ld_acquire(fl) != epoch) {
+              if (abort_flag || globaltimer() - t0 > TC_WAIT_NS) {
+                abort_flag = 1;
+                if (err) atomicExch(err, SPCA_E_TIMEOUT);
+                ok = false;
+                break;
+              }
+            }
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        __syncwarp();
+      }
+      const int row_l = quad * 32 + lane, row = m0 + row_l;
+      float *mine = ws + ((int64_t)slot * 2 + rank) * BN * TC_BM;
 #pragma unroll 1
       for (int cb = 0; cb < BN / 32; ++cb) {
         float v[32], w[32];
@@ -448,12 +540,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += w[j];
         }
-        if (row < M) {
+        if (contrib) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) mine[(int64_t)(cb * 32 + j) * TC_BM + row_l] = v[j];
+          continue;
+        }
+        if (owner && ok) {
+          for (int jj = slot + 1; jj <= jlast; ++jj) {
+            if (R.start(jj) >= R.start(jj + 1)) continue;
+            const float *part = ws + ((int64_t)jj * 2 + rank) * BN * TC_BM;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] += __ldcg(part + (int64_t)(cb * 32 + j) * TC_BM + row_l);
+          }
+        }
+        if (row < M && ok) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int col = n0 + cb * 32 + j;
             if (col < N) out[(int64_t)(col_map ? col_map[col] : col) * ldo + row] = v[j];
           }
+        }
+      }
+      // accumulators read: release them to the leader's next MMA
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(tmem_empty_leader);
+      if (contrib) {
+        // this part of the tile is in the workspace: publish it
+        epilogue_bar();
+        if (warp == 2 && lane == 0) {
+          __threadfence();
+          st_release(flags + (slot * 2 + (int)rank), epoch);
         }
       }
     }
@@ -583,22 +700,12 @@ namespace {
 template <int BN, int NA, int NB, int STAGES>
 cudaError_t launch_tc2_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, int K, const int *k_dev,
                             TcPairs pairs, float *out, int64_t ldo, const int *gate, const int *n_dev,
-                            const int *col_map, int *err, cudaStream_t st) {
+                            const int *col_map, int *err, const TcStreamK &sk, cudaStream_t st) {
   constexpr int BK = 64;
   constexpr int STAGE_BYTES = NA * TC_BM * BK * 2 + NB * (BN / 2) * BK * 2;
   constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
   auto kern = k_gemm_tc2<BN, NA, NB, STAGES>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  const int ntm = (M + TC_BM - 1) / TC_BM, ntn = (N + BN - 1) / BN;
-  dim3 grid((unsigned)(2 * ((ntm + 1) / 2) * ntn), 1);
-  const int kblocks = (K + BK - 1) / BK;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
   cfg.blockDim = dim3(TC_THREADS);
   cfg.dynamicSmemBytes = SMEM;
   cfg.stream = st;
@@ -609,8 +716,28 @@ cudaError_t launch_tc2_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, P.m[0], Q, M, N, ntn, kblocks, k_dev, pairs, out, ldo, gate, n_dev,
-                            col_map, err);
+  // the slots must all be resident at once (owners wait for other slots' parts): as many pairs
+  // as the device holds together, measured once per configuration
+  static int max_pairs = 0;
+  if (max_pairs == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3(2 * 64, 1);
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    max_pairs = n;
+  }
+  const int pm = ((M + TC_BM - 1) / TC_BM + 1) / 2, ntn = (N + BN - 1) / BN;
+  const int kblocks = (K + BK - 1) / BK;
+  const long long units = (long long)pm * ntn * kblocks;
+  int S = max_pairs < sk.slots ? max_pairs : sk.slots;
+  if (units < S) S = (int)(units > 0 ? units : 1);
+  cfg.gridDim = dim3((unsigned)(2 * S), 1);
+  const int epoch = ++(*sk.epoch);
+  return cudaLaunchKernelEx(&cfg, kern, P.m[0], Q, M, N, kblocks, k_dev, pairs, out, ldo, gate, n_dev, col_map,
+                            err, sk.ws, sk.flags, epoch);
 }
 }  // namespace
 
@@ -648,23 +775,27 @@ cudaError_t launch_gemm_tc_single(const PMaps &P, int na, const CUtensorMap &Q, 
 }
 }  // namespace
 
-// CTA pairs (256 x BN tiles) when there are at least two M tiles; one M tile runs on single CTAs
+// CTA pairs (256 x BN tiles, stream-K over the resident pairs) when there are at least two M
+// tiles; one M tile runs on single CTAs
 cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
                            const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const int *gate,
-                           const int *n_dev, const int *col_map, int *err, cudaStream_t st) {
-  if (M <= TC_BM)
+                           const int *n_dev, const int *col_map, int *err, const TcStreamK &sk, cudaStream_t st) {
+  if (M <= TC_BM || !sk.ws || !sk.flags || !sk.epoch || sk.slots < 1)
     return launch_gemm_tc_single(P, na, Q, nb, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
   if (na == 3 && nb == 1)
     return launch_tc2_impl<TC_PAIR_BN, 3, 1, tc_stages(1)>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
-                                                             col_map, err, st);
+                                                             col_map, err, sk, st);
   if (na == 3 && nb == 3)
     return launch_tc2_impl<TC_PAIR_BN, 3, 3, tc_stages(3)>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
-                                                             col_map, err, st);
+                                                             col_map, err, sk, st);
   return cudaErrorInvalidValue;
 }
 
 // Q-operand boxes: BN / 2 rows (half of a pair tile, or a whole single-CTA tile)
 int tc_box_rows(int nb) { (void)nb; return TC_PAIR_BN / 2; }
+
+// workspace of the stream-K schedule: one 256 x BN FP32 part per pair slot
+int64_t tc_sk_floats_per_slot() { return (int64_t)2 * TC_BM * TC_PAIR_BN; }
 int tc_bk(int nb) { (void)nb; return 64; }
 
 }  // namespace spca

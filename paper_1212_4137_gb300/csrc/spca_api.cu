@@ -48,6 +48,9 @@ struct spca_handle {
   int64_t *support_out = nullptr, *nnz_out = nullptr;
   int *flag = nullptr;        // device scratch flag
   int *dev_err = nullptr;     // device error word written by kernels (SPCA_E_TIMEOUT)
+  // stream-K scratch of the CTA-pair contraction (one part per resident pair, flags, epoch)
+  TcStreamK sk;
+  int sk_epoch = 0;
   Ctrl *h_ctrl = nullptr;     // pinned host mirror
   int *h_flag = nullptr;      // pinned host mirror (2 ints)
 
@@ -271,7 +274,7 @@ int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int 
                                           gate, nact, h->act, st);
       if (e != cudaSuccess) return e;
       return launch_gemm_tc(h->pmA, 3, h->tmX3, 3, n, nhost, p, nullptr, pairs_general(), h->U, h->ldU, gate, nact,
-                            h->act, h->dev_err, st);
+                            h->act, h->dev_err, h->sk, st);
     }));
   } else {
     CK(timed(h, SPCA_K_U_DENSE, 1, [&] {
@@ -291,7 +294,7 @@ int sweep_u_union(spca_handle *h, StartState S, const Ctrl *c, int nhost) {
                                           h->colpos, h->XS, (int64_t)h->r_cap * h->kcap, c, h->stream);
     if (e != cudaSuccess) return e;
     return launch_gemm_tc(h->pmAS, 3, h->tmXS3, 3, n, nhost, h->kcap, &c->kunion, pairs_general(), h->U, h->ldU,
-                          &c->use_union, &c->active, h->act, h->dev_err, h->stream);
+                          &c->use_union, &c->active, h->act, h->dev_err, h->sk, h->stream);
   }));
   return SPCA_OK;
 }
@@ -311,7 +314,7 @@ int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const i
     CK(timed(h, SPCA_K_V, 1, [&] {
       return launch_gemm_tc(h->pmAT, 3, l1 ? h->tmY1 : h->tmY3, l1 ? 1 : 3, p, nhost, n, nullptr,
                             l1 ? pairs_sign() : pairs_general(), h->V, h->ldX, nullptr, nact, h->act,
-                            h->dev_err, st);
+                            h->dev_err, h->sk, st);
     }));
   } else {
     CK(timed(h, SPCA_K_V, 1, [&] {
@@ -385,7 +388,7 @@ void spca_destroy(spca_handle *h) {
   drain_profile(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   free_workspace(h);
-  void *ptrs[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->flag, h->dev_err};
+  void *ptrs[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->flag, h->dev_err, h->sk.ws, h->sk.flags};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
@@ -457,6 +460,13 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
       }));
       CK(make_p_maps(&h->pmA, h->Apl, n, h->ldA, 3));
       CK(make_p_maps(&h->pmAT, h->ATpl, p, h->ldAT, 3));
+      int sms = 0;
+      CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      h->sk.slots = sms / 2 > 0 ? sms / 2 : 1;
+      CK(dalloc(&h->sk.ws, (size_t)h->sk.slots * tc_sk_floats_per_slot()));
+      CK(dalloc(&h->sk.flags, (size_t)2 * h->sk.slots));
+      CK(cudaMemsetAsync(h->sk.flags, 0, (size_t)2 * h->sk.slots * sizeof(int), h->stream));
+      h->sk.epoch = &h->sk_epoch;
     }
     CK(cudaStreamSynchronize(h->stream));
     if (*h->h_flag) return fail(h, SPCA_E_INVALID, "A has a non-finite entry%s");

@@ -139,9 +139,19 @@ cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld,
 // col_map when given, else the identity.  With gate != nullptr nothing runs unless *gate != 0;
 // a timed-out wait sets *err = SPCA_E_TIMEOUT
 // (K from *k_dev when k_dev != nullptr, K being then only an upper bound)
+// Stream-K scratch of the CTA-pair contraction: `slots` parts of tc_sk_floats_per_slot() floats,
+// 2 flags per slot (zeroed once), and the host-side launch counter the flags are compared with.
+// Without it (ws == nullptr) the single-CTA kernel runs.
+struct TcStreamK {
+  float *ws = nullptr;
+  int *flags = nullptr;
+  int slots = 0;
+  int *epoch = nullptr;
+};
+int64_t tc_sk_floats_per_slot();
 cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
                            const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const int *gate, const int *n_dev,
-                           const int *col_map, int *err, cudaStream_t st);
+                           const int *col_map, int *err, const TcStreamK &sk, cudaStream_t st);
 // BF16 planes of an FP32 matrix (plane t at dst + t * plane_stride elements): destination row r
 // comes from source row row_map[r] (identity when null), r < rows (*rows_dev when given); gated
 cudaError_t launch_split_planes(const float *src, int64_t rows, int64_t cols, int64_t lds, void *dst,

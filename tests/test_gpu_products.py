@@ -10,7 +10,10 @@ from paper_1212_4137_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(7, 9, 3), (300, 1003, 40), (129, 257, 300), (1000, 3000, 257), (2500, 700, 520)]
+# the CTA-pair contraction splits tiles over its resident pairs along K (stream-K): the shapes
+# include tiles cut into 16 one-K-block parts (300 x 1003 x 40) and a single start with a long
+# K (4000 x 300 x 1: each tile in about 38 parts), as well as whole tiles
+SHAPES = [(7, 9, 3), (300, 1003, 40), (129, 257, 300), (1000, 3000, 257), (2500, 700, 520), (4000, 300, 1)]
 
 
 @pytest.fixture(scope="module")
