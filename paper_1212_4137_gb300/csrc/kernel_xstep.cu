@@ -486,8 +486,9 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
 // Near convergence v moves little between sweeps, and every operator keeps only entries above a
 // threshold (the s-th or (s+1)-th largest |v_i|, lambda_s, or the penalty's fixed threshold).
 // One coalesced pass keeps the entries above a guess G -- the fixed threshold itself, or
-// kGuess times last sweep's -- in per-warp lists (index order), zeroes x, and sums |v| and v^2
-// for the lambda test; the operator then runs on the candidates in shared memory.  G is valid
+// kGuess times last sweep's -- in per-warp lists (index order) and sums |v| and v^2 for the
+// lambda test; the operator then runs on the candidates in shared memory, and x (zero outside
+// the last support list) changes only on the old and the new support.  G is valid
 // when the operator's threshold lies above it: at least s (or s + 1) candidates for the
 // selections, phi(G) < 0 for lambda_s (phi increases through its root); then the candidates
 // hold every surviving entry and the result is the full pass's.  Otherwise, or when a warp's
@@ -522,13 +523,17 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a, const float *__r
     G = kGuess * st.tprev[c];
   }
   const int need = uses_T(form) ? s_int : (is_pen(form) && a.calibrate ? s_int + 1 : 1);
-  if ((!exact && !(G > 0.0f)) || need > p || (uses_T(form) && s_int >= p)) {
+  // x is zero outside the last x-step's support list, so only that list is cleared below; after
+  // the start init (first sweep) x is dense and there is no list: the full pass writes all of x
+  if ((!exact && !(G > 0.0f)) || need > p || (uses_T(form) && s_int >= p) || st.iters[c] <= 1 || !sup_idx ||
+      st.nnz[c] > a.cap) {
     if (threadIdx.x == 0) st.xfast[c] = 0;
     return;
   }
   const uint32_t Gk = __float_as_uint(G);
 
-  // ---- one pass: candidates (key > Gk) into this warp's list, x = 0, sums for lambda_s
+  // ---- one pass: candidates (key > Gk) into this warp's list, sums for lambda_s.  Four 128-entry
+  // chunks per step, their loads issued before any is used.
   const float *vg = V + (int64_t)c * ldv;
   float *x = X + (int64_t)c * ldx;
   const int seg = ((p + XW - 1) / XW + 127) / 128 * 128;
@@ -538,48 +543,51 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a, const float *__r
   int wc = 0;
   bool over = false;
   float f1 = 0.0f, f2 = 0.0f;
-  for (int base = lo; base < hi && !over; base += 128) {
-    const int i0 = base + 4 * lane;
-    float e[4];
-    if (i0 + 3 < hi) {
-      const float4 t = *reinterpret_cast<const float4 *>(vg + i0);
-      e[0] = t.x; e[1] = t.y; e[2] = t.z; e[3] = t.w;
-      *reinterpret_cast<float4 *>(x + i0) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    } else {
+  for (int base = lo; base < hi && !over; base += 512) {
+    float e[4][4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        e[q] = (i0 + q < hi) ? vg[i0 + q] : 0.0f;
-        if (i0 + q < hi) x[i0 + q] = 0.0f;
+    for (int h = 0; h < 4; ++h) {
+      const int i0 = base + h * 128 + 4 * lane;
+      if (i0 + 3 < hi) {
+        const float4 t = *reinterpret_cast<const float4 *>(vg + i0);
+        e[h][0] = t.x; e[h][1] = t.y; e[h][2] = t.z; e[h][3] = t.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e[h][q] = (i0 + q < hi) ? vg[i0 + q] : 0.0f;
       }
     }
-    int cnt = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float av = fabsf(e[q]);
-      cnt += (i0 + q < hi && __float_as_uint(av) > Gk) ? 1 : 0;
-      f1 += av;
-      f2 = fmaf(av, av, f2);
-    }
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const int tot = __shfl_sync(0xffffffffu, incl, 31);
-    if (wc + tot > kCandW) {
-      over = true;
-    } else {
-      int q2 = wc + incl - cnt;
+    for (int h = 0; h < 4; ++h) {
+      const int i0 = base + h * 128 + 4 * lane;
+      int cnt = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        if (i0 + q < hi && abs_key(e[q]) > Gk) {
-          wv[q2] = e[q];
-          wi[q2] = i0 + q;
-          ++q2;
+        const float av = fabsf(e[h][q]);
+        cnt += (i0 + q < hi && __float_as_uint(av) > Gk) ? 1 : 0;
+        f1 += av;
+        f2 = fmaf(av, av, f2);
+      }
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int tot = __shfl_sync(0xffffffffu, incl, 31);
+      if (over || wc + tot > kCandW) {
+        over = true;
+      } else {
+        int q2 = wc + incl - cnt;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (i0 + q < hi && abs_key(e[h][q]) > Gk) {
+            wv[q2] = e[h][q];
+            wi[q2] = i0 + q;
+            ++q2;
+          }
         }
+        wc += tot;
       }
-      wc += tot;
     }
   }
   if (threadIdx.x == 0) fail_s = 0;
@@ -591,7 +599,8 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a, const float *__r
     if (threadIdx.x == 0) st.xfast[c] = 0;
     return;
   }
-  // ---- the warp lists, concatenated in warp order, are the candidates in index order
+  // ---- the warp lists, concatenated in warp order, are the candidates in index order; x is
+  // cleared on the last support (the finish writes the new one, after barriers)
   const int ncand = warp_offsets(lane == 0 ? wc : 0, sh);
   {
     const int off = sh.woff[w];
@@ -599,6 +608,9 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a, const float *__r
       cval[off + t] = wv[t];
       cidx[off + t] = wi[t];
     }
+    const int nnz_old = st.nnz[c];
+    const int *old = sup_idx + (int64_t)c * a.cap;
+    for (int t = threadIdx.x; t < nnz_old; t += XT) x[old[t]] = 0.0f;
   }
   __syncthreads();
 
