@@ -752,12 +752,12 @@ static_assert(TC_PAIR_BN == 128 || TC_PAIR_BN == 256, "pair tile width");
 
 namespace {
 // pipeline stages that fit in shared memory (227 KB per CTA, less 1 KB of alignment slack and
-// 1 KB of barriers): 3 P planes of 128 x 64 plus nb Q planes of (BN / 2) x 64, all BF16 -- the
-// same per CTA for the pair tile and for the single-CTA tile
-constexpr int tc_stages(int nb) {
-  return (230400 / (3 * TC_BM * 64 * 2 + nb * (TC_PAIR_BN / 2) * 64 * 2)) > 4
-             ? 4
-             : 230400 / (3 * TC_BM * 64 * 2 + nb * (TC_PAIR_BN / 2) * 64 * 2);
+// 1 KB of barriers): na P planes of 128 x 64 plus nb Q planes of (BN / 2) x 64, all BF16 -- the
+// same per CTA for the pair tile and for the single-CTA tile; at most 8
+constexpr int tc_stages(int na, int nb) {
+  return (230400 / (na * TC_BM * 64 * 2 + nb * (TC_PAIR_BN / 2) * 64 * 2)) > 8
+             ? 8
+             : 230400 / (na * TC_BM * 64 * 2 + nb * (TC_PAIR_BN / 2) * 64 * 2);
 }
 
 // the single-CTA kernel with its cluster multicast of P: 128 x (BN / 2) tiles
@@ -766,11 +766,14 @@ cudaError_t launch_gemm_tc_single(const PMaps &P, int na, const CUtensorMap &Q, 
                                   const int *n_dev, const int *col_map, int *err, cudaStream_t st) {
   constexpr int BN1 = TC_PAIR_BN / 2;
   if (na == 3 && nb == 1)
-    return launch_tc_impl<BN1, 3, 1, tc_stages(1), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
-                                                           col_map, err, st);
+    return launch_tc_impl<BN1, 3, 1, tc_stages(3, 1), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
+                                                          col_map, err, st);
   if (na == 3 && nb == 3)
-    return launch_tc_impl<BN1, 3, 3, tc_stages(3), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
-                                                           col_map, err, st);
+    return launch_tc_impl<BN1, 3, 3, tc_stages(3, 3), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
+                                                          col_map, err, st);
+  if (na == 1 && nb == 1)
+    return launch_tc_impl<BN1, 1, 1, tc_stages(1, 1), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
+                                                          col_map, err, st);
   return cudaErrorInvalidValue;
 }
 }  // namespace
@@ -783,11 +786,14 @@ cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb,
   if (M <= TC_BM || !sk.ws || !sk.flags || !sk.epoch || sk.slots < 1)
     return launch_gemm_tc_single(P, na, Q, nb, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
   if (na == 3 && nb == 1)
-    return launch_tc2_impl<TC_PAIR_BN, 3, 1, tc_stages(1)>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
-                                                             col_map, err, sk, st);
+    return launch_tc2_impl<TC_PAIR_BN, 3, 1, tc_stages(3, 1)>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
+                                                                col_map, err, sk, st);
   if (na == 3 && nb == 3)
-    return launch_tc2_impl<TC_PAIR_BN, 3, 3, tc_stages(3)>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
-                                                             col_map, err, sk, st);
+    return launch_tc2_impl<TC_PAIR_BN, 3, 3, tc_stages(3, 3)>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
+                                                                col_map, err, sk, st);
+  if (na == 1 && nb == 1)   // the leading planes only (low-precision sweeps)
+    return launch_tc2_impl<TC_PAIR_BN, 1, 1, tc_stages(1, 1)>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
+                                                                col_map, err, sk, st);
   return cudaErrorInvalidValue;
 }
 

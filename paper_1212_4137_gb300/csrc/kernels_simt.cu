@@ -390,6 +390,71 @@ __global__ void __launch_bounds__(256) k_gemm1_sparse(const float *__restrict__ 
   if (i4 + 3 < n) u[i4 + 3] = acc.w;
 }
 
+// The same gather over the leading BF16 plane of A^T (the low-precision sweeps): 8 rows per
+// thread as one 16-byte load, products and sums in FP32 in support order.
+__global__ void __launch_bounds__(256) k_gemm1_sparse_bf16(const __nv_bfloat16 *__restrict__ AT0, int64_t ldat,
+                                                           int n, const int *__restrict__ sup_idx,
+                                                           const float *__restrict__ sup_val, int cap,
+                                                           StartState s, float *__restrict__ U, int64_t ldu,
+                                                           const int *__restrict__ gate) {
+  if (*gate == 0) return;
+  const int c = blockIdx.y;
+  if (s.status[c] != ST_ACTIVE) return;
+  __shared__ int sidx[256];
+  __shared__ float sval[256];
+  const int nnz = s.nnz[c];
+  const int i8 = (blockIdx.x * blockDim.x + threadIdx.x) * 8;
+  const int *gi = sup_idx + (int64_t)c * cap;
+  const float *gv = sup_val + (int64_t)c * cap;
+  float acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+  auto step = [&](float xv, uint4 raw) {
+    const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&raw);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 f = __bfloat1622float2(h2[q]);
+      acc[2 * q] = fmaf(xv, f.x, acc[2 * q]);
+      acc[2 * q + 1] = fmaf(xv, f.y, acc[2 * q + 1]);
+    }
+  };
+  for (int t0 = 0; t0 < nnz; t0 += 256) {
+    __syncthreads();
+    if (t0 + (int)threadIdx.x < nnz) {
+      sidx[threadIdx.x] = gi[t0 + threadIdx.x];
+      sval[threadIdx.x] = gv[t0 + threadIdx.x];
+    }
+    __syncthreads();
+    const int m = min(256, nnz - t0);
+    if (i8 < n) {
+      const __nv_bfloat16 *base = AT0 + i8;
+      int t = 0;
+      for (; t + 8 <= m; t += 8) {
+        uint4 a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = __ldg(reinterpret_cast<const uint4 *>(base + (int64_t)sidx[t + q] * ldat));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) step(sval[t + q], a[q]);
+      }
+      for (; t < m; ++t) step(sval[t], __ldg(reinterpret_cast<const uint4 *>(base + (int64_t)sidx[t] * ldat)));
+    }
+  }
+  float *u = U + (int64_t)c * ldu;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (i8 + q < n) u[i8 + q] = acc[q];
+}
+
+cudaError_t launch_gemm1_sparse_bf16(const void *AT0, int64_t ldat, int n, const int *sup_idx,
+                                     const float *sup_val, int cap, StartState s, int r, float *U, int64_t ldu,
+                                     const int *gate, cudaStream_t st) {
+  if (ldat % 8 != 0 || (reinterpret_cast<uintptr_t>(AT0) & 15u) != 0) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((n + 2047) / 2048), (unsigned)r);
+  k_gemm1_sparse_bf16<<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(AT0), ldat, n, sup_idx, sup_val,
+                                            cap, s, U, ldu, gate);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int *sup_idx,
                                 const float *sup_val, int cap, StartState s, int r, float *U,
                                 int64_t ldu, const int *gate, cudaStream_t st) {

@@ -2,6 +2,7 @@
 // the kernels read), the solve driver that runs Algorithm 2 for r starts as a sequence of
 // kernels on one stream, and the step-level entry points (x-step, sweep products).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -26,7 +27,8 @@ struct spca_handle {
   int64_t ldX = 0, ldU = 0;
   float *X = nullptr, *V = nullptr, *U = nullptr, *Y = nullptr;
   void *Xpl = nullptr, *Ypl = nullptr;     // 3 BF16 planes each (tensor-core engine)
-  CUtensorMap tmX3{}, tmY1{}, tmY3{};      // Q-operand maps: X planes, y = +-1, y planes
+  CUtensorMap tmX3{}, tmX1{}, tmY1{}, tmY3{};   // Q-operand maps: X planes (3 or the leading one),
+                                                // y = +-1 or the leading plane of y, y planes
   int *sup_idx = nullptr;
   float *sup_val = nullptr;
   int *act = nullptr, *rank = nullptr;     // ordered list of the active starts and its inverse
@@ -187,6 +189,7 @@ int ensure_workspace(spca_handle *h, int r) {
     CK(cudaMemsetAsync(h->Xpl, 0, (size_t)3 * r * h->ldX * 2, h->stream));
     CK(cudaMemsetAsync(h->Ypl, 0, (size_t)3 * r * h->ldU * 2, h->stream));
     CK(make_plane_map(&h->tmX3, h->Xpl, r, h->ldX, 3, tc_box_rows(3), tc_bk(3)));
+    CK(make_plane_map(&h->tmX1, h->Xpl, r, h->ldX, 1, tc_box_rows(1), tc_bk(1)));
     CK(make_plane_map(&h->tmY1, h->Ypl, r, h->ldU, 1, tc_box_rows(1), tc_bk(1)));
     CK(make_plane_map(&h->tmY3, h->Ypl, r, h->ldU, 3, tc_box_rows(3), tc_bk(3)));
     h->kcap = (int)std::min<int64_t>(1024, (p + 63) / 64 * 64);
@@ -254,6 +257,17 @@ TcPairs pairs_general() {
   q.first_main = 5;
   return q;
 }
+// the leading planes only (low-precision sweeps): A_hi x B_hi
+TcPairs pairs_hi() {
+  TcPairs t{};
+  t.n = 1;
+  t.first_main = 0;
+  t.first_corr = -1;
+  t.a[0] = 0;
+  t.b[0] = 0;
+  return t;
+}
+
 TcPairs pairs_sign() {
   TcPairs q{};
   q.n = 3;
@@ -265,14 +279,17 @@ TcPairs pairs_sign() {
 
 // u = A x for every active row of h->X: dense contraction (gated: runs only if *gate != 0).  The
 // tensor-core engine packs the active starts (h->act, count *nact) into consecutive plane rows.
-int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int *nact, int nhost) {
+int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int *nact, int nhost, bool lowp) {
   const int n = (int)h->n, p = (int)h->p;
   cudaStream_t st = h->stream;
   if (engine == SPCA_ENGINE_TC) {
     CK(timed(h, SPCA_K_U_DENSE, 2, [&] {
-      cudaError_t e = launch_split_planes(h->X, r, p, h->ldX, h->Xpl, h->ldX, (int64_t)h->r_cap * h->ldX, 3,
-                                          gate, nact, h->act, st);
+      cudaError_t e = launch_split_planes(h->X, r, p, h->ldX, h->Xpl, h->ldX, (int64_t)h->r_cap * h->ldX,
+                                          lowp ? 1 : 3, gate, nact, h->act, st);
       if (e != cudaSuccess) return e;
+      if (lowp)
+        return launch_gemm_tc(h->pmA, 1, h->tmX1, 1, n, nhost, p, nullptr, pairs_hi(), h->U, h->ldU, gate, nact,
+                              h->act, h->dev_err, h->sk, st);
       return launch_gemm_tc(h->pmA, 3, h->tmX3, 3, n, nhost, p, nullptr, pairs_general(), h->U, h->ldU, gate, nact,
                             h->act, h->dev_err, h->sk, st);
     }));
@@ -300,7 +317,8 @@ int sweep_u_union(spca_handle *h, StartState S, const Ctrl *c, int nhost) {
 }
 
 // y-step and v = A^T y for every active row (tensor-core engine: packed active rows, see above)
-int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const int *nact, int nhost) {
+int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const int *nact, int nhost,
+              bool lowp = false) {
   const int n = (int)h->n, p = (int)h->p;
   cudaStream_t st = h->stream;
   const bool tc = engine == SPCA_ENGINE_TC;
@@ -309,7 +327,12 @@ int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const i
     return launch_ystep(form, h->U, h->ldU, n, r, tc ? nullptr : h->Y, tc ? h->Ypl : nullptr, ypstride,
                         tc ? h->rank : nullptr, S, h->X, h->ldX, p, st);
   }));
-  if (tc) {
+  if (tc && lowp) {
+    CK(timed(h, SPCA_K_V, 1, [&] {
+      return launch_gemm_tc(h->pmAT, 1, h->tmY1, 1, p, nhost, n, nullptr, pairs_hi(), h->V, h->ldX, nullptr, nact,
+                            h->act, h->dev_err, h->sk, st);
+    }));
+  } else if (tc) {
     const bool l1 = is_l1_var(form);
     CK(timed(h, SPCA_K_V, 1, [&] {
       return launch_gemm_tc(h->pmAT, 3, l1 ? h->tmY1 : h->tmY3, l1 ? 1 : 3, p, nhost, n, nullptr,
@@ -402,9 +425,8 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
   if (!out || !A) return SPCA_E_INVALID;
   if (n < 1 || p < 1 || lda < p || n > INT32_MAX || p > INT32_MAX) return SPCA_E_INVALID;
   if (in_dtype != SPCA_F32 && in_dtype != SPCA_F64) return SPCA_E_INVALID;
-  if (storage != SPCA_F32) {
-    if (storage == SPCA_BF16 || storage == SPCA_FP8_E4M3_COLSCALED || storage == SPCA_F64)
-      return SPCA_E_UNSUPPORTED;
+  if (storage != SPCA_F32 && storage != SPCA_BF16) {
+    if (storage == SPCA_FP8_E4M3_COLSCALED || storage == SPCA_F64) return SPCA_E_UNSUPPORTED;
     return SPCA_E_INVALID;
   }
   int ndev = 0, dev = 0;
@@ -420,6 +442,7 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     int major = 0;
     CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
     h->tc_ok = major >= 10;
+    if (storage == SPCA_BF16 && !h->tc_ok) return SPCA_E_UNSUPPORTED;   // the planes need tcgen05
     CK(cudaMallocHost((void **)&h->h_ctrl, 2 * sizeof(Ctrl)));
     CK(cudaMallocHost((void **)&h->h_flag, 2 * sizeof(int)));
     h->h_flag[0] = h->h_flag[1] = 0;
@@ -517,7 +540,7 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
   CK(cudaMemsetAsync(h->iters, 0, (size_t)r * sizeof(int), st));
   CK(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), st));
   CK(launch_active_list(h->status, nullptr, r, h->act, h->rank, &h->ctrl[0], st));
-  RC(sweep_u_dense(h, eng, r, nullptr, &h->ctrl[0].active, r));
+  RC(sweep_u_dense(h, eng, r, nullptr, &h->ctrl[0].active, r, false));
   RC(sweep_y_v(h, eng, form, r, state_of(h), &h->ctrl[0].active, r));
   CK(cudaMemcpy2DAsync(U, ldu * sizeof(float), h->U, h->ldU * sizeof(float), (size_t)n * sizeof(float), r,
                        cudaMemcpyDeviceToDevice, st));
@@ -536,8 +559,16 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   if (!std::isfinite(P.tol)) return fail(h, SPCA_E_INVALID, "tol must be finite%s");
   const bool target = is_pen(form) && P.gamma_mode == SPCA_GAMMA_TARGET_NNZ;
   if (target && P.gamma_calib_sweeps < 1) return fail(h, SPCA_E_INVALID, "gamma_calib_sweeps must be >= 1%s");
+  if (P.lowp_sweeps < 0 || P.refine_sweeps < 0 || P.timeout_us < 0)
+    return fail(h, SPCA_E_INVALID, "lowp_sweeps, refine_sweeps and timeout_us must be >= 0%s");
   int engine;
   RC(resolve_engine(h, P.engine, &engine));
+  if (P.lowp_sweeps > 0 && engine != SPCA_ENGINE_TC)
+    return fail(h, SPCA_E_UNSUPPORTED, "low-precision sweeps need the tensor-core engine%s");
+  const auto t_start = std::chrono::steady_clock::now();
+  const int L = P.lowp_sweeps;
+  const int max_iter = P.refine_sweeps > 0 ? (int)std::min<int64_t>(P.max_iter, (int64_t)L + P.refine_sweeps)
+                                           : P.max_iter;
 
   const int r = P.r, n = (int)h->n, p = (int)h->p;
   RC(ensure_workspace(h, r));
@@ -573,7 +604,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   xa.form = form; xa.p = p; xa.s = P.s;
   xa.thr_fixed = uses_U(form) ? u_threshold(P.gamma) : (float)P.gamma;
   xa.gamma_fixed = P.gamma;
-  xa.tol = P.tol; xa.max_iter = P.max_iter;
+  xa.tol = P.tol; xa.max_iter = max_iter;
   xa.cap = p;
   xa.sparse_cap = p / 8 > 0 ? p / 8 : 1;
   const int C = target ? P.gamma_calib_sweeps : 0;
@@ -591,22 +622,28 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   const int sparse_cap = xa.sparse_cap;
   int64_t max_nnz = uses_T(form) ? std::min<int64_t>((int64_t)P.s, p) : p;
   bool dense_queued = true;   // x^(0) is dense
-  for (int k = 1; k <= P.max_iter; ++k) {
+  for (int k = 1; k <= max_iter; ++k) {
     Ctrl *cur = h->ctrl + ((k - 1) & 1), *nxt = h->ctrl + (k & 1);
+    // the first L sweeps read the leading BF16 planes only (A rounded to BF16)
+    const bool lowp = k <= L;
     // u = A x: over the union of the supports when it is small (tensor cores), else the dense
     // contraction, or the per-start support gather when every support is small
-    if (dense_queued) RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, nhost));
+    if (dense_queued) RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, nhost, lowp));
     if (union_built) RC(sweep_u_union(h, S, cur, nhost));
     CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
+      if (lowp)
+        return launch_gemm1_sparse_bf16(h->ATpl, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
+                                        &cur->use_gather, st);
       return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
                                  &cur->use_gather, st);
     }));
     // y-step, v = A^T y
-    RC(sweep_y_v(h, engine, form, r, S, &cur->active, nhost));
+    RC(sweep_y_v(h, engine, form, r, S, &cur->active, nhost, lowp));
     CK(cudaMemsetAsync(nxt, 0, sizeof(Ctrl), st));
     xa.calibrate = target && k <= C;
     xa.per_start_thr = target && k > C;
-    xa.stop_test = P.tol >= 0.0 && k >= 2 && k >= C + 1;
+    // the stopping rule compares two FP32 sweeps
+    xa.stop_test = P.tol >= 0.0 && k >= 2 && k >= C + 1 && k >= L + 2;
     dense_queued = max_nnz > sparse_cap / 2;
     xa.sparse_cap = dense_queued ? sparse_cap : p;   // p: the gather for every support
     CK(timed(h, SPCA_K_XSTEP, 3, [&] {   // candidate x-step, full x-step, active list
@@ -614,16 +651,20 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
       if (e != cudaSuccess) return e;
       return launch_active_list(h->status, h->nnz, r, h->act, h->rank, nxt, st);   // for the next sweep
     }));
-    union_built = engine == SPCA_ENGINE_TC && sum_nnz <= (int64_t)kUnionTry * h->kcap;
+    union_built = engine == SPCA_ENGINE_TC && k + 1 > L && sum_nnz <= (int64_t)kUnionTry * h->kcap;
     if (union_built) {
       CK(timed(h, SPCA_K_U_SPARSE, 2, [&] {
         return launch_union(h->sup_idx, p, S, r, p, h->mark, h->colpos, h->collist, h->kcap, nxt, st);
       }));
     }
-    if (k == P.max_iter || k % check_every == 0) {
+    if (k == max_iter || k % check_every == 0) {
       CK(cudaMemcpyAsync(h->h_ctrl, nxt, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if (h->h_ctrl->active == 0) break;
+      if (P.timeout_us > 0 &&
+          std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t_start)
+                  .count() > P.timeout_us)
+        return fail(h, SPCA_E_TIMEOUT, "the solve ran past timeout_us%s");
       nhost = h->h_ctrl->active;   // counts only fall: any earlier value stays an upper bound
       sum_nnz = h->h_ctrl->sum_nnz;
       max_nnz = h->h_ctrl->max_nnz;

@@ -109,6 +109,11 @@ cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int 
                                 const float *sup_val, int cap, StartState s, int r, float *U,
                                 int64_t ldu, const int *gate, cudaStream_t st);
 
+// the same over the leading BF16 plane of A^T (low-precision sweeps)
+cudaError_t launch_gemm1_sparse_bf16(const void *AT0, int64_t ldat, int n, const int *sup_idx,
+                                     const float *sup_val, int cap, StartState s, int r, float *U, int64_t ldu,
+                                     const int *gate, cudaStream_t st);
+
 // y-step (S1 / S2 of Table 3) for active starts.  Writes Y as FP32 (Y != nullptr, row c) and/or
 // as BF16 planes (Ypl != nullptr, row rank[c] when rank is given, else c: 1 plane of +-1 for L1
 // variance, 3 planes hi/mid/lo for L2 variance, plane t at Ypl + t * plane_stride)

@@ -36,7 +36,7 @@ class spca_params(ctypes.Structure):
                 ("gamma_mode", ctypes.c_int), ("gamma_calib_sweeps", ctypes.c_int),
                 ("r", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("x0_is_device", ctypes.c_int), ("engine", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("lowp_sweeps", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("timeout_us", ctypes.c_int64)]
 
 
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -177,7 +177,7 @@ def spca_destroy(h) -> None:
 class Handle:
     """Owns an spca_handle; A is host numpy (float32/float64) or a torch CUDA tensor."""
 
-    def __init__(self, A, stream: int = 0):
+    def __init__(self, A, stream: int = 0, storage: int = SPCA_F32):
         try:
             import torch
             is_tensor = isinstance(A, torch.Tensor)
@@ -187,14 +187,14 @@ class Handle:
             assert A.is_cuda and A.dim() == 2 and A.stride(1) == 1
             dt = {"torch.float32": SPCA_F32, "torch.float64": SPCA_F64}[str(A.dtype)]
             n, p = A.shape
-            st, h = spca_create(A.data_ptr(), n, p, A.stride(0), dt, True, SPCA_F32, stream)
+            st, h = spca_create(A.data_ptr(), n, p, A.stride(0), dt, True, storage, stream)
         else:
             A = np.ascontiguousarray(A)
             dt = SPCA_F64 if A.dtype == np.float64 else SPCA_F32
             if A.dtype not in (np.float32, np.float64):
                 A = A.astype(np.float32)
             n, p = A.shape
-            st, h = spca_create(A, n, p, p, dt, False, SPCA_F32, stream)
+            st, h = spca_create(A, n, p, p, dt, False, storage, stream)
         _check(st, "spca_create")
         self.h, self.n, self.p = h, n, p
 
@@ -222,13 +222,15 @@ class Handle:
             pass
 
     def solve(self, form, r, s=1.0, gamma=0.0, gamma_target=False, calib=10, max_iter=100,
-              tol=1e-9, x0=None, seed=0, engine=SPCA_ENGINE_AUTO, want_starts=False, x0_device=False):
+              tol=1e-9, x0=None, seed=0, engine=SPCA_ENGINE_AUTO, want_starts=False, x0_device=False,
+              lowp_sweeps=0, refine_sweeps=0, timeout_us=0):
         """Returns a dict of numpy results.  x0: r x p float32 host array, device address
         (x0_device=True), or None for seeded starts."""
         prm = spca_params(form=form, s=s, gamma=gamma,
                           gamma_mode=SPCA_GAMMA_TARGET_NNZ if gamma_target else SPCA_GAMMA_FIXED,
                           gamma_calib_sweeps=calib, r=r, max_iter=max_iter, tol=tol, seed=seed,
-                          x0_is_device=int(x0_device), engine=engine)
+                          x0_is_device=int(x0_device), engine=engine, lowp_sweeps=lowp_sweeps,
+                          refine_sweeps=refine_sweeps, timeout_us=timeout_us)
         n, p = self.n, self.p
         out = {"x": np.zeros(p, np.float32), "y": np.zeros(n, np.float32),
                "support": np.zeros(p, np.int64)}

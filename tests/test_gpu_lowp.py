@@ -1,0 +1,122 @@
+"""GPU checks of the solve options around Algorithm 2: low-precision sweeps (A rounded to BF16
+for the first sweeps, then FP32 sweeps to the stopping rule), the cap on the FP32 sweeps, the
+wall-clock limit, and BF16 storage.
+
+Low-precision sweeps change the trajectory, so a start may reach another stationary point than in
+a plain FP32 solve, and in the gamma-targeting mode gamma is calibrated on the rounded v.  What
+the FP32 refinement guarantees, and what is checked: no start stops before two FP32 sweeps; every
+start's reported objective is the FP64 objective of its x; the best x is a fixed point of the
+FP64 map (constrained forms); and, for L2 variance with a cardinality bound, a start that ends on
+the same support as in the plain FP32 solve has the same objective."""
+import numpy as np
+import pytest
+
+from paper_1212_4137_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1212_4137_gb300 import build, spca
+    build.build()
+    spca.load()
+    return spca
+
+
+@pytest.fixture(scope="module")
+def spiked():
+    n, p = 700, 2600
+    A = I.spiked_matrix(n, p, I.spiked_thetas(n, p), 20, 711, dtype=np.float32)
+    G = I.raw_starts(p, 96, 712).astype(np.float32)
+    return A, G
+
+
+def _kw(form):
+    if form in (1, 2, 3, 4):
+        return dict(s=20.0)
+    return dict(s=20.0, gamma_target=True, calib=8)
+
+
+@pytest.mark.parametrize("form", range(1, 9))
+def test_lowp_then_fp32_refines(lib, oracle, spiked, form):
+    A, G = spiked
+    A64 = A.astype(np.float64)
+    h = lib.Handle(A)
+    r = G.shape[0]
+    ref = h.solve(form, r, x0=G, max_iter=80, tol=1e-7, want_starts=True, **_kw(form))
+    got = h.solve(form, r, x0=G, max_iter=80, tol=1e-7, want_starts=True, lowp_sweeps=12, **_kw(form))
+    h.close()
+    # no start stops during the low-precision sweeps or on the first FP32 sweep
+    done = got["start_status"] != lib.SPCA_ST_DEGENERATE
+    assert np.all(got["start_iters"][done] >= 14)
+    # reported objectives are the FP64 objectives of the returned x
+    for c in range(0, r, 12):
+        fo, evo = oracle.objective(A64, form, got["start_gamma"][c], got["start_x"][c].astype(np.float64))
+        assert abs(got["start_objective"][c] - fo) <= 1e-9 * max(1.0, abs(fo))
+    if form > 4:
+        return
+    # the best x is a fixed point of the FP64 map
+    b = got["best_start"]
+    x = got["start_x"][b].astype(np.float64)
+    one = oracle.solve(A64, form, x[None, :], max_iter=1, tol=-1, s=20.0)
+    if np.array_equal(one.X[0] != 0, x != 0):
+        assert np.max(np.abs(one.X[0] - x)) <= 1e-3
+    if form != 1:
+        return
+    # L2 variance with a cardinality bound: on a fixed support the fixed point is the leading
+    # singular vector of A restricted to it, so a start that ends on the same support as in the
+    # plain FP32 solve has the same objective
+    same = [c for c in range(r) if np.array_equal(got["start_x"][c] != 0, ref["start_x"][c] != 0)
+            and got["start_status"][c] == lib.SPCA_ST_CONVERGED and ref["start_status"][c] == lib.SPCA_ST_CONVERGED]
+    assert len(same) >= 1
+    for c in same:
+        assert abs(got["start_objective"][c] - ref["start_objective"][c]) <= 1e-5 * abs(ref["start_objective"][c])
+
+
+def test_refine_sweeps_cap(lib, spiked):
+    A, G = spiked
+    h = lib.Handle(A)
+    out = h.solve(1, 32, x0=G[:32], s=20.0, max_iter=100, tol=-1, lowp_sweeps=5, refine_sweeps=3,
+                  want_starts=True)
+    h.close()
+    assert np.all(out["start_iters"] == 8)
+    assert out["sweeps_total"] == 8 * 32
+
+
+def test_timeout_returns_status(lib, spiked):
+    A, G = spiked
+    h = lib.Handle(A)
+    with pytest.raises(lib.SpcaError) as e:
+        h.solve(1, 32, x0=G[:32], s=20.0, max_iter=10000, tol=-1, timeout_us=1)
+    assert e.value.status == lib.SPCA_E_TIMEOUT
+    # the handle stays usable
+    out = h.solve(1, 32, x0=G[:32], s=20.0, max_iter=5, tol=-1)
+    assert out["sweeps_total"] == 5 * 32
+    h.close()
+
+
+def test_lowp_needs_tensor_cores_engine(lib, spiked):
+    A, G = spiked
+    h = lib.Handle(A)
+    with pytest.raises(lib.SpcaError) as e:
+        h.solve(1, 8, x0=G[:8], s=20.0, lowp_sweeps=3, engine=lib.SPCA_ENGINE_SIMT)
+    assert e.value.status == lib.SPCA_E_UNSUPPORTED
+    with pytest.raises(lib.SpcaError) as e:
+        h.solve(1, 8, x0=G[:8], s=20.0, lowp_sweeps=-1)
+    assert e.value.status == lib.SPCA_E_INVALID
+    h.close()
+
+
+def test_bf16_storage_handle(lib, spiked):
+    A, G = spiked
+    h32 = lib.Handle(A)
+    h16 = lib.Handle(A, storage=lib.SPCA_BF16)
+    a = h32.solve(2, 24, x0=G[:24], s=20.0, max_iter=30, tol=-1, lowp_sweeps=10)
+    b = h16.solve(2, 24, x0=G[:24], s=20.0, max_iter=30, tol=-1, lowp_sweeps=10)
+    h32.close()
+    h16.close()
+    assert a["objective"] == b["objective"]
+    assert np.array_equal(a["support"], b["support"])
