@@ -96,11 +96,13 @@ typedef enum {
  *                device memory (a_is_device = 1).  Copied; the caller may free it on return.
  *                The library does not centre the columns (the paper assumes centred data,
  *                Section 1).
- *   storage      SPCA_F32, or SPCA_BF16: the representation the low-precision sweeps read
- *                (spca_params.lowp_sweeps).  Both keep the FP32 master copy and its exact
- *                three-plane BF16 split (hi + mid + lo = a); the low-precision sweeps read the
- *                leading plane (A rounded to BF16).  SPCA_BF16 needs tensor cores (sm_100+) and
- *                SPCA_FP8_E4M3_COLSCALED is not built: both return SPCA_E_UNSUPPORTED otherwise.
+ *   storage      SPCA_F32, or SPCA_BF16 (a 16-bit copy for the low-precision sweeps,
+ *                spca_params.lowp_sweeps).  Both keep the FP32 master copy and the tensor-core
+ *                operand format: two FP16 planes of a row-scaled copy (hi + lo carries 22
+ *                significant bits); the low-precision sweeps read the leading plane (A rounded
+ *                to 11 significant bits, finer than BF16's 8).  SPCA_BF16 needs tensor cores
+ *                (sm_100+) and SPCA_FP8_E4M3_COLSCALED is not built: both return
+ *                SPCA_E_UNSUPPORTED otherwise.
  *   cuda_stream  cudaStream_t the handle uses (NULL = the legacy default stream).
  * Errors: SPCA_E_INVALID (NULL pointers, n < 1, p < 1, lda < p, A not finite, unknown dtype),
  *         SPCA_E_UNSUPPORTED, SPCA_E_NOMEM, SPCA_E_CUDA.
@@ -127,9 +129,10 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
  *                       element (c, j) of the r x p block is normal number c*p + j.
  *   x0_is_device        x0 is a device pointer (1) or a host pointer (0).
  *   engine              spca_engine.
- *   lowp_sweeps         the first lowp_sweeps sweeps read A rounded to BF16 (its leading
- *                       plane: one tensor-core product per tile in v = A^T y and u = A x,
- *                       and a BF16 support gather), y's leading plane, FP32 accumulation;
+ *   lowp_sweeps         the first lowp_sweeps sweeps read A rounded to 11 significant bits
+ *                       (the leading FP16 plane: one tensor-core product per tile in v = A^T y
+ *                       and u = A x, and an FP16 support gather), y's leading plane, FP32
+ *                       accumulation;
  *                       no start stops during them.  Then FP32 sweeps refine every start
  *                       to the stopping rule.  0 = FP32 throughout.  Needs the tensor-core
  *                       engine (SPCA_E_UNSUPPORTED otherwise).

@@ -3,33 +3,34 @@
 // one elected thread issues tcgen05.mma with the accumulator in TMEM, four epilogue warps read
 // TMEM back with tcgen05.ld and store the result transposed (one start per output row).
 //
-// FP32 accuracy from BF16 tensor cores: every FP32 operand is stored as three BF16 planes
-// (hi = bf16(a), mid = bf16(a - hi), lo = a - hi - mid; hi + mid + lo == a exactly, since
-// each plane holds the next 8 significant bits).  A product sum a.b is then the sum over
-// plane pairs (i, j) of a_i . b_j, each product exact; the pairs with i + j <= 2 carry
-// everything above the 2^-24 relative level of FP32 (6 products for two general operands,
-// 3 when b is +-1 and has a single plane).  The tensor core's accumulation truncates, so the
-// error grows with the number of MMA steps into one accumulator: the hi x hi product goes to
-// its own TMEM accumulator and the correction products (2^-8 smaller and below) to a second
-// one; the epilogue adds the two with FP32 round-to-nearest.  Measured on GB300 against FP64
-// (K = 8192, relative to sum |a_k b_k|): one accumulator for all six products 3.5e-6, the
-// hi x hi product alone 7.6e-7.
+// FP32-class accuracy from FP16 tensor cores: every FP32 operand is stored as two FP16 planes of
+// a power-of-two scaled copy (hi = fp16(s a), lo = fp16(s a - hi): 22 significant bits; see
+// kPlanes in spca_internal.cuh).  A product sum a.b is then the sum over plane pairs (i, j) of
+// a_i . b_j, each product exact; the pairs hi.hi, hi.lo and lo.hi carry everything above the
+// 2^-21 relative level (3 products for two general operands, 2 when b is +-1 and has one
+// plane).  The tensor core's accumulation truncates, so the error grows with the number of MMA
+// steps into one accumulator: the hi x hi product goes to its own TMEM accumulator and the
+// correction products (2^-11 smaller) to a second one; the epilogue adds the two with FP32
+// round-to-nearest and undoes the scales (a power of two).  Measured with three BF16 planes on
+// GB300 against FP64 (K = 8192, relative to sum |a_k b_k|): one accumulator for all products
+// 3.5e-6, the hi x hi product alone 7.6e-7.
 //
 //   D[m, c] = sum_{(i,j) in pairs} sum_k P_i[m, k] Q_j[c, k]      out[c * ldo + m] = D[m, c]
 //
-// P (M x K) and Q (N x K) are K-contiguous BF16 planes; plane i of P starts at row i * M_alloc.
+// P (M x K) and Q (N x K) are K-contiguous FP16 planes; plane i of P starts at row i * M_alloc.
 // Tile 128 (M) x BN (N) x 64 (K); 2-stage TMA -> MMA pipeline over mbarriers.  The operand
 // delivery from L2, not the MMAs, bounds this contraction (measured: the time is the same with
-// 1, 2 or 3 plane products per stage), and the three P planes are its largest stream.  So the
+// 1, 2 or 3 plane products per stage), and the P planes are its largest stream.  So the
 // C CTAs (C = 1, 2, 4) that compute adjacent N tiles of one M tile form a thread-block cluster:
 // each loads 1/C of the P tile and multicasts it to all C, and each CTA's MMA commit frees the
 // stage in every CTA of the cluster.
 #include <cuda.h>
 #include <cudaTypedefs.h>
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdint>
 
+#include "block_util.cuh"
 #include "spca_internal.cuh"
 
 namespace spca {
@@ -126,9 +127,10 @@ __device__ __forceinline__ uint32_t cluster_size() {
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-// instruction descriptor, kind::f16: D f32, A bf16, B bf16, both K-major, M = 128, N = BN
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// instruction descriptor, kind::f16: D f32 (bit 4), A and B f16 (format 0 in bits 7-9 and
+// 10-12), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -164,6 +166,7 @@ template <int BN, int NA, int NB, int STAGES, int TC_BK>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int M, int N,
               int kblocks, const int *__restrict__ k_dev, TcPairs pairs, float *__restrict__ out, int64_t ldo,
+              const float *__restrict__ row_inv, const float *__restrict__ col_inv, float q_inv,
               const int *__restrict__ gate, const int *__restrict__ n_dev, const int *__restrict__ col_map,
               int *err) {
   constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;       // 16 KB per P plane tile
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
+    constexpr uint32_t idesc = idesc_f16(TC_BM, BN);
     bool ok = true;
     for (int kb = 0; kb < kblocks && ok; ++kb) {
       const int s = kb % STAGES;
@@ -280,10 +283,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int j = 0; j < 32; ++j) v[j] += w[j];
         }
         if (row < M) {
+          const float sc = (row_inv ? row_inv[row] : 1.0f) * q_inv;   // powers of two
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int col = n0 + cb * 32 + j;
-            if (col < N) out[(int64_t)(col_map ? col_map[col] : col) * ldo + row] = v[j];
+            if (col < N)
+              out[(int64_t)(col_map ? col_map[col] : col) * ldo + row] = v[j] * sc * (col_inv ? col_inv[col] : 1.0f);
           }
         }
       }
@@ -370,6 +375,7 @@ template <int BN, int NA, int NB, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc2(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int M, int N,
                int kblocks, const int *__restrict__ k_dev, TcPairs pairs, float *__restrict__ out, int64_t ldo,
+               const float *__restrict__ row_inv, const float *__restrict__ col_inv, float q_inv,
                const int *__restrict__ gate, const int *__restrict__ n_dev, const int *__restrict__ col_map,
                int *err, float *__restrict__ ws, int *__restrict__ flags, int epoch) {
   constexpr int BK = 64;
@@ -457,7 +463,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   } else if (warp == 1 && lane == 0 && rank == 0) {
     // ---------------------------------------------------------------- MMA issuer (leader)
-    constexpr uint32_t idesc = idesc_bf16(2 * TC_BM, BN);
+    constexpr uint32_t idesc = idesc_f16(2 * TC_BM, BN);
     uint32_t it = 0, seg = 0;
     bool ok = true;
     for (long long u = u0; u < u1 && ok; ++seg) {
@@ -554,10 +560,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
         if (row < M && ok) {
+          const float sc = (row_inv ? row_inv[row] : 1.0f) * q_inv;   // powers of two
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int col = n0 + cb * 32 + j;
-            if (col < N) out[(int64_t)(col_map ? col_map[col] : col) * ldo + row] = v[j];
+            if (col < N)
+              out[(int64_t)(col_map ? col_map[col] : col) * ldo + row] = v[j] * sc * (col_inv ? col_inv[col] : 1.0f);
           }
         }
       }
@@ -588,32 +596,64 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // ---------------------------------------------------------------------- planes
 // dst plane t (t < nplanes) of element e: the t-th BF16 piece of src (hi, mid, lo)
 __global__ void k_split_planes(const float *__restrict__ src, int64_t rows, int64_t cols, int64_t lds,
-                               __nv_bfloat16 *__restrict__ dst, int64_t ldd, int64_t plane_stride,
-                               int nplanes, const int *__restrict__ gate, const int *__restrict__ rows_dev,
-                               const int *__restrict__ row_map) {
+                               __half *__restrict__ dst, int64_t ldd, int64_t plane_stride, int nplanes,
+                               const float *__restrict__ row_scale, float scale, const int *__restrict__ gate,
+                               const int *__restrict__ rows_dev, const int *__restrict__ row_map) {
   if (gate && *gate == 0) return;
   if (rows_dev) rows = *rows_dev;
   const int64_t total = rows * cols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / cols, c = e - r * cols;
-    float a = src[(row_map ? (int64_t)row_map[r] : r) * lds + c];
+    // s a is exact (a power of two); hi = fp16(s a); the remainder s a - hi is exact in FP32
+    const float a = src[(row_map ? (int64_t)row_map[r] : r) * lds + c] * (row_scale ? row_scale[r] : scale);
+    const __half hi = __float2half_rn(a);
     const int64_t o = r * ldd + c;
-    for (int t = 0; t < nplanes; ++t) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(a);
-      dst[o + t * plane_stride] = h;
-      a -= __bfloat162float(h);
-    }
+    dst[o] = hi;
+    if (nplanes > 1) dst[o + plane_stride] = __float2half_rn(a - __half2float(hi));
   }
 }
 
 cudaError_t launch_split_planes(const float *src, int64_t rows, int64_t cols, int64_t lds, void *dst,
-                                int64_t ldd, int64_t plane_stride, int nplanes, const int *gate,
-                                const int *rows_dev, const int *row_map, cudaStream_t st) {
+                                int64_t ldd, int64_t plane_stride, int nplanes, const float *row_scale,
+                                float scale, const int *gate, const int *rows_dev, const int *row_map,
+                                cudaStream_t st) {
   // a grid-stride loop over 4 CTAs per SM: when the gate is off the launch costs only that many
   // early exits
-  k_split_planes<<<608, 256, 0, st>>>(src, rows, cols, lds, static_cast<__nv_bfloat16 *>(dst), ldd,
-                                          plane_stride, nplanes, gate, rows_dev, row_map);
+  k_split_planes<<<608, 256, 0, st>>>(src, rows, cols, lds, static_cast<__half *>(dst), ldd, plane_stride, nplanes,
+                                      row_scale, scale, gate, rows_dev, row_map);
+  return cudaGetLastError();
+}
+
+// one CTA per row: scale = 2^(13 - floor(log2 max |row|)), so the scaled row's largest entry lies
+// in [2^13, 2^14) (FP16's largest finite value is 65504); 1 for a zero row
+__global__ void __launch_bounds__(256) k_row_scale(const float *__restrict__ src, int64_t cols, int64_t lds,
+                                                   float *__restrict__ scale, float *__restrict__ inv,
+                                                   const int *__restrict__ gate, const int *__restrict__ rows_dev,
+                                                   const int *__restrict__ row_map) {
+  __shared__ unsigned red[32];
+  if (gate && *gate == 0) return;
+  if (rows_dev && (int)blockIdx.x >= *rows_dev) return;
+  const float *row = src + (row_map ? (int64_t)row_map[blockIdx.x] : (int64_t)blockIdx.x) * lds;
+  unsigned mk = 0u;
+  for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) mk = max(mk, __float_as_uint(fabsf(row[c])));
+  const unsigned m = block_max_u(mk, red);
+  if (threadIdx.x == 0) {
+    int e = 0;
+    if (m != 0u) {
+      const float mx = __uint_as_float(m);
+      e = 13 - ilogbf(mx);
+      e = max(-120, min(120, e));
+    }
+    scale[blockIdx.x] = ldexpf(1.0f, e);
+    inv[blockIdx.x] = ldexpf(1.0f, -e);
+  }
+}
+
+cudaError_t launch_row_scales(const float *src, int64_t rows, int64_t cols, int64_t lds, float *scale, float *inv,
+                              const int *gate, const int *rows_dev, const int *row_map, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  k_row_scale<<<(unsigned)rows, 256, 0, st>>>(src, cols, lds, scale, inv, gate, rows_dev, row_map);
   return cudaGetLastError();
 }
 
@@ -642,7 +682,7 @@ cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int
   cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * (cuuint64_t)rows};
   cuuint32_t box[3] = {(cuuint32_t)bk, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -660,8 +700,8 @@ cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld,
 namespace {
 template <int BN, int NA, int NB, int STAGES, int TC_BK>
 cudaError_t launch_tc_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, int K, const int *k_dev, TcPairs pairs,
-                           float *out, int64_t ldo, const int *gate, const int *n_dev, const int *col_map,
-                           int *err, cudaStream_t st) {
+                           float *out, int64_t ldo, const float *row_inv, const float *col_inv, float q_inv,
+                           const int *gate, const int *n_dev, const int *col_map, int *err, cudaStream_t st) {
   constexpr int STAGE_BYTES = NA * TC_BM * TC_BK * 2 + NB * BN * TC_BK * 2;
   constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
   auto kern = k_gemm_tc<BN, NA, NB, STAGES, TC_BK>;
@@ -690,17 +730,17 @@ cudaError_t launch_tc_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, i
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, P.m[lg], Q, M, N, kblocks, k_dev, pairs, out, ldo,
-                            gate, n_dev, col_map,
-                            err);
+  return cudaLaunchKernelEx(&cfg, kern, P.m[lg], Q, M, N, kblocks, k_dev, pairs, out, ldo, row_inv, col_inv, q_inv,
+                            gate, n_dev, col_map, err);
 }
 }  // namespace
 
 namespace {
 template <int BN, int NA, int NB, int STAGES>
 cudaError_t launch_tc2_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, int K, const int *k_dev,
-                            TcPairs pairs, float *out, int64_t ldo, const int *gate, const int *n_dev,
-                            const int *col_map, int *err, const TcStreamK &sk, cudaStream_t st) {
+                            TcPairs pairs, float *out, int64_t ldo, const float *row_inv, const float *col_inv,
+                            float q_inv, const int *gate, const int *n_dev, const int *col_map, int *err,
+                            const TcStreamK &sk, cudaStream_t st) {
   constexpr int BK = 64;
   constexpr int STAGE_BYTES = NA * TC_BM * BK * 2 + NB * (BN / 2) * BK * 2;
   constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
@@ -736,8 +776,8 @@ cudaError_t launch_tc2_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, 
   if (units < S) S = (int)(units > 0 ? units : 1);
   cfg.gridDim = dim3((unsigned)(2 * S), 1);
   const int epoch = ++(*sk.epoch);
-  return cudaLaunchKernelEx(&cfg, kern, P.m[0], Q, M, N, kblocks, k_dev, pairs, out, ldo, gate, n_dev, col_map,
-                            err, sk.ws, sk.flags, epoch);
+  return cudaLaunchKernelEx(&cfg, kern, P.m[0], Q, M, N, kblocks, k_dev, pairs, out, ldo, row_inv, col_inv, q_inv,
+                            gate, n_dev, col_map, err, sk.ws, sk.flags, epoch);
 }
 }  // namespace
 
@@ -752,8 +792,8 @@ static_assert(TC_PAIR_BN == 128 || TC_PAIR_BN == 256, "pair tile width");
 
 namespace {
 // pipeline stages that fit in shared memory (227 KB per CTA, less 1 KB of alignment slack and
-// 1 KB of barriers): na P planes of 128 x 64 plus nb Q planes of (BN / 2) x 64, all BF16 -- the
-// same per CTA for the pair tile and for the single-CTA tile; at most 8
+// 1 KB of barriers): na P planes of 128 x 64 plus nb Q planes of (BN / 2) x 64, FP16 -- the same
+// per CTA for the pair tile and for the single-CTA tile; at most 8
 constexpr int tc_stages(int na, int nb) {
   return (230400 / (na * TC_BM * 64 * 2 + nb * (TC_PAIR_BN / 2) * 64 * 2)) > 8
              ? 8
@@ -762,18 +802,19 @@ constexpr int tc_stages(int na, int nb) {
 
 // the single-CTA kernel with its cluster multicast of P: 128 x (BN / 2) tiles
 cudaError_t launch_gemm_tc_single(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
-                                  const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const int *gate,
-                                  const int *n_dev, const int *col_map, int *err, cudaStream_t st) {
+                                  const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const float *row_inv,
+                                  const float *col_inv, float q_inv, const int *gate, const int *n_dev,
+                                  const int *col_map, int *err, cudaStream_t st) {
   constexpr int BN1 = TC_PAIR_BN / 2;
-  if (na == 3 && nb == 1)
-    return launch_tc_impl<BN1, 3, 1, tc_stages(3, 1), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
-                                                          col_map, err, st);
-  if (na == 3 && nb == 3)
-    return launch_tc_impl<BN1, 3, 3, tc_stages(3, 3), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
-                                                          col_map, err, st);
+  if (na == 2 && nb == 2)
+    return launch_tc_impl<BN1, 2, 2, tc_stages(2, 2), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, row_inv, col_inv,
+                                                          q_inv, gate, n_dev, col_map, err, st);
+  if (na == 2 && nb == 1)
+    return launch_tc_impl<BN1, 2, 1, tc_stages(2, 1), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, row_inv, col_inv,
+                                                          q_inv, gate, n_dev, col_map, err, st);
   if (na == 1 && nb == 1)
-    return launch_tc_impl<BN1, 1, 1, tc_stages(1, 1), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
-                                                          col_map, err, st);
+    return launch_tc_impl<BN1, 1, 1, tc_stages(1, 1), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, row_inv, col_inv,
+                                                          q_inv, gate, n_dev, col_map, err, st);
   return cudaErrorInvalidValue;
 }
 }  // namespace
@@ -781,19 +822,21 @@ cudaError_t launch_gemm_tc_single(const PMaps &P, int na, const CUtensorMap &Q, 
 // CTA pairs (256 x BN tiles, stream-K over the resident pairs) when there are at least two M
 // tiles; one M tile runs on single CTAs
 cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
-                           const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const int *gate,
-                           const int *n_dev, const int *col_map, int *err, const TcStreamK &sk, cudaStream_t st) {
+                           const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const float *row_inv,
+                           const float *col_inv, float q_inv, const int *gate, const int *n_dev, const int *col_map,
+                           int *err, const TcStreamK &sk, cudaStream_t st) {
   if (M <= TC_BM || !sk.ws || !sk.flags || !sk.epoch || sk.slots < 1)
-    return launch_gemm_tc_single(P, na, Q, nb, M, N, K, k_dev, pairs, out, ldo, gate, n_dev, col_map, err, st);
-  if (na == 3 && nb == 1)
-    return launch_tc2_impl<TC_PAIR_BN, 3, 1, tc_stages(3, 1)>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
-                                                                col_map, err, sk, st);
-  if (na == 3 && nb == 3)
-    return launch_tc2_impl<TC_PAIR_BN, 3, 3, tc_stages(3, 3)>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
-                                                                col_map, err, sk, st);
+    return launch_gemm_tc_single(P, na, Q, nb, M, N, K, k_dev, pairs, out, ldo, row_inv, col_inv, q_inv, gate,
+                                 n_dev, col_map, err, st);
+  if (na == 2 && nb == 2)   // two general operands
+    return launch_tc2_impl<TC_PAIR_BN, 2, 2, tc_stages(2, 2)>(P, Q, M, N, K, k_dev, pairs, out, ldo, row_inv,
+                                                                col_inv, q_inv, gate, n_dev, col_map, err, sk, st);
+  if (na == 2 && nb == 1)   // y = +-1
+    return launch_tc2_impl<TC_PAIR_BN, 2, 1, tc_stages(2, 1)>(P, Q, M, N, K, k_dev, pairs, out, ldo, row_inv,
+                                                                col_inv, q_inv, gate, n_dev, col_map, err, sk, st);
   if (na == 1 && nb == 1)   // the leading planes only (low-precision sweeps)
-    return launch_tc2_impl<TC_PAIR_BN, 1, 1, tc_stages(1, 1)>(P, Q, M, N, K, k_dev, pairs, out, ldo, gate, n_dev,
-                                                                col_map, err, sk, st);
+    return launch_tc2_impl<TC_PAIR_BN, 1, 1, tc_stages(1, 1)>(P, Q, M, N, K, k_dev, pairs, out, ldo, row_inv,
+                                                                col_inv, q_inv, gate, n_dev, col_map, err, sk, st);
   return cudaErrorInvalidValue;
 }
 

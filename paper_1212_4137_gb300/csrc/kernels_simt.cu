@@ -1,7 +1,7 @@
 // kernels_simt.cu -- layout preparation, start initialisation, the y-step, and the FP32
 // CUDA-core contractions of one AM sweep (Algorithm 2): u = A x (dense or over the support of
 // x) and v = A^T y.
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdint>
 
@@ -150,7 +150,7 @@ cudaError_t launch_start_init(const float *x0, int64_t ld0, uint64_t seed, int r
 // y goes to Y (FP32) and/or to BF16 planes (hi, mid, lo; a single exact plane for +-1).
 __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict__ U, int64_t ldu,
                                                int n, float *__restrict__ Y,
-                                               __nv_bfloat16 *__restrict__ Ypl, int64_t pstride,
+                                               __half *__restrict__ Ypl, int64_t pstride,
                                                const int *__restrict__ rank, StartState s,
                                                float *__restrict__ X, int64_t ldX, int p) {
   __shared__ float redf[32];
@@ -158,13 +158,13 @@ __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict
   if (s.status[c] != ST_ACTIVE) return;
   const float *u = U + (int64_t)c * ldu;
   float *y = Y ? Y + (int64_t)c * ldu : nullptr;
-  __nv_bfloat16 *yp = Ypl ? Ypl + (int64_t)(rank ? rank[c] : c) * ldu : nullptr;
+  __half *yp = Ypl ? Ypl + (int64_t)(rank ? rank[c] : c) * ldu : nullptr;
   if (threadIdx.x == 0) s.iters[c] += 1;
   if (is_l1_var(form)) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const float yi = (u[i] >= 0.0f) ? 1.0f : -1.0f;
       if (y) y[i] = yi;
-      if (yp) yp[i] = __float2bfloat16_rn(yi);
+      if (yp) yp[i] = __float2half_rn(yi * kQScale);   // +-2^14, exact
     }
     return;
   }
@@ -186,12 +186,10 @@ __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict
     float yi = u[i] * inv;
     if (y) y[i] = yi;
     if (yp) {
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(yi);
-        yp[i + t * pstride] = h;
-        yi -= __bfloat162float(h);
-      }
+      const float ys = yi * kQScale;                 // exact (a power of two), |ys| <= 2^14
+      const __half hi = __float2half_rn(ys);
+      yp[i] = hi;
+      yp[i + pstride] = __float2half_rn(ys - __half2float(hi));
     }
   }
 }
@@ -199,7 +197,7 @@ __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict
 cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, float *Y, void *Ypl,
                          int64_t plane_stride, const int *rank, StartState s, float *X, int64_t ldX,
                          int p, cudaStream_t st) {
-  k_ystep<<<r, 256, 0, st>>>(form, U, ldu, n, Y, static_cast<__nv_bfloat16 *>(Ypl), plane_stride, rank,
+  k_ystep<<<r, 256, 0, st>>>(form, U, ldu, n, Y, static_cast<__half *>(Ypl), plane_stride, rank,
                              s, X, ldX, p);
   return cudaGetLastError();
 }
@@ -390,10 +388,12 @@ __global__ void __launch_bounds__(256) k_gemm1_sparse(const float *__restrict__ 
   if (i4 + 3 < n) u[i4 + 3] = acc.w;
 }
 
-// The same gather over the leading BF16 plane of A^T (the low-precision sweeps): 8 rows per
-// thread as one 16-byte load, products and sums in FP32 in support order.
-__global__ void __launch_bounds__(256) k_gemm1_sparse_bf16(const __nv_bfloat16 *__restrict__ AT0, int64_t ldat,
-                                                           int n, const int *__restrict__ sup_idx,
+// The same gather over the leading FP16 plane of A^T (the low-precision sweeps): row j of the
+// plane is A[:, j] times at_scale[j]; the inverse scale is folded into x_j.  8 rows per thread as
+// one 16-byte load, products and sums in FP32 in support order.
+__global__ void __launch_bounds__(256) k_gemm1_sparse_lowp(const __half *__restrict__ AT0, int64_t ldat,
+                                                           const float *__restrict__ at_inv, int n,
+                                                           const int *__restrict__ sup_idx,
                                                            const float *__restrict__ sup_val, int cap,
                                                            StartState s, float *__restrict__ U, int64_t ldu,
                                                            const int *__restrict__ gate) {
@@ -410,10 +410,10 @@ __global__ void __launch_bounds__(256) k_gemm1_sparse_bf16(const __nv_bfloat16 *
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
   auto step = [&](float xv, uint4 raw) {
-    const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&raw);
+    const __half2 *h2 = reinterpret_cast<const __half2 *>(&raw);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float2 f = __bfloat1622float2(h2[q]);
+      const float2 f = __half22float2(h2[q]);
       acc[2 * q] = fmaf(xv, f.x, acc[2 * q]);
       acc[2 * q + 1] = fmaf(xv, f.y, acc[2 * q + 1]);
     }
@@ -421,13 +421,14 @@ __global__ void __launch_bounds__(256) k_gemm1_sparse_bf16(const __nv_bfloat16 *
   for (int t0 = 0; t0 < nnz; t0 += 256) {
     __syncthreads();
     if (t0 + (int)threadIdx.x < nnz) {
-      sidx[threadIdx.x] = gi[t0 + threadIdx.x];
-      sval[threadIdx.x] = gv[t0 + threadIdx.x];
+      const int j = gi[t0 + threadIdx.x];
+      sidx[threadIdx.x] = j;
+      sval[threadIdx.x] = gv[t0 + threadIdx.x] * at_inv[j];
     }
     __syncthreads();
     const int m = min(256, nnz - t0);
     if (i8 < n) {
-      const __nv_bfloat16 *base = AT0 + i8;
+      const __half *base = AT0 + i8;
       int t = 0;
       for (; t + 8 <= m; t += 8) {
         uint4 a[8];
@@ -445,12 +446,12 @@ __global__ void __launch_bounds__(256) k_gemm1_sparse_bf16(const __nv_bfloat16 *
     if (i8 + q < n) u[i8 + q] = acc[q];
 }
 
-cudaError_t launch_gemm1_sparse_bf16(const void *AT0, int64_t ldat, int n, const int *sup_idx,
+cudaError_t launch_gemm1_sparse_lowp(const void *AT0, int64_t ldat, const float *at_inv, int n, const int *sup_idx,
                                      const float *sup_val, int cap, StartState s, int r, float *U, int64_t ldu,
                                      const int *gate, cudaStream_t st) {
   if (ldat % 8 != 0 || (reinterpret_cast<uintptr_t>(AT0) & 15u) != 0) return cudaErrorInvalidValue;
   dim3 grid((unsigned)((n + 2047) / 2048), (unsigned)r);
-  k_gemm1_sparse_bf16<<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(AT0), ldat, n, sup_idx, sup_val,
+  k_gemm1_sparse_lowp<<<grid, 256, 0, st>>>(static_cast<const __half *>(AT0), ldat, at_inv, n, sup_idx, sup_val,
                                             cap, s, U, ldu, gate);
   return cudaGetLastError();
 }

@@ -4,12 +4,13 @@
 //   1. one mark per column of A for every support entry, and an ordered compaction of the
 //      marks into S (column -> position, position -> column, K' = |S|), which also decides on
 //      the device whether the next sweep takes this path;
-//   2. the columns of A in S gathered into BF16 planes with the support position contiguous
-//      (n x K' per plane, zero-padded to a multiple of 64), from the rows of A^T;
-//   3. each active x scattered into the same K' positions (three BF16 planes);
+//   2. the columns of A in S gathered into the two FP16 planes of the tensor-core format (A's row
+//      scales) with the support position contiguous (n x K' per plane, zero-padded to a multiple
+//      of 64), from the rows of the FP32 A^T;
+//   3. each active x scattered into the same K' positions (two FP16 planes);
 // and the tensor-core contraction runs over K' instead of p (work n * K' instead of n * p per
 // start, and A is read once instead of once per start).
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdint>
 
@@ -83,55 +84,56 @@ cudaError_t launch_union(const int *sup_idx, int cap, StartState s, int r, int p
   return cudaGetLastError();
 }
 
-// AS[t][i * kcap + k] = plane t of A[i, collist[k]] (= A^T[collist[k], i]) for k < K', 0 for
-// K' <= k < kpad; 32 x 32 tiles transposed through shared memory (coalesced on both sides),
-// visited by a grid-stride loop so that a gated-off launch costs only a few early exits
-__global__ void __launch_bounds__(256) k_gather_cols(const __nv_bfloat16 *__restrict__ ATpl, int64_t ldat,
-                                                     int64_t at_pstride, int n, const int *__restrict__ collist,
-                                                     int kcap, __nv_bfloat16 *__restrict__ AS, int64_t as_pstride,
+// AS[t][i * kcap + k] = plane t of a_scale[i] A[i, collist[k]] (= a_scale[i] A^T[collist[k], i])
+// for k < K', 0 for K' <= k < kpad: the same operand format as the P planes of A (row scales of
+// A), read from the FP32 A^T; 32 x 32 tiles transposed through shared memory (coalesced on both
+// sides), visited by a grid-stride loop so that a gated-off launch costs only a few early exits
+__global__ void __launch_bounds__(256) k_gather_cols(const float *__restrict__ AT, int64_t ldat,
+                                                     const float *__restrict__ a_scale, int n,
+                                                     const int *__restrict__ collist, int kcap,
+                                                     __half *__restrict__ AS, int64_t as_pstride,
                                                      const Ctrl *__restrict__ ctrl) {
-  __shared__ __nv_bfloat16 tile[32][34];
+  __shared__ float tile[32][33];
   if (ctrl->use_union == 0) return;
   const int K = ctrl->kunion, kpad = min(kcap, (K + 63) / 64 * 64);
   const int tk = (kpad + 31) / 32, ti = (n + 31) / 32;
-  const int ntiles = tk * ti * 3;
+  const int ntiles = tk * ti;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int pl = t / (tk * ti), rem = t - pl * tk * ti;
-    const int k0 = (rem % tk) * 32, i0 = (rem / tk) * 32;
-    const __nv_bfloat16 *src = ATpl + pl * at_pstride;
-    __nv_bfloat16 *dst = AS + pl * as_pstride;
+    const int k0 = (t % tk) * 32, i0 = (t / tk) * 32;
     __syncthreads();
     for (int kk = ty; kk < 32; kk += 8) {
       const int k = k0 + kk, i = i0 + tx;
-      __nv_bfloat16 v = __float2bfloat16_rn(0.0f);
-      if (k < K && i < n) v = src[(int64_t)collist[k] * ldat + i];
-      tile[kk][tx] = v;
+      tile[kk][tx] = (k < K && i < n) ? AT[(int64_t)collist[k] * ldat + i] * a_scale[i] : 0.0f;
     }
     __syncthreads();
     for (int ii = ty; ii < 32; ii += 8) {
       const int i = i0 + ii, k = k0 + tx;
-      if (i < n && k < kpad) dst[(int64_t)i * kcap + k] = tile[tx][ii];
+      if (i < n && k < kpad) {
+        const float a = tile[tx][ii];
+        const __half hi = __float2half_rn(a);
+        AS[(int64_t)i * kcap + k] = hi;
+        AS[(int64_t)i * kcap + k + as_pstride] = __float2half_rn(a - __half2float(hi));
+      }
     }
   }
 }
 
-// XS[t][k * kcap + colpos[j]] = plane t of x_j for the k-th active start (rows zeroed first)
+// XS[t][k * kcap + colpos[j]] = plane t of kQScale x_j for the k-th active start (rows zeroed first)
 __global__ void __launch_bounds__(256) k_scatter_x(const int *__restrict__ sup_idx, const float *__restrict__ sup_val,
                                                    int cap, StartState s, const int *__restrict__ act,
                                                    const int *__restrict__ colpos, int kcap,
-                                                   __nv_bfloat16 *__restrict__ XS, int64_t xs_pstride,
+                                                   __half *__restrict__ XS, int64_t xs_pstride,
                                                    const Ctrl *__restrict__ ctrl) {
   if (ctrl->use_union == 0) return;
   const int k = blockIdx.x;
   if (k >= ctrl->active) return;
   const int kpad = min(kcap, (ctrl->kunion + 63) / 64 * 64);
   const int c = act[k];
-  __nv_bfloat16 *row = XS + (int64_t)k * kcap;
+  __half *row = XS + (int64_t)k * kcap;
   for (int q = threadIdx.x; q < kpad; q += blockDim.x) {
-    row[q] = __float2bfloat16_rn(0.0f);
-    row[q + xs_pstride] = __float2bfloat16_rn(0.0f);
-    row[q + 2 * xs_pstride] = __float2bfloat16_rn(0.0f);
+    row[q] = __float2half_rn(0.0f);
+    row[q + xs_pstride] = __float2half_rn(0.0f);
   }
   __syncthreads();
   const int nnz = s.nnz[c];
@@ -141,26 +143,23 @@ __global__ void __launch_bounds__(256) k_scatter_x(const int *__restrict__ sup_i
     const int pos = colpos[gi[t]];
     if (pos < 0 || pos >= kpad) continue;   // outside the union's first kpad columns (cannot
                                             // happen when use_union is set)
-    float a = gv[t];
-    for (int pl = 0; pl < 3; ++pl) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(a);
-      row[pos + pl * xs_pstride] = h;
-      a -= __bfloat162float(h);
-    }
+    const float a = gv[t] * kQScale;
+    const __half hi = __float2half_rn(a);
+    row[pos] = hi;
+    row[pos + xs_pstride] = __float2half_rn(a - __half2float(hi));
   }
 }
 
-cudaError_t launch_union_operands(const void *ATpl, int64_t ldat, int64_t at_pstride, int n, const int *collist,
+cudaError_t launch_union_operands(const float *AT, int64_t ldat, const float *a_scale, int n, const int *collist,
                                   int kcap, void *AS, int64_t as_pstride, const int *sup_idx,
                                   const float *sup_val, int cap, StartState s, const int *act, int nhost,
                                   const int *colpos, void *XS, int64_t xs_pstride, const Ctrl *c,
                                   cudaStream_t st) {
-  k_gather_cols<<<608, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(ATpl), ldat, at_pstride, n, collist, kcap,
-                                    static_cast<__nv_bfloat16 *>(AS), as_pstride, c);
+  k_gather_cols<<<608, 256, 0, st>>>(AT, ldat, a_scale, n, collist, kcap, static_cast<__half *>(AS), as_pstride, c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_scatter_x<<<nhost > 0 ? nhost : 1, 256, 0, st>>>(sup_idx, sup_val, cap, s, act, colpos, kcap,
-                                                      static_cast<__nv_bfloat16 *>(XS), xs_pstride, c);
+                                                      static_cast<__half *>(XS), xs_pstride, c);
   return cudaGetLastError();
 }
 

@@ -19,15 +19,18 @@ struct spca_handle {
   cudaStream_t stream = nullptr;
   float *A32 = nullptr, *AT32 = nullptr;   // FP32 copies
   bool tc_ok = false;                      // the device has tcgen05 tensor cores (sm_100+)
-  void *Apl = nullptr, *ATpl = nullptr;    // 3 BF16 planes each (hi, mid, lo)
+  void *Apl = nullptr, *ATpl = nullptr;    // tensor-core planes (kPlanes FP16 each, row-scaled)
+  float *a_scale = nullptr, *a_inv = nullptr;     // row scales of A (n) and their inverses
+  float *at_scale = nullptr, *at_inv = nullptr;   // row scales of A^T (p) and their inverses
   PMaps pmA{}, pmAT{};                     // P-operand maps of the planes (per cluster size)
 
   // per-solve workspace, grown on demand
   int r_cap = 0;
   int64_t ldX = 0, ldU = 0;
   float *X = nullptr, *V = nullptr, *U = nullptr, *Y = nullptr;
-  void *Xpl = nullptr, *Ypl = nullptr;     // 3 BF16 planes each (tensor-core engine)
-  CUtensorMap tmX3{}, tmX1{}, tmY1{}, tmY3{};   // Q-operand maps: X planes (3 or the leading one),
+  void *Xpl = nullptr, *Ypl = nullptr;     // kPlanes FP16 planes each (tensor-core engine)
+  float *x_scale = nullptr, *x_inv = nullptr;   // row scales of the packed X planes
+  CUtensorMap tmX2{}, tmX1{}, tmY1{}, tmY2{};   // Q-operand maps: X planes (both or the leading one),
                                                 // y = +-1 or the leading plane of y, y planes
   int *sup_idx = nullptr;
   float *sup_val = nullptr;
@@ -38,7 +41,7 @@ struct spca_handle {
   int *mark = nullptr, *colpos = nullptr, *collist = nullptr;
   void *AS = nullptr, *XS = nullptr;
   PMaps pmAS{};
-  CUtensorMap tmXS3{};
+  CUtensorMap tmXS2{};
   int *status = nullptr, *iters = nullptr, *nnz = nullptr;
   double *F = nullptr, *F_prev = nullptr, *gamma = nullptr, *f = nullptr, *ev = nullptr;
   float *thr = nullptr, *tprev = nullptr;
@@ -136,13 +139,14 @@ void free_workspace(spca_handle *h) {
   void *ptrs[] = {h->X, h->V, h->U, h->Y, h->Xpl, h->Ypl, h->sup_idx, h->sup_val, h->act, h->rank,
                   h->status, h->iters, h->nnz, h->F, h->F_prev, h->gamma, h->f, h->ev, h->thr, h->tprev, h->xfast,
                   h->partials, h->ctrl, h->best, h->y_out, h->x_out, h->support_out, h->nnz_out,
-                  h->mark, h->colpos, h->collist, h->AS, h->XS};
+                  h->mark, h->colpos, h->collist, h->AS, h->XS, h->x_scale, h->x_inv};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   h->mark = h->colpos = h->collist = nullptr;
   h->AS = h->XS = nullptr;
   h->X = h->V = h->U = h->Y = nullptr;
   h->Xpl = h->Ypl = nullptr;
+  h->x_scale = h->x_inv = nullptr;
   h->sup_idx = nullptr; h->sup_val = nullptr;
   h->act = h->rank = nullptr;
   h->status = h->iters = h->nnz = nullptr;
@@ -184,20 +188,21 @@ int ensure_workspace(spca_handle *h, int r) {
   CK(cudaMemsetAsync(h->U, 0, (size_t)r * h->ldU * sizeof(float), h->stream));
   CK(cudaMemsetAsync(h->Y, 0, (size_t)r * h->ldU * sizeof(float), h->stream));
   if (h->tc_ok) {
-    CK(dalloc(&h->Xpl, (size_t)3 * r * h->ldX, 2));
-    CK(dalloc(&h->Ypl, (size_t)3 * r * h->ldU, 2));
-    CK(cudaMemsetAsync(h->Xpl, 0, (size_t)3 * r * h->ldX * 2, h->stream));
-    CK(cudaMemsetAsync(h->Ypl, 0, (size_t)3 * r * h->ldU * 2, h->stream));
-    CK(make_plane_map(&h->tmX3, h->Xpl, r, h->ldX, 3, tc_box_rows(3), tc_bk(3)));
+    CK(dalloc(&h->Xpl, (size_t)kPlanes * r * h->ldX, 2));
+    CK(dalloc(&h->x_scale, (size_t)r)); CK(dalloc(&h->x_inv, (size_t)r));
+    CK(dalloc(&h->Ypl, (size_t)kPlanes * r * h->ldU, 2));
+    CK(cudaMemsetAsync(h->Xpl, 0, (size_t)kPlanes * r * h->ldX * 2, h->stream));
+    CK(cudaMemsetAsync(h->Ypl, 0, (size_t)kPlanes * r * h->ldU * 2, h->stream));
+    CK(make_plane_map(&h->tmX2, h->Xpl, r, h->ldX, 2, tc_box_rows(2), tc_bk(2)));
     CK(make_plane_map(&h->tmX1, h->Xpl, r, h->ldX, 1, tc_box_rows(1), tc_bk(1)));
     CK(make_plane_map(&h->tmY1, h->Ypl, r, h->ldU, 1, tc_box_rows(1), tc_bk(1)));
-    CK(make_plane_map(&h->tmY3, h->Ypl, r, h->ldU, 3, tc_box_rows(3), tc_bk(3)));
+    CK(make_plane_map(&h->tmY2, h->Ypl, r, h->ldU, 2, tc_box_rows(2), tc_bk(2)));
     h->kcap = (int)std::min<int64_t>(1024, (p + 63) / 64 * 64);
     CK(dalloc(&h->mark, (size_t)p)); CK(dalloc(&h->colpos, (size_t)p)); CK(dalloc(&h->collist, (size_t)h->kcap));
-    CK(dalloc(&h->AS, (size_t)3 * n * h->kcap, 2));
-    CK(dalloc(&h->XS, (size_t)3 * r * h->kcap, 2));
-    CK(make_p_maps(&h->pmAS, h->AS, n, h->kcap, 3));
-    CK(make_plane_map(&h->tmXS3, h->XS, r, h->kcap, 3, tc_box_rows(3), tc_bk(3)));
+    CK(dalloc(&h->AS, (size_t)kPlanes * n * h->kcap, 2));
+    CK(dalloc(&h->XS, (size_t)kPlanes * r * h->kcap, 2));
+    CK(make_p_maps(&h->pmAS, h->AS, n, h->kcap, 2));
+    CK(make_plane_map(&h->tmXS2, h->XS, r, h->kcap, 2, tc_box_rows(2), tc_bk(2)));
   }
   h->r_cap = r;
   return SPCA_OK;
@@ -246,15 +251,26 @@ int resolve_engine(spca_handle *h, int engine, int *out) {
   return SPCA_OK;
 }
 
-// plane products of the two contractions (smaller terms first): with three planes on both
-// sides every pair with i + j <= 2; with y = +-1 (one exact plane) the three pairs (i, 0)
+// plane products of the two contractions: hi x hi into the main accumulator, then the two
+// correction products hi x lo and lo x hi (two general operands), or lo x (+-1) when y = +-1 is
+// a single exact plane
 TcPairs pairs_general() {
   TcPairs q{};
-  const unsigned char a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
-  q.n = 6;
-  for (int i = 0; i < 6; ++i) { q.a[i] = a[i]; q.b[i] = b[i]; }
-  q.first_corr = 0;
-  q.first_main = 5;
+  q.n = 3;
+  q.a[0] = 0; q.b[0] = 0;
+  q.a[1] = 1; q.b[1] = 0;
+  q.a[2] = 0; q.b[2] = 1;
+  q.first_main = 0;
+  q.first_corr = 1;
+  return q;
+}
+TcPairs pairs_sign() {
+  TcPairs q{};
+  q.n = 2;
+  q.a[0] = 0; q.b[0] = 0;
+  q.a[1] = 1; q.b[1] = 0;
+  q.first_main = 0;
+  q.first_corr = 1;
   return q;
 }
 // the leading planes only (low-precision sweeps): A_hi x B_hi
@@ -268,30 +284,23 @@ TcPairs pairs_hi() {
   return t;
 }
 
-TcPairs pairs_sign() {
-  TcPairs q{};
-  q.n = 3;
-  q.a[0] = 2; q.a[1] = 1; q.a[2] = 0;
-  q.first_corr = 0;
-  q.first_main = 2;
-  return q;
-}
-
 // u = A x for every active row of h->X: dense contraction (gated: runs only if *gate != 0).  The
 // tensor-core engine packs the active starts (h->act, count *nact) into consecutive plane rows.
 int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int *nact, int nhost, bool lowp) {
   const int n = (int)h->n, p = (int)h->p;
   cudaStream_t st = h->stream;
   if (engine == SPCA_ENGINE_TC) {
-    CK(timed(h, SPCA_K_U_DENSE, 2, [&] {
-      cudaError_t e = launch_split_planes(h->X, r, p, h->ldX, h->Xpl, h->ldX, (int64_t)h->r_cap * h->ldX,
-                                          lowp ? 1 : 3, gate, nact, h->act, st);
+    CK(timed(h, SPCA_K_U_DENSE, 3, [&] {
+      cudaError_t e = launch_row_scales(h->X, nhost, p, h->ldX, h->x_scale, h->x_inv, gate, nact, h->act, st);
+      if (e != cudaSuccess) return e;
+      e = launch_split_planes(h->X, r, p, h->ldX, h->Xpl, h->ldX, (int64_t)h->r_cap * h->ldX, lowp ? 1 : 2,
+                              h->x_scale, 1.0f, gate, nact, h->act, st);
       if (e != cudaSuccess) return e;
       if (lowp)
-        return launch_gemm_tc(h->pmA, 1, h->tmX1, 1, n, nhost, p, nullptr, pairs_hi(), h->U, h->ldU, gate, nact,
-                              h->act, h->dev_err, h->sk, st);
-      return launch_gemm_tc(h->pmA, 3, h->tmX3, 3, n, nhost, p, nullptr, pairs_general(), h->U, h->ldU, gate, nact,
-                            h->act, h->dev_err, h->sk, st);
+        return launch_gemm_tc(h->pmA, 1, h->tmX1, 1, n, nhost, p, nullptr, pairs_hi(), h->U, h->ldU, h->a_inv,
+                              h->x_inv, 1.0f, gate, nact, h->act, h->dev_err, h->sk, st);
+      return launch_gemm_tc(h->pmA, 2, h->tmX2, 2, n, nhost, p, nullptr, pairs_general(), h->U, h->ldU, h->a_inv,
+                            h->x_inv, 1.0f, gate, nact, h->act, h->dev_err, h->sk, st);
     }));
   } else {
     CK(timed(h, SPCA_K_U_DENSE, 1, [&] {
@@ -302,16 +311,17 @@ int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int 
 }
 
 // u = A x for every active row over the union S of the active supports, when the control word
-// c chose it (|S| <= h->kcap): compact BF16 operands, then the tensor-core contraction over |S|
+// c chose it (|S| <= h->kcap): compact FP16 operands, then the tensor-core contraction over |S|
 int sweep_u_union(spca_handle *h, StartState S, const Ctrl *c, int nhost) {
   const int n = (int)h->n, p = (int)h->p;
   CK(timed(h, SPCA_K_U_SPARSE, 3, [&] {
-    cudaError_t e = launch_union_operands(h->ATpl, h->ldAT, (int64_t)p * h->ldAT, n, h->collist, h->kcap, h->AS,
+    cudaError_t e = launch_union_operands(h->AT32, h->ldAT, h->a_scale, n, h->collist, h->kcap, h->AS,
                                           (int64_t)n * h->kcap, h->sup_idx, h->sup_val, p, S, h->act, nhost,
                                           h->colpos, h->XS, (int64_t)h->r_cap * h->kcap, c, h->stream);
     if (e != cudaSuccess) return e;
-    return launch_gemm_tc(h->pmAS, 3, h->tmXS3, 3, n, nhost, h->kcap, &c->kunion, pairs_general(), h->U, h->ldU,
-                          &c->use_union, &c->active, h->act, h->dev_err, h->sk, h->stream);
+    return launch_gemm_tc(h->pmAS, 2, h->tmXS2, 2, n, nhost, h->kcap, &c->kunion, pairs_general(), h->U, h->ldU,
+                          h->a_inv, nullptr, kQInv, &c->use_union, &c->active, h->act, h->dev_err, h->sk,
+                          h->stream);
   }));
   return SPCA_OK;
 }
@@ -329,15 +339,15 @@ int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const i
   }));
   if (tc && lowp) {
     CK(timed(h, SPCA_K_V, 1, [&] {
-      return launch_gemm_tc(h->pmAT, 1, h->tmY1, 1, p, nhost, n, nullptr, pairs_hi(), h->V, h->ldX, nullptr, nact,
-                            h->act, h->dev_err, h->sk, st);
+      return launch_gemm_tc(h->pmAT, 1, h->tmY1, 1, p, nhost, n, nullptr, pairs_hi(), h->V, h->ldX, h->at_inv,
+                            nullptr, kQInv, nullptr, nact, h->act, h->dev_err, h->sk, st);
     }));
   } else if (tc) {
     const bool l1 = is_l1_var(form);
     CK(timed(h, SPCA_K_V, 1, [&] {
-      return launch_gemm_tc(h->pmAT, 3, l1 ? h->tmY1 : h->tmY3, l1 ? 1 : 3, p, nhost, n, nullptr,
-                            l1 ? pairs_sign() : pairs_general(), h->V, h->ldX, nullptr, nact, h->act,
-                            h->dev_err, h->sk, st);
+      return launch_gemm_tc(h->pmAT, 2, l1 ? h->tmY1 : h->tmY2, l1 ? 1 : 2, p, nhost, n, nullptr,
+                            l1 ? pairs_sign() : pairs_general(), h->V, h->ldX, h->at_inv, nullptr, kQInv, nullptr,
+                            nact, h->act, h->dev_err, h->sk, st);
     }));
   } else {
     CK(timed(h, SPCA_K_V, 1, [&] {
@@ -411,7 +421,8 @@ void spca_destroy(spca_handle *h) {
   drain_profile(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   free_workspace(h);
-  void *ptrs[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->flag, h->dev_err, h->sk.ws, h->sk.flags};
+  void *ptrs[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->a_scale, h->a_inv, h->at_scale, h->at_inv,
+                  h->flag, h->dev_err, h->sk.ws, h->sk.flags};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
@@ -472,17 +483,25 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     CK(timed(h, SPCA_K_PREP, 1,
              [&] { return launch_transpose_f32(h->A32, n, p, h->ldA, h->AT32, h->ldAT, h->stream); }));
     if (h->tc_ok) {
-      CK(dalloc(&h->Apl, (size_t)3 * n * h->ldA, 2));
-      CK(dalloc(&h->ATpl, (size_t)3 * p * h->ldAT, 2));
-      CK(timed(h, SPCA_K_PREP, 2, [&] {
-        cudaError_t e = launch_split_planes(h->A32, n, h->ldA, h->ldA, h->Apl, h->ldA, n * h->ldA, 3, nullptr,
-                                            nullptr, nullptr, h->stream);
-        if (e != cudaSuccess) return e;
-        return launch_split_planes(h->AT32, p, h->ldAT, h->ldAT, h->ATpl, h->ldAT, p * h->ldAT, 3, nullptr,
-                                   nullptr, nullptr, h->stream);
+      CK(dalloc(&h->Apl, (size_t)kPlanes * n * h->ldA, 2));
+      CK(dalloc(&h->ATpl, (size_t)kPlanes * p * h->ldAT, 2));
+      CK(dalloc(&h->a_scale, (size_t)n)); CK(dalloc(&h->a_inv, (size_t)n));
+      CK(dalloc(&h->at_scale, (size_t)p)); CK(dalloc(&h->at_inv, (size_t)p));
+      CK(timed(h, SPCA_K_PREP, 4, [&] {
+        cudaError_t e = launch_row_scales(h->A32, n, p, h->ldA, h->a_scale, h->a_inv, nullptr, nullptr, nullptr,
+                                          h->stream);
+        if (e == cudaSuccess)
+          e = launch_row_scales(h->AT32, p, n, h->ldAT, h->at_scale, h->at_inv, nullptr, nullptr, nullptr, h->stream);
+        if (e == cudaSuccess)
+          e = launch_split_planes(h->A32, n, h->ldA, h->ldA, h->Apl, h->ldA, n * h->ldA, kPlanes, h->a_scale, 1.0f,
+                                  nullptr, nullptr, nullptr, h->stream);
+        if (e == cudaSuccess)
+          e = launch_split_planes(h->AT32, p, h->ldAT, h->ldAT, h->ATpl, h->ldAT, p * h->ldAT, kPlanes, h->at_scale,
+                                  1.0f, nullptr, nullptr, nullptr, h->stream);
+        return e;
       }));
-      CK(make_p_maps(&h->pmA, h->Apl, n, h->ldA, 3));
-      CK(make_p_maps(&h->pmAT, h->ATpl, p, h->ldAT, 3));
+      CK(make_p_maps(&h->pmA, h->Apl, n, h->ldA, kPlanes));
+      CK(make_p_maps(&h->pmAT, h->ATpl, p, h->ldAT, kPlanes));
       int sms = 0;
       CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       h->sk.slots = sms / 2 > 0 ? sms / 2 : 1;
@@ -624,7 +643,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   bool dense_queued = true;   // x^(0) is dense
   for (int k = 1; k <= max_iter; ++k) {
     Ctrl *cur = h->ctrl + ((k - 1) & 1), *nxt = h->ctrl + (k & 1);
-    // the first L sweeps read the leading BF16 planes only (A rounded to BF16)
+    // the first L sweeps read the leading FP16 planes only (A rounded to 11 significant bits)
     const bool lowp = k <= L;
     // u = A x: over the union of the supports when it is small (tensor cores), else the dense
     // contraction, or the per-start support gather when every support is small
@@ -632,7 +651,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     if (union_built) RC(sweep_u_union(h, S, cur, nhost));
     CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
       if (lowp)
-        return launch_gemm1_sparse_bf16(h->ATpl, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
+        return launch_gemm1_sparse_lowp(h->ATpl, h->ldAT, h->at_inv, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
                                         &cur->use_gather, st);
       return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
                                  &cur->use_gather, st);

@@ -109,26 +109,43 @@ cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int 
                                 const float *sup_val, int cap, StartState s, int r, float *U,
                                 int64_t ldu, const int *gate, cudaStream_t st);
 
-// the same over the leading BF16 plane of A^T (low-precision sweeps)
-cudaError_t launch_gemm1_sparse_bf16(const void *AT0, int64_t ldat, int n, const int *sup_idx,
+// the same over the leading FP16 plane of A^T (low-precision sweeps): row j of that plane holds
+// A[:, j] times at_scale[j], undone here with at_inv[j]
+cudaError_t launch_gemm1_sparse_lowp(const void *AT0, int64_t ldat, const float *at_inv, int n, const int *sup_idx,
                                      const float *sup_val, int cap, StartState s, int r, float *U, int64_t ldu,
                                      const int *gate, cudaStream_t st);
 
 // y-step (S1 / S2 of Table 3) for active starts.  Writes Y as FP32 (Y != nullptr, row c) and/or
-// as BF16 planes (Ypl != nullptr, row rank[c] when rank is given, else c: 1 plane of +-1 for L1
-// variance, 3 planes hi/mid/lo for L2 variance, plane t at Ypl + t * plane_stride)
+// as tensor-core planes (Ypl != nullptr, row rank[c] when rank is given, else c; plane t at
+// Ypl + t * plane_stride): 1 plane of +-kQScale for L1 variance, the 2 planes of kQScale y for
+// L2 variance)
 cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, float *Y,
                          void *Ypl, int64_t plane_stride, const int *rank, StartState s, float *X,
                          int64_t ldX, int p, cudaStream_t st);
 
 // ---------------------------------------------------------------- tcgen05 engine
+// Operand format of the tensor-core contractions.  Every FP32 matrix they read is held as two
+// FP16 planes of a power-of-two scaled copy: hi = fp16(s a), lo = fp16(s a - hi), so that
+// hi + lo = s a to 22 significant bits (about 2^-22 relative; below 2^-17 of the scale's range
+// an entry keeps an absolute error under 2^-38 of it).  The P operand (A for u = A x, A^T for
+// v = A^T y, the union columns) has one scale per row, 2^(13 - floor(log2 max_k |a_mk|)), so
+// rows of any magnitude keep their precision.  The Q operand y (|y_i| <= 1 by construction) has
+// the fixed scale kQScale; x (any magnitude through spca_products) one scale per row, like P.
+// The epilogue multiplies by the inverse scales, powers of two.
+constexpr int kPlanes = 2;
+constexpr float kQScale = 16384.0f;
+constexpr float kQInv = 1.0f / 16384.0f;
+// per-row scales of an FP32 matrix: scale[r] = 2^(13 - floor(log2 max |src[row_map[r], :]|)) (1
+// for a zero row), inv[r] = 1 / scale[r], r < rows (*rows_dev when given); gated
+cudaError_t launch_row_scales(const float *src, int64_t rows, int64_t cols, int64_t lds, float *scale, float *inv,
+                              const int *gate, const int *rows_dev, const int *row_map, cudaStream_t st);
 struct TcPairs {      // plane products P plane a[q] x Q plane b[q], q < n; the hi x hi product
   int n;              // (a = b = 0, index first_main) accumulates apart from the corrections
   int first_main;     // (first of them at index first_corr, -1 if none)
   int first_corr;
   unsigned char a[8], b[8];
 };
-// 3-D TMA map over `planes` BF16 planes of rows x ld (K-contiguous), box 64 x box_rows
+// 3-D TMA map over `planes` FP16 planes of rows x ld (K-contiguous), box 64 x box_rows
 cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int64_t ld, int planes,
                            int box_rows, int bk);
 int tc_box_rows(int nb);   // Q-operand box height for nb planes (the tile's N)
@@ -139,7 +156,8 @@ struct PMaps {
   CUtensorMap m[3];     // 64-wide K blocks
 };
 cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld, int planes);
-// out[map(c) * ldo + m] = sum_q sum_k P_{a_q}[m, k] Q_{b_q}[c, k], m < M, c < N.  N bounds the
+// out[map(c) * ldo + m] = (row_inv[m] q_inv col_inv[c]) sum_q sum_k P_{a_q}[m, k] Q_{b_q}[c, k],
+// m < M, c < N (a null row_inv / col_inv counts as 1).  N bounds the
 // columns for the launch; with n_dev != nullptr the kernel uses *n_dev (<= N) instead; map =
 // col_map when given, else the identity.  With gate != nullptr nothing runs unless *gate != 0;
 // a timed-out wait sets *err = SPCA_E_TIMEOUT
@@ -155,23 +173,26 @@ struct TcStreamK {
 };
 int64_t tc_sk_floats_per_slot();
 cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
-                           const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const int *gate, const int *n_dev,
-                           const int *col_map, int *err, const TcStreamK &sk, cudaStream_t st);
-// BF16 planes of an FP32 matrix (plane t at dst + t * plane_stride elements): destination row r
-// comes from source row row_map[r] (identity when null), r < rows (*rows_dev when given); gated
+                           const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const float *row_inv,
+                           const float *col_inv, float q_inv, const int *gate, const int *n_dev, const int *col_map,
+                           int *err, const TcStreamK &sk, cudaStream_t st);
+// FP16 planes (hi, lo; the first nplanes) of a scaled FP32 matrix, plane t at dst + t *
+// plane_stride elements: destination row r is source row row_map[r] (identity when null) times
+// row_scale[r] (or `scale` when row_scale is null), r < rows (*rows_dev when given); gated
 cudaError_t launch_split_planes(const float *src, int64_t rows, int64_t cols, int64_t lds, void *dst,
-                                int64_t ldd, int64_t plane_stride, int nplanes, const int *gate,
-                                const int *rows_dev, const int *row_map, cudaStream_t st);
+                                int64_t ldd, int64_t plane_stride, int nplanes, const float *row_scale,
+                                float scale, const int *gate, const int *rows_dev, const int *row_map,
+                                cudaStream_t st);
 // union S of the active starts' supports: colpos[j] = position of column j in S (or -1),
 // collist[k] = the k-th column of S (k < kcap), c->kunion = |S|; then c->use_union (S fits in
 // kcap columns and no start needs the dense path) and, if set, c->use_gather = 0.
 // mark: p ints of scratch
 cudaError_t launch_union(const int *sup_idx, int cap, StartState s, int r, int p, int *mark, int *colpos,
                          int *collist, int kcap, Ctrl *c, cudaStream_t st);
-// operands of u = A x over S when c->use_union: AS planes n x kcap (row i: A[i, S], zero past
-// |S| up to the next multiple of 64) from the A^T planes, and XS planes (row k: the k-th active
-// x at the positions of S)
-cudaError_t launch_union_operands(const void *ATpl, int64_t ldat, int64_t at_pstride, int n, const int *collist,
+// operands of u = A x over S when c->use_union: AS planes n x kcap (row i: a_scale[i] A[i, S],
+// zero past |S| up to the next multiple of 64) from the FP32 A^T, and XS planes (row k: kQScale
+// times the k-th active x at the positions of S)
+cudaError_t launch_union_operands(const float *AT, int64_t ldat, const float *a_scale, int n, const int *collist,
                                   int kcap, void *AS, int64_t as_pstride, const int *sup_idx,
                                   const float *sup_val, int cap, StartState s, const int *act, int nhost,
                                   const int *colpos, void *XS, int64_t xs_pstride, const Ctrl *c,

@@ -1,6 +1,6 @@
-"""GPU checks of the solve options around Algorithm 2: low-precision sweeps (A rounded to BF16
-for the first sweeps, then FP32 sweeps to the stopping rule), the cap on the FP32 sweeps, the
-wall-clock limit, and BF16 storage.
+"""GPU checks of the solve options around Algorithm 2: low-precision sweeps (A rounded to 11
+significant bits, the leading FP16 plane, for the first sweeps, then FP32 sweeps to the stopping
+rule), the cap on the FP32 sweeps, the wall-clock limit, and 16-bit storage handles.
 
 Low-precision sweeps change the trajectory, so a start may reach another stationary point than in
 a plain FP32 solve, and in the gamma-targeting mode gamma is calibrated on the rounded v.  What

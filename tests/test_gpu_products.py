@@ -1,8 +1,8 @@
 """Step-level parity of the two contractions of a sweep (u = A x, y-step, v = A^T y) for both
-engines (FP32 CUDA cores; tcgen05 tensor cores on three BF16 planes per FP32 operand) against
-FP64, on shapes that span several tiles and ragged tails.  The tensor-core engine sums every
-plane product above the 2^-24 relative level, so both engines must agree with FP64 to FP32
-accumulation accuracy."""
+engines (FP32 CUDA cores; tcgen05 tensor cores on two row-scaled FP16 planes per FP32 operand)
+against FP64, on shapes that span several tiles and ragged tails.  The tensor-core engine keeps
+22 significant bits of every operand and sums every plane product above the 2^-21 relative
+level, so both engines must agree with FP64 to FP32 accumulation accuracy."""
 import numpy as np
 import pytest
 
@@ -91,3 +91,25 @@ def test_engines_agree_on_spiked(lib):
         assert np.abs(Us - Ut).max() <= 1e-5 * np.abs(Us).max()
         assert np.abs(Vs - Vt).max() <= 1e-5 * np.abs(Vs).max()
     h.close()
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_products_with_column_scales(lib, form):
+    """Columns of A spread over twelve orders of magnitude: the tensor-core operands carry one
+    power-of-two scale per row of A (u = A x) and per row of A^T (v = A^T y), so every entry of
+    v = A^T y keeps its relative accuracy whatever its column's magnitude, and u = A x keeps the
+    bound relative to sum |a_k x_k|."""
+    n, p, r = 900, 1500, 70
+    rng = np.random.default_rng(77)
+    A = (I.gaussian_matrix(n, p, 78) * 10.0 ** rng.uniform(-6, 6, size=p)).astype(np.float32)
+    A64 = A.astype(np.float64)
+    X = rng.standard_normal((r, p)).astype(np.float32)
+    X[:, rng.uniform(size=p) < 0.5] = 0.0
+    h = lib.Handle(A)
+    U, V = _run(lib, h, form, lib.SPCA_ENGINE_TC, X)
+    h.close()
+    err_u = np.abs(U - X.astype(np.float64) @ A64.T) / (np.abs(X.astype(np.float64)) @ np.abs(A64).T + 1e-300)
+    assert err_u.max() <= _bound("tc", p), err_u.max()
+    Yr = np.where(U >= 0, 1.0, -1.0) if form % 2 == 0 else U / np.linalg.norm(U, axis=1, keepdims=True)
+    err_v = np.abs(V - Yr @ A64) / (np.abs(Yr) @ np.abs(A64) + 1e-300)
+    assert err_v.max() <= _bound("tc", n), err_v.max()
