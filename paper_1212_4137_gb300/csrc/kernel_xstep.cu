@@ -482,6 +482,182 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
   xstep_finish(a, c, vv, p, nullptr, op, x, st, sup_idx, sup_val, ctrl, sh);
 }
 
+// ---------------------------------------------------------------- one-warp operator
+// After the candidate filter a start's surviving entries are few (at most kCand) and sit in
+// shared memory: one warp finishes the x-step without block barriers.
+
+// the j-th largest key among the |v_i| of vv[0 .. len), 1 <= j <= len, built bit by bit from
+// the top (K = the largest key with at least j keys >= K); *n_gt = #(key > K), *n_eq = #(key == K)
+__device__ uint32_t warp_select(const float *vv, int len, int j, int *n_gt, int *n_eq) {
+  const int lane = threadIdx.x & 31;
+  uint32_t K = 0u;
+  for (int bit = 30; bit >= 0; --bit) {
+    const uint32_t cand = K | (1u << bit);
+    int cnt = 0;
+    for (int i = lane; i < len; i += 32) cnt += abs_key(vv[i]) >= cand;
+    if (warp_sum_i(cnt) >= j) K = cand;
+  }
+  int gt = 0, eq = 0;
+  for (int i = lane; i < len; i += 32) {
+    const uint32_t k = abs_key(vv[i]);
+    gt += k > K;
+    eq += k == K;
+  }
+  *n_gt = warp_sum_i(gt);
+  *n_eq = warp_sum_i(eq);
+  return K;
+}
+
+// lambda_s over vv[0 .. len) when phi(key lo0) < 0 is known: the bisection and exact root of
+// lambda_s_bisect, with warp sums
+__device__ double warp_lambda_s(const float *vv, int len, double s, uint32_t lo0, uint32_t maxkey,
+                                uint32_t *lo_out) {
+  const int lane = threadIdx.x & 31;
+  uint32_t lo = lo0, hi = maxkey;
+  while (hi - lo > 1u) {
+    const uint32_t mid = lo + (hi - lo) / 2u;
+    const float lam = __uint_as_float(mid);
+    float sw = 0.0f, sw2 = 0.0f;
+    int in_lo = 0, in_hi = 0;
+    for (int i = lane; i < len; i += 32) {
+      const float a = fabsf(vv[i]);
+      const uint32_t key = __float_as_uint(a);
+      if (a > lam) {
+        const float w = a - lam;
+        sw += w;
+        sw2 = fmaf(w, w, sw2);
+      }
+      in_lo += (key > lo && key < mid);
+      in_hi += (key > mid && key < hi);
+    }
+    sw = warp_sum_f(sw);
+    sw2 = warp_sum_f(sw2);
+    in_lo = warp_sum_i(in_lo);
+    in_hi = warp_sum_i(in_hi);
+    const float phi = (float)s * sw2 - sw * sw;
+    if (phi < 0.0f) {
+      lo = mid;
+      if (in_hi == 0) break;
+    } else {
+      hi = mid;
+      if (in_lo == 0) break;
+    }
+  }
+  float a1 = 0.0f, c1 = 0.0f, a2 = 0.0f, c2 = 0.0f;
+  int kc = 0;
+  for (int i = lane; i < len; i += 32) {
+    const float a = fabsf(vv[i]);
+    if (__float_as_uint(a) > lo) {
+      ++kc;
+      kahan_add(a1, c1, a);
+      const float aa = a * a;
+      kahan_add(a2, c2, aa);
+      kahan_add(a2, c2, fmaf(a, a, -aa));
+    }
+  }
+  const double s1 = warp_sum_d((double)a1 + (double)c1), s2 = warp_sum_d((double)a2 + (double)c2);
+  const double k = (double)warp_sum_i(kc);
+  const double flo = (double)__uint_as_float(lo), fhi = (double)__uint_as_float(hi);
+  double lam;
+  if (k <= s) {
+    lam = flo;
+  } else {
+    double disc = s * (k * s2 - s1 * s1) / (k - s);
+    if (disc < 0.0) disc = 0.0;
+    lam = (s1 - sqrt(disc)) / k;
+    lam = fmin(fmax(lam, flo), fhi);
+  }
+  *lo_out = lo;
+  return lam;
+}
+
+// xstep_finish for one warp over vv[0 .. len) (element i is entry map[i]): ||w||, nnz, F, x on
+// the candidates, the support list in index order, the per-start outputs and the stopping rule
+__device__ void xstep_finish_warp(const XstepArgs &a, int c, const float *vv, int len, const int *map, const XOp &op,
+                                  float *x, StartState st, int *sup_idx, float *sup_val, Ctrl *ctrl) {
+  const int lane = threadIdx.x & 31;
+  const int form = a.form;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  auto wval = [&](float vi, uint32_t key, bool tie_keep) -> float {
+    if (op.mode == 0) return (key > op.K || (key == op.K && tie_keep)) ? vi : 0.0f;
+    if (key <= op.tkey) return 0.0f;
+    if (op.mode == 1) return vi;
+    return copysignf(fabsf(vi) - op.tval, vi);
+  };
+  float part = 0.0f;
+  int nnz = 0;
+  {
+    int eq_run = 0;
+    for (int base = 0; base < len; base += 32) {
+      const int i = base + lane;
+      const float vi = i < len ? vv[i] : 0.0f;
+      const uint32_t key = abs_key(vi);
+      bool tie_keep = false;
+      if (op.mode == 0) {
+        const unsigned b = __ballot_sync(0xffffffffu, i < len && key == op.K);
+        tie_keep = (eq_run + __popc(b & lt_mask)) < op.need_eq;
+        eq_run += __popc(b);
+      }
+      const float w = i < len ? wval(vi, key, tie_keep) : 0.0f;
+      part = fmaf(w, w, part);
+      nnz += __popc(__ballot_sync(0xffffffffu, w != 0.0f));
+    }
+  }
+  const double sumsq = (double)warp_sum_f(part);
+  const double nrm = sqrt(sumsq);
+  double F;
+  if (uses_T(form)) F = nrm;
+  else if (uses_lam(form)) F = op.gam * sqrt(a.s) + nrm;
+  else if (uses_U(form)) F = sumsq - op.gam * (double)nnz;
+  else F = nrm;
+  const float inv = nrm > 0.0 ? (float)(1.0 / nrm) : 0.0f;
+  int *gi = sup_idx + (int64_t)c * a.cap;
+  float *gv = sup_val + (int64_t)c * a.cap;
+  {
+    int eq_run = 0, pos = 0;
+    for (int base = 0; base < len; base += 32) {
+      const int i = base + lane;
+      const float vi = i < len ? vv[i] : 0.0f;
+      const uint32_t key = abs_key(vi);
+      bool tie_keep = false;
+      if (op.mode == 0) {
+        const unsigned b = __ballot_sync(0xffffffffu, i < len && key == op.K);
+        tie_keep = (eq_run + __popc(b & lt_mask)) < op.need_eq;
+        eq_run += __popc(b);
+      }
+      const float w = i < len ? wval(vi, key, tie_keep) : 0.0f;
+      const float xi = w * inv;
+      if (i < len) x[map[i]] = xi;
+      const unsigned nzb = __ballot_sync(0xffffffffu, xi != 0.0f);
+      if (xi != 0.0f) {
+        const int q = pos + __popc(nzb & lt_mask);
+        if (q < a.cap) {
+          gi[q] = map[i];
+          gv[q] = xi;
+        }
+      }
+      pos += __popc(nzb);
+    }
+  }
+  if (lane == 0) {
+    st.F[c] = F;
+    st.nnz[c] = nnz;
+    st.gamma[c] = op.gam;
+    st.tprev[c] = op.tnext;
+    int status = ST_ACTIVE;
+    if (nrm == 0.0) {
+      status = SPCA_ST_DEGENERATE;
+    } else if (a.stop_test && F <= (1.0 + a.tol) * st.F_prev[c]) {
+      status = SPCA_ST_CONVERGED;
+    } else if (st.iters[c] >= a.max_iter) {
+      status = SPCA_ST_MAXITER;
+    }
+    st.F_prev[c] = F;
+    st.status[c] = status;
+    if (status == ST_ACTIVE && ctrl && nnz > a.sparse_cap) atomicOr(&ctrl->need_dense, 1);
+  }
+}
+
 // ---------------------------------------------------------------- candidate x-step
 // Near convergence v moves little between sweeps, and every operator keeps only entries above a
 // threshold (the s-th or (s+1)-th largest |v_i|, lambda_s, or the penalty's fixed threshold).
@@ -614,21 +790,20 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a, const float *__r
   }
   __syncthreads();
 
-  // ---- the operator on the candidates, with the check that G lies below its threshold
+  // ---- the operator on the candidates, with the check that G lies below its threshold: one warp
+  if (w != 0) return;
   XOp op;
   bool ok = ncand >= need;
   if (ok && uses_T(form)) {
-    bool whole;
-    int eq_total;
-    radix_select(cval, ncand, s_int, false, sh, &op.K, &whole, &op.need_eq, &eq_total);
+    int gt, eq;
+    op.K = warp_select(cval, ncand, s_int, &gt, &eq);
+    op.need_eq = s_int - gt;
     op.tnext = __uint_as_float(op.K);
-    op.mode = 1;
-    if (whole) {
-      op.tkey = op.K == 0u ? 0u : op.K - 1u;
-    } else if (op.K == 0u || op.need_eq >= eq_total) {
-      op.tkey = op.K == 0u ? 0u : op.K - 1u;
+    if (op.need_eq >= eq) {   // every key equal to K is kept: keep key >= K
+      op.mode = 1;
+      op.tkey = op.K - 1u;
     } else {
-      op.mode = 0;
+      op.mode = 0;            // ties at K: the first need_eq in index order
     }
   } else if (ok && uses_lam(form)) {
     // lambda = 0 (phi(0) >= 0) keeps every entry: left to the full pass
@@ -636,22 +811,22 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a, const float *__r
     if (ok) {
       float sw = 0.0f, sw2 = 0.0f;
       unsigned mk = 0u;
-      const Seg sgc = warp_seg(ncand);
-      for (int i = sgc.lo + lane; i < sgc.hi; i += 32) {
+      for (int i = lane; i < ncand; i += 32) {
         const float av = fabsf(cval[i]);
         const float wv2 = av - G;
         sw += wv2;
         sw2 = fmaf(wv2, wv2, sw2);
         mk = max(mk, __float_as_uint(av));
       }
-      int e0 = 0, e1 = 0;
-      block_sum2f(sw, sw2, e0, e1, sh);
-      const uint32_t maxkey = block_max_u(mk, sh.red_u);
+      sw = warp_sum_f(sw);
+      sw2 = warp_sum_f(sw2);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
       ok = (float)a.s * sw2 - sw * sw < 0.0f;   // phi(G) < 0: lambda_s > G
       if (ok) {
         uint32_t lok;
         op.mode = 2;
-        op.gam = lambda_s_bisect(cval, ncand, a.s, Gk, maxkey, sh, &lok);
+        op.gam = warp_lambda_s(cval, ncand, a.s, Gk, mk, &lok);
         op.tkey = lok;
         op.tval = (float)op.gam;
         op.tnext = op.tval;
@@ -660,15 +835,13 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a, const float *__r
   } else if (ok) {  // penalties
     op.mode = uses_U(form) ? 1 : 2;
     if (a.calibrate) {
-      uint32_t tk;
-      int ne, et;
-      bool whole;
-      radix_select(cval, ncand, s_int + 1, true, sh, &tk, &whole, &ne, &et);
+      int gt, eq;
+      const uint32_t tk = warp_select(cval, ncand, s_int + 1, &gt, &eq);   // the (s+1)-th largest
       op.tkey = tk;
       op.tval = __uint_as_float(tk);
       op.gam = uses_U(form) ? (double)op.tval * (double)op.tval : (double)op.tval;
       op.tnext = op.tval;
-      if (threadIdx.x == 0) st.thr[c] = op.tval;
+      if (lane == 0) st.thr[c] = op.tval;
     } else if (a.per_start_thr) {
       op.tval = st.thr[c];
       op.gam = st.gamma[c];
@@ -681,12 +854,12 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a, const float *__r
       op.tnext = st.tprev[c];
     }
   }
-  if (!ok) {   // uniform: every input of ok is a block-wide value
-    if (threadIdx.x == 0) st.xfast[c] = 0;
+  if (!ok) {   // uniform over the warp: every input of ok is a warp- or block-wide value
+    if (lane == 0) st.xfast[c] = 0;
     return;
   }
-  xstep_finish(a, c, cval, ncand, cidx, op, x, st, sup_idx, sup_val, ctrl, sh);
-  if (threadIdx.x == 0) st.xfast[c] = 1;
+  xstep_finish_warp(a, c, cval, ncand, cidx, op, x, st, sup_idx, sup_val, ctrl);
+  if (lane == 0) st.xfast[c] = 1;
 }
 }  // namespace
 
