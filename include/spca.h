@@ -245,6 +245,20 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
                   float *U, int64_t ldu, float *V, int64_t ldv);
 
 /*
+ * spca_deflate -- projection deflation of the handle's matrix for a further component:
+ * A <- A (I - z z^T) with z = x / ||x||_2 (the paper computes several components, Section 1,
+ * without fixing a deflation scheme).  The next spca_solve on the handle then works on the
+ * deflated matrix, so z is not found again.  w = A z is accumulated as compensated FP32 pairs,
+ * each entry updated in FP64 and rounded once to FP32; the transposed copy and the tensor-core
+ * operands are rebuilt.  Synchronous on the handle's stream.
+ *   x            p floats (typically spca_result.x of the last solve), host memory
+ *                (x_is_device = 0) or device memory (x_is_device = 1); need not be normalised.
+ * Errors: SPCA_E_INVALID (NULL pointers, x not finite or zero: A is then unchanged),
+ *         SPCA_E_NOMEM, SPCA_E_CUDA.
+ */
+int spca_deflate(spca_handle *h, const float *x, int x_is_device);
+
+/*
  * Measurement hooks (not part of the method): per-kernel launch counts are always kept;
  * with profiling on, the launches of the selected kernel ids are also bracketed by CUDA
  * events on the handle's stream (each pair costs a few microseconds of host and device time).

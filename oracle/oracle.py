@@ -150,3 +150,15 @@ def solve(A, form: int, G, s: float = 1.0, gamma: float = 0.0, gamma_target: boo
                                 _p(ev), _p(F), _p(iters), _p(status), _p(gam), _p(F_hist),
                                 int(nthreads))
     return Solve(best, X, f, ev, F, iters, status, gam, F_hist[:, :max_iter])
+
+
+def deflate(A, x):
+    """Projection deflation for a further component: A (I - z z^T) with z = x / ||x||_2, in FP64.
+
+    The paper computes several components (Section 1) but leaves the deflation scheme open;
+    projection deflation removes the direction z from every row of A, so that z (and anything
+    it dominated) cannot be found again, and keeps A positive semidefinite as A^T A."""
+    A = np.asarray(A, dtype=np.float64)
+    z = np.asarray(x, dtype=np.float64)
+    z = z / np.linalg.norm(z)
+    return A - np.outer(A @ z, z)

@@ -19,6 +19,7 @@ struct spca_handle {
   cudaStream_t stream = nullptr;
   float *A32 = nullptr, *AT32 = nullptr;   // FP32 copies
   bool tc_ok = false;                      // the device has tcgen05 tensor cores (sm_100+)
+  int sms = 1;                             // streaming multiprocessors of the device
   void *Apl = nullptr, *ATpl = nullptr;    // tensor-core planes (kPlanes FP16 each, row-scaled)
   float *a_scale = nullptr, *a_inv = nullptr;     // row scales of A (n) and their inverses
   float *at_scale = nullptr, *at_inv = nullptr;   // row scales of A^T (p) and their inverses
@@ -53,6 +54,8 @@ struct spca_handle {
   int64_t *support_out = nullptr, *nnz_out = nullptr;
   int *flag = nullptr;        // device scratch flag
   int *dev_err = nullptr;     // device error word written by kernels (SPCA_E_TIMEOUT)
+  float *defl_x = nullptr;    // deflation: the direction (p) ...
+  double *defl_w = nullptr;   // ... and w = A z (n), then 1 / ||x||
   // stream-K scratch of the CTA-pair contraction (one part per resident pair, flags, epoch)
   TcStreamK sk;
   int sk_epoch = 0;
@@ -369,6 +372,28 @@ int read_dev_err(spca_handle *h) {
   return SPCA_OK;
 }
 
+// A^T and the tensor-core operands (row scales, FP16 planes) from the handle's FP32 A
+int build_operands(spca_handle *h) {
+  const int64_t n = h->n, p = h->p;
+  CK(timed(h, SPCA_K_PREP, 1,
+           [&] { return launch_transpose_f32(h->A32, n, p, h->ldA, h->AT32, h->ldAT, h->stream); }));
+  if (!h->tc_ok) return SPCA_OK;
+  CK(timed(h, SPCA_K_PREP, 4, [&] {
+    cudaError_t e = launch_row_scales(h->A32, n, p, h->ldA, h->a_scale, h->a_inv, nullptr, nullptr, nullptr,
+                                      h->stream);
+    if (e == cudaSuccess)
+      e = launch_row_scales(h->AT32, p, n, h->ldAT, h->at_scale, h->at_inv, nullptr, nullptr, nullptr, h->stream);
+    if (e == cudaSuccess)
+      e = launch_split_planes(h->A32, n, h->ldA, h->ldA, h->Apl, h->ldA, n * h->ldA, kPlanes, h->a_scale, 1.0f,
+                              nullptr, nullptr, nullptr, h->stream);
+    if (e == cudaSuccess)
+      e = launch_split_planes(h->AT32, p, h->ldAT, h->ldAT, h->ATpl, h->ldAT, p * h->ldAT, kPlanes, h->at_scale,
+                              1.0f, nullptr, nullptr, nullptr, h->stream);
+    return e;
+  }));
+  return SPCA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -387,6 +412,34 @@ const char *spca_strerror(int status) {
 }
 
 const char *spca_last_error(const spca_handle *h) { return h ? h->last_error : ""; }
+
+int spca_deflate(spca_handle *h, const float *x, int x_is_device) {
+  if (!h || !x) return fail(h, SPCA_E_INVALID, "NULL argument%s");
+  const int64_t n = h->n, p = h->p;
+  cudaStream_t st = h->stream;
+  if (!h->defl_x) {
+    CK(dalloc(&h->defl_x, (size_t)p));
+    CK(dalloc(&h->defl_w, (size_t)n + 1));
+  }
+  CK(cudaMemcpyAsync(h->defl_x, x, (size_t)p * sizeof(float),
+                     x_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  // x must be finite and nonzero
+  CK(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
+  CK(timed(h, SPCA_K_PREP, 1, [&] { return launch_check_finite(h->defl_x, 1, p, p, h->flag, st); }));
+  CK(cudaMemcpyAsync(h->h_flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (*h->h_flag) return fail(h, SPCA_E_INVALID, "x has a non-finite entry%s");
+  CK(timed(h, SPCA_K_PREP, 3, [&] {
+    return launch_deflate(h->A32, h->ldA, (int)n, (int)p, h->defl_x, h->defl_w + n, h->defl_w, h->sms, st);
+  }));
+  double inv = 0.0;
+  CK(cudaMemcpyAsync(&inv, h->defl_w + n, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (!(inv > 0.0)) return fail(h, SPCA_E_INVALID, "x is zero%s");
+  RC(build_operands(h));
+  CK(cudaStreamSynchronize(st));
+  return SPCA_OK;
+}
 
 int spca_profile_enable(spca_handle *h, int mask) {
   if (!h || mask < 0 || mask > SPCA_PROFILE_ALL) return SPCA_E_INVALID;
@@ -422,7 +475,7 @@ void spca_destroy(spca_handle *h) {
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   free_workspace(h);
   void *ptrs[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->a_scale, h->a_inv, h->at_scale, h->at_inv,
-                  h->flag, h->dev_err, h->sk.ws, h->sk.flags};
+                  h->flag, h->dev_err, h->sk.ws, h->sk.flags, h->defl_x, h->defl_w};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
@@ -453,6 +506,7 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     int major = 0;
     CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
     h->tc_ok = major >= 10;
+    CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
     if (storage == SPCA_BF16 && !h->tc_ok) return SPCA_E_UNSUPPORTED;   // the planes need tcgen05
     CK(cudaMallocHost((void **)&h->h_ctrl, 2 * sizeof(Ctrl)));
     CK(cudaMallocHost((void **)&h->h_flag, 2 * sizeof(int)));
@@ -480,31 +534,17 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     CK(timed(h, SPCA_K_PREP, 1, [&] { return launch_check_finite(h->A32, n, p, h->ldA, h->flag, h->stream); }));
     CK(cudaMemcpyAsync(h->h_flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CK(timed(h, SPCA_K_PREP, 1,
-             [&] { return launch_transpose_f32(h->A32, n, p, h->ldA, h->AT32, h->ldAT, h->stream); }));
     if (h->tc_ok) {
       CK(dalloc(&h->Apl, (size_t)kPlanes * n * h->ldA, 2));
       CK(dalloc(&h->ATpl, (size_t)kPlanes * p * h->ldAT, 2));
       CK(dalloc(&h->a_scale, (size_t)n)); CK(dalloc(&h->a_inv, (size_t)n));
       CK(dalloc(&h->at_scale, (size_t)p)); CK(dalloc(&h->at_inv, (size_t)p));
-      CK(timed(h, SPCA_K_PREP, 4, [&] {
-        cudaError_t e = launch_row_scales(h->A32, n, p, h->ldA, h->a_scale, h->a_inv, nullptr, nullptr, nullptr,
-                                          h->stream);
-        if (e == cudaSuccess)
-          e = launch_row_scales(h->AT32, p, n, h->ldAT, h->at_scale, h->at_inv, nullptr, nullptr, nullptr, h->stream);
-        if (e == cudaSuccess)
-          e = launch_split_planes(h->A32, n, h->ldA, h->ldA, h->Apl, h->ldA, n * h->ldA, kPlanes, h->a_scale, 1.0f,
-                                  nullptr, nullptr, nullptr, h->stream);
-        if (e == cudaSuccess)
-          e = launch_split_planes(h->AT32, p, h->ldAT, h->ldAT, h->ATpl, h->ldAT, p * h->ldAT, kPlanes, h->at_scale,
-                                  1.0f, nullptr, nullptr, nullptr, h->stream);
-        return e;
-      }));
+    }
+    RC(build_operands(h));
+    if (h->tc_ok) {
       CK(make_p_maps(&h->pmA, h->Apl, n, h->ldA, kPlanes));
       CK(make_p_maps(&h->pmAT, h->ATpl, p, h->ldAT, kPlanes));
-      int sms = 0;
-      CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      h->sk.slots = sms / 2 > 0 ? sms / 2 : 1;
+      h->sk.slots = h->sms / 2 > 0 ? h->sms / 2 : 1;
       CK(dalloc(&h->sk.ws, (size_t)h->sk.slots * tc_sk_floats_per_slot()));
       CK(dalloc(&h->sk.flags, (size_t)2 * h->sk.slots));
       CK(cudaMemsetAsync(h->sk.flags, 0, (size_t)2 * h->sk.slots * sizeof(int), h->stream));

@@ -123,6 +123,11 @@ cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, fl
                          void *Ypl, int64_t plane_stride, const int *rank, StartState s, float *X,
                          int64_t ldX, int p, cudaStream_t st);
 
+// projection deflation A <- A (I - z z^T), z = x / ||x||_2, in place on the FP32 A (n x p, lda):
+// *inv = 1 / ||x||_2 (0 when x = 0: A is then left as is), w (n doubles) = A z
+cudaError_t launch_deflate(float *A, int64_t lda, int n, int p, const float *x, double *inv, double *w,
+                           int sms, cudaStream_t st);
+
 // ---------------------------------------------------------------- tcgen05 engine
 // Operand format of the tensor-core contractions.  Every FP32 matrix they read is held as two
 // FP16 planes of a power-of-two scaled copy: hi = fp16(s a), lo = fp16(s a - hi), so that

@@ -21,7 +21,7 @@ SPCA_ST_MAXITER, SPCA_ST_CONVERGED, SPCA_ST_DEGENERATE = 0, 1, 2
 SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC = 0, 1, 2
 
 # every symbol include/spca.h declares
-EXPORTS = ("spca_create", "spca_solve", "spca_xstep", "spca_products", "spca_profile_enable",
+EXPORTS = ("spca_create", "spca_solve", "spca_xstep", "spca_products", "spca_deflate", "spca_profile_enable",
            "spca_profile_query", "spca_objective_noalloc",
            "spca_destroy", "spca_strerror", "spca_last_error")
 SPCA_K_ALL, SPCA_K_INIT, SPCA_K_U_DENSE, SPCA_K_U_SPARSE, SPCA_K_YSTEP, SPCA_K_V, SPCA_K_XSTEP, \
@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH):
         lib.spca_objective_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64,
                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                                ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.spca_deflate.restype = ctypes.c_int
+        lib.spca_deflate.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         lib.spca_profile_enable.restype = ctypes.c_int
         lib.spca_profile_enable.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.spca_profile_query.restype = ctypes.c_int
@@ -153,6 +155,15 @@ def spca_objective_noalloc(form, gamma, A, n, p, lda, X, ldx, r, f, ev, stream=0
                                          ctypes.c_void_p(ev), ctypes.c_void_p(stream))
 
 
+def spca_deflate(h, x, x_is_device: bool = False) -> int:
+    """x: p floats, a host numpy array or a device address (int)."""
+    ptr = x if isinstance(x, int) else np.ascontiguousarray(x, dtype=np.float32).ctypes.data
+    keep = None if isinstance(x, int) else np.ascontiguousarray(x, dtype=np.float32)
+    if keep is not None:
+        ptr = keep.ctypes.data
+    return load().spca_deflate(h, ctypes.c_void_p(ptr), int(x_is_device))
+
+
 SPCA_PROFILE_ALL = (1 << 8) - 1
 
 
@@ -197,6 +208,10 @@ class Handle:
             st, h = spca_create(A, n, p, p, dt, False, storage, stream)
         _check(st, "spca_create")
         self.h, self.n, self.p = h, n, p
+
+    def deflate(self, x, x_device: bool = False):
+        """Projection deflation A <- A (I - z z^T), z = x / ||x|| (x: host array or device address)."""
+        _check(spca_deflate(self.h, x, x_device), "spca_deflate", self.h)
 
     def profile(self, on: bool, kernels=None):
         """Time every kernel (on=True), only the given kernel ids, or nothing (on=False)."""
