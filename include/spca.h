@@ -103,7 +103,10 @@ typedef enum {
  *                to 11 significant bits, finer than BF16's 8).  SPCA_BF16 needs tensor cores
  *                (sm_100+) and SPCA_FP8_E4M3_COLSCALED is not built: both return
  *                SPCA_E_UNSUPPORTED otherwise.
- *   cuda_stream  cudaStream_t the handle uses (NULL = the legacy default stream).
+ *   cuda_stream  the caller's cudaStream_t (NULL = the legacy default stream): every call on
+ *                the handle starts after the work queued on it before the call and returns with
+ *                its own work complete.  The handle runs its kernels on a stream of its own, so
+ *                that the sweeps of a solve can be captured into CUDA graphs and replayed.
  * Errors: SPCA_E_INVALID (NULL pointers, n < 1, p < 1, lda < p, A not finite, unknown dtype),
  *         SPCA_E_UNSUPPORTED, SPCA_E_NOMEM, SPCA_E_CUDA.
  */

@@ -320,7 +320,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // A slot walks its range as segments, one per tile it touches; a segment is a whole tile (its
 // epilogue writes the output), the first K-blocks of a tile (the slot then owns the tile), or a
 // later part of one (the slot's first segment: it writes the partial to its workspace slot and
-// publishes a flag).  An owner's part is the last segment of its range, so by then the later
+// publishes a flag, set to `epoch` = 1; the flags are zeroed before every launch).  An owner's
+// part is the last segment of its range, so by then the later
 // parts, which other slots compute first, are mostly done: it waits for their flags (bounded),
 // adds them in slot order and writes the tile.  The TMEM accumulators are reused from segment to
 // segment: the epilogue of both CTAs releases them before the leader's next MMA.
@@ -775,9 +776,12 @@ cudaError_t launch_tc2_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, 
   int S = max_pairs < sk.slots ? max_pairs : sk.slots;
   if (units < S) S = (int)(units > 0 ? units : 1);
   cfg.gridDim = dim3((unsigned)(2 * S), 1);
-  const int epoch = ++(*sk.epoch);
+  // the flags of the parts start at 0 for every launch (a memset, so that a launch replayed from a
+  // CUDA graph does not see the parts of the previous replay); a published part sets its flag to 1
+  cudaError_t e = cudaMemsetAsync(sk.flags, 0, (size_t)2 * S * sizeof(int), st);
+  if (e != cudaSuccess) return e;
   return cudaLaunchKernelEx(&cfg, kern, P.m[0], Q, M, N, kblocks, k_dev, pairs, out, ldo, row_inv, col_inv, q_inv,
-                            gate, n_dev, col_map, err, sk.ws, sk.flags, epoch);
+                            gate, n_dev, col_map, err, sk.ws, sk.flags, 1);
 }
 }  // namespace
 
@@ -825,7 +829,7 @@ cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb,
                            const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const float *row_inv,
                            const float *col_inv, float q_inv, const int *gate, const int *n_dev, const int *col_map,
                            int *err, const TcStreamK &sk, cudaStream_t st) {
-  if (M <= TC_BM || !sk.ws || !sk.flags || !sk.epoch || sk.slots < 1)
+  if (M <= TC_BM || !sk.ws || !sk.flags || sk.slots < 1)
     return launch_gemm_tc_single(P, na, Q, nb, M, N, K, k_dev, pairs, out, ldo, row_inv, col_inv, q_inv, gate,
                                  n_dev, col_map, err, st);
   if (na == 2 && nb == 2)   // two general operands

@@ -2,6 +2,7 @@
 // the kernels read), the solve driver that runs Algorithm 2 for r starts as a sequence of
 // kernels on one stream, and the step-level entry points (x-step, sweep products).
 #include <algorithm>
+#include <tuple>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -13,10 +14,21 @@
 
 using namespace spca;
 
+// one captured segment of sweeps: the plan it was captured for, the executable graph, and the
+// launch counts and timing events of its kernels
+struct SegGraph {
+  std::vector<int> key;
+  cudaGraphExec_t exec = nullptr;
+  int64_t counts[SPCA_K_COUNT] = {0};
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> timings;
+};
+
 struct spca_handle {
   int64_t n = 0, p = 0;
   int64_t ldA = 0, ldAT = 0;  // padded leading dimensions of A (n x p) and A^T (p x n)
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;   // the handle's own non-blocking stream (all its work)
+  cudaStream_t user = nullptr;     // the caller's stream: each call starts after its prior work
+  cudaEvent_t order_ev = nullptr;
   float *A32 = nullptr, *AT32 = nullptr;   // FP32 copies
   bool tc_ok = false;                      // the device has tcgen05 tensor cores (sm_100+)
   int sms = 1;                             // streaming multiprocessors of the device
@@ -56,9 +68,8 @@ struct spca_handle {
   int *dev_err = nullptr;     // device error word written by kernels (SPCA_E_TIMEOUT)
   float *defl_x = nullptr;    // deflation: the direction (p) ...
   double *defl_w = nullptr;   // ... and w = A z (n), then 1 / ||x||
-  // stream-K scratch of the CTA-pair contraction (one part per resident pair, flags, epoch)
+  // stream-K scratch of the CTA-pair contraction (one part per resident pair, flags)
   TcStreamK sk;
-  int sk_epoch = 0;
   Ctrl *h_ctrl = nullptr;     // pinned host mirror
   int *h_flag = nullptr;      // pinned host mirror (2 ints)
 
@@ -68,6 +79,15 @@ struct spca_handle {
   double ms[SPCA_K_COUNT] = {0};
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[SPCA_K_COUNT];
   std::vector<cudaEvent_t> event_pool;
+  // graph replay of sweep segments (the sweeps between two read-backs of the control word):
+  // while a segment is captured, launch counts and timing events go to the capture's lists and
+  // are charged every time the graph runs
+  bool capturing = false;
+  int64_t cap_counts[SPCA_K_COUNT] = {0};
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> cap_timings;
+  std::vector<SegGraph> graphs;          // captured segments (see spca_solve)
+  int ws_gen = 0, graph_gen = 0;          // workspace generation the graphs were captured with
+  unsigned graph_prof = 0u;               // and the profiling selection
 
   char last_error[256] = {0};
 };
@@ -107,14 +127,39 @@ cudaEvent_t get_event(spca_handle *h) {
 // runs `launch` (which enqueues `nk` kernels of kind `kid`), counting and optionally timing it
 template <typename Fn>
 cudaError_t timed(spca_handle *h, int kid, int nk, Fn &&launch) {
-  h->launches[kid] += nk;
+  if (h->capturing) h->cap_counts[kid] += nk;
+  else h->launches[kid] += nk;
   if (!(h->prof_mask & (1u << kid))) return launch();
   cudaEvent_t a = get_event(h), b = get_event(h);
-  cudaEventRecord(a, h->stream);
-  cudaError_t e = launch();
-  cudaEventRecord(b, h->stream);
-  h->pending[kid].push_back({a, b});
+  // under stream capture an event must be an external record node to be timed after replays
+  const unsigned flags = h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  cudaError_t e = cudaEventRecordWithFlags(a, h->stream, flags);
+  if (e != cudaSuccess) return e;
+  e = launch();
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecordWithFlags(b, h->stream, flags);
+  if (h->capturing) h->cap_timings.emplace_back(kid, a, b);
+  else h->pending[kid].push_back({a, b});
   return e;
+}
+
+
+void release_graphs(spca_handle *h) {
+  for (SegGraph &g : h->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto &t : g.timings) {
+      h->event_pool.push_back(std::get<1>(t));
+      h->event_pool.push_back(std::get<2>(t));
+    }
+  }
+  h->graphs.clear();
+}
+
+// each call's work on the handle's stream starts after the work the caller queued before it
+int enter(spca_handle *h) {
+  CK(cudaEventRecord(h->order_ev, h->user));
+  CK(cudaStreamWaitEvent(h->stream, h->order_ev, 0));
+  return SPCA_OK;
 }
 
 cudaError_t drain_profile(spca_handle *h) {
@@ -165,6 +210,8 @@ constexpr int kUnionTry = 16;
 
 int ensure_workspace(spca_handle *h, int r) {
   if (r <= h->r_cap) return SPCA_OK;
+  release_graphs(h);   // they hold pointers into the workspace
+  ++h->ws_gen;
   free_workspace(h);
   const int64_t n = h->n, p = h->p;
   h->ldX = pad_ld(p);
@@ -415,6 +462,7 @@ const char *spca_last_error(const spca_handle *h) { return h ? h->last_error : "
 
 int spca_deflate(spca_handle *h, const float *x, int x_is_device) {
   if (!h || !x) return fail(h, SPCA_E_INVALID, "NULL argument%s");
+  RC(enter(h));
   const int64_t n = h->n, p = h->p;
   cudaStream_t st = h->stream;
   if (!h->defl_x) {
@@ -470,7 +518,8 @@ int spca_profile_query(spca_handle *h, int kernel, int64_t *launches, double *ms
 
 void spca_destroy(spca_handle *h) {
   if (!h) return;
-  cudaStreamSynchronize(h->stream);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  release_graphs(h);
   drain_profile(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   free_workspace(h);
@@ -480,6 +529,8 @@ void spca_destroy(spca_handle *h) {
     if (q) cudaFree(q);
   if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
   if (h->h_flag) cudaFreeHost(h->h_flag);
+  if (h->order_ev) cudaEventDestroy(h->order_ev);
+  if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
 
@@ -500,7 +551,10 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
   if (!h) return SPCA_E_NOMEM;
   int rc = [&]() -> int {
     h->n = n; h->p = p;
-    h->stream = (cudaStream_t)cuda_stream;
+    h->user = (cudaStream_t)cuda_stream;
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming));
+    RC(enter(h));
     h->ldA = pad_ld(p);
     h->ldAT = pad_ld(n);
     int major = 0;
@@ -548,7 +602,6 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
       CK(dalloc(&h->sk.ws, (size_t)h->sk.slots * tc_sk_floats_per_slot()));
       CK(dalloc(&h->sk.flags, (size_t)2 * h->sk.slots));
       CK(cudaMemsetAsync(h->sk.flags, 0, (size_t)2 * h->sk.slots * sizeof(int), h->stream));
-      h->sk.epoch = &h->sk_epoch;
     }
     CK(cudaStreamSynchronize(h->stream));
     if (*h->h_flag) return fail(h, SPCA_E_INVALID, "A has a non-finite entry%s");
@@ -577,6 +630,7 @@ int spca_xstep(spca_handle *h, int form, double s, double gamma, int calibrate, 
   a.cap = 0; a.sparse_cap = (int)h->p;
   StartState st{};
   st.nnz = nnz; st.F = F; st.gamma = thr;
+  RC(enter(h));
   CK(timed(h, SPCA_K_XSTEP, 1,
            [&] { return launch_xstep(a, V, ldv, r, X, ldx, st, nullptr, nullptr, nullptr, h->stream); }));
   CK(cudaStreamSynchronize(h->stream));
@@ -590,6 +644,7 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
   if (ldx < h->p || ldv < h->p || ldu < h->n) return fail(h, SPCA_E_INVALID, "leading dimension too small%s");
   int eng;
   RC(resolve_engine(h, engine, &eng));
+  RC(enter(h));
   RC(ensure_workspace(h, r));
   const int n = (int)h->n, p = (int)h->p;
   cudaStream_t st = h->stream;
@@ -624,6 +679,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   RC(resolve_engine(h, P.engine, &engine));
   if (P.lowp_sweeps > 0 && engine != SPCA_ENGINE_TC)
     return fail(h, SPCA_E_UNSUPPORTED, "low-precision sweeps need the tensor-core engine%s");
+  RC(enter(h));
   const auto t_start = std::chrono::steady_clock::now();
   const int L = P.lowp_sweeps;
   const int max_iter = P.refine_sweeps > 0 ? (int)std::min<int64_t>(P.max_iter, (int64_t)L + P.refine_sweeps)
@@ -681,54 +737,149 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   const int sparse_cap = xa.sparse_cap;
   int64_t max_nnz = uses_T(form) ? std::min<int64_t>((int64_t)P.s, p) : p;
   bool dense_queued = true;   // x^(0) is dense
-  for (int k = 1; k <= max_iter; ++k) {
-    Ctrl *cur = h->ctrl + ((k - 1) & 1), *nxt = h->ctrl + (k & 1);
-    // the first L sweeps read the leading FP16 planes only (A rounded to 11 significant bits)
-    const bool lowp = k <= L;
+  // The sweeps are queued in segments that end at a read-back (every check_every sweeps).  A
+  // segment's host decisions (the plan: which optional launches, the x-step's switches) are made
+  // up front from the last read-back; its kernels are captured into a CUDA graph once per distinct
+  // plan and replayed, so that in steady state a segment is one launch.
+  struct SweepPlan {
+    int k;
+    bool lowp, dense_in, union_in, union_out, calibrate, per_start_thr, stop_test;
+    int sparse_cap;
+  };
+  auto enqueue = [&](const SweepPlan &pl) -> int {
+    Ctrl *cur = h->ctrl + ((pl.k - 1) & 1), *nxt = h->ctrl + (pl.k & 1);
     // u = A x: over the union of the supports when it is small (tensor cores), else the dense
     // contraction, or the per-start support gather when every support is small
-    if (dense_queued) RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, nhost, lowp));
-    if (union_built) RC(sweep_u_union(h, S, cur, nhost));
+    if (pl.dense_in) RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, r, pl.lowp));
+    if (pl.union_in) RC(sweep_u_union(h, S, cur, r));
     CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
-      if (lowp)
+      if (pl.lowp)
         return launch_gemm1_sparse_lowp(h->ATpl, h->ldAT, h->at_inv, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
                                         &cur->use_gather, st);
       return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
                                  &cur->use_gather, st);
     }));
     // y-step, v = A^T y
-    RC(sweep_y_v(h, engine, form, r, S, &cur->active, nhost, lowp));
+    RC(sweep_y_v(h, engine, form, r, S, &cur->active, r, pl.lowp));
     CK(cudaMemsetAsync(nxt, 0, sizeof(Ctrl), st));
-    xa.calibrate = target && k <= C;
-    xa.per_start_thr = target && k > C;
-    // the stopping rule compares two FP32 sweeps
-    xa.stop_test = P.tol >= 0.0 && k >= 2 && k >= C + 1 && k >= L + 2;
-    dense_queued = max_nnz > sparse_cap / 2;
-    xa.sparse_cap = dense_queued ? sparse_cap : p;   // p: the gather for every support
+    XstepArgs xk = xa;
+    xk.calibrate = pl.calibrate;
+    xk.per_start_thr = pl.per_start_thr;
+    xk.stop_test = pl.stop_test;
+    xk.sparse_cap = pl.sparse_cap;
     CK(timed(h, SPCA_K_XSTEP, 3, [&] {   // candidate x-step, full x-step, active list
-      cudaError_t e = launch_xstep(xa, h->V, h->ldX, r, h->X, h->ldX, S, h->sup_idx, h->sup_val, nxt, st);
+      cudaError_t e = launch_xstep(xk, h->V, h->ldX, r, h->X, h->ldX, S, h->sup_idx, h->sup_val, nxt, st);
       if (e != cudaSuccess) return e;
       return launch_active_list(h->status, h->nnz, r, h->act, h->rank, nxt, st);   // for the next sweep
     }));
-    union_built = engine == SPCA_ENGINE_TC && k + 1 > L && sum_nnz <= (int64_t)kUnionTry * h->kcap;
-    if (union_built) {
+    if (pl.union_out) {
       CK(timed(h, SPCA_K_U_SPARSE, 2, [&] {
         return launch_union(h->sup_idx, p, S, r, p, h->mark, h->colpos, h->collist, h->kcap, nxt, st);
       }));
     }
-    if (k == max_iter || k % check_every == 0) {
-      CK(cudaMemcpyAsync(h->h_ctrl, nxt, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      if (h->h_ctrl->active == 0) break;
-      if (P.timeout_us > 0 &&
-          std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t_start)
-                  .count() > P.timeout_us)
-        return fail(h, SPCA_E_TIMEOUT, "the solve ran past timeout_us%s");
-      nhost = h->h_ctrl->active;   // counts only fall: any earlier value stays an upper bound
-      sum_nnz = h->h_ctrl->sum_nnz;
-      max_nnz = h->h_ctrl->max_nnz;
-    }
+    return SPCA_OK;
+  };
+  // captured segments live in the handle and are reused by later solves with the same
+  // parameters (every argument their kernels were captured with is in the key)
+  std::vector<SegGraph> &graphs = h->graphs;
+  if (h->graph_gen != h->ws_gen || h->graph_prof != h->prof_mask) {
+    release_graphs(h);
+    h->graph_gen = h->ws_gen;
+    h->graph_prof = h->prof_mask;
   }
+  if (graphs.size() > 64) release_graphs(h);
+  auto bits = [](double d) {
+    int64_t b;
+    memcpy(&b, &d, sizeof b);
+    return b;
+  };
+  const std::vector<int> solve_key = {form, engine, r, max_iter, C, L, (int)target,
+                                      (int)(bits(P.s) & 0xffffffff), (int)(bits(P.s) >> 32),
+                                      (int)(bits(P.gamma) & 0xffffffff), (int)(bits(P.gamma) >> 32),
+                                      (int)(bits(P.tol) & 0xffffffff), (int)(bits(P.tol) >> 32)};
+  std::vector<SweepPlan> plans;
+  std::vector<int> key;
+  int rc = SPCA_OK;
+  for (int k0 = 1; k0 <= max_iter && rc == SPCA_OK;) {
+    const int k1 = std::min(max_iter, (k0 + check_every - 1) / check_every * check_every);
+    plans.clear();
+    key = solve_key;
+    key.insert(key.end(), {k0 & 1, k1 - k0});
+    for (int k = k0; k <= k1; ++k) {
+      SweepPlan pl{};
+      pl.k = k;
+      // the first L sweeps read the leading FP16 planes only (A rounded to 11 significant bits)
+      pl.lowp = k <= L;
+      pl.dense_in = dense_queued;
+      pl.union_in = union_built;
+      pl.calibrate = target && k <= C;
+      pl.per_start_thr = target && k > C;
+      // the stopping rule compares two FP32 sweeps
+      pl.stop_test = P.tol >= 0.0 && k >= 2 && k >= C + 1 && k >= L + 2;
+      dense_queued = max_nnz > sparse_cap / 2;
+      pl.sparse_cap = dense_queued ? sparse_cap : p;   // p: the gather for every support
+      union_built = engine == SPCA_ENGINE_TC && k + 1 > L && sum_nnz <= (int64_t)kUnionTry * h->kcap;
+      pl.union_out = union_built;
+      plans.push_back(pl);
+      key.insert(key.end(), {pl.lowp, pl.dense_in, pl.union_in, pl.union_out, pl.calibrate, pl.per_start_thr,
+                             pl.stop_test, pl.sparse_cap});
+    }
+    SegGraph *g = nullptr;
+    for (SegGraph &c : graphs)
+      if (c.key == key) g = &c;
+    if (!g) {
+      // capture this plan's kernels (relaxed mode: the launchers may set function attributes)
+      graphs.emplace_back();
+      g = &graphs.back();
+      g->key = key;
+      h->capturing = true;
+      std::fill(std::begin(h->cap_counts), std::end(h->cap_counts), 0);
+      h->cap_timings.clear();
+      cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+      if (ce == cudaSuccess) {
+        for (const SweepPlan &pl : plans)
+          if ((rc = enqueue(pl)) != SPCA_OK) break;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(st, &graph);
+        if (ce == cudaSuccess) ce = ee;
+        if (ce == cudaSuccess && rc == SPCA_OK) ce = cudaGraphInstantiate(&g->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+      }
+      h->capturing = false;
+      std::copy(std::begin(h->cap_counts), std::end(h->cap_counts), std::begin(g->counts));
+      g->timings.swap(h->cap_timings);
+      if (rc == SPCA_OK && ce != cudaSuccess) rc = fail(h, SPCA_E_CUDA, "CUDA error: %s", cudaGetErrorString(ce));
+      if (rc != SPCA_OK) break;
+    }
+    if (cudaGraphLaunch(g->exec, st) != cudaSuccess) {
+      rc = fail(h, SPCA_E_CUDA, "CUDA error: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    for (int q = 0; q < SPCA_K_COUNT; ++q) h->launches[q] += g->counts[q];
+    Ctrl *last = h->ctrl + (k1 & 1);
+    if (cudaMemcpyAsync(h->h_ctrl, last, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      rc = fail(h, SPCA_E_CUDA, "CUDA error: %s", cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    for (auto &t : g->timings) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, std::get<1>(t), std::get<2>(t));
+      h->ms[std::get<0>(t)] += ms;
+    }
+    if (h->h_ctrl->active == 0) break;
+    if (P.timeout_us > 0 &&
+        std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t_start).count() >
+            P.timeout_us) {
+      rc = fail(h, SPCA_E_TIMEOUT, "the solve ran past timeout_us%s");
+      break;
+    }
+    nhost = h->h_ctrl->active;   // counts only fall: any earlier value stays an upper bound
+    sum_nnz = h->h_ctrl->sum_nnz;
+    max_nnz = h->h_ctrl->max_nnz;
+    k0 = k1 + 1;
+  }
+  RC(rc);
   RC(read_dev_err(h));
 
   // ---- a7: FP64 objective, best start, y(x) and support of the best x

@@ -167,14 +167,13 @@ cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld,
 // col_map when given, else the identity.  With gate != nullptr nothing runs unless *gate != 0;
 // a timed-out wait sets *err = SPCA_E_TIMEOUT
 // (K from *k_dev when k_dev != nullptr, K being then only an upper bound)
-// Stream-K scratch of the CTA-pair contraction: `slots` parts of tc_sk_floats_per_slot() floats,
-// 2 flags per slot (zeroed once), and the host-side launch counter the flags are compared with.
-// Without it (ws == nullptr) the single-CTA kernel runs.
+// Stream-K scratch of the CTA-pair contraction: `slots` parts of tc_sk_floats_per_slot() floats
+// and 2 flags per slot (zeroed by every launch).  Without it (ws == nullptr) the single-CTA kernel
+// runs.
 struct TcStreamK {
   float *ws = nullptr;
   int *flags = nullptr;
   int slots = 0;
-  int *epoch = nullptr;
 };
 int64_t tc_sk_floats_per_slot();
 cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
