@@ -375,6 +375,58 @@ def reduce_sum(val, world):
     return _reduce(val, world, _dist.ReduceOp.SUM if _dist else None)
 
 
+# ---------------------------------------------------------------------------- shape scan
+# The paper's GPU comparison (Section 5) on synthetic shapes: L1 variance with the L1 penalty
+# (formulation 8), n = p / 200, p from 10^3 to 10^5, r in {1, 16, 256} starts; N(0,1) data, gamma
+# by the Section 4.1 rule targeting 10 nonzeros, at most 100 sweeps, tol 1e-9.  Per shape: the
+# GPU's sweeps*starts/s and single-solve latency, and the FP64 oracle's rate on the host cores on
+# a bounded sample (its speedup is the ratio of the two).
+SCAN_SHAPES = [(p, r) for p in (1000, 10000, 100000) for r in (1, 16, 256)]
+
+
+def run_scan(args):
+    import torch
+
+    from oracle import oracle
+    from paper_1212_4137_gb300 import build, inputs as I, spca
+    build.build()
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    kw = dict(s=10.0, gamma_target=True, calib=10, max_iter=100, tol=1e-9)
+    for p, r in SCAN_SHAPES:
+        n = p // 200
+        A = I.gaussian_matrix(n, p, 900 + p).astype(np.float32)
+        G = I.raw_starts(p, r, 901).astype(np.float32)
+        Ad, Gd = torch.from_numpy(A).to(dev), torch.from_numpy(G).to(dev)
+        h = spca.Handle(Ad, stream=stream.cuda_stream)
+        for _ in range(args.warmup):
+            h.solve(8, r, x0=Gd.data_ptr(), x0_device=True, **kw)
+        lat, sweeps = [], 0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            t1 = time.perf_counter()
+            sweeps += h.solve(8, r, x0=Gd.data_ptr(), x0_device=True, **kw)["sweeps_total"]
+            lat.append(1e3 * (time.perf_counter() - t1))
+        dt = time.perf_counter() - t0
+        h.close()
+        # the oracle on a bounded sample: up to 16 starts, up to 20 sweeps
+        ks, kk = min(r, 16), 20
+        t1 = time.perf_counter()
+        ref = oracle.solve(A.astype(np.float64), 8, G[:ks].astype(np.float64), s=10.0, gamma_target=True,
+                           calib=10, max_iter=kk, tol=-1)
+        odt = time.perf_counter() - t1
+        gpu_rate, cpu_rate = sweeps / dt, int(ref.iters.sum()) / odt
+        print(json.dumps({"scan": "L1-var L1-pen (formulation 8), n = p/200", "n": n, "p": p, "r": r,
+                          "sweeps_starts_per_s": round(gpu_rate, 1), "solves_per_s": round(args.steps / dt, 2),
+                          "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                                         "p99": round(float(np.percentile(lat, 99)), 3)},
+                          "oracle_sweeps_starts_per_s": round(cpu_rate, 1), "oracle_cores": oracle.num_threads(),
+                          "oracle_sample": f"{ks} starts x {kk} sweeps", "speedup": round(gpu_rate / cpu_rate, 1)}),
+              flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -386,7 +438,12 @@ def main():
     # for profiler captures: a subset of the formulations, no end-to-end pass
     ap.add_argument("--forms", type=str, default=None, help="comma-separated formulations (default: all 8)")
     ap.add_argument("--no-e2e", action="store_true")
+    # the paper's shape scan (one JSON line per shape) instead of the benchmark line
+    ap.add_argument("--scan", choices=("paper-shapes",), default=None)
     args = ap.parse_args()
+    if args.scan:
+        run_scan(args)
+        return
     rank, world, local = init_dist()
     w = dict(WORKLOADS[args.workload])
     if args.forms:
