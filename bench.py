@@ -43,6 +43,13 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "spiked-5000x20000-r1024"
 
+# DRAM traffic of one v = A^T y launch of the tensor-core contraction at the spiked workload's size
+# with 1024 active starts (dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture: 479.8 MB
+# + 82.3 MB), and the algorithmic bytes of that launch: two FP16 planes of A^T (400 MB), two of Y
+# (20.5 MB), V written once (81.9 MB)
+V_TRAFFIC_BYTES = 562.0e6
+V_ALG_BYTES = 502.4e6
+
 # peak of the FP32 CUDA-core pipe: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz
 SIMT_FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -238,7 +245,12 @@ def run_ours(args, w, rank, world, local_rank):
         alg = 2.0 * n * p * sweeps / (vstats["ms"] / 1e3) / 1e12
         roof = {"kernel": "v = A^T y (k_gemm_tc2: tcgen05 FP16 x2-plane, FP32 accumulate)", "bound": "tensor",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4),
+                # DRAM read + write of one launch from an ncu capture of this kernel (the first
+                # v = A^T y of formulation 1: N = 1024 active starts, three plane products),
+                # against its algorithmic bytes (A planes once, Y planes, V written once)
+                "traffic": V_TRAFFIC_BYTES, "traffic_note": "bytes per launch, N = 1024 launch (ncu)",
+                "algorithmic_bytes_same_launch": V_ALG_BYTES,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; FP16 and BF16 dense rates are equal)",
                 "per_unit": "2*n*p*(2 plane products for L1 variance, 3 for L2 variance) FP16 flop per sweep*start (active starts only)",
                 "launches": vstats["launches"], "avg_launch_ms": round(vstats["ms"] / max(1, vstats["launches"]), 4),
