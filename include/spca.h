@@ -144,6 +144,13 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
  *   timeout_us          wall-clock limit of the solve in microseconds (0 = none), checked
  *                       each time the host reads the active count back (every 4 sweeps):
  *                       past it the solve returns SPCA_E_TIMEOUT and writes no result.
+ *   total_starts        on-the-fly replacement (Section 4.3): with total_starts > r the solve
+ *                       runs total_starts starts through r slots, a slot taking the next start
+ *                       (in index order) in the sweep its start stops; x0 then holds
+ *                       total_starts rows (the seeded start c is normal numbers c*p + j), the
+ *                       start_* outputs hold total_starts entries, and max_iter bounds each
+ *                       start's sweeps.  0 (or <= r) = all r starts at once.  Not combined with
+ *                       lowp_sweeps (SPCA_E_UNSUPPORTED).
  */
 typedef struct {
     int form;
@@ -160,6 +167,7 @@ typedef struct {
     int lowp_sweeps;
     int refine_sweeps;
     int64_t timeout_us;
+    int total_starts;
 } spca_params;
 
 /*
@@ -175,8 +183,9 @@ typedef struct {
  *   x [p], y [n]         the best start's normalised x and y = y(x) (S1 or S2 of Table 3).
  *   support [p]          indices of the nonzeros of x, ascending; nnz entries are written.
  *   start_* [r]          per-start objective, explained variance, last F value, sweeps,
- *                        status (spca_start_status), final gamma.
- *   start_x [r*p]        every start's final x, one per row.
+ *                        status (spca_start_status), final gamma ([total_starts] with
+ *                        on-the-fly replacement).
+ *   start_x [r*p]        every start's final x, one per row ([total_starts*p] likewise).
  */
 typedef struct {
     double objective;

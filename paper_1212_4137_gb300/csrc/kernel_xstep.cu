@@ -395,7 +395,7 @@ __device__ void xstep_finish(const XstepArgs &a, int c, const float *vv, int len
 // Every pass over all p entries of v (staged in shared memory when it fits).  Starts that the
 // candidate kernel below already finished in this sweep are skipped.
 template <bool kSmem>
-__global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restrict__ V, int64_t ldv,
+__global__ void __launch_bounds__(XT) k_xstep(XstepArgs a_in, const float *__restrict__ V, int64_t ldv,
                                               float *__restrict__ X, int64_t ldx, StartState st,
                                               int *__restrict__ sup_idx, float *__restrict__ sup_val,
                                               Ctrl *ctrl) {
@@ -404,6 +404,7 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a, const float *__restri
   const int c = blockIdx.x;
   if (st.status && st.status[c] != ST_ACTIVE) return;
   if (st.xfast && st.xfast[c]) return;
+  const XstepArgs a = xstep_switches(a_in, st.iters, c);
   const int p = a.p;
   const int lane = threadIdx.x & 31;
   const float *vg = V + (int64_t)c * ldv;
@@ -673,7 +674,7 @@ constexpr int kCandW = 64;               // candidates per warp
 constexpr int kCand = kCandW * XW;       // per start
 constexpr float kGuess = 0.85f;
 
-__global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a, const float *__restrict__ V, int64_t ldv,
+__global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a_in, const float *__restrict__ V, int64_t ldv,
                                                    float *__restrict__ X, int64_t ldx, StartState st,
                                                    int *__restrict__ sup_idx, float *__restrict__ sup_val,
                                                    Ctrl *ctrl) {
@@ -685,6 +686,7 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a, const float *__r
   __shared__ int fail_s;
   const int c = blockIdx.x;
   if (st.status[c] != ST_ACTIVE) return;
+  const XstepArgs a = xstep_switches(a_in, st.iters, c);
   const int p = a.p, form = a.form;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int s_int = (int)a.s;

@@ -105,14 +105,19 @@ __device__ __forceinline__ double bm_normal(uint64_t key, uint64_t i) {
 // Algorithm 2, "select initial point": x^(0) = g / ||g||_2 per start (block per start).
 __global__ void __launch_bounds__(256) k_start_init(const float *__restrict__ x0, int64_t ld0,
                                                     uint64_t key, int p, float *__restrict__ X,
-                                                    int64_t ldX, StartState s, double gamma0) {
+                                                    int64_t ldX, StartState s, double gamma0,
+                                                    const int *__restrict__ slot_list,
+                                                    const int *__restrict__ slot_start,
+                                                    const int *__restrict__ count) {
   __shared__ float redf[32];
-  const int c = blockIdx.x;
+  if (slot_list && (int)blockIdx.x >= *count) return;
+  const int c = slot_list ? slot_list[blockIdx.x] : (int)blockIdx.x;   // the slot (row of X)
+  const int64_t start = slot_list ? slot_start[c] : c;                 // the start it takes
   float *x = X + (int64_t)c * ldX;
-  const float *g = x0 ? x0 + (int64_t)c * ld0 : nullptr;
+  const float *g = x0 ? x0 + start * ld0 : nullptr;
   float part = 0.0f;
   for (int j = threadIdx.x; j < p; j += blockDim.x) {
-    const float gj = g ? g[j] : (float)bm_normal(key, (uint64_t)c * (uint64_t)p + (uint64_t)j);
+    const float gj = g ? g[j] : (float)bm_normal(key, (uint64_t)start * (uint64_t)p + (uint64_t)j);
     x[j] = gj;
     part = fmaf(gj, gj, part);
   }
@@ -132,7 +137,8 @@ __global__ void __launch_bounds__(256) k_start_init(const float *__restrict__ x0
 }
 
 cudaError_t launch_start_init(const float *x0, int64_t ld0, uint64_t seed, int r, int p, float *X,
-                              int64_t ldX, StartState s, double gamma0, cudaStream_t st) {
+                              int64_t ldX, StartState s, double gamma0, const int *slot_list,
+                              const int *slot_start, const int *count, cudaStream_t st) {
   // key = mix(seed ^ mix(stream)), stream 5 = starts (same definition as the host generator)
   auto mixh = [](uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -140,7 +146,7 @@ cudaError_t launch_start_init(const float *x0, int64_t ld0, uint64_t seed, int r
     return z ^ (z >> 31);
   };
   const uint64_t key = mixh(seed ^ mixh(5ull));
-  k_start_init<<<r, 256, 0, st>>>(x0, ld0, key, p, X, ldX, s, gamma0);
+  k_start_init<<<r, 256, 0, st>>>(x0, ld0, key, p, X, ldX, s, gamma0, slot_list, slot_start, count);
   return cudaGetLastError();
 }
 
@@ -344,6 +350,7 @@ __global__ void __launch_bounds__(256) k_gemm1_sparse(const float *__restrict__ 
   if (*gate == 0) return;
   const int c = blockIdx.y;
   if (s.status[c] != ST_ACTIVE) return;
+  if (s.iters[c] == 0) return;   // a start not swept yet has a dense x: the dense contraction
   __shared__ int sidx[256];
   __shared__ float sval[256];
   const int nnz = s.nnz[c];

@@ -66,6 +66,14 @@ struct spca_handle {
   int64_t *support_out = nullptr, *nnz_out = nullptr;
   int *flag = nullptr;        // device scratch flag
   int *dev_err = nullptr;     // device error word written by kernels (SPCA_E_TIMEOUT)
+  // on-the-fly replacement (grown on demand): the archive of the starts' results, the slots'
+  // starts, the next start, the stopped / refilled slot lists, and a device copy of host x0
+  int otf_l = 0, otf_r = 0;
+  OtfArchive arc{};
+  double *otf_partials = nullptr;
+  int *slot_start = nullptr, *next_start = nullptr, *retire_slot = nullptr, *retire_start = nullptr;
+  int *new_slot = nullptr;
+  float *otf_x0 = nullptr;
   float *defl_x = nullptr;    // deflation: the direction (p) ...
   double *defl_w = nullptr;   // ... and w = A z (n), then 1 / ||x||
   // stream-K scratch of the CTA-pair contraction (one part per resident pair, flags)
@@ -258,6 +266,39 @@ int ensure_workspace(spca_handle *h, int r) {
   return SPCA_OK;
 }
 
+void free_otf(spca_handle *h) {
+  void *ptrs[] = {h->arc.x, h->arc.U, h->arc.F, h->arc.gamma, h->arc.f, h->arc.ev, h->arc.iters, h->arc.status,
+                  h->arc.nnz, h->otf_partials, h->slot_start, h->next_start, h->retire_slot, h->retire_start,
+                  h->new_slot, h->otf_x0};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+  h->arc = OtfArchive{};
+  h->otf_partials = nullptr;
+  h->slot_start = h->next_start = h->retire_slot = h->retire_start = h->new_slot = nullptr;
+  h->otf_x0 = nullptr;
+  h->otf_l = h->otf_r = 0;
+}
+
+// the on-the-fly replacement's buffers for l starts through r slots
+int ensure_otf(spca_handle *h, int l, int r) {
+  if (l <= h->otf_l && r <= h->otf_r) return SPCA_OK;
+  release_graphs(h);   // they hold pointers into these buffers
+  ++h->ws_gen;
+  free_otf(h);
+  const int64_t n = h->n, p = h->p;
+  CK(dalloc(&h->arc.x, (size_t)l * h->ldX));
+  CK(dalloc(&h->arc.U, (size_t)l * h->ldU));
+  CK(dalloc(&h->arc.F, l)); CK(dalloc(&h->arc.gamma, l)); CK(dalloc(&h->arc.f, l)); CK(dalloc(&h->arc.ev, l));
+  CK(dalloc(&h->arc.iters, l)); CK(dalloc(&h->arc.status, l)); CK(dalloc(&h->arc.nnz, l));
+  CK(dalloc(&h->otf_partials, (size_t)l * ((n + 255) / 256) * 2));
+  CK(dalloc(&h->slot_start, r)); CK(dalloc(&h->next_start, 1));
+  CK(dalloc(&h->retire_slot, r)); CK(dalloc(&h->retire_start, r)); CK(dalloc(&h->new_slot, r));
+  CK(dalloc(&h->otf_x0, (size_t)l * p));
+  h->otf_l = l;
+  h->otf_r = r;
+  return SPCA_OK;
+}
+
 StartState state_of(spca_handle *h) {
   StartState s;
   s.status = h->status; s.iters = h->iters; s.nnz = h->nnz;
@@ -336,21 +377,23 @@ TcPairs pairs_hi() {
 
 // u = A x for every active row of h->X: dense contraction (gated: runs only if *gate != 0).  The
 // tensor-core engine packs the active starts (h->act, count *nact) into consecutive plane rows.
-int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int *nact, int nhost, bool lowp) {
+int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int *nact, int nhost, bool lowp,
+                  const int *list = nullptr) {
+  if (!list) list = h->act;
   const int n = (int)h->n, p = (int)h->p;
   cudaStream_t st = h->stream;
   if (engine == SPCA_ENGINE_TC) {
     CK(timed(h, SPCA_K_U_DENSE, 3, [&] {
-      cudaError_t e = launch_row_scales(h->X, nhost, p, h->ldX, h->x_scale, h->x_inv, gate, nact, h->act, st);
+      cudaError_t e = launch_row_scales(h->X, nhost, p, h->ldX, h->x_scale, h->x_inv, gate, nact, list, st);
       if (e != cudaSuccess) return e;
       e = launch_split_planes(h->X, r, p, h->ldX, h->Xpl, h->ldX, (int64_t)h->r_cap * h->ldX, lowp ? 1 : 2,
-                              h->x_scale, 1.0f, gate, nact, h->act, st);
+                              h->x_scale, 1.0f, gate, nact, list, st);
       if (e != cudaSuccess) return e;
       if (lowp)
         return launch_gemm_tc(h->pmA, 1, h->tmX1, 1, n, nhost, p, nullptr, pairs_hi(), h->U, h->ldU, h->a_inv,
-                              h->x_inv, 1.0f, gate, nact, h->act, h->dev_err, h->sk, st);
+                              h->x_inv, 1.0f, gate, nact, list, h->dev_err, h->sk, st);
       return launch_gemm_tc(h->pmA, 2, h->tmX2, 2, n, nhost, p, nullptr, pairs_general(), h->U, h->ldU, h->a_inv,
-                            h->x_inv, 1.0f, gate, nact, h->act, h->dev_err, h->sk, st);
+                            h->x_inv, 1.0f, gate, nact, list, h->dev_err, h->sk, st);
     }));
   } else {
     CK(timed(h, SPCA_K_U_DENSE, 1, [&] {
@@ -523,6 +566,7 @@ void spca_destroy(spca_handle *h) {
   drain_profile(h);
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   free_workspace(h);
+  free_otf(h);
   void *ptrs[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->a_scale, h->a_inv, h->at_scale, h->at_inv,
                   h->flag, h->dev_err, h->sk.ws, h->sk.flags, h->defl_x, h->defl_w};
   for (void *q : ptrs)
@@ -679,6 +723,11 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   RC(resolve_engine(h, P.engine, &engine));
   if (P.lowp_sweeps > 0 && engine != SPCA_ENGINE_TC)
     return fail(h, SPCA_E_UNSUPPORTED, "low-precision sweeps need the tensor-core engine%s");
+  // on-the-fly replacement: l starts through the r slots
+  const int l = P.total_starts > P.r ? P.total_starts : P.r;
+  const bool otf = l > P.r;
+  if (otf && P.lowp_sweeps > 0)
+    return fail(h, SPCA_E_UNSUPPORTED, "low-precision sweeps with on-the-fly replacement%s");
   RC(enter(h));
   const auto t_start = std::chrono::steady_clock::now();
   const int L = P.lowp_sweeps;
@@ -687,23 +736,49 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
 
   const int r = P.r, n = (int)h->n, p = (int)h->p;
   RC(ensure_workspace(h, r));
+  if (otf) RC(ensure_otf(h, l, r));
   cudaStream_t st = h->stream;
   StartState S = state_of(h);
 
   // ---- a1: starting points
   const double gamma0 = is_pen(form) && !target ? P.gamma : 0.0;
+  // the starts' source: x0 rows (copied into X for a plain solve, kept whole for on-the-fly
+  // replacement, where slots take later rows), or the seeded stream
+  const float *x0src = nullptr;
+  int64_t ld0 = 0;
   if (x0) {
-    CK(cudaMemcpy2DAsync(h->X, h->ldX * sizeof(float), x0, (size_t)p * sizeof(float), (size_t)p * sizeof(float),
-                         r, P.x0_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (otf) {
+      if (P.x0_is_device) {
+        x0src = x0;
+      } else {
+        CK(cudaMemcpyAsync(h->otf_x0, x0, (size_t)l * p * sizeof(float), cudaMemcpyHostToDevice, st));
+        x0src = h->otf_x0;
+      }
+      ld0 = p;
+    } else {
+      CK(cudaMemcpy2DAsync(h->X, h->ldX * sizeof(float), x0, (size_t)p * sizeof(float), (size_t)p * sizeof(float),
+                           r, P.x0_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+      x0src = h->X;
+      ld0 = h->ldX;
+    }
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
-    CK(timed(h, SPCA_K_PREP, 1, [&] { return launch_check_finite(h->X, r, p, h->ldX, h->flag, st); }));
+    CK(timed(h, SPCA_K_PREP, 1,
+             [&] { return launch_check_finite(x0src, otf ? l : r, p, ld0, h->flag, st); }));
     CK(cudaMemcpyAsync(h->h_flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (*h->h_flag) return fail(h, SPCA_E_INVALID, "x0 has a non-finite entry%s");
   }
   CK(timed(h, SPCA_K_INIT, 1, [&] {
-    return launch_start_init(x0 ? h->X : nullptr, h->ldX, P.seed, r, p, h->X, h->ldX, S, gamma0, st);
+    return launch_start_init(x0src, ld0, P.seed, r, p, h->X, h->ldX, S, gamma0, nullptr, nullptr, nullptr, st);
   }));
+  std::vector<int> iota;
+  if (otf) {   // slot c holds start c; the next start is r
+    iota.resize(r + 1);
+    for (int c = 0; c < r; ++c) iota[c] = c;
+    iota[r] = r;
+    CK(cudaMemcpyAsync(h->slot_start, iota.data(), r * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->next_start, iota.data() + r, sizeof(int), cudaMemcpyHostToDevice, st));
+  }
   memset(&h->h_ctrl[0], 0, sizeof(Ctrl));
   h->h_ctrl[0].active = r;
   h->h_ctrl[0].need_dense = 1;      // x^(0) is dense: the first sweep's u = A x is the dense one
@@ -723,6 +798,13 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   xa.cap = p;
   xa.sparse_cap = p / 8 > 0 ? p / 8 : 1;
   const int C = target ? P.gamma_calib_sweeps : 0;
+  // the x-step's switches follow each start's own sweep count (calibration sweeps of Section 4.1,
+  // then the frozen gamma; the stopping rule compares two FP32 sweeps)
+  xa.schedule = 1;
+  xa.target = target ? 1 : 0;
+  xa.calib_sweeps = C;
+  xa.lowp_sweeps = L;
+  xa.stop_enabled = P.tol >= 0.0 ? 1 : 0;
   // the host queues this many sweeps before it reads the active count back; every path decision
   // inside a sweep is taken on the device from the control word
   const int check_every = 4;
@@ -743,7 +825,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   // plan and replayed, so that in steady state a segment is one launch.
   struct SweepPlan {
     int k;
-    bool lowp, dense_in, union_in, union_out, calibrate, per_start_thr, stop_test;
+    bool lowp, dense_in, union_in, union_out;
     int sparse_cap;
   };
   auto enqueue = [&](const SweepPlan &pl) -> int {
@@ -751,6 +833,8 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     // u = A x: over the union of the supports when it is small (tensor cores), else the dense
     // contraction, or the per-start support gather when every support is small
     if (pl.dense_in) RC(sweep_u_dense(h, engine, r, &cur->need_dense, &cur->active, r, pl.lowp));
+    // slots that took a new start in the last sweep have a dense x (the gather skips them)
+    if (otf) RC(sweep_u_dense(h, engine, r, &cur->n_new, &cur->n_new, r, false, h->new_slot));
     if (pl.union_in) RC(sweep_u_union(h, S, cur, r));
     CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
       if (pl.lowp)
@@ -763,14 +847,22 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     RC(sweep_y_v(h, engine, form, r, S, &cur->active, r, pl.lowp));
     CK(cudaMemsetAsync(nxt, 0, sizeof(Ctrl), st));
     XstepArgs xk = xa;
-    xk.calibrate = pl.calibrate;
-    xk.per_start_thr = pl.per_start_thr;
-    xk.stop_test = pl.stop_test;
     xk.sparse_cap = pl.sparse_cap;
-    CK(timed(h, SPCA_K_XSTEP, 3, [&] {   // candidate x-step, full x-step, active list
-      cudaError_t e = launch_xstep(xk, h->V, h->ldX, r, h->X, h->ldX, S, h->sup_idx, h->sup_val, nxt, st);
-      if (e != cudaSuccess) return e;
-      return launch_active_list(h->status, h->nnz, r, h->act, h->rank, nxt, st);   // for the next sweep
+    CK(timed(h, SPCA_K_XSTEP, 2, [&] {   // candidate x-step, full x-step
+      return launch_xstep(xk, h->V, h->ldX, r, h->X, h->ldX, S, h->sup_idx, h->sup_val, nxt, st);
+    }));
+    if (otf) {
+      // stopped slots: archive their start, give them the next starts (Section 4.3)
+      CK(timed(h, SPCA_K_INIT, 3, [&] {
+        cudaError_t e = launch_otf_retire(r, l, S, h->slot_start, h->next_start, h->arc, h->retire_slot,
+                                          h->retire_start, h->new_slot, nxt, h->X, h->ldX, p, st);
+        if (e != cudaSuccess) return e;
+        return launch_start_init(x0src, ld0, P.seed, r, p, h->X, h->ldX, S, gamma0, h->new_slot, h->slot_start,
+                                 &nxt->n_new, st);
+      }));
+    }
+    CK(timed(h, SPCA_K_XSTEP, 1, [&] {   // the active list of the next sweep
+      return launch_active_list(h->status, h->nnz, r, h->act, h->rank, nxt, st);
     }));
     if (pl.union_out) {
       CK(timed(h, SPCA_K_U_SPARSE, 2, [&] {
@@ -793,15 +885,22 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     memcpy(&b, &d, sizeof b);
     return b;
   };
-  const std::vector<int> solve_key = {form, engine, r, max_iter, C, L, (int)target,
+  const std::vector<int> solve_key = {form, engine, r, l, (int)(x0src != nullptr), max_iter, C, L, (int)target,
                                       (int)(bits(P.s) & 0xffffffff), (int)(bits(P.s) >> 32),
                                       (int)(bits(P.gamma) & 0xffffffff), (int)(bits(P.gamma) >> 32),
-                                      (int)(bits(P.tol) & 0xffffffff), (int)(bits(P.tol) >> 32)};
+                                      (int)(bits(P.tol) & 0xffffffff), (int)(bits(P.tol) >> 32),
+                                      // on-the-fly replacement reads x0 and the seed in the sweeps
+                                      (int)(otf ? (reinterpret_cast<uintptr_t>(x0src) & 0xffffffffu) : 0),
+                                      (int)(otf ? (reinterpret_cast<uintptr_t>(x0src) >> 32) : 0),
+                                      (int)(otf ? (P.seed & 0xffffffffu) : 0), (int)(otf ? (P.seed >> 32) : 0)};
   std::vector<SweepPlan> plans;
   std::vector<int> key;
   int rc = SPCA_OK;
-  for (int k0 = 1; k0 <= max_iter && rc == SPCA_OK;) {
-    const int k1 = std::min(max_iter, (k0 + check_every - 1) / check_every * check_every);
+  // every start runs at most max_iter sweeps and every sweep advances at least one start, so l
+  // starts end within l * max_iter sweeps (the loop stops as soon as no slot is active)
+  const int max_total = otf ? (int)std::min<int64_t>((int64_t)l * max_iter, INT32_MAX / 2) : max_iter;
+  for (int k0 = 1; k0 <= max_total && rc == SPCA_OK;) {
+    const int k1 = std::min(max_total, (k0 + check_every - 1) / check_every * check_every);
     plans.clear();
     key = solve_key;
     key.insert(key.end(), {k0 & 1, k1 - k0});
@@ -812,17 +911,12 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
       pl.lowp = k <= L;
       pl.dense_in = dense_queued;
       pl.union_in = union_built;
-      pl.calibrate = target && k <= C;
-      pl.per_start_thr = target && k > C;
-      // the stopping rule compares two FP32 sweeps
-      pl.stop_test = P.tol >= 0.0 && k >= 2 && k >= C + 1 && k >= L + 2;
       dense_queued = max_nnz > sparse_cap / 2;
       pl.sparse_cap = dense_queued ? sparse_cap : p;   // p: the gather for every support
-      union_built = engine == SPCA_ENGINE_TC && k + 1 > L && sum_nnz <= (int64_t)kUnionTry * h->kcap;
+      union_built = engine == SPCA_ENGINE_TC && !otf && k + 1 > L && sum_nnz <= (int64_t)kUnionTry * h->kcap;
       pl.union_out = union_built;
       plans.push_back(pl);
-      key.insert(key.end(), {pl.lowp, pl.dense_in, pl.union_in, pl.union_out, pl.calibrate, pl.per_start_thr,
-                             pl.stop_test, pl.sparse_cap});
+      key.insert(key.end(), {pl.lowp, pl.dense_in, pl.union_in, pl.union_out, pl.sparse_cap});
     }
     SegGraph *g = nullptr;
     for (SegGraph &c : graphs)
@@ -882,28 +976,48 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   RC(rc);
   RC(read_dev_err(h));
 
-  // ---- a7: FP64 objective, best start, y(x) and support of the best x
-  CK(timed(h, SPCA_K_FINALISE, 4, [&] {
-    cudaError_t e = launch_finalise(form, h->AT32, h->ldAT, n, p, h->X, h->ldX, S, r, h->U, h->ldU, h->sup_idx,
-                                    h->sup_val, p, h->partials, st);
-    if (e == cudaSuccess) e = launch_best(form, target ? 1 : 0, S, r, h->best, st);
-    if (e == cudaSuccess)
-      e = launch_best_outputs(form, h->best, h->U, h->ldU, n, h->X, h->ldX, p, h->y_out, h->x_out,
-                              h->support_out, h->nnz_out, st);
-    return e;
-  }));
+  // ---- a7: FP64-class objective, best start, y(x) and support of the best x
+  if (otf) {
+    CK(timed(h, SPCA_K_FINALISE, 4, [&] {
+      cudaError_t e = launch_otf_objectives(form, h->AT32, h->ldAT, n, p, h->arc, l, h->ldX, h->ldU,
+                                            h->otf_partials, st);
+      StartState Sa{};
+      Sa.f = h->arc.f;
+      Sa.ev = h->arc.ev;
+      if (e == cudaSuccess) e = launch_best(form, target ? 1 : 0, Sa, l, h->best, st);
+      if (e == cudaSuccess)
+        e = launch_best_outputs(form, h->best, h->arc.U, h->ldU, n, h->arc.x, h->ldX, p, h->y_out, h->x_out,
+                                h->support_out, h->nnz_out, st);
+      return e;
+    }));
+  } else {
+    CK(timed(h, SPCA_K_FINALISE, 4, [&] {
+      cudaError_t e = launch_finalise(form, h->AT32, h->ldAT, n, p, h->X, h->ldX, S, r, h->U, h->ldU, h->sup_idx,
+                                      h->sup_val, p, h->partials, st);
+      if (e == cudaSuccess) e = launch_best(form, target ? 1 : 0, S, r, h->best, st);
+      if (e == cudaSuccess)
+        e = launch_best_outputs(form, h->best, h->U, h->ldU, n, h->X, h->ldX, p, h->y_out, h->x_out,
+                                h->support_out, h->nnz_out, st);
+      return e;
+    }));
+  }
 
-  // ---- results to the host
-  std::vector<int> status(r), iters(r);
-  std::vector<double> f(r), ev(r), gam(r), F(r);
+  // ---- results to the host (the archive of all l starts with on-the-fly replacement)
+  const int nres = l;
+  const int *d_status = otf ? h->arc.status : h->status, *d_iters = otf ? h->arc.iters : h->iters;
+  const double *d_f = otf ? h->arc.f : h->f, *d_ev = otf ? h->arc.ev : h->ev;
+  const double *d_gam = otf ? h->arc.gamma : h->gamma, *d_F = otf ? h->arc.F : h->F;
+  const float *d_x = otf ? h->arc.x : h->X;
+  std::vector<int> status(nres), iters(nres);
+  std::vector<double> f(nres), ev(nres), gam(nres), F(nres);
   int best = 0;
   int64_t nnz = 0;
-  CK(cudaMemcpyAsync(status.data(), h->status, r * sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(iters.data(), h->iters, r * sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(f.data(), h->f, r * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(ev.data(), h->ev, r * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(gam.data(), h->gamma, r * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(F.data(), h->F, r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(status.data(), d_status, nres * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(iters.data(), d_iters, nres * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(f.data(), d_f, nres * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ev.data(), d_ev, nres * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(gam.data(), d_gam, nres * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(F.data(), d_F, nres * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&best, h->best, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&nnz, h->nnz_out, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -912,13 +1026,13 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   if (res->support && nnz > 0)
     CK(cudaMemcpyAsync(res->support, h->support_out, (size_t)nnz * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   if (res->start_x)
-    CK(cudaMemcpy2DAsync(res->start_x, (size_t)p * sizeof(float), h->X, h->ldX * sizeof(float),
-                         (size_t)p * sizeof(float), r, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpy2DAsync(res->start_x, (size_t)p * sizeof(float), d_x, h->ldX * sizeof(float),
+                         (size_t)p * sizeof(float), nres, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
 
   int64_t sweeps = 0;
   int nconv = 0, ndeg = 0;
-  for (int c = 0; c < r; ++c) {
+  for (int c = 0; c < nres; ++c) {
     sweeps += iters[c];
     nconv += status[c] == SPCA_ST_CONVERGED;
     ndeg += status[c] == SPCA_ST_DEGENERATE;
@@ -933,13 +1047,13 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   res->degenerate = ndeg;
   res->sweeps_total = sweeps;
   res->nnz = nnz;
-  if (res->start_objective) memcpy(res->start_objective, f.data(), r * sizeof(double));
-  if (res->start_explained) memcpy(res->start_explained, ev.data(), r * sizeof(double));
-  if (res->start_F) memcpy(res->start_F, F.data(), r * sizeof(double));
-  if (res->start_iters) memcpy(res->start_iters, iters.data(), r * sizeof(int));
-  if (res->start_status) memcpy(res->start_status, status.data(), r * sizeof(int));
+  if (res->start_objective) memcpy(res->start_objective, f.data(), nres * sizeof(double));
+  if (res->start_explained) memcpy(res->start_explained, ev.data(), nres * sizeof(double));
+  if (res->start_F) memcpy(res->start_F, F.data(), nres * sizeof(double));
+  if (res->start_iters) memcpy(res->start_iters, iters.data(), nres * sizeof(int));
+  if (res->start_status) memcpy(res->start_status, status.data(), nres * sizeof(int));
   if (res->start_gamma) {
-    for (int c = 0; c < r; ++c) res->start_gamma[c] = is_pen(form) ? gam[c] : 0.0;
+    for (int c = 0; c < nres; ++c) res->start_gamma[c] = is_pen(form) ? gam[c] : 0.0;
   }
   return SPCA_OK;
 }

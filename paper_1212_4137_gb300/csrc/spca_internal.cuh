@@ -48,6 +48,9 @@ struct Ctrl {
   int err;         // kernel-reported error code (0 = none)
   int sum_nnz;     // sum of the active starts' support sizes (bounds the union; saturates)
   int max_nnz;     // largest active support
+  int n_retire;    // on-the-fly replacement: slots whose start stopped in this sweep ...
+  int n_new;       // ... and how many of them took a new start (dense x: the next u = A x of
+                   // those slots is the dense contraction over them)
 };
 
 // per-start state of one solve (device arrays, r each)
@@ -79,7 +82,26 @@ struct XstepArgs {
   int max_iter;
   int cap;             // capacity of each support list (entries per start)
   int sparse_cap;      // larger supports make the next sweep use the dense u = A x
+  // per-start schedule (solves): the switches above follow each start's own sweep count it
+  // (StartState::iters, counted by the y-step): calibrate while it <= calib_sweeps in the
+  // gamma-targeting mode, the frozen per-start threshold after, and the stopping rule from
+  // it >= max(2, calib_sweeps + 1, lowp_sweeps + 2) when stop_enabled
+  int schedule;
+  int target;
+  int calib_sweeps;
+  int lowp_sweeps;
+  int stop_enabled;
 };
+
+// the x-step switches of start c under XstepArgs::schedule (else as given)
+__device__ inline XstepArgs xstep_switches(XstepArgs a, const int *iters, int c) {
+  if (!a.schedule) return a;
+  const int it = iters[c];
+  a.calibrate = a.target && it <= a.calib_sweeps;
+  a.per_start_thr = a.target && it > a.calib_sweeps;
+  a.stop_test = a.stop_enabled && it >= 2 && it >= a.calib_sweeps + 1 && it >= a.lowp_sweeps + 2;
+  return a;
+}
 
 // ---------------------------------------------------------------- kernels (launchers)
 // each returns cudaGetLastError() of its launch(es)
@@ -93,9 +115,28 @@ cudaError_t launch_check_finite(const float *a, int64_t rows, int64_t cols, int6
                                 int *flag, cudaStream_t st);
 
 // a1: x^(0) = g / ||g||_2 (g from x0, or seeded normals when x0 == nullptr); resets the
-// per-start state (gamma0 = the fixed gamma of a penalty form, else 0)
+// per-start state (gamma0 = the fixed gamma of a penalty form, else 0).  Row c of X is start c;
+// with slot_list, the k-th listed slot (k < *count) takes start slot_start[slot] (its row of x0,
+// or normal numbers start * p + j of the seeded stream)
 cudaError_t launch_start_init(const float *x0, int64_t ld0, uint64_t seed, int r, int p,
-                              float *X, int64_t ldX, StartState s, double gamma0, cudaStream_t st);
+                              float *X, int64_t ldX, StartState s, double gamma0, const int *slot_list,
+                              const int *slot_start, const int *count, cudaStream_t st);
+
+// on-the-fly replacement (Section 4.3): the archive of the l starts' results
+struct OtfArchive {
+  float *x;        // l x ldX final iterates
+  float *U;        // l x ldU u = A x (objectives)
+  double *F, *gamma, *f, *ev;
+  int *iters, *status, *nnz;
+};
+// after an x-step: archive the stopped slots (scalars, then x), give the next starts to the first
+// of them (new_slot[k], k < ctrl->n_new; slot_start updated; *next_start advanced)
+cudaError_t launch_otf_retire(int r, int l, StartState s, int *slot_start, int *next_start, OtfArchive arc,
+                              int *retire_slot, int *retire_start, int *new_slot, Ctrl *ctrl, const float *X,
+                              int64_t ldx, int p, cudaStream_t st);
+// Table 1 objective, explained variance and u = A x of the l archived starts (gamma: arc.gamma)
+cudaError_t launch_otf_objectives(int form, const float *AT, int64_t ldat, int n, int p, OtfArchive arc, int l,
+                                  int64_t ldx, int64_t ldu, double *partials, cudaStream_t st);
 
 // C[m, j] = sum_k P[m, k] Q[j, k]  (both operands K-contiguous); with gate != nullptr the
 // launch does nothing unless *gate != 0 (the dense u = A x is needed this sweep)

@@ -36,7 +36,8 @@ class spca_params(ctypes.Structure):
                 ("gamma_mode", ctypes.c_int), ("gamma_calib_sweeps", ctypes.c_int),
                 ("r", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("x0_is_device", ctypes.c_int), ("engine", ctypes.c_int),
-                ("lowp_sweeps", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("timeout_us", ctypes.c_int64)]
+                ("lowp_sweeps", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("timeout_us", ctypes.c_int64),
+                ("total_starts", ctypes.c_int)]
 
 
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -238,27 +239,28 @@ class Handle:
 
     def solve(self, form, r, s=1.0, gamma=0.0, gamma_target=False, calib=10, max_iter=100,
               tol=1e-9, x0=None, seed=0, engine=SPCA_ENGINE_AUTO, want_starts=False, x0_device=False,
-              lowp_sweeps=0, refine_sweeps=0, timeout_us=0):
+              lowp_sweeps=0, refine_sweeps=0, timeout_us=0, total_starts=0):
         """Returns a dict of numpy results.  x0: r x p float32 host array, device address
         (x0_device=True), or None for seeded starts."""
         prm = spca_params(form=form, s=s, gamma=gamma,
                           gamma_mode=SPCA_GAMMA_TARGET_NNZ if gamma_target else SPCA_GAMMA_FIXED,
                           gamma_calib_sweeps=calib, r=r, max_iter=max_iter, tol=tol, seed=seed,
                           x0_is_device=int(x0_device), engine=engine, lowp_sweeps=lowp_sweeps,
-                          refine_sweeps=refine_sweeps, timeout_us=timeout_us)
+                          refine_sweeps=refine_sweeps, timeout_us=timeout_us, total_starts=total_starts)
         n, p = self.n, self.p
+        nres = max(r, total_starts)
         out = {"x": np.zeros(p, np.float32), "y": np.zeros(n, np.float32),
                "support": np.zeros(p, np.int64)}
         if want_starts:
-            out.update(start_objective=np.zeros(r), start_explained=np.zeros(r), start_F=np.zeros(r),
-                       start_iters=np.zeros(r, np.int32), start_status=np.zeros(r, np.int32),
-                       start_gamma=np.zeros(r), start_x=np.zeros((r, p), np.float32))
+            out.update(start_objective=np.zeros(nres), start_explained=np.zeros(nres), start_F=np.zeros(nres),
+                       start_iters=np.zeros(nres, np.int32), start_status=np.zeros(nres, np.int32),
+                       start_gamma=np.zeros(nres), start_x=np.zeros((nres, p), np.float32))
         res = spca_result()
         for k, v in out.items():
             setattr(res, k, v.ctypes.data_as(type(getattr(res, k))))
         if x0 is not None and not x0_device:
             x0 = np.ascontiguousarray(x0, dtype=np.float32)
-            assert x0.shape == (r, p)
+            assert x0.shape == (nres, p)
         _check(spca_solve(self.h, prm, x0, res), "spca_solve", self.h)
         out["support"] = out["support"][:res.nnz]
         for k in ("objective", "explained_variance", "gamma", "best_start", "best_iters", "best_status",
