@@ -4,8 +4,10 @@ TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU-bas
 of ``bench.py`` are the only callers.  The product path (``paper_1212_4137_gb300``) never
 imports this module.
 
-All arrays are float64; A is n x p row-major; starts and iterates are stored one per row
-(r x p).  Formulation numbers follow Table 1 of the paper.
+All arrays are float64; A is n x p row-major, or a scipy.sparse matrix (kept in compressed
+sparse rows: the products of Algorithm 2 run over the stored entries and give the dense
+result); starts and iterates are stored one per row (r x p).  Formulation numbers follow
+Table 1 of the paper.
 """
 from __future__ import annotations
 
@@ -57,6 +59,10 @@ def _load():
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                      _dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      _dp, _dp, _dp, _dp, _ip, _ip, _dp, _dp, ctypes.c_int]
+        lib.oracle_objective_csr.argtypes = [_i64p, _ip, _dp, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
+        lib.oracle_solve_csr.restype = ctypes.c_int
+        lib.oracle_solve_csr.argtypes = [_i64p, _ip, _dp] + lib.oracle_solve.argtypes[1:]
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -70,6 +76,19 @@ def _p(a):
     if a is None:
         return None
     return a.ctypes.data_as(_dp if a.dtype == np.float64 else (_ip if a.dtype == np.int32 else _i64p))
+
+
+def _csr(A):
+    """(indptr int64, indices int32, data float64, n, p) of a scipy.sparse matrix in canonical
+    compressed sparse rows (columns ascending within a row, repeated entries summed), or None
+    for a dense array."""
+    if not hasattr(A, "tocsr"):
+        return None
+    M = A.tocsr(copy=True)
+    M.sum_duplicates()
+    M.sort_indices()
+    n, p = M.shape
+    return (_c(M.indptr, np.int64), _c(M.indices, np.int32), _c(M.data), n, p)
 
 
 def num_threads() -> int:
@@ -116,9 +135,16 @@ def xstep(form: int, v, s: float, gamma: float = 0.0, calibrate: bool = False) -
 
 def objective(A, form: int, gamma: float, x):
     """(f(x) of Table 1, explained variance) in FP64."""
-    A = _c(A); x = _c(x); f = ctypes.c_double(); ev = ctypes.c_double()
-    _load().oracle_objective(_p(A), A.shape[0], A.shape[1], int(form), float(gamma), _p(x),
-                             ctypes.byref(f), ctypes.byref(ev))
+    x = _c(x); f = ctypes.c_double(); ev = ctypes.c_double()
+    sp = _csr(A)
+    if sp is not None:
+        ptr, col, val, n, p = sp
+        _load().oracle_objective_csr(_p(ptr), _p(col), _p(val), n, p, int(form), float(gamma),
+                                     _p(x), ctypes.byref(f), ctypes.byref(ev))
+    else:
+        A = _c(A)
+        _load().oracle_objective(_p(A), A.shape[0], A.shape[1], int(form), float(gamma), _p(x),
+                                 ctypes.byref(f), ctypes.byref(ev))
     return f.value, ev.value
 
 
@@ -138,17 +164,25 @@ class Solve:
 def solve(A, form: int, G, s: float = 1.0, gamma: float = 0.0, gamma_target: bool = False,
           calib: int = 10, max_iter: int = 100, tol: float = 1e-9, nthreads: int = 0) -> Solve:
     """Algorithm 2 from the raw starts G (r x p, one per row; normalised inside)."""
-    A = _c(A); G = _c(G)
-    n, p = A.shape
+    G = _c(G)
+    sp = _csr(A)
+    if sp is not None:
+        ptr, col, val, n, p = sp
+        mat = (_p(ptr), _p(col), _p(val))
+        entry = _load().oracle_solve_csr
+    else:
+        A = _c(A)
+        n, p = A.shape
+        mat = (_p(A),)
+        entry = _load().oracle_solve
     r = G.shape[0]
     assert G.shape[1] == p
     X = np.empty((r, p)); f = np.empty(r); ev = np.empty(r); F = np.empty(r)
     iters = np.empty(r, np.int32); status = np.empty(r, np.int32); gam = np.empty(r)
     F_hist = np.empty((r, max(max_iter, 1)))
-    best = _load().oracle_solve(_p(A), n, p, int(form), float(s), float(gamma), int(gamma_target),
-                                int(calib), _p(G), r, int(max_iter), float(tol), _p(X), _p(f),
-                                _p(ev), _p(F), _p(iters), _p(status), _p(gam), _p(F_hist),
-                                int(nthreads))
+    best = entry(*mat, n, p, int(form), float(s), float(gamma), int(gamma_target), int(calib),
+                 _p(G), r, int(max_iter), float(tol), _p(X), _p(f), _p(ev), _p(F), _p(iters),
+                 _p(status), _p(gam), _p(F_hist), int(nthreads))
     return Solve(best, X, f, ev, F, iters, status, gam, F_hist[:, :max_iter])
 
 

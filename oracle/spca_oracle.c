@@ -46,6 +46,46 @@ enum { F_L2_L0CON = 1, F_L1_L0CON = 2, F_L2_L1CON = 3, F_L1_L1CON = 4,
 /* per-start status codes */
 enum { ST_MAXITER = 0, ST_CONVERGED = 1, ST_DEGENERATE = 2 };
 
+/* The data matrix A (n x p), stored dense (row-major) or as compressed sparse rows: row i's
+ * entries are val[k] at column col[k] for ptr[i] <= k < ptr[i+1], in ascending column order
+ * and without repeated columns.  Storage changes only which terms of the two products of
+ * Algorithm 2 are formed: the sparse loops skip the entries that are zero and otherwise add
+ * the same products in the same order as the dense ones, so both give the same FP64 result. */
+typedef struct {
+    int64_t n, p;
+    const double *A;                       /* dense, or NULL */
+    const int64_t *ptr;                    /* sparse rows */
+    const int32_t *col;
+    const double *val;
+} Mat;
+
+/* u = A x: u_i = sum_j A_ij x_j, j ascending */
+static void mat_Ax(const Mat *M, const double *x, double *u)
+{
+    for (int64_t i = 0; i < M->n; ++i) {
+        double acc = 0.0;
+        if (M->A) {
+            for (int64_t j = 0; j < M->p; ++j) acc += M->A[i * M->p + j] * x[j];
+        } else {
+            for (int64_t k = M->ptr[i]; k < M->ptr[i + 1]; ++k) acc += M->val[k] * x[M->col[k]];
+        }
+        u[i] = acc;
+    }
+}
+
+/* v = A^T y: v_j = sum_i A_ij y_i, i ascending */
+static void mat_ATy(const Mat *M, const double *y, double *v)
+{
+    for (int64_t j = 0; j < M->p; ++j) v[j] = 0.0;
+    for (int64_t i = 0; i < M->n; ++i) {
+        if (M->A) {
+            for (int64_t j = 0; j < M->p; ++j) v[j] += M->A[i * M->p + j] * y[i];
+        } else {
+            for (int64_t k = M->ptr[i]; k < M->ptr[i + 1]; ++k) v[M->col[k]] += M->val[k] * y[i];
+        }
+    }
+}
+
 static int is_l1_variance(int form) { return form % 2 == 0; }           /* forms 2,4,6,8 */
 static int is_penalty(int form)     { return form >= 5; }                /* forms 5..8   */
 static int uses_U(int form)         { return form == 5 || form == 6; }   /* L0 penalty   */
@@ -222,17 +262,16 @@ int oracle_xstep(int form, const double *v, int64_t p, double s, double gamma, i
 
 /* f(x) of Table 1 (gamma = the penalty used) and the explained variance of Section 4.1
  * (||Ax||_2^2 for L2 variance, ||Ax||_1 for L1 variance). */
-void oracle_objective(const double *A, int64_t n, int64_t p, int form, double gamma,
-                      const double *x, double *f_out, double *ev_out)
+static void objective_of(const Mat *M, int form, double gamma, const double *x, double *u,
+                         double *f_out, double *ev_out)
 {
     double l1 = 0.0, l2sq = 0.0, x0 = 0.0, x1 = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
-        double u = 0.0;
-        for (int64_t j = 0; j < p; ++j) u += A[i * p + j] * x[j];
-        l1 += fabs(u);
-        l2sq += u * u;
+    mat_Ax(M, x, u);
+    for (int64_t i = 0; i < M->n; ++i) {
+        l1 += fabs(u[i]);
+        l2sq += u[i] * u[i];
     }
-    for (int64_t j = 0; j < p; ++j) { x0 += (x[j] != 0.0); x1 += fabs(x[j]); }
+    for (int64_t j = 0; j < M->p; ++j) { x0 += (x[j] != 0.0); x1 += fabs(x[j]); }
     double l2 = sqrt(l2sq), f;
     switch (form) {
     case F_L2_L0CON: case F_L2_L1CON: f = l2; break;
@@ -246,22 +285,43 @@ void oracle_objective(const double *A, int64_t n, int64_t p, int form, double ga
     *ev_out = is_l1_variance(form) ? l1 : l2sq;
 }
 
+void oracle_objective(const double *A, int64_t n, int64_t p, int form, double gamma,
+                      const double *x, double *f_out, double *ev_out)
+{
+    Mat M = {n, p, A, NULL, NULL, NULL};
+    double *u = (double *)malloc((size_t)n * sizeof(double));
+    objective_of(&M, form, gamma, x, u, f_out, ev_out);
+    free(u);
+}
+
+/* the same for A in compressed sparse rows */
+void oracle_objective_csr(const int64_t *ptr, const int32_t *col, const double *val, int64_t n,
+                          int64_t p, int form, double gamma, const double *x, double *f_out,
+                          double *ev_out)
+{
+    Mat M = {n, p, NULL, ptr, col, val};
+    double *u = (double *)malloc((size_t)n * sizeof(double));
+    objective_of(&M, form, gamma, x, u, f_out, ev_out);
+    free(u);
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Algorithm 2 for one start                                                            */
 /* ------------------------------------------------------------------------------------ */
 
 /*
  * Runs Algorithm 2 from the raw start g (x^(0) = g / ||g||_2).
- *   A       n x p row-major
+ *   M       the data matrix (n x p)
  *   x       out: final x (p)
  *   F_hist  out, optional: F(x^(k), y^(k-1)) for k = 1..iters (max_iter entries, rest NaN)
  * Returns the status (ST_*); *iters = number of sweeps (y-step + x-step) performed.
  */
-static int am_one_start(const double *A, int64_t n, int64_t p, int form, double s,
+static int am_one_start(const Mat *M, int form, double s,
                         double gamma, int gamma_target, int calib, int max_iter, double tol,
                         const double *g, double *x, double *u, double *y, double *v,
                         double *F_hist, int *iters, double *gamma_used, double *F_last)
 {
+    const int64_t n = M->n, p = M->p;
     /* Algorithm 2: select initial point */
     double nrm = 0.0;
     for (int64_t j = 0; j < p; ++j) nrm += g[j] * g[j];
@@ -277,11 +337,7 @@ static int am_one_start(const double *A, int64_t n, int64_t p, int form, double 
 
     for (k = 1; k <= max_iter; ++k) {
         /* u = A x^(k-1) */
-        for (int64_t i = 0; i < n; ++i) {
-            double acc = 0.0;
-            for (int64_t j = 0; j < p; ++j) acc += A[i * p + j] * x[j];
-            u[i] = acc;
-        }
+        mat_Ax(M, x, u);
         /* y-step: S2 (L1 variance) or S1 (L2 variance) */
         if (is_l1_variance(form)) {
             for (int64_t i = 0; i < n; ++i) y[i] = (u[i] >= 0.0) ? 1.0 : -1.0;
@@ -296,9 +352,7 @@ static int am_one_start(const double *A, int64_t n, int64_t p, int form, double 
             for (int64_t i = 0; i < n; ++i) y[i] = u[i] / un;
         }
         /* v = A^T y */
-        for (int64_t j = 0; j < p; ++j) v[j] = 0.0;
-        for (int64_t i = 0; i < n; ++i)
-            for (int64_t j = 0; j < p; ++j) v[j] += A[i * p + j] * y[i];
+        mat_ATy(M, y, v);
         /* x-step (S3..S6) */
         int64_t nnz;
         double thr;
@@ -332,11 +386,12 @@ static int am_one_start(const double *A, int64_t n, int64_t p, int form, double 
  *   F_hist (r x max_iter)                nthreads  OpenMP threads over starts (<=0: all)
  * Returns the best start index.
  */
-int oracle_solve(const double *A, int64_t n, int64_t p, int form, double s, double gamma,
-                 int gamma_target, int calib, const double *G, int r, int max_iter,
-                 double tol, double *X, double *f, double *ev, double *F, int *iters,
-                 int *status, double *gam, double *F_hist, int nthreads)
+static int solve_of(const Mat *M, int form, double s, double gamma, int gamma_target, int calib,
+                    const double *G, int r, int max_iter, double tol, double *X, double *f,
+                    double *ev, double *F, int *iters, int *status, double *gam, double *F_hist,
+                    int nthreads)
 {
+    const int64_t n = M->n, p = M->p;
     double *f_loc = (double *)malloc((size_t)r * sizeof(double));
     double *ev_loc = (double *)malloc((size_t)r * sizeof(double));
 #ifdef _OPENMP
@@ -349,10 +404,10 @@ int oracle_solve(const double *A, int64_t n, int64_t p, int form, double s, doub
         double *v = (double *)malloc((size_t)p * sizeof(double));
         int it, st;
         double g_used, F_last;
-        st = am_one_start(A, n, p, form, s, gamma, gamma_target, calib, max_iter, tol,
+        st = am_one_start(M, form, s, gamma, gamma_target, calib, max_iter, tol,
                           G + (int64_t)c * p, X + (int64_t)c * p, u, y, v,
                           F_hist ? F_hist + (int64_t)c * max_iter : NULL, &it, &g_used, &F_last);
-        oracle_objective(A, n, p, form, g_used, X + (int64_t)c * p, &f_loc[c], &ev_loc[c]);
+        objective_of(M, form, g_used, X + (int64_t)c * p, u, &f_loc[c], &ev_loc[c]);
         if (iters) iters[c] = it;
         if (status) status[c] = st;
         if (gam) gam[c] = g_used;
@@ -369,6 +424,28 @@ int oracle_solve(const double *A, int64_t n, int64_t p, int form, double s, doub
     if (ev) memcpy(ev, ev_loc, (size_t)r * sizeof(double));
     free(f_loc); free(ev_loc);
     return best;
+}
+
+int oracle_solve(const double *A, int64_t n, int64_t p, int form, double s, double gamma,
+                 int gamma_target, int calib, const double *G, int r, int max_iter,
+                 double tol, double *X, double *f, double *ev, double *F, int *iters,
+                 int *status, double *gam, double *F_hist, int nthreads)
+{
+    Mat M = {n, p, A, NULL, NULL, NULL};
+    return solve_of(&M, form, s, gamma, gamma_target, calib, G, r, max_iter, tol, X, f, ev, F,
+                    iters, status, gam, F_hist, nthreads);
+}
+
+/* the same for A in compressed sparse rows (ascending columns within a row, none repeated) */
+int oracle_solve_csr(const int64_t *ptr, const int32_t *col, const double *val, int64_t n,
+                     int64_t p, int form, double s, double gamma, int gamma_target, int calib,
+                     const double *G, int r, int max_iter, double tol, double *X, double *f,
+                     double *ev, double *F, int *iters, int *status, double *gam,
+                     double *F_hist, int nthreads)
+{
+    Mat M = {n, p, NULL, ptr, col, val};
+    return solve_of(&M, form, s, gamma, gamma_target, calib, G, r, max_iter, tol, X, f, ev, F,
+                    iters, status, gam, F_hist, nthreads);
 }
 
 int oracle_num_threads(void)

@@ -22,6 +22,10 @@ have the shapes of its workloads):
   * ``gaussian_matrix``: A_ij ~ N(0,1)            (small dense case, n=100, p=500)
   * ``spiked_matrix``:   A = sum_k theta_k u_k v_k^T + N(0,1) noise, u_k Gaussian unit-norm,
                          v_k unit-norm with ``nnz`` nonzeros at random indices, N(0,1) values.
+  * ``bag_of_words``:    a sparse document x word count matrix in compressed sparse rows, the
+                         stand-in for the text corpora of Section 5 (word counts per article):
+                         Zipf word popularity, log-normal document lengths, and a few planted
+                         topics (small word sets that co-occur in a share of the documents).
 """
 from __future__ import annotations
 
@@ -39,6 +43,11 @@ STREAM_SPIKE_U = 2
 STREAM_SPIKE_V = 3
 STREAM_SPIKE_IDX = 4
 STREAM_STARTS = 5
+STREAM_BOW_LEN = 6
+STREAM_BOW_PERM = 7
+STREAM_BOW_TOKENS = 8
+STREAM_BOW_TOPIC = 9
+STREAM_BOW_TOPIC_TOKENS = 10
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -135,3 +144,63 @@ def raw_starts(p: int, r: int, seed: int, dtype=np.float64) -> np.ndarray:
     X = np.empty((r, p), dtype=dtype)
     _fill_normals(X, stream_key(seed, STREAM_STARTS))
     return X
+
+
+def bag_of_words(n: int, p: int, nnz: int, seed: int, topics: int = 5, topic_words: int = 10,
+                 topic_share: float = 0.08, zipf: float = 1.0, chunk_docs: int = 8192):
+    """A sparse n x p word-count matrix (documents x words) in compressed sparse rows.
+
+    Returns (indptr int64 [n+1], indices int32 [nnz'], data float32 [nnz']) with columns
+    ascending within each row and no repeated column; nnz' is close to ``nnz``.
+
+    Recipe (every draw counter-based, so any document range can be built on its own):
+      * word popularity: Zipf, weight 1 / (rank + 1)**zipf, ranks given to the word ids by a
+        random permutation (the vocabulary order of a corpus does not follow frequency);
+      * document i draws m_i words with replacement from the popularity law, m_i log-normal
+        (sigma 0.5) with a mean of 1.35 nnz / n draws (repeated draws merge into counts);
+      * ``topics`` planted topics, each ``topic_words`` words of popularity rank in [50, 2000);
+        a document belongs to topic t with probability ``topic_share`` (else to none) and then
+        draws round(0.25 m_i) more words uniformly from that topic's words;
+      * A[i, j] = the number of times document i drew word j.
+    """
+    n, p = int(n), int(p)
+    mean_draws = 1.35 * nnz / n
+    z = normals(stream_key(seed, STREAM_BOW_LEN), 0, n)
+    m = np.maximum(1, np.rint(mean_draws * np.exp(0.5 * z - 0.125))).astype(np.int64)
+    perm = np.argsort(uniforms(stream_key(seed, STREAM_BOW_PERM), 0, p), kind="stable")  # rank -> word
+    w = 1.0 / np.power(np.arange(1, p + 1, dtype=np.float64), zipf)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    lo, hi = min(50, p - 1), min(2000, p)
+    tk = stream_key(seed, STREAM_BOW_TOPIC)
+    twords = np.empty((topics, topic_words), dtype=np.int64)
+    for t in range(topics):
+        ranks = lo + np.argsort(uniforms(tk, t * (hi - lo), hi - lo), kind="stable")[:topic_words]
+        twords[t] = perm[ranks]
+    u_topic = uniforms(tk, topics * (hi - lo), n)
+    topic = np.where(u_topic < topics * topic_share, np.minimum((u_topic / topic_share).astype(np.int64),
+                                                                  topics - 1), -1)
+    extra = np.where(topic >= 0, np.rint(0.25 * m), 0).astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(m)])
+    eoff = np.concatenate([[0], np.cumsum(extra)])
+    kt, ke = stream_key(seed, STREAM_BOW_TOKENS), stream_key(seed, STREAM_BOW_TOPIC_TOKENS)
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    cols, vals = [], []
+    for d0 in range(0, n, chunk_docs):
+        d1 = min(n, d0 + chunk_docs)
+        cnt = int(off[d1] - off[d0])
+        doc = np.repeat(np.arange(d0, d1, dtype=np.int64), m[d0:d1])
+        word = perm[np.minimum(np.searchsorted(cdf, uniforms(kt, int(off[d0]), cnt), side="right"), p - 1)]
+        ecnt = int(eoff[d1] - eoff[d0])
+        if ecnt:
+            edoc = np.repeat(np.arange(d0, d1, dtype=np.int64), extra[d0:d1])
+            pick = np.minimum((uniforms(ke, int(eoff[d0]), ecnt) * topic_words).astype(np.int64), topic_words - 1)
+            doc = np.concatenate([doc, edoc])
+            word = np.concatenate([word, twords[topic[edoc], pick]])
+        keys, counts = np.unique(doc * p + word, return_counts=True)
+        rows = keys // p
+        cols.append((keys - rows * p).astype(np.int32))
+        vals.append(counts.astype(np.float32))
+        indptr[d0 + 1:d1 + 1] = np.cumsum(np.bincount(rows - d0, minlength=d1 - d0))
+        indptr[d0 + 1:d1 + 1] += indptr[d0]
+    return indptr, np.concatenate(cols), np.concatenate(vals)
