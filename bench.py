@@ -439,6 +439,93 @@ def run_scan(args):
               flush=True)
 
 
+# The text corpora of Section 5 on a synthetic stand-in: a bag-of-words count matrix of the NYTimes
+# corpus's shape (300,000 documents x 102,660 words, about 70 million stored counts; Zipf word
+# popularity, log-normal document lengths, 5 planted topics), kept in compressed sparse rows.  The
+# paper's settings: s = 5 (L0 forms; the L1 radius sqrt(5); the Section 4.1 rule targeting 5
+# nonzeros for the penalty forms), 20 starts, at most 20 sweeps, tol 1e-6; and 256 starts for
+# throughput.  Per (formulation, r): the GPU's sweeps*starts/s and single-solve latency, the share
+# and DRAM-bound rate of v = A^T y, and (formulation 1) the FP64 oracle on a bounded sample.
+TEXT = dict(n=300000, p=102660, nnz=70_000_000, seed=11, s=5, max_iter=20, tol=1e-6, calib=10)
+
+
+def run_scan_text(args, forms=(1, 2, 3, 4, 5, 6, 7, 8), rs=(20, 256)):
+    import torch
+
+    from oracle import oracle
+    from paper_1212_4137_gb300 import build, inputs as I, spca
+    build.build()
+    oracle.build()
+    w = TEXT
+    n, p = w["n"], w["p"]
+    t0 = time.perf_counter()
+    ip, ix, v = I.bag_of_words(n, p, w["nnz"], w["seed"])
+    gen_s = time.perf_counter() - t0
+    nnz = int(ip[-1])
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    h = spca.Handle((ip, ix, v, (n, p)), stream=stream.cuda_stream)
+    create_s = time.perf_counter() - t0
+    peaks = load_peaks()
+    for r in rs:
+        G = I.raw_starts(p, r, 12).astype(np.float32)
+        Gd = torch.from_numpy(G).to(dev)
+        for form in forms:
+            kw = dict(s=float(w["s"]), max_iter=w["max_iter"], tol=w["tol"])
+            if form >= 5:
+                kw.update(gamma_target=True, calib=w["calib"])
+            for _ in range(args.warmup):
+                h.solve(form, r, x0=Gd.data_ptr(), x0_device=True, **kw)
+            lat, sweeps = [], 0
+            torch.cuda.synchronize(dev)
+            ts = time.perf_counter()
+            for _ in range(args.steps):
+                t1 = time.perf_counter()
+                sweeps += h.solve(form, r, x0=Gd.data_ptr(), x0_device=True, **kw)["sweeps_total"]
+                lat.append(1e3 * (time.perf_counter() - t1))
+            dt = time.perf_counter() - ts
+            # one more solve with every kernel timed: shares, and v = A^T y against DRAM
+            h.profile(True)
+            out = h.solve(form, r, x0=Gd.data_ptr(), x0_device=True, **kw)
+            kern = {name: h.profile_query(kid) for kid, name in spca.KERNEL_NAMES.items()}
+            h.profile(False)
+            tot = sum(ms for _, ms in kern.values()) or 1.0
+            nv, msv = kern["v"]
+            # algorithmic DRAM bytes of the sweeps' v = A^T y: A by columns once per sweep (index +
+            # value, 8 B per stored entry), y of the active starts once, v written once; the gather
+            # u = A x is queued once per sweep, so its launch count is the number of sweeps queued
+            nsw = kern["u_sparse"][0]
+            active = out["sweeps_total"]            # sweeps*starts = sum over sweeps of the active count
+            vbytes = nsw * 8.0 * nnz + 4.0 * (n + p) * active
+            line = {"scan": "text corpus (bag-of-words, NYTimes shape)", "form": form, "n": n, "p": p,
+                    "nnz": nnz, "r": r, "s": w["s"], "max_iter": w["max_iter"], "tol": w["tol"],
+                    "sweeps_starts_per_s": round(sweeps / dt, 1), "solves_per_s": round(args.steps / dt, 2),
+                    "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                                   "p99": round(float(np.percentile(lat, 99)), 3)},
+                    "sweeps_total": int(out["sweeps_total"]), "best_nnz": int(out["nnz"]),
+                    "kernels_ms_share": {k: round(ms / tot, 4) for k, (_, ms) in kern.items()},
+                    "v": {"sweeps": nsw, "launches": nv, "ms_per_sweep": round(msv / max(1, nsw), 4),
+                          "achieved_gbs": round(vbytes / (msv / 1e3) / 1e9, 1) if msv > 0 else None,
+                          "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                          "bytes": "8 B per stored entry per launch + 4 (n + p) B per active start"}}
+            if form == 1 and r == rs[0]:
+                A64 = sps_csr(ip, ix, v, n, p)
+                t1 = time.perf_counter()
+                ref = oracle.solve(A64, 1, G[:2].astype(np.float64), s=float(w["s"]), max_iter=2, tol=-1)
+                odt = time.perf_counter() - t1
+                line["oracle_sweeps_starts_per_s"] = round(int(ref.iters.sum()) / odt, 3)
+                line["oracle_sample"] = "2 starts x 2 sweeps, FP64 CSR products, %d threads" % oracle.num_threads()
+                line["generate_s"], line["create_s"] = round(gen_s, 2), round(create_s, 2)
+            print(json.dumps(line), flush=True)
+    h.close()
+
+
+def sps_csr(ip, ix, v, n, p):
+    import scipy.sparse as sps
+    return sps.csr_matrix((v.astype(np.float64), ix, ip), shape=(n, p))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,8 +538,17 @@ def main():
     ap.add_argument("--forms", type=str, default=None, help="comma-separated formulations (default: all 8)")
     ap.add_argument("--no-e2e", action="store_true")
     # the paper's shape scan (one JSON line per shape) instead of the benchmark line
-    ap.add_argument("--scan", choices=("paper-shapes",), default=None)
+    ap.add_argument("--scan", choices=("paper-shapes", "text-corpus"), default=None)
+    ap.add_argument("--rs", type=str, default=None, help="text-corpus scan: comma-separated start counts")
     args = ap.parse_args()
+    if args.scan == "text-corpus":
+        kw = {}
+        if args.forms:
+            kw["forms"] = tuple(int(t) for t in args.forms.split(","))
+        if args.rs:
+            kw["rs"] = tuple(int(t) for t in args.rs.split(","))
+        run_scan_text(args, **kw)
+        return
     if args.scan:
         run_scan(args)
         return

@@ -2,13 +2,13 @@
  * spca.h -- C ABI of the GB300 (sm_103a) alternating-maximization sparse PCA library
  * (libspca.so).
  *
- * The library computes, for one dense data matrix A (n samples x p variables), the
- * single-component sparse PCA problem OPT = max_{x in X} f(x) for any of the eight
- * formulations of Table 1 of Richtarik, Jahani, Ahipasaoglu, Takac, "Alternating
- * maximization: unifying framework for 8 sparse PCA formulations and efficient parallel
- * codes" (arXiv 1212.4137), by the alternating maximization method of Algorithm 2 run
- * from r starting points at once (Section 4: the r matrix-vector products of a sweep
- * become matrix-matrix products), keeping the best start.
+ * The library computes, for one data matrix A (n samples x p variables; dense, or sparse
+ * in compressed sparse rows), the single-component sparse PCA problem
+ * OPT = max_{x in X} f(x) for any of the eight formulations of Table 1 of Richtarik,
+ * Jahani, Ahipasaoglu, Takac, "Alternating maximization: unifying framework for 8 sparse
+ * PCA formulations and efficient parallel codes" (arXiv 1212.4137), by the alternating
+ * maximization method of Algorithm 2 run from r starting points at once (Section 4: the r
+ * matrix-vector products of a sweep become matrix-matrix products), keeping the best start.
  *
  * Conventions (all entry points):
  *   - every call returns an int status (spca_status); no exception crosses the ABI;
@@ -112,6 +112,33 @@ typedef enum {
  */
 int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t lda,
                 int in_dtype, int a_is_device, int storage, void *cuda_stream);
+
+/*
+ * spca_create_csr -- the same for a sparse A given in compressed sparse rows, the layout of the
+ * text corpora of Section 5 (document x word counts).  The handle keeps A by rows and by
+ * columns, each canonical (indices ascending within a row, repeated entries summed), in FP32;
+ * no dense copy is made.  The sweeps run on sparse CUDA-core kernels: u = A x over the stored
+ * entries (by rows) for a dense x, or over the columns of x's support (by columns) once x is
+ * sparse; v = A^T y over the stored entries (by columns); the finalise by rows in compensated
+ * FP32 pairs.
+ *   n, p         rows and columns, 1 .. 2^31 - 1.
+ *   nnz          stored entries, 0 .. 2^31 - 1 (= row_ptr[n]).
+ *   row_ptr      n + 1 int64 offsets: row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
+ *   col_idx      nnz int32 column indices in [0, p), in any order within a row; a repeated
+ *                (row, column) pair adds up.
+ *   values       nnz finite floats.
+ *   is_device    the three arrays are in device memory (1) or host memory (0).  Either way they
+ *                are copied (device input through the host, where the layouts are built) and
+ *                may be freed on return.
+ *   cuda_stream  as in spca_create.
+ * On such a handle spca_solve and spca_products take SPCA_ENGINE_AUTO or SPCA_ENGINE_SIMT
+ * (SPCA_ENGINE_TC and lowp_sweeps > 0 are SPCA_E_UNSUPPORTED), and spca_deflate is
+ * SPCA_E_UNSUPPORTED (projection deflation fills A in).
+ * Errors: SPCA_E_INVALID (NULL pointers, sizes out of range, row_ptr malformed, a column out of
+ *         range, a value or a sum of repeated values not finite), SPCA_E_NOMEM, SPCA_E_CUDA.
+ */
+int spca_create_csr(spca_handle **out, int64_t n, int64_t p, int64_t nnz, const int64_t *row_ptr,
+                    const int32_t *col_idx, const float *values, int is_device, void *cuda_stream);
 
 /*
  * Parameters of one solve (Algorithm 2 from r starts, Section 2.2 stopping rule).

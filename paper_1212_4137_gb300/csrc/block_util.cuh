@@ -112,6 +112,35 @@ __device__ __forceinline__ void f32pair_fma(F32Pair &s, float a, float b) {
   s.lo = __fadd_rn(s.lo, __fadd_rn(te, pe));
 }
 __device__ __forceinline__ double f32pair_value(const F32Pair &s) { return (double)s.hi + (double)s.lo; }
+// |a| of a pair (exact)
+__device__ __forceinline__ F32Pair f32pair_abs(const F32Pair &a) {
+  F32Pair r;
+  r.hi = fabsf(a.hi);
+  r.lo = a.hi < 0.0f ? -a.lo : a.lo;
+  return r;
+}
+// a^2 of a pair: the exact square of the leading part (one FMA for its error) plus 2 hi lo,
+// renormalised; relative error about 2^-44
+__device__ __forceinline__ F32Pair f32pair_sq(const F32Pair &a) {
+  const float p = __fmul_rn(a.hi, a.hi);
+  const float e = __fadd_rn(__fmaf_rn(a.hi, a.hi, -p), __fmul_rn(__fmul_rn(2.0f, a.hi), a.lo));
+  F32Pair r;
+  r.hi = __fadd_rn(p, e);
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, p));
+  return r;
+}
+// a + b of two pairs: Knuth's two-sum of the leading parts (exact), the trailing parts added to
+// its error, then renormalised (Dekker's fast two-sum); the same bits for a + b and b + a
+__device__ __forceinline__ F32Pair f32pair_add(const F32Pair &a, const F32Pair &b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bv = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));
+  const float lo = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  F32Pair r;
+  r.hi = __fadd_rn(s, lo);
+  r.lo = __fsub_rn(lo, __fsub_rn(r.hi, s));
+  return r;
+}
 
 // order-preserving key of |v|: the IEEE bits without the sign (monotone for |v| >= 0)
 __device__ __forceinline__ uint32_t abs_key(float v) { return __float_as_uint(v) & 0x7fffffffu; }

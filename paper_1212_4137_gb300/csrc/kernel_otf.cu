@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(OT) k_otf_obj(const float *__restrict__ AT, in
   }
 }
 
-// block per archived start: the partials in order, ||x||_0 and ||x||_1, then f (Table 1) and the
-// explained variance
+// block per start: the partials in order, ||x||_0 and ||x||_1, then f (Table 1) and the
+// explained variance (the archive's starts, or a solve's starts with a sparse A)
 __global__ void __launch_bounds__(OT) k_otf_reduce(int form, const double *__restrict__ partials, int nchunks,
                                                    int p, OtfArchive arc, int64_t ldx) {
   __shared__ double red[32];
@@ -169,7 +169,12 @@ cudaError_t launch_otf_objectives(int form, const float *AT, int64_t ldat, int n
   k_otf_obj<<<dim3((unsigned)nchunks, (unsigned)l), OT, 0, st>>>(AT, ldat, n, p, arc, ldx, ldu, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_otf_reduce<<<l, OT, 0, st>>>(form, partials, nchunks, p, arc, ldx);
+  return launch_objective_reduce(form, partials, nchunks, p, arc, l, ldx, st);
+}
+
+cudaError_t launch_objective_reduce(int form, const double *partials, int nchunks, int p, OtfArchive arc, int count,
+                                    int64_t ldx, cudaStream_t st) {
+  k_otf_reduce<<<count, OT, 0, st>>>(form, partials, nchunks, p, arc, ldx);
   return cudaGetLastError();
 }
 

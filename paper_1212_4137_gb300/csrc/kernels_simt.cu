@@ -200,9 +200,87 @@ __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict
   }
 }
 
+// The same for long u (n > 2 kYChunk), where one CTA per start would be latency-bound: a CTA per
+// chunk of kYChunk entries and start; L2 variance first sums u_i^2 per chunk (k_ystep_norm), then
+// every CTA of the start adds the chunk sums in chunk order and writes its chunk of y.
+__global__ void __launch_bounds__(256) k_ystep_norm(const float *__restrict__ U, int64_t ldu, int n, StartState s,
+                                                    float *__restrict__ ysum) {
+  __shared__ float redf[32];
+  const int b = blockIdx.x, c = blockIdx.y;
+  if (s.status[c] != ST_ACTIVE) return;
+  const float *u = U + (int64_t)c * ldu;
+  const int i1 = min(n, (b + 1) * kYChunk);
+  float part = 0.0f;
+  for (int i = b * kYChunk + threadIdx.x; i < i1; i += blockDim.x) part = fmaf(u[i], u[i], part);
+  const float t = block_sum_f(part, redf);
+  if (threadIdx.x == 0) ysum[(int64_t)c * gridDim.x + b] = t;
+}
+
+__global__ void __launch_bounds__(256) k_ystep_apply(int form, const float *__restrict__ U, int64_t ldu, int n,
+                                                     float *__restrict__ Y, __half *__restrict__ Ypl,
+                                                     int64_t pstride, const int *__restrict__ rank, StartState s,
+                                                     float *__restrict__ X, int64_t ldX, int p,
+                                                     const float *__restrict__ ysum) {
+  const int b = blockIdx.x, c = blockIdx.y, nch = gridDim.x;
+  // (the chunk-0 CTA alone may change the status below, and only when every CTA of the start
+  // returns without writing: ||u||_2 = 0)
+  if (s.status[c] != ST_ACTIVE) return;
+  const float *u = U + (int64_t)c * ldu;
+  float *y = Y ? Y + (int64_t)c * ldu : nullptr;
+  __half *yp = Ypl ? Ypl + (int64_t)(rank ? rank[c] : c) * ldu : nullptr;
+  const int i1 = min(n, (b + 1) * kYChunk);
+  if (b == 0 && threadIdx.x == 0) s.iters[c] += 1;
+  if (is_l1_var(form)) {
+    for (int i = b * kYChunk + threadIdx.x; i < i1; i += blockDim.x) {
+      const float yi = (u[i] >= 0.0f) ? 1.0f : -1.0f;
+      if (y) y[i] = yi;
+      if (yp) yp[i] = __float2half_rn(yi * kQScale);
+    }
+    return;
+  }
+  float tot = 0.0f;
+  for (int q = 0; q < nch; ++q) tot += ysum[(int64_t)c * nch + q];
+  const double nrm = sqrt((double)tot);
+  if (nrm == 0.0) {
+    if (b == 0) {
+      float *x = X + (int64_t)c * ldX;
+      for (int j = threadIdx.x; j < p; j += blockDim.x) x[j] = 0.0f;
+      if (threadIdx.x == 0) {
+        s.status[c] = SPCA_ST_DEGENERATE;
+        s.nnz[c] = 0;
+        s.F[c] = 0.0;
+      }
+    }
+    return;
+  }
+  const float inv = (float)(1.0 / nrm);
+  for (int i = b * kYChunk + threadIdx.x; i < i1; i += blockDim.x) {
+    const float yi = u[i] * inv;
+    if (y) y[i] = yi;
+    if (yp) {
+      const float ys = yi * kQScale;
+      const __half hi = __float2half_rn(ys);
+      yp[i] = hi;
+      yp[i + pstride] = __float2half_rn(ys - __half2float(hi));
+    }
+  }
+}
+
 cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, float *Y, void *Ypl,
                          int64_t plane_stride, const int *rank, StartState s, float *X, int64_t ldX,
-                         int p, cudaStream_t st) {
+                         int p, float *ysum, cudaStream_t st) {
+  const int nch = (n + kYChunk - 1) / kYChunk;
+  if (ysum && nch > 2) {
+    const dim3 grid((unsigned)nch, (unsigned)r);
+    if (!is_l1_var(form)) {
+      k_ystep_norm<<<grid, 256, 0, st>>>(U, ldu, n, s, ysum);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    k_ystep_apply<<<grid, 256, 0, st>>>(form, U, ldu, n, Y, static_cast<__half *>(Ypl), plane_stride, rank, s, X,
+                                        ldX, p, ysum);
+    return cudaGetLastError();
+  }
   k_ystep<<<r, 256, 0, st>>>(form, U, ldu, n, Y, static_cast<__half *>(Ypl), plane_stride, rank,
                              s, X, ldX, p);
   return cudaGetLastError();

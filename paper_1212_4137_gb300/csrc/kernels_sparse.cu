@@ -1,0 +1,529 @@
+// kernels_sparse.cu -- the products of an AM sweep (Algorithm 2) for a sparse A held in compressed
+// sparse rows, the layout of the text corpora of Section 5 (document x word counts).  The handle
+// keeps A by rows (CSR of A, n rows) and by columns (CSR of A^T, p rows); both are canonical
+// (indices ascending within a row, no repeats).
+//
+//   k_pack_t        B^T of the listed rows of X or Y, packed start-fastest: Bt[j * ldb + k] =
+//                   src[list[k]][j], so that one stored entry of A meets 8 starts in one 32-byte
+//                   sector of Bt;
+//   k_spmm          out[list[k]][row] = sum over the row's entries a_{row,j} Bt[j][k] (u = A x with
+//                   A by rows and a dense x; v = A^T y with A by columns), up to 32 starts.  Work
+//                   items of at most kSpItemNnz entries (a run of short rows, or a segment of a
+//                   long row) are taken by warps; a warp walks an item once, each lane keeping 8
+//                   FP32 sums per group of 8 starts over a strided subset of the entries, then the
+//                   warp reduces each group (reduce-scatter: lane L ends with start L / 4);
+//   k_spmm_wide     the same for many starts (more than 32): the starts are cut into slabs of 64,
+//                   slab-major, so that the slab of Bt the warps gather from (64 starts x the
+//                   operand's length) stays in L2; a warp takes an item of a slab, its lanes own 2
+//                   starts each and walk the item's entries in order (each entry's index and value
+//                   broadcast from the lane that loaded it), reading one 256-byte row segment of Bt
+//                   per entry;
+//   k_spmm_fix      a long row's segments' sums added in segment order;
+//   k_spmv_support  u = A x over the support of a sparse x: the support's columns (A^T's rows)
+//                   scattered into a shared-memory chunk of u, one column at a time in support
+//                   order, the FMA chain of each u_i in that order;
+//   k_fin_support   the finalise's u = A x in compensated FP32 pairs over a small support (the
+//                   column scatter into 256-row chunks), |u| and u^2 summed in pair arithmetic;
+//   k_fin_csr       the same by rows for the other starts, 8 starts per pass over a row.
+// Every sum runs in a fixed order: a start's result does not depend on the schedule or on the
+// other starts.
+#include <cstdint>
+
+#include "block_util.cuh"
+#include "spca_internal.cuh"
+
+namespace spca {
+
+namespace {
+constexpr int SPT = 256;            // threads per CTA of the SpMM
+constexpr int SCH = 4096;           // rows of u per CTA of the support scatter
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ void fma8v(float (&acc)[8], float a, const float (&x)[8]) {
+#pragma unroll
+  for (int t = 0; t < 8; ++t) acc[t] = fmaf(a, x[t], acc[t]);
+}
+
+// one 32-byte load (sm_100+: 256-bit vector loads; p 32-byte aligned) through the non-coherent
+// path: the 8 starts of a packed row segment in one L1 request instead of two
+__device__ __forceinline__ void ldg8(const float *p, float (&v)[8]) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+
+// Sum over the warp of a[q] for q = (lane >> 2) & 7, in 9 shuffles: at each of the levels 16, 8
+// and 4 a lane keeps half of its values, adds its partner's copy of them and hands over the
+// other half; levels 2 and 1 finish the sum.  Both lanes of a pair form the same sum.
+__device__ __forceinline__ float reduce8(const float (&a)[8], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float t[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float send = b4 ? a[q] : a[q + 4];
+    const float keep = b4 ? a[q + 4] : a[q];
+    t[q] = keep + __shfl_xor_sync(FULL, send, 16);
+  }
+  float u[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float send = b3 ? t[q] : t[q + 2];
+    const float keep = b3 ? t[q + 2] : t[q];
+    u[q] = keep + __shfl_xor_sync(FULL, send, 8);
+  }
+  float w = (b2 ? u[1] : u[0]) + __shfl_xor_sync(FULL, b2 ? u[0] : u[1], 4);
+  w += __shfl_xor_sync(FULL, w, 2);
+  w += __shfl_xor_sync(FULL, w, 1);
+  return w;
+}
+
+// first k in [b, e) with col[k] >= v (col ascending on [b, e))
+__device__ __forceinline__ int64_t lower_bound_col(const int *__restrict__ col, int64_t b, int64_t e, int v) {
+  while (b < e) {
+    const int64_t m = b + ((e - b) >> 1);
+    if (col[m] < v) b = m + 1;
+    else e = m;
+  }
+  return b;
+}
+}  // namespace
+
+// grid (ceil(len / 32), ceil(rmax / 32)), block (32, 8): a 32 x 32 tile through shared memory
+__global__ void k_pack_t(const float *__restrict__ src, int64_t ld, int len, const int *__restrict__ list,
+                         const int *__restrict__ count, int rmax, const int *__restrict__ gate,
+                         float *__restrict__ Bt, int ldb) {
+  if (gate && *gate == 0) return;
+  const int cnt = count ? *count : rmax;
+  const int k0 = blockIdx.y * 32;
+  const int kpad = (cnt + kSpGroup - 1) / kSpGroup * kSpGroup;
+  if (k0 >= kpad) return;
+  __shared__ float tile[32][33];
+  const int j0 = blockIdx.x * 32;
+  for (int q = threadIdx.y; q < 32; q += 8) {
+    const int k = k0 + q, j = j0 + threadIdx.x;
+    float v = 0.0f;
+    if (k < cnt && j < len) v = src[(int64_t)(list ? list[k] : k) * ld + j];
+    tile[q][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += 8) {
+    const int j = j0 + q, k = k0 + threadIdx.x;
+    if (j < len && k < kpad) Bt[(int64_t)j * ldb + k] = tile[threadIdx.x][q];
+  }
+}
+
+cudaError_t launch_pack_t(const float *src, int64_t ld, int len, const int *list, const int *count,
+                          const int *gate, int rmax, float *Bt, int ldb, cudaStream_t st) {
+  const dim3 grid((unsigned)((len + 31) / 32), (unsigned)((rmax + 31) / 32));
+  k_pack_t<<<grid, dim3(32, 8), 0, st>>>(src, ld, len, list, count, rmax, gate, Bt, ldb);
+  return cudaGetLastError();
+}
+
+// NG groups of 8 starts per pass over an item's entries (the host takes NG = ceil(rmax / 8) <= 4):
+// each entry's index and value are loaded once for all of them
+template <int NG>
+__global__ void __launch_bounds__(SPT) k_spmm(SpMat M, const SpItem *__restrict__ items, int nitems,
+                                              const float *__restrict__ Bt, int ldb, const int *__restrict__ count,
+                                              const int *__restrict__ gate, const int *__restrict__ list,
+                                              float *__restrict__ out, int64_t ldo, float *__restrict__ part) {
+  if (gate && *gate == 0) return;
+  const int cnt = *count;
+  if (cnt <= 0) return;
+  const int ng = min(NG, (cnt + kSpGroup - 1) / kSpGroup);
+  const int lane = threadIdx.x & 31, q = lane >> 2;
+  const int nw = gridDim.x * (SPT / 32);
+  for (int it = blockIdx.x * (SPT / 32) + (threadIdx.x >> 5); it < nitems; it += nw) {
+    const int4 head = __ldg(reinterpret_cast<const int4 *>(items + it));   // row0, row1, seg
+    const int seg = head.z;
+    for (int row = head.x; row < head.y; ++row) {
+      const int64_t b = seg >= 0 ? items[it].nz0 : M.ptr[row];
+      const int64_t e = seg >= 0 ? items[it].nz1 : M.ptr[row + 1];
+      float acc[NG][8];
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc[g][t] = 0.0f;
+      int64_t k = b + lane;
+      // two entries per lane in flight; each lane's sums still run in entry order
+      for (; k + 32 < e; k += 64) {
+        const int j0 = __ldg(M.col + k), j1 = __ldg(M.col + k + 32);
+        const float a0 = __ldg(M.val + k), a1 = __ldg(M.val + k + 32);
+        const float *p0 = Bt + (int64_t)j0 * ldb, *p1 = Bt + (int64_t)j1 * ldb;
+        float x0[NG][8], x1[NG][8];
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+          if (g < ng) {
+            ldg8(p0 + 8 * g, x0[g]);
+            ldg8(p1 + 8 * g, x1[g]);
+          }
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+          if (g < ng) {
+            fma8v(acc[g], a0, x0[g]);
+            fma8v(acc[g], a1, x1[g]);
+          }
+      }
+      if (k < e) {
+        const int j0 = __ldg(M.col + k);
+        const float a0 = __ldg(M.val + k);
+        const float *p0 = Bt + (int64_t)j0 * ldb;
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+          if (g < ng) {
+            float x0[8];
+            ldg8(p0 + 8 * g, x0);
+            fma8v(acc[g], a0, x0);
+          }
+      }
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        if (g >= ng) break;
+        const float v = reduce8(acc[g], lane);
+        const int kk = g * kSpGroup + q;
+        if ((lane & 3) == 0 && kk < cnt) {
+          if (seg >= 0) part[(int64_t)seg * ldb + kk] = v;
+          else out[(int64_t)(list ? list[kk] : kk) * ldo + row] = v;
+        }
+      }
+    }
+  }
+}
+
+constexpr int kWideSlab = 64;   // starts per slab of k_spmm_wide (2 per lane)
+
+__global__ void __launch_bounds__(SPT, 3) k_spmm_wide(SpMat M, const SpItem *__restrict__ items, int nitems,
+                                                   const float *__restrict__ Bt, int ldb,
+                                                   const int *__restrict__ count, const int *__restrict__ gate,
+                                                   const int *__restrict__ list, float *__restrict__ out,
+                                                   int64_t ldo, float *__restrict__ part) {
+  if (gate && *gate == 0) return;
+  const int cnt = *count;
+  if (cnt <= 0) return;
+  const int lane = threadIdx.x & 31;
+  const int nslab = (cnt + kWideSlab - 1) / kWideSlab;
+  const int64_t units = (int64_t)nslab * nitems;
+  const int64_t nw = (int64_t)gridDim.x * (SPT / 32);
+  for (int64_t w = (int64_t)blockIdx.x * (SPT / 32) + (threadIdx.x >> 5); w < units; w += nw) {
+    const int slab = (int)(w / nitems), it = (int)(w - (int64_t)slab * nitems);
+    const int k = slab * kWideSlab + 2 * lane;      // this lane's two starts: k, k + 1
+    const bool on = k < cnt;                        // k + 1 < ldb whenever k < cnt (both even-aligned)
+    const float *B = Bt + k;
+    const int4 head = __ldg(reinterpret_cast<const int4 *>(items + it));   // row0, row1, seg
+    const int seg = head.z;
+    for (int row = head.x; row < head.y; ++row) {
+      const int64_t b = seg >= 0 ? items[it].nz0 : M.ptr[row];
+      const int64_t e = seg >= 0 ? items[it].nz1 : M.ptr[row + 1];
+      float2 acc = make_float2(0.0f, 0.0f);
+      for (int64_t base = b; base < e; base += 32) {
+        const int m = (int)min((int64_t)32, e - base);
+        const int jl = lane < m ? __ldg(M.col + base + lane) : 0;
+        const float al = lane < m ? __ldg(M.val + base + lane) : 0.0f;
+        int q = 0;
+        // eight entries' loads in flight, summed in entry order
+        for (; q + 8 <= m; q += 8) {
+          float2 y[8];
+          float a[8];
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            const int j = __shfl_sync(FULL, jl, q + g);
+            a[g] = __shfl_sync(FULL, al, q + g);
+            y[g] = on ? __ldg(reinterpret_cast<const float2 *>(B + (int64_t)j * ldb)) : make_float2(0.0f, 0.0f);
+          }
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            acc.x = fmaf(a[g], y[g].x, acc.x);
+            acc.y = fmaf(a[g], y[g].y, acc.y);
+          }
+        }
+        for (; q < m; ++q) {
+          const int j = __shfl_sync(FULL, jl, q);
+          const float a = __shfl_sync(FULL, al, q);
+          const float2 y = on ? __ldg(reinterpret_cast<const float2 *>(B + (int64_t)j * ldb)) : make_float2(0.0f, 0.0f);
+          acc.x = fmaf(a, y.x, acc.x);
+          acc.y = fmaf(a, y.y, acc.y);
+        }
+      }
+      if (on) {
+        if (seg >= 0) {
+          part[(int64_t)seg * ldb + k] = acc.x;
+          if (k + 1 < cnt) part[(int64_t)seg * ldb + k + 1] = acc.y;
+        } else {
+          out[(int64_t)(list ? list[k] : k) * ldo + row] = acc.x;
+          if (k + 1 < cnt) out[(int64_t)(list ? list[k + 1] : k + 1) * ldo + row] = acc.y;
+        }
+      }
+    }
+  }
+}
+
+// block per long row: its segments' sums in segment order
+__global__ void __launch_bounds__(256) k_spmm_fix(const SpLong *__restrict__ longs, const float *__restrict__ part,
+                                                  int ldb, const int *__restrict__ count,
+                                                  const int *__restrict__ gate, const int *__restrict__ list,
+                                                  float *__restrict__ out, int64_t ldo) {
+  if (gate && *gate == 0) return;
+  const int cnt = *count;
+  const SpLong L = longs[blockIdx.x];
+  for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+    float s = 0.0f;
+    for (int g = 0; g < L.nseg; ++g) s += part[(int64_t)(L.seg0 + g) * ldb + k];
+    out[(int64_t)(list ? list[k] : k) * ldo + L.row] = s;
+  }
+}
+
+cudaError_t launch_spmm(SpMat M, const SpPlan &P, const float *Bt, int ldb, const int *count, const int *gate,
+                        const int *list, int rmax, float *out, int64_t ldo, float *part, int sms, cudaStream_t st) {
+  if (P.nitems > 0) {
+    // up to 32 starts: lanes over entries (8 starts per 32-byte sector); more: slabs of 64 starts,
+    // lanes over starts
+    const bool wide = rmax > 32;
+    const int64_t units = (int64_t)P.nitems * (wide ? (rmax + kWideSlab - 1) / kWideSlab : 1);
+    const int64_t want = (units + SPT / 32 - 1) / (SPT / 32);
+    const int blocks = (int)(want < sms * 8 ? want : sms * 8);
+    if (wide)
+      k_spmm_wide<<<blocks, SPT, 0, st>>>(M, P.items, P.nitems, Bt, ldb, count, gate, list, out, ldo, part);
+    else if (rmax <= 8)
+      k_spmm<1><<<blocks, SPT, 0, st>>>(M, P.items, P.nitems, Bt, ldb, count, gate, list, out, ldo, part);
+    else if (rmax <= 16)
+      k_spmm<2><<<blocks, SPT, 0, st>>>(M, P.items, P.nitems, Bt, ldb, count, gate, list, out, ldo, part);
+    else if (rmax <= 24)
+      k_spmm<3><<<blocks, SPT, 0, st>>>(M, P.items, P.nitems, Bt, ldb, count, gate, list, out, ldo, part);
+    else
+      k_spmm<4><<<blocks, SPT, 0, st>>>(M, P.items, P.nitems, Bt, ldb, count, gate, list, out, ldo, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (P.nlong > 0) {
+    k_spmm_fix<<<P.nlong, 256, 0, st>>>(P.longs, part, ldb, count, gate, list, out, ldo);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+// grid (ceil(n / SCH), r): u = A x for start c over x's support (A^T by rows = A by columns),
+// for the starts the gather serves (active, swept at least once)
+__global__ void __launch_bounds__(256) k_spmv_support(SpMat AT, int n, const int *__restrict__ sup_idx,
+                                                      const float *__restrict__ sup_val, int cap, StartState s,
+                                                      float *__restrict__ U, int64_t ldu,
+                                                      const int *__restrict__ gate) {
+  if (*gate == 0) return;
+  const int c = blockIdx.y;
+  if (s.status[c] != ST_ACTIVE) return;
+  if (s.iters[c] == 0) return;   // a start not swept yet has a dense x: the product by rows
+  __shared__ float us[SCH];
+  __shared__ int64_t lo[256], hi[256];
+  __shared__ float xv[256];
+  const int base = blockIdx.x * SCH;
+  const int rows = min(SCH, n - base);
+  for (int i = threadIdx.x; i < SCH; i += 256) us[i] = 0.0f;
+  const int nnz = s.nnz[c];
+  const int *gi = sup_idx + (int64_t)c * cap;
+  const float *gv = sup_val + (int64_t)c * cap;
+  for (int t0 = 0; t0 < nnz; t0 += 256) {
+    __syncthreads();
+    if (t0 + (int)threadIdx.x < nnz) {
+      const int j = gi[t0 + threadIdx.x];
+      xv[threadIdx.x] = gv[t0 + threadIdx.x];
+      const int64_t b = lower_bound_col(AT.col, AT.ptr[j], AT.ptr[j + 1], base);
+      lo[threadIdx.x] = b;
+      hi[threadIdx.x] = lower_bound_col(AT.col, b, AT.ptr[j + 1], base + rows);
+    }
+    __syncthreads();
+    const int m = min(256, nnz - t0);
+    for (int q = 0; q < m; ++q) {
+      // the rows of one column are distinct: no two threads update the same u_i
+      const float x = xv[q];
+      for (int64_t k = lo[q] + threadIdx.x; k < hi[q]; k += 256) {
+        const int i = __ldg(AT.col + k) - base;
+        us[i] = fmaf(x, __ldg(AT.val + k), us[i]);
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  float *u = U + (int64_t)c * ldu + base;
+  for (int i = threadIdx.x; i < rows; i += 256) u[i] = us[i];
+}
+
+cudaError_t launch_spmv_support(SpMat AT, int n, const int *sup_idx, const float *sup_val, int cap, StartState s,
+                                int r, float *U, int64_t ldu, const int *gate, cudaStream_t st) {
+  const dim3 grid((unsigned)((n + SCH - 1) / SCH), (unsigned)r);
+  k_spmv_support<<<grid, 256, 0, st>>>(AT, n, sup_idx, sup_val, cap, s, U, ldu, gate);
+  return cudaGetLastError();
+}
+
+// grid (ceil(n / 256), ceil(count / 8)): rows [256 b, 256 b + 256) of u = A x for the starts
+// 8 g .. 8 g + 7, whose x are packed start-fastest in Bt (one 32-byte sector per entry for the 8),
+// a warp per 32 rows.  Each lane keeps a compensated FP32-pair sum per start over a strided subset
+// of the row; the lanes' pairs are added in a fixed butterfly in pair arithmetic, and so are the
+// warp's sums of |u_i| and u_i^2 over its rows (GB300 issues FP64 at a small fraction of the FP32
+// rate, so no FP64 runs per row).  Per CTA and start the warps' sums are added in warp order, in
+// FP64, into partials[(c * nchunks + b) * 2 + {0, 1}].
+__global__ void __launch_bounds__(256) k_fin_csr(SpMat A, const float *__restrict__ Bt, int ldb, int count,
+                                                 const int *__restrict__ nnz, int cap, float *__restrict__ U,
+                                                 int64_t ldu, double *__restrict__ partials) {
+  __shared__ double red[8][8][2];
+  const int b = blockIdx.x, c0 = blockIdx.y * 8;
+  const int nc = min(8, count - c0);
+  if (nnz) {   // starts whose support the column scatter serves are done there
+    bool any = false;
+    for (int g = 0; g < nc; ++g) any |= nnz[c0 + g] > cap;
+    if (!any) return;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float *B = Bt + c0;
+  F32Pair l1[8], l2[8];
+  for (int q = 0; q < 32; ++q) {
+    const int i = b * 256 + w * 32 + q;
+    if (i >= A.rows) break;
+    F32Pair acc[8];
+    for (int64_t k = A.ptr[i] + lane; k < A.ptr[i + 1]; k += 32) {
+      const float a = A.val[k];
+      float xs[8];
+      ldg8(B + (int64_t)A.col[k] * ldb, xs);
+#pragma unroll
+      for (int g = 0; g < 8; ++g) f32pair_fma(acc[g], a, xs[g]);
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      F32Pair t = acc[g];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        F32Pair other;
+        other.hi = __shfl_xor_sync(FULL, t.hi, o);
+        other.lo = __shfl_xor_sync(FULL, t.lo, o);
+        t = f32pair_add(t, other);
+      }
+      // every lane now holds u_i
+      if (lane == 0 && g < nc && !(nnz && nnz[c0 + g] <= cap)) U[(int64_t)(c0 + g) * ldu + i] = __fadd_rn(t.hi, t.lo);
+      l1[g] = f32pair_add(l1[g], f32pair_abs(t));
+      l2[g] = f32pair_add(l2[g], f32pair_sq(t));
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      red[w][g][0] = f32pair_value(l1[g]);
+      red[w][g][1] = f32pair_value(l2[g]);
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nc && !(nnz && nnz[c0 + threadIdx.x] <= cap)) {
+    const int g = threadIdx.x;
+    double s1 = 0.0, s2 = 0.0;
+    for (int ww = 0; ww < 8; ++ww) {
+      s1 += red[ww][g][0];
+      s2 += red[ww][g][1];
+    }
+    double *o = partials + ((int64_t)(c0 + g) * gridDim.x + b) * 2;
+    o[0] = s1;
+    o[1] = s2;
+  }
+}
+
+// grid (ceil(n / 256), count): rows [256 b, 256 b + 256) of u = A x for start c over its support
+// (at most cap entries), from A by columns: each thread owns one row's compensated FP32-pair sum,
+// the support's columns are added one at a time in support order (the products of one column go
+// to distinct rows).  |u_i| and u_i^2 are summed over the CTA in pair arithmetic and written, as
+// FP64, to partials like k_fin_csr's.
+__global__ void __launch_bounds__(256) k_fin_support(SpMat AT, const int *__restrict__ sup_idx,
+                                                     const float *__restrict__ sup_val, int ldsup,
+                                                     const int *__restrict__ nnz, int cap, float *__restrict__ U,
+                                                     int64_t ldu, double *__restrict__ partials) {
+  __shared__ float us_hi[256], us_lo[256];
+  __shared__ int64_t lo_s[256], hi_s[256];
+  __shared__ float xv[256];
+  __shared__ double red[8][2];
+  const int b = blockIdx.x, c = blockIdx.y;
+  const int m = nnz[c];
+  if (m > cap) return;            // the rows' kernel serves this start
+  const int base = b * 256, rows = min(256, AT.cols - base);
+  us_hi[threadIdx.x] = 0.0f;
+  us_lo[threadIdx.x] = 0.0f;
+  for (int t0 = 0; t0 < m; t0 += 256) {
+    __syncthreads();
+    if (t0 + (int)threadIdx.x < m) {
+      const int j = sup_idx[(int64_t)c * ldsup + t0 + threadIdx.x];
+      xv[threadIdx.x] = sup_val[(int64_t)c * ldsup + t0 + threadIdx.x];
+      const int64_t lo = lower_bound_col(AT.col, AT.ptr[j], AT.ptr[j + 1], base);
+      lo_s[threadIdx.x] = lo;
+      hi_s[threadIdx.x] = lower_bound_col(AT.col, lo, AT.ptr[j + 1], base + rows);
+    }
+    __syncthreads();
+    const int mm = min(256, m - t0);
+    for (int q = 0; q < mm; ++q) {
+      // a column holds at most one entry per row: at most 256 entries in this chunk
+      const int64_t k = lo_s[q] + threadIdx.x;
+      if (k < hi_s[q]) {
+        const int i = AT.col[k] - base;
+        F32Pair s;
+        s.hi = us_hi[i];
+        s.lo = us_lo[i];
+        f32pair_fma(s, xv[q], AT.val[k]);
+        us_hi[i] = s.hi;
+        us_lo[i] = s.lo;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  F32Pair u;
+  u.hi = us_hi[threadIdx.x];
+  u.lo = us_lo[threadIdx.x];
+  if ((int)threadIdx.x < rows) U[(int64_t)c * ldu + base + threadIdx.x] = __fadd_rn(u.hi, u.lo);
+  F32Pair a1 = f32pair_abs(u), a2 = f32pair_sq(u);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    F32Pair t1, t2;
+    t1.hi = __shfl_xor_sync(FULL, a1.hi, o);
+    t1.lo = __shfl_xor_sync(FULL, a1.lo, o);
+    t2.hi = __shfl_xor_sync(FULL, a2.hi, o);
+    t2.lo = __shfl_xor_sync(FULL, a2.lo, o);
+    a1 = f32pair_add(a1, t1);
+    a2 = f32pair_add(a2, t2);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[w][0] = f32pair_value(a1);
+    red[w][1] = f32pair_value(a2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s1 = 0.0, s2 = 0.0;
+    for (int ww = 0; ww < 8; ++ww) {
+      s1 += red[ww][0];
+      s2 += red[ww][1];
+    }
+    double *o = partials + ((int64_t)c * gridDim.x + b) * 2;
+    o[0] = s1;
+    o[1] = s2;
+  }
+}
+
+// starts with at most kSpSupportCap nonzeros (when their support lists are given): the column
+// scatter; the others by rows, in groups of at most ldb (the packed operand's width)
+cudaError_t launch_fin_csr(SpMat A, SpMat AT, const float *X, int64_t ldx, int count, const int *nnz,
+                           const int *sup_idx, const float *sup_val, int ldsup, float *Bt, int ldb, float *U,
+                           int64_t ldu, double *partials, cudaStream_t st) {
+  const int nchunks = (A.rows + 255) / 256;
+  const int cap = sup_idx ? kSpSupportCap : -1;
+  if (sup_idx) {
+    k_fin_support<<<dim3((unsigned)nchunks, (unsigned)count), 256, 0, st>>>(AT, sup_idx, sup_val, ldsup, nnz, cap, U,
+                                                                              ldu, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  for (int c0 = 0; c0 < count; c0 += ldb) {
+    const int m = count - c0 < ldb ? count - c0 : ldb;
+    cudaError_t e = launch_pack_t(X + (int64_t)c0 * ldx, ldx, A.cols, nullptr, nullptr, nullptr, m, Bt, ldb, st);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)nchunks, (unsigned)((m + 7) / 8));
+    k_fin_csr<<<grid, 256, 0, st>>>(A, Bt, ldb, m, sup_idx ? nnz + c0 : nullptr, cap, U + (int64_t)c0 * ldu, ldu,
+                                    partials + (int64_t)c0 * nchunks * 2);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace spca

@@ -30,6 +30,17 @@ struct spca_handle {
   cudaStream_t user = nullptr;     // the caller's stream: each call starts after its prior work
   cudaEvent_t order_ev = nullptr;
   float *A32 = nullptr, *AT32 = nullptr;   // FP32 copies
+  // sparse A (spca_create_csr): by rows and by columns (A^T by rows), the SpMM work items of
+  // each, the packed transposed operand of the SpMM (rows x ldb, starts fastest) and the
+  // partial sums of split rows
+  bool sparse = false;
+  int64_t *a_ptr = nullptr, *at_ptr = nullptr;
+  int *a_col = nullptr, *at_col = nullptr;
+  float *a_val = nullptr, *at_val = nullptr;
+  SpPlan plan_a{}, plan_at{};
+  float *Bt = nullptr, *sp_part = nullptr;
+  int ldb = 0;
+  float *ysum = nullptr;                   // chunk sums of the y-step for long u (r x ceil(n / kYChunk))
   bool tc_ok = false;                      // the device has tcgen05 tensor cores (sm_100+)
   int sms = 1;                             // streaming multiprocessors of the device
   void *Apl = nullptr, *ATpl = nullptr;    // tensor-core planes (kPlanes FP16 each, row-scaled)
@@ -195,9 +206,11 @@ void free_workspace(spca_handle *h) {
   void *ptrs[] = {h->X, h->V, h->U, h->Y, h->Xpl, h->Ypl, h->sup_idx, h->sup_val, h->act, h->rank,
                   h->status, h->iters, h->nnz, h->F, h->F_prev, h->gamma, h->f, h->ev, h->thr, h->tprev, h->xfast,
                   h->partials, h->ctrl, h->best, h->y_out, h->x_out, h->support_out, h->nnz_out,
-                  h->mark, h->colpos, h->collist, h->AS, h->XS, h->x_scale, h->x_inv};
+                  h->mark, h->colpos, h->collist, h->AS, h->XS, h->x_scale, h->x_inv, h->Bt, h->sp_part, h->ysum};
   for (void *q : ptrs)
     if (q) cudaFree(q);
+  h->Bt = h->sp_part = h->ysum = nullptr;
+  h->ldb = 0;
   h->mark = h->colpos = h->collist = nullptr;
   h->AS = h->XS = nullptr;
   h->X = h->V = h->U = h->Y = nullptr;
@@ -237,6 +250,7 @@ int ensure_workspace(spca_handle *h, int r) {
   CK(dalloc(&h->f, r)); CK(dalloc(&h->ev, r)); CK(dalloc(&h->thr, r));
   CK(dalloc(&h->tprev, r)); CK(dalloc(&h->xfast, r));
   CK(dalloc(&h->partials, (size_t)r * nchunks * 2));
+  CK(dalloc(&h->ysum, (size_t)r * ((n + kYChunk - 1) / kYChunk)));
   CK(dalloc(&h->ctrl, 2)); CK(dalloc(&h->best, 1));
   CK(dalloc(&h->y_out, (size_t)h->ldU)); CK(dalloc(&h->x_out, (size_t)h->ldX));
   CK(dalloc(&h->support_out, (size_t)p)); CK(dalloc(&h->nnz_out, 1));
@@ -261,6 +275,14 @@ int ensure_workspace(spca_handle *h, int r) {
     CK(dalloc(&h->XS, (size_t)kPlanes * r * h->kcap, 2));
     CK(make_p_maps(&h->pmAS, h->AS, n, h->kcap, 2));
     CK(make_plane_map(&h->tmXS2, h->XS, r, h->kcap, 2, tc_box_rows(2), tc_bk(2)));
+  }
+  if (h->sparse) {
+    h->ldb = (r + kSpGroup - 1) / kSpGroup * kSpGroup;
+    const int64_t bt_rows = std::max(n, p);
+    const int nseg = std::max(1, std::max(h->plan_a.nseg, h->plan_at.nseg));
+    CK(dalloc(&h->Bt, (size_t)bt_rows * h->ldb));
+    CK(dalloc(&h->sp_part, (size_t)nseg * h->ldb));
+    CK(cudaMemsetAsync(h->Bt, 0, (size_t)bt_rows * h->ldb * sizeof(float), h->stream));
   }
   h->r_cap = r;
   return SPCA_OK;
@@ -336,6 +358,8 @@ int check_form_params(spca_handle *h, int form, double s, double gamma, int gamm
 int resolve_engine(spca_handle *h, int engine, int *out) {
   if (engine != SPCA_ENGINE_AUTO && engine != SPCA_ENGINE_SIMT && engine != SPCA_ENGINE_TC)
     return fail(h, SPCA_E_INVALID, "unknown engine%s");
+  if (engine == SPCA_ENGINE_TC && h->sparse)
+    return fail(h, SPCA_E_UNSUPPORTED, "a sparse A runs on the CUDA-core engine%s");
   if (engine == SPCA_ENGINE_TC && !h->tc_ok)
     return fail(h, SPCA_E_UNSUPPORTED, "tensor-core engine needs an sm_100+ device%s");
   *out = engine == SPCA_ENGINE_AUTO ? (h->tc_ok ? SPCA_ENGINE_TC : SPCA_ENGINE_SIMT) : engine;
@@ -375,11 +399,29 @@ TcPairs pairs_hi() {
   return t;
 }
 
+SpMat sp_rows(const spca_handle *h) { return SpMat{h->a_ptr, h->a_col, h->a_val, (int)h->n, (int)h->p}; }
+SpMat sp_cols(const spca_handle *h) { return SpMat{h->at_ptr, h->at_col, h->at_val, (int)h->p, (int)h->n}; }
+
+// sparse A: u = A x by rows for the listed rows of X (count *count, list null = the first
+// *count rows): x packed transposed, then the SpMM over A's rows (gated)
+int sweep_u_rows(spca_handle *h, int r, const int *gate, const int *count, const int *list) {
+  const int n = (int)h->n, p = (int)h->p;
+  CK(timed(h, SPCA_K_U_DENSE, 2 + (h->plan_a.nlong > 0), [&] {
+    cudaError_t e = launch_pack_t(h->X, h->ldX, p, list, count, gate, r, h->Bt, h->ldb, h->stream);
+    if (e != cudaSuccess) return e;
+    (void)n;
+    return launch_spmm(sp_rows(h), h->plan_a, h->Bt, h->ldb, count, gate, list, r, h->U, h->ldU, h->sp_part,
+                       h->sms, h->stream);
+  }));
+  return SPCA_OK;
+}
+
 // u = A x for every active row of h->X: dense contraction (gated: runs only if *gate != 0).  The
 // tensor-core engine packs the active starts (h->act, count *nact) into consecutive plane rows.
 int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int *nact, int nhost, bool lowp,
                   const int *list = nullptr) {
   if (!list) list = h->act;
+  if (h->sparse) return sweep_u_rows(h, r, gate, nact, list);
   const int n = (int)h->n, p = (int)h->p;
   cudaStream_t st = h->stream;
   if (engine == SPCA_ENGINE_TC) {
@@ -426,9 +468,24 @@ int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const i
   cudaStream_t st = h->stream;
   const bool tc = engine == SPCA_ENGINE_TC;
   const int64_t ypstride = (int64_t)h->r_cap * h->ldU;
+  if (h->sparse) {
+    // y-step, y of the active starts packed transposed, the SpMM over A's columns
+    CK(timed(h, SPCA_K_YSTEP, 2, [&] {
+      cudaError_t e = launch_ystep(form, h->U, h->ldU, n, r, h->Y, nullptr, 0, nullptr, S, h->X, h->ldX, p, h->ysum,
+                                   st);
+      if (e != cudaSuccess) return e;
+      return launch_pack_t(h->Y, h->ldU, n, h->act, nact, nullptr, r, h->Bt, h->ldb, st);
+    }));
+    CK(timed(h, SPCA_K_V, 1 + (h->plan_at.nlong > 0), [&] {
+      return launch_spmm(sp_cols(h), h->plan_at, h->Bt, h->ldb, nact, nullptr, h->act, r, h->V, h->ldX,
+                         h->sp_part, h->sms, st);
+    }));
+    (void)nhost;
+    return SPCA_OK;
+  }
   CK(timed(h, SPCA_K_YSTEP, 1, [&] {
     return launch_ystep(form, h->U, h->ldU, n, r, tc ? nullptr : h->Y, tc ? h->Ypl : nullptr, ypstride,
-                        tc ? h->rank : nullptr, S, h->X, h->ldX, p, st);
+                        tc ? h->rank : nullptr, S, h->X, h->ldX, p, h->ysum, st);
   }));
   if (tc && lowp) {
     CK(timed(h, SPCA_K_V, 1, [&] {
@@ -505,6 +562,7 @@ const char *spca_last_error(const spca_handle *h) { return h ? h->last_error : "
 
 int spca_deflate(spca_handle *h, const float *x, int x_is_device) {
   if (!h || !x) return fail(h, SPCA_E_INVALID, "NULL argument%s");
+  if (h->sparse) return fail(h, SPCA_E_UNSUPPORTED, "projection deflation of a sparse A%s");
   RC(enter(h));
   const int64_t n = h->n, p = h->p;
   cudaStream_t st = h->stream;
@@ -568,7 +626,9 @@ void spca_destroy(spca_handle *h) {
   free_workspace(h);
   free_otf(h);
   void *ptrs[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->a_scale, h->a_inv, h->at_scale, h->at_inv,
-                  h->flag, h->dev_err, h->sk.ws, h->sk.flags, h->defl_x, h->defl_w};
+                  h->flag, h->dev_err, h->sk.ws, h->sk.flags, h->defl_x, h->defl_w,
+                  h->a_ptr, h->a_col, h->a_val, h->at_ptr, h->at_col, h->at_val,
+                  h->plan_a.items, h->plan_a.longs, h->plan_at.items, h->plan_at.longs};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
@@ -649,6 +709,95 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     }
     CK(cudaStreamSynchronize(h->stream));
     if (*h->h_flag) return fail(h, SPCA_E_INVALID, "A has a non-finite entry%s");
+    return SPCA_OK;
+  }();
+  if (rc != SPCA_OK) {
+    spca_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return SPCA_OK;
+}
+
+int spca_create_csr(spca_handle **out, int64_t n, int64_t p, int64_t nnz, const int64_t *row_ptr,
+                    const int32_t *col_idx, const float *values, int is_device, void *cuda_stream) {
+  spca_handle *h = nullptr;
+  if (!out || !row_ptr || (nnz > 0 && (!col_idx || !values))) return SPCA_E_INVALID;
+  if (n < 1 || p < 1 || nnz < 0 || n > INT32_MAX || p > INT32_MAX || nnz > INT32_MAX) return SPCA_E_INVALID;
+  int ndev = 0, dev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SPCA_E_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPCA_E_CUDA;
+  h = new (std::nothrow) spca_handle();
+  if (!h) return SPCA_E_NOMEM;
+  int rc = [&]() -> int {
+    h->n = n; h->p = p;
+    h->sparse = true;
+    h->tc_ok = false;   // the sweeps run on the sparse CUDA-core kernels
+    h->user = (cudaStream_t)cuda_stream;
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming));
+    RC(enter(h));
+    CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaMallocHost((void **)&h->h_ctrl, 2 * sizeof(Ctrl)));
+    CK(cudaMallocHost((void **)&h->h_flag, 2 * sizeof(int)));
+    h->h_flag[0] = h->h_flag[1] = 0;
+    CK(dalloc(&h->flag, 1));
+    CK(dalloc(&h->dev_err, 1));
+    CK(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
+    // the input on the host (the canonical layouts are built there)
+    std::vector<int64_t> hp;
+    std::vector<int32_t> hc;
+    std::vector<float> hv;
+    const int64_t *P = row_ptr;
+    const int32_t *Cc = col_idx;
+    const float *Vv = values;
+    if (is_device) {
+      hp.resize((size_t)n + 1);
+      hc.resize((size_t)nnz);
+      hv.resize((size_t)nnz);
+      CK(cudaMemcpyAsync(hp.data(), row_ptr, hp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+      if (nnz > 0) {
+        CK(cudaMemcpyAsync(hc.data(), col_idx, hc.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(hv.data(), values, hv.size() * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+      }
+      CK(cudaStreamSynchronize(h->stream));
+      P = hp.data();
+      Cc = hc.data();
+      Vv = hv.data();
+    }
+    HostCsr A, AT;
+    if (const char *bad = sp_canonical(n, p, nnz, P, Cc, Vv, &A, &AT)) return fail(h, SPCA_E_INVALID, "%s", bad);
+    const size_t m = A.col.size();
+    CK(dalloc(&h->a_ptr, (size_t)n + 1));
+    CK(dalloc(&h->at_ptr, (size_t)p + 1));
+    CK(dalloc(&h->a_col, m + 1)); CK(dalloc(&h->a_val, m + 1));
+    CK(dalloc(&h->at_col, m + 1)); CK(dalloc(&h->at_val, m + 1));
+    CK(cudaMemcpyAsync(h->a_ptr, A.ptr.data(), A.ptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->at_ptr, AT.ptr.data(), AT.ptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                       h->stream));
+    if (m > 0) {
+      CK(cudaMemcpyAsync(h->a_col, A.col.data(), m * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(h->a_val, A.val.data(), m * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(h->at_col, AT.col.data(), m * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(h->at_val, AT.val.data(), m * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    }
+    // the SpMM work items of both layouts
+    for (int side = 0; side < 2; ++side) {
+      std::vector<SpItem> items;
+      std::vector<SpLong> longs;
+      SpPlan &pl = side == 0 ? h->plan_a : h->plan_at;
+      sp_plan(side == 0 ? A.ptr : AT.ptr, &items, &longs, &pl.nseg);
+      pl.nitems = (int)items.size();
+      pl.nlong = (int)longs.size();
+      CK(dalloc(&pl.items, items.size() + 1));
+      CK(dalloc(&pl.longs, longs.size() + 1));
+      if (!items.empty())
+        CK(cudaMemcpyAsync(pl.items, items.data(), items.size() * sizeof(SpItem), cudaMemcpyHostToDevice, h->stream));
+      if (!longs.empty())
+        CK(cudaMemcpyAsync(pl.longs, longs.data(), longs.size() * sizeof(SpLong), cudaMemcpyHostToDevice,
+                           h->stream));
+      CK(cudaStreamSynchronize(h->stream));   // the host vectors go out of scope
+    }
     return SPCA_OK;
   }();
   if (rc != SPCA_OK) {
@@ -796,7 +945,9 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   xa.gamma_fixed = P.gamma;
   xa.tol = P.tol; xa.max_iter = max_iter;
   xa.cap = p;
-  xa.sparse_cap = p / 8 > 0 ? p / 8 : 1;
+  // the support gather takes supports up to sparse_cap; a sparse A's gather scatters the
+  // support's columns one at a time, so it pays only for small supports
+  xa.sparse_cap = h->sparse ? std::min(p, kSpSupportCap) : (p / 8 > 0 ? p / 8 : 1);
   const int C = target ? P.gamma_calib_sweeps : 0;
   // the x-step's switches follow each start's own sweep count (calibration sweeps of Section 4.1,
   // then the frozen gamma; the stopping rule compares two FP32 sweeps)
@@ -837,6 +988,9 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     if (otf) RC(sweep_u_dense(h, engine, r, &cur->n_new, &cur->n_new, r, false, h->new_slot));
     if (pl.union_in) RC(sweep_u_union(h, S, cur, r));
     CK(timed(h, SPCA_K_U_SPARSE, 1, [&] {
+      if (h->sparse)
+        return launch_spmv_support(sp_cols(h), n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU, &cur->use_gather,
+                                   st);
       if (pl.lowp)
         return launch_gemm1_sparse_lowp(h->ATpl, h->ldAT, h->at_inv, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
                                         &cur->use_gather, st);
@@ -977,7 +1131,34 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   RC(read_dev_err(h));
 
   // ---- a7: FP64-class objective, best start, y(x) and support of the best x
-  if (otf) {
+  if (h->sparse) {
+    // u = A x by rows in compensated FP32 pairs, then f, the best start and its outputs
+    OtfArchive view = h->arc;
+    if (!otf) {
+      view.x = h->X;
+      view.U = h->U;
+      view.gamma = S.gamma;
+      view.f = S.f;
+      view.ev = S.ev;
+    }
+    const int cnt = otf ? l : r;
+    double *part = otf ? h->otf_partials : h->partials;
+    CK(timed(h, SPCA_K_FINALISE, 4, [&] {
+      // the support lists are kept for a plain solve's starts (on-the-fly replacement archives x only)
+      cudaError_t e = launch_fin_csr(sp_rows(h), sp_cols(h), view.x, h->ldX, cnt, otf ? nullptr : S.nnz,
+                                     otf ? nullptr : h->sup_idx, otf ? nullptr : h->sup_val, p, h->Bt, h->ldb, view.U,
+                                     h->ldU, part, st);
+      if (e == cudaSuccess) e = launch_objective_reduce(form, part, (n + 255) / 256, p, view, cnt, h->ldX, st);
+      StartState Sa{};
+      Sa.f = view.f;
+      Sa.ev = view.ev;
+      if (e == cudaSuccess) e = launch_best(form, target ? 1 : 0, Sa, cnt, h->best, st);
+      if (e == cudaSuccess)
+        e = launch_best_outputs(form, h->best, view.U, h->ldU, n, view.x, h->ldX, p, h->y_out, h->x_out,
+                                h->support_out, h->nnz_out, st);
+      return e;
+    }));
+  } else if (otf) {
     CK(timed(h, SPCA_K_FINALISE, 4, [&] {
       cudaError_t e = launch_otf_objectives(form, h->AT32, h->ldAT, n, p, h->arc, l, h->ldX, h->ldU,
                                             h->otf_partials, st);

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 #include "../../include/spca.h"
 
@@ -137,6 +138,72 @@ cudaError_t launch_otf_retire(int r, int l, StartState s, int *slot_start, int *
 // Table 1 objective, explained variance and u = A x of the l archived starts (gamma: arc.gamma)
 cudaError_t launch_otf_objectives(int form, const float *AT, int64_t ldat, int n, int p, OtfArchive arc, int l,
                                   int64_t ldx, int64_t ldu, double *partials, cudaStream_t st);
+// f (Table 1) and the explained variance of `count` starts from the FP64 partial sums of |u_i|
+// and u_i^2 (partials[(c * nchunks + b) * 2 + {0, 1}]) and ||x||_0, ||x||_1 of arc.x (gamma: arc.gamma)
+cudaError_t launch_objective_reduce(int form, const double *partials, int nchunks, int p, OtfArchive arc, int count,
+                                    int64_t ldx, cudaStream_t st);
+
+// ---------------------------------------------------------------- sparse A (compressed rows)
+// One CSR matrix on the device (rows x cols; indices ascending within a row, none repeated).
+struct SpMat {
+  const int64_t *ptr;
+  const int *col;
+  const float *val;
+  int rows, cols;
+};
+// Work item of the SpMM: whole rows [row0, row1) (seg < 0), or the entries [nz0, nz1) of the long
+// row row0 whose sums go to partial slot seg.  Items hold at most kSpItemNnz entries and
+// kSpItemRows rows.
+struct SpItem {
+  int row0, row1, seg, pad;
+  int64_t nz0, nz1;
+};
+struct SpLong {       // a row split into nseg segments, partial slots seg0 .. seg0 + nseg - 1
+  int row, seg0, nseg, pad;
+};
+struct SpPlan {       // device arrays of items and long rows
+  SpItem *items = nullptr;
+  SpLong *longs = nullptr;
+  int nitems = 0, nlong = 0, nseg = 0;
+};
+constexpr int kSpItemNnz = 2048;
+constexpr int kSpItemRows = 32;
+constexpr int kSpGroup = 8;     // starts per pass of the SpMM (one 32-byte sector of Bt)
+constexpr int kSpSupportCap = 256;   // largest support the column scatter serves
+// host side (sparse_host.cu): a CSR matrix in host memory
+struct HostCsr {
+  std::vector<int64_t> ptr;
+  std::vector<int> col;
+  std::vector<float> val;
+  int64_t rows = 0, cols = 0;
+};
+// checks a CSR input (n x p, nnz entries) and builds the canonical A by rows and by columns
+// (A^T by rows); returns nullptr, or what is wrong with the input
+const char *sp_canonical(int64_t n, int64_t p, int64_t nnz, const int64_t *ptr, const int32_t *col,
+                         const float *val, HostCsr *A, HostCsr *AT);
+// the SpMM work items of a CSR matrix given its row offsets
+void sp_plan(const std::vector<int64_t> &ptr, std::vector<SpItem> *items, std::vector<SpLong> *longs, int *nseg);
+// Bt[j * ldb + k] = src[list[k] * ld + j] (list = identity when null), j < len, k < *count (rmax
+// when count is null), and 0 for *count <= k < the next multiple of kSpGroup; rmax >= *count sizes
+// the grid; gated
+cudaError_t launch_pack_t(const float *src, int64_t ld, int len, const int *list, const int *count,
+                          const int *gate, int rmax, float *Bt, int ldb, cudaStream_t st);
+// out[list[k] * ldo + i] = sum_{e in row i of M} val_e Bt[col_e * ldb + k], i < M.rows, k < *count
+// <= rmax (part: P.nseg x ldb floats of scratch); gated
+cudaError_t launch_spmm(SpMat M, const SpPlan &P, const float *Bt, int ldb, const int *count, const int *gate,
+                        const int *list, int rmax, float *out, int64_t ldo, float *part, int sms, cudaStream_t st);
+// u = A x over the support lists of the starts the gather serves (active, swept at least once),
+// from A by columns (AT: CSR of A^T); gated
+cudaError_t launch_spmv_support(SpMat AT, int n, const int *sup_idx, const float *sup_val, int cap, StartState s,
+                                int r, float *U, int64_t ldu, const int *gate, cudaStream_t st);
+// u = A x of `count` rows of X in compensated FP32 pairs, into U; FP64 partial sums of |u_i| and
+// u_i^2 per 256-row chunk to partials (count * ceil(n / 256) * 2 doubles).  With support lists
+// (sup_idx / sup_val, row c at c * ldsup, nnz[c] entries), a start with at most kSpSupportCap
+// nonzeros is summed over its support from A by columns (AT); the others by rows of A, their x
+// packed into Bt (A.cols x ldb, ldb a multiple of 8) ldb starts at a time
+cudaError_t launch_fin_csr(SpMat A, SpMat AT, const float *X, int64_t ldx, int count, const int *nnz,
+                           const int *sup_idx, const float *sup_val, int ldsup, float *Bt, int ldb, float *U,
+                           int64_t ldu, double *partials, cudaStream_t st);
 
 // C[m, j] = sum_k P[m, k] Q[j, k]  (both operands K-contiguous); with gate != nullptr the
 // launch does nothing unless *gate != 0 (the dense u = A x is needed this sweep)
@@ -160,9 +227,12 @@ cudaError_t launch_gemm1_sparse_lowp(const void *AT0, int64_t ldat, const float 
 // as tensor-core planes (Ypl != nullptr, row rank[c] when rank is given, else c; plane t at
 // Ypl + t * plane_stride): 1 plane of +-kQScale for L1 variance, the 2 planes of kQScale y for
 // L2 variance)
+// With ysum (r * ceil(n / kYChunk) floats of scratch) and n > 2 kYChunk, a CTA per chunk of
+// kYChunk entries and start (L2 variance: the chunks' sums of u_i^2 added in chunk order).
+constexpr int kYChunk = 8192;
 cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, float *Y,
                          void *Ypl, int64_t plane_stride, const int *rank, StartState s, float *X,
-                         int64_t ldX, int p, cudaStream_t st);
+                         int64_t ldX, int p, float *ysum, cudaStream_t st);
 
 // projection deflation A <- A (I - z z^T), z = x / ||x||_2, in place on the FP32 A (n x p, lda):
 // *inv = 1 / ||x||_2 (0 when x = 0: A is then left as is), w (n doubles) = A z

@@ -21,7 +21,7 @@ SPCA_ST_MAXITER, SPCA_ST_CONVERGED, SPCA_ST_DEGENERATE = 0, 1, 2
 SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC = 0, 1, 2
 
 # every symbol include/spca.h declares
-EXPORTS = ("spca_create", "spca_solve", "spca_xstep", "spca_products", "spca_deflate", "spca_profile_enable",
+EXPORTS = ("spca_create", "spca_create_csr", "spca_solve", "spca_xstep", "spca_products", "spca_deflate", "spca_profile_enable",
            "spca_profile_query", "spca_objective_noalloc",
            "spca_destroy", "spca_strerror", "spca_last_error")
 SPCA_K_ALL, SPCA_K_INIT, SPCA_K_U_DENSE, SPCA_K_U_SPARSE, SPCA_K_YSTEP, SPCA_K_V, SPCA_K_XSTEP, \
@@ -77,6 +77,10 @@ def load(path: str = LIB_PATH):
                                     ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_void_p]
         lib.spca_solve.restype = ctypes.c_int
+        lib.spca_create_csr.restype = ctypes.c_int
+        lib.spca_create_csr.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.c_void_p]
         lib.spca_solve.argtypes = [ctypes.c_void_p, ctypes.POINTER(spca_params), ctypes.c_void_p,
                                    ctypes.POINTER(spca_result)]
         lib.spca_xstep.restype = ctypes.c_int
@@ -129,6 +133,22 @@ def spca_create(A, n: int, p: int, lda: int, in_dtype: int, a_is_device: bool, s
     ptr = A if isinstance(A, int) else A.ctypes.data
     st = load().spca_create(ctypes.byref(h), ctypes.c_void_p(ptr), n, p, lda, in_dtype,
                             int(a_is_device), storage, ctypes.c_void_p(stream))
+    return st, h
+
+
+def spca_create_csr(n: int, p: int, nnz: int, row_ptr, col_idx, values, is_device: bool, stream: int = 0):
+    """row_ptr (int64), col_idx (int32), values (float32): host numpy arrays, or device addresses
+    (ints) with is_device."""
+    h = ctypes.c_void_p()
+    if is_device:
+        ptrs = [int(row_ptr), int(col_idx), int(values)]
+    else:
+        arrs = [np.ascontiguousarray(row_ptr, dtype=np.int64), np.ascontiguousarray(col_idx, dtype=np.int32),
+                np.ascontiguousarray(values, dtype=np.float32)]
+        ptrs = [a.ctypes.data for a in arrs]
+    st = load().spca_create_csr(ctypes.byref(h), int(n), int(p), int(nnz), ctypes.c_void_p(ptrs[0]),
+                                ctypes.c_void_p(ptrs[1]), ctypes.c_void_p(ptrs[2]), int(is_device),
+                                ctypes.c_void_p(stream))
     return st, h
 
 
@@ -187,9 +207,21 @@ def spca_destroy(h) -> None:
 
 # ------------------------------------------------------------------ convenience wrappers
 class Handle:
-    """Owns an spca_handle; A is host numpy (float32/float64) or a torch CUDA tensor."""
+    """Owns an spca_handle; A is host numpy (float32/float64), a torch CUDA tensor, or a sparse
+    matrix (scipy.sparse, or a tuple (indptr, indices, data, (n, p)) of host arrays) kept in
+    compressed sparse rows."""
 
     def __init__(self, A, stream: int = 0, storage: int = SPCA_F32):
+        if isinstance(A, tuple) or hasattr(A, "indptr") or hasattr(A, "tocsr"):
+            if isinstance(A, tuple):
+                indptr, indices, data, (n, p) = A
+            else:
+                M = A.tocsr()
+                indptr, indices, data, (n, p) = M.indptr, M.indices, M.data, M.shape
+            st, h = spca_create_csr(n, p, int(np.asarray(indptr)[-1]), indptr, indices, data, False, stream)
+            _check(st, "spca_create_csr")
+            self.h, self.n, self.p = h, int(n), int(p)
+            return
         try:
             import torch
             is_tensor = isinstance(A, torch.Tensor)
