@@ -392,18 +392,12 @@ __device__ void xstep_finish(const XstepArgs &a, int c, const float *vv, int len
 }
 
 // ---------------------------------------------------------------- full x-step
-// Every pass over all p entries of v (staged in shared memory when it fits).  Starts that the
-// candidate kernel below already finished in this sweep are skipped.
-template <bool kSmem>
-__global__ void __launch_bounds__(XT) k_xstep(XstepArgs a_in, const float *__restrict__ V, int64_t ldv,
-                                              float *__restrict__ X, int64_t ldx, StartState st,
-                                              int *__restrict__ sup_idx, float *__restrict__ sup_val,
-                                              Ctrl *ctrl) {
-  extern __shared__ float vsm[];
-  __shared__ XShared sh;
-  const int c = blockIdx.x;
-  if (st.status && st.status[c] != ST_ACTIVE) return;
-  if (st.xfast && st.xfast[c]) return;
+// the full x-step of start c (block-wide; vsm: p floats of shared memory, or null to read v from
+// global memory)
+__device__ void xstep_full_one(const XstepArgs &a_in, int c, const float *__restrict__ V, int64_t ldv,
+                               float *__restrict__ X, int64_t ldx, StartState &st, int *__restrict__ sup_idx,
+                               float *__restrict__ sup_val, Ctrl *ctrl, float *vsm, XShared &sh) {
+  const bool kSmem = vsm != nullptr;
   const XstepArgs a = xstep_switches(a_in, st.iters, c);
   const int p = a.p;
   const int lane = threadIdx.x & 31;
@@ -482,6 +476,24 @@ __global__ void __launch_bounds__(XT) k_xstep(XstepArgs a_in, const float *__res
   }
   xstep_finish(a, c, vv, p, nullptr, op, x, st, sup_idx, sup_val, ctrl, sh);
 }
+
+// Every pass over all p entries of v (staged in shared memory when it fits), persistent CTAs over
+// the starts.  Starts that the candidate kernels below already finished in this sweep are skipped.
+template <bool kSmem>
+__global__ void __launch_bounds__(XT) k_xstep(XstepArgs a_in, const float *__restrict__ V, int64_t ldv, int r,
+                                              float *__restrict__ X, int64_t ldx, StartState st,
+                                              int *__restrict__ sup_idx, float *__restrict__ sup_val,
+                                              Ctrl *ctrl) {
+  extern __shared__ float vsm[];
+  __shared__ XShared sh;
+  for (int c = blockIdx.x; c < r; c += gridDim.x) {
+    if (st.status && st.status[c] != ST_ACTIVE) continue;
+    if (st.xfast && st.xfast[c]) continue;
+    xstep_full_one(a_in, c, V, ldv, X, ldx, st, sup_idx, sup_val, ctrl, kSmem ? vsm : nullptr, sh);
+    __syncthreads();   // shared memory is reused by the next start
+  }
+}
+
 
 // ---------------------------------------------------------------- one-warp operator
 // After the candidate filter a start's surviving entries are few (at most kCand) and sit in
@@ -672,46 +684,64 @@ __device__ void xstep_finish_warp(const XstepArgs &a, int c, const float *vv, in
 // list overflows, the start is left to k_xstep (xfast[c] = 0).
 constexpr int kCandW = 64;               // candidates per warp
 constexpr int kCand = kCandW * XW;       // per start
+static_assert(kCand == kXstepCand, "candidate scratch size");
 constexpr float kGuess = 0.85f;
 
-__global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a_in, const float *__restrict__ V, int64_t ldv,
-                                                   float *__restrict__ X, int64_t ldx, StartState st,
-                                                   int *__restrict__ sup_idx, float *__restrict__ sup_val,
-                                                   Ctrl *ctrl) {
+// the candidate x-step's per-start prelude: the guess G (exact: G is the threshold itself), the
+// number of candidates the operator needs, and whether the filter applies at all
+struct CandPlan {
+  XstepArgs a;
+  float G;
+  bool exact, usable;
+  int need, s_int;
+};
+__device__ __forceinline__ CandPlan cand_plan(const XstepArgs &a_in, const StartState &st, int c, bool lists) {
+  CandPlan q;
+  q.a = xstep_switches(a_in, st.iters, c);
+  const int p = q.a.p, form = q.a.form;
+  q.s_int = (int)q.a.s;
+  q.exact = false;
+  q.G = 0.0f;
+  if (is_pen(form) && !q.a.calibrate) {
+    q.exact = true;
+    q.G = q.a.per_start_thr ? st.thr[c] : q.a.thr_fixed;
+  } else {
+    q.G = kGuess * st.tprev[c];
+  }
+  q.need = uses_T(form) ? q.s_int : (is_pen(form) && q.a.calibrate ? q.s_int + 1 : 1);
+  // x is zero outside the last x-step's support list, so only that list is cleared; after the
+  // start init (first sweep) x is dense and there is no list: the full pass writes all of x
+  q.usable = !((!q.exact && !(q.G > 0.0f)) || q.need > p || (uses_T(form) && q.s_int >= p) || st.iters[c] <= 1 ||
+               !lists || st.nnz[c] > q.a.cap);
+  return q;
+}
+
+// Filter: one coalesced pass keeps the entries above G in per-warp lists, concatenated in warp
+// order (the candidates in index order) into cand_val / cand_idx (kCand per start), with the sums
+// of |v| and v^2 and the count in meta[c]; x is cleared on the last support.  A start the filter
+// cannot serve gets xfast[c] = 0 and meta[c].w = 0.
+__global__ void __launch_bounds__(XT) k_xstep_filter(XstepArgs a_in, const float *__restrict__ V, int64_t ldv,
+                                                     float *__restrict__ X, int64_t ldx, StartState st,
+                                                     const int *__restrict__ sup_idx, float *__restrict__ cand_val,
+                                                     int *__restrict__ cand_idx, int4 *__restrict__ meta) {
   __shared__ XShared sh;
   __shared__ float wval_s[kCand];
   __shared__ int widx_s[kCand];
-  __shared__ float cval[kCand];
-  __shared__ int cidx[kCand];
   __shared__ int fail_s;
   const int c = blockIdx.x;
   if (st.status[c] != ST_ACTIVE) return;
-  const XstepArgs a = xstep_switches(a_in, st.iters, c);
-  const int p = a.p, form = a.form;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int s_int = (int)a.s;
-
-  // ---- the guess (uniform over the CTA)
-  bool exact = false;   // G is the threshold itself (penalty forms after calibration / fixed)
-  float G = 0.0f;
-  if (is_pen(form) && !a.calibrate) {
-    exact = true;
-    G = a.per_start_thr ? st.thr[c] : a.thr_fixed;
-  } else {
-    G = kGuess * st.tprev[c];
-  }
-  const int need = uses_T(form) ? s_int : (is_pen(form) && a.calibrate ? s_int + 1 : 1);
-  // x is zero outside the last x-step's support list, so only that list is cleared below; after
-  // the start init (first sweep) x is dense and there is no list: the full pass writes all of x
-  if ((!exact && !(G > 0.0f)) || need > p || (uses_T(form) && s_int >= p) || st.iters[c] <= 1 || !sup_idx ||
-      st.nnz[c] > a.cap) {
-    if (threadIdx.x == 0) st.xfast[c] = 0;
+  const CandPlan q = cand_plan(a_in, st, c, sup_idx != nullptr);
+  if (!q.usable) {
+    if (threadIdx.x == 0) {
+      st.xfast[c] = 0;
+      meta[c].w = 0;
+    }
     return;
   }
-  const uint32_t Gk = __float_as_uint(G);
-
-  // ---- one pass: candidates (key > Gk) into this warp's list, sums for lambda_s.  Four 128-entry
-  // chunks per step, their loads issued before any is used.
+  const int p = q.a.p;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t Gk = __float_as_uint(q.G);
+  // four 128-entry chunks per step, their loads issued before any is used
   const float *vg = V + (int64_t)c * ldv;
   float *x = X + (int64_t)c * ldx;
   const int seg = ((p + XW - 1) / XW + 127) / 128 * 128;
@@ -731,7 +761,7 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a_in, const float *
         e[h][0] = t.x; e[h][1] = t.y; e[h][2] = t.z; e[h][3] = t.w;
       } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) e[h][q] = (i0 + q < hi) ? vg[i0 + q] : 0.0f;
+        for (int k = 0; k < 4; ++k) e[h][k] = (i0 + k < hi) ? vg[i0 + k] : 0.0f;
       }
     }
 #pragma unroll
@@ -739,9 +769,9 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a_in, const float *
       const int i0 = base + h * 128 + 4 * lane;
       int cnt = 0;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float av = fabsf(e[h][q]);
-        cnt += (i0 + q < hi && __float_as_uint(av) > Gk) ? 1 : 0;
+      for (int k = 0; k < 4; ++k) {
+        const float av = fabsf(e[h][k]);
+        cnt += (i0 + k < hi && __float_as_uint(av) > Gk) ? 1 : 0;
         f1 += av;
         f2 = fmaf(av, av, f2);
       }
@@ -757,10 +787,10 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a_in, const float *
       } else {
         int q2 = wc + incl - cnt;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (i0 + q < hi && abs_key(e[h][q]) > Gk) {
-            wv[q2] = e[h][q];
-            wi[q2] = i0 + q;
+        for (int k = 0; k < 4; ++k) {
+          if (i0 + k < hi && abs_key(e[h][k]) > Gk) {
+            wv[q2] = e[h][k];
+            wi[q2] = i0 + k;
             ++q2;
           }
         }
@@ -774,28 +804,60 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a_in, const float *
   int d0 = 0, d1 = 0;
   block_sum2f(f1, f2, d0, d1, sh);   // (its barriers also publish fail_s)
   if (fail_s) {
-    if (threadIdx.x == 0) st.xfast[c] = 0;
+    if (threadIdx.x == 0) {
+      st.xfast[c] = 0;
+      meta[c].w = 0;
+    }
     return;
   }
-  // ---- the warp lists, concatenated in warp order, are the candidates in index order; x is
-  // cleared on the last support (the finish writes the new one, after barriers)
   const int ncand = warp_offsets(lane == 0 ? wc : 0, sh);
-  {
-    const int off = sh.woff[w];
-    for (int t = lane; t < wc; t += 32) {
-      cval[off + t] = wv[t];
-      cidx[off + t] = wi[t];
-    }
-    const int nnz_old = st.nnz[c];
-    const int *old = sup_idx + (int64_t)c * a.cap;
-    for (int t = threadIdx.x; t < nnz_old; t += XT) x[old[t]] = 0.0f;
+  const int off = sh.woff[w];
+  float *gv = cand_val + (int64_t)c * kCand;
+  int *gi = cand_idx + (int64_t)c * kCand;
+  for (int t = lane; t < wc; t += 32) {
+    gv[off + t] = wv[t];
+    gi[off + t] = wi[t];
   }
-  __syncthreads();
+  const int nnz_old = st.nnz[c];
+  const int *old = sup_idx + (int64_t)c * q.a.cap;
+  for (int t = threadIdx.x; t < nnz_old; t += XT) x[old[t]] = 0.0f;
+  if (threadIdx.x == 0) meta[c] = make_int4(ncand, __float_as_int(f1), __float_as_int(f2), 1);
+}
 
-  // ---- the operator on the candidates, with the check that G lies below its threshold: one warp
-  if (w != 0) return;
+// Operator: a warp per start on the filter's candidates (staged in the warp's shared memory),
+// with the check that G lies below the operator's threshold; then the new x, F and support.
+constexpr int kOpWarps = 4;
+__global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int r, float *__restrict__ X,
+                                                            int64_t ldx, StartState st, int *__restrict__ sup_idx,
+                                                            float *__restrict__ sup_val,
+                                                            const float *__restrict__ cand_val,
+                                                            const int *__restrict__ cand_idx,
+                                                            const int4 *__restrict__ meta, Ctrl *ctrl) {
+  __shared__ float cval_s[kOpWarps][kCand];
+  __shared__ int cidx_s[kOpWarps][kCand];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kOpWarps + w;
+  if (c >= r) return;
+  if (st.status[c] != ST_ACTIVE) return;
+  const int4 m = meta[c];
+  if (m.w == 0) return;
+  const CandPlan q = cand_plan(a_in, st, c, true);
+  const XstepArgs &a = q.a;
+  const int form = a.form, s_int = q.s_int;
+  const int ncand = m.x;
+  const float f1 = __int_as_float(m.y), f2 = __int_as_float(m.z);
+  const float G = q.G;
+  const uint32_t Gk = __float_as_uint(G);
+  float *cval = cval_s[w];
+  int *cidx = cidx_s[w];
+  for (int t = lane; t < ncand; t += 32) {
+    cval[t] = cand_val[(int64_t)c * kCand + t];
+    cidx[t] = cand_idx[(int64_t)c * kCand + t];
+  }
+  __syncwarp();
+  float *x = X + (int64_t)c * ldx;
   XOp op;
-  bool ok = ncand >= need;
+  bool ok = ncand >= q.need;
   if (ok && uses_T(form)) {
     int gt, eq;
     op.K = warp_select(cval, ncand, s_int, &gt, &eq);
@@ -856,7 +918,7 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a_in, const float *
       op.tnext = st.tprev[c];
     }
   }
-  if (!ok) {   // uniform over the warp: every input of ok is a warp- or block-wide value
+  if (!ok) {   // uniform over the warp: every input of ok is a warp-wide value
     if (lane == 0) st.xfast[c] = 0;
     return;
   }
@@ -866,17 +928,34 @@ __global__ void __launch_bounds__(XT) k_xstep_cand(XstepArgs a_in, const float *
 }  // namespace
 
 cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,
-                         StartState s, int *sup_idx, float *sup_val, Ctrl *ctrl_next,
+                         StartState s, int *sup_idx, float *sup_val, Ctrl *ctrl_next, XstepScratch scratch,
                          cudaStream_t st) {
-  // the candidate kernel needs the per-start thresholds of the last sweep and 16-byte rows
+  // the candidate kernels need the per-start thresholds of the last sweep, 16-byte rows and their
+  // scratch (candidate lists, per-start counts)
   const bool cand = s.status && s.tprev && s.xfast && s.thr && ldv % 4 == 0 && ldx % 4 == 0 &&
-                    (reinterpret_cast<uintptr_t>(V) & 15u) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
+                    (reinterpret_cast<uintptr_t>(V) & 15u) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0 &&
+                    scratch.cand_val && scratch.cand_idx && scratch.meta;
   if (cand) {
-    k_xstep_cand<<<r, XT, 0, st>>>(a, V, ldv, X, ldx, s, sup_idx, sup_val, ctrl_next);
+    k_xstep_filter<<<r, XT, 0, st>>>(a, V, ldv, X, ldx, s, sup_idx, scratch.cand_val, scratch.cand_idx,
+                                     reinterpret_cast<int4 *>(scratch.meta));
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_xstep_op<<<(r + kOpWarps - 1) / kOpWarps, 32 * kOpWarps, 0, st>>>(
+        a, r, X, ldx, s, sup_idx, sup_val, scratch.cand_val, scratch.cand_idx,
+        reinterpret_cast<const int4 *>(scratch.meta), ctrl_next);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   } else {
     s.xfast = nullptr;
+  }
+  // the full pass for the starts the candidate kernels left: persistent CTAs (as many as fit),
+  // so that a sweep in which every start took the candidate path costs one short launch
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
   }
   const size_t bytes = (size_t)a.p * sizeof(float);
   if (bytes <= (size_t)XSTEP_SMEM_MAX) {
@@ -887,9 +966,10 @@ cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float 
       if (e != cudaSuccess) return e;
       configured = true;
     }
-    k_xstep<true><<<r, XT, bytes, st>>>(a, V, ldv, X, ldx, s, sup_idx, sup_val, ctrl_next);
+    const int per_sm = bytes <= 100u * 1024u ? 2 : 1;
+    k_xstep<true><<<min(r, per_sm * sms), XT, bytes, st>>>(a, V, ldv, r, X, ldx, s, sup_idx, sup_val, ctrl_next);
   } else {
-    k_xstep<false><<<r, XT, 0, st>>>(a, V, ldv, X, ldx, s, sup_idx, sup_val, ctrl_next);
+    k_xstep<false><<<min(r, 2 * sms), XT, 0, st>>>(a, V, ldv, r, X, ldx, s, sup_idx, sup_val, ctrl_next);
   }
   return cudaGetLastError();
 }

@@ -153,7 +153,7 @@ cudaError_t launch_start_init(const float *x0, int64_t ld0, uint64_t seed, int r
 // ------------------------------------------------------------------ y-step (Table 3 S1, S2)
 // Counts the sweep for every active start; L1 variance: y = sgn(u) with sgn(0) = +1;
 // L2 variance: y = u / ||u||_2, and ||u||_2 = 0 ends the start as degenerate (x = 0).
-// y goes to Y (FP32) and/or to BF16 planes (hi, mid, lo; a single exact plane for +-1).
+// y goes to Y (FP32) and/or to the FP16 planes of kQScale y (hi, lo; one exact plane for +-1).
 __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict__ U, int64_t ldu,
                                                int n, float *__restrict__ Y,
                                                __half *__restrict__ Ypl, int64_t pstride,
@@ -166,16 +166,37 @@ __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict
   float *y = Y ? Y + (int64_t)c * ldu : nullptr;
   __half *yp = Ypl ? Ypl + (int64_t)(rank ? rank[c] : c) * ldu : nullptr;
   if (threadIdx.x == 0) s.iters[c] += 1;
+  // four consecutive entries per thread and step (rows are 16-byte aligned: ldu is a multiple of 8)
+  const int n4 = n & ~3;
   if (is_l1_var(form)) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = 4 * threadIdx.x; i < n4; i += 4 * blockDim.x) {
+      const float4 uv = *reinterpret_cast<const float4 *>(u + i);
+      const float4 yv = make_float4(uv.x >= 0.0f ? 1.0f : -1.0f, uv.y >= 0.0f ? 1.0f : -1.0f,
+                                    uv.z >= 0.0f ? 1.0f : -1.0f, uv.w >= 0.0f ? 1.0f : -1.0f);
+      if (y) *reinterpret_cast<float4 *>(y + i) = yv;
+      if (yp) {
+        // +-2^14, exact
+        __half2 *h2 = reinterpret_cast<__half2 *>(yp + i);
+        h2[0] = __floats2half2_rn(yv.x * kQScale, yv.y * kQScale);
+        h2[1] = __floats2half2_rn(yv.z * kQScale, yv.w * kQScale);
+      }
+    }
+    for (int i = n4 + threadIdx.x; i < n; i += blockDim.x) {
       const float yi = (u[i] >= 0.0f) ? 1.0f : -1.0f;
       if (y) y[i] = yi;
-      if (yp) yp[i] = __float2half_rn(yi * kQScale);   // +-2^14, exact
+      if (yp) yp[i] = __float2half_rn(yi * kQScale);
     }
     return;
   }
   float part = 0.0f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) part = fmaf(u[i], u[i], part);
+  for (int i = 4 * threadIdx.x; i < n4; i += 4 * blockDim.x) {
+    const float4 uv = *reinterpret_cast<const float4 *>(u + i);
+    part = fmaf(uv.x, uv.x, part);
+    part = fmaf(uv.y, uv.y, part);
+    part = fmaf(uv.z, uv.z, part);
+    part = fmaf(uv.w, uv.w, part);
+  }
+  for (int i = n4 + threadIdx.x; i < n; i += blockDim.x) part = fmaf(u[i], u[i], part);
   const double nrm = sqrt((double)block_sum_f(part, redf));
   if (nrm == 0.0) {
     float *x = X + (int64_t)c * ldX;
@@ -188,14 +209,38 @@ __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict
     return;
   }
   const float inv = (float)(1.0 / nrm);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    float yi = u[i] * inv;
+  // y = u / ||u||_2, and its planes: kQScale y is exact (a power of two), |kQScale y| <= 2^14
+  auto planes = [&](float yi, __half &hi, __half &lo) {
+    const float ys = yi * kQScale;
+    hi = __float2half_rn(ys);
+    lo = __float2half_rn(ys - __half2float(hi));
+  };
+  for (int i = 4 * threadIdx.x; i < n4; i += 4 * blockDim.x) {
+    const float4 uv = *reinterpret_cast<const float4 *>(u + i);
+    const float4 yv = make_float4(uv.x * inv, uv.y * inv, uv.z * inv, uv.w * inv);
+    if (y) *reinterpret_cast<float4 *>(y + i) = yv;
+    if (yp) {
+      __half h[4], l[4];
+      planes(yv.x, h[0], l[0]);
+      planes(yv.y, h[1], l[1]);
+      planes(yv.z, h[2], l[2]);
+      planes(yv.w, h[3], l[3]);
+      __half2 *ph = reinterpret_cast<__half2 *>(yp + i);
+      __half2 *pl = reinterpret_cast<__half2 *>(yp + pstride + i);
+      ph[0] = __halves2half2(h[0], h[1]);
+      ph[1] = __halves2half2(h[2], h[3]);
+      pl[0] = __halves2half2(l[0], l[1]);
+      pl[1] = __halves2half2(l[2], l[3]);
+    }
+  }
+  for (int i = n4 + threadIdx.x; i < n; i += blockDim.x) {
+    const float yi = u[i] * inv;
     if (y) y[i] = yi;
     if (yp) {
-      const float ys = yi * kQScale;                 // exact (a power of two), |ys| <= 2^14
-      const __half hi = __float2half_rn(ys);
+      __half hi, lo;
+      planes(yi, hi, lo);
       yp[i] = hi;
-      yp[i + pstride] = __float2half_rn(ys - __half2float(hi));
+      yp[i + pstride] = lo;
     }
   }
 }

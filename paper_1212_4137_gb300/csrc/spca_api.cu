@@ -41,6 +41,7 @@ struct spca_handle {
   float *Bt = nullptr, *sp_part = nullptr;
   int ldb = 0;
   float *ysum = nullptr;                   // chunk sums of the y-step for long u (r x ceil(n / kYChunk))
+  XstepScratch xs{};                       // the candidate x-step's lists and counts
   bool tc_ok = false;                      // the device has tcgen05 tensor cores (sm_100+)
   int sms = 1;                             // streaming multiprocessors of the device
   void *Apl = nullptr, *ATpl = nullptr;    // tensor-core planes (kPlanes FP16 each, row-scaled)
@@ -206,10 +207,12 @@ void free_workspace(spca_handle *h) {
   void *ptrs[] = {h->X, h->V, h->U, h->Y, h->Xpl, h->Ypl, h->sup_idx, h->sup_val, h->act, h->rank,
                   h->status, h->iters, h->nnz, h->F, h->F_prev, h->gamma, h->f, h->ev, h->thr, h->tprev, h->xfast,
                   h->partials, h->ctrl, h->best, h->y_out, h->x_out, h->support_out, h->nnz_out,
-                  h->mark, h->colpos, h->collist, h->AS, h->XS, h->x_scale, h->x_inv, h->Bt, h->sp_part, h->ysum};
+                  h->mark, h->colpos, h->collist, h->AS, h->XS, h->x_scale, h->x_inv, h->Bt, h->sp_part, h->ysum,
+                  h->xs.cand_val, h->xs.cand_idx, h->xs.meta};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   h->Bt = h->sp_part = h->ysum = nullptr;
+  h->xs = XstepScratch{};
   h->ldb = 0;
   h->mark = h->colpos = h->collist = nullptr;
   h->AS = h->XS = nullptr;
@@ -251,6 +254,9 @@ int ensure_workspace(spca_handle *h, int r) {
   CK(dalloc(&h->tprev, r)); CK(dalloc(&h->xfast, r));
   CK(dalloc(&h->partials, (size_t)r * nchunks * 2));
   CK(dalloc(&h->ysum, (size_t)r * ((n + kYChunk - 1) / kYChunk)));
+  CK(dalloc(&h->xs.cand_val, (size_t)r * kXstepCand));
+  CK(dalloc(&h->xs.cand_idx, (size_t)r * kXstepCand));
+  CK(dalloc(&h->xs.meta, (size_t)r * 4));
   CK(dalloc(&h->ctrl, 2)); CK(dalloc(&h->best, 1));
   CK(dalloc(&h->y_out, (size_t)h->ldU)); CK(dalloc(&h->x_out, (size_t)h->ldX));
   CK(dalloc(&h->support_out, (size_t)p)); CK(dalloc(&h->nnz_out, 1));
@@ -824,8 +830,9 @@ int spca_xstep(spca_handle *h, int form, double s, double gamma, int calibrate, 
   StartState st{};
   st.nnz = nnz; st.F = F; st.gamma = thr;
   RC(enter(h));
-  CK(timed(h, SPCA_K_XSTEP, 1,
-           [&] { return launch_xstep(a, V, ldv, r, X, ldx, st, nullptr, nullptr, nullptr, h->stream); }));
+  CK(timed(h, SPCA_K_XSTEP, 1, [&] {
+    return launch_xstep(a, V, ldv, r, X, ldx, st, nullptr, nullptr, nullptr, XstepScratch{}, h->stream);
+  }));
   CK(cudaStreamSynchronize(h->stream));
   return SPCA_OK;
 }
@@ -1002,8 +1009,8 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     CK(cudaMemsetAsync(nxt, 0, sizeof(Ctrl), st));
     XstepArgs xk = xa;
     xk.sparse_cap = pl.sparse_cap;
-    CK(timed(h, SPCA_K_XSTEP, 2, [&] {   // candidate x-step, full x-step
-      return launch_xstep(xk, h->V, h->ldX, r, h->X, h->ldX, S, h->sup_idx, h->sup_val, nxt, st);
+    CK(timed(h, SPCA_K_XSTEP, 3, [&] {   // candidate filter and operator, full x-step
+      return launch_xstep(xk, h->V, h->ldX, r, h->X, h->ldX, S, h->sup_idx, h->sup_val, nxt, h->xs, st);
     }));
     if (otf) {
       // stopped slots: archive their start, give them the next starts (Section 4.3)

@@ -318,9 +318,17 @@ cudaError_t launch_union_operands(const float *AT, int64_t ldat, const float *a_
 cudaError_t launch_active_list(const int *status, const int *nnz, int r, int *act, int *rank, Ctrl *c,
                                cudaStream_t st);
 
-// x-step (S3..S6), objective F, stopping rule, support lists
+// x-step (S3..S6), objective F, stopping rule, support lists.  The candidate path needs scratch of
+// kXstepCand candidates (value, index) and one int4 per start; without it every start takes the
+// full pass.
+constexpr int kXstepCand = 1024;
+struct XstepScratch {
+  float *cand_val = nullptr;   // r * kXstepCand
+  int *cand_idx = nullptr;     // r * kXstepCand
+  int *meta = nullptr;         // r * 4 (16-byte aligned)
+};
 cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,
-                         StartState s, int *sup_idx, float *sup_val, Ctrl *ctrl_next,
+                         StartState s, int *sup_idx, float *sup_val, Ctrl *ctrl_next, XstepScratch scratch,
                          cudaStream_t st);
 
 // a7: Table 1 objective in FP64 for every start; u of each start into U

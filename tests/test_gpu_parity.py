@@ -239,8 +239,10 @@ def test_spiked_stopping_rule(lib, oracle, spiked, form, engine):
     ref = _oracle_solve(oracle, A64, form, G.astype(np.float64), kw, 200, 1e-6)
     bo = ref.f[ref.best]
     assert abs(out["objective"] - bo) <= OBJ_RTOL * max(1.0, abs(bo))
-    # most starts stop within a sweep or two of the oracle
-    close = np.abs(out["start_iters"] - ref.iters) <= 2
+    # most starts stop within a few sweeps of the oracle: near convergence the relative change of F
+    # shrinks by a factor rho per sweep, and FP32's ~1e-7 relative noise on F moves the sweep at
+    # which it crosses tol = 1e-6 by about log(1 +- 0.1) / log(rho) sweeps (3 for rho = 0.97)
+    close = np.abs(out["start_iters"] - ref.iters) <= 3
     assert close.mean() >= 0.9
     h.close()
 
