@@ -775,17 +775,16 @@ __global__ void __launch_bounds__(XT) k_xstep_filter(XstepArgs a_in, const float
         f1 += av;
         f2 = fmaf(av, av, f2);
       }
-      int incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      const int tot = __shfl_sync(0xffffffffu, incl, 31);
+      // the warp's exclusive prefix of cnt (0..4) from the ballots of its three bits
+      const unsigned lt = (1u << lane) - 1u;
+      const unsigned b0 = __ballot_sync(0xffffffffu, cnt & 1), b1 = __ballot_sync(0xffffffffu, cnt & 2),
+                     b2 = __ballot_sync(0xffffffffu, cnt & 4);
+      const int excl = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+      const int tot = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
       if (over || wc + tot > kCandW) {
         over = true;
       } else {
-        int q2 = wc + incl - cnt;
+        int q2 = wc + excl;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (i0 + k < hi && abs_key(e[h][k]) > Gk) {
@@ -884,8 +883,7 @@ __global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int 
       }
       sw = warp_sum_f(sw);
       sw2 = warp_sum_f(sw2);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+      mk = warp_max_u(mk);
       ok = (float)a.s * sw2 - sw * sw < 0.0f;   // phi(G) < 0: lambda_s > G
       if (ok) {
         uint32_t lok;
