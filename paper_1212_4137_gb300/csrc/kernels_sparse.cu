@@ -18,6 +18,9 @@
 //                   starts each and walk the item's entries in order (each entry's index and value
 //                   broadcast from the lane that loaded it), reading one 256-byte row segment of Bt
 //                   per entry;
+//   k_pack_t_h, k_spmm_h, k_spmm_wide_h
+//                   the same for y = +-1 (L1 variance), which FP16 holds exactly: 16 starts per
+//                   32-byte sector (slabs of 128 starts), products and sums in FP32;
 //   k_spmm_fix      a long row's segments' sums added in segment order;
 //   k_spmv_support  u = A x over the support of a sparse x: the support's columns (A^T's rows)
 //                   scattered into a shared-memory chunk of u, one column at a time in support
@@ -27,6 +30,8 @@
 //   k_fin_csr       the same by rows for the other starts, 8 starts per pass over a row.
 // Every sum runs in a fixed order: a start's result does not depend on the schedule or on the
 // other starts.
+#include <cuda_fp16.h>
+
 #include <cstdint>
 
 #include "block_util.cuh"
@@ -50,6 +55,34 @@ __device__ __forceinline__ void ldg8(const float *p, float (&v)[8]) {
   asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
                : "l"(p));
+}
+
+// the same load as raw 32-bit words (16 FP16 values)
+__device__ __forceinline__ void ldg8u(const void *p, uint32_t (&v)[8]) {
+  asm("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+      : "l"(p));
+}
+__device__ __forceinline__ float2 half2_bits(uint32_t u) {
+  __half2 h;
+  memcpy(&h, &u, sizeof h);
+  return __half22float2(h);
+}
+
+// Sum over the warp of a[q] for q = (lane >> 1) & 15, in 16 shuffles (the levels 16, 8, 4 and 2
+// halve the values a lane keeps, as in reduce8 below)
+__device__ __forceinline__ float reduce16(const float (&a)[16], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  float t8[8], t4[4], t2[2];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) t8[q] = (b4 ? a[q + 8] : a[q]) + __shfl_xor_sync(FULL, b4 ? a[q] : a[q + 8], 16);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) t4[q] = (b3 ? t8[q + 4] : t8[q]) + __shfl_xor_sync(FULL, b3 ? t8[q] : t8[q + 4], 8);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) t2[q] = (b2 ? t4[q + 2] : t4[q]) + __shfl_xor_sync(FULL, b2 ? t4[q] : t4[q + 2], 4);
+  float w = (b1 ? t2[1] : t2[0]) + __shfl_xor_sync(FULL, b1 ? t2[0] : t2[1], 2);
+  w += __shfl_xor_sync(FULL, w, 1);
+  return w;
 }
 
 // Sum over the warp of a[q] for q = (lane >> 2) & 7, in 9 shuffles: at each of the levels 16, 8
@@ -295,6 +328,205 @@ cudaError_t launch_spmm(SpMat M, const SpPlan &P, const float *Bt, int ldb, cons
   }
   if (P.nlong > 0) {
     k_spmm_fix<<<P.nlong, 256, 0, st>>>(P.longs, part, ldb, count, gate, list, out, ldo);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- y = +-1 in FP16
+// Bt16[j * ldb + k] = fp16(src[list[k]][j]) (exact for +-1), zero up to the next multiple of 16
+__global__ void k_pack_t_h(const float *__restrict__ src, int64_t ld, int len, const int *__restrict__ list,
+                           const int *__restrict__ count, __half *__restrict__ Bt, int ldb) {
+  const int cnt = *count;
+  const int k0 = blockIdx.y * 32;
+  const int kpad = (cnt + 15) / 16 * 16;
+  if (k0 >= kpad) return;
+  __shared__ float tile[32][33];
+  const int j0 = blockIdx.x * 32;
+  for (int q = threadIdx.y; q < 32; q += 8) {
+    const int k = k0 + q, j = j0 + threadIdx.x;
+    float v = 0.0f;
+    if (k < cnt && j < len) v = src[(int64_t)(list ? list[k] : k) * ld + j];
+    tile[q][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += 8) {
+    const int j = j0 + q, k = k0 + threadIdx.x;
+    if (j < len && k < kpad) Bt[(int64_t)j * ldb + k] = __float2half_rn(tile[threadIdx.x][q]);
+  }
+}
+
+// up to 32 starts: NG groups of 16 per pass over the entries, one 256-bit load per group
+template <int NG>
+__global__ void __launch_bounds__(SPT) k_spmm_h(SpMat M, const SpItem *__restrict__ items, int nitems,
+                                                const __half *__restrict__ Bt, int ldb,
+                                                const int *__restrict__ count, const int *__restrict__ list,
+                                                float *__restrict__ out, int64_t ldo, float *__restrict__ part,
+                                                int ldp) {
+  const int cnt = *count;
+  if (cnt <= 0) return;
+  const int ng = min(NG, (cnt + 15) / 16);
+  const int lane = threadIdx.x & 31, q = lane >> 1;
+  const int nw = gridDim.x * (SPT / 32);
+  for (int it = blockIdx.x * (SPT / 32) + (threadIdx.x >> 5); it < nitems; it += nw) {
+    const int4 head = __ldg(reinterpret_cast<const int4 *>(items + it));
+    const int seg = head.z;
+    for (int row = head.x; row < head.y; ++row) {
+      const int64_t b = seg >= 0 ? items[it].nz0 : M.ptr[row];
+      const int64_t e = seg >= 0 ? items[it].nz1 : M.ptr[row + 1];
+      float acc[NG][16];
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int t = 0; t < 16; ++t) acc[g][t] = 0.0f;
+      auto fma16 = [&](float (&ac)[16], float a, const uint32_t (&w)[8]) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const float2 y2 = half2_bits(w[t]);
+          ac[2 * t] = fmaf(a, y2.x, ac[2 * t]);
+          ac[2 * t + 1] = fmaf(a, y2.y, ac[2 * t + 1]);
+        }
+      };
+      int64_t k = b + lane;
+      // two entries per lane in flight; each lane's sums still run in entry order
+      for (; k + 32 < e; k += 64) {
+        const int j0 = __ldg(M.col + k), j1 = __ldg(M.col + k + 32);
+        const float a0 = __ldg(M.val + k), a1 = __ldg(M.val + k + 32);
+        const __half *p0 = Bt + (int64_t)j0 * ldb, *p1 = Bt + (int64_t)j1 * ldb;
+        uint32_t w0[NG][8], w1[NG][8];
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+          if (g < ng) {
+            ldg8u(p0 + 16 * g, w0[g]);
+            ldg8u(p1 + 16 * g, w1[g]);
+          }
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+          if (g < ng) {
+            fma16(acc[g], a0, w0[g]);
+            fma16(acc[g], a1, w1[g]);
+          }
+      }
+      if (k < e) {
+        const int j0 = __ldg(M.col + k);
+        const float a0 = __ldg(M.val + k);
+        const __half *p0 = Bt + (int64_t)j0 * ldb;
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+          if (g < ng) {
+            uint32_t w0[8];
+            ldg8u(p0 + 16 * g, w0);
+            fma16(acc[g], a0, w0);
+          }
+      }
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        if (g >= ng) break;
+        const float v = reduce16(acc[g], lane);
+        const int kk = g * 16 + q;
+        if ((lane & 1) == 0 && kk < cnt) {
+          if (seg >= 0) part[(int64_t)seg * ldp + kk] = v;
+          else out[(int64_t)(list ? list[kk] : kk) * ldo + row] = v;
+        }
+      }
+    }
+  }
+}
+
+// more than 32 starts: slabs of 128 starts, each lane 4 (one 8-byte load per entry)
+constexpr int kWideSlabH = 128;
+__global__ void __launch_bounds__(SPT, 3) k_spmm_wide_h(SpMat M, const SpItem *__restrict__ items, int nitems,
+                                                        const __half *__restrict__ Bt, int ldb,
+                                                        const int *__restrict__ count, const int *__restrict__ list,
+                                                        float *__restrict__ out, int64_t ldo,
+                                                        float *__restrict__ part, int ldp) {
+  const int cnt = *count;
+  if (cnt <= 0) return;
+  const int lane = threadIdx.x & 31;
+  const int nslab = (cnt + kWideSlabH - 1) / kWideSlabH;
+  const int64_t units = (int64_t)nslab * nitems;
+  const int64_t nw = (int64_t)gridDim.x * (SPT / 32);
+  for (int64_t w = (int64_t)blockIdx.x * (SPT / 32) + (threadIdx.x >> 5); w < units; w += nw) {
+    const int slab = (int)(w / nitems), it = (int)(w - (int64_t)slab * nitems);
+    const int k = slab * kWideSlabH + 4 * lane;   // this lane's starts k .. k + 3
+    const bool on = k < cnt;                      // k + 3 < ldb whenever k < cnt (ldb a multiple of 16)
+    const __half *B = Bt + k;
+    const int4 head = __ldg(reinterpret_cast<const int4 *>(items + it));
+    const int seg = head.z;
+    for (int row = head.x; row < head.y; ++row) {
+      const int64_t b = seg >= 0 ? items[it].nz0 : M.ptr[row];
+      const int64_t e = seg >= 0 ? items[it].nz1 : M.ptr[row + 1];
+      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      for (int64_t base = b; base < e; base += 32) {
+        const int m = (int)min((int64_t)32, e - base);
+        const int jl = lane < m ? __ldg(M.col + base + lane) : 0;
+        const float al = lane < m ? __ldg(M.val + base + lane) : 0.0f;
+        int qq = 0;
+        for (; qq + 8 <= m; qq += 8) {
+          uint2 y[8];
+          float a[8];
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            const int j = __shfl_sync(FULL, jl, qq + g);
+            a[g] = __shfl_sync(FULL, al, qq + g);
+            y[g] = on ? __ldg(reinterpret_cast<const uint2 *>(B + (int64_t)j * ldb)) : make_uint2(0u, 0u);
+          }
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            const float2 lo = half2_bits(y[g].x), hi = half2_bits(y[g].y);
+            acc[0] = fmaf(a[g], lo.x, acc[0]);
+            acc[1] = fmaf(a[g], lo.y, acc[1]);
+            acc[2] = fmaf(a[g], hi.x, acc[2]);
+            acc[3] = fmaf(a[g], hi.y, acc[3]);
+          }
+        }
+        for (; qq < m; ++qq) {
+          const int j = __shfl_sync(FULL, jl, qq);
+          const float a = __shfl_sync(FULL, al, qq);
+          const uint2 y = on ? __ldg(reinterpret_cast<const uint2 *>(B + (int64_t)j * ldb)) : make_uint2(0u, 0u);
+          const float2 lo = half2_bits(y.x), hi = half2_bits(y.y);
+          acc[0] = fmaf(a, lo.x, acc[0]);
+          acc[1] = fmaf(a, lo.y, acc[1]);
+          acc[2] = fmaf(a, hi.x, acc[2]);
+          acc[3] = fmaf(a, hi.y, acc[3]);
+        }
+      }
+      if (on) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (k + t >= cnt) break;
+          if (seg >= 0) part[(int64_t)seg * ldp + k + t] = acc[t];
+          else out[(int64_t)(list ? list[k + t] : k + t) * ldo + row] = acc[t];
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_spmm_h(SpMat M, const SpPlan &P, const float *Y, int64_t ldy, int len, const int *list,
+                          const int *count, int rmax, void *Bt, int ldb16, float *out, int64_t ldo, float *part,
+                          int ldp, int sms, cudaStream_t st) {
+  __half *B = static_cast<__half *>(Bt);
+  const dim3 pgrid((unsigned)((len + 31) / 32), (unsigned)((rmax + 31) / 32));
+  k_pack_t_h<<<pgrid, dim3(32, 8), 0, st>>>(Y, ldy, len, list, count, B, ldb16);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (P.nitems > 0) {
+    const bool wide = rmax > 32;
+    const int64_t units = (int64_t)P.nitems * (wide ? (rmax + kWideSlabH - 1) / kWideSlabH : 1);
+    const int64_t want = (units + SPT / 32 - 1) / (SPT / 32);
+    const int blocks = (int)(want < sms * 8 ? want : sms * 8);
+    if (wide)
+      k_spmm_wide_h<<<blocks, SPT, 0, st>>>(M, P.items, P.nitems, B, ldb16, count, list, out, ldo, part, ldp);
+    else if (rmax <= 16)
+      k_spmm_h<1><<<blocks, SPT, 0, st>>>(M, P.items, P.nitems, B, ldb16, count, list, out, ldo, part, ldp);
+    else
+      k_spmm_h<2><<<blocks, SPT, 0, st>>>(M, P.items, P.nitems, B, ldb16, count, list, out, ldo, part, ldp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (P.nlong > 0) {
+    k_spmm_fix<<<P.nlong, 256, 0, st>>>(P.longs, part, ldp, count, nullptr, list, out, ldo);
     return cudaGetLastError();
   }
   return cudaSuccess;

@@ -475,17 +475,27 @@ int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const i
   const bool tc = engine == SPCA_ENGINE_TC;
   const int64_t ypstride = (int64_t)h->r_cap * h->ldU;
   if (h->sparse) {
-    // y-step, y of the active starts packed transposed, the SpMM over A's columns
-    CK(timed(h, SPCA_K_YSTEP, 2, [&] {
+    // y-step, y of the active starts packed transposed, the SpMM over A's columns; y = +-1 (L1
+    // variance) is packed in FP16, exactly, 16 starts to a 32-byte sector
+    const bool half = is_l1_var(form);
+    CK(timed(h, SPCA_K_YSTEP, half ? 1 : 2, [&] {
       cudaError_t e = launch_ystep(form, h->U, h->ldU, n, r, h->Y, nullptr, 0, nullptr, S, h->X, h->ldX, p, h->ysum,
                                    st);
-      if (e != cudaSuccess) return e;
+      if (e != cudaSuccess || half) return e;
       return launch_pack_t(h->Y, h->ldU, n, h->act, nact, nullptr, r, h->Bt, h->ldb, st);
     }));
-    CK(timed(h, SPCA_K_V, 1 + (h->plan_at.nlong > 0), [&] {
-      return launch_spmm(sp_cols(h), h->plan_at, h->Bt, h->ldb, nact, nullptr, h->act, r, h->V, h->ldX,
-                         h->sp_part, h->sms, st);
-    }));
+    if (half) {
+      const int ldb16 = (h->r_cap + 15) / 16 * 16;   // fits in Bt: ldb16 halves <= 2 ldb halves
+      CK(timed(h, SPCA_K_V, 2 + (h->plan_at.nlong > 0), [&] {
+        return launch_spmm_h(sp_cols(h), h->plan_at, h->Y, h->ldU, n, h->act, nact, r, h->Bt, ldb16, h->V, h->ldX,
+                             h->sp_part, h->ldb, h->sms, st);
+      }));
+    } else {
+      CK(timed(h, SPCA_K_V, 1 + (h->plan_at.nlong > 0), [&] {
+        return launch_spmm(sp_cols(h), h->plan_at, h->Bt, h->ldb, nact, nullptr, h->act, r, h->V, h->ldX,
+                           h->sp_part, h->sms, st);
+      }));
+    }
     (void)nhost;
     return SPCA_OK;
   }

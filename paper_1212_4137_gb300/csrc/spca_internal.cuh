@@ -192,6 +192,12 @@ cudaError_t launch_pack_t(const float *src, int64_t ld, int len, const int *list
 // <= rmax (part: P.nseg x ldb floats of scratch); gated
 cudaError_t launch_spmm(SpMat M, const SpPlan &P, const float *Bt, int ldb, const int *count, const int *gate,
                         const int *list, int rmax, float *out, int64_t ldo, float *part, int sms, cudaStream_t st);
+// v = A^T y for y = +-1 (L1 variance): the listed rows of Y (FP32, +-1) packed as FP16 into Bt
+// (A.cols x ldb16 halves, ldb16 a multiple of 16; exact), then the SpMM as above (part: row
+// stride ldp floats)
+cudaError_t launch_spmm_h(SpMat M, const SpPlan &P, const float *Y, int64_t ldy, int len, const int *list,
+                          const int *count, int rmax, void *Bt, int ldb16, float *out, int64_t ldo, float *part,
+                          int ldp, int sms, cudaStream_t st);
 // u = A x over the support lists of the starts the gather serves (active, swept at least once),
 // from A by columns (AT: CSR of A^T); gated
 cudaError_t launch_spmv_support(SpMat AT, int n, const int *sup_idx, const float *sup_val, int cap, StartState s,
