@@ -132,8 +132,8 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
  *                may be freed on return.
  *   cuda_stream  as in spca_create.
  * On such a handle spca_solve and spca_products take SPCA_ENGINE_AUTO or SPCA_ENGINE_SIMT
- * (SPCA_ENGINE_TC and lowp_sweeps > 0 are SPCA_E_UNSUPPORTED), and spca_deflate is
- * SPCA_E_UNSUPPORTED (projection deflation fills A in).
+ * (SPCA_ENGINE_TC and lowp_sweeps > 0 are SPCA_E_UNSUPPORTED); spca_deflate keeps A sparse and
+ * holds the deflations as a low-rank update (see spca_deflate).
  * Errors: SPCA_E_INVALID (NULL pointers, sizes out of range, row_ptr malformed, a column out of
  *         range, a value or a sum of repeated values not finite), SPCA_E_NOMEM, SPCA_E_CUDA.
  */
@@ -287,9 +287,12 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
  * spca_deflate -- projection deflation of the handle's matrix for a further component:
  * A <- A (I - z z^T) with z = x / ||x||_2 (the paper computes several components, Section 1,
  * without fixing a deflation scheme).  The next spca_solve on the handle then works on the
- * deflated matrix, so z is not found again.  w = A z is accumulated as compensated FP32 pairs,
- * each entry updated in FP64 and rounded once to FP32; the transposed copy and the tensor-core
- * operands are rebuilt.  Synchronous on the handle's stream.
+ * deflated matrix, so z is not found again.  Dense A: w = A z is accumulated as compensated FP32
+ * pairs, each entry updated in FP64 and rounded once to FP32; the transposed copy and the
+ * tensor-core operands are rebuilt.  Sparse A (spca_create_csr): A stays as given and the
+ * deflations are kept as A_k = A - W Z^T (z_i in FP32, w_i = A_{i-1} z_i in compensated FP32
+ * pairs, rounded once); every sweep subtracts W (Z^T x) from u and Z (W^T y) from v, and the
+ * finalise subtracts W (Z^T x) in pair arithmetic.  Synchronous on the handle's stream.
  *   x            p floats (typically spca_result.x of the last solve), host memory
  *                (x_is_device = 0) or device memory (x_is_device = 1); need not be normalised.
  * Errors: SPCA_E_INVALID (NULL pointers, x not finite or zero: A is then unchanged),

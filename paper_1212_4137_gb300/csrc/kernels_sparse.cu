@@ -27,7 +27,11 @@
 //                   order, the FMA chain of each u_i in that order;
 //   k_fin_support   the finalise's u = A x in compensated FP32 pairs over a small support (the
 //                   column scatter into 256-row chunks), |u| and u^2 summed in pair arithmetic;
-//   k_fin_csr       the same by rows for the other starts, 8 starts per pass over a row.
+//   k_fin_csr       the same by rows for the other starts, 8 starts per pass over a row;
+//   k_lowrank_*     projection deflation of a sparse A kept as a low-rank update: after k
+//                   components, A_k = A (I - z_1 z_1^T) ... (I - z_k z_k^T) = A - W Z^T with z_i
+//                   unit and w_i = A_{i-1} z_i, so u = A x - W (Z^T x) and v = A^T y - Z (W^T y)
+//                   (the finalise subtracts W (Z^T x) in pair arithmetic before its sums).
 // Every sum runs in a fixed order: a start's result does not depend on the schedule or on the
 // other starts.
 #include <cuda_fp16.h>
@@ -591,9 +595,22 @@ cudaError_t launch_spmv_support(SpMat AT, int n, const int *sup_idx, const float
 // warp's sums of |u_i| and u_i^2 over its rows (GB300 issues FP64 at a small fraction of the FP32
 // rate, so no FP64 runs per row).  Per CTA and start the warps' sums are added in warp order, in
 // FP64, into partials[(c * nchunks + b) * 2 + {0, 1}].
+// u_i -= sum_q coef[q] W[q, i] in pair arithmetic (coef in FP64, split into two floats)
+__device__ __forceinline__ void lowrank_sub(F32Pair &u, const double *__restrict__ coef, const float *__restrict__ W,
+                                            int64_t ldw, int k, int i) {
+  for (int q = 0; q < k; ++q) {
+    const float w = W[(int64_t)q * ldw + i];
+    const float ch = (float)coef[q];
+    const float cl = (float)(coef[q] - (double)ch);
+    f32pair_fma(u, -ch, w);
+    f32pair_fma(u, -cl, w);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_fin_csr(SpMat A, const float *__restrict__ Bt, int ldb, int count,
                                                  const int *__restrict__ nnz, int cap, float *__restrict__ U,
-                                                 int64_t ldu, double *__restrict__ partials) {
+                                                 int64_t ldu, double *__restrict__ partials, const double *__restrict__ coef,
+                                                 const float *__restrict__ W, int64_t ldw, int kdef) {
   __shared__ double red[8][8][2];
   const int b = blockIdx.x, c0 = blockIdx.y * 8;
   const int nc = min(8, count - c0);
@@ -626,7 +643,8 @@ __global__ void __launch_bounds__(256) k_fin_csr(SpMat A, const float *__restric
         other.lo = __shfl_xor_sync(FULL, t.lo, o);
         t = f32pair_add(t, other);
       }
-      // every lane now holds u_i
+      // every lane now holds u_i (of A x; then of A_k x after deflation)
+      if (kdef > 0 && g < nc) lowrank_sub(t, coef + (int64_t)(c0 + g) * kdef, W, ldw, kdef, i);
       if (lane == 0 && g < nc && !(nnz && nnz[c0 + g] <= cap)) U[(int64_t)(c0 + g) * ldu + i] = __fadd_rn(t.hi, t.lo);
       l1[g] = f32pair_add(l1[g], f32pair_abs(t));
       l2[g] = f32pair_add(l2[g], f32pair_sq(t));
@@ -661,7 +679,9 @@ __global__ void __launch_bounds__(256) k_fin_csr(SpMat A, const float *__restric
 __global__ void __launch_bounds__(256) k_fin_support(SpMat AT, const int *__restrict__ sup_idx,
                                                      const float *__restrict__ sup_val, int ldsup,
                                                      const int *__restrict__ nnz, int cap, float *__restrict__ U,
-                                                     int64_t ldu, double *__restrict__ partials) {
+                                                     int64_t ldu, double *__restrict__ partials,
+                                                     const double *__restrict__ coef, const float *__restrict__ W,
+                                                     int64_t ldw, int kdef) {
   __shared__ float us_hi[256], us_lo[256];
   __shared__ int64_t lo_s[256], hi_s[256];
   __shared__ float xv[256];
@@ -702,6 +722,7 @@ __global__ void __launch_bounds__(256) k_fin_support(SpMat AT, const int *__rest
   F32Pair u;
   u.hi = us_hi[threadIdx.x];
   u.lo = us_lo[threadIdx.x];
+  if (kdef > 0 && (int)threadIdx.x < rows) lowrank_sub(u, coef + (int64_t)c * kdef, W, ldw, kdef, base + threadIdx.x);
   if ((int)threadIdx.x < rows) U[(int64_t)c * ldu + base + threadIdx.x] = __fadd_rn(u.hi, u.lo);
   F32Pair a1 = f32pair_abs(u), a2 = f32pair_sq(u);
 #pragma unroll
@@ -736,12 +757,12 @@ __global__ void __launch_bounds__(256) k_fin_support(SpMat AT, const int *__rest
 // scatter; the others by rows, in groups of at most ldb (the packed operand's width)
 cudaError_t launch_fin_csr(SpMat A, SpMat AT, const float *X, int64_t ldx, int count, const int *nnz,
                            const int *sup_idx, const float *sup_val, int ldsup, float *Bt, int ldb, float *U,
-                           int64_t ldu, double *partials, cudaStream_t st) {
+                           int64_t ldu, double *partials, LowRank L, cudaStream_t st) {
   const int nchunks = (A.rows + 255) / 256;
   const int cap = sup_idx ? kSpSupportCap : -1;
   if (sup_idx) {
     k_fin_support<<<dim3((unsigned)nchunks, (unsigned)count), 256, 0, st>>>(AT, sup_idx, sup_val, ldsup, nnz, cap, U,
-                                                                              ldu, partials);
+                                                                              ldu, partials, L.coef, L.W, L.ldw, L.k);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -751,11 +772,88 @@ cudaError_t launch_fin_csr(SpMat A, SpMat AT, const float *X, int64_t ldx, int c
     if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)nchunks, (unsigned)((m + 7) / 8));
     k_fin_csr<<<grid, 256, 0, st>>>(A, Bt, ldb, m, sup_idx ? nnz + c0 : nullptr, cap, U + (int64_t)c0 * ldu, ldu,
-                                    partials + (int64_t)c0 * nchunks * 2);
+                                    partials + (int64_t)c0 * nchunks * 2, L.k > 0 ? L.coef + (int64_t)c0 * L.k : nullptr,
+                                    L.W, L.ldw, L.k);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- low-rank deflation
+// grid (count): coef[list[b] * k + q] = z_q^T x_c for the start c = list[b] (or b), in FP64 from
+// compensated FP32-pair sums per thread
+__global__ void __launch_bounds__(256) k_lowrank_coef(const float *__restrict__ X, int64_t ldx, int p,
+                                                      const int *__restrict__ list, const int *__restrict__ count,
+                                                      int count_host, const float *__restrict__ Z, int64_t ldz, int k,
+                                                      double *__restrict__ coef) {
+  __shared__ double red[32];
+  const int cnt = count ? *count : count_host;
+  if ((int)blockIdx.x >= cnt) return;
+  const int c = list ? list[blockIdx.x] : (int)blockIdx.x;
+  const float *x = X + (int64_t)c * ldx;
+  for (int q = 0; q < k; ++q) {
+    const float *z = Z + (int64_t)q * ldz;
+    F32Pair s;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) f32pair_fma(s, z[j], x[j]);
+    const double t = block_sum_d(f32pair_value(s), red);
+    if (threadIdx.x == 0) coef[(int64_t)c * k + q] = t;
+    __syncthreads();
+  }
+}
+
+// grid (ceil(len / 1024), count): out[c][i] -= sum_q coef[c * k + q] B[q][i] (u -= W (Z^T x) with
+// B = W, v -= Z (W^T y) with B = Z), FP32
+__global__ void __launch_bounds__(256) k_lowrank_axpy(float *__restrict__ out, int64_t ldo, int len,
+                                                      const int *__restrict__ list, const int *__restrict__ count,
+                                                      int count_host, const float *__restrict__ B, int64_t ldb_, int k,
+                                                      const double *__restrict__ coef) {
+  const int cnt = count ? *count : count_host;
+  if ((int)blockIdx.y >= cnt) return;
+  const int c = list ? list[blockIdx.y] : (int)blockIdx.y;
+  float *o = out + (int64_t)c * ldo;
+  for (int i = blockIdx.x * 1024 + threadIdx.x; i < min(len, (int)(blockIdx.x + 1) * 1024); i += blockDim.x) {
+    float v = o[i];
+    for (int q = 0; q < k; ++q) v = fmaf(-(float)coef[(int64_t)c * k + q], B[(int64_t)q * ldb_ + i], v);
+    o[i] = v;
+  }
+}
+
+cudaError_t launch_lowrank_coef(const float *src, int64_t lds, int src_len, const int *list, const int *count,
+                                int rmax, const float *Cdot, int64_t ldc, int k, double *coef, cudaStream_t st) {
+  if (k <= 0) return cudaSuccess;
+  k_lowrank_coef<<<rmax, 256, 0, st>>>(src, lds, src_len, list, count, rmax, Cdot, ldc, k, coef);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lowrank(const float *src, int64_t lds, int src_len, float *out, int64_t ldo, int out_len,
+                           const int *list, const int *count, int rmax, const float *Cdot, int64_t ldc,
+                           const float *B, int64_t ldb_, int k, double *coef, cudaStream_t st) {
+  if (k <= 0) return cudaSuccess;
+  cudaError_t e = launch_lowrank_coef(src, lds, src_len, list, count, rmax, Cdot, ldc, k, coef, st);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)((out_len + 1023) / 1024), (unsigned)rmax);
+  k_lowrank_axpy<<<grid, 256, 0, st>>>(out, ldo, out_len, list, count, rmax, B, ldb_, k, coef);
+  return cudaGetLastError();
+}
+
+// one CTA: z = x / ||x||_2 (||x|| in FP64); *bad = 1 when x = 0 (z left as is)
+__global__ void __launch_bounds__(1024) k_unit(const float *__restrict__ x, int p, float *__restrict__ z, int *bad) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) s += (double)x[j] * (double)x[j];
+  const double nrm = sqrt(block_sum_d(s, red));
+  if (!(nrm > 0.0)) {
+    if (threadIdx.x == 0) *bad = 1;
+    return;
+  }
+  const double inv = 1.0 / nrm;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) z[j] = (float)((double)x[j] * inv);
+}
+
+cudaError_t launch_unit(const float *x, int p, float *z, int *bad, cudaStream_t st) {
+  k_unit<<<1, 1024, 0, st>>>(x, p, z, bad);
+  return cudaGetLastError();
 }
 
 }  // namespace spca

@@ -41,6 +41,13 @@ struct spca_handle {
   float *Bt = nullptr, *sp_part = nullptr;
   int ldb = 0;
   float *ysum = nullptr;                   // chunk sums of the y-step for long u (r x ceil(n / kYChunk))
+  // projection deflation of a sparse A as the low-rank update A - W Z^T: k directions z (rows of
+  // Zd, p floats, ldX apart) and w = A_{i-1} z (rows of Wd, n floats, ldU apart), room for
+  // defl_cap; per-start coefficients Z^T x or W^T y (lr_rows x defl_cap doubles)
+  int defl_k = 0, defl_cap = 0;
+  float *Wd = nullptr, *Zd = nullptr;
+  double *lr_coef = nullptr;
+  int lr_rows = 0;
   XstepScratch xs{};                       // the candidate x-step's lists and counts
   bool tc_ok = false;                      // the device has tcgen05 tensor cores (sm_100+)
   int sms = 1;                             // streaming multiprocessors of the device
@@ -407,6 +414,41 @@ TcPairs pairs_hi() {
 
 SpMat sp_rows(const spca_handle *h) { return SpMat{h->a_ptr, h->a_col, h->a_val, (int)h->n, (int)h->p}; }
 SpMat sp_cols(const spca_handle *h) { return SpMat{h->at_ptr, h->at_col, h->at_val, (int)h->p, (int)h->n}; }
+LowRank low_rank(const spca_handle *h) {
+  LowRank L;
+  L.W = h->Wd;
+  L.Z = h->Zd;
+  L.ldw = pad_ld(h->n);
+  L.ldz = pad_ld(h->p);
+  L.k = h->defl_k;
+  L.coef = h->lr_coef;
+  return L;
+}
+
+// room for the low-rank coefficients of `rows` starts (graphs hold the old pointer: a new
+// workspace generation)
+int ensure_lr_coef(spca_handle *h, int rows) {
+  if (h->defl_cap == 0 || rows <= h->lr_rows) return SPCA_OK;
+  release_graphs(h);
+  ++h->ws_gen;
+  if (h->lr_coef) cudaFree(h->lr_coef);
+  h->lr_coef = nullptr;
+  h->lr_rows = 0;
+  CK(dalloc(&h->lr_coef, (size_t)rows * h->defl_cap));
+  h->lr_rows = rows;
+  return SPCA_OK;
+}
+
+// deflated sparse A: u -= W (Z^T x) for the listed rows of X (the sweep's u = A x is done)
+int sweep_lowrank_u(spca_handle *h, int r, const int *count, const int *list) {
+  if (!h->sparse || h->defl_k == 0) return SPCA_OK;
+  const LowRank L = low_rank(h);
+  CK(timed(h, SPCA_K_U_DENSE, 2, [&] {
+    return launch_lowrank(h->X, h->ldX, (int)h->p, h->U, h->ldU, (int)h->n, list, count, r, L.Z, L.ldz, L.W, L.ldw,
+                          L.k, L.coef, h->stream);
+  }));
+  return SPCA_OK;
+}
 
 // sparse A: u = A x by rows for the listed rows of X (count *count, list null = the first
 // *count rows): x packed transposed, then the SpMM over A's rows (gated)
@@ -496,6 +538,13 @@ int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const i
                            h->sp_part, h->sms, st);
       }));
     }
+    if (h->defl_k > 0) {   // deflated: v -= Z (W^T y)
+      const LowRank L = low_rank(h);
+      CK(timed(h, SPCA_K_V, 2, [&] {
+        return launch_lowrank(h->Y, h->ldU, n, h->V, h->ldX, p, h->act, nact, r, L.W, L.ldw, L.Z, L.ldz, L.k, L.coef,
+                              st);
+      }));
+    }
     (void)nhost;
     return SPCA_OK;
   }
@@ -532,6 +581,70 @@ int read_dev_err(spca_handle *h) {
     cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream);
     return fail(h, code, "a device-side wait timed out%s");
   }
+  return SPCA_OK;
+}
+
+// Projection deflation of a sparse A: A_k = A_{k-1} (I - z z^T) = A_{k-1} - w z^T with
+// w = A_{k-1} z, kept as one more row of W and Z (A itself stays as given)
+int deflate_sparse(spca_handle *h, const float *x, int x_is_device) {
+  RC(enter(h));
+  const int64_t n = h->n, p = h->p, ldw = pad_ld(n), ldz = pad_ld(p);
+  cudaStream_t st = h->stream;
+  RC(ensure_workspace(h, h->r_cap > 0 ? h->r_cap : 1));   // packed operand and partial sums
+  if (h->defl_k == h->defl_cap) {   // grow the rows of W and Z (and the coefficients)
+    const int cap = h->defl_cap ? 2 * h->defl_cap : 4;
+    float *W = nullptr, *Z = nullptr;
+    CK(dalloc(&W, (size_t)cap * ldw));
+    cudaError_t e = dalloc(&Z, (size_t)cap * ldz);
+    if (e != cudaSuccess) {
+      cudaFree(W);
+      CK(e);
+    }
+    if (h->defl_k > 0) {
+      CK(cudaMemcpyAsync(W, h->Wd, (size_t)h->defl_k * ldw * sizeof(float), cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(Z, h->Zd, (size_t)h->defl_k * ldz * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    cudaFree(h->Wd);
+    cudaFree(h->Zd);
+    h->Wd = W;
+    h->Zd = Z;
+    CK(cudaMemsetAsync(h->Wd + (size_t)h->defl_k * ldw, 0, (size_t)(cap - h->defl_k) * ldw * sizeof(float), st));
+    CK(cudaMemsetAsync(h->Zd + (size_t)h->defl_k * ldz, 0, (size_t)(cap - h->defl_k) * ldz * sizeof(float), st));
+    h->defl_cap = cap;
+    const int rows = h->lr_rows > 0 ? h->lr_rows : 1;
+    h->lr_rows = 0;
+    RC(ensure_lr_coef(h, rows));
+    release_graphs(h);
+    ++h->ws_gen;
+  }
+  if (!h->defl_x) {
+    CK(dalloc(&h->defl_x, (size_t)p));
+    CK(dalloc(&h->defl_w, (size_t)n + 1));
+  }
+  CK(cudaMemcpyAsync(h->defl_x, x, (size_t)p * sizeof(float),
+                     x_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
+  CK(timed(h, SPCA_K_PREP, 1, [&] { return launch_check_finite(h->defl_x, 1, p, p, h->flag, st); }));
+  CK(cudaMemcpyAsync(h->h_flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (*h->h_flag) return fail(h, SPCA_E_INVALID, "x has a non-finite entry%s");
+  const int k = h->defl_k;
+  float *z = h->Zd + (size_t)k * ldz, *w = h->Wd + (size_t)k * ldw;
+  CK(timed(h, SPCA_K_PREP, 1, [&] { return launch_unit(h->defl_x, (int)p, z, h->flag, st); }));
+  CK(cudaMemcpyAsync(h->h_flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (*h->h_flag) return fail(h, SPCA_E_INVALID, "x is zero%s");
+  // w = A_{k-1} z = A z - W (Z^T z), by rows in compensated FP32 pairs (the finalise's product)
+  const LowRank L = low_rank(h);
+  CK(timed(h, SPCA_K_PREP, 3, [&] {
+    cudaError_t e = launch_lowrank_coef(z, ldz, (int)p, nullptr, nullptr, 1, L.Z, L.ldz, L.k, L.coef, st);
+    if (e != cudaSuccess) return e;
+    return launch_fin_csr(sp_rows(h), sp_cols(h), z, ldz, 1, nullptr, nullptr, nullptr, 0, h->Bt, h->ldb, w, ldw,
+                          h->partials, L, st);
+  }));
+  CK(cudaStreamSynchronize(st));
+  h->defl_k = k + 1;
   return SPCA_OK;
 }
 
@@ -578,7 +691,7 @@ const char *spca_last_error(const spca_handle *h) { return h ? h->last_error : "
 
 int spca_deflate(spca_handle *h, const float *x, int x_is_device) {
   if (!h || !x) return fail(h, SPCA_E_INVALID, "NULL argument%s");
-  if (h->sparse) return fail(h, SPCA_E_UNSUPPORTED, "projection deflation of a sparse A%s");
+  if (h->sparse) return deflate_sparse(h, x, x_is_device);
   RC(enter(h));
   const int64_t n = h->n, p = h->p;
   cudaStream_t st = h->stream;
@@ -643,7 +756,7 @@ void spca_destroy(spca_handle *h) {
   free_otf(h);
   void *ptrs[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->a_scale, h->a_inv, h->at_scale, h->at_inv,
                   h->flag, h->dev_err, h->sk.ws, h->sk.flags, h->defl_x, h->defl_w,
-                  h->a_ptr, h->a_col, h->a_val, h->at_ptr, h->at_col, h->at_val,
+                  h->a_ptr, h->a_col, h->a_val, h->at_ptr, h->at_col, h->at_val, h->Wd, h->Zd, h->lr_coef,
                   h->plan_a.items, h->plan_a.longs, h->plan_at.items, h->plan_at.longs};
   for (void *q : ptrs)
     if (q) cudaFree(q);
@@ -856,6 +969,7 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
   RC(resolve_engine(h, engine, &eng));
   RC(enter(h));
   RC(ensure_workspace(h, r));
+  RC(ensure_lr_coef(h, r));
   const int n = (int)h->n, p = (int)h->p;
   cudaStream_t st = h->stream;
   CK(cudaMemcpy2DAsync(h->X, h->ldX * sizeof(float), X, ldx * sizeof(float), (size_t)p * sizeof(float), r,
@@ -865,6 +979,7 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
   CK(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), st));
   CK(launch_active_list(h->status, nullptr, r, h->act, h->rank, &h->ctrl[0], st));
   RC(sweep_u_dense(h, eng, r, nullptr, &h->ctrl[0].active, r, false));
+  RC(sweep_lowrank_u(h, r, &h->ctrl[0].active, h->act));
   RC(sweep_y_v(h, eng, form, r, state_of(h), &h->ctrl[0].active, r));
   CK(cudaMemcpy2DAsync(U, ldu * sizeof(float), h->U, h->ldU * sizeof(float), (size_t)n * sizeof(float), r,
                        cudaMemcpyDeviceToDevice, st));
@@ -903,6 +1018,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   const int r = P.r, n = (int)h->n, p = (int)h->p;
   RC(ensure_workspace(h, r));
   if (otf) RC(ensure_otf(h, l, r));
+  RC(ensure_lr_coef(h, l));
   cudaStream_t st = h->stream;
   StartState S = state_of(h);
 
@@ -1014,6 +1130,8 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
       return launch_gemm1_sparse(h->AT32, h->ldAT, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
                                  &cur->use_gather, st);
     }));
+    // deflated sparse A: u -= W (Z^T x)
+    RC(sweep_lowrank_u(h, r, &cur->active, h->act));
     // y-step, v = A^T y
     RC(sweep_y_v(h, engine, form, r, S, &cur->active, r, pl.lowp));
     CK(cudaMemsetAsync(nxt, 0, sizeof(Ctrl), st));
@@ -1057,6 +1175,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     return b;
   };
   const std::vector<int> solve_key = {form, engine, r, l, (int)(x0src != nullptr), max_iter, C, L, (int)target,
+                                      h->defl_k,
                                       (int)(bits(P.s) & 0xffffffff), (int)(bits(P.s) >> 32),
                                       (int)(bits(P.gamma) & 0xffffffff), (int)(bits(P.gamma) >> 32),
                                       (int)(bits(P.tol) & 0xffffffff), (int)(bits(P.tol) >> 32),
@@ -1161,10 +1280,14 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     const int cnt = otf ? l : r;
     double *part = otf ? h->otf_partials : h->partials;
     CK(timed(h, SPCA_K_FINALISE, 4, [&] {
-      // the support lists are kept for a plain solve's starts (on-the-fly replacement archives x only)
-      cudaError_t e = launch_fin_csr(sp_rows(h), sp_cols(h), view.x, h->ldX, cnt, otf ? nullptr : S.nnz,
-                                     otf ? nullptr : h->sup_idx, otf ? nullptr : h->sup_val, p, h->Bt, h->ldb, view.U,
-                                     h->ldU, part, st);
+      // the support lists are kept for a plain solve's starts (on-the-fly replacement archives x only);
+      // after deflation u is A_k x = A x - W (Z^T x)
+      const LowRank L = low_rank(h);
+      cudaError_t e = launch_lowrank_coef(view.x, h->ldX, p, nullptr, nullptr, cnt, L.Z, L.ldz, L.k, L.coef, st);
+      if (e == cudaSuccess)
+        e = launch_fin_csr(sp_rows(h), sp_cols(h), view.x, h->ldX, cnt, otf ? nullptr : S.nnz,
+                           otf ? nullptr : h->sup_idx, otf ? nullptr : h->sup_val, p, h->Bt, h->ldb, view.U, h->ldU,
+                           part, L, st);
       if (e == cudaSuccess) e = launch_objective_reduce(form, part, (n + 255) / 256, p, view, cnt, h->ldX, st);
       StartState Sa{};
       Sa.f = view.f;

@@ -202,14 +202,35 @@ cudaError_t launch_spmm_h(SpMat M, const SpPlan &P, const float *Y, int64_t ldy,
 // from A by columns (AT: CSR of A^T); gated
 cudaError_t launch_spmv_support(SpMat AT, int n, const int *sup_idx, const float *sup_val, int cap, StartState s,
                                 int r, float *U, int64_t ldu, const int *gate, cudaStream_t st);
+// Projection deflation of a sparse A as a low-rank update A_k = A - W Z^T (k rows of W: n
+// floats, ldw apart; of Z: p floats, ldz apart), with per-start coefficients coef (k doubles per
+// start row) as scratch
+struct LowRank {
+  const float *W = nullptr, *Z = nullptr;
+  int64_t ldw = 0, ldz = 0;
+  int k = 0;
+  double *coef = nullptr;
+};
+// out rows (list[b] or b, b < *count, or rmax when count is null) -= B^T (Cdot src): the
+// coefficients Cdot_q^T src_c (FP64) into coef, then out_c -= sum_q coef_q B_q.  u -= W (Z^T x):
+// src = X, Cdot = Z, B = W; v -= Z (W^T y): src = Y, Cdot = W, B = Z
+cudaError_t launch_lowrank(const float *src, int64_t lds, int src_len, float *out, int64_t ldo, int out_len,
+                           const int *list, const int *count, int rmax, const float *Cdot, int64_t ldc,
+                           const float *B, int64_t ldb_, int k, double *coef, cudaStream_t st);
+// the coefficients alone (coef rows list[b] or b)
+cudaError_t launch_lowrank_coef(const float *src, int64_t lds, int src_len, const int *list, const int *count,
+                                int rmax, const float *Cdot, int64_t ldc, int k, double *coef, cudaStream_t st);
+// z = x / ||x||_2 (p floats); *bad = 1 when x = 0
+cudaError_t launch_unit(const float *x, int p, float *z, int *bad, cudaStream_t st);
 // u = A x of `count` rows of X in compensated FP32 pairs, into U; FP64 partial sums of |u_i| and
 // u_i^2 per 256-row chunk to partials (count * ceil(n / 256) * 2 doubles).  With support lists
 // (sup_idx / sup_val, row c at c * ldsup, nnz[c] entries), a start with at most kSpSupportCap
 // nonzeros is summed over its support from A by columns (AT); the others by rows of A, their x
 // packed into Bt (A.cols x ldb, ldb a multiple of 8) ldb starts at a time
+// After deflation (L.k > 0) u is A_k x = A x - W (Z^T x), with L.coef holding Z^T x per start.
 cudaError_t launch_fin_csr(SpMat A, SpMat AT, const float *X, int64_t ldx, int count, const int *nnz,
                            const int *sup_idx, const float *sup_val, int ldsup, float *Bt, int ldb, float *U,
-                           int64_t ldu, double *partials, cudaStream_t st);
+                           int64_t ldu, double *partials, LowRank L, cudaStream_t st);
 
 // C[m, j] = sum_k P[m, k] Q[j, k]  (both operands K-contiguous); with gate != nullptr the
 // launch does nothing unless *gate != 0 (the dense u = A x is needed this sweep)

@@ -11,8 +11,10 @@ starts a lane sums a whole item (at most 2048 terms).
 
 Solve level: every formulation against the FP64 oracle on the same starts (the oracle's own
 products over the same stored entries); the sparse handle against a dense handle of the same
-matrix; on-the-fly replacement; edge cases (empty rows and columns, no entries at all, repeated
-and unsorted input, device input) and the requests a sparse handle refuses."""
+matrix; on-the-fly replacement; projection deflation (kept as a low-rank update of the sparse A)
+against the FP64 deflated matrix, by products and by a sequence of components; edge cases (empty
+rows and columns, no entries at all, repeated and unsorted input, device input) and the requests a
+sparse handle refuses."""
 import numpy as np
 import pytest
 
@@ -238,9 +240,6 @@ def test_sparse_edge_cases(lib, oracle):
     with pytest.raises(lib.SpcaError) as e:
         hdev.solve(1, 4, s=3.0, lowp_sweeps=2)
     assert e.value.status == lib.SPCA_E_UNSUPPORTED
-    with pytest.raises(lib.SpcaError) as e:
-        hdev.deflate(np.ones(p, np.float32))
-    assert e.value.status == lib.SPCA_E_UNSUPPORTED
     hdev.close()
 
 
@@ -262,3 +261,56 @@ def test_sparse_invalid_input(lib):
         assert st == lib.SPCA_E_INVALID and not h
     st, h = lib.spca_create_csr(0, p, 0, np.zeros(1, np.int64), good[1], good[2], False)
     assert st == lib.SPCA_E_INVALID
+
+
+@pytest.mark.parametrize("r", [24, 48])
+@pytest.mark.parametrize("form", [1, 2])
+def test_sparse_deflated_products_match_fp64(lib, oracle, form, r):
+    """A_2 = A (I - z1 z1^T)(I - z2 z2^T) = A - W Z^T, w_i = A_{i-1} z_i: the GPU keeps A sparse and
+    subtracts W (Z^T x) and Z (W^T y).  Its errors are relative to the sizes of both parts."""
+    n, p = 700, 1900
+    ip, ix, v, A64 = _bow(n, p, 30000, 80 + r)
+    rng = np.random.default_rng(81)
+    xs = [rng.standard_normal(p).astype(np.float32) * 3.0 for _ in range(2)]
+    D = A64.toarray()
+    zs, ws = [], []
+    for x in xs:
+        z = x.astype(np.float64) / np.linalg.norm(x.astype(np.float64))
+        ws.append(D @ z)
+        zs.append(z)
+        D = oracle.deflate(D, x.astype(np.float64))
+    h = lib.Handle((ip, ix, v, (n, p)))
+    for x in xs:
+        h.deflate(x)
+    X = rng.standard_normal((r, p)).astype(np.float32)
+    X[1] = xs[1]                                                   # A_2 z2 = 0
+    U, V = _products(lib, h, form, X)
+    h.close()
+    X64 = X.astype(np.float64)
+    absA = abs(A64)
+    scale_u = (absA @ np.abs(X64).T).T + sum(np.outer(np.abs(X64 @ z), np.abs(w)) for z, w in zip(zs, ws))
+    assert np.max(np.abs(U - X64 @ D.T) / (scale_u + 1e-300)) <= 2e-5
+    Y = np.where(U >= 0, 1.0, -1.0) if form == 2 else U / np.linalg.norm(U, axis=1, keepdims=True)
+    scale_v = (absA.T @ np.abs(Y).T).T + sum(np.outer(np.abs(Y @ w), np.abs(z)) for z, w in zip(zs, ws))
+    live = np.linalg.norm(U, axis=1) > 0
+    assert np.max((np.abs(V - Y @ D) / (scale_v + 1e-300))[live]) <= 2e-5
+
+
+def test_sparse_components_match_fp64_sequence(lib, oracle):
+    """Several components of a bag of words (formulation 1, s = 5, as for the text corpora): each
+    solve, then deflation by its x; the objective and support of every component match the FP64
+    sequence (oracle solve on the densified deflated matrix, oracle deflation by the oracle's x)."""
+    n, p, r = 600, 900, 24
+    ip, ix, v, A64 = _bow(n, p, 20000, 90, topics=4, topic_words=6, topic_share=0.15)
+    G = I.raw_starts(p, r, 91).astype(np.float32)
+    h = lib.Handle((ip, ix, v, (n, p)))
+    D64 = A64.toarray()
+    for comp in range(4):
+        out = h.solve(1, r, s=5.0, x0=G, max_iter=200, tol=1e-9)
+        ref = oracle.solve(D64, 1, G.astype(np.float64), s=5.0, max_iter=200, tol=1e-9)
+        xr = ref.X[ref.best]
+        assert abs(out["objective"] - ref.f[ref.best]) <= 1e-5 * ref.f[ref.best], (comp, out["objective"])
+        assert np.array_equal(out["support"], np.flatnonzero(xr)), comp
+        h.deflate(out["x"])
+        D64 = oracle.deflate(D64, xr)
+    h.close()
