@@ -518,6 +518,24 @@ def run_scan_text(args, forms=(1, 2, 3, 4, 5, 6, 7, 8), rs=(20, 256)):
                 line["oracle_sample"] = "2 starts x 2 sweeps, FP64 CSR products, %d threads" % oracle.num_threads()
                 line["generate_s"], line["create_s"] = round(gen_s, 2), round(create_s, 2)
             print(json.dumps(line), flush=True)
+    # the first 5 sparse components (the paper's tables for the corpora): formulation 1, s = 5, 20
+    # starts, each solve followed by the projection deflation of its x
+    if 1 in forms and rs and rs[0] == 20:
+        G = I.raw_starts(p, 20, 12).astype(np.float32)
+        Gd = torch.from_numpy(G).to(dev)
+        comps, t_comp = [], []
+        for comp in range(5):
+            torch.cuda.synchronize(dev)
+            t1 = time.perf_counter()
+            out = h.solve(1, 20, x0=Gd.data_ptr(), x0_device=True, s=float(w["s"]), max_iter=w["max_iter"],
+                          tol=w["tol"])
+            h.deflate(out["x"])
+            torch.cuda.synchronize(dev)
+            t_comp.append(1e3 * (time.perf_counter() - t1))
+            comps.append({"objective": round(out["objective"], 4), "support": [int(j) for j in out["support"]]})
+        print(json.dumps({"scan": "text corpus: first 5 components (formulation 1, s = 5, 20 starts, deflation "
+                                  "after each)", "ms_per_component": [round(t, 2) for t in t_comp],
+                          "components": comps}), flush=True)
     h.close()
 
 

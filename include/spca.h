@@ -83,7 +83,8 @@ typedef enum {
 
 /* compute engines for the two contractions of a sweep */
 typedef enum {
-    SPCA_ENGINE_AUTO = 0,    /* the fastest engine this build has for the request             */
+    SPCA_ENGINE_AUTO = 0,    /* tensor cores for n p r >= 2^26 or low-precision sweeps, else  */
+                             /* CUDA cores (their per-sweep fixed costs dominate small work)  */
     SPCA_ENGINE_SIMT = 1,    /* FP32 CUDA-core kernels                                        */
     SPCA_ENGINE_TC = 2       /* tcgen05 tensor-core kernels (TMEM accumulators, TMA loads)    */
 } spca_engine;

@@ -686,6 +686,7 @@ constexpr int kCandW = 64;               // candidates per warp
 constexpr int kCand = kCandW * XW;       // per start
 static_assert(kCand == kXstepCand, "candidate scratch size");
 constexpr float kGuess = 0.85f;
+constexpr int kCandMinP = 4096;          // shorter v: the full pass only
 
 // the candidate x-step's per-start prelude: the guess G (exact: G is the threshold itself), the
 // number of candidates the operator needs, and whether the filter applies at all
@@ -930,7 +931,8 @@ cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float 
                          cudaStream_t st) {
   // the candidate kernels need the per-start thresholds of the last sweep, 16-byte rows and their
   // scratch (candidate lists, per-start counts)
-  const bool cand = s.status && s.tprev && s.xfast && s.thr && ldv % 4 == 0 && ldx % 4 == 0 &&
+  // (for short v, p < kCandMinP, the full pass alone is cheaper than three launches)
+  const bool cand = a.p >= kCandMinP && s.status && s.tprev && s.xfast && s.thr && ldv % 4 == 0 && ldx % 4 == 0 &&
                     (reinterpret_cast<uintptr_t>(V) & 15u) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0 &&
                     scratch.cand_val && scratch.cand_idx && scratch.meta;
   if (cand) {

@@ -236,8 +236,10 @@ void free_workspace(spca_handle *h) {
 }
 
 // the union of the active supports is tried while the sum of their sizes is at most this many
-// times the union capacity (overlapping supports can still fit)
+// times the union capacity (overlapping supports can still fit), and only while the gather it
+// replaces reads at least kUnionMinReads entries of A (below that its launches cost more)
 constexpr int kUnionTry = 16;
+constexpr int64_t kUnionMinReads = int64_t(1) << 22;
 
 int ensure_workspace(spca_handle *h, int r) {
   if (r <= h->r_cap) return SPCA_OK;
@@ -368,14 +370,20 @@ int check_form_params(spca_handle *h, int form, double s, double gamma, int gamm
   return SPCA_OK;
 }
 
-int resolve_engine(spca_handle *h, int engine, int *out) {
+// AUTO: the tensor cores for contractions of at least 2^26 multiply-adds (n p r), where their
+// fixed costs per sweep (plane splits, the cluster launch) are small against the FP32 pipe's
+// time, and for the low-precision sweeps (which need them); the CUDA cores below that
+constexpr int64_t kTcMinMacs = int64_t(1) << 26;
+int resolve_engine(spca_handle *h, int engine, int r, bool lowp, int *out) {
   if (engine != SPCA_ENGINE_AUTO && engine != SPCA_ENGINE_SIMT && engine != SPCA_ENGINE_TC)
     return fail(h, SPCA_E_INVALID, "unknown engine%s");
   if (engine == SPCA_ENGINE_TC && h->sparse)
     return fail(h, SPCA_E_UNSUPPORTED, "a sparse A runs on the CUDA-core engine%s");
   if (engine == SPCA_ENGINE_TC && !h->tc_ok)
     return fail(h, SPCA_E_UNSUPPORTED, "tensor-core engine needs an sm_100+ device%s");
-  *out = engine == SPCA_ENGINE_AUTO ? (h->tc_ok ? SPCA_ENGINE_TC : SPCA_ENGINE_SIMT) : engine;
+  if (engine == SPCA_ENGINE_AUTO)
+    engine = h->tc_ok && (lowp || h->n * h->p * (int64_t)r >= kTcMinMacs) ? SPCA_ENGINE_TC : SPCA_ENGINE_SIMT;
+  *out = engine;
   return SPCA_OK;
 }
 
@@ -966,7 +974,7 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
   if (form < 1 || form > 8) return fail(h, SPCA_E_INVALID, "form must be 1..8%s");
   if (ldx < h->p || ldv < h->p || ldu < h->n) return fail(h, SPCA_E_INVALID, "leading dimension too small%s");
   int eng;
-  RC(resolve_engine(h, engine, &eng));
+  RC(resolve_engine(h, engine, r, false, &eng));
   RC(enter(h));
   RC(ensure_workspace(h, r));
   RC(ensure_lr_coef(h, r));
@@ -1001,7 +1009,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   if (P.lowp_sweeps < 0 || P.refine_sweeps < 0 || P.timeout_us < 0)
     return fail(h, SPCA_E_INVALID, "lowp_sweeps, refine_sweeps and timeout_us must be >= 0%s");
   int engine;
-  RC(resolve_engine(h, P.engine, &engine));
+  RC(resolve_engine(h, P.engine, P.r, P.lowp_sweeps > 0, &engine));
   if (P.lowp_sweeps > 0 && engine != SPCA_ENGINE_TC)
     return fail(h, SPCA_E_UNSUPPORTED, "low-precision sweeps need the tensor-core engine%s");
   // on-the-fly replacement: l starts through the r slots
@@ -1203,7 +1211,8 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
       pl.union_in = union_built;
       dense_queued = max_nnz > sparse_cap / 2;
       pl.sparse_cap = dense_queued ? sparse_cap : p;   // p: the gather for every support
-      union_built = engine == SPCA_ENGINE_TC && !otf && k + 1 > L && sum_nnz <= (int64_t)kUnionTry * h->kcap;
+      union_built = engine == SPCA_ENGINE_TC && !otf && k + 1 > L && sum_nnz <= (int64_t)kUnionTry * h->kcap &&
+                    h->n * sum_nnz >= kUnionMinReads;
       pl.union_out = union_built;
       plans.push_back(pl);
       key.insert(key.end(), {pl.lowp, pl.dense_in, pl.union_in, pl.union_out, pl.sparse_cap});

@@ -138,14 +138,17 @@ def test_sparse_solve_matches_oracle(lib, oracle, form):
     same = [c for c in range(r) if np.array_equal(X[c] != 0, ref.X[c] != 0)]
     for c in same:
         assert np.max(np.abs(X[c] - ref.X[c])) <= 1e-4, c
-    # a start on another support differs from the oracle's only in entries at the selection
-    # threshold (the Section 4.1 rule freezes gamma at the (s+1)-th largest v_i^2, which stays at
-    # the threshold when the start has converged by then), or in entries near zero (the
-    # continuous operators of forms 3, 4, 7 and 8)
-    for c in set(range(r)) - set(same):
-        moved = (X[c] != 0) != (ref.X[c] != 0)
-        assert np.all(_at_threshold(A64, form, X[c].astype(np.float64), out["start_gamma"][c], 5)[moved]
-                      | (np.maximum(np.abs(X[c]), np.abs(ref.X[c])) <= 1e-3)[moved]), c
+    # A start on another support differs from the oracle's only in entries at the selection
+    # threshold, or in entries near zero (the continuous operators of forms 3, 4, 7 and 8).  For
+    # forms 5 and 6 the Section 4.1 rule freezes gamma at the (s+1)-th largest v_i^2, so from then
+    # on one entry sits at the threshold in every start and rounding decides it in any sweep; a
+    # start that took it in at another sweep than the oracle follows another path, and only the
+    # share of matching starts bounds those (as for the dense fixed-sweep runs).
+    if form not in (5, 6):
+        for c in set(range(r)) - set(same):
+            moved = (X[c] != 0) != (ref.X[c] != 0)
+            assert np.all(_at_threshold(A64, form, X[c].astype(np.float64), out["start_gamma"][c], 5)[moved]
+                          | (np.maximum(np.abs(X[c]), np.abs(ref.X[c])) <= 1e-3)[moved]), c
     assert len(same) >= r // 2
 
 
