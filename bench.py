@@ -539,6 +539,57 @@ def run_scan_text(args, forms=(1, 2, 3, 4, 5, 6, 7, 8), rs=(20, 256)):
     h.close()
 
 
+# Few starts on the spiked workload (n = 5000, p = 20000, FP32; formulations 1 and 2, the settings
+# of the benchmark): the streaming GEMV path (AUTO for r <= 8) and, at r = 1, the tensor-core
+# engine beside it.  Per line: sweeps*starts/s, solve latency, and v = A^T y per sweep with its
+# DRAM rate (A^T read once: 4 n p bytes, + 4 (n + p) bytes per start).
+def run_scan_small_r(args):
+    import torch
+
+    from paper_1212_4137_gb300 import build, inputs as I, spca
+    build.build()
+    w = WORKLOADS[DEFAULT_WORKLOAD]
+    n, p = w["n"], w["p"]
+    A = make_inputs(w)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    h = spca.Handle(torch.from_numpy(A).to(dev), stream=stream.cuda_stream)
+    peaks = load_peaks()
+    for r, eng in ((1, spca.SPCA_ENGINE_AUTO), (1, spca.SPCA_ENGINE_TC), (4, spca.SPCA_ENGINE_AUTO),
+                   (8, spca.SPCA_ENGINE_AUTO)):
+        G = I.raw_starts(p, r, w["start_seed"]).astype(np.float32)
+        Gd = torch.from_numpy(G).to(dev)
+        for form in (1, 2):
+            kw = dict(max_iter=w["max_iter"], tol=w["tol"], x0=Gd.data_ptr(), x0_device=True, engine=eng,
+                      **solve_kwargs(w, form))
+            for _ in range(args.warmup):
+                h.solve(form, r, **kw)
+            lat, sweeps = [], 0
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                t1 = time.perf_counter()
+                sweeps += h.solve(form, r, **kw)["sweeps_total"]
+                lat.append(1e3 * (time.perf_counter() - t1))
+            dt = time.perf_counter() - t0
+            h.profile(True, kernels=(spca.SPCA_K_V,))
+            out = h.solve(form, r, **kw)
+            nv, msv = h.profile_query(spca.SPCA_K_V)
+            h.profile(False)
+            vbytes = nv * 4.0 * n * p + 4.0 * (n + p) * out["sweeps_total"]
+            print(json.dumps({"scan": "few starts, spiked 5000 x 20000", "form": form, "r": r,
+                              "engine": {0: "auto", 1: "simt", 2: "tc"}[eng],
+                              "sweeps_starts_per_s": round(sweeps / dt, 1),
+                              "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                                             "p99": round(float(np.percentile(lat, 99)), 3)},
+                              "v": {"launches": nv, "ms_per_launch": round(msv / max(1, nv), 4),
+                                    "dram_gbs": round(vbytes / (msv / 1e3) / 1e9, 1) if msv > 0 else None,
+                                    "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                                    "bytes": "4 n p per launch (A^T once) + 4 (n + p) per start-sweep"}}),
+                  flush=True)
+    h.close()
+
+
 def sps_csr(ip, ix, v, n, p):
     import scipy.sparse as sps
     return sps.csr_matrix((v.astype(np.float64), ix, ip), shape=(n, p))
@@ -556,7 +607,7 @@ def main():
     ap.add_argument("--forms", type=str, default=None, help="comma-separated formulations (default: all 8)")
     ap.add_argument("--no-e2e", action="store_true")
     # the paper's shape scan (one JSON line per shape) instead of the benchmark line
-    ap.add_argument("--scan", choices=("paper-shapes", "text-corpus"), default=None)
+    ap.add_argument("--scan", choices=("paper-shapes", "text-corpus", "few-starts"), default=None)
     ap.add_argument("--rs", type=str, default=None, help="text-corpus scan: comma-separated start counts")
     args = ap.parse_args()
     if args.scan == "text-corpus":
@@ -566,6 +617,9 @@ def main():
         if args.rs:
             kw["rs"] = tuple(int(t) for t in args.rs.split(","))
         run_scan_text(args, **kw)
+        return
+    if args.scan == "few-starts":
+        run_scan_small_r(args)
         return
     if args.scan:
         run_scan(args)

@@ -3,6 +3,7 @@
 // x) and v = A^T y.
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "block_util.cuh"
@@ -593,6 +594,107 @@ cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int 
   dim3 grid((unsigned)((n + 1023) / 1024), (unsigned)r);
   k_gemm1_sparse<<<grid, 256, 0, st>>>(AT, ldat, n, sup_idx, sup_val, cap, s, U, ldu, gate);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ few starts: streaming GEMV
+// out[orow(c)][m] = sum_k P[m, k] Q[qrow(c), k] for the first *count (<= R) starts: the Q rows in
+// shared memory, a warp per row of P (two rows for R >= 4, which then share each read of Q) read
+// once with 16-byte loads, each lane's R sums per row over its strided part, then the warp's
+// sums in a fixed butterfly.
+// P's rows and Q's rows are zero past K up to the next multiple of 4 (padded layouts).
+template <int R, int NR>
+__global__ void __launch_bounds__(512, 1) k_gemv(const float *__restrict__ P, int64_t ldp, int M, int K,
+                                                 const float *__restrict__ Q, int64_t ldq,
+                                                 const int *__restrict__ rows, const int *__restrict__ count,
+                                                 float *__restrict__ out, int64_t ldo, const int *__restrict__ gate) {
+  extern __shared__ __align__(16) float qs[];
+  if (gate && *gate == 0) return;
+  const int cnt = count ? min(*count, R) : R;
+  if (cnt <= 0) return;
+  const int K4 = (K + 3) / 4, Kp = 4 * K4;
+  for (int c = 0; c < R; ++c) {
+    const float *q = Q + (int64_t)(c < cnt ? (rows ? rows[c] : c) : 0) * ldq;
+    for (int k = threadIdx.x; k < Kp; k += blockDim.x) qs[c * Kp + k] = c < cnt && k < K ? q[k] : 0.0f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+  // NR rows per warp and step: every shared-memory read of Q serves all of them
+  for (int m0 = NR * (blockIdx.x * warps + (threadIdx.x >> 5)); m0 < M; m0 += NR * gridDim.x * warps) {
+    const float4 *pr[NR];
+#pragma unroll
+    for (int t = 0; t < NR; ++t) pr[t] = reinterpret_cast<const float4 *>(P + (int64_t)min(m0 + t, M - 1) * ldp);
+    float acc[NR][R];
+#pragma unroll
+    for (int t = 0; t < NR; ++t)
+#pragma unroll
+      for (int c = 0; c < R; ++c) acc[t][c] = 0.0f;
+#pragma unroll 4
+    for (int k4 = lane; k4 < K4; k4 += 32) {
+      float4 a[NR];
+#pragma unroll
+      for (int t = 0; t < NR; ++t) a[t] = __ldg(pr[t] + k4);
+#pragma unroll
+      for (int c = 0; c < R; ++c) {
+        const float4 q = reinterpret_cast<const float4 *>(qs + c * Kp)[k4];
+#pragma unroll
+        for (int t = 0; t < NR; ++t) {
+          acc[t][c] = fmaf(a[t].x, q.x, acc[t][c]);
+          acc[t][c] = fmaf(a[t].y, q.y, acc[t][c]);
+          acc[t][c] = fmaf(a[t].z, q.z, acc[t][c]);
+          acc[t][c] = fmaf(a[t].w, q.w, acc[t][c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NR; ++t)
+#pragma unroll
+      for (int c = 0; c < R; ++c) acc[t][c] = warp_sum_f(acc[t][c]);
+    if (lane < cnt) {
+      float *o = out + (int64_t)(rows ? rows[lane] : lane) * ldo;
+#pragma unroll
+      for (int t = 0; t < NR; ++t) {
+        float v = acc[t][0];
+#pragma unroll
+        for (int c = 1; c < R; ++c)
+          if (lane == c) v = acc[t][c];
+        if (m0 + t < M) o[m0 + t] = v;
+      }
+    }
+  }
+}
+
+int gemv_width(int r) { return r <= 1 ? 1 : r <= 2 ? 2 : r <= 4 ? 4 : r <= kGemvMaxR ? kGemvMaxR : 0; }
+
+bool gemv_fits(int r, int64_t K) {
+  const int w = gemv_width(r);
+  return w > 0 && (int64_t)w * ((K + 3) / 4 * 4) * 4 <= kGemvSmemMax;
+}
+
+cudaError_t launch_gemv(const float *P, int64_t ldp, int M, int K, const float *Q, int64_t ldq, const int *rows,
+                        const int *count, int r, float *out, int64_t ldo, const int *gate, int sms, cudaStream_t st) {
+  const int w = gemv_width(r);
+  const size_t smem = (size_t)w * ((K + 3) / 4 * 4) * sizeof(float);
+  if (w == 0 || smem > (size_t)kGemvSmemMax) return cudaErrorInvalidValue;
+  // CTAs resident per SM by shared memory (two at least for the streaming), a grid of that many
+  // per SM, each CTA loading the Q rows once
+  const int per_sm = smem <= 48 * 1024 ? 4 : (smem <= 100 * 1024 ? 2 : 1);
+  const int blocks = std::min((M + 15) / 16, per_sm * sms);
+  static bool configured[4] = {false, false, false, false};
+  auto go = [&](auto kern, int slot) -> cudaError_t {
+    if (!configured[slot]) {   // once per process: the largest shared memory the launcher allows
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemvSmemMax);
+      if (e != cudaSuccess) return e;
+      configured[slot] = true;
+    }
+    kern<<<blocks, 512, smem, st>>>(P, ldp, M, K, Q, ldq, rows, count, out, ldo, gate);
+    return cudaGetLastError();
+  };
+  switch (w) {
+    case 1: return go(k_gemv<1, 1>, 0);
+    case 2: return go(k_gemv<2, 1>, 1);
+    case 4: return go(k_gemv<4, 2>, 2);
+    default: return go(k_gemv<kGemvMaxR, 2>, 3);
+  }
 }
 
 }  // namespace spca

@@ -372,7 +372,8 @@ int check_form_params(spca_handle *h, int form, double s, double gamma, int gamm
 
 // AUTO: the tensor cores for contractions of at least 2^26 multiply-adds (n p r), where their
 // fixed costs per sweep (plane splits, the cluster launch) are small against the FP32 pipe's
-// time, and for the low-precision sweeps (which need them); the CUDA cores below that
+// time, and for the low-precision sweeps (which need them); the CUDA cores below that and for
+// up to kGemvMaxR starts (the streaming GEMV)
 constexpr int64_t kTcMinMacs = int64_t(1) << 26;
 int resolve_engine(spca_handle *h, int engine, int r, bool lowp, int *out) {
   if (engine != SPCA_ENGINE_AUTO && engine != SPCA_ENGINE_SIMT && engine != SPCA_ENGINE_TC)
@@ -381,8 +382,13 @@ int resolve_engine(spca_handle *h, int engine, int r, bool lowp, int *out) {
     return fail(h, SPCA_E_UNSUPPORTED, "a sparse A runs on the CUDA-core engine%s");
   if (engine == SPCA_ENGINE_TC && !h->tc_ok)
     return fail(h, SPCA_E_UNSUPPORTED, "tensor-core engine needs an sm_100+ device%s");
-  if (engine == SPCA_ENGINE_AUTO)
-    engine = h->tc_ok && (lowp || h->n * h->p * (int64_t)r >= kTcMinMacs) ? SPCA_ENGINE_TC : SPCA_ENGINE_SIMT;
+  if (engine == SPCA_ENGINE_AUTO) {
+    // few starts: the streaming GEMV on the CUDA cores reads A once per product at HBM speed,
+    // where the tensor-core tiles would pad the starts to 256 columns
+    const bool gemv = !h->sparse && gemv_fits(r, h->n);
+    engine = h->tc_ok && (lowp || (!gemv && h->n * h->p * (int64_t)r >= kTcMinMacs)) ? SPCA_ENGINE_TC
+                                                                                    : SPCA_ENGINE_SIMT;
+  }
   *out = engine;
   return SPCA_OK;
 }
@@ -493,6 +499,10 @@ int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int 
       return launch_gemm_tc(h->pmA, 2, h->tmX2, 2, n, nhost, p, nullptr, pairs_general(), h->U, h->ldU, h->a_inv,
                             h->x_inv, 1.0f, gate, nact, list, h->dev_err, h->sk, st);
     }));
+  } else if (gemv_fits(r, p)) {
+    CK(timed(h, SPCA_K_U_DENSE, 1, [&] {
+      return launch_gemv(h->A32, h->ldA, n, p, h->X, h->ldX, list, nact, r, h->U, h->ldU, gate, h->sms, st);
+    }));
   } else {
     CK(timed(h, SPCA_K_U_DENSE, 1, [&] {
       return launch_gemm_nt_f32(h->X, h->ldX, h->A32, h->ldA, h->U, h->ldU, r, n, (int)h->ldX, gate, st);
@@ -571,6 +581,10 @@ int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const i
       return launch_gemm_tc(h->pmAT, 2, l1 ? h->tmY1 : h->tmY2, l1 ? 1 : 2, p, nhost, n, nullptr,
                             l1 ? pairs_sign() : pairs_general(), h->V, h->ldX, h->at_inv, nullptr, kQInv, nullptr,
                             nact, h->act, h->dev_err, h->sk, st);
+    }));
+  } else if (gemv_fits(r, n)) {
+    CK(timed(h, SPCA_K_V, 1, [&] {
+      return launch_gemv(h->AT32, h->ldAT, p, n, h->Y, h->ldU, h->act, nact, r, h->V, h->ldX, nullptr, h->sms, st);
     }));
   } else {
     CK(timed(h, SPCA_K_V, 1, [&] {

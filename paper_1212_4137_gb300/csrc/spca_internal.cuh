@@ -232,6 +232,16 @@ cudaError_t launch_fin_csr(SpMat A, SpMat AT, const float *X, int64_t ldx, int c
                            const int *sup_idx, const float *sup_val, int ldsup, float *Bt, int ldb, float *U,
                            int64_t ldu, double *partials, LowRank L, cudaStream_t st);
 
+// Few starts (r <= kGemvMaxR): out[rows[c]][m] = sum_k P[m, k] Q[rows[c], k], c < *count (r when
+// count is null; rows null = identity), m < M, streaming P once with the Q rows in shared memory
+// (at most kGemvSmemMax bytes: gemv_fits); gated
+constexpr int kGemvMaxR = 8;
+constexpr int kGemvSmemMax = 200 * 1024;
+int gemv_width(int r);
+bool gemv_fits(int r, int64_t K);
+cudaError_t launch_gemv(const float *P, int64_t ldp, int M, int K, const float *Q, int64_t ldq, const int *rows,
+                        const int *count, int r, float *out, int64_t ldo, const int *gate, int sms, cudaStream_t st);
+
 // C[m, j] = sum_k P[m, k] Q[j, k]  (both operands K-contiguous); with gate != nullptr the
 // launch does nothing unless *gate != 0 (the dense u = A x is needed this sweep)
 cudaError_t launch_gemm_nt_f32(const float *P, int64_t ldp, const float *Q, int64_t ldq,
