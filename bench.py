@@ -590,6 +590,50 @@ def run_scan_small_r(args):
     h.close()
 
 
+# The precision configuration: the spiked model at n = 20000, p = 50000 (FP32 A, 4 GB), 4096 starts,
+# L0-constrained L2 and L1 variance (formulations 1 and 2), s = 100, at most 60 sweeps, tol 1e-9:
+# plain FP32 sweeps against 20 low-precision sweeps (A's leading FP16 plane, 11 significant bits)
+# followed by FP32 sweeps to the stopping rule.  Per formulation and mode: the solve's wall time
+# (CUDA events), sweeps*starts/s, and the best objective (FP64-class finalise) with its relative
+# difference from the plain FP32 solve's.
+def run_scan_precision(args):
+    import torch
+
+    from paper_1212_4137_gb300 import build, inputs as I, spca
+    build.build()
+    n, p, r, s = 20000, 50000, 4096, 100
+    A = I.spiked_matrix(n, p, I.spiked_thetas(n, p), 100, 20000, dtype=np.float32)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    h = spca.Handle(torch.from_numpy(A).to(dev), stream=stream.cuda_stream)
+    del A
+    for form in (1, 2):
+        best = {}
+        for mode, extra in (("fp32", {}), ("lowp20+fp32", {"lowp_sweeps": 20})):
+            kw = dict(s=float(s), seed=20001, max_iter=60, tol=1e-9, **extra)
+            for _ in range(args.warmup):
+                h.solve(form, r, **kw)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms, sweeps, out = 0.0, 0, None
+            for _ in range(max(1, args.steps)):
+                torch.cuda.synchronize(dev)
+                e0.record(stream)
+                out = h.solve(form, r, **kw)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms += e0.elapsed_time(e1)
+                sweeps += out["sweeps_total"]
+            best[mode] = out["objective"]
+            line = {"scan": "precision, spiked 20000 x 50000, 4096 starts", "form": form, "mode": mode, "s": s,
+                    "solve_ms": round(ms / max(1, args.steps), 2), "sweeps_starts_per_s": round(sweeps / (ms / 1e3), 1),
+                    "sweeps_per_start": round(out["sweeps_total"] / r, 2), "best_objective": out["objective"],
+                    "best_nnz": int(out["nnz"])}
+            if mode != "fp32":
+                line["rel_diff_vs_fp32"] = (out["objective"] - best["fp32"]) / abs(best["fp32"])
+            print(json.dumps(line), flush=True)
+    h.close()
+
+
 def sps_csr(ip, ix, v, n, p):
     import scipy.sparse as sps
     return sps.csr_matrix((v.astype(np.float64), ix, ip), shape=(n, p))
@@ -607,7 +651,7 @@ def main():
     ap.add_argument("--forms", type=str, default=None, help="comma-separated formulations (default: all 8)")
     ap.add_argument("--no-e2e", action="store_true")
     # the paper's shape scan (one JSON line per shape) instead of the benchmark line
-    ap.add_argument("--scan", choices=("paper-shapes", "text-corpus", "few-starts"), default=None)
+    ap.add_argument("--scan", choices=("paper-shapes", "text-corpus", "few-starts", "precision"), default=None)
     ap.add_argument("--rs", type=str, default=None, help="text-corpus scan: comma-separated start counts")
     args = ap.parse_args()
     if args.scan == "text-corpus":
@@ -620,6 +664,9 @@ def main():
         return
     if args.scan == "few-starts":
         run_scan_small_r(args)
+        return
+    if args.scan == "precision":
+        run_scan_precision(args)
         return
     if args.scan:
         run_scan(args)
