@@ -144,6 +144,22 @@ int spca_create_csr(spca_handle **out, int64_t n, int64_t p, int64_t nnz, const 
                     const int32_t *col_idx, const float *values, int is_device, void *cuda_stream);
 
 /*
+ * spca_clone -- a new handle on the matrix another handle holds, for solves on several streams or
+ * host threads at once (one handle per thread: a handle is not thread-safe).  The clone shares
+ * the source's device copies of A and their layouts, read-only, and has its own stream, workspace
+ * and captured graphs; the matrix is freed with the last handle that holds it.  While a matrix
+ * is shared, spca_deflate on any of its handles is SPCA_E_UNSUPPORTED.  A clone's contractions
+ * run on the cluster kernel: the pair kernel's stream-K schedule needs every CTA of a launch
+ * resident at once, which launches of other handles at the same time cannot guarantee (the
+ * source handle keeps stream-K; solve on clones alone while several run together).
+ *   out          receives the new handle.
+ *   src          a handle from spca_create, spca_create_csr or spca_clone.
+ *   cuda_stream  as in spca_create.
+ * Errors: SPCA_E_INVALID, SPCA_E_NOMEM, SPCA_E_CUDA.
+ */
+int spca_clone(spca_handle **out, spca_handle *src, void *cuda_stream);
+
+/*
  * Parameters of one solve (Algorithm 2 from r starts, Section 2.2 stopping rule).
  *   form                Table 1 formulation (1..8).
  *   s                   L0 forms 1, 2: the cardinality bound (integer 1..p).

@@ -660,16 +660,17 @@ cudaError_t launch_row_scales(const float *src, int64_t rows, int64_t cols, int6
 
 // ---------------------------------------------------------------------- host side
 namespace {
+// (function-local statics: initialised once, thread-safe, for handles used from several threads)
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 }  // namespace
@@ -706,12 +707,8 @@ cudaError_t launch_tc_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, i
   constexpr int STAGE_BYTES = NA * TC_BM * TC_BK * 2 + NB * BN * TC_BK * 2;
   constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
   auto kern = k_gemm_tc<BN, NA, NB, STAGES, TC_BK>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static const cudaError_t configured = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+  if (configured != cudaSuccess) return configured;
   // cluster of C CTAs over adjacent N tiles (C = 1, 2, 4: at most the number of N tiles)
   const int ntn = (N + BN - 1) / BN;
   int lg = 0;
@@ -759,17 +756,15 @@ cudaError_t launch_tc2_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, 
   cfg.numAttrs = 1;
   // the slots must all be resident at once (owners wait for other slots' parts): as many pairs
   // as the device holds together, measured once per configuration
-  static int max_pairs = 0;
-  if (max_pairs == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    if (e != cudaSuccess) return e;
-    cfg.gridDim = dim3(2 * 64, 1);
+  static const int max_pairs = [&] {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess) return 0;
+    cudaLaunchConfig_t c = cfg;
+    c.gridDim = dim3(2 * 64, 1);
     int n = 0;
-    e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
-    if (e != cudaSuccess) return e;
-    if (n < 1) return cudaErrorInvalidConfiguration;
-    max_pairs = n;
-  }
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &c) != cudaSuccess) return 0;
+    return n;
+  }();
+  if (max_pairs < 1) return cudaErrorInvalidConfiguration;
   const int pm = ((M + TC_BM - 1) / TC_BM + 1) / 2, ntn = (N + BN - 1) / BN;
   const int kblocks = (K + BK - 1) / BK;
   const long long units = (long long)pm * ntn * kblocks;

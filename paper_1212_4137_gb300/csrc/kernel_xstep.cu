@@ -950,22 +950,20 @@ cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float 
   }
   // the full pass for the starts the candidate kernels left: persistent CTAs (as many as fit),
   // so that a sweep in which every start took the candidate path costs one short launch
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-  }
+  // (function-local statics: initialised once, thread-safe)
+  static const int sms = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+      return 0;
+    return v;
+  }();
+  if (sms < 1) return cudaErrorInvalidDevice;
   const size_t bytes = (size_t)a.p * sizeof(float);
   if (bytes <= (size_t)XSTEP_SMEM_MAX) {
-    static bool configured = false;
-    if (!configured) {
-      cudaError_t e = cudaFuncSetAttribute(k_xstep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           XSTEP_SMEM_MAX);
-      if (e != cudaSuccess) return e;
-      configured = true;
-    }
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(k_xstep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, XSTEP_SMEM_MAX);
+    if (configured != cudaSuccess) return configured;
     const int per_sm = bytes <= 100u * 1024u ? 2 : 1;
     k_xstep<true><<<min(r, per_sm * sms), XT, bytes, st>>>(a, V, ldv, r, X, ldx, s, sup_idx, sup_val, ctrl_next);
   } else {

@@ -663,6 +663,14 @@ __global__ void __launch_bounds__(512, 1) k_gemv(const float *__restrict__ P, in
   }
 }
 
+// once per kernel and process (thread-safe): the largest shared memory the launcher allows
+template <int R, int NR>
+cudaError_t gemv_configured() {
+  static const cudaError_t e =
+      cudaFuncSetAttribute(k_gemv<R, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemvSmemMax);
+  return e;
+}
+
 int gemv_width(int r) { return r <= 1 ? 1 : r <= 2 ? 2 : r <= 4 ? 4 : r <= kGemvMaxR ? kGemvMaxR : 0; }
 
 bool gemv_fits(int r, int64_t K) {
@@ -679,21 +687,16 @@ cudaError_t launch_gemv(const float *P, int64_t ldp, int M, int K, const float *
   // per SM, each CTA loading the Q rows once
   const int per_sm = smem <= 48 * 1024 ? 4 : (smem <= 100 * 1024 ? 2 : 1);
   const int blocks = std::min((M + 15) / 16, per_sm * sms);
-  static bool configured[4] = {false, false, false, false};
-  auto go = [&](auto kern, int slot) -> cudaError_t {
-    if (!configured[slot]) {   // once per process: the largest shared memory the launcher allows
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemvSmemMax);
-      if (e != cudaSuccess) return e;
-      configured[slot] = true;
-    }
+  auto go = [&](auto kern, cudaError_t configured) -> cudaError_t {
+    if (configured != cudaSuccess) return configured;
     kern<<<blocks, 512, smem, st>>>(P, ldp, M, K, Q, ldq, rows, count, out, ldo, gate);
     return cudaGetLastError();
   };
   switch (w) {
-    case 1: return go(k_gemv<1, 1>, 0);
-    case 2: return go(k_gemv<2, 1>, 1);
-    case 4: return go(k_gemv<4, 2>, 2);
-    default: return go(k_gemv<kGemvMaxR, 2>, 3);
+    case 1: return go(k_gemv<1, 1>, gemv_configured<1, 1>());
+    case 2: return go(k_gemv<2, 1>, gemv_configured<2, 1>());
+    case 4: return go(k_gemv<4, 2>, gemv_configured<4, 2>());
+    default: return go(k_gemv<kGemvMaxR, 2>, gemv_configured<kGemvMaxR, 2>());
   }
 }
 

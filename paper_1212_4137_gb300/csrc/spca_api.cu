@@ -2,6 +2,7 @@
 // the kernels read), the solve driver that runs Algorithm 2 for r starts as a sequence of
 // kernels on one stream, and the step-level entry points (x-step, sweep products).
 #include <algorithm>
+#include <atomic>
 #include <tuple>
 #include <chrono>
 #include <cmath>
@@ -23,7 +24,14 @@ struct SegGraph {
   std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> timings;
 };
 
+// the matrix a handle holds (its copies of A, the layouts the kernels read, the deflation state),
+// shared read-only by the handles spca_clone makes; freed with the last of them
+struct SharedMatrix {
+  std::atomic<int> refs{1};
+};
+
 struct spca_handle {
+  SharedMatrix *shared = nullptr;
   int64_t n = 0, p = 0;
   int64_t ldA = 0, ldAT = 0;  // padded leading dimensions of A (n x p) and A^T (p x n)
   cudaStream_t stream = nullptr;   // the handle's own non-blocking stream (all its work)
@@ -713,6 +721,8 @@ const char *spca_last_error(const spca_handle *h) { return h ? h->last_error : "
 
 int spca_deflate(spca_handle *h, const float *x, int x_is_device) {
   if (!h || !x) return fail(h, SPCA_E_INVALID, "NULL argument%s");
+  if (h->shared && h->shared->refs.load() > 1)
+    return fail(h, SPCA_E_UNSUPPORTED, "the matrix is shared with another handle (spca_clone)%s");
   if (h->sparse) return deflate_sparse(h, x, x_is_device);
   RC(enter(h));
   const int64_t n = h->n, p = h->p;
@@ -776,12 +786,19 @@ void spca_destroy(spca_handle *h) {
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   free_workspace(h);
   free_otf(h);
-  void *ptrs[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->a_scale, h->a_inv, h->at_scale, h->at_inv,
-                  h->flag, h->dev_err, h->sk.ws, h->sk.flags, h->defl_x, h->defl_w,
-                  h->a_ptr, h->a_col, h->a_val, h->at_ptr, h->at_col, h->at_val, h->Wd, h->Zd, h->lr_coef,
-                  h->plan_a.items, h->plan_a.longs, h->plan_at.items, h->plan_at.longs};
-  for (void *q : ptrs)
+  // this handle's own buffers
+  void *own[] = {h->flag, h->dev_err, h->sk.ws, h->sk.flags, h->defl_x, h->defl_w, h->lr_coef};
+  for (void *q : own)
     if (q) cudaFree(q);
+  // the matrix, with the last handle that holds it
+  if (!h->shared || h->shared->refs.fetch_sub(1) == 1) {
+    void *mat[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->a_scale, h->a_inv, h->at_scale, h->at_inv,
+                   h->a_ptr, h->a_col, h->a_val, h->at_ptr, h->at_col, h->at_val, h->Wd, h->Zd,
+                   h->plan_a.items, h->plan_a.longs, h->plan_at.items, h->plan_at.longs};
+    for (void *q : mat)
+      if (q) cudaFree(q);
+    delete h->shared;
+  }
   if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
   if (h->h_flag) cudaFreeHost(h->h_flag);
   if (h->order_ev) cudaEventDestroy(h->order_ev);
@@ -804,6 +821,11 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
   if (cudaGetDevice(&dev) != cudaSuccess) return SPCA_E_CUDA;
   h = new (std::nothrow) spca_handle();
   if (!h) return SPCA_E_NOMEM;
+  h->shared = new (std::nothrow) SharedMatrix();
+  if (!h->shared) {
+    delete h;
+    return SPCA_E_NOMEM;
+  }
   int rc = [&]() -> int {
     h->n = n; h->p = p;
     h->user = (cudaStream_t)cuda_stream;
@@ -880,6 +902,11 @@ int spca_create_csr(spca_handle **out, int64_t n, int64_t p, int64_t nnz, const 
   if (cudaGetDevice(&dev) != cudaSuccess) return SPCA_E_CUDA;
   h = new (std::nothrow) spca_handle();
   if (!h) return SPCA_E_NOMEM;
+  h->shared = new (std::nothrow) SharedMatrix();
+  if (!h->shared) {
+    delete h;
+    return SPCA_E_NOMEM;
+  }
   int rc = [&]() -> int {
     h->n = n; h->p = p;
     h->sparse = true;
@@ -949,6 +976,53 @@ int spca_create_csr(spca_handle **out, int64_t n, int64_t p, int64_t nnz, const 
                            h->stream));
       CK(cudaStreamSynchronize(h->stream));   // the host vectors go out of scope
     }
+    return SPCA_OK;
+  }();
+  if (rc != SPCA_OK) {
+    spca_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return SPCA_OK;
+}
+
+int spca_clone(spca_handle **out, spca_handle *src, void *cuda_stream) {
+  if (!out || !src || !src->shared) return SPCA_E_INVALID;
+  spca_handle *h = new (std::nothrow) spca_handle();
+  if (!h) return SPCA_E_NOMEM;
+  // the matrix: shared, read-only
+  h->shared = src->shared;
+  h->shared->refs.fetch_add(1);
+  h->n = src->n; h->p = src->p;
+  h->ldA = src->ldA; h->ldAT = src->ldAT;
+  h->A32 = src->A32; h->AT32 = src->AT32;
+  h->sparse = src->sparse;
+  h->a_ptr = src->a_ptr; h->at_ptr = src->at_ptr;
+  h->a_col = src->a_col; h->at_col = src->at_col;
+  h->a_val = src->a_val; h->at_val = src->at_val;
+  h->plan_a = src->plan_a; h->plan_at = src->plan_at;
+  h->defl_k = src->defl_k; h->defl_cap = src->defl_cap;
+  h->Wd = src->Wd; h->Zd = src->Zd;
+  h->tc_ok = src->tc_ok; h->sms = src->sms;
+  h->Apl = src->Apl; h->ATpl = src->ATpl;
+  h->a_scale = src->a_scale; h->a_inv = src->a_inv;
+  h->at_scale = src->at_scale; h->at_inv = src->at_inv;
+  h->pmA = src->pmA; h->pmAT = src->pmAT;
+  int rc = [&]() -> int {
+    h->user = (cudaStream_t)cuda_stream;
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming));
+    RC(enter(h));
+    CK(cudaMallocHost((void **)&h->h_ctrl, 2 * sizeof(Ctrl)));
+    CK(cudaMallocHost((void **)&h->h_flag, 2 * sizeof(int)));
+    h->h_flag[0] = h->h_flag[1] = 0;
+    CK(dalloc(&h->flag, 1));
+    CK(dalloc(&h->dev_err, 1));
+    CK(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
+    // no stream-K scratch: its schedule needs every CTA of a launch resident at once, which
+    // launches of other handles running at the same time cannot guarantee; the contractions take
+    // the cluster kernel, whose CTAs never wait for other clusters
+    CK(cudaStreamSynchronize(h->stream));
     return SPCA_OK;
   }();
   if (rc != SPCA_OK) {

@@ -21,7 +21,7 @@ SPCA_ST_MAXITER, SPCA_ST_CONVERGED, SPCA_ST_DEGENERATE = 0, 1, 2
 SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC = 0, 1, 2
 
 # every symbol include/spca.h declares
-EXPORTS = ("spca_create", "spca_create_csr", "spca_solve", "spca_xstep", "spca_products", "spca_deflate", "spca_profile_enable",
+EXPORTS = ("spca_create", "spca_create_csr", "spca_clone", "spca_solve", "spca_xstep", "spca_products", "spca_deflate", "spca_profile_enable",
            "spca_profile_query", "spca_objective_noalloc",
            "spca_destroy", "spca_strerror", "spca_last_error")
 SPCA_K_ALL, SPCA_K_INIT, SPCA_K_U_DENSE, SPCA_K_U_SPARSE, SPCA_K_YSTEP, SPCA_K_V, SPCA_K_XSTEP, \
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH):
         lib.spca_create_csr.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int64,
                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int, ctypes.c_void_p]
+        lib.spca_clone.restype = ctypes.c_int
+        lib.spca_clone.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p]
         lib.spca_solve.argtypes = [ctypes.c_void_p, ctypes.POINTER(spca_params), ctypes.c_void_p,
                                    ctypes.POINTER(spca_result)]
         lib.spca_xstep.restype = ctypes.c_int
@@ -241,6 +243,14 @@ class Handle:
             st, h = spca_create(A, n, p, p, dt, False, storage, stream)
         _check(st, "spca_create")
         self.h, self.n, self.p = h, n, p
+
+    def clone(self, stream: int = 0) -> "Handle":
+        """A handle sharing this one's matrix (read-only), with its own stream and workspace."""
+        h = ctypes.c_void_p()
+        _check(load().spca_clone(ctypes.byref(h), self.h, ctypes.c_void_p(stream)), "spca_clone", self.h)
+        other = Handle.__new__(Handle)
+        other.h, other.n, other.p = h, self.n, self.p
+        return other
 
     def deflate(self, x, x_device: bool = False):
         """Projection deflation A <- A (I - z z^T), z = x / ||x|| (x: host array or device address)."""
