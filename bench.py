@@ -634,6 +634,115 @@ def run_scan_precision(args):
     h.close()
 
 
+def _log_uniform(rng, lo, hi):
+    return int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi))))))
+
+
+# Many problems (the batching configuration, scaled to 64 problems so that the host generates them
+# in seconds): spiked models with k = 3 spikes (theta = (40, 30, 20) sqrt(n / p), 20 nonzeros
+# each), n log-uniform in [200, 4000], p log-uniform in [500, 20000], FP32; per problem a uniform
+# formulation, s uniform in [5, 100] (at most p), r = 64 starts, at most 100 sweeps, tol 1e-9.
+# All problems are solved one after another on one handle each, then queued at once to the
+# request loop with 4 and with 8 workers (solves overlapping on the device).
+def run_scan_many(args, count=64, workers=(4, 8)):
+    import torch
+
+    from paper_1212_4137_gb300 import build, inputs as I, serve
+    build.build()
+    rng = np.random.default_rng(4)
+    probs = []
+    for q in range(count):
+        n, p = _log_uniform(rng, 200, 4000), _log_uniform(rng, 500, 20000)
+        A = I.spiked_matrix(n, p, I.spiked_thetas(n, p, (40.0, 30.0, 20.0)), 20, 5000 + q, dtype=np.float32)
+        form = int(rng.integers(1, 9))
+        s = float(min(int(rng.integers(5, 101)), p))
+        kw = dict(s=s, seed=6000 + q, max_iter=100, tol=1e-9)
+        if form >= 5:
+            kw.update(gamma_target=True, calib=10)
+        probs.append((f"m{q}", A, form, kw))
+    for mode, nw in [("one after another", 1)] + [(f"{w} workers", w) for w in workers]:
+        with serve.Server(workers=nw, budget_bytes=64 << 30) as s:
+            for name, A, _, _ in probs:
+                s.register(name, A)
+            for name, _, form, kw in probs[:nw]:   # warm-up: one solve per worker
+                s.submit(name, form, 64, **kw).result()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            futs = [s.submit(name, form, 64, **kw) for name, _, form, kw in probs]
+            outs = [f.result() for f in futs]
+            dt = time.perf_counter() - t0
+        sweeps = sum(o["sweeps_total"] for o in outs)
+        print(json.dumps({"scan": f"many problems ({count} spiked, k = 3, n in [200, 4000], p in [500, 20000], "
+                                  "r = 64)", "mode": mode, "wall_s": round(dt, 3),
+                          "sweeps_starts_per_s": round(sweeps / dt, 1), "solves_per_s": round(count / dt, 1),
+                          "sum_n_p": int(sum(A.size for _, A, _, _ in probs))}), flush=True)
+
+
+# Serving (scaled to 8 resident matrices, 2 GB in all, so that the host generates them in seconds):
+# spiked models (5 spikes), n log-uniform in [1000, 8000], p log-uniform in [2000, 20000], FP32.
+# Requests: a uniform matrix, formulation 1..8, s uniform in [10, 200] (at most p), r uniform in
+# {1, 16, 256}, at most 100 sweeps, tol 1e-9.  A closed-loop run (all requests queued at once)
+# gives the capacity; then Poisson arrivals at 0.8 x capacity give the latency (p50 / p99 from
+# submission to result).  8 workers.
+def run_scan_serving(args, mats=8, closed=96, open_requests=240, workers=8):
+    import torch
+
+    from paper_1212_4137_gb300 import build, inputs as I, serve
+    build.build()
+    rng = np.random.default_rng(5)
+    shapes = {}
+    with serve.Server(workers=workers, budget_bytes=96 << 30) as srv:
+        for q in range(mats):
+            n, p = _log_uniform(rng, 1000, 8000), _log_uniform(rng, 2000, 20000)
+            srv.register(f"s{q}", I.spiked_matrix(n, p, I.spiked_thetas(n, p), 50, 7000 + q, dtype=np.float32))
+            shapes[f"s{q}"] = (n, p)
+
+        def request(i):
+            name = f"s{int(rng.integers(0, mats))}"
+            form = int(rng.integers(1, 9))
+            s = float(min(int(rng.integers(10, 201)), shapes[name][1]))
+            r = int(rng.choice([1, 16, 256]))
+            kw = dict(s=s, seed=8000 + i, max_iter=100, tol=1e-9)
+            if form >= 5:
+                kw.update(gamma_target=True, calib=10)
+            return name, form, r, kw
+
+        for i in range(2 * workers):   # warm-up
+            srv.submit(*request(i)[:3], **request(i)[3]).result()
+        torch.cuda.synchronize()
+        reqs = [request(100 + i) for i in range(closed)]
+        t0 = time.perf_counter()
+        outs = [f.result() for f in [srv.submit(nm, f, r, **kw) for nm, f, r, kw in reqs]]
+        dt = time.perf_counter() - t0
+        capacity = closed / dt
+        print(json.dumps({"scan": "serving, closed loop (capacity)", "requests": closed, "workers": workers,
+                          "solves_per_s": round(capacity, 2),
+                          "sweeps_starts_per_s": round(sum(o["sweeps_total"] for o in outs) / dt, 1)}), flush=True)
+        rate = 0.8 * capacity
+        reqs = [request(1000 + i) for i in range(open_requests)]
+        gaps = rng.exponential(1.0 / rate, open_requests)
+        futs = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for (nm, f, r, kw), g in zip(reqs, gaps):
+            t_next += g
+            while time.perf_counter() < t_next:
+                time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
+            futs.append(srv.submit(nm, f, r, **kw))
+        outs = [f.result() for f in futs]
+        dt = time.perf_counter() - t0
+        lat = np.array([o["latency_ms"] for o in outs])
+        by_r = {int(r): round(float(np.percentile([o["latency_ms"] for o, q in zip(outs, reqs) if q[2] == r], 50)), 2)
+                for r in (1, 16, 256) if any(q[2] == r for q in reqs)}
+        print(json.dumps({"scan": "serving, Poisson arrivals at 0.8 x capacity", "requests": open_requests,
+                          "offered_per_s": round(rate, 2), "solves_per_s": round(open_requests / dt, 2),
+                          "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 2),
+                                         "p99": round(float(np.percentile(lat, 99)), 2)},
+                          "p50_by_r_ms": by_r,
+                          "queue_ms_p50": round(float(np.percentile([o["queue_ms"] for o in outs], 50)), 2)}),
+              flush=True)
+
+
 def sps_csr(ip, ix, v, n, p):
     import scipy.sparse as sps
     return sps.csr_matrix((v.astype(np.float64), ix, ip), shape=(n, p))
@@ -651,7 +760,8 @@ def main():
     ap.add_argument("--forms", type=str, default=None, help="comma-separated formulations (default: all 8)")
     ap.add_argument("--no-e2e", action="store_true")
     # the paper's shape scan (one JSON line per shape) instead of the benchmark line
-    ap.add_argument("--scan", choices=("paper-shapes", "text-corpus", "few-starts", "precision"), default=None)
+    ap.add_argument("--scan", choices=("paper-shapes", "text-corpus", "few-starts", "precision", "many-problems",
+                                       "serving"), default=None)
     ap.add_argument("--rs", type=str, default=None, help="text-corpus scan: comma-separated start counts")
     args = ap.parse_args()
     if args.scan == "text-corpus":
@@ -667,6 +777,12 @@ def main():
         return
     if args.scan == "precision":
         run_scan_precision(args)
+        return
+    if args.scan == "many-problems":
+        run_scan_many(args)
+        return
+    if args.scan == "serving":
+        run_scan_serving(args)
         return
     if args.scan:
         run_scan(args)
