@@ -592,8 +592,9 @@ def run_scan_small_r(args):
 
 # The precision configuration: the spiked model at n = 20000, p = 50000 (FP32 A, 4 GB), 4096 starts,
 # L0-constrained L2 and L1 variance (formulations 1 and 2), s = 100, at most 60 sweeps, tol 1e-9:
-# plain FP32 sweeps against 20 low-precision sweeps (A's leading FP16 plane, 11 significant bits)
-# followed by FP32 sweeps to the stopping rule.  Per formulation and mode: the solve's wall time
+# plain FP32 sweeps against 20 low-precision sweeps followed by FP32 sweeps to the stopping rule,
+# the low-precision sweeps on A's leading FP16 plane (11 significant bits) or on its FP8 E4M3 copy
+# (4 significant bits, the tensor cores' 8-bit kind).  Per formulation and mode: the solve's wall time
 # (CUDA events), sweeps*starts/s, and the best objective (FP64-class finalise) with its relative
 # difference from the plain FP32 solve's.
 def run_scan_precision(args):
@@ -605,20 +606,23 @@ def run_scan_precision(args):
     A = I.spiked_matrix(n, p, I.spiked_thetas(n, p), 100, 20000, dtype=np.float32)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
-    h = spca.Handle(torch.from_numpy(A).to(dev), stream=stream.cuda_stream)
-    del A
+    Ad = torch.from_numpy(A).to(dev)
+    h = spca.Handle(Ad, stream=stream.cuda_stream)
+    h8 = spca.Handle(Ad, stream=stream.cuda_stream, storage=spca.SPCA_FP8_E4M3_COLSCALED)
+    del A, Ad
     for form in (1, 2):
         best = {}
-        for mode, extra in (("fp32", {}), ("lowp20+fp32", {"lowp_sweeps": 20})):
+        for mode, hh, extra in (("fp32", h, {}), ("lowp20+fp32", h, {"lowp_sweeps": 20}),
+                                ("fp8-lowp20+fp32", h8, {"lowp_sweeps": 20})):
             kw = dict(s=float(s), seed=20001, max_iter=60, tol=1e-9, **extra)
             for _ in range(args.warmup):
-                h.solve(form, r, **kw)
+                hh.solve(form, r, **kw)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ms, sweeps, out = 0.0, 0, None
             for _ in range(max(1, args.steps)):
                 torch.cuda.synchronize(dev)
                 e0.record(stream)
-                out = h.solve(form, r, **kw)
+                out = hh.solve(form, r, **kw)
                 e1.record(stream)
                 torch.cuda.synchronize(dev)
                 ms += e0.elapsed_time(e1)
@@ -632,6 +636,7 @@ def run_scan_precision(args):
                 line["rel_diff_vs_fp32"] = (out["objective"] - best["fp32"]) / abs(best["fp32"])
             print(json.dumps(line), flush=True)
     h.close()
+    h8.close()
 
 
 def _log_uniform(rng, lo, hi):

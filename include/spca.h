@@ -88,7 +88,9 @@ typedef enum {
                              /* the CUDA cores' streaming GEMV reads A at HBM speed); else    */
                              /* CUDA cores (their per-sweep fixed costs dominate small work)  */
     SPCA_ENGINE_SIMT = 1,    /* FP32 CUDA-core kernels                                        */
-    SPCA_ENGINE_TC = 2       /* tcgen05 tensor-core kernels (TMEM accumulators, TMA loads)    */
+    SPCA_ENGINE_TC = 2,      /* tcgen05 tensor-core kernels (TMEM accumulators, TMA loads)    */
+    SPCA_ENGINE_TC_LOWP = 3  /* spca_products only: the tensor cores on the low-precision      */
+                             /* copies (as in the first lowp_sweeps sweeps of a solve)         */
 } spca_engine;
 
 /*
@@ -99,13 +101,18 @@ typedef enum {
  *                device memory (a_is_device = 1).  Copied; the caller may free it on return.
  *                The library does not centre the columns (the paper assumes centred data,
  *                Section 1).
- *   storage      SPCA_F32, or SPCA_BF16 (a 16-bit copy for the low-precision sweeps,
- *                spca_params.lowp_sweeps).  Both keep the FP32 master copy and the tensor-core
- *                operand format: two FP16 planes of a row-scaled copy (hi + lo carries 22
- *                significant bits); the low-precision sweeps read the leading plane (A rounded
- *                to 11 significant bits, finer than BF16's 8).  SPCA_BF16 needs tensor cores
- *                (sm_100+) and SPCA_FP8_E4M3_COLSCALED is not built: both return
- *                SPCA_E_UNSUPPORTED otherwise.
+ *   storage      SPCA_F32, SPCA_BF16 (a 16-bit copy for the low-precision sweeps,
+ *                spca_params.lowp_sweeps) or SPCA_FP8_E4M3_COLSCALED.  All keep the FP32 master
+ *                copy and the tensor-core operand format: two FP16 planes of a row-scaled copy
+ *                (hi + lo carries 22 significant bits); with SPCA_BF16 the low-precision sweeps
+ *                read the leading plane (A rounded to 11 significant bits, finer than BF16's 8).
+ *                SPCA_FP8_E4M3_COLSCALED adds E4M3 copies of A and of A^T with power-of-two
+ *                scales per row of A and per column of A (A rounded to 4 significant bits; the
+ *                largest entry of a row or column in [128, 256)); the low-precision sweeps then
+ *                run the tensor cores' 8-bit kind (y in E4M3 at scale 2^7, x per row scaled)
+ *                and an 8-bit support gather, accumulating in FP32 (a clone's low-precision
+ *                sweeps read the FP16 leading plane instead).  Both 16- and 8-bit storage need
+ *                tensor cores (sm_100+): SPCA_E_UNSUPPORTED otherwise.
  *   cuda_stream  the caller's cudaStream_t (NULL = the legacy default stream): every call on
  *                the handle starts after the work queued on it before the call and returns with
  *                its own work complete.  The handle runs its kernels on a stream of its own, so
@@ -292,7 +299,8 @@ int spca_xstep(spca_handle *h, int form, double s, double gamma, int calibrate,
  * L2 variance, S2 with sgn(0) = +1 for L1 variance, chosen by `form`), and v = A^T y.
  * Exposed so that the contractions of each engine can be checked on their own.
  *   form    Table 1 formulation (only its variance norm matters here).
- *   engine  spca_engine.
+ *   engine  spca_engine; SPCA_ENGINE_TC_LOWP runs both contractions as a low-precision sweep
+ *           does (the leading FP16 planes, or the E4M3 copies of an FP8 handle), to check them.
  *   X       device, r x p float iterates (ldx >= p).
  *   U       device, r x n float output u = A x (ldu >= n).
  *   V       device, r x p float output v = A^T y (ldv >= p); unspecified for a row whose

@@ -27,6 +27,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <cstdint>
 
@@ -341,6 +342,16 @@ __device__ __forceinline__ void mma_bf16_pair(uint32_t tmem_d, uint64_t adesc, u
       ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// the same for 8-bit operands (kind::f8f6f4; with A and B both E4M3 the instruction descriptor's
+// format fields are 0, as for f16: K = 32 elements, 32 bytes, per instruction)
+__device__ __forceinline__ void mma_f8_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 __device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
@@ -372,16 +383,19 @@ struct SkRange {   // slot j's share of the W units: [u0, u1)
   __device__ long long start(int j) const { return (long long)j * W / S; }
 };
 
-template <int BN, int NA, int NB, int STAGES>
+// F8: operands in FP8 E4M3 (one byte each; a K-block of 128 elements keeps the 128-byte swizzled
+// rows of the FP16 layout, so the stage layout, descriptors and the 32-byte MMA steps are the same)
+template <int BN, int NA, int NB, int STAGES, bool F8 = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc2(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int M, int N,
                int kblocks, const int *__restrict__ k_dev, TcPairs pairs, float *__restrict__ out, int64_t ldo,
                const float *__restrict__ row_inv, const float *__restrict__ col_inv, float q_inv,
                const int *__restrict__ gate, const int *__restrict__ n_dev, const int *__restrict__ col_map,
                int *err, float *__restrict__ ws, int *__restrict__ flags, int epoch) {
-  constexpr int BK = 64;
-  constexpr uint32_t A_BYTES = TC_BM * BK * 2;          // this CTA's 128 rows of one P plane
-  constexpr uint32_t B_BYTES = (BN / 2) * BK * 2;       // this CTA's half of one Q plane
+  constexpr int ES = F8 ? 1 : 2;                        // bytes per element
+  constexpr int BK = 128 / ES;                          // elements per K-block: 128-byte rows
+  constexpr uint32_t A_BYTES = TC_BM * BK * ES;         // this CTA's 128 rows of one P plane
+  constexpr uint32_t B_BYTES = (BN / 2) * BK * ES;      // this CTA's half of one Q plane
   constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
   constexpr uint32_t TMEM_COLS = 2 * BN;
 
@@ -487,9 +501,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t d = tmem + (main ? 0u : (uint32_t)BN);
           const bool first = kb == kb0 && q == (main ? pairs.first_main : pairs.first_corr);
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            mma_bf16_pair(d, sw_desc<BK>(a_base + kk * 32), sw_desc<BK>(b_base + kk * 32), idesc,
+          for (int kk = 0; kk < 4; ++kk) {   // 32 bytes of K per instruction
+            if (F8)
+              mma_f8_pair(d, sw_desc<64>(a_base + kk * 32), sw_desc<64>(b_base + kk * 32), idesc,
                           (first && kk == 0) ? 0u : 1u);
+            else
+              mma_bf16_pair(d, sw_desc<64>(a_base + kk * 32), sw_desc<64>(b_base + kk * 32), idesc,
+                            (first && kk == 0) ? 0u : 1u);
           }
         }
         mma_commit_pair(smem_u32(&empty_bar[s]));   // frees stage s in both CTAs
@@ -626,6 +644,43 @@ cudaError_t launch_split_planes(const float *src, int64_t rows, int64_t cols, in
   return cudaGetLastError();
 }
 
+// dst row r = E4M3(src row row_map[r] (identity when null) x row_scale[r] x mul (x mul alone
+// when row_scale is null)), saturating at the largest finite E4M3; r < rows (*rows_dev when given);
+// gated
+__global__ void k_split_f8(const float *__restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                           uint8_t *__restrict__ dst, int64_t ldd, const float *__restrict__ row_scale, float mul,
+                           const int *__restrict__ gate, const int *__restrict__ rows_dev,
+                           const int *__restrict__ row_map) {
+  if (gate && *gate == 0) return;
+  if (rows_dev) rows = *rows_dev;
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e - r * cols;
+    const float a = src[(row_map ? (int64_t)row_map[r] : r) * lds + c] * ((row_scale ? row_scale[r] : 1.0f) * mul);
+    dst[r * ldd + c] = __nv_cvt_float_to_fp8(a, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+cudaError_t launch_split_f8(const float *src, int64_t rows, int64_t cols, int64_t lds, uint8_t *dst, int64_t ldd,
+                            const float *row_scale, float mul, const int *gate, const int *rows_dev,
+                            const int *row_map, cudaStream_t st) {
+  k_split_f8<<<608, 256, 0, st>>>(src, rows, cols, lds, dst, ldd, row_scale, mul, gate, rows_dev, row_map);
+  return cudaGetLastError();
+}
+
+// dst[i] = src[i] x mul, i < n (the inverse scales of a copy scaled by 1 / mul); gated
+__global__ void k_scale_copy(const float *__restrict__ src, int n, float mul, float *__restrict__ dst,
+                             const int *__restrict__ gate) {
+  if (gate && *gate == 0) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i] * mul;
+}
+
+cudaError_t launch_scale_copy(const float *src, int n, float mul, float *dst, const int *gate, cudaStream_t st) {
+  k_scale_copy<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, st>>>(src, n, mul, dst, gate);
+  return cudaGetLastError();
+}
+
 // one CTA per row: scale = 2^(13 - floor(log2 max |row|)), so the scaled row's largest entry lies
 // in [2^13, 2^14) (FP16's largest finite value is 65504); 1 for a zero row
 __global__ void __launch_bounds__(256) k_row_scale(const float *__restrict__ src, int64_t cols, int64_t lds,
@@ -690,6 +745,21 @@ cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+// one FP8 (one byte per element) plane of rows x ld, box 128 x box_rows, 128-byte swizzle (ld a
+// multiple of 16 bytes)
+cudaError_t make_f8_map(CUtensorMap *map, const void *base, int64_t rows, int64_t ld, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  if (ld % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return cudaErrorInvalidValue;
+  cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)ld, (cuuint64_t)ld * (cuuint64_t)rows};
+  cuuint32_t box[3] = {128, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld, int planes) {
   for (int i = 0; i < 3; ++i) {
@@ -734,15 +804,16 @@ cudaError_t launch_tc_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, i
 }  // namespace
 
 namespace {
-template <int BN, int NA, int NB, int STAGES>
+template <int BN, int NA, int NB, int STAGES, bool F8 = false>
 cudaError_t launch_tc2_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, int K, const int *k_dev,
                             TcPairs pairs, float *out, int64_t ldo, const float *row_inv, const float *col_inv,
                             float q_inv, const int *gate, const int *n_dev, const int *col_map, int *err,
                             const TcStreamK &sk, cudaStream_t st) {
-  constexpr int BK = 64;
-  constexpr int STAGE_BYTES = NA * TC_BM * BK * 2 + NB * (BN / 2) * BK * 2;
+  constexpr int ES = F8 ? 1 : 2;
+  constexpr int BK = 128 / ES;
+  constexpr int STAGE_BYTES = NA * TC_BM * BK * ES + NB * (BN / 2) * BK * ES;
   constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
-  auto kern = k_gemm_tc2<BN, NA, NB, STAGES>;
+  auto kern = k_gemm_tc2<BN, NA, NB, STAGES, F8>;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(TC_THREADS);
   cfg.dynamicSmemBytes = SMEM;
@@ -840,6 +911,19 @@ cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb,
 }
 
 // Q-operand boxes: BN / 2 rows (half of a pair tile, or a whole single-CTA tile)
+cudaError_t launch_gemm_tc_f8(const PMaps &P, const CUtensorMap &Q, int M, int N, int K, const int *k_dev,
+                              float *out, int64_t ldo, const float *row_inv, const float *col_inv, float q_inv,
+                              const int *gate, const int *n_dev, const int *col_map, int *err, const TcStreamK &sk,
+                              cudaStream_t st) {
+  if (M <= TC_BM || !sk.ws || !sk.flags || sk.slots < 1) return cudaErrorInvalidValue;   // pair kernel only
+  TcPairs hi{};
+  hi.n = 1;
+  hi.first_main = 0;
+  hi.first_corr = -1;
+  return launch_tc2_impl<TC_PAIR_BN, 1, 1, tc_stages(1, 1), true>(P, Q, M, N, K, k_dev, hi, out, ldo, row_inv,
+                                                                  col_inv, q_inv, gate, n_dev, col_map, err, sk, st);
+}
+
 int tc_box_rows(int nb) { (void)nb; return TC_PAIR_BN / 2; }
 
 // workspace of the stream-K schedule: one 256 x BN FP32 part per pair slot

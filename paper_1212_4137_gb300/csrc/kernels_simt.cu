@@ -2,6 +2,7 @@
 // CUDA-core contractions of one AM sweep (Algorithm 2): u = A x (dense or over the support of
 // x) and v = A^T y.
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cstdint>
@@ -575,6 +576,77 @@ __global__ void __launch_bounds__(256) k_gemm1_sparse_lowp(const __half *__restr
 #pragma unroll
   for (int q = 0; q < 8; ++q)
     if (i8 + q < n) u[i8 + q] = acc[q];
+}
+
+// The same gather over the FP8 E4M3 copy of A^T (the low-precision sweeps of an FP8 handle): row j
+// is A[:, j] times its scale, undone with at8_inv[j] folded into x_j; 16 rows per thread as one
+// 16-byte load, products and sums in FP32 in support order.
+__global__ void __launch_bounds__(256) k_gemm1_sparse_f8(const uint8_t *__restrict__ AT8, int64_t ldat,
+                                                         const float *__restrict__ at_inv, int n,
+                                                         const int *__restrict__ sup_idx,
+                                                         const float *__restrict__ sup_val, int cap, StartState s,
+                                                         float *__restrict__ U, int64_t ldu,
+                                                         const int *__restrict__ gate) {
+  if (*gate == 0) return;
+  const int c = blockIdx.y;
+  if (s.status[c] != ST_ACTIVE) return;
+  __shared__ int sidx[256];
+  __shared__ float sval[256];
+  const int nnz = s.nnz[c];
+  const int i16 = (blockIdx.x * blockDim.x + threadIdx.x) * 16;
+  const int *gi = sup_idx + (int64_t)c * cap;
+  const float *gv = sup_val + (int64_t)c * cap;
+  float acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
+  auto step = [&](float xv, uint4 raw) {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[q] >> (16 * h)), __NV_E4M3);
+        const float2 f = __half22float2(__half2(hr));
+        acc[4 * q + 2 * h] = fmaf(xv, f.x, acc[4 * q + 2 * h]);
+        acc[4 * q + 2 * h + 1] = fmaf(xv, f.y, acc[4 * q + 2 * h + 1]);
+      }
+    }
+  };
+  for (int t0 = 0; t0 < nnz; t0 += 256) {
+    __syncthreads();
+    if (t0 + (int)threadIdx.x < nnz) {
+      const int j = gi[t0 + threadIdx.x];
+      sidx[threadIdx.x] = j;
+      sval[threadIdx.x] = gv[t0 + threadIdx.x] * at_inv[j];
+    }
+    __syncthreads();
+    const int m = min(256, nnz - t0);
+    if (i16 < n) {
+      const uint8_t *base = AT8 + i16;
+      int t = 0;
+      for (; t + 8 <= m; t += 8) {
+        uint4 a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = __ldg(reinterpret_cast<const uint4 *>(base + (int64_t)sidx[t + q] * ldat));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) step(sval[t + q], a[q]);
+      }
+      for (; t < m; ++t) step(sval[t], __ldg(reinterpret_cast<const uint4 *>(base + (int64_t)sidx[t] * ldat)));
+    }
+  }
+  float *u = U + (int64_t)c * ldu;
+#pragma unroll
+  for (int q = 0; q < 16; ++q)
+    if (i16 + q < n) u[i16 + q] = acc[q];
+}
+
+cudaError_t launch_gemm1_sparse_f8(const uint8_t *AT8, int64_t ldat, const float *at_inv, int n, const int *sup_idx,
+                                   const float *sup_val, int cap, StartState s, int r, float *U, int64_t ldu,
+                                   const int *gate, cudaStream_t st) {
+  if (ldat % 16 != 0 || (reinterpret_cast<uintptr_t>(AT8) & 15u) != 0) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)((n + 4095) / 4096), (unsigned)r);
+  k_gemm1_sparse_f8<<<grid, 256, 0, st>>>(AT8, ldat, at_inv, n, sup_idx, sup_val, cap, s, U, ldu, gate);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gemm1_sparse_lowp(const void *AT0, int64_t ldat, const float *at_inv, int n, const int *sup_idx,

@@ -63,12 +63,23 @@ struct spca_handle {
   float *a_scale = nullptr, *a_inv = nullptr;     // row scales of A (n) and their inverses
   float *at_scale = nullptr, *at_inv = nullptr;   // row scales of A^T (p) and their inverses
   PMaps pmA{}, pmAT{};                     // P-operand maps of the planes (per cluster size)
+  // FP8 E4M3 copies for the low-precision sweeps (storage SPCA_FP8_E4M3_COLSCALED): A (rows scaled)
+  // and A^T (A's columns scaled), their inverse scales and P-operand maps (128-row boxes)
+  bool fp8 = false;
+  uint8_t *A8 = nullptr, *AT8 = nullptr;
+  int64_t ldA8 = 0, ldAT8 = 0;
+  float *a8_inv = nullptr, *at8_inv = nullptr;
+  PMaps pmA8{}, pmAT8{};
 
   // per-solve workspace, grown on demand
   int r_cap = 0;
   int64_t ldX = 0, ldU = 0;
   float *X = nullptr, *V = nullptr, *U = nullptr, *Y = nullptr;
   void *Xpl = nullptr, *Ypl = nullptr;     // kPlanes FP16 planes each (tensor-core engine)
+  uint8_t *X8 = nullptr, *Y8 = nullptr;    // FP8 operands of the low-precision sweeps (FP8 storage)
+  int64_t ldX8 = 0, ldU8 = 0;
+  float *x8_inv = nullptr;
+  CUtensorMap tmX8{}, tmY8{};
   float *x_scale = nullptr, *x_inv = nullptr;   // row scales of the packed X planes
   CUtensorMap tmX2{}, tmX1{}, tmY1{}, tmY2{};   // Q-operand maps: X planes (both or the leading one),
                                                 // y = +-1 or the leading plane of y, y planes
@@ -223,9 +234,11 @@ void free_workspace(spca_handle *h) {
                   h->status, h->iters, h->nnz, h->F, h->F_prev, h->gamma, h->f, h->ev, h->thr, h->tprev, h->xfast,
                   h->partials, h->ctrl, h->best, h->y_out, h->x_out, h->support_out, h->nnz_out,
                   h->mark, h->colpos, h->collist, h->AS, h->XS, h->x_scale, h->x_inv, h->Bt, h->sp_part, h->ysum,
-                  h->xs.cand_val, h->xs.cand_idx, h->xs.meta};
+                  h->xs.cand_val, h->xs.cand_idx, h->xs.meta, h->X8, h->Y8, h->x8_inv};
   for (void *q : ptrs)
     if (q) cudaFree(q);
+  h->X8 = h->Y8 = nullptr;
+  h->x8_inv = nullptr;
   h->Bt = h->sp_part = h->ysum = nullptr;
   h->xs = XstepScratch{};
   h->ldb = 0;
@@ -298,6 +311,17 @@ int ensure_workspace(spca_handle *h, int r) {
     CK(dalloc(&h->XS, (size_t)kPlanes * r * h->kcap, 2));
     CK(make_p_maps(&h->pmAS, h->AS, n, h->kcap, 2));
     CK(make_plane_map(&h->tmXS2, h->XS, r, h->kcap, 2, tc_box_rows(2), tc_bk(2)));
+  }
+  if (h->fp8 && h->tc_ok) {
+    h->ldX8 = (p + 15) / 16 * 16;
+    h->ldU8 = (n + 15) / 16 * 16;
+    CK(dalloc(&h->X8, (size_t)r * h->ldX8));
+    CK(dalloc(&h->Y8, (size_t)r * h->ldU8));
+    CK(dalloc(&h->x8_inv, (size_t)r));
+    CK(cudaMemsetAsync(h->X8, 0, (size_t)r * h->ldX8, h->stream));
+    CK(cudaMemsetAsync(h->Y8, 0, (size_t)r * h->ldU8, h->stream));
+    CK(make_f8_map(&h->tmX8, h->X8, r, h->ldX8, tc_box_rows(1)));
+    CK(make_f8_map(&h->tmY8, h->Y8, r, h->ldU8, tc_box_rows(1)));
   }
   if (h->sparse) {
     h->ldb = (r + kSpGroup - 1) / kSpGroup * kSpGroup;
@@ -434,6 +458,12 @@ TcPairs pairs_hi() {
   return t;
 }
 
+// the low-precision sweeps of an FP8 handle run on its E4M3 copies (the pair kernel: both sides of
+// A above one 128-row tile and stream-K scratch; a clone's sweeps take the FP16 leading planes)
+bool f8_sweeps(const spca_handle *h) {
+  return h->fp8 && h->sk.ws && h->n > TC_BM_ROWS && h->p > TC_BM_ROWS;
+}
+
 SpMat sp_rows(const spca_handle *h) { return SpMat{h->a_ptr, h->a_col, h->a_val, (int)h->n, (int)h->p}; }
 SpMat sp_cols(const spca_handle *h) { return SpMat{h->at_ptr, h->at_col, h->at_val, (int)h->p, (int)h->n}; }
 LowRank low_rank(const spca_handle *h) {
@@ -494,7 +524,19 @@ int sweep_u_dense(spca_handle *h, int engine, int r, const int *gate, const int 
   if (h->sparse) return sweep_u_rows(h, r, gate, nact, list);
   const int n = (int)h->n, p = (int)h->p;
   cudaStream_t st = h->stream;
-  if (engine == SPCA_ENGINE_TC) {
+  if (engine == SPCA_ENGINE_TC && lowp && f8_sweeps(h)) {
+    // FP8 low-precision sweep: x in E4M3 with the planes' row scales times 2^-6
+    CK(timed(h, SPCA_K_U_DENSE, 4, [&] {
+      cudaError_t e = launch_row_scales(h->X, nhost, p, h->ldX, h->x_scale, h->x_inv, gate, nact, list, st);
+      if (e != cudaSuccess) return e;
+      e = launch_split_f8(h->X, r, p, h->ldX, h->X8, h->ldX8, h->x_scale, kF8Mul, gate, nact, list, st);
+      if (e != cudaSuccess) return e;
+      e = launch_scale_copy(h->x_inv, r, 1.0f / kF8Mul, h->x8_inv, gate, st);
+      if (e != cudaSuccess) return e;
+      return launch_gemm_tc_f8(h->pmA8, h->tmX8, n, nhost, p, nullptr, h->U, h->ldU, h->a8_inv, h->x8_inv, 1.0f,
+                               gate, nact, list, h->dev_err, h->sk, st);
+    }));
+  } else if (engine == SPCA_ENGINE_TC) {
     CK(timed(h, SPCA_K_U_DENSE, 3, [&] {
       cudaError_t e = launch_row_scales(h->X, nhost, p, h->ldX, h->x_scale, h->x_inv, gate, nact, list, st);
       if (e != cudaSuccess) return e;
@@ -574,11 +616,22 @@ int sweep_y_v(spca_handle *h, int engine, int form, int r, StartState S, const i
     (void)nhost;
     return SPCA_OK;
   }
+  // the FP8 low-precision sweep reads y as FP32 (converted to E4M3 below); the others read the planes
+  const bool f8 = tc && lowp && f8_sweeps(h);
   CK(timed(h, SPCA_K_YSTEP, 1, [&] {
-    return launch_ystep(form, h->U, h->ldU, n, r, tc ? nullptr : h->Y, tc ? h->Ypl : nullptr, ypstride,
-                        tc ? h->rank : nullptr, S, h->X, h->ldX, p, h->ysum, st);
+    return launch_ystep(form, h->U, h->ldU, n, r, tc && !f8 ? nullptr : h->Y, tc && !f8 ? h->Ypl : nullptr,
+                        ypstride, tc ? h->rank : nullptr, S, h->X, h->ldX, p, h->ysum, st);
   }));
-  if (tc && lowp) {
+  if (f8) {
+    // FP8 low-precision sweep: y (written as FP32 by the y-step) in E4M3 at scale 2^7
+    CK(timed(h, SPCA_K_V, 2, [&] {
+      cudaError_t e = launch_split_f8(h->Y, r, n, h->ldU, h->Y8, h->ldU8, nullptr, kF8QScale, nullptr, nact, h->act,
+                                      st);
+      if (e != cudaSuccess) return e;
+      return launch_gemm_tc_f8(h->pmAT8, h->tmY8, p, nhost, n, nullptr, h->V, h->ldX, h->at8_inv, nullptr,
+                               1.0f / kF8QScale, nullptr, nact, h->act, h->dev_err, h->sk, st);
+    }));
+  } else if (tc && lowp) {
     CK(timed(h, SPCA_K_V, 1, [&] {
       return launch_gemm_tc(h->pmAT, 1, h->tmY1, 1, p, nhost, n, nullptr, pairs_hi(), h->V, h->ldX, h->at_inv,
                             nullptr, kQInv, nullptr, nact, h->act, h->dev_err, h->sk, st);
@@ -697,6 +750,18 @@ int build_operands(spca_handle *h) {
                               1.0f, nullptr, nullptr, nullptr, h->stream);
     return e;
   }));
+  if (!h->fp8) return SPCA_OK;
+  // FP8 copies: the planes' row scales times 2^-6 (the largest entry of a row in [128, 256))
+  CK(timed(h, SPCA_K_PREP, 4, [&] {
+    cudaError_t e = launch_split_f8(h->A32, n, p, h->ldA, h->A8, h->ldA8, h->a_scale, kF8Mul, nullptr, nullptr,
+                                    nullptr, h->stream);
+    if (e == cudaSuccess) e = launch_scale_copy(h->a_inv, (int)n, 1.0f / kF8Mul, h->a8_inv, nullptr, h->stream);
+    if (e == cudaSuccess)
+      e = launch_split_f8(h->AT32, p, n, h->ldAT, h->AT8, h->ldAT8, h->at_scale, kF8Mul, nullptr, nullptr, nullptr,
+                          h->stream);
+    if (e == cudaSuccess) e = launch_scale_copy(h->at_inv, (int)p, 1.0f / kF8Mul, h->at8_inv, nullptr, h->stream);
+    return e;
+  }));
   return SPCA_OK;
 }
 
@@ -792,7 +857,8 @@ void spca_destroy(spca_handle *h) {
     if (q) cudaFree(q);
   // the matrix, with the last handle that holds it
   if (!h->shared || h->shared->refs.fetch_sub(1) == 1) {
-    void *mat[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->a_scale, h->a_inv, h->at_scale, h->at_inv,
+    void *mat[] = {h->A32, h->AT32, h->Apl, h->ATpl, h->a_scale, h->a_inv, h->at_scale, h->at_inv, h->A8, h->AT8,
+                   h->a8_inv, h->at8_inv,
                    h->a_ptr, h->a_col, h->a_val, h->at_ptr, h->at_col, h->at_val, h->Wd, h->Zd,
                    h->plan_a.items, h->plan_a.longs, h->plan_at.items, h->plan_at.longs};
     for (void *q : mat)
@@ -812,8 +878,8 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
   if (!out || !A) return SPCA_E_INVALID;
   if (n < 1 || p < 1 || lda < p || n > INT32_MAX || p > INT32_MAX) return SPCA_E_INVALID;
   if (in_dtype != SPCA_F32 && in_dtype != SPCA_F64) return SPCA_E_INVALID;
-  if (storage != SPCA_F32 && storage != SPCA_BF16) {
-    if (storage == SPCA_FP8_E4M3_COLSCALED || storage == SPCA_F64) return SPCA_E_UNSUPPORTED;
+  if (storage != SPCA_F32 && storage != SPCA_BF16 && storage != SPCA_FP8_E4M3_COLSCALED) {
+    if (storage == SPCA_F64) return SPCA_E_UNSUPPORTED;
     return SPCA_E_INVALID;
   }
   int ndev = 0, dev = 0;
@@ -838,7 +904,9 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
     h->tc_ok = major >= 10;
     CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
-    if (storage == SPCA_BF16 && !h->tc_ok) return SPCA_E_UNSUPPORTED;   // the planes need tcgen05
+    if ((storage == SPCA_BF16 || storage == SPCA_FP8_E4M3_COLSCALED) && !h->tc_ok)
+      return SPCA_E_UNSUPPORTED;   // the planes need tcgen05
+    h->fp8 = storage == SPCA_FP8_E4M3_COLSCALED;
     CK(cudaMallocHost((void **)&h->h_ctrl, 2 * sizeof(Ctrl)));
     CK(cudaMallocHost((void **)&h->h_flag, 2 * sizeof(int)));
     h->h_flag[0] = h->h_flag[1] = 0;
@@ -870,6 +938,17 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
       CK(dalloc(&h->ATpl, (size_t)kPlanes * p * h->ldAT, 2));
       CK(dalloc(&h->a_scale, (size_t)n)); CK(dalloc(&h->a_inv, (size_t)n));
       CK(dalloc(&h->at_scale, (size_t)p)); CK(dalloc(&h->at_inv, (size_t)p));
+    }
+    if (h->fp8) {
+      h->ldA8 = (p + 15) / 16 * 16;
+      h->ldAT8 = (n + 15) / 16 * 16;
+      CK(dalloc(&h->A8, (size_t)n * h->ldA8));
+      CK(dalloc(&h->AT8, (size_t)p * h->ldAT8));
+      CK(cudaMemsetAsync(h->A8, 0, (size_t)n * h->ldA8, h->stream));
+      CK(cudaMemsetAsync(h->AT8, 0, (size_t)p * h->ldAT8, h->stream));
+      CK(dalloc(&h->a8_inv, (size_t)n)); CK(dalloc(&h->at8_inv, (size_t)p));
+      CK(make_f8_map(&h->pmA8.m[0], h->A8, n, h->ldA8, TC_BM_ROWS));
+      CK(make_f8_map(&h->pmAT8.m[0], h->AT8, p, h->ldAT8, TC_BM_ROWS));
     }
     RC(build_operands(h));
     if (h->tc_ok) {
@@ -1008,6 +1087,11 @@ int spca_clone(spca_handle **out, spca_handle *src, void *cuda_stream) {
   h->a_scale = src->a_scale; h->a_inv = src->a_inv;
   h->at_scale = src->at_scale; h->at_inv = src->at_inv;
   h->pmA = src->pmA; h->pmAT = src->pmAT;
+  h->fp8 = src->fp8;
+  h->A8 = src->A8; h->AT8 = src->AT8;
+  h->ldA8 = src->ldA8; h->ldAT8 = src->ldAT8;
+  h->a8_inv = src->a8_inv; h->at8_inv = src->at8_inv;
+  h->pmA8 = src->pmA8; h->pmAT8 = src->pmAT8;
   int rc = [&]() -> int {
     h->user = (cudaStream_t)cuda_stream;
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
@@ -1061,8 +1145,9 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
   if (!h || !X || !U || !V || r < 1) return fail(h, SPCA_E_INVALID, "bad argument%s");
   if (form < 1 || form > 8) return fail(h, SPCA_E_INVALID, "form must be 1..8%s");
   if (ldx < h->p || ldv < h->p || ldu < h->n) return fail(h, SPCA_E_INVALID, "leading dimension too small%s");
+  const bool lowp = engine == SPCA_ENGINE_TC_LOWP;
   int eng;
-  RC(resolve_engine(h, engine, r, false, &eng));
+  RC(resolve_engine(h, lowp ? SPCA_ENGINE_TC : engine, r, lowp, &eng));
   RC(enter(h));
   RC(ensure_workspace(h, r));
   RC(ensure_lr_coef(h, r));
@@ -1074,9 +1159,9 @@ int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t 
   CK(cudaMemsetAsync(h->iters, 0, (size_t)r * sizeof(int), st));
   CK(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), st));
   CK(launch_active_list(h->status, nullptr, r, h->act, h->rank, &h->ctrl[0], st));
-  RC(sweep_u_dense(h, eng, r, nullptr, &h->ctrl[0].active, r, false));
+  RC(sweep_u_dense(h, eng, r, nullptr, &h->ctrl[0].active, r, lowp));
   RC(sweep_lowrank_u(h, r, &h->ctrl[0].active, h->act));
-  RC(sweep_y_v(h, eng, form, r, state_of(h), &h->ctrl[0].active, r));
+  RC(sweep_y_v(h, eng, form, r, state_of(h), &h->ctrl[0].active, r, lowp));
   CK(cudaMemcpy2DAsync(U, ldu * sizeof(float), h->U, h->ldU * sizeof(float), (size_t)n * sizeof(float), r,
                        cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpy2DAsync(V, ldv * sizeof(float), h->V, h->ldX * sizeof(float), (size_t)p * sizeof(float), r,
@@ -1220,6 +1305,9 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
       if (h->sparse)
         return launch_spmv_support(sp_cols(h), n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU, &cur->use_gather,
                                    st);
+      if (pl.lowp && f8_sweeps(h))
+        return launch_gemm1_sparse_f8(h->AT8, h->ldAT8, h->at8_inv, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
+                                      &cur->use_gather, st);
       if (pl.lowp)
         return launch_gemm1_sparse_lowp(h->ATpl, h->ldAT, h->at_inv, n, h->sup_idx, h->sup_val, p, S, r, h->U, h->ldU,
                                         &cur->use_gather, st);

@@ -286,6 +286,7 @@ cudaError_t launch_deflate(float *A, int64_t lda, int n, int p, const float *x, 
 // the fixed scale kQScale; x (any magnitude through spca_products) one scale per row, like P.
 // The epilogue multiplies by the inverse scales, powers of two.
 constexpr int kPlanes = 2;
+constexpr int TC_BM_ROWS = 128;   // rows of a P tile per CTA (the contraction's M tile)
 constexpr float kQScale = 16384.0f;
 constexpr float kQInv = 1.0f / 16384.0f;
 // per-row scales of an FP32 matrix: scale[r] = 2^(13 - floor(log2 max |src[row_map[r], :]|)) (1
@@ -335,7 +336,33 @@ cudaError_t launch_split_planes(const float *src, int64_t rows, int64_t cols, in
                                 int64_t ldd, int64_t plane_stride, int nplanes, const float *row_scale,
                                 float scale, const int *gate, const int *rows_dev, const int *row_map,
                                 cudaStream_t st);
-// union S of the active starts' supports: colpos[j] = position of column j in S (or -1),
+// FP8 E4M3 operands (the low-precision sweeps of a handle stored as SPCA_FP8_E4M3_COLSCALED):
+// one plane of rows x ld bytes (ld a multiple of 16), box 128 x box_rows, 128-byte swizzle
+cudaError_t make_f8_map(CUtensorMap *map, const void *base, int64_t rows, int64_t ld, int box_rows);
+// the pair contraction on one FP8 plane of each operand (kind::f8f6f4), FP32 accumulation; the pair
+// kernel only (M > 128 and stream-K scratch), else cudaErrorInvalidValue
+cudaError_t launch_gemm_tc_f8(const PMaps &P, const CUtensorMap &Q, int M, int N, int K, const int *k_dev,
+                              float *out, int64_t ldo, const float *row_inv, const float *col_inv, float q_inv,
+                              const int *gate, const int *n_dev, const int *col_map, int *err, const TcStreamK &sk,
+                              cudaStream_t st);
+// dst row r = E4M3(src row row_map[r] x row_scale[r] x mul), saturating; rows from *rows_dev when
+// given; gated
+cudaError_t launch_split_f8(const float *src, int64_t rows, int64_t cols, int64_t lds, uint8_t *dst, int64_t ldd,
+                            const float *row_scale, float mul, const int *gate, const int *rows_dev,
+                            const int *row_map, cudaStream_t st);
+// dst = src x mul (n floats); gated
+cudaError_t launch_scale_copy(const float *src, int n, float mul, float *dst, const int *gate, cudaStream_t st);
+// u = A x over the supports from the FP8 copy of A^T (rows scaled; at_inv undoes it)
+cudaError_t launch_gemm1_sparse_f8(const uint8_t *AT8, int64_t ldat, const float *at_inv, int n, const int *sup_idx,
+                                   const float *sup_val, int cap, StartState s, int r, float *U, int64_t ldu,
+                                   const int *gate, cudaStream_t st);
+// the FP8 scales: the FP16 planes' row scales (largest entry in [2^13, 2^14)) times 2^-6, so that
+// the largest entry lies in [128, 256) below E4M3's largest finite value (448); y (|y_i| <= 1)
+// takes 2^7
+constexpr float kF8Mul = 1.0f / 64.0f;
+constexpr float kF8QScale = 128.0f;
+
+// union S of the active starts' supports:// union S of the active starts' supports: colpos[j] = position of column j in S (or -1),
 // collist[k] = the k-th column of S (k < kcap), c->kunion = |S|; then c->use_union (S fits in
 // kcap columns and no start needs the dense path) and, if set, c->use_gather = 0.
 // mark: p ints of scratch

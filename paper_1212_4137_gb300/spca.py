@@ -18,7 +18,7 @@ SPCA_OK, SPCA_E_INVALID, SPCA_E_NOMEM, SPCA_E_CUDA, SPCA_E_TIMEOUT, SPCA_E_BUSY,
 SPCA_F32, SPCA_F64, SPCA_BF16, SPCA_FP8_E4M3_COLSCALED = range(4)
 SPCA_GAMMA_FIXED, SPCA_GAMMA_TARGET_NNZ = 0, 1
 SPCA_ST_MAXITER, SPCA_ST_CONVERGED, SPCA_ST_DEGENERATE = 0, 1, 2
-SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC = 0, 1, 2
+SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC, SPCA_ENGINE_TC_LOWP = 0, 1, 2, 3
 
 # every symbol include/spca.h declares
 EXPORTS = ("spca_create", "spca_create_csr", "spca_clone", "spca_solve", "spca_xstep", "spca_products", "spca_deflate", "spca_profile_enable",

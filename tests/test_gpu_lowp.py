@@ -1,6 +1,8 @@
 """GPU checks of the solve options around Algorithm 2: low-precision sweeps (A rounded to 11
-significant bits, the leading FP16 plane, for the first sweeps, then FP32 sweeps to the stopping
-rule), the cap on the FP32 sweeps, the wall-clock limit, and 16-bit storage handles.
+significant bits, the leading FP16 plane, or to 4 with FP8 E4M3 storage, for the first sweeps,
+then FP32 sweeps to the stopping rule), the cap on the FP32 sweeps, the wall-clock limit, 16- and
+8-bit storage handles, and the low-precision contractions themselves against FP64 with the bound
+their rounding gives.
 
 Low-precision sweeps change the trajectory, so a start may reach another stationary point than in
 a plain FP32 solve, and in the gamma-targeting mode gamma is calibrated on the rounded v.  What
@@ -40,11 +42,12 @@ def _kw(form):
     return dict(s=20.0, gamma_target=True, calib=8)
 
 
+@pytest.mark.parametrize("storage", ["f32", "fp8"])
 @pytest.mark.parametrize("form", range(1, 9))
-def test_lowp_then_fp32_refines(lib, oracle, spiked, form):
+def test_lowp_then_fp32_refines(lib, oracle, spiked, form, storage):
     A, G = spiked
     A64 = A.astype(np.float64)
-    h = lib.Handle(A)
+    h = lib.Handle(A, storage=lib.SPCA_FP8_E4M3_COLSCALED if storage == "fp8" else lib.SPCA_F32)
     r = G.shape[0]
     ref = h.solve(form, r, x0=G, max_iter=80, tol=1e-7, want_starts=True, **_kw(form))
     got = h.solve(form, r, x0=G, max_iter=80, tol=1e-7, want_starts=True, lowp_sweeps=12, **_kw(form))
@@ -120,3 +123,58 @@ def test_bf16_storage_handle(lib, spiked):
     h16.close()
     assert a["objective"] == b["objective"]
     assert np.array_equal(a["support"], b["support"])
+
+
+def _products_lowp(lib, h, form, X):
+    import torch
+    r, p = X.shape
+    n = h.n
+    Xd = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
+    Ud = torch.zeros((r, n), dtype=torch.float32, device="cuda")
+    Vd = torch.zeros((r, p), dtype=torch.float32, device="cuda")
+    st = lib.spca_products(h.h, form, lib.SPCA_ENGINE_TC_LOWP, Xd.data_ptr(), p, r, Ud.data_ptr(), n, Vd.data_ptr(), p)
+    assert st == 0, lib.spca_last_error(h.h)
+    torch.cuda.synchronize()
+    return Ud.cpu().numpy().astype(np.float64), Vd.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("storage,eps", [("bf16", 2.0 ** -12), ("fp8", 2.0 ** -4)])
+@pytest.mark.parametrize("form", [1, 2])
+def test_lowp_contractions_within_rounding(lib, spiked, storage, eps, form):
+    """u = A x and v = A^T y on the low-precision copies.  Both operands are rounded to nearest
+    with relative error at most eps (the leading FP16 plane: 2^-12; E4M3: 2^-4), each product then
+    errs by at most (2 eps + eps^2) |a b|, and the FP32 sums add little: the error of every output
+    stays below 2.1 eps of sum |a_k b_k| (E4M3 flushes entries below 2^-9 of the scaled range to
+    zero, far below that).  y = +-1 (form 2) is exact in both formats."""
+    A, G = spiked
+    r = 40
+    X = G[:r].copy()
+    X[3, :: 2] = 0.0
+    st = {"bf16": lib.SPCA_BF16, "fp8": lib.SPCA_FP8_E4M3_COLSCALED}[storage]
+    h = lib.Handle(A, storage=st)
+    U, V = _products_lowp(lib, h, form, X)
+    h.close()
+    A64, X64 = A.astype(np.float64), X.astype(np.float64)
+    scale_u = np.abs(X64) @ np.abs(A64).T
+    err_u = np.abs(U - X64 @ A64.T) / scale_u
+    assert err_u.max() <= 2.1 * eps, err_u.max()
+    Y = np.where(U >= 0, 1.0, -1.0) if form == 2 else U / np.linalg.norm(U, axis=1, keepdims=True)
+    scale_v = np.abs(Y) @ np.abs(A64)
+    err_v = np.abs(V - Y @ A64) / scale_v
+    assert err_v.max() <= (1.1 if form == 2 else 2.1) * eps, err_v.max()
+    # and the errors are rounding, not a misplaced operand: far below the bound on average
+    assert np.median(err_u) <= 0.25 * eps and np.median(err_v) <= 0.25 * eps
+
+
+def test_fp8_storage_handle(lib, spiked):
+    A, G = spiked
+    h8 = lib.Handle(A, storage=lib.SPCA_FP8_E4M3_COLSCALED)
+    out = h8.solve(1, 24, x0=G[:24], s=20.0, max_iter=40, tol=-1, lowp_sweeps=10, want_starts=True)
+    # FP32 sweeps (no low-precision ones) are those of an FP32 handle
+    h32 = lib.Handle(A)
+    a = h32.solve(1, 24, x0=G[:24], s=20.0, max_iter=30, tol=-1)
+    b = h8.solve(1, 24, x0=G[:24], s=20.0, max_iter=30, tol=-1)
+    h32.close()
+    h8.close()
+    assert a["objective"] == b["objective"] and np.array_equal(a["support"], b["support"])
+    assert np.all(out["start_iters"] == 40)
