@@ -44,10 +44,10 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "spiked-5000x20000-r1024"
 
 # DRAM traffic of one v = A^T y launch of the tensor-core contraction at the spiked workload's size
-# with 1024 active starts (dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture: 479.8 MB
-# + 82.3 MB), and the algorithmic bytes of that launch: two FP16 planes of A^T (400 MB), two of Y
+# with 1024 active starts (dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture: 481.8 MB
+# + 83.1 MB), and the algorithmic bytes of that launch: two FP16 planes of A^T (400 MB), two of Y
 # (20.5 MB), V written once (81.9 MB)
-V_TRAFFIC_BYTES = 562.0e6
+V_TRAFFIC_BYTES = 564.9e6
 V_ALG_BYTES = 502.4e6
 
 # peak of the FP32 CUDA-core pipe: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz
