@@ -674,25 +674,32 @@ __device__ void xstep_finish_warp(const XstepArgs &a, int c, const float *vv, in
 // ---------------------------------------------------------------- candidate x-step
 // Near convergence v moves little between sweeps, and every operator keeps only entries above a
 // threshold (the s-th or (s+1)-th largest |v_i|, lambda_s, or the penalty's fixed threshold).
-// One coalesced pass keeps the entries above a guess G -- the fixed threshold itself, or
-// kGuess times last sweep's -- in per-warp lists (index order) and sums |v| and v^2 for the
-// lambda test; the operator then runs on the candidates in shared memory, and x (zero outside
-// the last support list) changes only on the old and the new support.  G is valid
-// when the operator's threshold lies above it: at least s (or s + 1) candidates for the
-// selections, phi(G) < 0 for lambda_s (phi increases through its root); then the candidates
-// hold every surviving entry and the result is the full pass's.  Otherwise, or when a warp's
-// list overflows, the start is left to k_xstep (xfast[c] = 0).
+// One coalesced pass keeps the entries above a guess in per-warp lists (index order) and sums
+// |v| and v^2 for the lambda test; the operator then runs on the candidates in shared memory, and
+// x (zero outside the last support list) changes only on the old and the new support.  A guess G
+// is valid when the operator's threshold lies above it: at least s (or s + 1) candidates for the
+// selections, phi(G) < 0 for lambda_s (phi increases through its root); then the candidates hold
+// every surviving entry and the result is the full pass's.
+// Two guesses from last sweep's threshold t: the filter keeps the entries above G_lo = kGuessLo t
+// while every warp's list has room, and above G_hi = kGuess t otherwise (a warp whose list would
+// overflow drops its entries at or below G_hi and goes on with G_hi; then every warp does).  The
+// operator takes G_hi when it is valid (fewer candidates) and G_lo otherwise: early sweeps, where
+// the threshold can fall by more than a few per cent, then still avoid the full pass.  A penalty
+// with its threshold fixed uses that threshold alone (exact).  When no guess is valid, or a list
+// overflows at G_hi, the start is left to k_xstep (xfast[c] = 0).
 constexpr int kCandW = 64;               // candidates per warp
 constexpr int kCand = kCandW * XW;       // per start
 static_assert(kCand == kXstepCand, "candidate scratch size");
 constexpr float kGuess = 0.85f;
+constexpr float kGuessLo = 0.6f;
 constexpr int kCandMinP = 4096;          // shorter v: the full pass only
+constexpr int kMetaHi = 1, kMetaLo = 2;  // meta[c].w: the list holds the entries above G_hi / G_lo
 
-// the candidate x-step's per-start prelude: the guess G (exact: G is the threshold itself), the
-// number of candidates the operator needs, and whether the filter applies at all
+// the candidate x-step's per-start prelude: the guesses (exact: G_hi = G_lo = the threshold
+// itself), the number of candidates the operator needs, and whether the filter applies at all
 struct CandPlan {
   XstepArgs a;
-  float G;
+  float G, Glo;
   bool exact, usable;
   int need, s_int;
 };
@@ -702,25 +709,57 @@ __device__ __forceinline__ CandPlan cand_plan(const XstepArgs &a_in, const Start
   const int p = q.a.p, form = q.a.form;
   q.s_int = (int)q.a.s;
   q.exact = false;
-  q.G = 0.0f;
   if (is_pen(form) && !q.a.calibrate) {
     q.exact = true;
     q.G = q.a.per_start_thr ? st.thr[c] : q.a.thr_fixed;
+    q.Glo = q.G;
   } else {
-    q.G = kGuess * st.tprev[c];
+    const float t = st.tprev[c];
+    q.G = kGuess * t;
+    q.Glo = kGuessLo * t;
   }
   q.need = uses_T(form) ? q.s_int : (is_pen(form) && q.a.calibrate ? q.s_int + 1 : 1);
   // x is zero outside the last x-step's support list, so only that list is cleared; after the
   // start init (first sweep) x is dense and there is no list: the full pass writes all of x
-  q.usable = !((!q.exact && !(q.G > 0.0f)) || q.need > p || (uses_T(form) && q.s_int >= p) || st.iters[c] <= 1 ||
+  q.usable = !((!q.exact && !(q.Glo > 0.0f)) || q.need > p || (uses_T(form) && q.s_int >= p) || st.iters[c] <= 1 ||
                !lists || st.nnz[c] > q.a.cap);
   return q;
 }
 
-// Filter: one coalesced pass keeps the entries above G in per-warp lists, concatenated in warp
-// order (the candidates in index order) into cand_val / cand_idx (kCand per start), with the sums
-// of |v| and v^2 and the count in meta[c]; x is cleared on the last support.  A start the filter
-// cannot serve gets xfast[c] = 0 and meta[c].w = 0.
+// keep the entries of a warp's list (val, idx)[0 .. len) whose key is above Gk, in order, in place;
+// returns the new length (every lane)
+__device__ __forceinline__ int warp_compact_above(float *val, int *idx, int len, uint32_t Gk) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int out = 0;
+  __syncwarp();     // the list's entries written by other lanes are visible
+  for (int base = 0; base < len; base += 32) {
+    const int t = base + lane;
+    float v = 0.0f;
+    int ix = 0;
+    bool keep = false;
+    if (t < len) {
+      v = val[t];
+      ix = idx[t];
+      keep = abs_key(v) > Gk;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, keep);
+    __syncwarp();   // every lane has read its entry before any is overwritten
+    if (keep) {     // slot <= t: entries of later rounds are untouched
+      const int q = out + __popc(b & lt);
+      val[q] = v;
+      idx[q] = ix;
+    }
+    out += __popc(b);
+    __syncwarp();
+  }
+  return out;
+}
+
+// Filter: one coalesced pass keeps the entries above the guess in per-warp lists, concatenated in
+// warp order (the candidates in index order) into cand_val / cand_idx (kCand per start), with the
+// sums of |v| and v^2 (lambda forms) and the count in meta[c]; x is cleared on the last support.
+// A start the filter cannot serve gets xfast[c] = 0 and meta[c].w = 0.
 __global__ void __launch_bounds__(XT) k_xstep_filter(XstepArgs a_in, const float *__restrict__ V, int64_t ldv,
                                                      float *__restrict__ X, int64_t ldx, StartState st,
                                                      const int *__restrict__ sup_idx, float *__restrict__ cand_val,
@@ -728,7 +767,7 @@ __global__ void __launch_bounds__(XT) k_xstep_filter(XstepArgs a_in, const float
   __shared__ XShared sh;
   __shared__ float wval_s[kCand];
   __shared__ int widx_s[kCand];
-  __shared__ int fail_s;
+  __shared__ int fail_s, raised_s;
   const int c = blockIdx.x;
   if (st.status[c] != ST_ACTIVE) return;
   const CandPlan q = cand_plan(a_in, st, c, sup_idx != nullptr);
@@ -740,8 +779,12 @@ __global__ void __launch_bounds__(XT) k_xstep_filter(XstepArgs a_in, const float
     return;
   }
   const int p = q.a.p;
+  const bool sums = uses_lam(q.a.form);   // |v| and v^2 sums: the lambda forms' phi(0) test
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t Gk = __float_as_uint(q.G);
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t Ghi = __float_as_uint(q.G);
+  uint32_t Gk = __float_as_uint(q.Glo);   // the warp's current guess (warp-uniform)
+  bool raised = Gk == Ghi;
   // four 128-entry chunks per step, their loads issued before any is used
   const float *vg = V + (int64_t)c * ldv;
   float *x = X + (int64_t)c * ldx;
@@ -754,55 +797,74 @@ __global__ void __launch_bounds__(XT) k_xstep_filter(XstepArgs a_in, const float
   float f1 = 0.0f, f2 = 0.0f;
   for (int base = lo; base < hi && !over; base += 512) {
     float e[4][4];
+    const bool full = base + 512 <= hi;
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       const int i0 = base + h * 128 + 4 * lane;
-      if (i0 + 3 < hi) {
+      if (full || i0 + 3 < hi) {
         const float4 t = *reinterpret_cast<const float4 *>(vg + i0);
         e[h][0] = t.x; e[h][1] = t.y; e[h][2] = t.z; e[h][3] = t.w;
       } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) e[h][k] = (i0 + k < hi) ? vg[i0 + k] : 0.0f;
+        for (int k = 0; k < 4; ++k) e[h][k] = (i0 + k < hi) ? vg[i0 + k] : 0.0f;   // 0 is never kept
       }
     }
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       const int i0 = base + h * 128 + 4 * lane;
-      int cnt = 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float av = fabsf(e[h][k]);
-        cnt += (i0 + k < hi && __float_as_uint(av) > Gk) ? 1 : 0;
-        f1 += av;
-        f2 = fmaf(av, av, f2);
-      }
-      // the warp's exclusive prefix of cnt (0..4) from the ballots of its three bits
-      const unsigned lt = (1u << lane) - 1u;
-      const unsigned b0 = __ballot_sync(0xffffffffu, cnt & 1), b1 = __ballot_sync(0xffffffffu, cnt & 2),
-                     b2 = __ballot_sync(0xffffffffu, cnt & 4);
-      const int excl = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
-      const int tot = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
-      if (over || wc + tot > kCandW) {
-        over = true;
-      } else {
-        int q2 = wc + excl;
+      if (sums) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          if (i0 + k < hi && abs_key(e[h][k]) > Gk) {
-            wv[q2] = e[h][k];
-            wi[q2] = i0 + k;
-            ++q2;
-          }
+          const float av = fabsf(e[h][k]);
+          f1 += av;
+          f2 = fmaf(av, av, f2);
         }
-        wc += tot;
       }
+      int cnt = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cnt += abs_key(e[h][k]) > Gk ? 1 : 0;
+      if (!__any_sync(0xffffffffu, cnt != 0)) continue;   // the common case: nothing above the guess
+      // the warp's exclusive prefix of cnt (0..4) from the ballots of its three bits
+      unsigned b0 = __ballot_sync(0xffffffffu, cnt & 1), b1 = __ballot_sync(0xffffffffu, cnt & 2),
+               b2 = __ballot_sync(0xffffffffu, cnt & 4);
+      int tot = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+      if (wc + tot > kCandW && !raised) {   // no room at G_lo: keep only the entries above G_hi
+        wc = warp_compact_above(wv, wi, wc, Ghi);
+        Gk = Ghi;
+        raised = true;
+        cnt = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cnt += abs_key(e[h][k]) > Gk ? 1 : 0;
+        b0 = __ballot_sync(0xffffffffu, cnt & 1);
+        b1 = __ballot_sync(0xffffffffu, cnt & 2);
+        b2 = __ballot_sync(0xffffffffu, cnt & 4);
+        tot = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+      }
+      if (wc + tot > kCandW) {
+        over = true;
+        break;
+      }
+      int q2 = wc + __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (abs_key(e[h][k]) > Gk) {
+          wv[q2] = e[h][k];
+          wi[q2] = i0 + k;
+          ++q2;
+        }
+      }
+      wc += tot;
     }
   }
-  if (threadIdx.x == 0) fail_s = 0;
+  if (threadIdx.x == 0) {
+    fail_s = 0;
+    raised_s = 0;
+  }
   __syncthreads();
   if (lane == 0 && over) fail_s = 1;
+  if (lane == 0 && Gk != __float_as_uint(q.Glo)) raised_s = 1;   // this warp went on with G_hi
   int d0 = 0, d1 = 0;
-  block_sum2f(f1, f2, d0, d1, sh);   // (its barriers also publish fail_s)
+  block_sum2f(f1, f2, d0, d1, sh);   // (its barriers also publish fail_s and raised_s)
   if (fail_s) {
     if (threadIdx.x == 0) {
       st.xfast[c] = 0;
@@ -810,6 +872,9 @@ __global__ void __launch_bounds__(XT) k_xstep_filter(XstepArgs a_in, const float
     }
     return;
   }
+  const bool at_hi = raised_s || Ghi == __float_as_uint(q.Glo);
+  __syncwarp();
+  if (at_hi && Gk != Ghi) wc = warp_compact_above(wv, wi, wc, Ghi);   // every warp on one guess
   const int ncand = warp_offsets(lane == 0 ? wc : 0, sh);
   const int off = sh.woff[w];
   float *gv = cand_val + (int64_t)c * kCand;
@@ -821,11 +886,13 @@ __global__ void __launch_bounds__(XT) k_xstep_filter(XstepArgs a_in, const float
   const int nnz_old = st.nnz[c];
   const int *old = sup_idx + (int64_t)c * q.a.cap;
   for (int t = threadIdx.x; t < nnz_old; t += XT) x[old[t]] = 0.0f;
-  if (threadIdx.x == 0) meta[c] = make_int4(ncand, __float_as_int(f1), __float_as_int(f2), 1);
+  if (threadIdx.x == 0)
+    meta[c] = make_int4(ncand, __float_as_int(f1), __float_as_int(f2), at_hi ? kMetaHi : kMetaLo);
 }
 
-// Operator: a warp per start on the filter's candidates (staged in the warp's shared memory),
-// with the check that G lies below the operator's threshold; then the new x, F and support.
+// Operator: a warp per start on the filter's candidates (staged in the warp's shared memory).
+// A list above G_lo is first cut to the entries above G_hi when G_hi is valid; then the operator,
+// with the check that the guess lies below the operator's threshold, the new x, F and support.
 constexpr int kOpWarps = 4;
 __global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int r, float *__restrict__ X,
                                                             int64_t ldx, StartState st, int *__restrict__ sup_idx,
@@ -844,10 +911,8 @@ __global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int 
   const CandPlan q = cand_plan(a_in, st, c, true);
   const XstepArgs &a = q.a;
   const int form = a.form, s_int = q.s_int;
-  const int ncand = m.x;
+  int ncand = m.x;
   const float f1 = __int_as_float(m.y), f2 = __int_as_float(m.z);
-  const float G = q.G;
-  const uint32_t Gk = __float_as_uint(G);
   float *cval = cval_s[w];
   int *cidx = cidx_s[w];
   for (int t = lane; t < ncand; t += 32) {
@@ -855,6 +920,37 @@ __global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int 
     cidx[t] = cand_idx[(int64_t)c * kCand + t];
   }
   __syncwarp();
+  // phi(G) < 0 over the candidates above G (all of v's entries above G when the list holds them)
+  auto phi_below = [&](float G, int len) {
+    const uint32_t Gk = __float_as_uint(G);
+    float sw = 0.0f, sw2 = 0.0f;
+    for (int i = lane; i < len; i += 32) {
+      const float av = fabsf(cval[i]);
+      if (__float_as_uint(av) > Gk) {
+        const float wv2 = av - G;
+        sw += wv2;
+        sw2 = fmaf(wv2, wv2, sw2);
+      }
+    }
+    sw = warp_sum_f(sw);
+    sw2 = warp_sum_f(sw2);
+    return (float)a.s * sw2 - sw * sw < 0.0f;
+  };
+  float G = q.G;
+  if (m.w == kMetaLo) {   // the list holds the entries above G_lo: cut it to G_hi if G_hi is valid
+    const uint32_t Ghi = __float_as_uint(q.G);
+    bool hi_ok;
+    if (uses_lam(form)) {
+      hi_ok = phi_below(q.G, ncand);
+    } else {
+      int n_hi = 0;
+      for (int i = lane; i < ncand; i += 32) n_hi += abs_key(cval[i]) > Ghi ? 1 : 0;
+      hi_ok = warp_sum_i(n_hi) >= q.need;
+    }
+    if (hi_ok) ncand = warp_compact_above(cval, cidx, ncand, Ghi);
+    else G = q.Glo;
+  }
+  const uint32_t Gk = __float_as_uint(G);
   float *x = X + (int64_t)c * ldx;
   XOp op;
   bool ok = ncand >= q.need;
@@ -872,28 +968,17 @@ __global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int 
   } else if (ok && uses_lam(form)) {
     // lambda = 0 (phi(0) >= 0) keeps every entry: left to the full pass
     ok = (float)a.s * f2 - f1 * f1 < 0.0f;
+    if (ok) ok = phi_below(G, ncand);   // phi(G) < 0: lambda_s > G
     if (ok) {
-      float sw = 0.0f, sw2 = 0.0f;
       unsigned mk = 0u;
-      for (int i = lane; i < ncand; i += 32) {
-        const float av = fabsf(cval[i]);
-        const float wv2 = av - G;
-        sw += wv2;
-        sw2 = fmaf(wv2, wv2, sw2);
-        mk = max(mk, __float_as_uint(av));
-      }
-      sw = warp_sum_f(sw);
-      sw2 = warp_sum_f(sw2);
+      for (int i = lane; i < ncand; i += 32) mk = max(mk, abs_key(cval[i]));
       mk = warp_max_u(mk);
-      ok = (float)a.s * sw2 - sw * sw < 0.0f;   // phi(G) < 0: lambda_s > G
-      if (ok) {
-        uint32_t lok;
-        op.mode = 2;
-        op.gam = warp_lambda_s(cval, ncand, a.s, Gk, mk, &lok);
-        op.tkey = lok;
-        op.tval = (float)op.gam;
-        op.tnext = op.tval;
-      }
+      uint32_t lok;
+      op.mode = 2;
+      op.gam = warp_lambda_s(cval, ncand, a.s, Gk, mk, &lok);
+      op.tkey = lok;
+      op.tval = (float)op.gam;
+      op.tnext = op.tval;
     }
   } else if (ok) {  // penalties
     op.mode = uses_U(form) ? 1 : 2;

@@ -227,6 +227,52 @@ def test_single_sweep_parity(lib, oracle, spiked, form, engine):
 
 
 @pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("s", [12, 60])
+@pytest.mark.parametrize("form", range(1, 9))
+def test_single_sweep_parity_candidate_xstep(lib, oracle, form, s, engine):
+    """The same single-sweep check with p = 6000, where every sweep after the first takes the
+    candidate x-step: the filter keeps the entries above a guess from last sweep's threshold
+    (0.6 or 0.85 of it; a fixed penalty threshold exactly) and the operator runs on those.  The
+    early sweeps, where the threshold can fall by more than 15%, need the lower guess; s = 60
+    fills the per-warp lists (64 entries over 384 indices) so that warps move to the higher one.
+    Whatever path a start takes, the sweep must equal the FP64 oracle's sweep from the same x."""
+    n, p, r, C = 300, 6000, 40, 5
+    A = I.spiked_matrix(n, p, I.spiked_thetas(n, p), 12, 21, dtype=np.float32)
+    A64 = A.astype(np.float64)
+    G = I.raw_starts(p, r, 22).astype(np.float32)
+    kw = _kw(form, float(s) if form in (3, 4) else s, 0.0, True)
+    if form >= 5:
+        kw["calib"] = C
+    h = lib.Handle(A)
+    checked = 0
+    for k in (1, 2, 3, 5, 12):
+        o = h.solve(form, r, max_iter=k, tol=-1, x0=G, want_starts=True, engine=_engine(lib, engine), **kw)
+        Xk, stat = o["start_x"].astype(np.float64), o["start_status"]
+        o1 = h.solve(form, r, max_iter=k + 1, tol=-1, x0=G, want_starts=True, engine=_engine(lib, engine), **kw)
+        for c in range(r):
+            if stat[c] == lib.SPCA_ST_DEGENERATE or o1["start_status"][c] == lib.SPCA_ST_DEGENERATE:
+                continue
+            okw = dict(kw)
+            if form >= 5 and k + 1 > C:
+                okw = dict(gamma=float(o1["start_gamma"][c]))
+            elif form >= 5:
+                okw["calib"] = 1
+            ref = oracle.solve(A64, form, Xk[c:c + 1], max_iter=1, tol=-1, **okw)
+            fixed_gamma = okw["gamma"] if (form >= 5 and not okw.get("gamma_target")) else None
+            if _near_tie(A64, form, Xk[c], s, fixed_gamma):
+                continue
+            scaleF = abs(ref.F[0]) + (ref.gamma[0] * np.count_nonzero(ref.X[0]) if form in (5, 6) else 0.0)
+            assert abs(o1["start_F"][c] - ref.F[0]) <= OBJ_RTOL * max(1.0, scaleF), (k, c)
+            err = np.abs(o1["start_x"][c] - ref.X[0]).max()
+            assert err <= X_ATOL, (form, k, c, err)
+            if form in (1, 2, 5, 6):   # hard selections away from ties: the same support
+                assert np.array_equal(o1["start_x"][c] != 0, ref.X[0] != 0), (k, c)
+            checked += 1
+    h.close()
+    assert checked >= 0.8 * 5 * r
+
+
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("form", [1, 4, 5, 8])
 def test_spiked_stopping_rule(lib, oracle, spiked, form, engine):
     A = spiked
