@@ -467,10 +467,12 @@ cudaError_t launch_gemm_nt_f32(const float *P, int64_t ldp, const float *Q, int6
 // ------------------------------------------------------------------ u = A x over supp(x)
 // U[c, i] = sum_t val[c, t] AT[idx[c, t], i] (t over the support of x, ascending index).
 // Runs only when *gate != 0 (the control word chose this path for the sweep).
-// Grid: x over the starts, y over the row blocks, so the CTAs in flight share a row block: its
-// slice of every column in the starts' supports (1024 rows x 4 bytes each; 72 MB for 18,000
-// distinct columns) stays in L2, and a column used by several starts is read from DRAM once.
-__global__ void __launch_bounds__(256) k_gemm1_sparse(const float *__restrict__ AT, int64_t ldat,
+// Grid: x over the starts, y over row blocks of 512 (128 threads), so the CTAs in flight share a
+// few row blocks: their slices of the columns in the starts' supports (512 rows x 4 bytes each;
+// 37 MB per row block for 18,000 distinct columns) stay in L2, and a column used by several
+// starts is read from DRAM about once.
+constexpr int kGatherThreads = 128;
+__global__ void __launch_bounds__(kGatherThreads) k_gemm1_sparse(const float *__restrict__ AT, int64_t ldat,
                                                       int n, const int *__restrict__ sup_idx,
                                                       const float *__restrict__ sup_val, int cap,
                                                       StartState s, float *__restrict__ U,
@@ -479,13 +481,13 @@ __global__ void __launch_bounds__(256) k_gemm1_sparse(const float *__restrict__ 
   const int c = blockIdx.x;
   if (s.status[c] != ST_ACTIVE) return;
   if (s.iters[c] == 0) return;   // a start not swept yet has a dense x: the dense contraction
-  __shared__ int sidx[256];
-  __shared__ float sval[256];
+  __shared__ int sidx[kGatherThreads];
+  __shared__ float sval[kGatherThreads];
   const int nnz = s.nnz[c];
   // four consecutive rows per thread, read as one 16-byte vector (ldat is a multiple of 8, so
   // the rows up to the padded width are in bounds); eight columns' loads are issued before
   // their FMAs, which still run in support order
-  const int i4 = (blockIdx.y * blockDim.x + threadIdx.x) * 4;
+  const int i4 = (blockIdx.y * kGatherThreads + threadIdx.x) * 4;
   const int *gi = sup_idx + (int64_t)c * cap;
   const float *gv = sup_val + (int64_t)c * cap;
   float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -495,14 +497,14 @@ __global__ void __launch_bounds__(256) k_gemm1_sparse(const float *__restrict__ 
     acc.z = fmaf(xv, a.z, acc.z);
     acc.w = fmaf(xv, a.w, acc.w);
   };
-  for (int t0 = 0; t0 < nnz; t0 += 256) {
+  for (int t0 = 0; t0 < nnz; t0 += kGatherThreads) {
     __syncthreads();
     if (t0 + (int)threadIdx.x < nnz) {
       sidx[threadIdx.x] = gi[t0 + threadIdx.x];
       sval[threadIdx.x] = gv[t0 + threadIdx.x];
     }
     __syncthreads();
-    const int m = min(256, nnz - t0);
+    const int m = min(kGatherThreads, nnz - t0);
     if (i4 < n) {
       const float *base = AT + i4;
       int t = 0;
@@ -666,8 +668,10 @@ cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int 
                                 const float *sup_val, int cap, StartState s, int r, float *U,
                                 int64_t ldu, const int *gate, cudaStream_t st) {
   if (ldat % 4 != 0 || (reinterpret_cast<uintptr_t>(AT) & 15u) != 0) return cudaErrorInvalidValue;
-  dim3 grid((unsigned)r, (unsigned)((n + 1023) / 1024));
-  k_gemm1_sparse<<<grid, 256, 0, st>>>(AT, ldat, n, sup_idx, sup_val, cap, s, U, ldu, gate);
+  const int blocks = (n + 4 * kGatherThreads - 1) / (4 * kGatherThreads);
+  if (blocks > 65535) return cudaErrorInvalidValue;   // grid y limit: n above 33.5 million rows
+  dim3 grid((unsigned)r, (unsigned)blocks);
+  k_gemm1_sparse<<<grid, kGatherThreads, 0, st>>>(AT, ldat, n, sup_idx, sup_val, cap, s, U, ldu, gate);
   return cudaGetLastError();
 }
 
