@@ -13,8 +13,10 @@ namespace {
 constexpr int FT = 256;
 }
 
-// grid (ceil(n / FT), r): u_i = sum_t x_{j_t} A[i, j_t] over the support (compensated FP32
+// grid (r, ceil(n / FT)): u_i = sum_t x_{j_t} A[i, j_t] over the support (compensated FP32
 // pairs); per-CTA FP64 partial sums of |u_i| and u_i^2 go to partials (fixed order later).
+// Starts on x, row chunks on y: the CTAs in flight share row chunks, so a column slice used by
+// several starts' supports is read from DRAM about once.
 __global__ void __launch_bounds__(FT) k_fin_partial(const float *__restrict__ AT, int64_t ldat, int n,
                                                     const int *__restrict__ sup_idx,
                                                     const float *__restrict__ sup_val, int cap,
@@ -23,8 +25,8 @@ __global__ void __launch_bounds__(FT) k_fin_partial(const float *__restrict__ AT
   __shared__ int sidx[FT];
   __shared__ float sval[FT];
   __shared__ double red[32];
-  const int c = blockIdx.y;
-  const int i = blockIdx.x * FT + threadIdx.x;
+  const int c = blockIdx.x;
+  const int i = blockIdx.y * FT + threadIdx.x;
   const int nnz = st.nnz[c];
   const int *gi = sup_idx + (int64_t)c * cap;
   const float *gv = sup_val + (int64_t)c * cap;
@@ -45,7 +47,7 @@ __global__ void __launch_bounds__(FT) k_fin_partial(const float *__restrict__ AT
   const double l1 = block_sum_d(i < n ? fabs(acc) : 0.0, red);
   const double l2 = block_sum_d(i < n ? acc * acc : 0.0, red);
   if (threadIdx.x == 0) {
-    double *o = partials + ((int64_t)c * gridDim.x + blockIdx.x) * 2;
+    double *o = partials + ((int64_t)c * gridDim.y + blockIdx.y) * 2;
     o[0] = l1;
     o[1] = l2;
   }
@@ -87,7 +89,8 @@ cudaError_t launch_finalise(int form, const float *AT, int64_t ldat, int n, int 
                             cudaStream_t st) {
   (void)p; (void)X; (void)ldX;
   const int nchunks = (n + FT - 1) / FT;
-  k_fin_partial<<<dim3((unsigned)nchunks, (unsigned)r), FT, 0, st>>>(AT, ldat, n, sup_idx, sup_val,
+  if (nchunks > 65535) return cudaErrorInvalidValue;   // grid y limit: n above 16.7 million rows
+  k_fin_partial<<<dim3((unsigned)r, (unsigned)nchunks), FT, 0, st>>>(AT, ldat, n, sup_idx, sup_val,
                                                                       cap, s, U, ldu, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -684,9 +684,10 @@ __device__ void xstep_finish_warp(const XstepArgs &a, int c, const float *vv, in
 // while every warp's list has room, and above G_hi = kGuess t otherwise (a warp whose list would
 // overflow drops its entries at or below G_hi and goes on with G_hi; then every warp does).  The
 // operator takes G_hi when it is valid (fewer candidates) and G_lo otherwise: early sweeps, where
-// the threshold can fall by more than a few per cent, then still avoid the full pass.  A penalty
-// with its threshold fixed uses that threshold alone (exact).  When no guess is valid, or a list
-// overflows at G_hi, the start is left to k_xstep (xfast[c] = 0).
+// the threshold can fall by more than a few per cent, then still avoid the full pass.  A start
+// whose last sweep took G_hi filters with G_hi alone.  A penalty with its threshold fixed uses
+// that threshold alone (exact).  When no guess is valid, or a list overflows at G_hi, the start is
+// left to k_xstep (xfast[c] = 0; otherwise 1 for G_hi, 2 for G_lo).
 constexpr int kCandW = 64;               // candidates per warp
 constexpr int kCand = kCandW * XW;       // per start
 static_assert(kCand == kXstepCand, "candidate scratch size");
@@ -714,9 +715,11 @@ __device__ __forceinline__ CandPlan cand_plan(const XstepArgs &a_in, const Start
     q.G = q.a.per_start_thr ? st.thr[c] : q.a.thr_fixed;
     q.Glo = q.G;
   } else {
+    // one guess while the threshold holds steady (last sweep accepted G_hi: xfast == 1), two
+    // otherwise (the first sweeps, and after a G_lo or a full pass)
     const float t = st.tprev[c];
     q.G = kGuess * t;
-    q.Glo = kGuessLo * t;
+    q.Glo = st.xfast[c] == 1 ? q.G : kGuessLo * t;
   }
   q.need = uses_T(form) ? q.s_int : (is_pen(form) && q.a.calibrate ? q.s_int + 1 : 1);
   // x is zero outside the last x-step's support list, so only that list is cleared; after the
@@ -760,7 +763,9 @@ __device__ __forceinline__ int warp_compact_above(float *val, int *idx, int len,
 // warp order (the candidates in index order) into cand_val / cand_idx (kCand per start), with the
 // sums of |v| and v^2 (lambda forms) and the count in meta[c]; x is cleared on the last support.
 // A start the filter cannot serve gets xfast[c] = 0 and meta[c].w = 0.
-__global__ void __launch_bounds__(XT) k_xstep_filter(XstepArgs a_in, const float *__restrict__ V, int64_t ldv,
+constexpr int kFilterChunks = 4;      // 128-entry chunks per warp and step, loaded before use
+constexpr int kFilterMinBlocks = 2;   // resident CTAs per SM the register budget is set for
+__global__ void __launch_bounds__(XT, kFilterMinBlocks) k_xstep_filter(XstepArgs a_in, const float *__restrict__ V, int64_t ldv,
                                                      float *__restrict__ X, int64_t ldx, StartState st,
                                                      const int *__restrict__ sup_idx, float *__restrict__ cand_val,
                                                      int *__restrict__ cand_idx, int4 *__restrict__ meta) {
@@ -785,7 +790,7 @@ __global__ void __launch_bounds__(XT) k_xstep_filter(XstepArgs a_in, const float
   const uint32_t Ghi = __float_as_uint(q.G);
   uint32_t Gk = __float_as_uint(q.Glo);   // the warp's current guess (warp-uniform)
   bool raised = Gk == Ghi;
-  // four 128-entry chunks per step, their loads issued before any is used
+  // kFilterChunks 128-entry chunks per step, their loads issued before any is used
   const float *vg = V + (int64_t)c * ldv;
   float *x = X + (int64_t)c * ldx;
   const int seg = ((p + XW - 1) / XW + 127) / 128 * 128;
@@ -795,11 +800,11 @@ __global__ void __launch_bounds__(XT) k_xstep_filter(XstepArgs a_in, const float
   int wc = 0;
   bool over = false;
   float f1 = 0.0f, f2 = 0.0f;
-  for (int base = lo; base < hi && !over; base += 512) {
-    float e[4][4];
-    const bool full = base + 512 <= hi;
+  for (int base = lo; base < hi && !over; base += 128 * kFilterChunks) {
+    float e[kFilterChunks][4];
+    const bool full = base + 128 * kFilterChunks <= hi;
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
+    for (int h = 0; h < kFilterChunks; ++h) {
       const int i0 = base + h * 128 + 4 * lane;
       if (full || i0 + 3 < hi) {
         const float4 t = *reinterpret_cast<const float4 *>(vg + i0);
@@ -810,7 +815,7 @@ __global__ void __launch_bounds__(XT) k_xstep_filter(XstepArgs a_in, const float
       }
     }
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
+    for (int h = 0; h < kFilterChunks; ++h) {
       const int i0 = base + h * 128 + 4 * lane;
       if (sums) {
 #pragma unroll
@@ -1007,7 +1012,7 @@ __global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int 
     return;
   }
   xstep_finish_warp(a, c, cval, ncand, cidx, op, x, st, sup_idx, sup_val, ctrl);
-  if (lane == 0) st.xfast[c] = 1;
+  if (lane == 0) st.xfast[c] = G == q.G ? 1 : 2;   // the guess taken (a fixed threshold counts as 1)
 }
 }  // namespace
 

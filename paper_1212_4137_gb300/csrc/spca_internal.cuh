@@ -67,7 +67,7 @@ struct StartState {
   double *ev;       // explained variance (finalise)
   float *tprev;     // last sweep's x-step threshold in |v| units (0: none); seeds the
                     // candidate filter of the next x-step
-  int *xfast;       // 1 when the candidate x-step finished the start in this sweep
+  int *xfast;       // nonzero when the candidate x-step finished the start in this sweep (its guess)
 };
 
 struct XstepArgs {
