@@ -693,6 +693,7 @@ constexpr int kCand = kCandW * XW;       // per start
 static_assert(kCand == kXstepCand, "candidate scratch size");
 constexpr float kGuess = 0.85f;
 constexpr float kGuessLo = 0.6f;
+constexpr float kSteady = 0.05f;         // |t_new / t - 1| below this: one guess next sweep
 constexpr int kCandMinP = 4096;          // shorter v: the full pass only
 constexpr int kMetaHi = 1, kMetaLo = 2;  // meta[c].w: the list holds the entries above G_hi / G_lo
 
@@ -700,7 +701,7 @@ constexpr int kMetaHi = 1, kMetaLo = 2;  // meta[c].w: the list holds the entrie
 // itself), the number of candidates the operator needs, and whether the filter applies at all
 struct CandPlan {
   XstepArgs a;
-  float G, Glo;
+  float G, Glo, t;
   bool exact, usable;
   int need, s_int;
 };
@@ -714,10 +715,13 @@ __device__ __forceinline__ CandPlan cand_plan(const XstepArgs &a_in, const Start
     q.exact = true;
     q.G = q.a.per_start_thr ? st.thr[c] : q.a.thr_fixed;
     q.Glo = q.G;
+    q.t = q.G;
   } else {
-    // one guess while the threshold holds steady (last sweep accepted G_hi: xfast == 1), two
-    // otherwise (the first sweeps, and after a G_lo or a full pass)
+    // one guess while the threshold holds steady (last sweep took G_hi and moved the threshold
+    // by less than kSteady: xfast == 1), two otherwise (the first sweeps, after a G_lo or a full
+    // pass, and while the threshold still moves)
     const float t = st.tprev[c];
+    q.t = t;
     q.G = kGuess * t;
     q.Glo = st.xfast[c] == 1 ? q.G : kGuessLo * t;
   }
@@ -1012,7 +1016,10 @@ __global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int 
     return;
   }
   xstep_finish_warp(a, c, cval, ncand, cidx, op, x, st, sup_idx, sup_val, ctrl);
-  if (lane == 0) st.xfast[c] = G == q.G ? 1 : 2;   // the guess taken (a fixed threshold counts as 1)
+  if (lane == 0) {   // 1: G_hi taken and the threshold steady (a fixed threshold counts as steady)
+    const bool steady = q.exact || (op.tnext >= (1.0f - kSteady) * q.t && op.tnext <= (1.0f + kSteady) * q.t);
+    st.xfast[c] = G == q.G && steady ? 1 : 2;
+  }
 }
 }  // namespace
 
