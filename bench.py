@@ -266,11 +266,7 @@ def run_ours(args, w, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "p": p, "r": r, "formulations": list(w["forms"]),
-                   "s": w["s"], "gamma_mode": "target_nnz (Section 4.1), 10 calibration sweeps",
-                   "max_iter": w["max_iter"], "tol": w["tol"], "storage": "fp32",
-                   "engine": "auto", "l2": "inputs larger than L2 (A = %d MB)" % (A.nbytes // 2**20),
-                   "parallelism": f"replicas x{world} (starts sharded, no collective)"},
+        "config": workload_config(args, w, world),
         "solves_per_s": round(solves_all / (ms_max / 1e3), 3),
         "solve_latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
                              "p99": round(float(np.percentile(lat_ms, 99)), 3)},
@@ -313,6 +309,17 @@ def cpu_baseline(w, A, G, starts=32, sweeps=10):
                       f"({sw} sweeps*starts in {dt:.1f} s), FP64, OpenMP over starts"}
 
 
+def workload_config(args, w, world):
+    """The `config` object of the benchmark line (the same for both arms)."""
+    a_bytes = w["n"] * w["p"] * 4
+    l2 = ("inputs larger than L2 (A = %d MB)" % (a_bytes // 2**20) if a_bytes > 129 * 2**20
+          else "A = %.1f MB stays in L2, not flushed: a resident problem's solve latency" % (a_bytes / 2**20))
+    return {"workload": args.workload, "n": w["n"], "p": w["p"], "r": w["r"], "formulations": list(w["forms"]),
+            "s": w["s"], "gamma_mode": "target_nnz (Section 4.1), %d calibration sweeps" % w["calib"],
+            "max_iter": w["max_iter"], "tol": w["tol"], "storage": "fp32", "engine": "auto", "l2": l2,
+            "parallelism": f"replicas x{world} (starts sharded, no collective)"}
+
+
 def run_reference(args, w, rank, world):
     if rank != 0:
         return None
@@ -338,7 +345,7 @@ def run_reference(args, w, rank, world):
             "warmup": args.warmup, "ms_per_step": round(1e3 * tot_dt / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "n": w["n"], "p": w["p"], "r": w["r"]},
+            "config": workload_config(args, w, world),
             "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
