@@ -21,6 +21,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -90,7 +91,9 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # the samples' file: SPCA_CLOCKS_DIR, else the system's temporary directory
+        out_dir = os.environ.get("SPCA_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"spca_clocks_rank{device_index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
