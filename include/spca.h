@@ -40,7 +40,7 @@ typedef enum {
     SPCA_E_CUDA = 3,         /* a CUDA runtime error (no device, launch failure, ...)             */
     SPCA_E_TIMEOUT = 4,      /* a bounded device-side wait gave up (reported by the kernel)       */
     SPCA_E_BUSY = 5,         /* the handle is in use                                              */
-    SPCA_E_UNSUPPORTED = 6   /* a valid request this build does not implement                     */
+    SPCA_E_UNSUPPORTED = 6   /* a valid request the library does not implement                     */
 } spca_status;
 
 /* element types */

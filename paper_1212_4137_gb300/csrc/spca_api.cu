@@ -777,7 +777,7 @@ const char *spca_strerror(int status) {
     case SPCA_E_CUDA: return "CUDA error";
     case SPCA_E_TIMEOUT: return "device-side wait timed out";
     case SPCA_E_BUSY: return "handle busy";
-    case SPCA_E_UNSUPPORTED: return "not supported by this build";
+    case SPCA_E_UNSUPPORTED: return "not supported by the library";
     default: return "unknown status";
   }
 }
