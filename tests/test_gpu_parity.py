@@ -272,6 +272,49 @@ def test_single_sweep_parity_candidate_xstep(lib, oracle, form, s, engine):
     assert checked >= 0.8 * 5 * r
 
 
+@pytest.mark.parametrize("s", [200, 600])
+@pytest.mark.parametrize("form", [1, 2, 5])
+def test_single_sweep_parity_candidate_lists_overflow(lib, oracle, form, s):
+    """Candidate lists that overflow: A ~ N(0,1) with no spike makes |v| flat.  With p = 6000 (384
+    indices per warp) and s = 200, 70-100 entries of a warp's segment lie above the lower guess
+    (room for 64), so warps move to the higher one (about 30 entries); with s = 600 the higher
+    guess overflows too for most starts (65-90 entries), which then take the full pass.  Each sweep
+    must still equal the oracle's sweep from the same x.  Flat |v| puts more selections within
+    1e-4 of a tie, so fewer start-sweeps are checked."""
+    n, p, r, C = 300, 6000, 24, 5
+    A = I.gaussian_matrix(n, p, 23).astype(np.float32)
+    A64 = A.astype(np.float64)
+    G = I.raw_starts(p, r, 24).astype(np.float32)
+    kw = _kw(form, s, 0.0, True)
+    if form >= 5:
+        kw["calib"] = C
+    h = lib.Handle(A)
+    checked = 0
+    for k in (1, 2, 4, 8):
+        o = h.solve(form, r, max_iter=k, tol=-1, x0=G, want_starts=True, engine=lib.SPCA_ENGINE_TC, **kw)
+        Xk, stat = o["start_x"].astype(np.float64), o["start_status"]
+        o1 = h.solve(form, r, max_iter=k + 1, tol=-1, x0=G, want_starts=True, engine=lib.SPCA_ENGINE_TC, **kw)
+        for c in range(r):
+            if stat[c] == lib.SPCA_ST_DEGENERATE or o1["start_status"][c] == lib.SPCA_ST_DEGENERATE:
+                continue
+            okw = dict(kw)
+            if form >= 5 and k + 1 > C:
+                okw = dict(gamma=float(o1["start_gamma"][c]))
+            elif form >= 5:
+                okw["calib"] = 1
+            ref = oracle.solve(A64, form, Xk[c:c + 1], max_iter=1, tol=-1, **okw)
+            fixed_gamma = okw["gamma"] if (form >= 5 and not okw.get("gamma_target")) else None
+            if _near_tie(A64, form, Xk[c], s, fixed_gamma):
+                continue
+            scaleF = abs(ref.F[0]) + (ref.gamma[0] * np.count_nonzero(ref.X[0]) if form in (5, 6) else 0.0)
+            assert abs(o1["start_F"][c] - ref.F[0]) <= OBJ_RTOL * max(1.0, scaleF), (k, c)
+            assert np.abs(o1["start_x"][c] - ref.X[0]).max() <= X_ATOL, (form, k, c)
+            assert np.array_equal(o1["start_x"][c] != 0, ref.X[0] != 0), (k, c)
+            checked += 1
+    h.close()
+    assert checked >= 0.3 * 4 * r
+
+
 @pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("form", [1, 4, 5, 8])
 def test_spiked_stopping_rule(lib, oracle, spiked, form, engine):
