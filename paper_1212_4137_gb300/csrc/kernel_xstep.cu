@@ -685,9 +685,10 @@ __device__ void xstep_finish_warp(const XstepArgs &a, int c, const float *vv, in
 // overflow drops its entries at or below G_hi and goes on with G_hi; then every warp does).  The
 // operator takes G_hi when it is valid (fewer candidates) and G_lo otherwise: early sweeps, where
 // the threshold can fall by more than a few per cent, then still avoid the full pass.  A start
-// whose last sweep took G_hi filters with G_hi alone.  A penalty with its threshold fixed uses
-// that threshold alone (exact).  When no guess is valid, or a list overflows at G_hi, the start is
-// left to k_xstep (xfast[c] = 0; otherwise 1 for G_hi, 2 for G_lo).
+// whose last sweep took G_hi and moved its threshold by less than kSteady filters with G_hi alone.
+// A penalty with its threshold fixed uses that threshold alone (exact).  When no guess is valid,
+// or a list overflows at G_hi, the start is left to k_xstep (xfast[c] = 0; otherwise 1 for G_hi
+// with a steady threshold, 2 for the rest).
 constexpr int kCandW = 64;               // candidates per warp
 constexpr int kCand = kCandW * XW;       // per start
 static_assert(kCand == kXstepCand, "candidate scratch size");
