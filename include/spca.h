@@ -118,7 +118,9 @@ typedef enum {
  *                its own work complete.  The handle runs its kernels on a stream of its own, so
  *                that the sweeps of a solve can be captured into CUDA graphs and replayed.
  * Errors: SPCA_E_INVALID (NULL pointers, n < 1, p < 1, lda < p, A not finite, unknown dtype),
- *         SPCA_E_UNSUPPORTED, SPCA_E_NOMEM, SPCA_E_CUDA.
+ *         SPCA_E_UNSUPPORTED (n above 16,776,960 = 65535 * 256 rows: the finalise takes a dense
+ *         A's rows in blocks of 256 on a grid dimension of at most 65535; SPCA_F64 storage;
+ *         16- or 8-bit storage without tensor cores), SPCA_E_NOMEM, SPCA_E_CUDA.
  */
 int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t lda,
                 int in_dtype, int a_is_device, int storage, void *cuda_stream);
@@ -175,7 +177,8 @@ int spca_clone(spca_handle **out, spca_handle *src, void *cuda_stream);
  *   gamma               penalty forms, SPCA_GAMMA_FIXED mode: gamma >= 0.
  *   gamma_mode          spca_gamma_mode (penalty forms only).
  *   gamma_calib_sweeps  sweeps during which gamma is re-targeted (>= 1; typical 10).
- *   r                   number of starts (>= 1).
+ *   r                   number of starts (1 .. 65535; several kernels put the starts on a
+ *                       grid dimension of at most 65535: SPCA_E_UNSUPPORTED above).
  *   max_iter            maximum sweeps per start (>= 1).
  *   tol                 stopping tolerance; a start stops after sweep k >= 2 when
  *                       F(x^(k), y^(k-1)) <= (1 + tol) F(x^(k-1), y^(k-2)), comparing only
@@ -202,8 +205,9 @@ int spca_clone(spca_handle **out, spca_handle *src, void *cuda_stream);
  *                       (in index order) in the sweep its start stops; x0 then holds
  *                       total_starts rows (the seeded start c is normal numbers c*p + j), the
  *                       start_* outputs hold total_starts entries, and max_iter bounds each
- *                       start's sweeps.  0 (or <= r) = all r starts at once.  Not combined with
- *                       lowp_sweeps (SPCA_E_UNSUPPORTED).
+ *                       start's sweeps.  0 (or <= r) = all r starts at once.  At most 65535
+ *                       (SPCA_E_UNSUPPORTED above).  Not combined with lowp_sweeps
+ *                       (SPCA_E_UNSUPPORTED).
  */
 typedef struct {
     int form;
@@ -305,7 +309,8 @@ int spca_xstep(spca_handle *h, int form, double s, double gamma, int calibrate,
  *   U       device, r x n float output u = A x (ldu >= n).
  *   V       device, r x p float output v = A^T y (ldv >= p); unspecified for a row whose
  *           u is 0 under L2 variance.
- * Errors: SPCA_E_INVALID, SPCA_E_UNSUPPORTED (engine), SPCA_E_NOMEM, SPCA_E_CUDA, SPCA_E_TIMEOUT.
+ * Errors: SPCA_E_INVALID, SPCA_E_UNSUPPORTED (engine; r above 65535), SPCA_E_NOMEM, SPCA_E_CUDA,
+ *         SPCA_E_TIMEOUT.
  */
 int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t ldx, int r,
                   float *U, int64_t ldu, float *V, int64_t ldv);
@@ -372,7 +377,8 @@ int spca_profile_query(spca_handle *h, int kernel, int64_t *launches, double *ms
  *   f, ev        device, r doubles each (outputs).
  *   cuda_stream  cudaStream_t the kernels are queued on (NULL = the legacy default stream);
  *                the call returns once they are queued.
- * Limits: r * ceil(n / 256) <= SPCA_NOALLOC_MAX_PARTIALS, else SPCA_E_INVALID and nothing runs.
+ * Limits: r <= 65535 and r * ceil(n / 256) <= SPCA_NOALLOC_MAX_PARTIALS, else SPCA_E_INVALID and
+ * nothing runs.
  * The first call on a device looks up the scratch's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.  Every call shares the
  * one scratch array: calls whose kernels overlap on the GPU (other streams, other threads)

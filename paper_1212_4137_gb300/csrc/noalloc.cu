@@ -135,6 +135,7 @@ extern "C" int spca_objective_noalloc(int form, double gamma, const float *A, in
   if (form < 1 || form > 8 || !A || !X || !f || !ev) return SPCA_E_INVALID;
   if (n < 1 || p < 1 || r < 1 || lda < p || ldx < p || n > INT32_MAX || p > INT32_MAX) return SPCA_E_INVALID;
   if (!std::isfinite(gamma) || gamma < 0.0) return SPCA_E_INVALID;
+  if (r > spca::kMaxStarts) return SPCA_E_INVALID;   // the starts ride on the grid's y dimension
   const int64_t nchunks = (n + NT - 1) / NT;
   if ((int64_t)r * nchunks > (int64_t)SPCA_NOALLOC_MAX_PARTIALS) return SPCA_E_INVALID;   // beyond the scratch
   double *partials = nullptr;

@@ -877,6 +877,7 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
   spca_handle *h = nullptr;
   if (!out || !A) return SPCA_E_INVALID;
   if (n < 1 || p < 1 || lda < p || n > INT32_MAX || p > INT32_MAX) return SPCA_E_INVALID;
+  if (n > kMaxDenseRows) return SPCA_E_UNSUPPORTED;
   if (in_dtype != SPCA_F32 && in_dtype != SPCA_F64) return SPCA_E_INVALID;
   if (storage != SPCA_F32 && storage != SPCA_BF16 && storage != SPCA_FP8_E4M3_COLSCALED) {
     if (storage == SPCA_F64) return SPCA_E_UNSUPPORTED;
@@ -1143,6 +1144,7 @@ int spca_xstep(spca_handle *h, int form, double s, double gamma, int calibrate, 
 int spca_products(spca_handle *h, int form, int engine, const float *X, int64_t ldx, int r, float *U,
                   int64_t ldu, float *V, int64_t ldv) {
   if (!h || !X || !U || !V || r < 1) return fail(h, SPCA_E_INVALID, "bad argument%s");
+  if (r > kMaxStarts) return fail(h, SPCA_E_UNSUPPORTED, "more than 65535 rows%s");
   if (form < 1 || form > 8) return fail(h, SPCA_E_INVALID, "form must be 1..8%s");
   if (ldx < h->p || ldv < h->p || ldu < h->n) return fail(h, SPCA_E_INVALID, "leading dimension too small%s");
   const bool lowp = engine == SPCA_ENGINE_TC_LOWP;
@@ -1187,6 +1189,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     return fail(h, SPCA_E_UNSUPPORTED, "low-precision sweeps need the tensor-core engine%s");
   // on-the-fly replacement: l starts through the r slots
   const int l = P.total_starts > P.r ? P.total_starts : P.r;
+  if (l > kMaxStarts) return fail(h, SPCA_E_UNSUPPORTED, "more than 65535 starts%s");
   const bool otf = l > P.r;
   if (otf && P.lowp_sweeps > 0)
     return fail(h, SPCA_E_UNSUPPORTED, "low-precision sweeps with on-the-fly replacement%s");

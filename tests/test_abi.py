@@ -93,6 +93,17 @@ def test_bad_arguments_rejected_before_device(lib):
     assert st == lib.SPCA_E_UNSUPPORTED     # FP64 storage is not built
     st = so.spca_create(ctypes.byref(h), ctypes.c_void_p(A.ctypes.data), 2, 3, 3, 0, 0, 9, None)
     assert st == lib.SPCA_E_INVALID
+    # a dense A's rows ride on a grid dimension in blocks of 256 (at most 65535 blocks); A is not read
+    st = so.spca_create(ctypes.byref(h), ctypes.c_void_p(A.ctypes.data), 65535 * 256 + 1, 1, 1, 0, 0, 0, None)
+    assert st == lib.SPCA_E_UNSUPPORTED
+    f = np.zeros(4)
+    so.spca_objective_noalloc.restype = ctypes.c_int
+    for r, want in ((65536, lib.SPCA_E_INVALID), (0, lib.SPCA_E_INVALID)):
+        st = so.spca_objective_noalloc(1, ctypes.c_double(0.0), ctypes.c_void_p(A.ctypes.data), ctypes.c_int64(2),
+                                       ctypes.c_int64(3), ctypes.c_int64(3), ctypes.c_void_p(A.ctypes.data),
+                                       ctypes.c_int64(3), r, ctypes.c_void_p(f.ctypes.data),
+                                       ctypes.c_void_p(f.ctypes.data), None)
+        assert st == want, r
     assert so.spca_solve(None, None, None, None) == lib.SPCA_E_INVALID
     assert so.spca_profile_enable(None, 1) == lib.SPCA_E_INVALID
     so.spca_destroy(None)
