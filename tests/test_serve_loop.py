@@ -94,3 +94,17 @@ def test_errors_reach_the_future():
     s.close()
     with pytest.raises(RuntimeError):
         s.submit("a", 1, 4)
+
+
+def test_registration_and_configuration_errors():
+    with pytest.raises(ValueError):
+        _server(workers=0)
+    with _server(workers=1, budget_bytes=1 << 30) as s:
+        s.register("a", (10, 20))
+        with pytest.raises(ValueError):
+            s.register("a", (10, 20))
+        futs = [s.submit("a", 1, 4, tag=i) for i in range(5)]
+        s.drain()                               # returns only when every queued request is done
+        assert all(f.done() for f in futs)
+        assert [f.result()["tag"] for f in futs] == list(range(5))
+    assert FakeHandle.live == 0
