@@ -13,6 +13,9 @@ Metric: AM sweeps x starts per second (the sum over solves of the sweeps each st
 with solves/s and the p50/p99 latency of single solves.  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
+  python bench.py --scan paper-shapes|text-corpus|few-starts|precision|many-problems|serving
+(the scans print one JSON line per case; the clocks sampled during a run go to SPCA_CLOCKS_DIR,
+else the temporary directory)
 """
 from __future__ import annotations
 
