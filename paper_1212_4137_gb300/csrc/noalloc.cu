@@ -8,9 +8,9 @@
 // device memory; this entry point adds nothing to the device heap.
 //
 // The computation is the one spca_solve reports per start (u = A x with FP64 products and sums,
-// then f(x) of Table 1 and ||Ax||_2^2 or ||Ax||_1), done by a variant of the finalisation
-// kernels whose per-(start, row chunk) partial sums live in a file-scope __device__ array
-// instead of handle memory.
+// then the objective of the formulation and ||Ax||_2^2 or ||Ax||_1), done by a variant of the
+// finalisation kernels whose per-(start, row chunk) partial sums live in a file-scope
+// __device__ array instead of handle memory.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -23,15 +23,21 @@
 namespace spca {
 namespace {
 
-constexpr int NT = 256;                 // rows of A per CTA (one row per thread)
+constexpr int NT = 256;                 // rows of A per CTA (a chunk), and threads per CTA
+constexpr int NW = NT / 32;             // warps per CTA; warp w takes rows w, w + NW, ... of the chunk
+constexpr int RPW = NT / NW;            // rows per warp (32)
 constexpr int XCHUNK = 1024;            // nonzeros of x staged in shared memory at a time
 
 // the scratch: (r * ceil(n / 256)) pairs of doubles, at most SPCA_NOALLOC_MAX_PARTIALS pairs.
 // Every GPU that loads the library holds these 4 MiB until the process exits.
 __device__ __align__(256) double g_partials[2 * SPCA_NOALLOC_MAX_PARTIALS];
 
-// grid (nchunks, r): u_i = sum_j x_j A[i, j] over the nonzeros of x (ascending j), products
-// and sums in FP64; this CTA's sums of |u_i| and u_i^2 go to partials[(c * nchunks + b) * 2]
+// grid (nchunks, r): u_i = sum_j x_j A[i, j] over the nonzeros of x, products and sums in FP64,
+// for the 256 rows of chunk b; this CTA's sums of |u_i| and u_i^2 go to
+// partials[(c * nchunks + b) * 2].  A warp owns 32 rows; for each row its lanes walk the staged
+// nonzeros of x together (lane t reads column sj[t], and the staged columns ascend, so a warp's
+// loads of one row are contiguous when x is dense), each lane keeping one FP64 sum per row that
+// the warp adds up in a fixed order at the end.
 __global__ void __launch_bounds__(NT) k_obj_partial(const float *__restrict__ A, int64_t lda, int n, int p,
                                                     const float *__restrict__ X, int64_t ldx,
                                                     double *__restrict__ partials) {
@@ -40,10 +46,12 @@ __global__ void __launch_bounds__(NT) k_obj_partial(const float *__restrict__ A,
   __shared__ int red_i[32];
   __shared__ double red[32];
   const int c = blockIdx.y;
-  const int i = blockIdx.x * NT + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int row0 = blockIdx.x * NT;
   const float *x = X + (int64_t)c * ldx;
-  const float *arow = A + (int64_t)(i < n ? i : 0) * lda;
-  double acc = 0.0;
+  double acc[RPW];
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) acc[k] = 0.0;
   // walk x in chunks of NT entries; stage its nonzeros (in index order) and use them
   int staged = 0;
   for (int base = 0; base < p; base += NT) {
@@ -59,14 +67,31 @@ __global__ void __launch_bounds__(NT) k_obj_partial(const float *__restrict__ A,
     // flush when the staging buffer could overflow on the next chunk, or at the end
     if (staged > XCHUNK - NT || base + NT >= p) {
       __syncthreads();
-      if (i < n)
-        for (int t = 0; t < staged; ++t) acc = fma((double)sx[t], (double)arow[sj[t]], acc);
+#pragma unroll
+      for (int k = 0; k < RPW; ++k) {
+        const int i = row0 + w + k * NW;
+        if (i < n) {
+          const float *arow = A + (int64_t)i * lda;
+          for (int t = lane; t < staged; t += 32) acc[k] = fma((double)sx[t], (double)arow[sj[t]], acc[k]);
+        }
+      }
       __syncthreads();
       staged = 0;
     }
   }
-  const double l1 = block_sum_d(i < n ? fabs(acc) : 0.0, red);
-  const double l2 = block_sum_d(i < n ? acc * acc : 0.0, red);
+  // u_i for the warp's rows (lane sums added in a fixed order), then |u_i| and u_i^2
+  double l1 = 0.0, l2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const double u = warp_sum_d(acc[k]);
+    if (row0 + w + k * NW < n) {
+      l1 += fabs(u);
+      l2 += u * u;
+    }
+  }
+  // every lane holds the warp's sums: lane 0 of each warp contributes them
+  l1 = block_sum_d(lane == 0 ? l1 : 0.0, red);
+  l2 = block_sum_d(lane == 0 ? l2 : 0.0, red);
   if (threadIdx.x == 0) {
     double *o = partials + ((int64_t)c * gridDim.x + blockIdx.x) * 2;
     o[0] = l1;
@@ -74,7 +99,7 @@ __global__ void __launch_bounds__(NT) k_obj_partial(const float *__restrict__ A,
   }
 }
 
-// one thread per start: the partials in chunk order, ||x||_0, ||x||_1, then Table 1
+// one thread per start: the partials in chunk order, ||x||_0, ||x||_1, then the objective
 __global__ void __launch_bounds__(NT) k_obj_reduce(int form, double gamma, const double *__restrict__ partials,
                                                    int nchunks, const float *__restrict__ X, int64_t ldx, int p,
                                                    int r, double *__restrict__ f, double *__restrict__ ev) {
@@ -135,7 +160,7 @@ extern "C" int spca_objective_noalloc(int form, double gamma, const float *A, in
   if (form < 1 || form > 8 || !A || !X || !f || !ev) return SPCA_E_INVALID;
   if (n < 1 || p < 1 || r < 1 || lda < p || ldx < p || n > INT32_MAX || p > INT32_MAX) return SPCA_E_INVALID;
   if (!std::isfinite(gamma) || gamma < 0.0) return SPCA_E_INVALID;
-  if (r > spca::kMaxStarts) return SPCA_E_INVALID;   // the starts ride on the grid's y dimension
+  if (r > spca::kMaxStarts) return SPCA_E_UNSUPPORTED;   // the starts ride on the grid's y dimension
   const int64_t nchunks = (n + NT - 1) / NT;
   if ((int64_t)r * nchunks > (int64_t)SPCA_NOALLOC_MAX_PARTIALS) return SPCA_E_INVALID;   // beyond the scratch
   double *partials = nullptr;
