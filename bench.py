@@ -48,10 +48,10 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "spiked-5000x20000-r1024"
 
 # DRAM traffic of one v = A^T y launch of the tensor-core contraction at the spiked workload's size
-# with 1024 active starts (dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture: 481.8 MB
-# + 83.1 MB), and the algorithmic bytes of that launch: two FP16 planes of A^T (400 MB), two of Y
+# with 1024 active starts (dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture: 473.5 MB
+# + 83.0 MB), and the algorithmic bytes of that launch: two FP16 planes of A^T (400 MB), two of Y
 # (20.5 MB), V written once (81.9 MB)
-V_TRAFFIC_BYTES = 564.9e6
+V_TRAFFIC_BYTES = 556.5e6
 V_ALG_BYTES = 502.4e6
 
 # peak of the FP32 CUDA-core pipe: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.070 GHz
@@ -158,7 +158,7 @@ def run_ours(args, w, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     h = spca.Handle(Ad, stream=stream.cuda_stream)
 
-    vstats = {"launches": 0, "ms": 0.0, "tensor_flop": 0.0}
+    vstats = {"launches": 0, "ms": 0.0, "tensor_flop": 0.0, "method_flop": 0.0}
 
     def one_step(times=None):
         sw = 0
@@ -177,6 +177,7 @@ def run_ours(args, w, rank, world, local_rank):
                 vstats["launches"] += l1 - l0
                 vstats["ms"] += m1 - m0
                 vstats["tensor_flop"] += out["sweeps_total"] * 2.0 * n * p * (2 if form % 2 == 0 else 3)
+                vstats["method_flop"] += out["sweeps_total"] * 2.0 * n * p
             sw += out["sweeps_total"]
         return sw
 
@@ -215,7 +216,7 @@ def run_ours(args, w, rank, world, local_rank):
     value = sweeps_all / (ms_max / 1e3)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 3))
+    e2e_steps = 0 if args.no_e2e else args.steps   # the same number of steps as the device-timed value
     if e2e_steps:
         A_pin = torch.from_numpy(A).pin_memory()
         G_pin = torch.from_numpy(G).pin_memory()
@@ -246,21 +247,25 @@ def run_ours(args, w, rank, world, local_rank):
     peaks = load_peaks()
     roof = None
     if dom == "v" and vstats["ms"] > 0:
-        achieved = vstats["tensor_flop"] / (vstats["ms"] / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        alg = 2.0 * n * p * sweeps / (vstats["ms"] / 1e3) / 1e12
-        roof = {"kernel": "v = A^T y (k_gemm_tc2: tcgen05 FP16 x2-plane, FP32 accumulate)", "bound": "tensor",
-                "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
-                "frac": round(achieved / peak, 4),
+        # the method's work (2 n p flop per sweep*start: every entry of v = A^T y of every active
+        # start) over the measured launch time of v; the executed plane products beside it
+        method = vstats["method_flop"] / (vstats["ms"] / 1e3) / 1e12
+        executed = vstats["tensor_flop"] / (vstats["ms"] / 1e3) / 1e12
+        roof = {"kernel": "v = A^T y (k_gemm_tc2: tcgen05 on FP16 planes, FP32 accumulate)", "bound": "tensor",
+                "achieved": round(method, 1), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(method / peak, 4),
+                "per_unit": "2*n*p flop per sweep*start (active starts only): the algorithmic work of v = A^T y",
+                "units_per_launch": "the active starts of one sweep",
+                "executed_plane_tflops": round(executed, 1), "executed_plane_frac": round(executed / peak, 4),
+                "executed_per_unit": "2*n*p*(2 plane products for L1 variance, 3 for L2 variance) FP16 flop",
                 # DRAM read + write of one launch from an ncu capture of this kernel (the first
                 # v = A^T y of formulation 1: N = 1024 active starts, three plane products),
                 # against its algorithmic bytes (A planes once, Y planes, V written once)
                 "traffic": V_TRAFFIC_BYTES, "traffic_note": "bytes per launch, N = 1024 launch (ncu)",
                 "algorithmic_bytes_same_launch": V_ALG_BYTES,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; FP16 and BF16 dense rates are equal)",
-                "per_unit": "2*n*p*(2 plane products for L1 variance, 3 for L2 variance) FP16 flop per sweep*start (active starts only)",
-                "launches": vstats["launches"], "avg_launch_ms": round(vstats["ms"] / max(1, vstats["launches"]), 4),
-                "fp32_equivalent_algorithmic_tflops": round(alg, 1)}
+                "launches": vstats["launches"], "avg_launch_ms": round(vstats["ms"] / max(1, vstats["launches"]), 4)}
     elif dom == "xstep" and kern["xstep"][1] > 0:
         achieved = 8.0 * p * sweeps / (kern["xstep"][1] / 1e3) / 1e9
         roof = {"kernel": "x-step (k_xstep)", "bound": "hbm", "achieved": round(achieved, 1),

@@ -362,35 +362,56 @@ int spca_profile_enable(spca_handle *h, int mask);
 int spca_profile_query(spca_handle *h, int kernel, int64_t *launches, double *ms);
 
 /*
- * spca_objective_noalloc -- the objective f(x) of Table 1 and the explained variance
- * (||Ax||_2^2 for L2 variance, ||Ax||_1 for L1 variance) of r given vectors x, with u = A x
- * accumulated in FP64: the values spca_solve reports per start (start_objective,
- * start_explained).  The paper has no counterpart: this entry point exists for callers that
- * cannot allocate device memory -- code running inside someone else's CUDA graph capture,
- * under an allocator that owns the whole device, or in a latency-critical loop where an
- * allocation's implicit synchronisation is not acceptable.  It needs no handle and allocates
- * nothing: its scratch is a fixed array in the library's device memory (4 MiB, held on every
- * GPU that loads the library until the process exits).
- *   form, gamma  Table 1 formulation (1..8) and the penalty weight (>= 0; ignored by 1..4).
+ * spca_objective_noalloc -- the objective and the explained variance of r given vectors x,
+ * with u = A x accumulated in FP64: the values spca_solve reports per start (start_objective,
+ * start_explained).  Per formulation the objective is
+ *   1, 3: ||Ax||_2          2, 4: ||Ax||_1
+ *   5:    ||Ax||_2^2 - gamma ||x||_0      6: ||Ax||_1^2 - gamma ||x||_0
+ *   7:    ||Ax||_2 - gamma ||x||_1        8: ||Ax||_1 - gamma ||x||_1
+ * and the explained variance ||Ax||_2^2 (odd forms) or ||Ax||_1 (even forms).  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device memory -- code
+ * running inside someone else's CUDA graph capture (an allocation there is an error or breaks
+ * the capture), under an allocator or memory pool that owns the whole device, or in a
+ * latency-critical loop where an allocation's implicit synchronisation is not acceptable.  It
+ * needs no handle and allocates nothing: its scratch is a fixed array in the library's device
+ * memory (4 MiB, held on every GPU that loads the library until the process exits).
+ *   form, gamma  formulation (1..8) and the penalty weight (>= 0; ignored by 1..4).
  *   A            device, n x p float, row-major, leading dimension lda >= p.
  *   X            device, r x p float, one vector per row, leading dimension ldx >= p.
  *   f, ev        device, r doubles each (outputs).
  *   cuda_stream  cudaStream_t the kernels are queued on (NULL = the legacy default stream);
  *                the call returns once they are queued.
- * Limits: r <= 65535 and r * ceil(n / 256) <= SPCA_NOALLOC_MAX_PARTIALS, else SPCA_E_INVALID and
- * nothing runs.
+ * Limits: r * ceil(n / 256) <= SPCA_NOALLOC_MAX_PARTIALS (the scratch), else SPCA_E_INVALID
+ * and nothing runs; r <= 65535 (a grid dimension), else SPCA_E_UNSUPPORTED.
  * The first call on a device looks up the scratch's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.  Every call shares the
  * one scratch array: calls whose kernels overlap on the GPU (other streams, other threads)
  * race and must be serialised by the caller.  The scratch keeps the last call's contents; each
  * call writes every entry it reads.
- * Errors: SPCA_E_INVALID (form, sizes, leading dimensions, NULL pointers, gamma, limit),
- *         SPCA_E_CUDA.
+ * Errors: SPCA_E_INVALID (form, sizes, leading dimensions, NULL pointers, gamma, scratch limit),
+ *         SPCA_E_UNSUPPORTED (r above 65535), SPCA_E_CUDA.
  */
 #define SPCA_NOALLOC_MAX_PARTIALS 262144
 int spca_objective_noalloc(int form, double gamma, const float *A, int64_t n, int64_t p, int64_t lda,
                            const float *X, int64_t ldx, int r, double *f, double *ev,
                            void *cuda_stream);
+
+/*
+ * spca_set_waits -- the bounded device-side waits of the handle's tensor-core contractions.
+ * Every wait inside those kernels (a pipeline stage, the accumulator, the part of a split tile
+ * that another CTA pair computes) gives up after wait_limit_us microseconds: the kernel records
+ * SPCA_E_TIMEOUT, lets the loads it has in flight land, frees its tensor memory and returns, and
+ * the call that launched it returns SPCA_E_TIMEOUT; the handle stays usable.  This is the
+ * failure detection of the device side: a stalled CTA pair turns into an error status instead
+ * of a kernel that never ends.  Not part of the method (the paper has no counterpart).
+ *   wait_limit_us      1 .. 60,000,000 (the default is 2,000,000: 2 s).
+ *   unpublished_parts  test switch: nonzero makes the CTAs that finish a split tile wait for a
+ *                      part flag that no CTA ever sets, so that their waits run out and the
+ *                      timeout path above runs; 0 for normal work.
+ * Captured sweep graphs are dropped (they hold the old settings).
+ * Errors: SPCA_E_INVALID (NULL handle, limit out of range).
+ */
+int spca_set_waits(spca_handle *h, int64_t wait_limit_us, int unpublished_parts);
 
 /* spca_destroy -- free the handle's device memory (waits for its stream). NULL is a no-op. */
 void spca_destroy(spca_handle *h);

@@ -18,12 +18,10 @@
 //   D[m, c] = sum_{(i,j) in pairs} sum_k P_i[m, k] Q_j[c, k]      out[c * ldo + m] = D[m, c]
 //
 // P (M x K) and Q (N x K) are K-contiguous FP16 planes; plane i of P starts at row i * M_alloc.
-// Tile 128 (M) x BN (N) x 64 (K); 2-stage TMA -> MMA pipeline over mbarriers.  The operand
-// delivery from L2, not the MMAs, bounds this contraction (measured: the time is the same with
-// 1, 2 or 3 plane products per stage), and the P planes are its largest stream.  So the
-// C CTAs (C = 1, 2, 4) that compute adjacent N tiles of one M tile form a thread-block cluster:
-// each loads 1/C of the P tile and multicasts it to all C, and each CTA's MMA commit frees the
-// stage in every CTA of the cluster.
+// Two kernels: the CTA-pair kernel (k_gemm_tc2, 256-row tiles, persistent stream-K) whenever
+// the output has two or more 128-row tiles, and a single-CTA kernel (k_gemm_tc, 128-row tiles,
+// one CTA per output tile, no cluster) for a lone M tile and for handles that share the
+// device with other solves.  Every CTA loads its own operand tiles; no load is multicast.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -40,7 +38,14 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_THREADS = 192;           // warp 0 TMA + TMEM alloc, warp 1 MMA, warps 2-5 epilogue
-constexpr uint64_t TC_WAIT_NS = 2000000000ull;   // bounded waits: 2 s, then error + exit
+// the CTA-pair kernel: warp 0 TMA + TMEM alloc, warp 1 MMA, warps 2-9 epilogue (two warps per TMEM
+// lane quarter, each holding the running sum of 128 of the tile's 256 columns in registers)
+constexpr int TC2_THREADS = 320;
+constexpr int TC2_EPI_WARPS = 8;
+// bounded waits: the limit is a launch argument (2 s unless a handle sets a shorter one), after
+// which a kernel records SPCA_E_TIMEOUT and winds down; loads still in flight then get at most
+// TC_DRAIN_NS to land before the CTA exits
+constexpr uint64_t TC_DRAIN_NS = 1000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -66,19 +71,39 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// wait for the phase with the given parity; false (and *err set) after TC_WAIT_NS
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag) {
+// non-blocking test of the same
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait for the phase with the given parity; false (and *err set) after wait_ns nanoseconds, or
+// at once when another thread of the CTA has given up (*abort_flag)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag,
+                                          uint64_t wait_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (globaltimer() - t0 > TC_WAIT_NS) {
+    if (globaltimer() - t0 > wait_ns) {
       *abort_flag = 1;
       if (err) atomicExch(err, SPCA_E_TIMEOUT);
       return false;
     }
   }
+}
+// the same without error reporting, for the clean-up after a wait gave up
+__device__ __forceinline__ bool mbar_wait_quiet(uint32_t bar, uint32_t parity, uint64_t wait_ns) {
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try(bar, parity))
+    if (globaltimer() - t0 > wait_ns) return false;
+  return true;
 }
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
                                             uint32_t bar) {
@@ -99,30 +124,9 @@ __device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
   d |= (uint64_t)(BK == 64 ? 2 : 4) << 61;               // swizzle: 128B or 64B
   return d;
 }
-// multicast variant: the box lands at the same offset in every CTA of ctaMask, and the
-// complete_tx goes to the barrier at the same offset in each of them
-__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
-                                               uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3, %4}], [%5], %6;"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-      ::"r"(bar), "h"(mask)
-      : "memory");
-}
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_size() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
   return r;
 }
 __device__ __forceinline__ void cluster_sync_all() {
@@ -161,6 +165,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+      "%13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 }  // namespace
 
 template <int BN, int NA, int NB, int STAGES, int TC_BK>
@@ -169,33 +186,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               int kblocks, const int *__restrict__ k_dev, TcPairs pairs, float *__restrict__ out, int64_t ldo,
               const float *__restrict__ row_inv, const float *__restrict__ col_inv, float q_inv,
               const int *__restrict__ gate, const int *__restrict__ n_dev, const int *__restrict__ col_map,
-              int *err) {
+              int *err, uint64_t wait_ns, int ntn_launch) {
   constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;       // 16 KB per P plane tile
-  constexpr uint32_t B_BYTES = BN * TC_BK * 2;          // 32 KB (BN = 256) per Q plane tile
+  constexpr uint32_t B_BYTES = BN * TC_BK * 2;          // 16 KB (BN = 128) per Q plane tile
   constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
-  constexpr uint32_t TMEM_COLS = 2 * BN;                // two FP32 accumulators of BN columns x 128 lanes
+  // four FP32 accumulators of BN columns x 128 lanes: the hi x hi product of K-block kb goes to
+  // accumulator kb mod nmain (three of them, four without correction products) and the
+  // corrections to the last one.  The tensor core's accumulation truncates, so its error grows
+  // with the steps into one accumulator and with the accumulator's magnitude: spreading the
+  // main product over three accumulators cuts that error threefold.
+  constexpr uint32_t TMEM_COLS = 4 * BN;
+  static_assert(TMEM_COLS <= 512, "TMEM columns");
 
   extern __shared__ __align__(1024) uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
-  const uint32_t crank = cluster_rank(), csize = cluster_size();
   if (gate && *gate == 0) return;   // uniform over the grid: the contraction is not needed
   if (n_dev) N = *n_dev;            // columns (active starts) known only on the device
   if (k_dev) kblocks = (*k_dev + TC_BK - 1) / TC_BK;   // contraction length known only on the device
   if (kblocks <= 0) return;
-  if ((int)(blockIdx.x - crank) * BN >= N) return;   // uniform over the cluster
+  // one linear grid over the output tiles, N tiles fastest (CTAs sharing a P tile run together);
+  // ntn_launch = the N tiles the grid was sized for (N may be smaller when read from the device)
+  const int tn = (int)(blockIdx.x % (unsigned)ntn_launch), tm = (int)(blockIdx.x / (unsigned)ntn_launch);
+  if (tn * BN >= N) return;   // uniform over the CTA
 
   uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;   // N fastest: CTAs sharing a P tile run together
-  const uint16_t cmask = (uint16_t)((1u << csize) - 1u);
+  const int m0 = tm * TC_BM, n0 = tn * BN;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
-      mbar_init(smem_u32(&empty_bar[s]), csize);         // one MMA commit from every CTA
+      mbar_init(smem_u32(&empty_bar[s]), 1);             // this CTA's MMA commit
     }
     mbar_init(smem_u32(&accum_bar), 1);
     abort_flag = 0;
@@ -210,76 +234,82 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  cluster_sync_all();               // every CTA's barriers exist before any multicast reaches them
   const uint32_t tmem = tmem_slot;
 
+  // the producer counts the stages whose loads it issued, the MMA issuer the stages it consumed:
+  // after a timed-out wait the producer waits (bounded) for the loads still in flight
+  __shared__ int issued, consumed;
   if (warp == 0 && lane == 0) {
     // ---------------------------------------------------------------- TMA producer
-    const int rows_per = TC_BM / (int)csize;                    // this CTA's slice of the P tile
-    const uint32_t slice = (uint32_t)(crank * rows_per) * (TC_BK * 2);
-    for (int kb = 0; kb < kblocks; ++kb) {
+    int kb = 0;
+    for (; kb < kblocks; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, err, &abort_flag)) break;
+      if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, err, &abort_flag, wait_ns)) break;
       const uint32_t fb = smem_u32(&full_bar[s]);
       mbar_expect_tx(fb, STAGE_BYTES);
       uint8_t *st = tiles + (size_t)s * STAGE_BYTES;
 #pragma unroll
-      for (int a = 0; a < NA; ++a) {
-        if (csize == 1)
-          tma_load_3d(smem_u32(st + a * A_BYTES), &tmP, kb * TC_BK, m0, a, fb);
-        else
-          tma_load_3d_mc(smem_u32(st + a * A_BYTES) + slice, &tmP, kb * TC_BK, m0 + (int)crank * rows_per, a, fb,
-                         cmask);
-      }
+      for (int a = 0; a < NA; ++a) tma_load_3d(smem_u32(st + a * A_BYTES), &tmP, kb * TC_BK, m0, a, fb);
 #pragma unroll
       for (int b = 0; b < NB; ++b)
         tma_load_3d(smem_u32(st + NA * A_BYTES + b * B_BYTES), &tmQ, kb * TC_BK, n0, b, fb);
     }
+    issued = kb;
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------------- MMA issuer
     constexpr uint32_t idesc = idesc_f16(TC_BM, BN);
+    const int nmain = pairs.first_corr >= 0 ? 3 : 4;
     bool ok = true;
-    for (int kb = 0; kb < kblocks && ok; ++kb) {
+    int kb = 0;
+    for (; kb < kblocks && ok; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!mbar_wait(smem_u32(&full_bar[s]), ph, err, &abort_flag)) { ok = false; break; }
+      if (!mbar_wait(smem_u32(&full_bar[s]), ph, err, &abort_flag, wait_ns)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = smem_u32(tiles + (size_t)s * STAGE_BYTES);
       for (int q = 0; q < pairs.n; ++q) {
         const uint32_t a_base = st + pairs.a[q] * A_BYTES;
         const uint32_t b_base = st + NA * A_BYTES + pairs.b[q] * B_BYTES;
-        const bool main = (pairs.a[q] | pairs.b[q]) == 0;   // hi x hi -> accumulator 0
-        const uint32_t d = tmem + (main ? 0u : (uint32_t)BN);
-        const bool first = kb == 0 && q == (main ? pairs.first_main : pairs.first_corr);
+        const bool main = (pairs.a[q] | pairs.b[q]) == 0;   // hi x hi -> accumulator kb mod nmain
+        const uint32_t d = tmem + (uint32_t)BN * (main ? (uint32_t)(kb % nmain) : 3u);
+        const bool first = main ? (kb < nmain && q == pairs.first_main) : (kb == 0 && q == pairs.first_corr);
 #pragma unroll
         for (int kk = 0; kk < TC_BK / 16; ++kk) {
           mma_bf16(d, sw_desc<TC_BK>(a_base + kk * 32), sw_desc<TC_BK>(b_base + kk * 32), idesc,
                    (first && kk == 0) ? 0u : 1u);
         }
       }
-      // frees the stage (in every CTA of the cluster) once these MMAs have read it
-      if (csize == 1)
-        mma_commit(smem_u32(&empty_bar[s]));
-      else
-        mma_commit_mc(smem_u32(&empty_bar[s]), cmask);
+      mma_commit(smem_u32(&empty_bar[s]));   // frees the stage once these MMAs have read it
     }
-    if (ok) mma_commit(smem_u32(&accum_bar));  // accumulator complete
+    consumed = kb;
+    // the accumulator is complete (after a wait gave up: the MMAs issued so far are done, which
+    // the clean-up below waits for before it frees TMEM)
+    mma_commit(smem_u32(&accum_bar));
   } else if (warp >= 2) {
     // ---------------------------------------------------------------- epilogue (TMEM -> HBM)
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
     // tcgen05.ld is warp-collective: take the barrier result uniformly over the warp
-    const bool ready = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accum_bar), 0, err, &abort_flag));
+    const bool ready = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accum_bar), 0, err, &abort_flag, wait_ns) &&
+                                                   !abort_flag);
     if (ready) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int row = m0 + quad * 32 + lane;
+      const int nmain = pairs.first_corr >= 0 ? 3 : 4;
+      const int nused = kblocks < nmain ? kblocks : nmain;   // main accumulators written
 #pragma unroll 1
       for (int cb = 0; cb < BN / 32; ++cb) {
         float v[32], w[32];
         const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 32);
         tmem_ld32(ta, v);
+        // the main accumulators in order, then the corrections
+        for (int i = 1; i < nused; ++i) {
+          tmem_ld32(ta + (uint32_t)(i * BN), w);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += w[j];
+        }
         if (pairs.first_corr >= 0) {
-          tmem_ld32(ta + (uint32_t)BN, w);
+          tmem_ld32(ta + (uint32_t)(3 * BN), w);
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += w[j];
         }
@@ -297,12 +327,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (abort_flag && threadIdx.x == 0) {
+    // a wait gave up: the MMAs issued so far may still run, and the loads of the stages issued
+    // but not consumed may still be landing in this CTA's shared memory; wait for both (bounded)
+    // before TMEM is freed and the CTA exits
+    mbar_wait_quiet(smem_u32(&accum_bar), 0, wait_ns);
+    for (int kb = consumed; kb < issued; ++kb)
+      mbar_wait_quiet(smem_u32(&full_bar[kb % STAGES]), (uint32_t)(kb / STAGES) & 1u, TC_DRAIN_NS);
+  }
+  __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
-  // no CTA leaves while a peer may still multicast into it or arrive on its barriers
-  cluster_sync_all();
 }
 
 // ---------------------------------------------------------------------- CTA-pair variant
@@ -363,6 +400,9 @@ __device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
   return r;
 }
+__device__ __forceinline__ void st_cluster_s32(uint32_t addr_cluster, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr_cluster), "r"(v) : "memory");
+}
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
@@ -374,8 +414,21 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 __device__ __forceinline__ void st_release(int *p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-// the four epilogue warps (128 threads) only
-__device__ __forceinline__ void epilogue_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_local(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// split points of a tile's K range for the main accumulator: the multiples of `piece` K-blocks
+// (piece <= 0: none)
+__device__ __forceinline__ bool is_split(int kb, int piece) { return piece > 0 && kb > 0 && kb % piece == 0; }
+// the smallest split point above kb (INT32_MAX when there is none)
+__device__ __forceinline__ int next_split(int kb, int piece) {
+  return piece > 0 ? (kb / piece + 1) * piece : 0x7fffffff;
+}
+// split points strictly inside (kb0, kb1)
+__device__ __forceinline__ int splits_inside(int kb0, int kb1, int piece) {
+  return piece > 0 && kb1 - 1 > kb0 ? (kb1 - 1) / piece - kb0 / piece : 0;
+}
 
 struct SkRange {   // slot j's share of the W units: [u0, u1)
   long long W;
@@ -386,12 +439,13 @@ struct SkRange {   // slot j's share of the W units: [u0, u1)
 // F8: operands in FP8 E4M3 (one byte each; a K-block of 128 elements keeps the 128-byte swizzled
 // rows of the FP16 layout, so the stage layout, descriptors and the 32-byte MMA steps are the same)
 template <int BN, int NA, int NB, int STAGES, bool F8 = false>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC2_THREADS, 1)
     k_gemm_tc2(const __grid_constant__ CUtensorMap tmP, const __grid_constant__ CUtensorMap tmQ, int M, int N,
                int kblocks, const int *__restrict__ k_dev, TcPairs pairs, float *__restrict__ out, int64_t ldo,
                const float *__restrict__ row_inv, const float *__restrict__ col_inv, float q_inv,
                const int *__restrict__ gate, const int *__restrict__ n_dev, const int *__restrict__ col_map,
-               int *err, float *__restrict__ ws, int *__restrict__ flags, int epoch) {
+               int *err, float *__restrict__ ws, int *__restrict__ flags, int epoch, int wait_epoch,
+               uint64_t wait_ns, int piece) {
   constexpr int ES = F8 ? 1 : 2;                        // bytes per element
   constexpr int BK = 128 / ES;                          // elements per K-block: 128-byte rows
   constexpr uint32_t A_BYTES = TC_BM * BK * ES;         // this CTA's 128 rows of one P plane
@@ -400,9 +454,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   constexpr uint32_t TMEM_COLS = 2 * BN;
 
   extern __shared__ __align__(1024) uint8_t dsmem[];
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar, tmem_empty_bar;
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar, tmem_empty_bar, mma_done_bar,
+      part_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
+  // clean-up bookkeeping: stages whose loads this CTA issued, stages the leader's MMAs consumed,
+  // and (in the leader) the peer's issued count and abort flag, written by the peer
+  __shared__ int issued, consumed, peer_issued, peer_abort;
 
   const uint32_t rank = cluster_rank();   // 0: leader (even M tile of the pair), 1: peer
   const int slot = (int)(blockIdx.x >> 1), S = (int)(gridDim.x >> 1);
@@ -425,8 +483,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     mbar_init(smem_u32(&accum_bar), 1);
-    mbar_init(smem_u32(&tmem_empty_bar), 8);   // 4 epilogue warps in each CTA of the pair
+    mbar_init(smem_u32(&tmem_empty_bar), 2 * TC2_EPI_WARPS);   // the epilogue warps of both CTAs
+    mbar_init(smem_u32(&mma_done_bar), 1);     // the leader's last commit: every MMA done
+    mbar_init(smem_u32(&part_bar), TC2_EPI_WARPS);   // the epilogue warps wrote a stream-K part (one per slot)
     abort_flag = 0;
+    issued = consumed = peer_issued = peer_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -463,7 +524,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = (int)(it % STAGES);
         const uint32_t ph = (it / STAGES) & 1u;
-        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, err, &abort_flag)) { ok = false; break; }
+        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, err, &abort_flag, wait_ns)) { ok = false; break; }
         const uint32_t own = smem_u32(&full_bar[s]);
         const uint32_t fb = rank == 0 ? own : map_to_rank(own, 0);   // the leader's full barrier
         if (rank == 0) mbar_expect_tx(own, 2 * STAGE_BYTES);         // both CTAs' bytes
@@ -476,60 +537,162 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                            fb);
       }
     }
+    issued = (int)it;
   } else if (warp == 1 && lane == 0 && rank == 0) {
     // ---------------------------------------------------------------- MMA issuer (leader)
+    // Every commit to accum_bar is one "drain": the epilogues of both CTAs read the accumulators
+    // (the main one alone at a split point, main and corrections at the end of a segment) and
+    // release them on tmem_empty_bar; drain d's release is phase d of that barrier.
+    // At a split point of the tile's K range the main accumulator is drained into the epilogue's
+    // registers and restarted, so that no main accumulation spans more than `piece` K-blocks (the
+    // accumulation truncates, and its error grows with the steps into one accumulator and with
+    // the accumulator's magnitude).  To keep the tensor pipe busy meanwhile, the last STAGES
+    // stages before a split issue their main products only; once the drain is committed their
+    // correction products follow (into their own accumulator) while the epilogue reads the main
+    // one.  Each accumulator still receives its products in K order, so the result does not
+    // depend on the timing.
     constexpr uint32_t idesc = idesc_f16(2 * TC_BM, BN);
-    uint32_t it = 0, seg = 0;
+    const bool has_corr = pairs.first_corr >= 0;
+    uint32_t it = 0, nd = 0;
     bool ok = true;
-    for (long long u = u0; u < u1 && ok; ++seg) {
+    auto issue = [&](uint32_t st, bool do_main, bool do_corr, bool main_first, bool corr_first) {
+      for (int q = 0; q < pairs.n; ++q) {
+        const bool main = (pairs.a[q] | pairs.b[q]) == 0;
+        if (main ? !do_main : !do_corr) continue;
+        const uint32_t a_base = st + pairs.a[q] * A_BYTES;
+        const uint32_t b_base = st + NA * A_BYTES + pairs.b[q] * B_BYTES;
+        const uint32_t d = tmem + (main ? 0u : (uint32_t)BN);
+        const bool first = main ? (main_first && q == pairs.first_main) : (corr_first && q == pairs.first_corr);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {   // 32 bytes of K per instruction
+          if (F8)
+            mma_f8_pair(d, sw_desc<64>(a_base + kk * 32), sw_desc<64>(b_base + kk * 32), idesc,
+                        (first && kk == 0) ? 0u : 1u);
+          else
+            mma_bf16_pair(d, sw_desc<64>(a_base + kk * 32), sw_desc<64>(b_base + kk * 32), idesc,
+                          (first && kk == 0) ? 0u : 1u);
+        }
+      }
+    };
+    uint32_t pend_st[STAGES];   // stages whose correction products wait for the next split's drain
+    int pend_s[STAGES];
+    bool pend_first[STAGES];
+    for (long long u = u0; u < u1 && ok;) {
       long long t;
       int kb0, kb1;
       next_seg(u, t, kb0, kb1);
-      // the epilogues of both CTAs have read the previous segment's accumulators
-      if (seg > 0 && !mbar_wait(smem_u32(&tmem_empty_bar), (seg - 1) & 1u, err, &abort_flag)) break;
+      // the epilogues of both CTAs have read the previous drain
+      if (nd > 0 && !mbar_wait(smem_u32(&tmem_empty_bar), (nd - 1) & 1u, err, &abort_flag, wait_ns)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      bool main_first = true;
+      int npend = 0;
+      int nxt = has_corr ? next_split(kb0, piece) : 0x7fffffff;   // the next split point after kb0
       for (int kb = kb0; kb < kb1; ++kb, ++it) {
         const int s = (int)(it % STAGES);
         const uint32_t ph = (it / STAGES) & 1u;
-        if (!mbar_wait(smem_u32(&full_bar[s]), ph, err, &abort_flag)) { ok = false; break; }
+        if (!mbar_wait(smem_u32(&full_bar[s]), ph, err, &abort_flag, wait_ns)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t st = smem_u32(tiles + (size_t)s * STAGE_BYTES);
-        for (int q = 0; q < pairs.n; ++q) {
-          const uint32_t a_base = st + pairs.a[q] * A_BYTES;
-          const uint32_t b_base = st + NA * A_BYTES + pairs.b[q] * B_BYTES;
-          const bool main = (pairs.a[q] | pairs.b[q]) == 0;
-          const uint32_t d = tmem + (main ? 0u : (uint32_t)BN);
-          const bool first = kb == kb0 && q == (main ? pairs.first_main : pairs.first_corr);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {   // 32 bytes of K per instruction
-            if (F8)
-              mma_f8_pair(d, sw_desc<64>(a_base + kk * 32), sw_desc<64>(b_base + kk * 32), idesc,
-                          (first && kk == 0) ? 0u : 1u);
-            else
-              mma_bf16_pair(d, sw_desc<64>(a_base + kk * 32), sw_desc<64>(b_base + kk * 32), idesc,
-                            (first && kk == 0) ? 0u : 1u);
-          }
+        if (nxt < kb1 && nxt - kb <= STAGES) {
+          // one of the last STAGES stages before a split: main products now, corrections later
+          issue(st, true, false, main_first, false);
+          pend_st[npend] = st;
+          pend_s[npend] = s;
+          pend_first[npend] = kb == kb0;
+          ++npend;
+        } else {
+          issue(st, true, true, main_first, kb == kb0);
+          mma_commit_pair(smem_u32(&empty_bar[s]));   // frees stage s in both CTAs
         }
-        mma_commit_pair(smem_u32(&empty_bar[s]));   // frees stage s in both CTAs
+        main_first = false;
+        if (kb + 1 == nxt && nxt < kb1) {
+          // the main piece ends here: drain nd reads the main accumulator alone
+          mma_commit_pair(smem_u32(&accum_bar));
+          ++nd;
+          for (int q = 0; q < npend; ++q) {
+            issue(pend_st[q], false, true, false, pend_first[q]);
+            mma_commit_pair(smem_u32(&empty_bar[pend_s[q]]));
+          }
+          npend = 0;
+          if (!mbar_wait(smem_u32(&tmem_empty_bar), (nd - 1) & 1u, err, &abort_flag, wait_ns)) {
+            ok = false;
+            ++it;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          main_first = true;
+          nxt = next_split(nxt, piece);
+        }
       }
-      if (ok) mma_commit_pair(smem_u32(&accum_bar));
+      if (ok) {
+        mma_commit_pair(smem_u32(&accum_bar));      // drain nd: the segment's result
+        ++nd;
+      }
     }
+    consumed = (int)it;
+    // every MMA issued so far is done when this completes (in both CTAs): the clean-up waits for
+    // it before TMEM is freed
+    mma_commit_pair(smem_u32(&mma_done_bar));
   } else if (warp >= 2) {
     // ---------------------------------------------------------------- epilogue (own 128 rows)
-    const int quad = warp & 3;
+    // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows of this CTA's half of the tile) and
+    // columns 128 h .. 128 h + 127, h = (w - 2) / 4; the running sum of those 128 columns of its
+    // row stays in registers, so a split drain costs four TMEM loads and no memory traffic
+    const int quad = warp & 3, half = (warp - 2) >> 2;
     const uint32_t tmem_empty_leader = map_to_rank(smem_u32(&tmem_empty_bar), 0);
-    uint32_t seg = 0;
+    const int row_l = quad * 32 + lane, cbase = half * 128;
+    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)cbase;
+    const bool has_corr = pairs.first_corr >= 0;
+    uint32_t nd = 0;
     bool ok = true;
-    for (long long u = u0; u < u1 && ok; ++seg) {
+    for (long long u = u0; u < u1 && ok;) {
+      float acc[128];
       long long t;
       int kb0, kb1;
       next_seg(u, t, kb0, kb1);
       const bool owner = kb0 == 0 && kb1 < KB, contrib = kb0 > 0;
       const int m0 = (2 * (int)(t % pm) + (int)rank) * TC_BM, n0 = (int)(t / pm) * BN;
-      ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accum_bar), seg & 1u, err, &abort_flag));
+      // the split drains of the main accumulator inside this segment, then the segment's result:
+      // acc = ((main_1 + main_2) + ... + main_last) + corrections, in that order
+      const int nsplit = has_corr ? splits_inside(kb0, kb1, piece) : 0;
+      for (int d = 0; d <= nsplit && ok; ++d) {
+        ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accum_bar), nd & 1u, err, &abort_flag, wait_ns));
+        ++nd;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (d == 0) {
+#pragma unroll
+          for (int cb = 0; cb < 8; ++cb) {
+            float v[16];
+            tmem_ld16(tbase + (uint32_t)(cb * 16), v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[cb * 16 + j] = v[j];
+          }
+        } else {
+#pragma unroll
+          for (int cb = 0; cb < 8; ++cb) {
+            float v[16];
+            tmem_ld16(tbase + (uint32_t)(cb * 16), v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[cb * 16 + j] += v[j];
+          }
+        }
+        if (d == nsplit && has_corr) {
+#pragma unroll
+          for (int cb = 0; cb < 8; ++cb) {
+            float v[16];
+            tmem_ld16(tbase + (uint32_t)BN + (uint32_t)(cb * 16), v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[cb * 16 + j] += v[j];
+          }
+        }
+        // accumulators read: release them to the leader's next MMA
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(tmem_empty_leader);
+      }
       if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // an owner first waits for the later parts of its tile (slots slot+1, slot+2, ...)
+      // an owner waits for the later parts of its tile (slots slot+1, slot+2, ...)
       int jlast = slot;
       if (owner) {
         const long long tend = (t + 1) * KB;
@@ -538,10 +701,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int j = slot + 1; j <= jlast && ok; ++j) {
             if (R.start(j) >= R.start(j + 1)) continue;   // empty share: no part
             const int *fl = flags + (j * 2 + (int)rank);
-            if (ld_acquire(fl) == epoch) continue;
+            if (ld_acquire(fl) == wait_epoch) continue;
             const uint64_t t0 = globaltimer();
-            while (ld_acquire(fl) != epoch) {
-              if (abort_flag || globaltimer() - t0 > TC_WAIT_NS) {
+            while (ld_acquire(fl) != wait_epoch) {
+              if (abort_flag || globaltimer() - t0 > wait_ns) {
                 abort_flag = 1;
                 if (err) atomicExch(err, SPCA_E_TIMEOUT);
                 ok = false;
@@ -553,63 +716,78 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         ok = __shfl_sync(0xffffffffu, ok, 0);
         __syncwarp();
       }
-      const int row_l = quad * 32 + lane, row = m0 + row_l;
+      const int row = m0 + row_l;
       float *mine = ws + ((int64_t)slot * 2 + rank) * BN * TC_BM;
-#pragma unroll 1
-      for (int cb = 0; cb < BN / 32; ++cb) {
-        float v[32], w[32];
-        const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 32);
-        tmem_ld32(ta, v);
-        if (pairs.first_corr >= 0) {
-          tmem_ld32(ta + (uint32_t)BN, w);
+      if (contrib) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] += w[j];
+        for (int c = 0; c < 128; ++c) __stcg(mine + (int64_t)(cbase + c) * TC_BM + row_l, acc[c]);
+        // this part of the tile is in the workspace: each warp signals its rows, then warp 2
+        // publishes the part once all of them have (a bounded wait on an mbarrier rather than a
+        // named barrier, so that a warp that gave up cannot leave the others blocked)
+        __syncwarp();
+        if (lane == 0) mbar_arrive_local(smem_u32(&part_bar));
+        if (warp == 2 && lane == 0 && mbar_wait(smem_u32(&part_bar), 0, err, &abort_flag, wait_ns)) {
+          __threadfence();
+          st_release(flags + (slot * 2 + (int)rank), epoch);
         }
-        if (contrib) {
+        continue;
+      }
+      if (owner && ok) {
+        for (int jj = slot + 1; jj <= jlast; ++jj) {
+          if (R.start(jj) >= R.start(jj + 1)) continue;
+          const float *part = ws + ((int64_t)jj * 2 + rank) * BN * TC_BM + (int64_t)cbase * TC_BM + row_l;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) mine[(int64_t)(cb * 32 + j) * TC_BM + row_l] = v[j];
-          continue;
-        }
-        if (owner && ok) {
-          for (int jj = slot + 1; jj <= jlast; ++jj) {
-            if (R.start(jj) >= R.start(jj + 1)) continue;
-            const float *part = ws + ((int64_t)jj * 2 + rank) * BN * TC_BM;
+          for (int cb = 0; cb < 8; ++cb) {   // 16 loads in flight at a time
+            float v[16];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] += __ldcg(part + (int64_t)(cb * 32 + j) * TC_BM + row_l);
-          }
-        }
-        if (row < M && ok) {
-          const float sc = (row_inv ? row_inv[row] : 1.0f) * q_inv;   // powers of two
+            for (int j = 0; j < 16; ++j) v[j] = __ldcg(part + (int64_t)(cb * 16 + j) * TC_BM);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = n0 + cb * 32 + j;
-            if (col < N)
-              out[(int64_t)(col_map ? col_map[col] : col) * ldo + row] = v[j] * sc * (col_inv ? col_inv[col] : 1.0f);
+            for (int j = 0; j < 16; ++j) acc[cb * 16 + j] += v[j];
+            __syncwarp();
           }
         }
       }
-      // accumulators read: release them to the leader's next MMA
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(tmem_empty_leader);
-      if (contrib) {
-        // this part of the tile is in the workspace: publish it
-        epilogue_bar();
-        if (warp == 2 && lane == 0) {
-          __threadfence();
-          st_release(flags + (slot * 2 + (int)rank), epoch);
+      // (row < M differs between the lanes of the last row tile: no warp-wide operation below)
+      if (row < M && ok) {
+        const float sc = (row_inv ? row_inv[row] : 1.0f) * q_inv;   // powers of two
+#pragma unroll
+        for (int c = 0; c < 128; ++c) {
+          const int col = n0 + cbase + c;
+          if (col < N)
+            out[(int64_t)(col_map ? col_map[col] : col) * ldo + row] = acc[c] * sc * (col_inv ? col_inv[col] : 1.0f);
         }
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  cluster_sync_all();   // the leader's MMAs into this CTA's TMEM are complete in both CTAs
+  if (rank == 1 && threadIdx.x == 0) {
+    // the peer's loads complete on the leader's barriers: tell the leader how far they went
+    st_cluster_s32(map_to_rank(smem_u32(&peer_issued), 0), issued);
+    st_cluster_s32(map_to_rank(smem_u32(&peer_abort), 0), abort_flag);
+  }
+  cluster_sync_all();
+  if (threadIdx.x == 0) {
+    // the leader's MMAs into this CTA's TMEM (and out of its shared memory) are done
+    mbar_wait_quiet(smem_u32(&mma_done_bar), 0, wait_ns);
+    if (rank == 0 && (abort_flag || peer_abort)) {
+      // a wait gave up: stages loaded but not consumed may still be landing in either CTA's
+      // shared memory.  Each such stage has one open phase on the leader's full barrier; a stage
+      // only the peer loaded is armed here for the peer's bytes.  Bounded waits.
+      const int top = issued > peer_issued ? issued : peer_issued;
+      for (int q = consumed; q < top; ++q) {
+        const uint32_t fb = smem_u32(&full_bar[q % STAGES]);
+        if (q >= issued) mbar_expect_tx(fb, STAGE_BYTES);
+        mbar_wait_quiet(fb, (uint32_t)(q / STAGES) & 1u, TC_DRAIN_NS);
+      }
+    }
+  }
+  __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
-  cluster_sync_all();
+  cluster_sync_all();   // the peer leaves only after the leader's clean-up
 }
 
 // ---------------------------------------------------------------------- planes
@@ -762,44 +940,29 @@ cudaError_t make_f8_map(CUtensorMap *map, const void *base, int64_t rows, int64_
 }
 
 cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld, int planes) {
-  for (int i = 0; i < 3; ++i) {
-    cudaError_t e = make_plane_map(&maps->m[i], base, rows, ld, planes, TC_BM >> i, 64);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return make_plane_map(&maps->m[0], base, rows, ld, planes, TC_BM, 64);
 }
 
 namespace {
 template <int BN, int NA, int NB, int STAGES, int TC_BK>
 cudaError_t launch_tc_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, int K, const int *k_dev, TcPairs pairs,
                            float *out, int64_t ldo, const float *row_inv, const float *col_inv, float q_inv,
-                           const int *gate, const int *n_dev, const int *col_map, int *err, cudaStream_t st) {
+                           const int *gate, const int *n_dev, const int *col_map, int *err, uint64_t wait_ns,
+                           cudaStream_t st) {
   constexpr int STAGE_BYTES = NA * TC_BM * TC_BK * 2 + NB * BN * TC_BK * 2;
   constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
   auto kern = k_gemm_tc<BN, NA, NB, STAGES, TC_BK>;
   static const cudaError_t configured = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
   if (configured != cudaSuccess) return configured;
-  // cluster of C CTAs over adjacent N tiles (C = 1, 2, 4: at most the number of N tiles)
+  // one CTA per 128 x BN output tile, N tiles fastest so that the CTAs reading one P tile run
+  // together and share it through L2
   const int ntn = (N + BN - 1) / BN;
-  int lg = 0;
-  while (lg < 2 && (2 << lg) <= ntn) ++lg;
-  const int C = 1 << lg;
-  dim3 grid((unsigned)((ntn + C - 1) / C * C), (unsigned)((M + TC_BM - 1) / TC_BM));
+  const int64_t ctas = (int64_t)ntn * ((M + TC_BM - 1) / TC_BM);
+  if (ctas < 1 || ctas > INT32_MAX) return cudaErrorInvalidValue;
   const int kblocks = (K + TC_BK - 1) / TC_BK;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = dim3(TC_THREADS);
-  cfg.dynamicSmemBytes = SMEM;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, P.m[lg], Q, M, N, kblocks, k_dev, pairs, out, ldo, row_inv, col_inv, q_inv,
-                            gate, n_dev, col_map, err);
+  kern<<<(unsigned)ctas, TC_THREADS, SMEM, st>>>(P.m[0], Q, M, N, kblocks, k_dev, pairs, out, ldo, row_inv, col_inv,
+                                                q_inv, gate, n_dev, col_map, err, wait_ns, ntn);
+  return cudaGetLastError();
 }
 }  // namespace
 
@@ -815,7 +978,7 @@ cudaError_t launch_tc2_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, 
   constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
   auto kern = k_gemm_tc2<BN, NA, NB, STAGES, F8>;
   cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(TC_THREADS);
+  cfg.blockDim = dim3(TC2_THREADS);
   cfg.dynamicSmemBytes = SMEM;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -846,8 +1009,17 @@ cudaError_t launch_tc2_impl(const PMaps &P, const CUtensorMap &Q, int M, int N, 
   // CUDA graph does not see the parts of the previous replay); a published part sets its flag to 1
   cudaError_t e = cudaMemsetAsync(sk.flags, 0, (size_t)2 * S * sizeof(int), st);
   if (e != cudaSuccess) return e;
+  // the main product's K pieces: as even as possible, at most sk.piece_kb K-blocks each (with
+  // correction products only: the leading-plane products need no FP32-class accuracy)
+  int piece = 0;
+  if (pairs.first_corr >= 0 && sk.piece_kb > 0 && kblocks > sk.piece_kb) {
+    const int npieces = (kblocks + sk.piece_kb - 1) / sk.piece_kb;
+    piece = (kblocks + npieces - 1) / npieces;
+  }
+  // parts are published with epoch 1; owners wait for sk.wait_epoch (1 unless a test asks for parts
+  // that never come)
   return cudaLaunchKernelEx(&cfg, kern, P.m[0], Q, M, N, kblocks, k_dev, pairs, out, ldo, row_inv, col_inv, q_inv,
-                            gate, n_dev, col_map, err, sk.ws, sk.flags, 1);
+                            gate, n_dev, col_map, err, sk.ws, sk.flags, 1, sk.wait_epoch, sk.wait_ns, piece);
 }
 }  // namespace
 
@@ -870,21 +1042,21 @@ constexpr int tc_stages(int na, int nb) {
              : 230400 / (na * TC_BM * 64 * 2 + nb * (TC_PAIR_BN / 2) * 64 * 2);
 }
 
-// the single-CTA kernel with its cluster multicast of P: 128 x (BN / 2) tiles
+// the single-CTA kernel: 128 x (BN / 2) tiles
 cudaError_t launch_gemm_tc_single(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,
                                   const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const float *row_inv,
                                   const float *col_inv, float q_inv, const int *gate, const int *n_dev,
-                                  const int *col_map, int *err, cudaStream_t st) {
+                                  const int *col_map, int *err, uint64_t wait_ns, cudaStream_t st) {
   constexpr int BN1 = TC_PAIR_BN / 2;
   if (na == 2 && nb == 2)
     return launch_tc_impl<BN1, 2, 2, tc_stages(2, 2), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, row_inv, col_inv,
-                                                          q_inv, gate, n_dev, col_map, err, st);
+                                                          q_inv, gate, n_dev, col_map, err, wait_ns, st);
   if (na == 2 && nb == 1)
     return launch_tc_impl<BN1, 2, 1, tc_stages(2, 1), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, row_inv, col_inv,
-                                                          q_inv, gate, n_dev, col_map, err, st);
+                                                          q_inv, gate, n_dev, col_map, err, wait_ns, st);
   if (na == 1 && nb == 1)
     return launch_tc_impl<BN1, 1, 1, tc_stages(1, 1), 64>(P, Q, M, N, K, k_dev, pairs, out, ldo, row_inv, col_inv,
-                                                          q_inv, gate, n_dev, col_map, err, st);
+                                                          q_inv, gate, n_dev, col_map, err, wait_ns, st);
   return cudaErrorInvalidValue;
 }
 }  // namespace
@@ -897,7 +1069,7 @@ cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb,
                            int *err, const TcStreamK &sk, cudaStream_t st) {
   if (M <= TC_BM || !sk.ws || !sk.flags || sk.slots < 1)
     return launch_gemm_tc_single(P, na, Q, nb, M, N, K, k_dev, pairs, out, ldo, row_inv, col_inv, q_inv, gate,
-                                 n_dev, col_map, err, st);
+                                 n_dev, col_map, err, sk.wait_ns, st);
   if (na == 2 && nb == 2)   // two general operands
     return launch_tc2_impl<TC_PAIR_BN, 2, 2, tc_stages(2, 2)>(P, Q, M, N, K, k_dev, pairs, out, ldo, row_inv,
                                                                 col_inv, q_inv, gate, n_dev, col_map, err, sk, st);

@@ -16,21 +16,26 @@ namespace spca {
 __global__ void k_transpose_f32(const float *__restrict__ src, int64_t rows, int64_t cols,
                                 int64_t lds, float *__restrict__ dst, int64_t ldd) {
   __shared__ float tile[32][33];
-  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int64_t r = r0 + k, c = c0 + threadIdx.x;
-    tile[k][threadIdx.x] = (r < rows && c < cols) ? src[r * lds + c] : 0.0f;
-  }
-  __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int64_t c = c0 + k, r = r0 + threadIdx.x;  // dst row = src column
-    if (c < cols && r < rows) dst[c * ldd + r] = tile[threadIdx.x][k];
+  const int64_t c0 = (int64_t)blockIdx.x * 32;
+  // row blocks of 32 on grid y, strided: rows may exceed 32 x 65535 (the grid's y limit)
+  for (int64_t r0 = (int64_t)blockIdx.y * 32; r0 < rows; r0 += (int64_t)gridDim.y * 32) {
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+      const int64_t r = r0 + k, c = c0 + threadIdx.x;
+      tile[k][threadIdx.x] = (r < rows && c < cols) ? src[r * lds + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+      const int64_t c = c0 + k, r = r0 + threadIdx.x;  // dst row = src column
+      if (c < cols && r < rows) dst[c * ldd + r] = tile[threadIdx.x][k];
+    }
+    __syncthreads();
   }
 }
 
 cudaError_t launch_transpose_f32(const float *src, int64_t rows, int64_t cols, int64_t lds,
                                  float *dst, int64_t ldd, cudaStream_t st) {
-  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  const int64_t rb = (rows + 31) / 32;
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)(rb < 65535 ? rb : 65535));
   k_transpose_f32<<<grid, dim3(32, 8), 0, st>>>(src, rows, cols, lds, dst, ldd);
   return cudaGetLastError();
 }

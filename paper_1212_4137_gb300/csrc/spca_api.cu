@@ -816,6 +816,17 @@ int spca_deflate(spca_handle *h, const float *x, int x_is_device) {
   return SPCA_OK;
 }
 
+int spca_set_waits(spca_handle *h, int64_t wait_limit_us, int unpublished_parts) {
+  if (!h) return SPCA_E_INVALID;
+  if (wait_limit_us < 1 || wait_limit_us > 60000000) return fail(h, SPCA_E_INVALID, "wait_limit_us out of range%s");
+  CK(cudaStreamSynchronize(h->stream));
+  release_graphs(h);   // captured launches hold the old settings
+  ++h->ws_gen;
+  h->sk.wait_ns = (uint64_t)wait_limit_us * 1000ull;
+  h->sk.wait_epoch = unpublished_parts ? 2 : 1;   // parts are published as 1
+  return SPCA_OK;
+}
+
 int spca_profile_enable(spca_handle *h, int mask) {
   if (!h || mask < 0 || mask > SPCA_PROFILE_ALL) return SPCA_E_INVALID;
   CK(drain_profile(h));

@@ -309,10 +309,9 @@ cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int
                            int box_rows, int bk);
 int tc_box_rows(int nb);   // Q-operand box height for nb planes (the tile's N)
 int tc_bk(int nb);         // K-block width of the contraction with nb Q planes
-// P-operand maps with 128-, 64- and 32-row boxes (the slice one CTA of a 1-, 2- or 4-CTA
-// cluster loads and multicasts)
+// P-operand map: 128-row boxes of 64-wide K blocks (each CTA loads its own 128 rows)
 struct PMaps {
-  CUtensorMap m[3];     // 64-wide K blocks
+  CUtensorMap m[1];
 };
 cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld, int planes);
 // out[map(c) * ldo + m] = (row_inv[m] q_inv col_inv[c]) sum_q sum_k P_{a_q}[m, k] Q_{b_q}[c, k],
@@ -324,10 +323,20 @@ cudaError_t make_p_maps(PMaps *maps, const void *base, int64_t rows, int64_t ld,
 // Stream-K scratch of the CTA-pair contraction: `slots` parts of tc_sk_floats_per_slot() floats
 // and 2 flags per slot (zeroed by every launch).  Without it (ws == nullptr) the single-CTA kernel
 // runs.
+// Every wait inside the contraction kernels gives up after wait_ns nanoseconds (SPCA_E_TIMEOUT in
+// *err); the owners of split tiles wait for parts flagged wait_epoch (parts are published as 1, so
+// any other value is a flag that nothing sets: the test of the bounded waits).
+// piece_kb: the pair kernel accumulates the main (hi x hi) product of a tile in pieces of at most
+// piece_kb K-blocks (with correction products only), each in a fresh accumulator, the pieces
+// summed in FP32 registers: the tensor core's accumulation truncates, so its error grows with the
+// length of one accumulation.
 struct TcStreamK {
   float *ws = nullptr;
   int *flags = nullptr;
   int slots = 0;
+  uint64_t wait_ns = 2000000000ull;
+  int wait_epoch = 1;
+  int piece_kb = 40;
 };
 int64_t tc_sk_floats_per_slot();
 cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb, int M, int N, int K,

@@ -22,7 +22,7 @@ SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC, SPCA_ENGINE_TC_LOWP = 0, 1, 
 
 # every symbol include/spca.h declares
 EXPORTS = ("spca_create", "spca_create_csr", "spca_clone", "spca_solve", "spca_xstep", "spca_products", "spca_deflate", "spca_profile_enable",
-           "spca_profile_query", "spca_objective_noalloc",
+           "spca_profile_query", "spca_objective_noalloc", "spca_set_waits",
            "spca_destroy", "spca_strerror", "spca_last_error")
 SPCA_K_ALL, SPCA_K_INIT, SPCA_K_U_DENSE, SPCA_K_U_SPARSE, SPCA_K_YSTEP, SPCA_K_V, SPCA_K_XSTEP, \
     SPCA_K_FINALISE, SPCA_K_PREP = range(-1, 8)
@@ -98,6 +98,8 @@ def load(path: str = LIB_PATH):
         lib.spca_objective_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64,
                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                                ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.spca_set_waits.restype = ctypes.c_int
+        lib.spca_set_waits.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
         lib.spca_deflate.restype = ctypes.c_int
         lib.spca_deflate.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         lib.spca_profile_enable.restype = ctypes.c_int
@@ -187,6 +189,10 @@ def spca_deflate(h, x, x_is_device: bool = False) -> int:
     return load().spca_deflate(h, ctypes.c_void_p(ptr), int(x_is_device))
 
 
+def spca_set_waits(h, wait_limit_us: int, unpublished_parts: bool = False) -> int:
+    return load().spca_set_waits(h, int(wait_limit_us), int(unpublished_parts))
+
+
 SPCA_PROFILE_ALL = (1 << 8) - 1
 
 
@@ -255,6 +261,10 @@ class Handle:
     def deflate(self, x, x_device: bool = False):
         """Projection deflation A <- A (I - z z^T), z = x / ||x|| (x: host array or device address)."""
         _check(spca_deflate(self.h, x, x_device), "spca_deflate", self.h)
+
+    def set_waits(self, wait_limit_us: int, unpublished_parts: bool = False):
+        """Limit of the tensor-core kernels' device-side waits; unpublished_parts tests its expiry."""
+        _check(spca_set_waits(self.h, wait_limit_us, unpublished_parts), "spca_set_waits", self.h)
 
     def profile(self, on: bool, kernels=None):
         """Time every kernel (on=True), only the given kernel ids, or nothing (on=False)."""

@@ -98,7 +98,7 @@ def test_bad_arguments_rejected_before_device(lib):
     assert st == lib.SPCA_E_UNSUPPORTED
     f = np.zeros(4)
     so.spca_objective_noalloc.restype = ctypes.c_int
-    for r, want in ((65536, lib.SPCA_E_INVALID), (0, lib.SPCA_E_INVALID)):
+    for r, want in ((65536, lib.SPCA_E_UNSUPPORTED), (0, lib.SPCA_E_INVALID)):
         st = so.spca_objective_noalloc(1, ctypes.c_double(0.0), ctypes.c_void_p(A.ctypes.data), ctypes.c_int64(2),
                                        ctypes.c_int64(3), ctypes.c_int64(3), ctypes.c_void_p(A.ctypes.data),
                                        ctypes.c_int64(3), r, ctypes.c_void_p(f.ctypes.data),
@@ -106,6 +106,8 @@ def test_bad_arguments_rejected_before_device(lib):
         assert st == want, r
     assert so.spca_solve(None, None, None, None) == lib.SPCA_E_INVALID
     assert so.spca_profile_enable(None, 1) == lib.SPCA_E_INVALID
+    so.spca_set_waits.restype = ctypes.c_int
+    assert so.spca_set_waits(None, ctypes.c_int64(1000), 0) == lib.SPCA_E_INVALID
     so.spca_destroy(None)
 
 

@@ -12,6 +12,19 @@ from paper_1212_4137_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
+
+def _f_scale(form, ref):
+    """Magnitude of the terms of the sweep's Table 3 value, the scale of its rounding error: the
+    penalty values are differences, S5 = sum_S v_i^2 - gamma |S| and S6 = x^T v - gamma ||x||_1
+    (x = V_gamma(v) / ||V_gamma(v)||_2), so a relative error eps in v moves them by about eps
+    times |F| + gamma |S| or |F| + gamma ||x||_1."""
+    F, x, g = abs(ref.F[0]), ref.X[0], ref.gamma[0]
+    if form in (5, 6):
+        return F + g * np.count_nonzero(x)
+    if form in (7, 8):
+        return F + g * np.abs(x).sum()
+    return F
+
 OBJ_RTOL = 1e-5
 X_ATOL = 1e-4
 
@@ -217,7 +230,7 @@ def test_single_sweep_parity(lib, oracle, spiked, form, engine):
             if _near_tie(A64, form, Xk[c], 12, fixed_gamma):
                 continue   # the selection boundary is within FP32 noise: either choice is correct
             # S5's value sum(v_i^2) - gamma * nnz cancels: scale its tolerance by the terms
-            scaleF = abs(ref.F[0]) + (ref.gamma[0] * np.count_nonzero(ref.X[0]) if form in (5, 6) else 0.0)
+            scaleF = _f_scale(form, ref)
             assert abs(o1["start_F"][c] - ref.F[0]) <= OBJ_RTOL * max(1.0, scaleF), (k, c)
             err = np.abs(o1["start_x"][c] - ref.X[0]).max()
             worst = max(worst, err)
@@ -261,7 +274,7 @@ def test_single_sweep_parity_candidate_xstep(lib, oracle, form, s, engine):
             fixed_gamma = okw["gamma"] if (form >= 5 and not okw.get("gamma_target")) else None
             if _near_tie(A64, form, Xk[c], s, fixed_gamma):
                 continue
-            scaleF = abs(ref.F[0]) + (ref.gamma[0] * np.count_nonzero(ref.X[0]) if form in (5, 6) else 0.0)
+            scaleF = _f_scale(form, ref)
             assert abs(o1["start_F"][c] - ref.F[0]) <= OBJ_RTOL * max(1.0, scaleF), (k, c)
             err = np.abs(o1["start_x"][c] - ref.X[0]).max()
             assert err <= X_ATOL, (form, k, c, err)
@@ -306,7 +319,7 @@ def test_single_sweep_parity_candidate_lists_overflow(lib, oracle, form, s):
             fixed_gamma = okw["gamma"] if (form >= 5 and not okw.get("gamma_target")) else None
             if _near_tie(A64, form, Xk[c], s, fixed_gamma):
                 continue
-            scaleF = abs(ref.F[0]) + (ref.gamma[0] * np.count_nonzero(ref.X[0]) if form in (5, 6) else 0.0)
+            scaleF = _f_scale(form, ref)
             assert abs(o1["start_F"][c] - ref.F[0]) <= OBJ_RTOL * max(1.0, scaleF), (k, c)
             assert np.abs(o1["start_x"][c] - ref.X[0]).max() <= X_ATOL, (form, k, c)
             assert np.array_equal(o1["start_x"][c] != 0, ref.X[0] != 0), (k, c)
