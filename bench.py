@@ -13,7 +13,7 @@ Metric: AM sweeps x starts per second (the sum over solves of the sweeps each st
 with solves/s and the p50/p99 latency of single solves.  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
-  python bench.py --scan paper-shapes|text-corpus|few-starts|precision|many-problems|serving
+  python bench.py --scan paper-shapes|text-corpus|few-starts|precision|many-problems|serving|economies
 (the scans print one JSON line per case; the clocks sampled during a run go to SPCA_CLOCKS_DIR,
 else the temporary directory)
 """
@@ -457,6 +457,70 @@ def run_scan(args):
               flush=True)
 
 
+# The economies-of-scale experiment of Section 4.2: the L0-penalised L2-variance formulation (5) on N(0,1)
+# matrices with p = 1000, 2000, ..., 32000, l = 256 starting points, at most 10 sweeps each, run in
+# batches of r = 1 (NAI), 4, 16, 64 and 256 (SFA) starts one batch after another.  The paper does not
+# state n; here n = p / 10.  gamma by the Section 4.1 rule targeting 10 nonzeros over the first 5
+# sweeps (the paper does not state gamma either); every start runs exactly 10 sweeps (tol < 0), so
+# all batch sizes do the same work.  Per (p, r): sweeps*starts/s of the whole set of 256 starts and
+# the speedup over r = 1; per p: the FP64 oracle's rate on one host core and on all of them, on a
+# bounded sample.
+ECON_PS = (1000, 2000, 4000, 8000, 16000, 32000)
+ECON_RS = (1, 4, 16, 64, 256)
+
+
+def run_scan_economies(args, l=256, sweeps=10):
+    import torch
+
+    from oracle import oracle
+    from paper_1212_4137_gb300 import build, inputs as I, spca
+    build.build()
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    kw = dict(s=10.0, gamma_target=True, calib=5, max_iter=sweeps, tol=-1)
+    for p in ECON_PS:
+        n = p // 10
+        A = I.gaussian_matrix(n, p, 4000 + p).astype(np.float32)
+        G = I.raw_starts(p, l, 4001).astype(np.float32)
+        Ad, Gd = torch.from_numpy(A).to(dev), torch.from_numpy(G).to(dev)
+        h = spca.Handle(Ad, stream=stream.cuda_stream)
+        rates = {}
+        for r in ECON_RS:
+            batches = [Gd[b:b + r] for b in range(0, l, r)]
+            for _ in range(max(1, args.warmup)):
+                h.solve(5, r, x0=batches[0].data_ptr(), x0_device=True, **kw)
+            torch.cuda.synchronize(dev)
+            best = None
+            for _ in range(max(1, args.steps)):
+                t0 = time.perf_counter()
+                done = 0
+                for xb in batches:
+                    done += h.solve(5, r, x0=xb.data_ptr(), x0_device=True, **kw)["sweeps_total"]
+                dt = time.perf_counter() - t0
+                best = dt if best is None or dt < best else best
+            assert done == l * sweeps
+            rates[r] = l * sweeps / best
+        h.close()
+        # the oracle on a bounded sample: 4 starts on one core, 32 on all cores, 2 sweeps each
+        A64 = A.astype(np.float64)
+        okw = dict(s=10.0, gamma_target=True, calib=5, max_iter=2, tol=-1)
+        t1 = time.perf_counter()
+        o1 = oracle.solve(A64, 5, G[:4].astype(np.float64), nthreads=1, **okw)
+        one = int(o1.iters.sum()) / (time.perf_counter() - t1)
+        t1 = time.perf_counter()
+        oa = oracle.solve(A64, 5, G[:32].astype(np.float64), **okw)
+        allc = int(oa.iters.sum()) / (time.perf_counter() - t1)
+        print(json.dumps({"scan": "economies of scale (Section 4.2), L0-pen L2-var (formulation 5)", "n": n, "p": p,
+                          "l": l, "sweeps": sweeps,
+                          "sweeps_starts_per_s": {f"BAT{r}": round(v, 1) for r, v in rates.items()},
+                          "speedup_vs_NAI": {f"BAT{r}": round(v / rates[1], 2) for r, v in rates.items()},
+                          "oracle_sweeps_starts_per_s": {"1 core": round(one, 1),
+                                                         f"{oracle.num_threads()} cores": round(allc, 1)},
+                          "oracle_sample": "4 starts (1 core) and 32 starts (all cores), 2 sweeps each"}),
+              flush=True)
+
+
 # The text corpora of Section 5 on a synthetic stand-in: a bag-of-words count matrix of the NYTimes
 # corpus's shape (300,000 documents x 102,660 words, about 70 million stored counts; Zipf word
 # popularity, log-normal document lengths, 5 planted topics), kept in compressed sparse rows.  The
@@ -784,7 +848,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     # the paper's shape scan (one JSON line per shape) instead of the benchmark line
     ap.add_argument("--scan", choices=("paper-shapes", "text-corpus", "few-starts", "precision", "many-problems",
-                                       "serving"), default=None)
+                                       "serving", "economies"), default=None)
     ap.add_argument("--rs", type=str, default=None, help="text-corpus scan: comma-separated start counts")
     args = ap.parse_args()
     if args.scan == "text-corpus":
@@ -806,6 +870,9 @@ def main():
         return
     if args.scan == "serving":
         run_scan_serving(args)
+        return
+    if args.scan == "economies":
+        run_scan_economies(args)
         return
     if args.scan:
         run_scan(args)

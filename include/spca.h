@@ -84,9 +84,9 @@ typedef enum {
 /* compute engines for the two contractions of a sweep */
 typedef enum {
     SPCA_ENGINE_AUTO = 0,    /* tensor cores for low-precision sweeps, and for n p r >= 2^26  */
-                             /* unless the starts are few (r <= 8 with r n floats <= 200 KB:  */
-                             /* the CUDA cores' streaming GEMV reads A at HBM speed); else    */
-                             /* CUDA cores (their per-sweep fixed costs dominate small work)  */
+                             /* unless the starts are few (r <= 8: the CUDA cores' streaming  */
+                             /* GEMV reads A once per product at HBM speed); else CUDA cores  */
+                             /* (their per-sweep fixed costs dominate small work)             */
     SPCA_ENGINE_SIMT = 1,    /* FP32 CUDA-core kernels                                        */
     SPCA_ENGINE_TC = 2,      /* tcgen05 tensor-core kernels (TMEM accumulators, TMA loads)    */
     SPCA_ENGINE_TC_LOWP = 3  /* spca_products only: the tensor cores on the low-precision      */

@@ -684,10 +684,11 @@ cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int 
 // out[orow(c)][m] = sum_k P[m, k] Q[qrow(c), k] for the first *count (<= R) starts: the Q rows in
 // shared memory, a warp per row of P (two rows for R >= 4, which then share each read of Q) read
 // once with 16-byte loads, each lane's R sums per row over its strided part, then the warp's
-// sums in a fixed butterfly.
+// sums in a fixed butterfly.  Q rows longer than the shared memory holds are taken in chunks of
+// Kc columns (the row sums carried in registers across the chunks, in K order).
 // P's rows and Q's rows are zero past K up to the next multiple of 4 (padded layouts).
 template <int R, int NR>
-__global__ void __launch_bounds__(512, 1) k_gemv(const float *__restrict__ P, int64_t ldp, int M, int K,
+__global__ void __launch_bounds__(512, 1) k_gemv(const float *__restrict__ P, int64_t ldp, int M, int K, int Kc,
                                                  const float *__restrict__ Q, int64_t ldq,
                                                  const int *__restrict__ rows, const int *__restrict__ count,
                                                  float *__restrict__ out, int64_t ldo, const int *__restrict__ gate) {
@@ -696,14 +697,24 @@ __global__ void __launch_bounds__(512, 1) k_gemv(const float *__restrict__ P, in
   const int cnt = count ? min(*count, R) : R;
   if (cnt <= 0) return;
   const int K4 = (K + 3) / 4, Kp = 4 * K4;
-  for (int c = 0; c < R; ++c) {
-    const float *q = Q + (int64_t)(c < cnt ? (rows ? rows[c] : c) : 0) * ldq;
-    for (int k = threadIdx.x; k < Kp; k += blockDim.x) qs[c * Kp + k] = c < cnt && k < K ? q[k] : 0.0f;
+  const int nchunks = (Kp + Kc - 1) / Kc;
+  // columns [k0, k0 + Kc) of the Q rows into shared memory (zero past K)
+  auto load_q = [&](int k0) {
+    for (int c = 0; c < R; ++c) {
+      const float *q = Q + (int64_t)(c < cnt ? (rows ? rows[c] : c) : 0) * ldq;
+      for (int k = threadIdx.x; k < Kc; k += blockDim.x)
+        qs[c * Kc + k] = c < cnt && k0 + k < K ? q[k0 + k] : 0.0f;
+    }
+  };
+  if (nchunks == 1) {
+    load_q(0);
+    __syncthreads();
   }
-  __syncthreads();
   const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
-  // NR rows per warp and step: every shared-memory read of Q serves all of them
-  for (int m0 = NR * (blockIdx.x * warps + (threadIdx.x >> 5)); m0 < M; m0 += NR * gridDim.x * warps) {
+  // NR rows per warp and step: every shared-memory read of Q serves all of them.  The loop count
+  // is the same for every warp of the CTA (the chunked path synchronises inside it).
+  for (int base = NR * blockIdx.x * warps; base < M; base += NR * gridDim.x * warps) {
+    const int m0 = base + NR * (threadIdx.x >> 5);
     const float4 *pr[NR];
 #pragma unroll
     for (int t = 0; t < NR; ++t) pr[t] = reinterpret_cast<const float4 *>(P + (int64_t)min(m0 + t, M - 1) * ldp);
@@ -712,23 +723,33 @@ __global__ void __launch_bounds__(512, 1) k_gemv(const float *__restrict__ P, in
     for (int t = 0; t < NR; ++t)
 #pragma unroll
       for (int c = 0; c < R; ++c) acc[t][c] = 0.0f;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int k0 = ch * Kc;
+      if (nchunks > 1) {
+        __syncthreads();   // the previous chunk is consumed
+        load_q(k0);
+        __syncthreads();
+      }
+      const int c4 = min(Kc, Kp - k0) / 4;   // float4 columns of this chunk
 #pragma unroll 4
-    for (int k4 = lane; k4 < K4; k4 += 32) {
-      float4 a[NR];
+      for (int k4 = lane; k4 < c4; k4 += 32) {
+        float4 a[NR];
 #pragma unroll
-      for (int t = 0; t < NR; ++t) a[t] = __ldg(pr[t] + k4);
+        for (int t = 0; t < NR; ++t) a[t] = m0 < M ? __ldg(pr[t] + k0 / 4 + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int c = 0; c < R; ++c) {
-        const float4 q = reinterpret_cast<const float4 *>(qs + c * Kp)[k4];
+        for (int c = 0; c < R; ++c) {
+          const float4 q = reinterpret_cast<const float4 *>(qs + c * Kc)[k4];
 #pragma unroll
-        for (int t = 0; t < NR; ++t) {
-          acc[t][c] = fmaf(a[t].x, q.x, acc[t][c]);
-          acc[t][c] = fmaf(a[t].y, q.y, acc[t][c]);
-          acc[t][c] = fmaf(a[t].z, q.z, acc[t][c]);
-          acc[t][c] = fmaf(a[t].w, q.w, acc[t][c]);
+          for (int t = 0; t < NR; ++t) {
+            acc[t][c] = fmaf(a[t].x, q.x, acc[t][c]);
+            acc[t][c] = fmaf(a[t].y, q.y, acc[t][c]);
+            acc[t][c] = fmaf(a[t].z, q.z, acc[t][c]);
+            acc[t][c] = fmaf(a[t].w, q.w, acc[t][c]);
+          }
         }
       }
     }
+    if (m0 >= M) continue;   // uniform over the warp
 #pragma unroll
     for (int t = 0; t < NR; ++t)
 #pragma unroll
@@ -757,23 +778,26 @@ cudaError_t gemv_configured() {
 
 int gemv_width(int r) { return r <= 1 ? 1 : r <= 2 ? 2 : r <= 4 ? 4 : r <= kGemvMaxR ? kGemvMaxR : 0; }
 
-bool gemv_fits(int r, int64_t K) {
-  const int w = gemv_width(r);
-  return w > 0 && (int64_t)w * ((K + 3) / 4 * 4) * 4 <= kGemvSmemMax;
-}
+// any K: Q rows that do not fit in shared memory are streamed in chunks
+bool gemv_fits(int r, int64_t K) { return gemv_width(r) > 0 && K > 0 && K < INT32_MAX; }
 
 cudaError_t launch_gemv(const float *P, int64_t ldp, int M, int K, const float *Q, int64_t ldq, const int *rows,
                         const int *count, int r, float *out, int64_t ldo, const int *gate, int sms, cudaStream_t st) {
   const int w = gemv_width(r);
-  const size_t smem = (size_t)w * ((K + 3) / 4 * 4) * sizeof(float);
-  if (w == 0 || smem > (size_t)kGemvSmemMax) return cudaErrorInvalidValue;
+  if (w == 0 || K < 1) return cudaErrorInvalidValue;
+  const int64_t Kp = (int64_t)(K + 3) / 4 * 4;
+  // chunk of the Q rows held in shared memory: all of them when they fit, else the largest
+  // multiple of 128 columns that fits (whole float4 steps of every lane)
+  int64_t Kc = Kp;
+  if ((int64_t)w * Kp * 4 > kGemvSmemMax) Kc = (int64_t)kGemvSmemMax / (4 * w) / 128 * 128;
+  const size_t smem = (size_t)w * Kc * sizeof(float);
   // CTAs resident per SM by shared memory (two at least for the streaming), a grid of that many
-  // per SM, each CTA loading the Q rows once
+  // per SM, each CTA loading the Q rows once (per row batch when they are chunked)
   const int per_sm = smem <= 48 * 1024 ? 4 : (smem <= 100 * 1024 ? 2 : 1);
   const int blocks = std::min((M + 15) / 16, per_sm * sms);
   auto go = [&](auto kern, cudaError_t configured) -> cudaError_t {
     if (configured != cudaSuccess) return configured;
-    kern<<<blocks, 512, smem, st>>>(P, ldp, M, K, Q, ldq, rows, count, out, ldo, gate);
+    kern<<<blocks, 512, smem, st>>>(P, ldp, M, K, (int)Kc, Q, ldq, rows, count, out, ldo, gate);
     return cudaGetLastError();
   };
   switch (w) {

@@ -234,7 +234,7 @@ cudaError_t launch_fin_csr(SpMat A, SpMat AT, const float *X, int64_t ldx, int c
 
 // Few starts (r <= kGemvMaxR): out[rows[c]][m] = sum_k P[m, k] Q[rows[c], k], c < *count (r when
 // count is null; rows null = identity), m < M, streaming P once with the Q rows in shared memory
-// (at most kGemvSmemMax bytes: gemv_fits); gated
+// (at most kGemvSmemMax bytes of them at a time: longer rows in chunks); gated
 // Size limits from the grid's y dimension (at most 65535 blocks): several kernels put the starts
 // on it, and the finalise puts a dense A's rows there in blocks of 256
 constexpr int kMaxStarts = 65535;

@@ -13,7 +13,10 @@ pytestmark = pytest.mark.gpu
 # the CTA-pair contraction splits tiles over its resident pairs along K (stream-K): the shapes
 # include tiles cut into 16 one-K-block parts (300 x 1003 x 40) and a single start with a long
 # K (4000 x 300 x 1: each tile in about 38 parts), as well as whole tiles
-SHAPES = [(7, 9, 3), (300, 1003, 40), (129, 257, 300), (1000, 3000, 257), (2500, 700, 520), (4000, 300, 1)]
+# and few starts with rows longer than the streaming GEMV's shared memory holds (1200 x 17000 x 5:
+# u = A x streams x in three chunks of 6400 columns)
+SHAPES = [(7, 9, 3), (300, 1003, 40), (129, 257, 300), (1000, 3000, 257), (2500, 700, 520), (4000, 300, 1),
+          (1200, 17000, 5)]
 
 
 @pytest.fixture(scope="module")
