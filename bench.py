@@ -679,7 +679,24 @@ def run_scan_small_r(args):
 # (4 significant bits, the tensor cores' 8-bit kind).  Per formulation and mode: the solve's wall time
 # (CUDA events), sweeps*starts/s, and the best objective (FP64-class finalise) with its relative
 # difference from the plain FP32 solve's.
-def run_scan_precision(args):
+# The precision configuration: spiked 20000 x 50000 (5 spikes of 100 nonzeros), FP32 A, 4096 starts,
+# formulations 1 and 2 with s = 100, at most 60 sweeps, tol 1e-9.  Plain FP32 sweeps against
+# schedules with a window of low-precision sweeps (A's 16-bit leading plane: 11 significant bits
+# with per-row power-of-two scales; or the E4M3 copy of an FP8 handle: 4 significant bits with
+# per-row and per-column power-of-two scales), FP32 accumulation throughout:
+#   F10+L40: 10 FP32 sweeps (they decide which stationary point a start reaches), 40
+#            low-precision sweeps, FP32 sweeps to the end;
+#   L20:     the low-precision sweeps first (20), then FP32 (scan only).
+# Per mode: solve time (CUDA events on the stream), sweeps*starts/s, the best objective and its
+# relative difference from plain FP32's (the metric's bar is a shortfall of at most 1e-3).
+PRECISION_MODES = (("fp32", "f32", {}),
+                   ("fp16-plane F10+L40", "f32", {"lowp_first": 10, "lowp_sweeps": 40}),
+                   ("fp8 F10+L40", "fp8", {"lowp_first": 10, "lowp_sweeps": 40}))
+PRECISION_SCAN_EXTRA = (("fp16-plane L20", "f32", {"lowp_sweeps": 20}),
+                        ("fp8 L20", "fp8", {"lowp_sweeps": 20}))
+
+
+def precision_measure(modes, steps=1, warmup=1):
     import torch
 
     from paper_1212_4137_gb300 import build, inputs as I, spca
@@ -689,19 +706,20 @@ def run_scan_precision(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     Ad = torch.from_numpy(A).to(dev)
-    h = spca.Handle(Ad, stream=stream.cuda_stream)
-    h8 = spca.Handle(Ad, stream=stream.cuda_stream, storage=spca.SPCA_FP8_E4M3_COLSCALED)
+    handles = {"f32": spca.Handle(Ad, stream=stream.cuda_stream),
+               "fp8": spca.Handle(Ad, stream=stream.cuda_stream, storage=spca.SPCA_FP8_E4M3_COLSCALED)}
     del A, Ad
+    rows = []
     for form in (1, 2):
-        best = {}
-        for mode, hh, extra in (("fp32", h, {}), ("lowp20+fp32", h, {"lowp_sweeps": 20}),
-                                ("fp8-lowp20+fp32", h8, {"lowp_sweeps": 20})):
+        base = None
+        for name, hk, extra in modes:
+            hh = handles[hk]
             kw = dict(s=float(s), seed=20001, max_iter=60, tol=1e-9, **extra)
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 hh.solve(form, r, **kw)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ms, sweeps, out = 0.0, 0, None
-            for _ in range(max(1, args.steps)):
+            for _ in range(max(1, steps)):
                 torch.cuda.synchronize(dev)
                 e0.record(stream)
                 out = hh.solve(form, r, **kw)
@@ -709,16 +727,27 @@ def run_scan_precision(args):
                 torch.cuda.synchronize(dev)
                 ms += e0.elapsed_time(e1)
                 sweeps += out["sweeps_total"]
-            best[mode] = out["objective"]
-            line = {"scan": "precision, spiked 20000 x 50000, 4096 starts", "form": form, "mode": mode, "s": s,
-                    "solve_ms": round(ms / max(1, args.steps), 2), "sweeps_starts_per_s": round(sweeps / (ms / 1e3), 1),
-                    "sweeps_per_start": round(out["sweeps_total"] / r, 2), "best_objective": out["objective"],
-                    "best_nnz": int(out["nnz"])}
-            if mode != "fp32":
-                line["rel_diff_vs_fp32"] = (out["objective"] - best["fp32"]) / abs(best["fp32"])
-            print(json.dumps(line), flush=True)
-    h.close()
-    h8.close()
+            ms /= max(1, steps)
+            row = {"form": form, "mode": name, "solve_ms": round(ms, 2),
+                   "sweeps_starts_per_s": round(sweeps / max(1, steps) / (ms / 1e3), 1),
+                   "sweeps_per_start": round(out["sweeps_total"] / r, 2), "best_objective": out["objective"],
+                   "best_nnz": int(out["nnz"])}
+            if base is None:
+                base = row
+            else:
+                row["speedup_vs_fp32"] = round(base["solve_ms"] / ms, 3)
+                row["best_rel_vs_fp32"] = (out["objective"] - base["best_objective"]) / abs(base["best_objective"])
+            rows.append(row)
+    for hh in handles.values():
+        hh.close()
+    return rows
+
+
+def run_scan_precision(args):
+    for row in precision_measure(PRECISION_MODES + PRECISION_SCAN_EXTRA, steps=args.steps, warmup=args.warmup):
+        row = dict(row)
+        row["scan"] = "precision, spiked 20000 x 50000, 4096 starts, s = 100, <= 60 sweeps, tol 1e-9"
+        print(json.dumps(row), flush=True)
 
 
 def _log_uniform(rng, lo, hi):
@@ -846,6 +875,7 @@ def main():
     # for profiler captures: a subset of the formulations, no end-to-end pass
     ap.add_argument("--forms", type=str, default=None, help="comma-separated formulations (default: all 8)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the precision configuration's extra key")
     # the paper's shape scan (one JSON line per shape) instead of the benchmark line
     ap.add_argument("--scan", choices=("paper-shapes", "text-corpus", "few-starts", "precision", "many-problems",
                                        "serving", "economies"), default=None)
@@ -889,6 +919,13 @@ def main():
             from paper_1212_4137_gb300 import inputs as I
             G = I.raw_starts(w["p"], w["r"], w["start_seed"]).astype(np.float32)
             line["cpu_baseline"] = cpu_baseline(w, make_inputs(w), G)
+        if line is not None and world == 1 and not args.no_precision and args.workload == DEFAULT_WORKLOAD:
+            # the precision configuration (not part of the timed region above): one solve per mode
+            # and formulation after one warm-up
+            line["precision"] = {
+                "workload": "spiked 20000 x 50000, 4096 starts, formulations 1 and 2, s = 100, <= 60 sweeps, "
+                            "tol 1e-9; low-precision window of 40 sweeps after 10 FP32 sweeps",
+                "results": precision_measure(PRECISION_MODES)}
     if line is not None:
         print(json.dumps(line), flush=True)
     if _dist is not None:

@@ -43,11 +43,13 @@ typedef enum {
     SPCA_E_UNSUPPORTED = 6   /* a valid request the library does not implement                     */
 } spca_status;
 
-/* element types */
+/* element types (the low-precision storage is FP16 with power-of-two row scales rather than
+ * BF16: the same bytes and tensor-core rate, three more significant bits, and the row scales
+ * cover the range BF16's wider exponent would) */
 typedef enum {
     SPCA_F32 = 0,
     SPCA_F64 = 1,
-    SPCA_BF16 = 2,
+    SPCA_FP16 = 2,            /* storage only: a 16-bit FP16 copy of A, row-scaled (see spca_create) */
     SPCA_FP8_E4M3_COLSCALED = 3
 } spca_dtype;
 
@@ -101,11 +103,12 @@ typedef enum {
  *                device memory (a_is_device = 1).  Copied; the caller may free it on return.
  *                The library does not centre the columns (the paper assumes centred data,
  *                Section 1).
- *   storage      SPCA_F32, SPCA_BF16 (a 16-bit copy for the low-precision sweeps,
+ *   storage      SPCA_F32, SPCA_FP16 (a 16-bit copy for the low-precision sweeps,
  *                spca_params.lowp_sweeps) or SPCA_FP8_E4M3_COLSCALED.  All keep the FP32 master
  *                copy and the tensor-core operand format: two FP16 planes of a row-scaled copy
- *                (hi + lo carries 22 significant bits); with SPCA_BF16 the low-precision sweeps
- *                read the leading plane (A rounded to 11 significant bits, finer than BF16's 8).
+ *                (hi + lo carries 22 significant bits); the 16-bit copy is the leading plane
+ *                (A rounded to 11 significant bits with one power-of-two scale per row), which
+ *                the low-precision sweeps of SPCA_F32 and SPCA_FP16 handles read.
  *                SPCA_FP8_E4M3_COLSCALED adds E4M3 copies of A and of A^T with power-of-two
  *                scales per row of A and per column of A (A rounded to 4 significant bits; the
  *                largest entry of a row or column in [128, 256)); the low-precision sweeps then
@@ -188,13 +191,17 @@ int spca_clone(spca_handle **out, spca_handle *src, void *cuda_stream);
  *                       element (c, j) of the r x p block is normal number c*p + j.
  *   x0_is_device        x0 is a device pointer (1) or a host pointer (0).
  *   engine              spca_engine.
- *   lowp_sweeps         the first lowp_sweeps sweeps read A rounded to 11 significant bits
+ *   lowp_sweeps         lowp_sweeps sweeps (after the first lowp_first ones) read A rounded to
+ *                       11 significant bits
  *                       (the leading FP16 plane: one tensor-core product per tile in v = A^T y
  *                       and u = A x, and an FP16 support gather), y's leading plane, FP32
  *                       accumulation;
  *                       no start stops during them.  Then FP32 sweeps refine every start
  *                       to the stopping rule.  0 = FP32 throughout.  Needs the tensor-core
  *                       engine (SPCA_E_UNSUPPORTED otherwise).
+ *   lowp_first          FP32 sweeps before the low-precision ones (0 = the low-precision
+ *                       sweeps come first).  The early sweeps decide which stationary point a
+ *                       start reaches; running them in FP32 keeps each start on its FP32 path.
  *   refine_sweeps       at most this many FP32 sweeps after the low-precision ones
  *                       (0 = up to max_iter sweeps in all).
  *   timeout_us          wall-clock limit of the solve in microseconds (0 = none), checked
@@ -225,6 +232,7 @@ typedef struct {
     int refine_sweeps;
     int64_t timeout_us;
     int total_starts;
+    int lowp_first;
 } spca_params;
 
 /*

@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------- planes
-// dst plane t (t < nplanes) of element e: the t-th BF16 piece of src (hi, mid, lo)
+// dst plane t (t < nplanes) of element e: the t-th FP16 piece of the scaled src (hi, lo)
 __global__ void k_split_planes(const float *__restrict__ src, int64_t rows, int64_t cols, int64_t lds,
                                __half *__restrict__ dst, int64_t ldd, int64_t plane_stride, int nplanes,
                                const float *__restrict__ row_scale, float scale, const int *__restrict__ gate,
@@ -908,7 +908,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 }  // namespace
 
-// 3-D map over `planes` BF16 planes of `rows` x `ld` (K-contiguous), box bk x box_rows x 1
+// 3-D map over `planes` FP16 planes of `rows` x `ld` (K-contiguous), box bk x box_rows x 1
 cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int64_t ld, int planes,
                            int box_rows, int bk) {
   auto enc = get_encode();

@@ -890,7 +890,7 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
   if (n < 1 || p < 1 || lda < p || n > INT32_MAX || p > INT32_MAX) return SPCA_E_INVALID;
   if (n > kMaxDenseRows) return SPCA_E_UNSUPPORTED;
   if (in_dtype != SPCA_F32 && in_dtype != SPCA_F64) return SPCA_E_INVALID;
-  if (storage != SPCA_F32 && storage != SPCA_BF16 && storage != SPCA_FP8_E4M3_COLSCALED) {
+  if (storage != SPCA_F32 && storage != SPCA_FP16 && storage != SPCA_FP8_E4M3_COLSCALED) {
     if (storage == SPCA_F64) return SPCA_E_UNSUPPORTED;
     return SPCA_E_INVALID;
   }
@@ -916,7 +916,7 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
     h->tc_ok = major >= 10;
     CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
-    if ((storage == SPCA_BF16 || storage == SPCA_FP8_E4M3_COLSCALED) && !h->tc_ok)
+    if ((storage == SPCA_FP16 || storage == SPCA_FP8_E4M3_COLSCALED) && !h->tc_ok)
       return SPCA_E_UNSUPPORTED;   // the planes need tcgen05
     h->fp8 = storage == SPCA_FP8_E4M3_COLSCALED;
     CK(cudaMallocHost((void **)&h->h_ctrl, 2 * sizeof(Ctrl)));
@@ -1192,8 +1192,8 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   if (!std::isfinite(P.tol)) return fail(h, SPCA_E_INVALID, "tol must be finite%s");
   const bool target = is_pen(form) && P.gamma_mode == SPCA_GAMMA_TARGET_NNZ;
   if (target && P.gamma_calib_sweeps < 1) return fail(h, SPCA_E_INVALID, "gamma_calib_sweeps must be >= 1%s");
-  if (P.lowp_sweeps < 0 || P.refine_sweeps < 0 || P.timeout_us < 0)
-    return fail(h, SPCA_E_INVALID, "lowp_sweeps, refine_sweeps and timeout_us must be >= 0%s");
+  if (P.lowp_sweeps < 0 || P.refine_sweeps < 0 || P.timeout_us < 0 || P.lowp_first < 0)
+    return fail(h, SPCA_E_INVALID, "lowp_sweeps, lowp_first, refine_sweeps and timeout_us must be >= 0%s");
   int engine;
   RC(resolve_engine(h, P.engine, P.r, P.lowp_sweeps > 0, &engine));
   if (P.lowp_sweeps > 0 && engine != SPCA_ENGINE_TC)
@@ -1206,8 +1206,9 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     return fail(h, SPCA_E_UNSUPPORTED, "low-precision sweeps with on-the-fly replacement%s");
   RC(enter(h));
   const auto t_start = std::chrono::steady_clock::now();
-  const int L = P.lowp_sweeps;
-  const int max_iter = P.refine_sweeps > 0 ? (int)std::min<int64_t>(P.max_iter, (int64_t)L + P.refine_sweeps)
+  // low-precision sweeps: F0 FP32 sweeps first, then L low-precision ones, then FP32 again
+  const int L = P.lowp_sweeps, F0 = L > 0 ? P.lowp_first : 0;
+  const int max_iter = P.refine_sweeps > 0 ? (int)std::min<int64_t>(P.max_iter, (int64_t)F0 + L + P.refine_sweeps)
                                            : P.max_iter;
 
   const int r = P.r, n = (int)h->n, p = (int)h->p;
@@ -1282,7 +1283,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   xa.schedule = 1;
   xa.target = target ? 1 : 0;
   xa.calib_sweeps = C;
-  xa.lowp_sweeps = L;
+  xa.lowp_sweeps = F0 + L;   // the stopping rule compares FP32 sweeps after the window
   xa.stop_enabled = P.tol >= 0.0 ? 1 : 0;
   // the host queues this many sweeps before it reads the active count back; every path decision
   // inside a sweep is taken on the device from the control word
@@ -1372,7 +1373,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     memcpy(&b, &d, sizeof b);
     return b;
   };
-  const std::vector<int> solve_key = {form, engine, r, l, (int)(x0src != nullptr), max_iter, C, L, (int)target,
+  const std::vector<int> solve_key = {form, engine, r, l, (int)(x0src != nullptr), max_iter, C, L, F0, (int)target,
                                       h->defl_k,
                                       (int)(bits(P.s) & 0xffffffff), (int)(bits(P.s) >> 32),
                                       (int)(bits(P.gamma) & 0xffffffff), (int)(bits(P.gamma) >> 32),
@@ -1395,13 +1396,14 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     for (int k = k0; k <= k1; ++k) {
       SweepPlan pl{};
       pl.k = k;
-      // the first L sweeps read the leading FP16 planes only (A rounded to 11 significant bits)
-      pl.lowp = k <= L;
+      // sweeps F0 + 1 .. F0 + L read the low-precision copy of A (the leading FP16 plane or E4M3)
+      pl.lowp = k > F0 && k <= F0 + L;
       pl.dense_in = dense_queued;
       pl.union_in = union_built;
       dense_queued = max_nnz > sparse_cap / 2;
       pl.sparse_cap = dense_queued ? sparse_cap : p;   // p: the gather for every support
-      union_built = engine == SPCA_ENGINE_TC && !otf && k + 1 > L && sum_nnz <= (int64_t)kUnionTry * h->kcap &&
+      const bool next_lowp = k + 1 > F0 && k + 1 <= F0 + L;
+      union_built = engine == SPCA_ENGINE_TC && !otf && !next_lowp && sum_nnz <= (int64_t)kUnionTry * h->kcap &&
                     h->n * sum_nnz >= kUnionMinReads;
       pl.union_out = union_built;
       plans.push_back(pl);

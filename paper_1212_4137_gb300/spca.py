@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libspca.so")
 
 SPCA_OK, SPCA_E_INVALID, SPCA_E_NOMEM, SPCA_E_CUDA, SPCA_E_TIMEOUT, SPCA_E_BUSY, SPCA_E_UNSUPPORTED = range(7)
-SPCA_F32, SPCA_F64, SPCA_BF16, SPCA_FP8_E4M3_COLSCALED = range(4)
+SPCA_F32, SPCA_F64, SPCA_FP16, SPCA_FP8_E4M3_COLSCALED = range(4)
 SPCA_GAMMA_FIXED, SPCA_GAMMA_TARGET_NNZ = 0, 1
 SPCA_ST_MAXITER, SPCA_ST_CONVERGED, SPCA_ST_DEGENERATE = 0, 1, 2
 SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC, SPCA_ENGINE_TC_LOWP = 0, 1, 2, 3
@@ -37,7 +37,7 @@ class spca_params(ctypes.Structure):
                 ("r", ctypes.c_int), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("x0_is_device", ctypes.c_int), ("engine", ctypes.c_int),
                 ("lowp_sweeps", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("timeout_us", ctypes.c_int64),
-                ("total_starts", ctypes.c_int)]
+                ("total_starts", ctypes.c_int), ("lowp_first", ctypes.c_int)]
 
 
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -291,14 +291,15 @@ class Handle:
 
     def solve(self, form, r, s=1.0, gamma=0.0, gamma_target=False, calib=10, max_iter=100,
               tol=1e-9, x0=None, seed=0, engine=SPCA_ENGINE_AUTO, want_starts=False, x0_device=False,
-              lowp_sweeps=0, refine_sweeps=0, timeout_us=0, total_starts=0):
+              lowp_sweeps=0, refine_sweeps=0, timeout_us=0, total_starts=0, lowp_first=0):
         """Returns a dict of numpy results.  x0: r x p float32 host array, device address
         (x0_device=True), or None for seeded starts."""
         prm = spca_params(form=form, s=s, gamma=gamma,
                           gamma_mode=SPCA_GAMMA_TARGET_NNZ if gamma_target else SPCA_GAMMA_FIXED,
                           gamma_calib_sweeps=calib, r=r, max_iter=max_iter, tol=tol, seed=seed,
                           x0_is_device=int(x0_device), engine=engine, lowp_sweeps=lowp_sweeps,
-                          refine_sweeps=refine_sweeps, timeout_us=timeout_us, total_starts=total_starts)
+                          refine_sweeps=refine_sweeps, timeout_us=timeout_us, total_starts=total_starts,
+                          lowp_first=lowp_first)
         n, p = self.n, self.p
         nres = max(r, total_starts)
         out = {"x": np.zeros(p, np.float32), "y": np.zeros(n, np.float32),

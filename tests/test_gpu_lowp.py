@@ -113,10 +113,10 @@ def test_lowp_needs_tensor_cores_engine(lib, spiked):
     h.close()
 
 
-def test_bf16_storage_handle(lib, spiked):
+def test_fp16_storage_handle(lib, spiked):
     A, G = spiked
     h32 = lib.Handle(A)
-    h16 = lib.Handle(A, storage=lib.SPCA_BF16)
+    h16 = lib.Handle(A, storage=lib.SPCA_FP16)
     a = h32.solve(2, 24, x0=G[:24], s=20.0, max_iter=30, tol=-1, lowp_sweeps=10)
     b = h16.solve(2, 24, x0=G[:24], s=20.0, max_iter=30, tol=-1, lowp_sweeps=10)
     h32.close()
@@ -138,7 +138,7 @@ def _products_lowp(lib, h, form, X):
     return Ud.cpu().numpy().astype(np.float64), Vd.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("storage,eps", [("bf16", 2.0 ** -12), ("fp8", 2.0 ** -4)])
+@pytest.mark.parametrize("storage,eps", [("fp16", 2.0 ** -12), ("fp8", 2.0 ** -4)])
 @pytest.mark.parametrize("form", [1, 2])
 def test_lowp_contractions_within_rounding(lib, spiked, storage, eps, form):
     """u = A x and v = A^T y on the low-precision copies.  Both operands are rounded to nearest
@@ -150,7 +150,7 @@ def test_lowp_contractions_within_rounding(lib, spiked, storage, eps, form):
     r = 40
     X = G[:r].copy()
     X[3, :: 2] = 0.0
-    st = {"bf16": lib.SPCA_BF16, "fp8": lib.SPCA_FP8_E4M3_COLSCALED}[storage]
+    st = {"fp16": lib.SPCA_FP16, "fp8": lib.SPCA_FP8_E4M3_COLSCALED}[storage]
     h = lib.Handle(A, storage=st)
     U, V = _products_lowp(lib, h, form, X)
     h.close()
@@ -178,3 +178,33 @@ def test_fp8_storage_handle(lib, spiked):
     h8.close()
     assert a["objective"] == b["objective"] and np.array_equal(a["support"], b["support"])
     assert np.all(out["start_iters"] == 40)
+
+
+def test_lowp_first_schedule(lib, oracle, spiked):
+    """lowp_first = F runs F FP32 sweeps before the low-precision window (sweeps F+1 .. F+L), then
+    FP32 again: a solve that stops at F sweeps is bit for bit the plain FP32 solve; no start
+    stops inside the window or before two FP32 sweeps after it; every per-start objective is the
+    FP64 objective of the returned x; and a window that starts after the basin is fixed leaves
+    most starts where plain FP32 sweeps take them."""
+    A, G = spiked
+    r, F, L = 24, 6, 10
+    h = lib.Handle(A)
+    tc = lib.SPCA_ENGINE_TC   # the low-precision sweeps run on the tensor cores: compare like with like
+    plain = h.solve(1, r, x0=G[:r], s=20.0, max_iter=F, tol=-1, engine=tc, want_starts=True)
+    early = h.solve(1, r, x0=G[:r], s=20.0, max_iter=F, tol=-1, lowp_sweeps=L, lowp_first=F, engine=tc,
+                    want_starts=True)
+    assert np.array_equal(plain["start_x"], early["start_x"])
+    out = h.solve(1, r, x0=G[:r], s=20.0, max_iter=60, tol=1e-6, lowp_sweeps=L, lowp_first=F, want_starts=True)
+    ok = out["start_status"] != lib.SPCA_ST_DEGENERATE
+    assert np.all(out["start_iters"][ok] >= F + L + 2)
+    A64 = A.astype(np.float64)
+    for c in range(r):
+        fo, _ = oracle.objective(A64, 1, 0.0, out["start_x"][c].astype(np.float64))
+        assert abs(out["start_objective"][c] - fo) <= 1e-9 * max(1.0, abs(fo))
+    ref = h.solve(1, r, x0=G[:r], s=20.0, max_iter=60, tol=1e-6, engine=tc, want_starts=True)
+    same = [np.array_equal(out["start_x"][c] != 0, ref["start_x"][c] != 0) for c in range(r)]
+    assert np.mean(same) >= 0.75
+    with pytest.raises(lib.SpcaError) as e:
+        h.solve(1, r, x0=G[:r], s=20.0, lowp_sweeps=L, lowp_first=-1)
+    assert e.value.status == lib.SPCA_E_INVALID
+    h.close()
