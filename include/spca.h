@@ -421,6 +421,53 @@ int spca_objective_noalloc(int form, double gamma, const float *A, int64_t n, in
  */
 int spca_set_waits(spca_handle *h, int64_t wait_limit_us, int unpublished_parts);
 
+/*
+ * Groups of problems: Algorithm 2 for many independent problems in one solve, each with its own
+ * matrix (a handle), formulation, s or gamma and starts (the batching of Section 4 carried across
+ * problems).  Every phase of a sweep is one launch over all problems: the dense u = A x of the
+ * first sweep and v = A^T y of every sweep as one persistent tensor-core launch over the tiles of
+ * all problems, the support gather, y-step, x-step (full pass) and active lists as one launch each
+ * over all starts or problems; the sweeps are captured into CUDA graphs and replayed.  Each
+ * problem's results are those spca_solve gives for it alone, up to the order of rounding in the
+ * contractions (the same FP32-class arithmetic).
+ *
+ * spca_group_create -- a group object: its own stream and a workspace grown on demand.
+ *   cuda_stream  as in spca_create: each solve starts after the work queued on it.
+ * spca_group_destroy -- free it (waits for its stream); NULL is a no-op.
+ * spca_group_last_error -- static text for the group's last failure ("" if none).
+ *
+ * spca_solve_group -- solve `count` problems (1 .. 1024).  Problem i:
+ *   h     a handle from spca_create (dense A) on a device with tensor cores, or a clone of one;
+ *         read only (several problems may share a handle).
+ *   prm   as for spca_solve, with lowp_sweeps = 0, total_starts <= r, engine AUTO or TC,
+ *         r in 1 .. 65535; timeout_us is not checked; the support gather serves every support
+ *         after the first sweep.
+ *   x0    r x p starts (host or device per prm.x0_is_device), or NULL for seeded starts (the
+ *         same starts as spca_solve with that seed).
+ *   res   caller-owned host buffers as for spca_solve (results of this problem).
+ * tiles   the tile shape of the grouped contraction: tile_n (64 or 128 columns) and stages (2..4
+ *         for 64, 2..3 for 128); NULL or {0, 0} = 64 columns, 4 stages.  bench.py --tune times the
+ *         shapes per problem mix and the chosen shape is passed here.
+ * Errors: SPCA_E_INVALID (arguments, a problem's parameters, non-finite x0; spca_group_last_error
+ *         says which), SPCA_E_UNSUPPORTED (more than 1024 problems), SPCA_E_NOMEM, SPCA_E_CUDA,
+ *         SPCA_E_TIMEOUT (a bounded device-side wait gave up).
+ */
+typedef struct spca_group spca_group;
+typedef struct {
+    spca_handle *h;
+    spca_params prm;
+    const float *x0;
+    spca_result *res;
+} spca_problem;
+typedef struct {
+    int tile_n;
+    int stages;
+} spca_group_tiles;
+int spca_group_create(spca_group **out, void *cuda_stream);
+void spca_group_destroy(spca_group *g);
+const char *spca_group_last_error(const spca_group *g);
+int spca_solve_group(spca_group *g, spca_problem *probs, int count, const spca_group_tiles *tiles);
+
 /* spca_destroy -- free the handle's device memory (waits for its stream). NULL is a no-op. */
 void spca_destroy(spca_handle *h);
 

@@ -71,17 +71,6 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// non-blocking test of the same
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 // wait for the phase with the given parity; false (and *err set) after wait_ns nanoseconds, or
 // at once when another thread of the CTA has given up (*abort_flag)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag,
@@ -413,6 +402,11 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 }
 __device__ __forceinline__ void st_release(int *p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// order earlier generic-proxy writes of a tensor map in global memory before tensor loads through it
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+               : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_local(uint32_t bar) {
   asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -1094,6 +1088,261 @@ cudaError_t launch_gemm_tc_f8(const PMaps &P, const CUtensorMap &Q, int M, int N
   hi.first_corr = -1;
   return launch_tc2_impl<TC_PAIR_BN, 1, 1, tc_stages(1, 1), true>(P, Q, M, N, K, k_dev, hi, out, ldo, row_inv,
                                                                   col_inv, q_inv, gate, n_dev, col_map, err, sk, st);
+}
+
+// ---------------------------------------------------------------------- grouped contraction
+// One persistent launch over the tiles of many independent contractions (one per problem of a
+// group): task i computes out_i[map(c) * ldo + m] = (row_inv[m] q_inv col_inv[c]) sum_q sum_k
+// P_i,a_q[m, k] Q_i,b_q[c, k] for m < M_i and c < *n_dev_i, like launch_gemm_tc, each with its own
+// tensor maps (held in global memory), K, plane products and output.  The tiles (128 x BN) of all
+// tasks form one list, numbered task by task (the host orders the tasks by falling K so that the
+// round-robin below balances); CTA b takes tiles b, b + G, b + 2G, ...  Every role of a CTA walks
+// the same tile sequence, so no tile index is exchanged between them.
+// TMEM: NBUF = 512 / (4 BN) buffers of four accumulators (BN = 64: two buffers, so a tile's
+// epilogue overlaps the next tile's MMAs).  The hi x hi product of K-block kb goes to accumulator
+// kb mod 3 and the correction products to the fourth (FP32-class accuracy, see k_gemm_tc).
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_grouped(const GTask *__restrict__ tasks, int ntasks, int total_tiles, int *err, uint64_t wait_ns) {
+  constexpr int NA = 2, NBMAX = 2;
+  constexpr uint32_t A_BYTES = TC_BM * 64 * 2;            // 16 KB per P plane tile
+  constexpr uint32_t B_BYTES = BN * 64 * 2;               // one Q plane tile (BN rows)
+  constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NBMAX * B_BYTES;
+  constexpr int NBUF = 512 / (4 * BN);
+  constexpr uint32_t TMEM_COLS = 512;
+  static_assert(NBUF >= 1, "TMEM");
+
+  extern __shared__ __align__(1024) uint8_t dsmem[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar[NBUF], tmem_empty_bar[NBUF],
+      mma_done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  __shared__ int issued, consumed;
+  __shared__ int s_tile0[kGroupMaxTasks + 1];
+
+  const int G = gridDim.x;
+  if ((int)blockIdx.x >= total_tiles) return;
+  uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < ntasks; i += blockDim.x) s_tile0[i] = tasks[i].tile0;
+  if (threadIdx.x == 0) {
+    s_tile0[ntasks] = total_tiles;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(smem_u32(&accum_bar[b]), 1);
+      mbar_init(smem_u32(&tmem_empty_bar[b]), 4);   // the four epilogue warps
+    }
+    mbar_init(smem_u32(&mma_done_bar), 1);            // the MMA issuer's last commit
+    abort_flag = 0;
+    issued = consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  // tile t -> (task, M tile, N tile); false when the tile lies past the task's active columns
+  auto locate = [&](int t, int &ti, int &m0, int &n0, int &N) -> bool {
+    int lo = 0, hi = ntasks - 1;   // the last task whose first tile is <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_tile0[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    ti = lo;
+    const GTask &T = tasks[ti];
+    const int local = t - s_tile0[ti];
+    const int tn = local % T.nt, tm = local / T.nt;
+    m0 = tm * TC_BM;
+    n0 = tn * BN;
+    N = T.n_dev ? *T.n_dev : T.nmax;
+    return n0 < N && T.kblocks > 0;
+  };
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    uint32_t it = 0;
+    bool ok = true;
+    int last_task = -1;
+    for (int t = blockIdx.x; t < total_tiles && ok; t += G) {
+      int ti, m0, n0, N;
+      if (!locate(t, ti, m0, n0, N)) continue;
+      const GTask &T = tasks[ti];
+      if (ti != last_task) {
+        // the maps live in global memory and may have been rewritten since an earlier launch:
+        // order those writes before this CTA's tensor loads through them
+        tensormap_acquire(T.pmap);
+        tensormap_acquire(T.qmap);
+        last_task = ti;
+      }
+      const uint32_t bytes = NA * A_BYTES + (uint32_t)T.nb * B_BYTES;
+      for (int kb = 0; kb < T.kblocks; ++kb, ++it) {
+        const int s = (int)(it % STAGES);
+        const uint32_t ph = (it / STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, err, &abort_flag, wait_ns)) { ok = false; break; }
+        const uint32_t fb = smem_u32(&full_bar[s]);
+        mbar_expect_tx(fb, bytes);
+        uint8_t *st = tiles + (size_t)s * STAGE_BYTES;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) tma_load_3d(smem_u32(st + a * A_BYTES), T.pmap, kb * 64, m0, a, fb);
+        for (int b = 0; b < T.nb; ++b)
+#pragma unroll
+          for (int h = 0; h < BN / 64; ++h)
+            tma_load_3d(smem_u32(st + NA * A_BYTES + b * B_BYTES + h * 64 * 128), T.qmap, kb * 64, n0 + 64 * h, b,
+                        fb);
+      }
+    }
+    issued = (int)it;
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------------- MMA issuer
+    constexpr uint32_t idesc = idesc_f16(TC_BM, BN);
+    uint32_t it = 0, ntile = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < total_tiles && ok; t += G) {
+      int ti, m0, n0, N;
+      if (!locate(t, ti, m0, n0, N)) continue;
+      const GTask &T = tasks[ti];
+      const TcPairs pairs = T.pairs;
+      const int b = (int)(ntile % NBUF);
+      // this buffer's previous tile has been read by the epilogue
+      if (ntile >= (uint32_t)NBUF &&
+          !mbar_wait(smem_u32(&tmem_empty_bar[b]), ((ntile / NBUF) - 1) & 1u, err, &abort_flag, wait_ns)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t dbase = tmem + (uint32_t)(b * 4 * BN);
+      for (int kb = 0; kb < T.kblocks; ++kb, ++it) {
+        const int s = (int)(it % STAGES);
+        const uint32_t ph = (it / STAGES) & 1u;
+        if (!mbar_wait(smem_u32(&full_bar[s]), ph, err, &abort_flag, wait_ns)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = smem_u32(tiles + (size_t)s * STAGE_BYTES);
+        for (int q = 0; q < pairs.n; ++q) {
+          const uint32_t a_base = st + pairs.a[q] * A_BYTES;
+          const uint32_t b_base = st + NA * A_BYTES + pairs.b[q] * B_BYTES;
+          const bool main = (pairs.a[q] | pairs.b[q]) == 0;
+          const uint32_t d = dbase + (uint32_t)BN * (main ? (uint32_t)(kb % 3) : 3u);
+          const bool first = main ? (kb < 3 && q == pairs.first_main) : (kb == 0 && q == pairs.first_corr);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            mma_bf16(d, sw_desc<64>(a_base + kk * 32), sw_desc<64>(b_base + kk * 32), idesc,
+                     (first && kk == 0) ? 0u : 1u);
+        }
+        mma_commit(smem_u32(&empty_bar[s]));
+      }
+      if (!ok) break;
+      mma_commit(smem_u32(&accum_bar[b]));
+      ++ntile;
+    }
+    consumed = (int)it;
+    mma_commit(smem_u32(&mma_done_bar));   // completes once every MMA issued so far is done
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------------- epilogue
+    const int quad = warp & 3;
+    const int row_l = quad * 32 + lane;
+    uint32_t ntile = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < total_tiles && ok; t += G) {
+      int ti, m0, n0, N;
+      if (!locate(t, ti, m0, n0, N)) continue;
+      const GTask &T = tasks[ti];
+      const int b = (int)(ntile % NBUF);
+      ok = __all_sync(0xffffffffu,
+                      mbar_wait(smem_u32(&accum_bar[b]), (ntile / NBUF) & 1u, err, &abort_flag, wait_ns) &&
+                          !abort_flag);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int nused = T.kblocks < 3 ? T.kblocks : 3;
+      const bool corr = T.pairs.first_corr >= 0;
+      const int row = m0 + row_l;
+      const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 4 * BN);
+#pragma unroll 1
+      for (int cb = 0; cb < BN / 32; ++cb) {
+        float v[32], w[32];
+        tmem_ld32(tb + (uint32_t)(cb * 32), v);
+        for (int i = 1; i < nused; ++i) {
+          tmem_ld32(tb + (uint32_t)(i * BN + cb * 32), w);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += w[j];
+        }
+        if (corr) {
+          tmem_ld32(tb + (uint32_t)(3 * BN + cb * 32), w);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += w[j];
+        }
+        if (row < T.M) {
+          const float sc = (T.row_inv ? T.row_inv[row] : 1.0f) * T.q_inv;   // powers of two
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + cb * 32 + j;
+            if (col < N)
+              T.out[(int64_t)(T.col_map ? T.col_map[col] : col) * T.ldo + row] =
+                  v[j] * sc * (T.col_inv ? T.col_inv[col] : 1.0f);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_local(smem_u32(&tmem_empty_bar[b]));
+      ++ntile;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // every MMA is done before TMEM is freed; after a wait gave up, the loads issued but not
+    // consumed also land (bounded) before the CTA exits
+    mbar_wait_quiet(smem_u32(&mma_done_bar), 0, wait_ns);
+    if (abort_flag)
+      for (int q = consumed; q < issued; ++q)
+        mbar_wait_quiet(smem_u32(&full_bar[q % STAGES]), (uint32_t)(q / STAGES) & 1u, TC_DRAIN_NS);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+namespace {
+template <int BN, int STAGES>
+cudaError_t launch_grouped_impl(const GTask *tasks, int ntasks, int total_tiles, int grid, int *err,
+                                uint64_t wait_ns, cudaStream_t st) {
+  constexpr int STAGE_BYTES = 2 * TC_BM * 64 * 2 + 2 * BN * 64 * 2;
+  constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+  auto kern = k_gemm_grouped<BN, STAGES>;
+  static const cudaError_t configured = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+  if (configured != cudaSuccess) return configured;
+  kern<<<grid, TC_THREADS, SMEM, st>>>(tasks, ntasks, total_tiles, err, wait_ns);
+  return cudaGetLastError();
+}
+}  // namespace
+
+bool grouped_config_ok(int bn, int stages) {
+  return (bn == 64 && (stages == 2 || stages == 3 || stages == 4)) || (bn == 128 && (stages == 2 || stages == 3));
+}
+
+cudaError_t launch_gemm_grouped(const GTask *tasks, int ntasks, int total_tiles, int bn, int stages, int sms, int *err,
+                                uint64_t wait_ns, cudaStream_t st) {
+  if (ntasks < 1 || ntasks > kGroupMaxTasks || total_tiles < 1) return cudaErrorInvalidValue;
+  const int grid = total_tiles < sms ? total_tiles : sms;
+  if (bn == 64 && stages == 2) return launch_grouped_impl<64, 2>(tasks, ntasks, total_tiles, grid, err, wait_ns, st);
+  if (bn == 64 && stages == 3) return launch_grouped_impl<64, 3>(tasks, ntasks, total_tiles, grid, err, wait_ns, st);
+  if (bn == 64 && stages == 4) return launch_grouped_impl<64, 4>(tasks, ntasks, total_tiles, grid, err, wait_ns, st);
+  if (bn == 128 && stages == 2) return launch_grouped_impl<128, 2>(tasks, ntasks, total_tiles, grid, err, wait_ns, st);
+  if (bn == 128 && stages == 3) return launch_grouped_impl<128, 3>(tasks, ntasks, total_tiles, grid, err, wait_ns, st);
+  return cudaErrorInvalidValue;
 }
 
 int tc_box_rows(int nb) { (void)nb; return TC_PAIR_BN / 2; }

@@ -1024,6 +1024,39 @@ __global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int 
 }
 }  // namespace
 
+// groups of problems: the full pass for every active start of every problem, persistent CTAs over
+// the global starts (v staged in shared memory when the longest v fits)
+template <bool kSmem>
+__global__ void __launch_bounds__(XT) k_g_xstep(const GProb *__restrict__ P, const int *__restrict__ prob, int R,
+                                                int parity) {
+  extern __shared__ float vsm[];
+  __shared__ XShared sh;
+  for (int g = blockIdx.x; g < R; g += gridDim.x) {
+    const GProb &q = P[prob[g]];
+    const int c = g - q.start0;
+    StartState st = q.st;
+    if (st.status[c] != ST_ACTIVE) continue;
+    st.xfast = nullptr;
+    xstep_full_one(q.xa, c, q.V, q.ldX, q.X, q.ldX, st, q.sup_idx, q.sup_val, q.ctrl[parity], kSmem ? vsm : nullptr,
+                   sh);
+    __syncthreads();   // shared memory is reused by the next start
+  }
+}
+
+cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p, int parity, int sms, cudaStream_t st) {
+  const size_t bytes = (size_t)max_p * sizeof(float);
+  if (bytes <= (size_t)XSTEP_SMEM_MAX) {
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(k_g_xstep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, XSTEP_SMEM_MAX);
+    if (configured != cudaSuccess) return configured;
+    const int per_sm = bytes <= 100u * 1024u ? 2 : 1;
+    k_g_xstep<true><<<min(R, per_sm * sms), XT, bytes, st>>>(P, prob, R, parity);
+  } else {
+    k_g_xstep<false><<<min(R, 2 * sms), XT, 0, st>>>(P, prob, R, parity);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,
                          StartState s, int *sup_idx, float *sup_val, Ctrl *ctrl_next, XstepScratch scratch,
                          cudaStream_t st) {

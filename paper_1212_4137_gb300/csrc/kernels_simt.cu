@@ -109,17 +109,11 @@ __device__ __forceinline__ double bm_normal(uint64_t key, uint64_t i) {
   return (i & 1) ? rad * sin(ang) : rad * cos(ang);
 }
 
-// Algorithm 2, "select initial point": x^(0) = g / ||g||_2 per start (block per start).
-__global__ void __launch_bounds__(256) k_start_init(const float *__restrict__ x0, int64_t ld0,
-                                                    uint64_t key, int p, float *__restrict__ X,
-                                                    int64_t ldX, StartState s, double gamma0,
-                                                    const int *__restrict__ slot_list,
-                                                    const int *__restrict__ slot_start,
-                                                    const int *__restrict__ count) {
-  __shared__ float redf[32];
-  if (slot_list && (int)blockIdx.x >= *count) return;
-  const int c = slot_list ? slot_list[blockIdx.x] : (int)blockIdx.x;   // the slot (row of X)
-  const int64_t start = slot_list ? slot_start[c] : c;                 // the start it takes
+// Algorithm 2, "select initial point": x^(0) = g / ||g||_2 for the start in row c of X, taking
+// start `start` (its row of x0, or normal numbers start * p + j of the seeded stream).
+__device__ void start_init_body(const float *__restrict__ x0, int64_t ld0, uint64_t key, int p,
+                                float *__restrict__ X, int64_t ldX, StartState s, double gamma0, int c,
+                                int64_t start, float *redf) {
   float *x = X + (int64_t)c * ldX;
   const float *g = x0 ? x0 + start * ld0 : nullptr;
   float part = 0.0f;
@@ -143,6 +137,20 @@ __global__ void __launch_bounds__(256) k_start_init(const float *__restrict__ x0
   }
 }
 
+// block per start (or per listed slot)
+__global__ void __launch_bounds__(256) k_start_init(const float *__restrict__ x0, int64_t ld0,
+                                                    uint64_t key, int p, float *__restrict__ X,
+                                                    int64_t ldX, StartState s, double gamma0,
+                                                    const int *__restrict__ slot_list,
+                                                    const int *__restrict__ slot_start,
+                                                    const int *__restrict__ count) {
+  __shared__ float redf[32];
+  if (slot_list && (int)blockIdx.x >= *count) return;
+  const int c = slot_list ? slot_list[blockIdx.x] : (int)blockIdx.x;   // the slot (row of X)
+  const int64_t start = slot_list ? slot_start[c] : c;                 // the start it takes
+  start_init_body(x0, ld0, key, p, X, ldX, s, gamma0, c, start, redf);
+}
+
 cudaError_t launch_start_init(const float *x0, int64_t ld0, uint64_t seed, int r, int p, float *X,
                               int64_t ldX, StartState s, double gamma0, const int *slot_list,
                               const int *slot_start, const int *count, cudaStream_t st) {
@@ -161,13 +169,9 @@ cudaError_t launch_start_init(const float *x0, int64_t ld0, uint64_t seed, int r
 // Counts the sweep for every active start; L1 variance: y = sgn(u) with sgn(0) = +1;
 // L2 variance: y = u / ||u||_2, and ||u||_2 = 0 ends the start as degenerate (x = 0).
 // y goes to Y (FP32) and/or to the FP16 planes of kQScale y (hi, lo; one exact plane for +-1).
-__global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict__ U, int64_t ldu,
-                                               int n, float *__restrict__ Y,
-                                               __half *__restrict__ Ypl, int64_t pstride,
-                                               const int *__restrict__ rank, StartState s,
-                                               float *__restrict__ X, int64_t ldX, int p) {
-  __shared__ float redf[32];
-  const int c = blockIdx.x;
+__device__ void ystep_body(int form, const float *__restrict__ U, int64_t ldu, int n, float *__restrict__ Y,
+                           __half *__restrict__ Ypl, int64_t pstride, const int *__restrict__ rank, StartState s,
+                           float *__restrict__ X, int64_t ldX, int p, int c, float *redf) {
   if (s.status[c] != ST_ACTIVE) return;
   const float *u = U + (int64_t)c * ldu;
   float *y = Y ? Y + (int64_t)c * ldu : nullptr;
@@ -250,6 +254,15 @@ __global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict
       yp[i + pstride] = lo;
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_ystep(int form, const float *__restrict__ U, int64_t ldu,
+                                               int n, float *__restrict__ Y,
+                                               __half *__restrict__ Ypl, int64_t pstride,
+                                               const int *__restrict__ rank, StartState s,
+                                               float *__restrict__ X, int64_t ldX, int p) {
+  __shared__ float redf[32];
+  ystep_body(form, U, ldu, n, Y, Ypl, pstride, rank, s, X, ldX, p, (int)blockIdx.x, redf);
 }
 
 // The same for long u (n > 2 kYChunk), where one CTA per start would be latency-bound: a CTA per
@@ -340,9 +353,8 @@ cudaError_t launch_ystep(int form, const float *U, int64_t ldu, int n, int r, fl
 
 // ------------------------------------------------------------------ active-start list
 // one CTA: ordered compaction of the flags status[c] == ST_ACTIVE over r starts
-__global__ void __launch_bounds__(1024) k_active_list(const int *__restrict__ status, const int *__restrict__ nnz,
-                                                      int r, int *__restrict__ act, int *__restrict__ rank,
-                                                      Ctrl *__restrict__ ctrl) {
+__device__ void active_list_body(const int *__restrict__ status, const int *__restrict__ nnz, int r,
+                                 int *__restrict__ act, int *__restrict__ rank, Ctrl *__restrict__ ctrl) {
   __shared__ int red[32];
   __shared__ long long red_l[32];
   __shared__ int red_m[32];
@@ -386,6 +398,12 @@ __global__ void __launch_bounds__(1024) k_active_list(const int *__restrict__ st
     ctrl->use_gather = (ctrl->need_dense == 0 && base_pos > 0) ? 1 : 0;
     ctrl->sum_nnz = (int)(t < 0x7fffffffLL ? t : 0x7fffffffLL);
   }
+}
+
+__global__ void __launch_bounds__(1024) k_active_list(const int *__restrict__ status, const int *__restrict__ nnz,
+                                                      int r, int *__restrict__ act, int *__restrict__ rank,
+                                                      Ctrl *__restrict__ ctrl) {
+  active_list_body(status, nnz, r, act, rank, ctrl);
 }
 
 cudaError_t launch_active_list(const int *status, const int *nnz, int r, int *act, int *rank, Ctrl *c,
@@ -477,22 +495,17 @@ cudaError_t launch_gemm_nt_f32(const float *P, int64_t ldp, const float *Q, int6
 // 37 MB per row block for 18,000 distinct columns) stay in L2, and a column used by several
 // starts is read from DRAM about once.
 constexpr int kGatherThreads = 128;
-__global__ void __launch_bounds__(kGatherThreads) k_gemm1_sparse(const float *__restrict__ AT, int64_t ldat,
-                                                      int n, const int *__restrict__ sup_idx,
-                                                      const float *__restrict__ sup_val, int cap,
-                                                      StartState s, float *__restrict__ U,
-                                                      int64_t ldu, const int *__restrict__ gate) {
-  if (*gate == 0) return;
-  const int c = blockIdx.x;
+// rows 4 (yb kGatherThreads + t) .. + 3 of u = A x for start c (block of kGatherThreads threads)
+__device__ void gather_body(const float *__restrict__ AT, int64_t ldat, int n, const int *__restrict__ sup_idx,
+                            const float *__restrict__ sup_val, int cap, StartState s, float *__restrict__ U,
+                            int64_t ldu, int c, int yb, int *sidx, float *sval) {
   if (s.status[c] != ST_ACTIVE) return;
   if (s.iters[c] == 0) return;   // a start not swept yet has a dense x: the dense contraction
-  __shared__ int sidx[kGatherThreads];
-  __shared__ float sval[kGatherThreads];
   const int nnz = s.nnz[c];
   // four consecutive rows per thread, read as one 16-byte vector (ldat is a multiple of 8, so
   // the rows up to the padded width are in bounds); eight columns' loads are issued before
   // their FMAs, which still run in support order
-  const int i4 = (blockIdx.y * kGatherThreads + threadIdx.x) * 4;
+  const int i4 = (yb * kGatherThreads + threadIdx.x) * 4;
   const int *gi = sup_idx + (int64_t)c * cap;
   const float *gv = sup_val + (int64_t)c * cap;
   float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -669,6 +682,17 @@ cudaError_t launch_gemm1_sparse_lowp(const void *AT0, int64_t ldat, const float 
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(kGatherThreads) k_gemm1_sparse(const float *__restrict__ AT, int64_t ldat,
+                                                      int n, const int *__restrict__ sup_idx,
+                                                      const float *__restrict__ sup_val, int cap,
+                                                      StartState s, float *__restrict__ U,
+                                                      int64_t ldu, const int *__restrict__ gate) {
+  __shared__ int sidx[kGatherThreads];
+  __shared__ float sval[kGatherThreads];
+  if (*gate == 0) return;
+  gather_body(AT, ldat, n, sup_idx, sup_val, cap, s, U, ldu, (int)blockIdx.x, (int)blockIdx.y, sidx, sval);
+}
+
 cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int *sup_idx,
                                 const float *sup_val, int cap, StartState s, int r, float *U,
                                 int64_t ldu, const int *gate, cudaStream_t st) {
@@ -677,6 +701,95 @@ cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int 
   if (blocks > 65535) return cudaErrorInvalidValue;   // grid y limit: n above 33.5 million rows
   dim3 grid((unsigned)r, (unsigned)blocks);
   k_gemm1_sparse<<<grid, kGatherThreads, 0, st>>>(AT, ldat, n, sup_idx, sup_val, cap, s, U, ldu, gate);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ groups of problems
+// The per-start phases for all problems of a group in one launch each: block g (or blockIdx.x for
+// the per-problem active lists) looks its problem up and runs the single-problem body on that
+// problem's blocks of the workspace.
+__global__ void __launch_bounds__(256) k_g_start_init(const GProb *__restrict__ P, const int *__restrict__ prob) {
+  __shared__ float redf[32];
+  const GProb &q = P[prob[blockIdx.x]];
+  const int c = (int)blockIdx.x - q.start0;
+  start_init_body(q.x0, q.ld0, q.key, q.p, q.X, q.ldX, q.st, q.gamma0, c, c, redf);
+}
+
+cudaError_t launch_g_start_init(const GProb *P, const int *prob, int R, cudaStream_t st) {
+  k_g_start_init<<<R, 256, 0, st>>>(P, prob);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(1024) k_g_active(const GProb *__restrict__ P, int parity) {
+  const GProb &q = P[blockIdx.x];
+  active_list_body(q.st.status, q.st.nnz, q.r, q.act, q.rank, q.ctrl[parity]);
+}
+
+cudaError_t launch_g_active(const GProb *P, int np, int parity, cudaStream_t st) {
+  k_g_active<<<np, 1024, 0, st>>>(P, parity);
+  return cudaGetLastError();
+}
+
+// FP16 planes of x for the dense u = A x (the first sweep): per active start, the power-of-two
+// scale putting max |x_j| in [2^13, 2^14), then hi = fp16(s x), lo = fp16(s x - hi) at the start's
+// packed row (its rank), and 1 / s at the same index
+__global__ void __launch_bounds__(256) k_g_xplanes(const GProb *__restrict__ P, const int *__restrict__ prob) {
+  __shared__ unsigned red[32];
+  const GProb &q = P[prob[blockIdx.x]];
+  const int c = (int)blockIdx.x - q.start0;
+  if (q.st.status[c] != ST_ACTIVE) return;
+  const float *x = q.X + (int64_t)c * q.ldX;
+  unsigned mk = 0u;
+  for (int j = threadIdx.x; j < q.p; j += blockDim.x) mk = max(mk, __float_as_uint(fabsf(x[j])));
+  const unsigned m = block_max_u(mk, red);
+  int e = 0;
+  if (m != 0u) e = max(-120, min(120, 13 - ilogbf(__uint_as_float(m))));
+  const float sc = ldexpf(1.0f, e);
+  const int row = q.rank[c];
+  __half *hi = q.Xpl + (int64_t)row * q.ldX;
+  for (int j = threadIdx.x; j < q.p; j += blockDim.x) {
+    const float a = x[j] * sc;
+    const __half h = __float2half_rn(a);
+    hi[j] = h;
+    hi[j + q.xps] = __float2half_rn(a - __half2float(h));
+  }
+  if (threadIdx.x == 0) {
+    q.x_scale[row] = sc;
+    q.x_inv[row] = ldexpf(1.0f, -e);
+  }
+}
+
+cudaError_t launch_g_xplanes(const GProb *P, const int *prob, int R, cudaStream_t st) {
+  k_g_xplanes<<<R, 256, 0, st>>>(P, prob);
+  return cudaGetLastError();
+}
+
+// grid (R, row blocks of the largest n): blocks past a problem's n exit
+__global__ void __launch_bounds__(kGatherThreads) k_g_gather(const GProb *__restrict__ P, const int *__restrict__ prob) {
+  __shared__ int sidx[kGatherThreads];
+  __shared__ float sval[kGatherThreads];
+  const GProb &q = P[prob[blockIdx.x]];
+  if ((int)blockIdx.y * 4 * kGatherThreads >= q.n) return;
+  const int c = (int)blockIdx.x - q.start0;
+  gather_body(q.AT32, q.ldAT, q.n, q.sup_idx, q.sup_val, q.p, q.st, q.U, q.ldU, c, (int)blockIdx.y, sidx, sval);
+}
+
+cudaError_t launch_g_gather(const GProb *P, const int *prob, int R, int max_n, cudaStream_t st) {
+  const int blocks = (max_n + 4 * kGatherThreads - 1) / (4 * kGatherThreads);
+  if (blocks > 65535 || R > 0x7fffffff) return cudaErrorInvalidValue;
+  k_g_gather<<<dim3((unsigned)R, (unsigned)blocks), kGatherThreads, 0, st>>>(P, prob);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_g_ystep(const GProb *__restrict__ P, const int *__restrict__ prob) {
+  __shared__ float redf[32];
+  const GProb &q = P[prob[blockIdx.x]];
+  const int c = (int)blockIdx.x - q.start0;
+  ystep_body(q.form, q.U, q.ldU, q.n, nullptr, q.Ypl, q.yps, q.rank, q.st, q.X, q.ldX, q.p, c, redf);
+}
+
+cudaError_t launch_g_ystep(const GProb *P, const int *prob, int R, cudaStream_t st) {
+  k_g_ystep<<<R, 256, 0, st>>>(P, prob);
   return cudaGetLastError();
 }
 

@@ -13,8 +13,10 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <vector>
 
@@ -304,6 +306,37 @@ struct TcPairs {      // plane products P plane a[q] x Q plane b[q], q < n; the 
   int first_corr;
   unsigned char a[8], b[8];
 };
+// plane products of the two contractions: hi x hi into the main accumulator, then the two
+// correction products hi x lo and lo x hi (two general operands), or lo x (+-1) when y = +-1 is
+// a single exact plane; pairs_hi: the leading planes only (low-precision sweeps)
+inline TcPairs pairs_general() {
+  TcPairs q{};
+  q.n = 3;
+  q.a[0] = 0; q.b[0] = 0;
+  q.a[1] = 1; q.b[1] = 0;
+  q.a[2] = 0; q.b[2] = 1;
+  q.first_main = 0;
+  q.first_corr = 1;
+  return q;
+}
+inline TcPairs pairs_sign() {
+  TcPairs q{};
+  q.n = 2;
+  q.a[0] = 0; q.b[0] = 0;
+  q.a[1] = 1; q.b[1] = 0;
+  q.first_main = 0;
+  q.first_corr = 1;
+  return q;
+}
+inline TcPairs pairs_hi() {
+  TcPairs t{};
+  t.n = 1;
+  t.first_main = 0;
+  t.first_corr = -1;
+  t.a[0] = 0;
+  t.b[0] = 0;
+  return t;
+}
 // 3-D TMA map over `planes` FP16 planes of rows x ld (K-contiguous), box 64 x box_rows
 cudaError_t make_plane_map(CUtensorMap *map, const void *base, int64_t rows, int64_t ld, int planes,
                            int box_rows, int bk);
@@ -343,6 +376,68 @@ cudaError_t launch_gemm_tc(const PMaps &P, int na, const CUtensorMap &Q, int nb,
                            const int *k_dev, TcPairs pairs, float *out, int64_t ldo, const float *row_inv,
                            const float *col_inv, float q_inv, const int *gate, const int *n_dev, const int *col_map,
                            int *err, const TcStreamK &sk, cudaStream_t st);
+// threshold in |v| units for U_gamma: the largest float t with t <= sqrt(gamma), so that for
+// every float v, |v| > t  <=>  v^2 > gamma
+inline float u_threshold(double gamma) {
+  const double r = std::sqrt(gamma);
+  float t = (float)r;
+  if ((double)t > r) t = std::nextafterf(t, 0.0f);
+  return t;
+}
+
+// ---------------------------------------------------------------- groups of problems
+// One problem of a group solve: its matrix (from its handle) and its blocks of the group's
+// workspace (r starts, one vector per row), in device memory.  The per-start scalars (st) of all
+// problems are consecutive: problem i's starts are global starts start0 .. start0 + r - 1.
+struct GProb {
+  int n, p, r, start0, form;
+  int64_t ldX, ldU, ldAT;
+  const float *AT32;            // A^T (p x ldAT): the support gather reads columns of A as its rows
+  float *X, *V, *U;             // r x ldX, r x ldX, r x ldU
+  __half *Xpl, *Ypl;            // two FP16 planes each (x row-scaled, y scaled by kQScale), packed rows
+  int64_t xps, yps;             // plane strides (elements)
+  float *x_scale, *x_inv;       // per packed row of Xpl
+  int *sup_idx;                 // r x p support lists (index, value)
+  float *sup_val;
+  int *act, *rank;              // active list (r)
+  Ctrl *ctrl[2];                // control word of each sweep parity
+  StartState st;
+  XstepArgs xa;
+  const float *x0;              // starts (r x ld0, device) or null (seeded: key)
+  int64_t ld0;
+  uint64_t key;
+  double gamma0;
+};
+// the phases of a sweep for every problem of a group, one launch each (prob[g] = the problem of
+// global start g, R starts in all)
+cudaError_t launch_g_start_init(const GProb *P, const int *prob, int R, cudaStream_t st);
+cudaError_t launch_g_active(const GProb *P, int np, int parity, cudaStream_t st);
+cudaError_t launch_g_xplanes(const GProb *P, const int *prob, int R, cudaStream_t st);
+cudaError_t launch_g_gather(const GProb *P, const int *prob, int R, int max_n, cudaStream_t st);
+cudaError_t launch_g_ystep(const GProb *P, const int *prob, int R, cudaStream_t st);
+cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p, int parity, int sms, cudaStream_t st);
+
+// Grouped contraction: one persistent launch over the tiles of many contractions (one per problem
+// of a group), each described by a task in device memory.  pmap / qmap are device addresses of
+// tensor maps (P: 128-row boxes over two FP16 planes; Q: 64-row boxes over nb planes), 64-byte
+// aligned.  Tile shapes: (bn, stages) in {64: 2, 3, 4; 128: 2, 3} (grouped_config_ok).
+constexpr int kGroupMaxTasks = 1024;
+struct GTask {
+  const CUtensorMap *pmap, *qmap;
+  int M, kblocks, nmax, nb;     // output rows, K-blocks (of 64), column bound, Q planes loaded
+  const int *n_dev;             // active columns (device; <= nmax), or null for nmax
+  const int *col_map;           // output row of column c (null = c)
+  float *out;
+  int64_t ldo;
+  const float *row_inv, *col_inv;
+  float q_inv;
+  TcPairs pairs;
+  int tile0, mt, nt;            // first tile in the launch's list; M and N tiles (N tiles of bn)
+};
+bool grouped_config_ok(int bn, int stages);
+cudaError_t launch_gemm_grouped(const GTask *tasks, int ntasks, int total_tiles, int bn, int stages, int sms, int *err,
+                                uint64_t wait_ns, cudaStream_t st);
+
 // FP16 planes (hi, lo; the first nplanes) of a scaled FP32 matrix, plane t at dst + t *
 // plane_stride elements: destination row r is source row row_map[r] (identity when null) times
 // row_scale[r] (or `scale` when row_scale is null), r < rows (*rows_dev when given); gated

@@ -23,6 +23,7 @@ SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC, SPCA_ENGINE_TC_LOWP = 0, 1, 
 # every symbol include/spca.h declares
 EXPORTS = ("spca_create", "spca_create_csr", "spca_clone", "spca_solve", "spca_xstep", "spca_products", "spca_deflate", "spca_profile_enable",
            "spca_profile_query", "spca_objective_noalloc", "spca_set_waits",
+           "spca_group_create", "spca_group_destroy", "spca_group_last_error", "spca_solve_group",
            "spca_destroy", "spca_strerror", "spca_last_error")
 SPCA_K_ALL, SPCA_K_INIT, SPCA_K_U_DENSE, SPCA_K_U_SPARSE, SPCA_K_YSTEP, SPCA_K_V, SPCA_K_XSTEP, \
     SPCA_K_FINALISE, SPCA_K_PREP = range(-1, 8)
@@ -54,6 +55,15 @@ class spca_result(ctypes.Structure):
                 ("x", _fp), ("y", _fp), ("support", _i64p), ("start_objective", _dp),
                 ("start_explained", _dp), ("start_F", _dp), ("start_iters", _ip),
                 ("start_status", _ip), ("start_gamma", _dp), ("start_x", _fp)]
+
+
+class spca_problem(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_void_p), ("prm", spca_params), ("x0", ctypes.c_void_p),
+                ("res", ctypes.POINTER(spca_result))]
+
+
+class spca_group_tiles(ctypes.Structure):
+    _fields_ = [("tile_n", ctypes.c_int), ("stages", ctypes.c_int)]
 
 
 class SpcaError(RuntimeError):
@@ -98,6 +108,15 @@ def load(path: str = LIB_PATH):
         lib.spca_objective_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64,
                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                                ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.spca_group_create.restype = ctypes.c_int
+        lib.spca_group_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]
+        lib.spca_group_destroy.restype = None
+        lib.spca_group_destroy.argtypes = [ctypes.c_void_p]
+        lib.spca_group_last_error.restype = ctypes.c_char_p
+        lib.spca_group_last_error.argtypes = [ctypes.c_void_p]
+        lib.spca_solve_group.restype = ctypes.c_int
+        lib.spca_solve_group.argtypes = [ctypes.c_void_p, ctypes.POINTER(spca_problem), ctypes.c_int,
+                                         ctypes.POINTER(spca_group_tiles)]
         lib.spca_set_waits.restype = ctypes.c_int
         lib.spca_set_waits.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
         lib.spca_deflate.restype = ctypes.c_int
@@ -294,29 +313,101 @@ class Handle:
               lowp_sweeps=0, refine_sweeps=0, timeout_us=0, total_starts=0, lowp_first=0):
         """Returns a dict of numpy results.  x0: r x p float32 host array, device address
         (x0_device=True), or None for seeded starts."""
-        prm = spca_params(form=form, s=s, gamma=gamma,
-                          gamma_mode=SPCA_GAMMA_TARGET_NNZ if gamma_target else SPCA_GAMMA_FIXED,
-                          gamma_calib_sweeps=calib, r=r, max_iter=max_iter, tol=tol, seed=seed,
-                          x0_is_device=int(x0_device), engine=engine, lowp_sweeps=lowp_sweeps,
+        prm = make_params(form, r, s=s, gamma=gamma, gamma_target=gamma_target, calib=calib, max_iter=max_iter,
+                          tol=tol, seed=seed, x0_device=x0_device, engine=engine, lowp_sweeps=lowp_sweeps,
                           refine_sweeps=refine_sweeps, timeout_us=timeout_us, total_starts=total_starts,
                           lowp_first=lowp_first)
-        n, p = self.n, self.p
         nres = max(r, total_starts)
-        out = {"x": np.zeros(p, np.float32), "y": np.zeros(n, np.float32),
-               "support": np.zeros(p, np.int64)}
-        if want_starts:
-            out.update(start_objective=np.zeros(nres), start_explained=np.zeros(nres), start_F=np.zeros(nres),
-                       start_iters=np.zeros(nres, np.int32), start_status=np.zeros(nres, np.int32),
-                       start_gamma=np.zeros(nres), start_x=np.zeros((nres, p), np.float32))
-        res = spca_result()
-        for k, v in out.items():
-            setattr(res, k, v.ctypes.data_as(type(getattr(res, k))))
+        out, res = _result_buffers(self.n, self.p, nres, want_starts)
         if x0 is not None and not x0_device:
             x0 = np.ascontiguousarray(x0, dtype=np.float32)
-            assert x0.shape == (nres, p)
+            assert x0.shape == (nres, self.p)
         _check(spca_solve(self.h, prm, x0, res), "spca_solve", self.h)
-        out["support"] = out["support"][:res.nnz]
-        for k in ("objective", "explained_variance", "gamma", "best_start", "best_iters", "best_status",
-                  "converged", "degenerate", "sweeps_total", "nnz"):
-            out[k] = getattr(res, k)
-        return out
+        return _result_dict(out, res)
+
+
+def make_params(form, r, s=1.0, gamma=0.0, gamma_target=False, calib=10, max_iter=100, tol=1e-9, seed=0,
+                x0_device=False, engine=SPCA_ENGINE_AUTO, lowp_sweeps=0, refine_sweeps=0, timeout_us=0,
+                total_starts=0, lowp_first=0) -> spca_params:
+    return spca_params(form=form, s=s, gamma=gamma,
+                       gamma_mode=SPCA_GAMMA_TARGET_NNZ if gamma_target else SPCA_GAMMA_FIXED,
+                       gamma_calib_sweeps=calib, r=r, max_iter=max_iter, tol=tol, seed=seed,
+                       x0_is_device=int(x0_device), engine=engine, lowp_sweeps=lowp_sweeps,
+                       refine_sweeps=refine_sweeps, timeout_us=timeout_us, total_starts=total_starts,
+                       lowp_first=lowp_first)
+
+
+def _result_buffers(n, p, nres, want_starts):
+    out = {"x": np.zeros(p, np.float32), "y": np.zeros(n, np.float32), "support": np.zeros(p, np.int64)}
+    if want_starts:
+        out.update(start_objective=np.zeros(nres), start_explained=np.zeros(nres), start_F=np.zeros(nres),
+                   start_iters=np.zeros(nres, np.int32), start_status=np.zeros(nres, np.int32),
+                   start_gamma=np.zeros(nres), start_x=np.zeros((nres, p), np.float32))
+    res = spca_result()
+    for k, v in out.items():
+        setattr(res, k, v.ctypes.data_as(type(getattr(res, k))))
+    return out, res
+
+
+def _result_dict(out, res):
+    out["support"] = out["support"][:res.nnz]
+    for k in ("objective", "explained_variance", "gamma", "best_start", "best_iters", "best_status",
+              "converged", "degenerate", "sweeps_total", "nnz"):
+        out[k] = getattr(res, k)
+    return out
+
+
+class Group:
+    """Owns an spca_group: many problems solved together, each sweep phase one launch over all."""
+
+    def __init__(self, stream: int = 0):
+        g = ctypes.c_void_p()
+        st = load().spca_group_create(ctypes.byref(g), ctypes.c_void_p(stream))
+        _check(st, "spca_group_create")
+        self.g = g
+
+    def last_error(self) -> str:
+        return load().spca_group_last_error(self.g).decode()
+
+    def solve(self, problems, tiles=None, want_starts=False):
+        """problems: list of (Handle, form, r, kwargs) with the keyword arguments of Handle.solve
+        (x0: host array or device address with x0_device=True).  tiles: (tile_n, stages) or None.
+        Returns one result dict per problem, as Handle.solve does."""
+        count = len(problems)
+        arr = (spca_problem * count)()
+        keep, outs = [], []
+        for i, (h, form, r, kw) in enumerate(problems):
+            kw = dict(kw)
+            x0 = kw.pop("x0", None)
+            ws = kw.pop("want_starts", want_starts)
+            prm = make_params(form, r, **kw)
+            out, res = _result_buffers(h.n, h.p, r, ws)
+            if x0 is not None and not prm.x0_is_device:
+                x0 = np.ascontiguousarray(x0, dtype=np.float32)
+                assert x0.shape == (r, h.p)
+                keep.append(x0)
+                x0p = x0.ctypes.data
+            else:
+                x0p = x0
+            keep.append(res)
+            arr[i].h = h.h
+            arr[i].prm = prm
+            arr[i].x0 = x0p
+            arr[i].res = ctypes.pointer(res)
+            outs.append((out, res))
+        t = spca_group_tiles(*(tiles or (0, 0)))
+        st = load().spca_solve_group(self.g, arr, count, ctypes.byref(t))
+        if st != SPCA_OK:
+            raise SpcaError(st, f"spca_solve_group failed: {spca_strerror(st)} {self.last_error()}")
+        return [_result_dict(out, res) for out, res in outs]
+
+    def close(self):
+        if getattr(self, "g", None):
+            load().spca_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
