@@ -14,6 +14,7 @@ with solves/s and the p50/p99 latency of single solves.  Prints ONE JSON line (r
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
   python bench.py --scan paper-shapes|text-corpus|few-starts|precision|many-problems|serving|economies
+  python bench.py --tune   (the grouped contraction's tile shapes: writes paper_1212_4137_gb300/grouped_tiles.json)
 (the scans print one JSON line per case; the clocks sampled during a run go to SPCA_CLOCKS_DIR,
 else the temporary directory)
 """
@@ -754,44 +755,117 @@ def _log_uniform(rng, lo, hi):
     return int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi))))))
 
 
-# Many problems (the batching configuration, scaled to 64 problems so that the host generates them
-# in seconds): spiked models with k = 3 spikes (theta = (40, 30, 20) sqrt(n / p), 20 nonzeros
-# each), n log-uniform in [200, 4000], p log-uniform in [500, 20000], FP32; per problem a uniform
-# formulation, s uniform in [5, 100] (at most p), r = 64 starts, at most 100 sweeps, tol 1e-9.
-# All problems are solved one after another on one handle each, then queued at once to the
-# request loop with 4 and with 8 workers (solves overlapping on the device).
-def run_scan_many(args, count=64, workers=(4, 8)):
-    import torch
-
-    from paper_1212_4137_gb300 import build, inputs as I, serve
-    build.build()
-    rng = np.random.default_rng(4)
-    probs = []
+# The batching configuration: 256 independent spiked problems (k = 3 spikes, theta = (40, 30, 20)
+# sqrt(n / p), 20 nonzeros each), n log-uniform in [200, 4000], p log-uniform in [500, 20000], FP32;
+# per problem a uniform formulation, s uniform in [5, 100] (at most p), r = 64 starts, at most 100
+# sweeps, tol 1e-9.  Modes: every problem solved one after another on its own handle; the same
+# problems in one grouped solve (every sweep phase one launch over all 256, the tile shape from the
+# tuning table); and the previous design, whole solves overlapping from 8 worker threads.
+def draw_problems(count, seed, n_range=(200, 4000), p_range=(500, 20000), s_range=(5, 100), r=64, threads=16):
+    """The batching configuration's problems: (name, A, form, solve kwargs, r); the matrices are
+    generated on host threads (the generator's array operations release the interpreter lock)."""
+    from paper_1212_4137_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    spec = []
     for q in range(count):
-        n, p = _log_uniform(rng, 200, 4000), _log_uniform(rng, 500, 20000)
-        A = I.spiked_matrix(n, p, I.spiked_thetas(n, p, (40.0, 30.0, 20.0)), 20, 5000 + q, dtype=np.float32)
+        n, p = _log_uniform(rng, *n_range), _log_uniform(rng, *p_range)
         form = int(rng.integers(1, 9))
-        s = float(min(int(rng.integers(5, 101)), p))
+        s = float(min(int(rng.integers(s_range[0], s_range[1] + 1)), p))
         kw = dict(s=s, seed=6000 + q, max_iter=100, tol=1e-9)
         if form >= 5:
             kw.update(gamma_target=True, calib=10)
-        probs.append((f"m{q}", A, form, kw))
-    for mode, nw in [("one after another", 1)] + [(f"{w} workers", w) for w in workers]:
-        with serve.Server(workers=nw, budget_bytes=64 << 30) as s:
-            for name, A, _, _ in probs:
-                s.register(name, A)
-            for name, _, form, kw in probs[:nw]:   # warm-up: one solve per worker
-                s.submit(name, form, 64, **kw).result()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            futs = [s.submit(name, form, 64, **kw) for name, _, form, kw in probs]
-            outs = [f.result() for f in futs]
-            dt = time.perf_counter() - t0
-        sweeps = sum(o["sweeps_total"] for o in outs)
-        print(json.dumps({"scan": f"many problems ({count} spiked, k = 3, n in [200, 4000], p in [500, 20000], "
-                                  "r = 64)", "mode": mode, "wall_s": round(dt, 3),
-                          "sweeps_starts_per_s": round(sweeps / dt, 1), "solves_per_s": round(count / dt, 1),
-                          "sum_n_p": int(sum(A.size for _, A, _, _ in probs))}), flush=True)
+        spec.append((f"m{q}", n, p, form, kw))
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        mats = list(ex.map(lambda t: I.spiked_matrix(t[1], t[2], I.spiked_thetas(t[1], t[2], (40.0, 30.0, 20.0)), 20,
+                                                     5000 + int(t[0][1:]), dtype=np.float32), spec))
+    return [(name, A, form, kw, r) for (name, _, _, form, kw), A in zip(spec, mats)]
+
+
+def run_scan_many(args, count=256, workers=8):
+    import torch
+
+    from paper_1212_4137_gb300 import build, serve, spca, tuning
+    build.build()
+    t0 = time.perf_counter()
+    probs = draw_problems(count, 4)
+    gen_s = time.perf_counter() - t0
+    handles = [spca.Handle(A) for _, A, _, _, _ in probs]
+    sum_np = int(sum(A.size for _, A, _, _, _ in probs))
+    head = {"scan": f"many problems ({count} spiked, k = 3, n in [200, 4000], p in [500, 20000], r = 64)",
+            "sum_n_p": sum_np, "host_generation_s": round(gen_s, 1)}
+
+    def report(mode, dt, outs, extra=None):
+        line = dict(head, mode=mode, wall_s=round(dt, 3),
+                    sweeps_starts_per_s=round(sum(o["sweeps_total"] for o in outs) / dt, 1),
+                    solves_per_s=round(count / dt, 1))
+        line.update(extra or {})
+        print(json.dumps(line), flush=True)
+
+    # one after another
+    for h, (_, _, form, kw, r) in list(zip(handles, probs))[:8]:   # warm-up
+        h.solve(form, r, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    solo = [h.solve(form, r, **kw) for h, (_, _, form, kw, r) in zip(handles, probs)]
+    report("one after another", time.perf_counter() - t0, solo)
+    # one grouped solve
+    g = spca.Group()
+    req = [(h, form, r, kw) for h, (_, _, form, kw, r) in zip(handles, probs)]
+    shape = tuning.choose(64) or (64, 4)
+    g.solve(req, tiles=shape)   # warm-up: captures the graphs
+    best = None
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        grouped = g.solve(req, tiles=shape)
+        dt = time.perf_counter() - t0
+        best = dt if best is None or dt < best else best
+    rel = [abs(a["objective"] - b["objective"]) / max(1.0, abs(b["objective"])) for a, b in zip(grouped, solo)]
+    report(f"one grouped solve (tiles {shape[0]} x {shape[1]} stages)", best, grouped,
+           {"max_rel_objective_diff_vs_one_after_another": float(max(rel)),
+            "problems_within_1e-5": int(sum(x <= 1e-5 for x in rel))})
+    g.close()
+    for h in handles:
+        h.close()
+    # the previous design: whole solves on clones from concurrent workers
+    with serve.Server(workers=workers, budget_bytes=64 << 30) as s:
+        for name, A, _, _, _ in probs:
+            s.register(name, A)
+        for name, _, form, kw, r in probs[:workers]:
+            s.submit(name, form, r, **kw).result()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        outs = [f.result() for f in [s.submit(name, form, r, **kw) for name, _, form, kw, r in probs]]
+        report(f"{workers} workers, whole solves overlapping", time.perf_counter() - t0, outs)
+
+
+# The tuning of the grouped contraction's tile shape (tuning.py): for each bucket of start counts a
+# problem mix drawn like the batching configuration (64 problems, r = 16, 64, 256), every shape the
+# library builds timed on one grouped solve (best of 2 after a warm-up); writes the table beside
+# tuning.py and prints it.
+def run_tune(args, count=64):
+    import torch
+
+    from paper_1212_4137_gb300 import build, spca, tuning
+    build.build()
+    table = {"how": "bench.py --tune: per bucket, one grouped solve of 64 problems drawn like the batching "
+                    "configuration (n log-uniform in [200, 4000], p in [500, 20000], k = 3 spikes, uniform "
+                    "formulation and s in [5, 100]) with r starts each; wall-clock ms, best of 2 after a warm-up",
+             "gpu": torch.cuda.get_device_name(0), "buckets": {}}
+    for r in (16, 64, 256):
+        probs = draw_problems(count, 40 + r, r=r)
+        handles = [spca.Handle(A) for _, A, _, _, _ in probs]
+        g = spca.Group()
+        req = [(h, form, rr, kw) for h, (_, _, form, kw, rr) in zip(handles, probs)]
+        res = tuning.tune(g, req)
+        table["buckets"][tuning.bucket(r)] = dict(res, problems=count, r=r)
+        print(json.dumps({"tune": tuning.bucket(r), **res}), flush=True)
+        g.close()
+        for h in handles:
+            h.close()
+    with open(tuning.TABLE, "w") as fh:
+        json.dump(table, fh, indent=1)
 
 
 # Serving (scaled to 8 resident matrices, 2 GB in all, so that the host generates them in seconds):
@@ -880,7 +954,11 @@ def main():
     ap.add_argument("--scan", choices=("paper-shapes", "text-corpus", "few-starts", "precision", "many-problems",
                                        "serving", "economies"), default=None)
     ap.add_argument("--rs", type=str, default=None, help="text-corpus scan: comma-separated start counts")
+    ap.add_argument("--tune", action="store_true", help="measure the grouped contraction's tile shapes")
     args = ap.parse_args()
+    if args.tune:
+        run_tune(args)
+        return
     if args.scan == "text-corpus":
         kw = {}
         if args.forms:

@@ -371,7 +371,8 @@ class Group:
 
     def solve(self, problems, tiles=None, want_starts=False):
         """problems: list of (Handle, form, r, kwargs) with the keyword arguments of Handle.solve
-        (x0: host array or device address with x0_device=True).  tiles: (tile_n, stages) or None.
+        (x0: host array or device address with x0_device=True).  tiles: (tile_n, stages), "auto"
+        (the measured shape of tuning.py's table) or None (the library's default).
         Returns one result dict per problem, as Handle.solve does."""
         count = len(problems)
         arr = (spca_problem * count)()
@@ -395,6 +396,9 @@ class Group:
             arr[i].x0 = x0p
             arr[i].res = ctypes.pointer(res)
             outs.append((out, res))
+        if tiles == "auto":   # the measured shape for this mix's bucket (tuning.py), else the default
+            from . import tuning
+            tiles = tuning.choose(max(r for _, _, r, _ in problems))
         t = spca_group_tiles(*(tiles or (0, 0)))
         st = load().spca_solve_group(self.g, arr, count, ctypes.byref(t))
         if st != SPCA_OK:
