@@ -422,34 +422,51 @@ int spca_objective_noalloc(int form, double gamma, const float *A, int64_t n, in
 int spca_set_waits(spca_handle *h, int64_t wait_limit_us, int unpublished_parts);
 
 /*
- * Groups of problems: Algorithm 2 for many independent problems in one solve, each with its own
+ * Groups of problems: Algorithm 2 for many independent problems at once, each with its own
  * matrix (a handle), formulation, s or gamma and starts (the batching of Section 4 carried across
- * problems).  Every phase of a sweep is one launch over all problems: the dense u = A x of the
- * first sweep and v = A^T y of every sweep as one persistent tensor-core launch over the tiles of
- * all problems, the support gather, y-step, x-step (full pass) and active lists as one launch each
- * over all starts or problems; the sweeps are captured into CUDA graphs and replayed.  Each
- * problem's results are those spca_solve gives for it alone, up to the order of rounding in the
- * contractions (the same FP32-class arithmetic).
+ * problems).  Every phase of a sweep is one launch over all the group's problems: the dense
+ * u = A x of a problem's first sweep and v = A^T y of every sweep as one persistent tensor-core
+ * launch over the tiles of all problems, the support gather, y-step, x-step (full pass) and
+ * active lists as one launch each over all starts or problems.  Each problem's results do not
+ * depend on the other problems of the group (the same bits alone and in any mix) and agree with
+ * spca_solve's for it up to the order of rounding in the contractions.
  *
- * spca_group_create -- a group object: its own stream and a workspace grown on demand.
- *   cuda_stream  as in spca_create: each solve starts after the work queued on it.
- * spca_group_destroy -- free it (waits for its stream); NULL is a no-op.
- * spca_group_last_error -- static text for the group's last failure ("" if none).
- *
- * spca_solve_group -- solve `count` problems (1 .. 1024).  Problem i:
+ * A group is also a session: problems can be admitted between segments of sweeps while others
+ * run (spca_group_admit), and spca_group_step runs the next sweeps of every member, finalising
+ * and retiring the members whose starts have all stopped -- continuous batching at sweep
+ * boundaries.  Problem i of a call:
  *   h     a handle from spca_create (dense A) on a device with tensor cores, or a clone of one;
- *         read only (several problems may share a handle).
+ *         read only (several problems and groups may use one handle at once).
  *   prm   as for spca_solve, with lowp_sweeps = 0, total_starts <= r, engine AUTO or TC,
  *         r in 1 .. 65535; timeout_us is not checked; the support gather serves every support
  *         after the first sweep.
- *   x0    r x p starts (host or device per prm.x0_is_device), or NULL for seeded starts (the
- *         same starts as spca_solve with that seed).
- *   res   caller-owned host buffers as for spca_solve (results of this problem).
- * tiles   the tile shape of the grouped contraction: tile_n (64 or 128 columns) and stages (2..4
- *         for 64, 2..3 for 128); NULL or {0, 0} = 64 columns, 4 stages.  bench.py --tune times the
- *         shapes per problem mix and the chosen shape is passed here.
- * Errors: SPCA_E_INVALID (arguments, a problem's parameters, non-finite x0; spca_group_last_error
- *         says which), SPCA_E_UNSUPPORTED (more than 1024 problems), SPCA_E_NOMEM, SPCA_E_CUDA,
+ *   x0    r x p starts (host or device per prm.x0_is_device; copied at admission), or NULL for
+ *         seeded starts (the same starts as spca_solve with that seed).
+ *   res   caller-owned host buffers as for spca_solve, written when the problem finishes; they
+ *         must stay valid until then.
+ *
+ * spca_group_create    a group: its own stream; each call starts after the work queued on
+ *                      cuda_stream (as in spca_create).
+ * spca_group_destroy   frees it, with any admitted problems (their results are not written);
+ *                      NULL is a no-op.
+ * spca_group_last_error  static text for the group's last failure ("" if none).
+ * spca_group_set_tiles the tile shape of the grouped contraction: tile_n (64 or 128 columns)
+ *                      and stages (2..4 for 64, 2..3 for 128); NULL or {0, 0} = 64 x 4.
+ *                      bench.py --tune measures the shapes per bucket of start counts.
+ * spca_group_admit     admit `count` problems (tags[i] identifies problem i in the finished
+ *                      lists; NULL = 0 .. count - 1); a member's device memory is allocated here
+ *                      (stream-ordered).  On failure none of the call's problems is admitted.
+ * spca_group_step      run `sweeps` sweeps of every member (the members admitted since the last
+ *                      step begin with their first sweep), then finalise the members whose starts
+ *                      have all stopped: their results are written and their tags listed in
+ *                      finished[0 .. min(*nfinished, cap)).  Synchronous.
+ * spca_group_pending   members admitted and not finished.
+ * spca_solve_group     admit the problems, sweep until every start of every problem has stopped
+ *                      (the segments captured into CUDA graphs and replayed), write every result;
+ *                      the group must have no members.
+ * Errors: SPCA_E_INVALID (arguments, a problem's parameters, non-finite x0, an unknown tile shape;
+ *         spca_group_last_error says which), SPCA_E_UNSUPPORTED (more than 1024 members),
+ *         SPCA_E_BUSY (spca_solve_group on a group with members), SPCA_E_NOMEM, SPCA_E_CUDA,
  *         SPCA_E_TIMEOUT (a bounded device-side wait gave up).
  */
 typedef struct spca_group spca_group;
@@ -466,6 +483,10 @@ typedef struct {
 int spca_group_create(spca_group **out, void *cuda_stream);
 void spca_group_destroy(spca_group *g);
 const char *spca_group_last_error(const spca_group *g);
+int spca_group_set_tiles(spca_group *g, const spca_group_tiles *tiles);
+int spca_group_admit(spca_group *g, spca_problem *probs, int count, const int *tags);
+int spca_group_step(spca_group *g, int sweeps, int *finished, int cap, int *nfinished);
+int spca_group_pending(const spca_group *g);
 int spca_solve_group(spca_group *g, spca_problem *probs, int count, const spca_group_tiles *tiles);
 
 /* spca_destroy -- free the handle's device memory (waits for its stream). NULL is a no-op. */

@@ -1,11 +1,17 @@
-// group.cu -- spca_solve_group: Algorithm 2 for many independent problems at once (each with its own
-// matrix, formulation, s or gamma and starts), every phase of a sweep one launch over all of them:
-// the dense u = A x of the first sweep and v = A^T y of every sweep as one persistent tensor-core
-// launch over the tiles of all problems (k_gemm_grouped), the support gather, y-step, x-step and
-// active lists as one launch each over all starts or problems.  The sweeps between two read-backs
-// of the problems' control words are captured into a CUDA graph and replayed.
+// group.cu -- groups of problems: Algorithm 2 for many independent problems at once (each with its
+// own matrix, formulation, s or gamma and starts), every phase of a sweep one launch over all of
+// them: the dense u = A x of a problem's first sweep and v = A^T y of every sweep as one persistent
+// tensor-core launch over the tiles of all problems (k_gemm_grouped), the support gather, y-step,
+// x-step and active lists as one launch each over all starts or problems.
+//
+// A group is a session: problems are admitted between segments of sweeps (each into a block of
+// device memory of its own), every member sweeps in the same launches (a new member's first sweep,
+// with its dense u = A x, beside the others' later ones), and a member whose starts have all
+// stopped is finalised (Table 1 objective, best start, its outputs) and retired at the end of the
+// segment.  spca_solve_group admits a whole set and steps it to the end with every segment
+// captured into a CUDA graph; spca_group_admit / spca_group_step serve requests that arrive while
+// others run (continuous batching at sweep boundaries).
 #include <algorithm>
-#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,19 +30,63 @@ struct GroupGraph {
   cudaGraphExec_t exec = nullptr;
 };
 
+// bump allocator over a block: 256-byte aligned pieces
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  }
+};
+
+// one admitted problem: its request, its block of device memory and its table entry
+struct Member {
+  spca_handle *h = nullptr;
+  spca_params P{};
+  spca_result *res = nullptr;
+  int tag = 0;
+  int r = 0, n = 0, p = 0, target = 0;
+  int64_t ldX = 0, ldU = 0;
+  char *mem = nullptr;            // the member's device block
+  GProb d{};                      // its table entry (start0 set when the table is built)
+  CUtensorMap *maps = nullptr;    // device: A planes, A^T planes, X planes, Y planes
+  double *partials = nullptr;
+  float *y_out = nullptr, *x_out = nullptr;
+  int64_t *support_out = nullptr, *nnz_out = nullptr;
+  int *best = nullptr;
+  bool first_pending = true;      // its first sweep (the dense u = A x) is still to run
+};
+
+uint64_t fnv(uint64_t h, const void *p, size_t n) {
+  const unsigned char *b = static_cast<const unsigned char *>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
 }  // namespace
 
 struct spca_group {
-  cudaStream_t stream = nullptr;   // the group's own non-blocking stream (captured into graphs)
-  cudaStream_t user = nullptr;     // the caller's stream: each solve starts after its prior work
+  cudaStream_t stream = nullptr;   // the group's own non-blocking stream
+  cudaStream_t user = nullptr;     // the caller's stream: each call starts after its prior work
   cudaEvent_t order_ev = nullptr;
   int sms = 1;
-  char *ws = nullptr;              // device workspace, grown on demand
-  size_t ws_bytes = 0;
-  Ctrl *h_ctrl = nullptr;          // pinned mirror of one parity's control words
-  int h_ctrl_cap = 0;
-  int *h_err = nullptr;            // pinned mirror of the device error word
-  std::vector<GroupGraph> graphs;  // captured sweep segments and finalisations
+  std::vector<Member> members;     // admitted, unfinished problems
+  int64_t k = 0;                   // sweeps run so far (the parity of the control words)
+  // the tables of the current members (device), grown on demand
+  char *tab = nullptr;
+  size_t tab_bytes = 0;
+  GProb *dP = nullptr;
+  int *d_start_prob = nullptr, *d_active = nullptr;
+  GTask *d_tasks = nullptr;
+  int R = 0, total_u = 0, total_v = 0, n_u = 0, max_n = 1, max_p = 1;
+  bool tables_ok = false;
+  int *h_active = nullptr;         // pinned: active counts at a segment's end
+  int h_active_cap = 0;
+  int *h_err = nullptr;            // pinned: the device error word
+  int *d_err = nullptr;
+  int bn = 64, stages = 4;
+  std::vector<GroupGraph> graphs;
   char last_error[256] = {0};
 };
 
@@ -47,42 +97,20 @@ int gfail(spca_group *g, int code, const char *msg) {
   return code;
 }
 
-#define GCK(expr)                                                                          \
-  do {                                                                                     \
-    cudaError_t e_ = (expr);                                                               \
-    if (e_ != cudaSuccess) {                                                               \
+#define GCK(expr)                                                                                     \
+  do {                                                                                                \
+    cudaError_t e_ = (expr);                                                                          \
+    if (e_ != cudaSuccess) {                                                                          \
       if (g) snprintf(g->last_error, sizeof(g->last_error), "CUDA error: %s", cudaGetErrorString(e_)); \
-      return e_ == cudaErrorMemoryAllocation ? SPCA_E_NOMEM : SPCA_E_CUDA;                 \
-    }                                                                                      \
+      return e_ == cudaErrorMemoryAllocation ? SPCA_E_NOMEM : SPCA_E_CUDA;                            \
+    }                                                                                                 \
   } while (0)
 
-// FNV-1a over bytes (keys of the captured graphs)
-uint64_t fnv(uint64_t h, const void *p, size_t n) {
-  const unsigned char *b = static_cast<const unsigned char *>(p);
-  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
-  return h;
-}
-
-// bump allocator over the workspace: 256-byte aligned blocks
-struct Layout {
-  size_t off = 0;
-  size_t take(size_t bytes) {
-    const size_t o = off;
-    off += (bytes + 255) / 256 * 256;
-    return o;
-  }
-};
-
-// per-problem host bookkeeping
-struct HostProb {
-  spca_handle *h;
-  spca_params P;
-  const float *x0;
-  spca_result *res;
-  int r, n, p, start0, target, calib;
-  int64_t ldX, ldU;
-  size_t oX, oV, oU, oXpl, oYpl, oxs, oxi, osi, osv, opart, oyout, oxout, osup;
-};
+#define GRC(expr)                   \
+  do {                              \
+    int rc_ = (expr);               \
+    if (rc_ != SPCA_OK) return rc_; \
+  } while (0)
 
 // the problem's parameters against Algorithm 2's requirements (as spca_solve checks them)
 const char *check_problem(const spca_problem &q) {
@@ -111,6 +139,435 @@ const char *check_problem(const spca_problem &q) {
   return nullptr;
 }
 
+uint64_t seed_key(uint64_t seed) {
+  auto mixh = [](uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  return mixh(seed ^ mixh(5ull));   // the starts' stream of the single solve
+}
+
+// device bytes of a member's block for r starts on an n x p matrix
+size_t member_layout(Member &m, size_t *o) {
+  Layout L;
+  const size_t r = (size_t)m.r;
+  o[0] = L.take(4 * r * m.ldX);              // X
+  o[1] = L.take(4 * r * m.ldX);              // V
+  o[2] = L.take(4 * r * m.ldU);              // U
+  o[3] = L.take(2 * 2 * r * m.ldX);          // X planes
+  o[4] = L.take(2 * 2 * r * m.ldU);          // Y planes
+  o[5] = L.off;                              // (end of the zeroed part: padded columns)
+  o[6] = L.take(4 * r);                      // x_scale
+  o[7] = L.take(4 * r);                      // x_inv
+  o[8] = L.take(4 * r * m.p);                // sup_idx
+  o[9] = L.take(4 * r * m.p);                // sup_val
+  o[10] = L.take(16 * r * ((m.n + 255) / 256));   // partials
+  o[11] = L.take(4 * (size_t)m.ldU);         // y_out
+  o[12] = L.take(4 * (size_t)m.ldX);         // x_out
+  o[13] = L.take(8 * (size_t)m.p);           // support_out
+  o[14] = L.take(4 * r * 5);                 // status, iters, nnz, act, rank
+  o[15] = L.take(8 * r * 6);                 // F, F_prev, gamma, f, ev (+ pad)
+  o[16] = L.take(4 * r * 3);                 // thr, tprev, xfast
+  o[17] = L.take(sizeof(Ctrl) * 2);          // ctrl of each parity
+  o[18] = L.take(16);                        // best, nnz_out
+  o[19] = L.take(sizeof(CUtensorMap) * 4);   // maps
+  return L.off;
+}
+
+// admit one problem: its block, its starts normalised, its first active list (for sweep k + 1)
+int admit_one(spca_group *g, const spca_problem &q, int tag) {
+  cudaStream_t st = g->stream;
+  Member m;
+  m.h = q.h;
+  m.P = q.prm;
+  m.res = q.res;
+  m.tag = tag;
+  m.r = m.P.r;
+  m.n = (int)m.h->n;
+  m.p = (int)m.h->p;
+  m.target = is_pen(m.P.form) && m.P.gamma_mode == SPCA_GAMMA_TARGET_NNZ;
+  m.ldX = pad_ld(m.p);
+  m.ldU = pad_ld(m.n);
+  size_t o[20];
+  const size_t bytes = member_layout(m, o);
+  GCK(cudaMallocAsync((void **)&m.mem, bytes, st));
+  auto at = [&](int i) { return m.mem + o[i]; };
+  GCK(cudaMemsetAsync(m.mem, 0, o[5], st));
+  GProb &d = m.d;
+  d.n = m.n;
+  d.p = m.p;
+  d.r = m.r;
+  d.form = m.P.form;
+  d.ldX = m.ldX;
+  d.ldU = m.ldU;
+  d.ldAT = m.h->ldAT;
+  d.AT32 = m.h->AT32;
+  d.X = reinterpret_cast<float *>(at(0));
+  d.V = reinterpret_cast<float *>(at(1));
+  d.U = reinterpret_cast<float *>(at(2));
+  d.Xpl = reinterpret_cast<__half *>(at(3));
+  d.Ypl = reinterpret_cast<__half *>(at(4));
+  d.xps = (int64_t)m.r * m.ldX;
+  d.yps = (int64_t)m.r * m.ldU;
+  d.x_scale = reinterpret_cast<float *>(at(6));
+  d.x_inv = reinterpret_cast<float *>(at(7));
+  d.sup_idx = reinterpret_cast<int *>(at(8));
+  d.sup_val = reinterpret_cast<float *>(at(9));
+  m.partials = reinterpret_cast<double *>(at(10));
+  m.y_out = reinterpret_cast<float *>(at(11));
+  m.x_out = reinterpret_cast<float *>(at(12));
+  m.support_out = reinterpret_cast<int64_t *>(at(13));
+  int *ip = reinterpret_cast<int *>(at(14));
+  double *dp = reinterpret_cast<double *>(at(15));
+  float *fp = reinterpret_cast<float *>(at(16));
+  StartState &s = d.st;
+  s.status = ip;
+  s.iters = ip + m.r;
+  s.nnz = ip + 2 * m.r;
+  d.act = ip + 3 * m.r;
+  d.rank = ip + 4 * m.r;
+  s.F = dp;
+  s.F_prev = dp + m.r;
+  s.gamma = dp + 2 * m.r;
+  s.f = dp + 3 * m.r;
+  s.ev = dp + 4 * m.r;
+  s.thr = fp;
+  s.tprev = fp + m.r;
+  s.xfast = reinterpret_cast<int *>(fp + 2 * m.r);
+  Ctrl *ctrl = reinterpret_cast<Ctrl *>(at(17));
+  d.ctrl[0] = ctrl;
+  d.ctrl[1] = ctrl + 1;
+  m.best = reinterpret_cast<int *>(at(18));
+  m.nnz_out = reinterpret_cast<int64_t *>(at(18) + 8);
+  m.maps = reinterpret_cast<CUtensorMap *>(at(19));
+  GCK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl) * 2, st));
+  XstepArgs &a = d.xa;
+  a = XstepArgs{};
+  a.form = m.P.form;
+  a.p = m.p;
+  a.s = m.P.s;
+  a.thr_fixed = uses_U(m.P.form) ? u_threshold(m.P.gamma) : (float)m.P.gamma;
+  a.gamma_fixed = m.P.gamma;
+  a.tol = m.P.tol;
+  a.max_iter = m.P.max_iter;
+  a.cap = m.p;
+  a.sparse_cap = m.p;   // the support gather serves every support after the first sweep
+  a.schedule = 1;
+  a.target = m.target;
+  a.calib_sweeps = m.target ? m.P.gamma_calib_sweeps : 0;
+  a.lowp_sweeps = 0;
+  a.stop_enabled = m.P.tol >= 0.0 ? 1 : 0;
+  d.gamma0 = is_pen(m.P.form) && !m.target ? m.P.gamma : 0.0;
+  d.ld0 = m.ldX;
+  d.key = seed_key(m.P.seed);
+  d.x0 = nullptr;
+  if (q.x0) {   // the given starts, copied into X and normalised there (they must be finite)
+    d.x0 = d.X;
+    GCK(cudaMemcpy2DAsync(d.X, m.ldX * sizeof(float), q.x0, (size_t)m.p * sizeof(float), (size_t)m.p * sizeof(float),
+                          m.r, m.P.x0_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    GCK(cudaMemsetAsync(g->d_err, 0, sizeof(int), st));
+    GCK(launch_check_finite(d.X, m.r, m.p, m.ldX, g->d_err, st));
+    GCK(cudaMemcpyAsync(g->h_err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GCK(cudaStreamSynchronize(st));
+    if (*g->h_err) {
+      cudaFreeAsync(m.mem, st);
+      return gfail(g, SPCA_E_INVALID, "x0 has a non-finite entry");
+    }
+  }
+  CUtensorMap maps[4];
+  maps[0] = m.h->pmA.m[0];
+  maps[1] = m.h->pmAT.m[0];
+  GCK(make_plane_map(&maps[2], d.Xpl, m.r, m.ldX, 2, 64, 64));
+  GCK(make_plane_map(&maps[3], d.Ypl, m.r, m.ldU, 2, 64, 64));
+  GCK(cudaMemcpyAsync(m.maps, maps, sizeof(maps), cudaMemcpyHostToDevice, st));
+  GCK(launch_start_init(d.x0, d.ld0, m.P.seed, m.r, m.p, d.X, m.ldX, s, d.gamma0, nullptr, nullptr, nullptr, st));
+  // the next sweep is k + 1: it reads the control words of parity k & 1
+  GCK(launch_active_list(s.status, nullptr, m.r, d.act, d.rank, d.ctrl[g->k & 1], st));
+  m.first_pending = true;
+  g->members.push_back(m);
+  g->tables_ok = false;
+  return SPCA_OK;
+}
+
+// the tables of the current members: problem entries, start -> problem map, tile tasks (u for the
+// members whose first sweep is pending, v for each parity), each task list ordered by falling K
+int build_tables(spca_group *g) {
+  const int np = (int)g->members.size();
+  cudaStream_t st = g->stream;
+  std::vector<GProb> P(np);
+  int R = 0, max_n = 1, max_p = 1;
+  for (int i = 0; i < np; ++i) {
+    Member &m = g->members[i];
+    m.d.start0 = R;
+    P[i] = m.d;
+    R += m.r;
+    max_n = std::max(max_n, m.n);
+    max_p = std::max(max_p, m.p);
+  }
+  std::vector<int> start_prob(R);
+  for (int i = 0; i < np; ++i)
+    for (int c = 0; c < g->members[i].r; ++c) start_prob[P[i].start0 + c] = i;
+  std::vector<GTask> tasks(3 * np);
+  int n_u = 0;
+  auto build = [&](bool u, int parity, GTask *base, int *count) -> int {
+    std::vector<int> order;
+    for (int i = 0; i < np; ++i)
+      if (!u || g->members[i].first_pending) order.push_back(i);
+    auto kb = [&](int i) { return u ? (g->members[i].p + 63) / 64 : (g->members[i].n + 63) / 64; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return kb(a) > kb(b); });
+    int t0 = 0;
+    for (size_t k = 0; k < order.size(); ++k) {
+      const int i = order[k];
+      const Member &m = g->members[i];
+      GTask &T = base[k];
+      T = GTask{};
+      T.pmap = m.maps + (u ? 0 : 1);
+      T.qmap = m.maps + (u ? 2 : 3);
+      T.M = u ? m.n : m.p;
+      T.kblocks = kb(i);
+      T.nmax = m.r;
+      T.nb = u || !is_l1_var(m.P.form) ? 2 : 1;
+      T.n_dev = &m.d.ctrl[parity]->active;
+      T.col_map = m.d.act;
+      T.out = u ? m.d.U : m.d.V;
+      T.ldo = u ? m.ldU : m.ldX;
+      T.row_inv = u ? m.h->a_inv : m.h->at_inv;
+      T.col_inv = u ? m.d.x_inv : nullptr;
+      T.q_inv = u ? 1.0f : kQInv;
+      T.pairs = u || !is_l1_var(m.P.form) ? pairs_general() : pairs_sign();
+      T.mt = (T.M + TC_BM_ROWS - 1) / TC_BM_ROWS;
+      T.nt = (m.r + g->bn - 1) / g->bn;
+      T.tile0 = t0;
+      t0 += T.mt * T.nt;
+    }
+    *count = (int)order.size();
+    return t0;
+  };
+  // the pending members' first sweep is the next one, k + 1: it reads parity k & 1
+  int nv = 0;
+  g->total_u = build(true, (int)(g->k & 1), tasks.data(), &n_u);
+  g->total_v = build(false, 0, tasks.data() + np, &nv);
+  build(false, 1, tasks.data() + 2 * np, &nv);
+  Layout L;
+  const size_t oP = L.take(sizeof(GProb) * np), oS = L.take(sizeof(int) * R), oT = L.take(sizeof(GTask) * 3 * np),
+               oA = L.take(sizeof(int) * np);
+  if (L.off > g->tab_bytes) {
+    GCK(cudaStreamSynchronize(st));
+    if (g->tab) cudaFree(g->tab);
+    g->tab = nullptr;
+    g->tab_bytes = 0;
+    GCK(cudaMalloc((void **)&g->tab, L.off));
+    g->tab_bytes = L.off;
+    for (GroupGraph &q : g->graphs)
+      if (q.exec) cudaGraphExecDestroy(q.exec);
+    g->graphs.clear();
+  }
+  if (g->h_active_cap < np) {
+    if (g->h_active) cudaFreeHost(g->h_active);
+    g->h_active = nullptr;
+    g->h_active_cap = 0;
+    GCK(cudaMallocHost((void **)&g->h_active, sizeof(int) * np));
+    g->h_active_cap = np;
+  }
+  g->dP = reinterpret_cast<GProb *>(g->tab + oP);
+  g->d_start_prob = reinterpret_cast<int *>(g->tab + oS);
+  g->d_tasks = reinterpret_cast<GTask *>(g->tab + oT);
+  g->d_active = reinterpret_cast<int *>(g->tab + oA);
+  GCK(cudaMemcpyAsync(g->dP, P.data(), sizeof(GProb) * np, cudaMemcpyHostToDevice, st));
+  GCK(cudaMemcpyAsync(g->d_start_prob, start_prob.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
+  GCK(cudaMemcpyAsync(g->d_tasks, tasks.data(), sizeof(GTask) * 3 * np, cudaMemcpyHostToDevice, st));
+  GCK(cudaStreamSynchronize(st));   // the host vectors go out of scope
+  g->R = R;
+  g->n_u = n_u;
+  g->max_n = max_n;
+  g->max_p = max_p;
+  g->tables_ok = true;
+  return SPCA_OK;
+}
+
+// the launches of global sweep k (the members' tables as built)
+cudaError_t enqueue_sweep(spca_group *g, int64_t k, bool first_of_segment) {
+  cudaStream_t st = g->stream;
+  const int np = (int)g->members.size();
+  const int cur = (int)((k - 1) & 1), nxt = (int)(k & 1);
+  const uint64_t wait_ns = 2000000000ull;
+  cudaError_t e = cudaSuccess;
+  if (first_of_segment && g->n_u > 0) {
+    // the first sweep of the members admitted before this segment: the dense u = A x
+    e = launch_g_xplanes(g->dP, g->d_start_prob, g->R, st);
+    if (e == cudaSuccess) e = launch_gemm_grouped(g->d_tasks, g->n_u, g->total_u, g->bn, g->stages, g->sms, g->d_err,
+                                                  wait_ns, st);
+  }
+  if (e == cudaSuccess) e = launch_g_gather(g->dP, g->d_start_prob, g->R, g->max_n, st);
+  if (e == cudaSuccess) e = launch_g_ystep(g->dP, g->d_start_prob, g->R, st);
+  if (e == cudaSuccess)
+    e = launch_gemm_grouped(g->d_tasks + (1 + cur) * np, np, g->total_v, g->bn, g->stages, g->sms, g->d_err, wait_ns,
+                            st);
+  if (e == cudaSuccess) e = launch_g_ctrl(g->dP, np, nxt, 1, nullptr, st);
+  if (e == cudaSuccess) e = launch_g_xstep(g->dP, g->d_start_prob, g->R, g->max_p, nxt, g->sms, st);
+  if (e == cudaSuccess) e = launch_g_active(g->dP, np, nxt, st);
+  return e;
+}
+
+// Table 1 objective of every start, the best start and its outputs, then the results to the host
+int finish_member(spca_group *g, Member &m) {
+  cudaStream_t st = g->stream;
+  const GProb &d = m.d;
+  GCK(launch_finalise(m.P.form, m.h->AT32, m.h->ldAT, m.n, m.p, d.X, m.ldX, d.st, m.r, d.U, m.ldU, d.sup_idx,
+                      d.sup_val, m.p, m.partials, st));
+  GCK(launch_best(m.P.form, m.target, d.st, m.r, m.best, st));
+  GCK(launch_best_outputs(m.P.form, m.best, d.U, m.ldU, m.n, d.X, m.ldX, m.p, m.y_out, m.x_out, m.support_out,
+                          m.nnz_out, st));
+  const int r = m.r;
+  std::vector<int> status(r), iters(r);
+  std::vector<double> f(r), ev(r), gam(r), F(r);
+  int best = 0;
+  int64_t nnz = 0;
+  GCK(cudaMemcpyAsync(status.data(), d.st.status, sizeof(int) * r, cudaMemcpyDeviceToHost, st));
+  GCK(cudaMemcpyAsync(iters.data(), d.st.iters, sizeof(int) * r, cudaMemcpyDeviceToHost, st));
+  GCK(cudaMemcpyAsync(f.data(), d.st.f, 8 * r, cudaMemcpyDeviceToHost, st));
+  GCK(cudaMemcpyAsync(ev.data(), d.st.ev, 8 * r, cudaMemcpyDeviceToHost, st));
+  GCK(cudaMemcpyAsync(gam.data(), d.st.gamma, 8 * r, cudaMemcpyDeviceToHost, st));
+  GCK(cudaMemcpyAsync(F.data(), d.st.F, 8 * r, cudaMemcpyDeviceToHost, st));
+  GCK(cudaMemcpyAsync(&best, m.best, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GCK(cudaMemcpyAsync(&nnz, m.nnz_out, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  GCK(cudaStreamSynchronize(st));
+  spca_result *res = m.res;
+  if (res->x) GCK(cudaMemcpyAsync(res->x, m.x_out, (size_t)m.p * 4, cudaMemcpyDeviceToHost, st));
+  if (res->y) GCK(cudaMemcpyAsync(res->y, m.y_out, (size_t)m.n * 4, cudaMemcpyDeviceToHost, st));
+  if (res->support && nnz > 0) GCK(cudaMemcpyAsync(res->support, m.support_out, (size_t)nnz * 8, cudaMemcpyDeviceToHost, st));
+  if (res->start_x)
+    GCK(cudaMemcpy2DAsync(res->start_x, (size_t)m.p * 4, d.X, m.ldX * 4, (size_t)m.p * 4, r, cudaMemcpyDeviceToHost, st));
+  GCK(cudaStreamSynchronize(st));
+  int64_t sweeps = 0;
+  int nconv = 0, ndeg = 0;
+  for (int c = 0; c < r; ++c) {
+    sweeps += iters[c];
+    nconv += status[c] == SPCA_ST_CONVERGED;
+    ndeg += status[c] == SPCA_ST_DEGENERATE;
+  }
+  const bool pen = is_pen(m.P.form);
+  res->objective = f[best];
+  res->explained_variance = ev[best];
+  res->gamma = pen ? gam[best] : 0.0;
+  res->best_start = best;
+  res->best_iters = iters[best];
+  res->best_status = status[best];
+  res->converged = nconv;
+  res->degenerate = ndeg;
+  res->sweeps_total = sweeps;
+  res->nnz = nnz;
+  for (int c = 0; c < r; ++c) {
+    if (res->start_objective) res->start_objective[c] = f[c];
+    if (res->start_explained) res->start_explained[c] = ev[c];
+    if (res->start_F) res->start_F[c] = F[c];
+    if (res->start_iters) res->start_iters[c] = iters[c];
+    if (res->start_status) res->start_status[c] = status[c];
+    if (res->start_gamma) res->start_gamma[c] = pen ? gam[c] : 0.0;
+  }
+  return SPCA_OK;
+}
+
+void release_member(spca_group *g, Member &m) {
+  if (m.mem) cudaFreeAsync(m.mem, g->stream);
+  m.mem = nullptr;
+}
+
+int check_device_err(spca_group *g) {
+  GCK(cudaMemcpyAsync(g->h_err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  GCK(cudaStreamSynchronize(g->stream));
+  if (*g->h_err) {
+    const int code = *g->h_err;
+    cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream);
+    return gfail(g, code, "a device-side wait timed out");
+  }
+  return SPCA_OK;
+}
+
+// run `sweeps` sweeps for the current members (captured into a graph when `capture`), then the
+// active counts; finished members (no active start) are finalised and retired when `retire`
+int run_segment(spca_group *g, int sweeps, bool capture, bool retire, int *finished, int cap, int *nfin) {
+  cudaStream_t st = g->stream;
+  if (nfin) *nfin = 0;
+  if (g->members.empty()) return SPCA_OK;
+  if (!g->tables_ok) GRC(build_tables(g));
+  const int np = (int)g->members.size();
+  if (capture) {
+    uint64_t key = 1469598103934665603ull;
+    key = fnv(key, &g->tab, sizeof g->tab);
+    for (const Member &m : g->members) key = fnv(key, &m.d, sizeof m.d);
+    const int64_t par = g->k & 1;
+    const int pend = g->n_u;
+    key = fnv(key, &par, sizeof par);
+    key = fnv(key, &pend, sizeof pend);
+    key = fnv(key, &sweeps, sizeof sweeps);
+    key = fnv(key, &g->bn, sizeof g->bn);
+    key = fnv(key, &g->stages, sizeof g->stages);
+    GroupGraph *gg = nullptr;
+    for (GroupGraph &q : g->graphs)
+      if (q.key == key) gg = &q;
+    if (!gg) {
+      if (g->graphs.size() > 32) {
+        GCK(cudaStreamSynchronize(st));
+        for (GroupGraph &q : g->graphs)
+          if (q.exec) cudaGraphExecDestroy(q.exec);
+        g->graphs.clear();
+      }
+      g->graphs.emplace_back();
+      gg = &g->graphs.back();
+      gg->key = key;
+      cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+      cudaError_t be = cudaSuccess;
+      if (ce == cudaSuccess) {
+        for (int j = 0; j < sweeps && be == cudaSuccess; ++j) be = enqueue_sweep(g, g->k + 1 + j, j == 0);
+        cudaGraph_t graph = nullptr;
+        ce = cudaStreamEndCapture(st, &graph);
+        if (ce == cudaSuccess && be == cudaSuccess) ce = cudaGraphInstantiate(&gg->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+      }
+      if (be != cudaSuccess) ce = be;
+      if (ce != cudaSuccess) {
+        g->graphs.pop_back();
+        GCK(ce);
+      }
+    }
+    GCK(cudaGraphLaunch(gg->exec, st));
+  } else {
+    for (int j = 0; j < sweeps; ++j) GCK(enqueue_sweep(g, g->k + 1 + j, j == 0));
+  }
+  g->k += sweeps;
+  if (g->n_u > 0) {   // the pending members have had their first sweep
+    for (Member &m : g->members) m.first_pending = false;
+    g->tables_ok = false;
+  }
+  GCK(launch_g_ctrl(g->dP, np, (int)(g->k & 1), 0, g->d_active, st));
+  GCK(cudaMemcpyAsync(g->h_active, g->d_active, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
+  GCK(cudaStreamSynchronize(st));
+  GRC(check_device_err(g));
+  if (!retire) return SPCA_OK;
+  std::vector<Member> keep;
+  int nf = 0;
+  const std::vector<int> active(g->h_active, g->h_active + np);
+  for (int i = 0; i < np; ++i) {
+    Member &m = g->members[i];
+    if (active[i] > 0) {
+      keep.push_back(m);
+      continue;
+    }
+    GRC(finish_member(g, m));
+    if (finished && nf < cap) finished[nf] = m.tag;
+    ++nf;
+    release_member(g, m);
+  }
+  if (nf > 0) {
+    g->members.swap(keep);
+    g->tables_ok = false;
+  }
+  if (nfin) *nfin = nf;
+  return SPCA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -125,7 +582,9 @@ int spca_group_create(spca_group **out, void *cuda_stream) {
   if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&g->order_ev, cudaEventDisableTiming) != cudaSuccess ||
       cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaMallocHost((void **)&g->h_err, sizeof(int)) != cudaSuccess) {
+      cudaMallocHost((void **)&g->h_err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void **)&g->d_err, sizeof(int)) != cudaSuccess ||
+      cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream) != cudaSuccess) {
     spca_group_destroy(g);
     return SPCA_E_CUDA;
   }
@@ -135,11 +594,14 @@ int spca_group_create(spca_group **out, void *cuda_stream) {
 
 void spca_group_destroy(spca_group *g) {
   if (!g) return;
+  for (Member &m : g->members) release_member(g, m);
+  g->members.clear();
   if (g->stream) cudaStreamSynchronize(g->stream);
   for (GroupGraph &q : g->graphs)
     if (q.exec) cudaGraphExecDestroy(q.exec);
-  if (g->ws) cudaFree(g->ws);
-  if (g->h_ctrl) cudaFreeHost(g->h_ctrl);
+  if (g->tab) cudaFree(g->tab);
+  if (g->d_err) cudaFree(g->d_err);
+  if (g->h_active) cudaFreeHost(g->h_active);
   if (g->h_err) cudaFreeHost(g->h_err);
   if (g->order_ev) cudaEventDestroy(g->order_ev);
   if (g->stream) cudaStreamDestroy(g->stream);
@@ -148,410 +610,78 @@ void spca_group_destroy(spca_group *g) {
 
 const char *spca_group_last_error(const spca_group *g) { return g ? g->last_error : ""; }
 
-int spca_solve_group(spca_group *g, spca_problem *probs, int count, const spca_group_tiles *tiles) {
-  if (!g || !probs || count < 1) return gfail(g, SPCA_E_INVALID, "NULL group or problems, or count < 1");
-  if (count > kGroupMaxTasks) return gfail(g, SPCA_E_UNSUPPORTED, "more than 1024 problems in one group");
+int spca_group_set_tiles(spca_group *g, const spca_group_tiles *tiles) {
+  if (!g) return SPCA_E_INVALID;
   int bn = 64, stages = 4;
   if (tiles && (tiles->tile_n || tiles->stages)) {
     bn = tiles->tile_n;
     stages = tiles->stages;
     if (!grouped_config_ok(bn, stages)) return gfail(g, SPCA_E_INVALID, "unknown tile shape (tile_n, stages)");
   }
+  if (bn != g->bn) g->tables_ok = false;   // the N tiles of the tasks change
+  g->bn = bn;
+  g->stages = stages;
+  return SPCA_OK;
+}
+
+int spca_group_admit(spca_group *g, spca_problem *probs, int count, const int *tags) {
+  if (!g || (count > 0 && !probs) || count < 0) return gfail(g, SPCA_E_INVALID, "NULL group or problems");
+  if ((int64_t)g->members.size() + count > kGroupMaxTasks)
+    return gfail(g, SPCA_E_UNSUPPORTED, "more than 1024 problems in one group");
   for (int i = 0; i < count; ++i)
     if (const char *bad = check_problem(probs[i])) return gfail(g, SPCA_E_INVALID, bad);
-  cudaStream_t st = g->stream;
   GCK(cudaEventRecord(g->order_ev, g->user));
-  GCK(cudaStreamWaitEvent(st, g->order_ev, 0));
-
-  // ---- layout of the workspace
-  std::vector<HostProb> hp(count);
-  Layout L;
-  int64_t R = 0;
-  int max_n = 1, max_p = 1, max_iter = 1;
+  GCK(cudaStreamWaitEvent(g->stream, g->order_ev, 0));
+  const size_t before = g->members.size();
   for (int i = 0; i < count; ++i) {
-    HostProb &q = hp[i];
-    q.h = probs[i].h;
-    q.P = probs[i].prm;
-    q.x0 = probs[i].x0;
-    q.res = probs[i].res;
-    q.r = q.P.r;
-    q.n = (int)q.h->n;
-    q.p = (int)q.h->p;
-    q.start0 = (int)R;
-    q.target = is_pen(q.P.form) && q.P.gamma_mode == SPCA_GAMMA_TARGET_NNZ;
-    q.calib = q.target ? q.P.gamma_calib_sweeps : 0;
-    q.ldX = pad_ld(q.p);
-    q.ldU = pad_ld(q.n);
-    R += q.r;
-    max_n = std::max(max_n, q.n);
-    max_p = std::max(max_p, q.p);
-    max_iter = std::max(max_iter, q.P.max_iter);
-  }
-  if (R > INT32_MAX / 2) return gfail(g, SPCA_E_UNSUPPORTED, "too many starts in one group");
-  const size_t o_prob = L.take(sizeof(GProb) * count);
-  const size_t o_map = L.take(sizeof(CUtensorMap) * 4 * count);   // A planes, A^T planes, X planes, Y planes
-  const size_t o_task = L.take(sizeof(GTask) * 3 * count);        // u (first sweep), v for each parity
-  const size_t o_start_prob = L.take(sizeof(int) * R);
-  const size_t o_ctrl = L.take(sizeof(Ctrl) * 2 * count);         // parity-major
-  const size_t o_best = L.take(sizeof(int) * count);
-  const size_t o_nnzout = L.take(sizeof(int64_t) * count);
-  const size_t o_err = L.take(sizeof(int));
-  const size_t o_status = L.take(sizeof(int) * R), o_iters = L.take(sizeof(int) * R), o_nnz = L.take(sizeof(int) * R);
-  const size_t o_F = L.take(8 * R), o_Fp = L.take(8 * R), o_gam = L.take(8 * R), o_f = L.take(8 * R), o_ev = L.take(8 * R);
-  const size_t o_thr = L.take(4 * R), o_tprev = L.take(4 * R), o_xfast = L.take(4 * R);
-  const size_t o_act = L.take(sizeof(int) * R), o_rank = L.take(sizeof(int) * R);
-  const size_t zero_from = L.off;   // the vector blocks below start zeroed (padded columns)
-  for (HostProb &q : hp) {
-    q.oX = L.take(4 * (size_t)q.r * q.ldX);
-    q.oV = L.take(4 * (size_t)q.r * q.ldX);
-    q.oU = L.take(4 * (size_t)q.r * q.ldU);
-    q.oXpl = L.take(2 * 2 * (size_t)q.r * q.ldX);
-    q.oYpl = L.take(2 * 2 * (size_t)q.r * q.ldU);
-  }
-  const size_t zero_to = L.off;
-  for (HostProb &q : hp) {
-    q.oxs = L.take(4 * (size_t)q.r);
-    q.oxi = L.take(4 * (size_t)q.r);
-    q.osi = L.take(4 * (size_t)q.r * q.p);
-    q.osv = L.take(4 * (size_t)q.r * q.p);
-    q.opart = L.take(16 * (size_t)q.r * ((q.n + 255) / 256));
-    q.oyout = L.take(4 * (size_t)q.ldU);
-    q.oxout = L.take(4 * (size_t)q.ldX);
-    q.osup = L.take(8 * (size_t)q.p);
-  }
-  if (L.off > g->ws_bytes) {
-    GCK(cudaStreamSynchronize(st));
-    for (GroupGraph &q : g->graphs)
-      if (q.exec) cudaGraphExecDestroy(q.exec);
-    g->graphs.clear();
-    if (g->ws) cudaFree(g->ws);
-    g->ws = nullptr;
-    g->ws_bytes = 0;
-    GCK(cudaMalloc((void **)&g->ws, L.off));
-    g->ws_bytes = L.off;
-  }
-  if (g->h_ctrl_cap < count) {
-    if (g->h_ctrl) cudaFreeHost(g->h_ctrl);
-    g->h_ctrl = nullptr;
-    g->h_ctrl_cap = 0;
-    GCK(cudaMallocHost((void **)&g->h_ctrl, sizeof(Ctrl) * count));
-    g->h_ctrl_cap = count;
-  }
-  char *W = g->ws;
-  auto at = [&](size_t o) { return W + o; };
-  GProb *dP = reinterpret_cast<GProb *>(at(o_prob));
-  CUtensorMap *dmaps = reinterpret_cast<CUtensorMap *>(at(o_map));
-  GTask *dtasks = reinterpret_cast<GTask *>(at(o_task));
-  int *d_start_prob = reinterpret_cast<int *>(at(o_start_prob));
-  Ctrl *dctrl = reinterpret_cast<Ctrl *>(at(o_ctrl));
-  int *dbest = reinterpret_cast<int *>(at(o_best));
-  int64_t *dnnzout = reinterpret_cast<int64_t *>(at(o_nnzout));
-  int *derr = reinterpret_cast<int *>(at(o_err));
-  StartState all{};
-  all.status = reinterpret_cast<int *>(at(o_status));
-  all.iters = reinterpret_cast<int *>(at(o_iters));
-  all.nnz = reinterpret_cast<int *>(at(o_nnz));
-  all.F = reinterpret_cast<double *>(at(o_F));
-  all.F_prev = reinterpret_cast<double *>(at(o_Fp));
-  all.gamma = reinterpret_cast<double *>(at(o_gam));
-  all.f = reinterpret_cast<double *>(at(o_f));
-  all.ev = reinterpret_cast<double *>(at(o_ev));
-  all.thr = reinterpret_cast<float *>(at(o_thr));
-  all.tprev = reinterpret_cast<float *>(at(o_tprev));
-  all.xfast = reinterpret_cast<int *>(at(o_xfast));
-  int *dact = reinterpret_cast<int *>(at(o_act)), *drank = reinterpret_cast<int *>(at(o_rank));
-  GCK(cudaMemsetAsync(at(zero_from), 0, zero_to - zero_from, st));
-  GCK(cudaMemsetAsync(derr, 0, sizeof(int), st));
-  GCK(cudaMemsetAsync(dctrl, 0, sizeof(Ctrl) * 2 * count, st));
-
-  // ---- problem table, tensor maps, tile tasks
-  std::vector<GProb> P(count);
-  std::vector<CUtensorMap> maps(4 * count);
-  std::vector<int> start_prob(R);
-  for (int i = 0; i < count; ++i) {
-    HostProb &q = hp[i];
-    GProb &d = P[i];
-    d.n = q.n;
-    d.p = q.p;
-    d.r = q.r;
-    d.start0 = q.start0;
-    d.form = q.P.form;
-    d.ldX = q.ldX;
-    d.ldU = q.ldU;
-    d.ldAT = q.h->ldAT;
-    d.AT32 = q.h->AT32;
-    d.X = reinterpret_cast<float *>(at(q.oX));
-    d.V = reinterpret_cast<float *>(at(q.oV));
-    d.U = reinterpret_cast<float *>(at(q.oU));
-    d.Xpl = reinterpret_cast<__half *>(at(q.oXpl));
-    d.Ypl = reinterpret_cast<__half *>(at(q.oYpl));
-    d.xps = (int64_t)q.r * q.ldX;
-    d.yps = (int64_t)q.r * q.ldU;
-    d.x_scale = reinterpret_cast<float *>(at(q.oxs));
-    d.x_inv = reinterpret_cast<float *>(at(q.oxi));
-    d.sup_idx = reinterpret_cast<int *>(at(q.osi));
-    d.sup_val = reinterpret_cast<float *>(at(q.osv));
-    d.act = dact + q.start0;
-    d.rank = drank + q.start0;
-    d.ctrl[0] = dctrl + i;
-    d.ctrl[1] = dctrl + count + i;
-    StartState s = all;
-    s.status += q.start0; s.iters += q.start0; s.nnz += q.start0;
-    s.F += q.start0; s.F_prev += q.start0; s.gamma += q.start0; s.f += q.start0; s.ev += q.start0;
-    s.thr += q.start0; s.tprev += q.start0; s.xfast += q.start0;
-    d.st = s;
-    XstepArgs &a = d.xa;
-    a = XstepArgs{};
-    a.form = q.P.form;
-    a.p = q.p;
-    a.s = q.P.s;
-    a.thr_fixed = uses_U(q.P.form) ? u_threshold(q.P.gamma) : (float)q.P.gamma;
-    a.gamma_fixed = q.P.gamma;
-    a.tol = q.P.tol;
-    a.max_iter = q.P.max_iter;
-    a.cap = q.p;
-    a.sparse_cap = q.p;   // the support gather serves every support after the first sweep
-    a.schedule = 1;
-    a.target = q.target;
-    a.calib_sweeps = q.calib;
-    a.lowp_sweeps = 0;
-    a.stop_enabled = q.P.tol >= 0.0 ? 1 : 0;
-    d.ld0 = q.ldX;
-    d.x0 = nullptr;
-    d.key = 0;
-    if (q.x0) {
-      // the given starts, copied into X and normalised there
-      d.x0 = d.X;
-      GCK(cudaMemcpy2DAsync(d.X, q.ldX * sizeof(float), q.x0, (size_t)q.p * sizeof(float), (size_t)q.p * sizeof(float),
-                            q.r, q.P.x0_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    } else {
-      auto mixh = [](uint64_t z) {
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        return z ^ (z >> 31);
-      };
-      d.key = mixh(q.P.seed ^ mixh(5ull));   // the starts' stream of the single solve
-    }
-    d.gamma0 = is_pen(q.P.form) && !q.target ? q.P.gamma : 0.0;
-    for (int c = 0; c < q.r; ++c) start_prob[q.start0 + c] = i;
-    maps[4 * i + 0] = q.h->pmA.m[0];
-    maps[4 * i + 1] = q.h->pmAT.m[0];
-    GCK(make_plane_map(&maps[4 * i + 2], d.Xpl, q.r, q.ldX, 2, 64, 64));
-    GCK(make_plane_map(&maps[4 * i + 3], d.Ypl, q.r, q.ldU, 2, 64, 64));
-  }
-  // x0 must be finite (as spca_solve checks)
-  {
-    int *flag = derr;   // borrowed before the sweeps; zeroed again below
-    for (int i = 0; i < count; ++i)
-      if (hp[i].x0) GCK(launch_check_finite(P[i].X, hp[i].r, hp[i].p, hp[i].ldX, flag, st));
-    GCK(cudaMemcpyAsync(g->h_err, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GCK(cudaStreamSynchronize(st));
-    if (*g->h_err) return gfail(g, SPCA_E_INVALID, "x0 has a non-finite entry");
-    GCK(cudaMemsetAsync(derr, 0, sizeof(int), st));
-  }
-  // tile tasks: u = A x (first sweep) and v = A^T y (per parity), each list ordered by falling K
-  std::vector<GTask> tasks(3 * count);
-  int total_u = 0, total_v = 0;
-  auto build = [&](int which, int parity, int *total) {
-    std::vector<int> order(count);
-    std::iota(order.begin(), order.end(), 0);
-    auto kb = [&](int i) { return which == 0 ? (hp[i].p + 63) / 64 : (hp[i].n + 63) / 64; };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return kb(a) > kb(b); });
-    GTask *base = tasks.data() + (which == 0 ? 0 : (1 + parity) * count);
-    int t0 = 0;
-    for (int k = 0; k < count; ++k) {
-      const int i = order[k];
-      const HostProb &q = hp[i];
-      GTask &T = base[k];
-      T = GTask{};
-      const bool u = which == 0;
-      T.pmap = dmaps + 4 * i + (u ? 0 : 1);
-      T.qmap = dmaps + 4 * i + (u ? 2 : 3);
-      T.M = u ? q.n : q.p;
-      T.kblocks = kb(i);
-      T.nmax = q.r;
-      T.nb = u || !is_l1_var(q.P.form) ? 2 : 1;
-      T.n_dev = &P[i].ctrl[parity]->active;
-      T.col_map = P[i].act;
-      T.out = u ? P[i].U : P[i].V;
-      T.ldo = u ? q.ldU : q.ldX;
-      T.row_inv = u ? q.h->a_inv : q.h->at_inv;
-      T.col_inv = u ? P[i].x_inv : nullptr;
-      T.q_inv = u ? 1.0f : kQInv;
-      T.pairs = u || !is_l1_var(q.P.form) ? pairs_general() : pairs_sign();
-      T.mt = (T.M + TC_BM_ROWS - 1) / TC_BM_ROWS;
-      T.nt = (q.r + bn - 1) / bn;
-      T.tile0 = t0;
-      t0 += T.mt * T.nt;
-    }
-    *total = t0;
-  };
-  build(0, 0, &total_u);   // the first sweep reads parity 0
-  build(1, 0, &total_v);
-  build(1, 1, &total_v);
-  GCK(cudaMemcpyAsync(dP, P.data(), sizeof(GProb) * count, cudaMemcpyHostToDevice, st));
-  GCK(cudaMemcpyAsync(dmaps, maps.data(), sizeof(CUtensorMap) * 4 * count, cudaMemcpyHostToDevice, st));
-  GCK(cudaMemcpyAsync(dtasks, tasks.data(), sizeof(GTask) * 3 * count, cudaMemcpyHostToDevice, st));
-  GCK(cudaMemcpyAsync(d_start_prob, start_prob.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
-  const uint64_t wait_ns = 2000000000ull;
-
-  // ---- starts, active lists of the first sweep
-  GCK(launch_g_start_init(dP, d_start_prob, (int)R, st));
-  GCK(launch_g_active(dP, count, 0, st));
-
-  // ---- the sweeps, in captured segments of up to 4 between read-backs
-  uint64_t skey = 1469598103934665603ull;
-  skey = fnv(skey, P.data(), sizeof(GProb) * count);
-  skey = fnv(skey, tasks.data(), sizeof(GTask) * 3 * count);
-  skey = fnv(skey, &bn, sizeof bn);
-  skey = fnv(skey, &stages, sizeof stages);
-  if (g->graphs.size() > 32) {
-    GCK(cudaStreamSynchronize(st));
-    for (GroupGraph &q : g->graphs)
-      if (q.exec) cudaGraphExecDestroy(q.exec);
-    g->graphs.clear();
-  }
-  auto enqueue_sweep = [&](int k) -> cudaError_t {
-    const int cur = (k - 1) & 1, nxt = k & 1;
-    cudaError_t e;
-    if (k == 1) {
-      e = launch_g_xplanes(dP, d_start_prob, (int)R, st);
-      if (e == cudaSuccess) e = launch_gemm_grouped(dtasks, count, total_u, bn, stages, g->sms, derr, wait_ns, st);
-    } else {
-      e = launch_g_gather(dP, d_start_prob, (int)R, max_n, st);
-    }
-    if (e == cudaSuccess) e = launch_g_ystep(dP, d_start_prob, (int)R, st);
-    if (e == cudaSuccess)
-      e = launch_gemm_grouped(dtasks + (1 + cur) * count, count, total_v, bn, stages, g->sms, derr, wait_ns, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dctrl + nxt * count, 0, sizeof(Ctrl) * count, st);
-    if (e == cudaSuccess) e = launch_g_xstep(dP, d_start_prob, (int)R, max_p, nxt, g->sms, st);
-    if (e == cudaSuccess) e = launch_g_active(dP, count, nxt, st);
-    return e;
-  };
-  auto run_captured = [&](uint64_t key, auto &&body) -> int {
-    GroupGraph *gg = nullptr;
-    for (GroupGraph &q : g->graphs)
-      if (q.key == key) gg = &q;
-    if (!gg) {
-      g->graphs.emplace_back();
-      gg = &g->graphs.back();
-      gg->key = key;
-      cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
-      cudaError_t be = cudaSuccess;
-      if (ce == cudaSuccess) {
-        be = body();
-        cudaGraph_t graph = nullptr;
-        ce = cudaStreamEndCapture(st, &graph);
-        if (ce == cudaSuccess && be == cudaSuccess) ce = cudaGraphInstantiate(&gg->exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-      }
-      if (be != cudaSuccess) ce = be;
-      if (ce != cudaSuccess) {
-        g->graphs.pop_back();
-        GCK(ce);
-      }
-    }
-    GCK(cudaGraphLaunch(gg->exec, st));
-    return SPCA_OK;
-  };
-  const int check_every = 4;
-  for (int k0 = 1; k0 <= max_iter;) {
-    const int k1 = std::min(max_iter, k0 + check_every - 1);
-    uint64_t key = fnv(skey, &k0, sizeof k0);
-    key = fnv(key, &k1, sizeof k1);
-    const int rc = run_captured(key, [&]() -> cudaError_t {
-      for (int k = k0; k <= k1; ++k) {
-        cudaError_t e = enqueue_sweep(k);
-        if (e != cudaSuccess) return e;
-      }
-      return cudaSuccess;
-    });
-    if (rc != SPCA_OK) return rc;
-    GCK(cudaMemcpyAsync(g->h_ctrl, dctrl + (k1 & 1) * count, sizeof(Ctrl) * count, cudaMemcpyDeviceToHost, st));
-    GCK(cudaStreamSynchronize(st));
-    int64_t active = 0;
-    for (int i = 0; i < count; ++i) active += g->h_ctrl[i].active;
-    if (active == 0) break;
-    k0 = k1 + 1;
-  }
-  GCK(cudaMemcpyAsync(g->h_err, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
-  GCK(cudaStreamSynchronize(st));
-  if (*g->h_err) return gfail(g, *g->h_err, "a device-side wait timed out");
-
-  // ---- the Table 1 objective of every start, the best start of each problem and its outputs
-  const int rc = run_captured(fnv(skey, "fin", 3), [&]() -> cudaError_t {
-    for (int i = 0; i < count; ++i) {
-      const HostProb &q = hp[i];
-      const GProb &d = P[i];
-      cudaError_t e = launch_finalise(q.P.form, q.h->AT32, q.h->ldAT, q.n, q.p, d.X, q.ldX, d.st, q.r, d.U, q.ldU,
-                                      d.sup_idx, d.sup_val, q.p, reinterpret_cast<double *>(at(q.opart)), st);
-      if (e == cudaSuccess) e = launch_best(q.P.form, q.target, d.st, q.r, dbest + i, st);
-      if (e == cudaSuccess)
-        e = launch_best_outputs(q.P.form, dbest + i, d.U, q.ldU, q.n, d.X, q.ldX, q.p,
-                                reinterpret_cast<float *>(at(q.oyout)), reinterpret_cast<float *>(at(q.oxout)),
-                                reinterpret_cast<int64_t *>(at(q.osup)), dnnzout + i, st);
-      if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-  });
-  if (rc != SPCA_OK) return rc;
-
-  // ---- results to the host
-  std::vector<int> status(R), iters(R), best(count);
-  std::vector<double> f(R), ev(R), gam(R), F(R);
-  std::vector<int64_t> nnz(count);
-  GCK(cudaMemcpyAsync(status.data(), all.status, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(iters.data(), all.iters, sizeof(int) * R, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(f.data(), all.f, 8 * R, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(ev.data(), all.ev, 8 * R, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(gam.data(), all.gamma, 8 * R, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(F.data(), all.F, 8 * R, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(best.data(), dbest, sizeof(int) * count, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(nnz.data(), dnnzout, sizeof(int64_t) * count, cudaMemcpyDeviceToHost, st));
-  GCK(cudaStreamSynchronize(st));
-  for (int i = 0; i < count; ++i) {
-    const HostProb &q = hp[i];
-    spca_result *res = q.res;
-    if (res->x) GCK(cudaMemcpyAsync(res->x, at(q.oxout), (size_t)q.p * 4, cudaMemcpyDeviceToHost, st));
-    if (res->y) GCK(cudaMemcpyAsync(res->y, at(q.oyout), (size_t)q.n * 4, cudaMemcpyDeviceToHost, st));
-    if (res->support && nnz[i] > 0)
-      GCK(cudaMemcpyAsync(res->support, at(q.osup), (size_t)nnz[i] * 8, cudaMemcpyDeviceToHost, st));
-    if (res->start_x)
-      GCK(cudaMemcpy2DAsync(res->start_x, (size_t)q.p * 4, at(q.oX), q.ldX * 4, (size_t)q.p * 4, q.r,
-                            cudaMemcpyDeviceToHost, st));
-  }
-  GCK(cudaStreamSynchronize(st));
-  for (int i = 0; i < count; ++i) {
-    const HostProb &q = hp[i];
-    spca_result *res = q.res;
-    const int b = best[i], o = q.start0;
-    int64_t sweeps = 0;
-    int nconv = 0, ndeg = 0;
-    for (int c = 0; c < q.r; ++c) {
-      sweeps += iters[o + c];
-      nconv += status[o + c] == SPCA_ST_CONVERGED;
-      ndeg += status[o + c] == SPCA_ST_DEGENERATE;
-    }
-    res->objective = f[o + b];
-    res->explained_variance = ev[o + b];
-    res->gamma = is_pen(q.P.form) ? gam[o + b] : 0.0;
-    res->best_start = b;
-    res->best_iters = iters[o + b];
-    res->best_status = status[o + b];
-    res->converged = nconv;
-    res->degenerate = ndeg;
-    res->sweeps_total = sweeps;
-    res->nnz = nnz[i];
-    for (int c = 0; c < q.r; ++c) {
-      if (res->start_objective) res->start_objective[c] = f[o + c];
-      if (res->start_explained) res->start_explained[c] = ev[o + c];
-      if (res->start_F) res->start_F[c] = F[o + c];
-      if (res->start_iters) res->start_iters[c] = iters[o + c];
-      if (res->start_status) res->start_status[c] = status[o + c];
-      if (res->start_gamma) res->start_gamma[c] = is_pen(q.P.form) ? gam[o + c] : 0.0;
+    const int rc = admit_one(g, probs[i], tags ? tags[i] : i);
+    if (rc != SPCA_OK) {   // none of this call's problems stays admitted
+      for (size_t j = before; j < g->members.size(); ++j) release_member(g, g->members[j]);
+      g->members.resize(before);
+      g->tables_ok = false;
+      return rc;
     }
   }
   return SPCA_OK;
+}
+
+int spca_group_step(spca_group *g, int sweeps, int *finished, int cap, int *nfinished) {
+  if (!g || sweeps < 1 || (cap > 0 && !finished)) return gfail(g, SPCA_E_INVALID, "bad arguments");
+  GCK(cudaEventRecord(g->order_ev, g->user));
+  GCK(cudaStreamWaitEvent(g->stream, g->order_ev, 0));
+  return run_segment(g, sweeps, false, true, finished, cap, nfinished);
+}
+
+int spca_group_pending(const spca_group *g) { return g ? (int)g->members.size() : 0; }
+
+int spca_solve_group(spca_group *g, spca_problem *probs, int count, const spca_group_tiles *tiles) {
+  if (!g || !probs || count < 1) return gfail(g, SPCA_E_INVALID, "NULL group or problems, or count < 1");
+  if (!g->members.empty()) return gfail(g, SPCA_E_BUSY, "the group has admitted problems in progress");
+  GRC(spca_group_set_tiles(g, tiles));
+  GRC(spca_group_admit(g, probs, count, nullptr));
+  // every member stays in the tables until the last one is done, so every segment but the first
+  // (which holds the members' first sweeps) replays one captured graph
+  int max_iter = 1;
+  for (const Member &m : g->members) max_iter = std::max(max_iter, m.P.max_iter);
+  const int check_every = 4;
+  int rc = SPCA_OK;
+  for (int64_t done = 0; done < max_iter && rc == SPCA_OK;) {
+    const int seg = (int)std::min<int64_t>(check_every, max_iter - done);
+    rc = run_segment(g, seg, true, false, nullptr, 0, nullptr);
+    done += seg;
+    if (rc != SPCA_OK) break;
+    int64_t active = 0;
+    for (size_t i = 0; i < g->members.size(); ++i) active += g->h_active[i];
+    if (active == 0) break;
+  }
+  if (rc == SPCA_OK) {
+    for (Member &m : g->members)
+      if ((rc = finish_member(g, m)) != SPCA_OK) break;
+  }
+  for (Member &m : g->members) release_member(g, m);
+  g->members.clear();
+  g->tables_ok = false;
+  return rc;
 }
 
 }  // extern "C"

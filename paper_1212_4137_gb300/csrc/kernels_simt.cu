@@ -730,6 +730,24 @@ cudaError_t launch_g_active(const GProb *P, int np, int parity, cudaStream_t st)
   return cudaGetLastError();
 }
 
+// the control words of one sweep parity: cleared before an x-step, and their active counts gathered
+// for the host (out[i] = problem i's count)
+__global__ void k_g_ctrl(const GProb *__restrict__ P, int np, int parity, int clear, int *__restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+    Ctrl *c = P[i].ctrl[parity];
+    if (clear) {
+      *c = Ctrl{};
+    } else {
+      out[i] = c->active;
+    }
+  }
+}
+
+cudaError_t launch_g_ctrl(const GProb *P, int np, int parity, int clear, int *out, cudaStream_t st) {
+  k_g_ctrl<<<(np + 255) / 256, 256, 0, st>>>(P, np, parity, clear, out);
+  return cudaGetLastError();
+}
+
 // FP16 planes of x for the dense u = A x (the first sweep): per active start, the power-of-two
 // scale putting max |x_j| in [2^13, 2^14), then hi = fp16(s x), lo = fp16(s x - hi) at the start's
 // packed row (its rank), and 1 / s at the same index
@@ -737,7 +755,8 @@ __global__ void __launch_bounds__(256) k_g_xplanes(const GProb *__restrict__ P, 
   __shared__ unsigned red[32];
   const GProb &q = P[prob[blockIdx.x]];
   const int c = (int)blockIdx.x - q.start0;
-  if (q.st.status[c] != ST_ACTIVE) return;
+  // only starts not swept yet (a problem's first sweep; the others take the support gather)
+  if (q.st.status[c] != ST_ACTIVE || q.st.iters[c] != 0) return;
   const float *x = q.X + (int64_t)c * q.ldX;
   unsigned mk = 0u;
   for (int j = threadIdx.x; j < q.p; j += blockDim.x) mk = max(mk, __float_as_uint(fabsf(x[j])));

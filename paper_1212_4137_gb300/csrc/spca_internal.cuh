@@ -412,6 +412,8 @@ struct GProb {
 // global start g, R starts in all)
 cudaError_t launch_g_start_init(const GProb *P, const int *prob, int R, cudaStream_t st);
 cudaError_t launch_g_active(const GProb *P, int np, int parity, cudaStream_t st);
+// clear (clear != 0) the control words of one parity, or gather their active counts into out[np]
+cudaError_t launch_g_ctrl(const GProb *P, int np, int parity, int clear, int *out, cudaStream_t st);
 cudaError_t launch_g_xplanes(const GProb *P, const int *prob, int R, cudaStream_t st);
 cudaError_t launch_g_gather(const GProb *P, const int *prob, int R, int max_n, cudaStream_t st);
 cudaError_t launch_g_ystep(const GProb *P, const int *prob, int R, cudaStream_t st);

@@ -24,6 +24,7 @@ SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC, SPCA_ENGINE_TC_LOWP = 0, 1, 
 EXPORTS = ("spca_create", "spca_create_csr", "spca_clone", "spca_solve", "spca_xstep", "spca_products", "spca_deflate", "spca_profile_enable",
            "spca_profile_query", "spca_objective_noalloc", "spca_set_waits",
            "spca_group_create", "spca_group_destroy", "spca_group_last_error", "spca_solve_group",
+           "spca_group_set_tiles", "spca_group_admit", "spca_group_step", "spca_group_pending",
            "spca_destroy", "spca_strerror", "spca_last_error")
 SPCA_K_ALL, SPCA_K_INIT, SPCA_K_U_DENSE, SPCA_K_U_SPARSE, SPCA_K_YSTEP, SPCA_K_V, SPCA_K_XSTEP, \
     SPCA_K_FINALISE, SPCA_K_PREP = range(-1, 8)
@@ -117,6 +118,14 @@ def load(path: str = LIB_PATH):
         lib.spca_solve_group.restype = ctypes.c_int
         lib.spca_solve_group.argtypes = [ctypes.c_void_p, ctypes.POINTER(spca_problem), ctypes.c_int,
                                          ctypes.POINTER(spca_group_tiles)]
+        lib.spca_group_set_tiles.restype = ctypes.c_int
+        lib.spca_group_set_tiles.argtypes = [ctypes.c_void_p, ctypes.POINTER(spca_group_tiles)]
+        lib.spca_group_admit.restype = ctypes.c_int
+        lib.spca_group_admit.argtypes = [ctypes.c_void_p, ctypes.POINTER(spca_problem), ctypes.c_int, _ip]
+        lib.spca_group_step.restype = ctypes.c_int
+        lib.spca_group_step.argtypes = [ctypes.c_void_p, ctypes.c_int, _ip, ctypes.c_int, _ip]
+        lib.spca_group_pending.restype = ctypes.c_int
+        lib.spca_group_pending.argtypes = [ctypes.c_void_p]
         lib.spca_set_waits.restype = ctypes.c_int
         lib.spca_set_waits.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
         lib.spca_deflate.restype = ctypes.c_int
@@ -369,20 +378,19 @@ class Group:
     def last_error(self) -> str:
         return load().spca_group_last_error(self.g).decode()
 
-    def solve(self, problems, tiles=None, want_starts=False):
-        """problems: list of (Handle, form, r, kwargs) with the keyword arguments of Handle.solve
-        (x0: host array or device address with x0_device=True).  tiles: (tile_n, stages), "auto"
-        (the measured shape of tuning.py's table) or None (the library's default).
-        Returns one result dict per problem, as Handle.solve does."""
+    def _problems(self, problems, want_starts):
+        """The C array for `problems` and, per problem, its result buffers and the host arrays that
+        must outlive the call."""
         count = len(problems)
         arr = (spca_problem * count)()
-        keep, outs = [], []
+        entries = []
         for i, (h, form, r, kw) in enumerate(problems):
             kw = dict(kw)
             x0 = kw.pop("x0", None)
             ws = kw.pop("want_starts", want_starts)
             prm = make_params(form, r, **kw)
             out, res = _result_buffers(h.n, h.p, r, ws)
+            keep = [res]
             if x0 is not None and not prm.x0_is_device:
                 x0 = np.ascontiguousarray(x0, dtype=np.float32)
                 assert x0.shape == (r, h.p)
@@ -390,20 +398,67 @@ class Group:
                 x0p = x0.ctypes.data
             else:
                 x0p = x0
-            keep.append(res)
             arr[i].h = h.h
             arr[i].prm = prm
             arr[i].x0 = x0p
             arr[i].res = ctypes.pointer(res)
-            outs.append((out, res))
+            entries.append((out, res, keep))
+        return arr, entries
+
+    def _fail(self, st, what):
+        raise SpcaError(st, f"{what} failed: {spca_strerror(st)} {self.last_error()}")
+
+    def solve(self, problems, tiles=None, want_starts=False):
+        """problems: list of (Handle, form, r, kwargs) with the keyword arguments of Handle.solve
+        (x0: host array or device address with x0_device=True).  tiles: (tile_n, stages), "auto"
+        (the measured shape of tuning.py's table) or None (the library's default).
+        Returns one result dict per problem, as Handle.solve does."""
+        arr, entries = self._problems(problems, want_starts)
         if tiles == "auto":   # the measured shape for this mix's bucket (tuning.py), else the default
             from . import tuning
             tiles = tuning.choose(max(r for _, _, r, _ in problems))
         t = spca_group_tiles(*(tiles or (0, 0)))
-        st = load().spca_solve_group(self.g, arr, count, ctypes.byref(t))
+        st = load().spca_solve_group(self.g, arr, len(problems), ctypes.byref(t))
         if st != SPCA_OK:
-            raise SpcaError(st, f"spca_solve_group failed: {spca_strerror(st)} {self.last_error()}")
-        return [_result_dict(out, res) for out, res in outs]
+            self._fail(st, "spca_solve_group")
+        return [_result_dict(out, res) for out, res, _ in entries]
+
+    # ---- the group as a session: admit problems while others run, step their sweeps
+    def set_tiles(self, tiles=None):
+        t = spca_group_tiles(*(tiles or (0, 0)))
+        st = load().spca_group_set_tiles(self.g, ctypes.byref(t))
+        if st != SPCA_OK:
+            self._fail(st, "spca_group_set_tiles")
+
+    def admit(self, problems, tags, want_starts=False):
+        """Admit problems (as for solve) under integer tags; their results come back from step()."""
+        arr, entries = self._problems(problems, want_starts)
+        tg = (ctypes.c_int * len(tags))(*tags)
+        st = load().spca_group_admit(self.g, arr, len(problems), tg)
+        if st != SPCA_OK:
+            self._fail(st, "spca_group_admit")
+        if not hasattr(self, "_held"):
+            self._held = {}
+        for t, e in zip(tags, entries):
+            self._held[int(t)] = e
+
+    def step(self, sweeps: int = 4):
+        """Run `sweeps` sweeps of every member; returns [(tag, result dict)] of the members that
+        finished."""
+        cap = max(1, self.pending())
+        fin = (ctypes.c_int * cap)()
+        nf = ctypes.c_int(0)
+        st = load().spca_group_step(self.g, int(sweeps), fin, cap, ctypes.byref(nf))
+        if st != SPCA_OK:
+            self._fail(st, "spca_group_step")
+        done = []
+        for i in range(min(nf.value, cap)):
+            out, res, _ = self._held.pop(int(fin[i]))
+            done.append((int(fin[i]), _result_dict(out, res)))
+        return done
+
+    def pending(self) -> int:
+        return int(load().spca_group_pending(self.g))
 
     def close(self):
         if getattr(self, "g", None):

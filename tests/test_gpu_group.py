@@ -113,3 +113,37 @@ def test_group_rejects_bad_problems(lib):
     g.close()
     h.close()
     hs.close()
+
+
+def test_group_session_admits_while_others_run(lib):
+    """Continuous batching at sweep boundaries: problems admitted at different times into a running
+    group sweep in the same launches as the others; each problem's result is bit for bit its result
+    alone (a group of one), whatever else is in the mix."""
+    probs = _draw(9, 3)
+    r = 32
+    handles = [lib.Handle(A) for A, _, _ in probs]
+    kws = [dict(kw, seed=500 + i, max_iter=[12, 30, 60][i % 3], tol=1e-7 if i % 2 else -1)
+           for i, (A, form, kw) in enumerate(probs)]
+    alone = []
+    g1 = lib.Group()
+    for h, (A, form, _), kw in zip(handles, probs, kws):
+        alone.append(g1.solve([(h, form, r, kw)], want_starts=True)[0])
+    g1.close()
+    g = lib.Group()
+    done = {}
+    waves = [[0, 1, 2], [3, 4], [5], [6, 7, 8]]
+    for wave in waves:
+        g.admit([(handles[i], probs[i][1], r, kws[i]) for i in wave], wave, want_starts=True)
+        for tag, out in g.step(4):
+            done[tag] = out
+    while g.pending():
+        for tag, out in g.step(4):
+            done[tag] = out
+    assert sorted(done) == list(range(len(probs)))
+    for i, out in done.items():
+        assert np.array_equal(out["start_x"], alone[i]["start_x"]), i
+        assert np.array_equal(out["start_iters"], alone[i]["start_iters"]), i
+        assert out["objective"] == alone[i]["objective"] and out["best_start"] == alone[i]["best_start"], i
+    g.close()
+    for h in handles:
+        h.close()
