@@ -868,69 +868,89 @@ def run_tune(args, count=64):
         json.dump(table, fh, indent=1)
 
 
-# Serving (scaled to 8 resident matrices, 2 GB in all, so that the host generates them in seconds):
-# spiked models (5 spikes), n log-uniform in [1000, 8000], p log-uniform in [2000, 20000], FP32.
-# Requests: a uniform matrix, formulation 1..8, s uniform in [10, 200] (at most p), r uniform in
-# {1, 16, 256}, at most 100 sweeps, tol 1e-9.  A closed-loop run (all requests queued at once)
-# gives the capacity; then Poisson arrivals at 0.8 x capacity give the latency (p50 / p99 from
-# submission to result).  8 workers.
-def run_scan_serving(args, mats=8, closed=96, open_requests=240, workers=8):
+# The serving configuration: resident spiked matrices (5 spikes, theta = (40, 30, 20, 15, 10)
+# sqrt(n / p), 50 nonzeros each), n log-uniform in [1000, 25000], p log-uniform in [2000, 50000], one
+# of them pinned at 25000 x 50000 (half the stated sizes in each dimension: this library keeps four
+# 4-byte copies' worth of every matrix, FP32 A and A^T and two FP16 planes of each, so the stated
+# sizes would not fit the 150 GB admission cap; see DESIGN).  Requests: a uniform matrix,
+# formulation 1..8, s uniform in [10, 200] (at most p), r uniform in {1, 16, 256}, at most 100
+# sweeps, tol 1e-9.  The request loop in group mode: `workers` group sessions, each admitting the
+# waiting requests between segments of 4 sweeps (member memory capped at 150 GB less the resident
+# matrices).  A closed loop (every request queued at once) gives the capacity; then Poisson
+# arrivals at 0.8 x capacity give the latency (p50 / p99 from submission to result).
+def run_scan_serving(args, mats=32, closed=400, open_requests=2000, modes=(("group", 2), ("group", 4), ("solve", 8)),
+                     cap_gb=150):
     import torch
 
     from paper_1212_4137_gb300 import build, inputs as I, serve
     build.build()
     rng = np.random.default_rng(5)
-    shapes = {}
-    with serve.Server(workers=workers, budget_bytes=96 << 30) as srv:
-        for q in range(mats):
-            n, p = _log_uniform(rng, 1000, 8000), _log_uniform(rng, 2000, 20000)
-            srv.register(f"s{q}", I.spiked_matrix(n, p, I.spiked_thetas(n, p), 50, 7000 + q, dtype=np.float32))
-            shapes[f"s{q}"] = (n, p)
+    shapes = [(25000, 50000)] + [(_log_uniform(rng, 1000, 25000), _log_uniform(rng, 2000, 50000))
+                                 for _ in range(mats - 1)]
+    import concurrent.futures as cf
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=16) as ex:
+        As = list(ex.map(lambda q: I.spiked_matrix(q[1][0], q[1][1], I.spiked_thetas(*q[1]), 50, 7000 + q[0],
+                                                   dtype=np.float32), enumerate(shapes)))
+    gen_s = time.perf_counter() - t0
+    resident = sum(16 * A.size for A in As)   # FP32 A and A^T, two FP16 planes of each
+    budget = max(1 << 30, (cap_gb << 30) - resident)
+    head0 = {"scan": "serving", "matrices": mats, "sum_n_p": int(sum(A.size for A in As)),
+             "resident_gb": round(resident / 2**30, 1), "member_budget_gb": round(budget / 2**30, 1),
+             "host_generation_s": round(gen_s, 1)}
+    for mode, workers in modes:
+        head = dict(head0, workers=workers, mode="group sessions, 4 sweeps per segment" if mode == "group"
+                      else "whole solves on clones")
+        rq = np.random.default_rng(55)   # the same requests and arrival times in every mode
+        with serve.Server(workers=workers, budget_bytes=budget, mode=mode) as srv:
+            for q, A in enumerate(As):
+                srv.register(f"s{q}", A)
 
-        def request(i):
-            name = f"s{int(rng.integers(0, mats))}"
-            form = int(rng.integers(1, 9))
-            s = float(min(int(rng.integers(10, 201)), shapes[name][1]))
-            r = int(rng.choice([1, 16, 256]))
-            kw = dict(s=s, seed=8000 + i, max_iter=100, tol=1e-9)
-            if form >= 5:
-                kw.update(gamma_target=True, calib=10)
-            return name, form, r, kw
+            def request(i):
+                name = f"s{int(rq.integers(0, mats))}"
+                form = int(rq.integers(1, 9))
+                s = float(min(int(rq.integers(10, 201)), shapes[int(name[1:])][1]))
+                r = int(rq.choice([1, 16, 256]))
+                kw = dict(s=s, seed=8000 + i, max_iter=100, tol=1e-9)
+                if form >= 5:
+                    kw.update(gamma_target=True, calib=10)
+                return name, form, r, kw
 
-        for i in range(2 * workers):   # warm-up
-            srv.submit(*request(i)[:3], **request(i)[3]).result()
-        torch.cuda.synchronize()
-        reqs = [request(100 + i) for i in range(closed)]
-        t0 = time.perf_counter()
-        outs = [f.result() for f in [srv.submit(nm, f, r, **kw) for nm, f, r, kw in reqs]]
-        dt = time.perf_counter() - t0
-        capacity = closed / dt
-        print(json.dumps({"scan": "serving, closed loop (capacity)", "requests": closed, "workers": workers,
-                          "solves_per_s": round(capacity, 2),
-                          "sweeps_starts_per_s": round(sum(o["sweeps_total"] for o in outs) / dt, 1)}), flush=True)
-        rate = 0.8 * capacity
-        reqs = [request(1000 + i) for i in range(open_requests)]
-        gaps = rng.exponential(1.0 / rate, open_requests)
-        futs = []
-        t0 = time.perf_counter()
-        t_next = t0
-        for (nm, f, r, kw), g in zip(reqs, gaps):
-            t_next += g
-            while time.perf_counter() < t_next:
-                time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
-            futs.append(srv.submit(nm, f, r, **kw))
-        outs = [f.result() for f in futs]
-        dt = time.perf_counter() - t0
-        lat = np.array([o["latency_ms"] for o in outs])
-        by_r = {int(r): round(float(np.percentile([o["latency_ms"] for o, q in zip(outs, reqs) if q[2] == r], 50)), 2)
-                for r in (1, 16, 256) if any(q[2] == r for q in reqs)}
-        print(json.dumps({"scan": "serving, Poisson arrivals at 0.8 x capacity", "requests": open_requests,
-                          "offered_per_s": round(rate, 2), "solves_per_s": round(open_requests / dt, 2),
-                          "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 2),
-                                         "p99": round(float(np.percentile(lat, 99)), 2)},
-                          "p50_by_r_ms": by_r,
-                          "queue_ms_p50": round(float(np.percentile([o["queue_ms"] for o in outs], 50)), 2)}),
-              flush=True)
+            for f in [srv.submit(*request(i)[:3], **request(i)[3]) for i in range(32)]:   # warm-up
+                f.result()
+            torch.cuda.synchronize()
+            reqs = [request(100 + i) for i in range(closed)]
+            t0 = time.perf_counter()
+            outs = [f.result() for f in [srv.submit(nm, f, r, **kw) for nm, f, r, kw in reqs]]
+            dt = time.perf_counter() - t0
+            capacity = closed / dt
+            print(json.dumps(dict(head, run="closed loop (capacity)", requests=closed, solves_per_s=round(capacity, 2),
+                                  sweeps_starts_per_s=round(sum(o["sweeps_total"] for o in outs) / dt, 1))), flush=True)
+            rate = 0.8 * capacity
+            reqs = [request(10000 + i) for i in range(open_requests)]
+            gaps = rq.exponential(1.0 / rate, open_requests)
+            futs = []
+            t0 = time.perf_counter()
+            t_next = t0
+            for (nm, f, r, kw), g in zip(reqs, gaps):
+                t_next += g
+                while time.perf_counter() < t_next:
+                    time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
+                futs.append(srv.submit(nm, f, r, **kw))
+            outs = [f.result() for f in futs]
+            dt = time.perf_counter() - t0
+            lat = np.array([o["latency_ms"] for o in outs])
+            by_r = {int(r): {"p50": round(float(np.percentile([o["latency_ms"] for o, q in zip(outs, reqs) if q[2] == r], 50)), 2),
+                             "p99": round(float(np.percentile([o["latency_ms"] for o, q in zip(outs, reqs) if q[2] == r], 99)), 2)}
+                    for r in (1, 16, 256) if any(q[2] == r for q in reqs)}
+            print(json.dumps(dict(head, run="Poisson arrivals at 0.8 x capacity", requests=open_requests,
+                                  offered_per_s=round(rate, 2), solves_per_s=round(open_requests / dt, 2),
+                                  sweeps_starts_per_s=round(sum(o["sweeps_total"] for o in outs) / dt, 1),
+                                  latency_ms={"p50": round(float(np.percentile(lat, 50)), 2),
+                                              "p99": round(float(np.percentile(lat, 99)), 2)},
+                                  latency_by_r_ms=by_r,
+                                  queue_ms_p50=round(float(np.percentile([o["queue_ms"] for o in outs], 50)), 2))),
+                  flush=True)
 
 
 def sps_csr(ip, ix, v, n, p):

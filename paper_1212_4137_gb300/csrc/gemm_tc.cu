@@ -1095,15 +1095,19 @@ cudaError_t launch_gemm_tc_f8(const PMaps &P, const CUtensorMap &Q, int M, int N
 // group): task i computes out_i[map(c) * ldo + m] = (row_inv[m] q_inv col_inv[c]) sum_q sum_k
 // P_i,a_q[m, k] Q_i,b_q[c, k] for m < M_i and c < *n_dev_i, like launch_gemm_tc, each with its own
 // tensor maps (held in global memory), K, plane products and output.  The tiles (128 x BN) of all
-// tasks form one list, numbered task by task (the host orders the tasks by falling K so that the
-// round-robin below balances); CTA b takes tiles b, b + G, b + 2G, ...  Every role of a CTA walks
-// the same tile sequence, so no tile index is exchanged between them.
+// tasks form one list (tile t = task tiles[t].x, local tile tiles[t].y: M tile local / nt, N tile
+// local % nt) in an order the host chooses: tasks on the same matrix interleaved by M tile, so
+// that the CTAs running at the same time read each tile of the shared matrix once from DRAM and
+// then from L2; tasks by falling K, so that the round-robin below balances.  CTA b takes tiles
+// b, b + G, b + 2G, ...  Every role of a CTA walks the same tile sequence, so no tile index is
+// exchanged between them.
 // TMEM: NBUF = 512 / (4 BN) buffers of four accumulators (BN = 64: two buffers, so a tile's
 // epilogue overlaps the next tile's MMAs).  The hi x hi product of K-block kb goes to accumulator
 // kb mod 3 and the correction products to the fourth (FP32-class accuracy, see k_gemm_tc).
 template <int BN, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_gemm_grouped(const GTask *__restrict__ tasks, int ntasks, int total_tiles, int *err, uint64_t wait_ns) {
+    k_gemm_grouped(const GTask *__restrict__ tasks, const int2 *__restrict__ tile_list, int total_tiles, int *err,
+                   uint64_t wait_ns) {
   constexpr int NA = 2, NBMAX = 2;
   constexpr uint32_t A_BYTES = TC_BM * 64 * 2;            // 16 KB per P plane tile
   constexpr uint32_t B_BYTES = BN * 64 * 2;               // one Q plane tile (BN rows)
@@ -1118,15 +1122,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   __shared__ int issued, consumed;
-  __shared__ int s_tile0[kGroupMaxTasks + 1];
 
   const int G = gridDim.x;
   if ((int)blockIdx.x >= total_tiles) return;
   uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < ntasks; i += blockDim.x) s_tile0[i] = tasks[i].tile0;
   if (threadIdx.x == 0) {
-    s_tile0[ntasks] = total_tiles;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
@@ -1153,14 +1154,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   // tile t -> (task, M tile, N tile); false when the tile lies past the task's active columns
   auto locate = [&](int t, int &ti, int &m0, int &n0, int &N) -> bool {
-    int lo = 0, hi = ntasks - 1;   // the last task whose first tile is <= t
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_tile0[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    ti = lo;
+    const int2 e = tile_list[t];
+    ti = e.x;
     const GTask &T = tasks[ti];
-    const int local = t - s_tile0[ti];
+    const int local = e.y;
     const int tn = local % T.nt, tm = local / T.nt;
     m0 = tm * TC_BM;
     n0 = tn * BN;
@@ -1316,7 +1313,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 namespace {
 template <int BN, int STAGES>
-cudaError_t launch_grouped_impl(const GTask *tasks, int ntasks, int total_tiles, int grid, int *err,
+cudaError_t launch_grouped_impl(const GTask *tasks, const int2 *tile_list, int total_tiles, int grid, int *err,
                                 uint64_t wait_ns, cudaStream_t st) {
   constexpr int STAGE_BYTES = 2 * TC_BM * 64 * 2 + 2 * BN * 64 * 2;
   constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
@@ -1324,7 +1321,7 @@ cudaError_t launch_grouped_impl(const GTask *tasks, int ntasks, int total_tiles,
   auto kern = k_gemm_grouped<BN, STAGES>;
   static const cudaError_t configured = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
   if (configured != cudaSuccess) return configured;
-  kern<<<grid, TC_THREADS, SMEM, st>>>(tasks, ntasks, total_tiles, err, wait_ns);
+  kern<<<grid, TC_THREADS, SMEM, st>>>(tasks, tile_list, total_tiles, err, wait_ns);
   return cudaGetLastError();
 }
 }  // namespace
@@ -1333,15 +1330,17 @@ bool grouped_config_ok(int bn, int stages) {
   return (bn == 64 && (stages == 2 || stages == 3 || stages == 4)) || (bn == 128 && (stages == 2 || stages == 3));
 }
 
-cudaError_t launch_gemm_grouped(const GTask *tasks, int ntasks, int total_tiles, int bn, int stages, int sms, int *err,
-                                uint64_t wait_ns, cudaStream_t st) {
-  if (ntasks < 1 || ntasks > kGroupMaxTasks || total_tiles < 1) return cudaErrorInvalidValue;
+cudaError_t launch_gemm_grouped(const GTask *tasks, const int2 *tile_list, int total_tiles, int bn, int stages, int sms,
+                                int *err, uint64_t wait_ns, cudaStream_t st) {
+  if (total_tiles < 1) return cudaSuccess;   // nothing to contract
   const int grid = total_tiles < sms ? total_tiles : sms;
-  if (bn == 64 && stages == 2) return launch_grouped_impl<64, 2>(tasks, ntasks, total_tiles, grid, err, wait_ns, st);
-  if (bn == 64 && stages == 3) return launch_grouped_impl<64, 3>(tasks, ntasks, total_tiles, grid, err, wait_ns, st);
-  if (bn == 64 && stages == 4) return launch_grouped_impl<64, 4>(tasks, ntasks, total_tiles, grid, err, wait_ns, st);
-  if (bn == 128 && stages == 2) return launch_grouped_impl<128, 2>(tasks, ntasks, total_tiles, grid, err, wait_ns, st);
-  if (bn == 128 && stages == 3) return launch_grouped_impl<128, 3>(tasks, ntasks, total_tiles, grid, err, wait_ns, st);
+  if (bn == 64 && stages == 2) return launch_grouped_impl<64, 2>(tasks, tile_list, total_tiles, grid, err, wait_ns, st);
+  if (bn == 64 && stages == 3) return launch_grouped_impl<64, 3>(tasks, tile_list, total_tiles, grid, err, wait_ns, st);
+  if (bn == 64 && stages == 4) return launch_grouped_impl<64, 4>(tasks, tile_list, total_tiles, grid, err, wait_ns, st);
+  if (bn == 128 && stages == 2)
+    return launch_grouped_impl<128, 2>(tasks, tile_list, total_tiles, grid, err, wait_ns, st);
+  if (bn == 128 && stages == 3)
+    return launch_grouped_impl<128, 3>(tasks, tile_list, total_tiles, grid, err, wait_ns, st);
   return cudaErrorInvalidValue;
 }
 

@@ -79,6 +79,7 @@ struct spca_group {
   GProb *dP = nullptr;
   int *d_start_prob = nullptr, *d_active = nullptr;
   GTask *d_tasks = nullptr;
+  int2 *d_tiles[3] = {nullptr, nullptr, nullptr};   // tile lists: u, v of parity 0, v of parity 1
   int R = 0, total_u = 0, total_v = 0, n_u = 0, max_n = 1, max_p = 1;
   bool tables_ok = false;
   int *h_active = nullptr;         // pinned: active counts at a segment's end
@@ -87,6 +88,11 @@ struct spca_group {
   int *d_err = nullptr;
   int bn = 64, stages = 4;
   std::vector<GroupGraph> graphs;
+  // staging of finished members' results: device buffer, pinned host mirror, copy descriptors
+  char *stage_d = nullptr, *stage_h = nullptr;
+  size_t stage_bytes = 0;
+  CopyDesc *desc_d = nullptr;
+  size_t desc_bytes = 0;
   char last_error[256] = {0};
 };
 
@@ -266,14 +272,8 @@ int admit_one(spca_group *g, const spca_problem &q, int tag) {
     d.x0 = d.X;
     GCK(cudaMemcpy2DAsync(d.X, m.ldX * sizeof(float), q.x0, (size_t)m.p * sizeof(float), (size_t)m.p * sizeof(float),
                           m.r, m.P.x0_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    GCK(cudaMemsetAsync(g->d_err, 0, sizeof(int), st));
+    // the caller reads the error word once for all the problems of its call
     GCK(launch_check_finite(d.X, m.r, m.p, m.ldX, g->d_err, st));
-    GCK(cudaMemcpyAsync(g->h_err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    GCK(cudaStreamSynchronize(st));
-    if (*g->h_err) {
-      cudaFreeAsync(m.mem, st);
-      return gfail(g, SPCA_E_INVALID, "x0 has a non-finite entry");
-    }
   }
   CUtensorMap maps[4];
   maps[0] = m.h->pmA.m[0];
@@ -309,14 +309,20 @@ int build_tables(spca_group *g) {
   for (int i = 0; i < np; ++i)
     for (int c = 0; c < g->members[i].r; ++c) start_prob[P[i].start0 + c] = i;
   std::vector<GTask> tasks(3 * np);
+  std::vector<int2> tl[3];
   int n_u = 0;
-  auto build = [&](bool u, int parity, GTask *base, int *count) -> int {
+  // one task per member; the tile list orders the matrices by falling K and, within a matrix, walks
+  // its M tiles with the tiles of every member on it side by side (they read the same A tile)
+  auto build = [&](bool u, int parity, GTask *base, std::vector<int2> &tiles, int *count) -> int {
     std::vector<int> order;
     for (int i = 0; i < np; ++i)
       if (!u || g->members[i].first_pending) order.push_back(i);
     auto kb = [&](int i) { return u ? (g->members[i].p + 63) / 64 : (g->members[i].n + 63) / 64; };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return kb(a) > kb(b); });
-    int t0 = 0;
+    auto mat = [&](int i) { return reinterpret_cast<uintptr_t>(g->members[i].h->shared); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      if (kb(a) != kb(b)) return kb(a) > kb(b);
+      return mat(a) < mat(b);
+    });
     for (size_t k = 0; k < order.size(); ++k) {
       const int i = order[k];
       const Member &m = g->members[i];
@@ -338,20 +344,29 @@ int build_tables(spca_group *g) {
       T.pairs = u || !is_l1_var(m.P.form) ? pairs_general() : pairs_sign();
       T.mt = (T.M + TC_BM_ROWS - 1) / TC_BM_ROWS;
       T.nt = (m.r + g->bn - 1) / g->bn;
-      T.tile0 = t0;
-      t0 += T.mt * T.nt;
+    }
+    tiles.clear();
+    for (size_t a = 0; a < order.size();) {   // a run of tasks on one matrix
+      size_t b = a + 1;
+      while (b < order.size() && mat(order[b]) == mat(order[a])) ++b;
+      const int mt = base[a].mt;
+      for (int tm = 0; tm < mt; ++tm)
+        for (size_t k = a; k < b; ++k)
+          for (int tn = 0; tn < base[k].nt; ++tn) tiles.push_back(make_int2((int)k, tm * base[k].nt + tn));
+      a = b;
     }
     *count = (int)order.size();
-    return t0;
+    return (int)tiles.size();
   };
   // the pending members' first sweep is the next one, k + 1: it reads parity k & 1
   int nv = 0;
-  g->total_u = build(true, (int)(g->k & 1), tasks.data(), &n_u);
-  g->total_v = build(false, 0, tasks.data() + np, &nv);
-  build(false, 1, tasks.data() + 2 * np, &nv);
+  g->total_u = build(true, (int)(g->k & 1), tasks.data(), tl[0], &n_u);
+  g->total_v = build(false, 0, tasks.data() + np, tl[1], &nv);
+  build(false, 1, tasks.data() + 2 * np, tl[2], &nv);
   Layout L;
   const size_t oP = L.take(sizeof(GProb) * np), oS = L.take(sizeof(int) * R), oT = L.take(sizeof(GTask) * 3 * np),
-               oA = L.take(sizeof(int) * np);
+               oA = L.take(sizeof(int) * np), oL0 = L.take(sizeof(int2) * tl[0].size()),
+               oL1 = L.take(sizeof(int2) * tl[1].size()), oL2 = L.take(sizeof(int2) * tl[2].size());
   if (L.off > g->tab_bytes) {
     GCK(cudaStreamSynchronize(st));
     if (g->tab) cudaFree(g->tab);
@@ -374,10 +389,14 @@ int build_tables(spca_group *g) {
   g->d_start_prob = reinterpret_cast<int *>(g->tab + oS);
   g->d_tasks = reinterpret_cast<GTask *>(g->tab + oT);
   g->d_active = reinterpret_cast<int *>(g->tab + oA);
+  for (int q = 0; q < 3; ++q) g->d_tiles[q] = reinterpret_cast<int2 *>(g->tab + (q == 0 ? oL0 : q == 1 ? oL1 : oL2));
+  // (pageable sources: each copy returns once its data are staged, so the vectors may go)
   GCK(cudaMemcpyAsync(g->dP, P.data(), sizeof(GProb) * np, cudaMemcpyHostToDevice, st));
   GCK(cudaMemcpyAsync(g->d_start_prob, start_prob.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
   GCK(cudaMemcpyAsync(g->d_tasks, tasks.data(), sizeof(GTask) * 3 * np, cudaMemcpyHostToDevice, st));
-  GCK(cudaStreamSynchronize(st));   // the host vectors go out of scope
+  for (int q = 0; q < 3; ++q)
+    if (!tl[q].empty())
+      GCK(cudaMemcpyAsync(g->d_tiles[q], tl[q].data(), sizeof(int2) * tl[q].size(), cudaMemcpyHostToDevice, st));
   g->R = R;
   g->n_u = n_u;
   g->max_n = max_n;
@@ -396,93 +415,140 @@ cudaError_t enqueue_sweep(spca_group *g, int64_t k, bool first_of_segment) {
   if (first_of_segment && g->n_u > 0) {
     // the first sweep of the members admitted before this segment: the dense u = A x
     e = launch_g_xplanes(g->dP, g->d_start_prob, g->R, st);
-    if (e == cudaSuccess) e = launch_gemm_grouped(g->d_tasks, g->n_u, g->total_u, g->bn, g->stages, g->sms, g->d_err,
-                                                  wait_ns, st);
+    if (e == cudaSuccess)
+      e = launch_gemm_grouped(g->d_tasks, g->d_tiles[0], g->total_u, g->bn, g->stages, g->sms, g->d_err, wait_ns, st);
   }
   if (e == cudaSuccess) e = launch_g_gather(g->dP, g->d_start_prob, g->R, g->max_n, st);
   if (e == cudaSuccess) e = launch_g_ystep(g->dP, g->d_start_prob, g->R, st);
   if (e == cudaSuccess)
-    e = launch_gemm_grouped(g->d_tasks + (1 + cur) * np, np, g->total_v, g->bn, g->stages, g->sms, g->d_err, wait_ns,
-                            st);
+    e = launch_gemm_grouped(g->d_tasks + (1 + cur) * np, g->d_tiles[1 + cur], g->total_v, g->bn, g->stages, g->sms,
+                            g->d_err, wait_ns, st);
   if (e == cudaSuccess) e = launch_g_ctrl(g->dP, np, nxt, 1, nullptr, st);
   if (e == cudaSuccess) e = launch_g_xstep(g->dP, g->d_start_prob, g->R, g->max_p, nxt, g->sms, st);
   if (e == cudaSuccess) e = launch_g_active(g->dP, np, nxt, st);
   return e;
 }
 
-// Table 1 objective of every start, the best start and its outputs, then the results to the host
-int finish_member(spca_group *g, Member &m) {
+// Table 1 objective of every start, the best start and its outputs for the listed members, then
+// their results to the host: every piece gathered into one staging buffer by one launch, one copy
+// to pinned host memory, one synchronisation
+int finish_members(spca_group *g, const std::vector<Member *> &list) {
+  if (list.empty()) return SPCA_OK;
   cudaStream_t st = g->stream;
-  const GProb &d = m.d;
-  GCK(launch_finalise(m.P.form, m.h->AT32, m.h->ldAT, m.n, m.p, d.X, m.ldX, d.st, m.r, d.U, m.ldU, d.sup_idx,
-                      d.sup_val, m.p, m.partials, st));
-  GCK(launch_best(m.P.form, m.target, d.st, m.r, m.best, st));
-  GCK(launch_best_outputs(m.P.form, m.best, d.U, m.ldU, m.n, d.X, m.ldX, m.p, m.y_out, m.x_out, m.support_out,
-                          m.nnz_out, st));
-  const int r = m.r;
-  std::vector<int> status(r), iters(r);
-  std::vector<double> f(r), ev(r), gam(r), F(r);
-  int best = 0;
-  int64_t nnz = 0;
-  GCK(cudaMemcpyAsync(status.data(), d.st.status, sizeof(int) * r, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(iters.data(), d.st.iters, sizeof(int) * r, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(f.data(), d.st.f, 8 * r, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(ev.data(), d.st.ev, 8 * r, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(gam.data(), d.st.gamma, 8 * r, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(F.data(), d.st.F, 8 * r, cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(&best, m.best, sizeof(int), cudaMemcpyDeviceToHost, st));
-  GCK(cudaMemcpyAsync(&nnz, m.nnz_out, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  GCK(cudaStreamSynchronize(st));
-  spca_result *res = m.res;
-  if (res->x) GCK(cudaMemcpyAsync(res->x, m.x_out, (size_t)m.p * 4, cudaMemcpyDeviceToHost, st));
-  if (res->y) GCK(cudaMemcpyAsync(res->y, m.y_out, (size_t)m.n * 4, cudaMemcpyDeviceToHost, st));
-  if (res->support && nnz > 0) GCK(cudaMemcpyAsync(res->support, m.support_out, (size_t)nnz * 8, cudaMemcpyDeviceToHost, st));
-  if (res->start_x)
-    GCK(cudaMemcpy2DAsync(res->start_x, (size_t)m.p * 4, d.X, m.ldX * 4, (size_t)m.p * 4, r, cudaMemcpyDeviceToHost, st));
-  GCK(cudaStreamSynchronize(st));
-  int64_t sweeps = 0;
-  int nconv = 0, ndeg = 0;
-  for (int c = 0; c < r; ++c) {
-    sweeps += iters[c];
-    nconv += status[c] == SPCA_ST_CONVERGED;
-    ndeg += status[c] == SPCA_ST_DEGENERATE;
+  struct Piece {
+    size_t off;
+    int64_t bytes;
+  };
+  std::vector<CopyDesc> desc;
+  std::vector<std::vector<Piece>> pieces(list.size());
+  size_t off = 0;
+  auto add = [&](size_t k, const void *src, int64_t bytes) {
+    desc.push_back(CopyDesc{src, nullptr, bytes});
+    pieces[k].push_back(Piece{off, bytes});
+    off += (bytes + 15) / 16 * 16;
+  };
+  for (size_t k = 0; k < list.size(); ++k) {
+    Member &m = *list[k];
+    const GProb &d = m.d;
+    GCK(launch_finalise(m.P.form, m.h->AT32, m.h->ldAT, m.n, m.p, d.X, m.ldX, d.st, m.r, d.U, m.ldU, d.sup_idx,
+                        d.sup_val, m.p, m.partials, st));
+    GCK(launch_best(m.P.form, m.target, d.st, m.r, m.best, st));
+    GCK(launch_best_outputs(m.P.form, m.best, d.U, m.ldU, m.n, d.X, m.ldX, m.p, m.y_out, m.x_out, m.support_out,
+                            m.nnz_out, st));
+    const int64_t r = m.r;
+    add(k, d.st.status, 4 * r);
+    add(k, d.st.iters, 4 * r);
+    add(k, d.st.f, 8 * r);
+    add(k, d.st.ev, 8 * r);
+    add(k, d.st.gamma, 8 * r);
+    add(k, d.st.F, 8 * r);
+    add(k, m.best, 4);
+    add(k, m.nnz_out, 8);
+    add(k, m.x_out, 4 * (int64_t)m.p);
+    add(k, m.y_out, 4 * (int64_t)m.n);
+    add(k, m.support_out, 8 * (int64_t)m.p);
   }
-  const bool pen = is_pen(m.P.form);
-  res->objective = f[best];
-  res->explained_variance = ev[best];
-  res->gamma = pen ? gam[best] : 0.0;
-  res->best_start = best;
-  res->best_iters = iters[best];
-  res->best_status = status[best];
-  res->converged = nconv;
-  res->degenerate = ndeg;
-  res->sweeps_total = sweeps;
-  res->nnz = nnz;
-  for (int c = 0; c < r; ++c) {
-    if (res->start_objective) res->start_objective[c] = f[c];
-    if (res->start_explained) res->start_explained[c] = ev[c];
-    if (res->start_F) res->start_F[c] = F[c];
-    if (res->start_iters) res->start_iters[c] = iters[c];
-    if (res->start_status) res->start_status[c] = status[c];
-    if (res->start_gamma) res->start_gamma[c] = pen ? gam[c] : 0.0;
+  if (off > g->stage_bytes) {
+    GCK(cudaStreamSynchronize(st));
+    if (g->stage_d) cudaFree(g->stage_d);
+    if (g->stage_h) cudaFreeHost(g->stage_h);
+    g->stage_d = nullptr;
+    g->stage_h = nullptr;
+    g->stage_bytes = 0;
+    GCK(cudaMalloc((void **)&g->stage_d, off));
+    GCK(cudaMallocHost((void **)&g->stage_h, off));
+    g->stage_bytes = off;
   }
+  const size_t dbytes = sizeof(CopyDesc) * desc.size();
+  if (dbytes > g->desc_bytes) {
+    GCK(cudaStreamSynchronize(st));
+    if (g->desc_d) cudaFree(g->desc_d);
+    g->desc_d = nullptr;
+    g->desc_bytes = 0;
+    GCK(cudaMalloc((void **)&g->desc_d, dbytes));
+    g->desc_bytes = dbytes;
+  }
+  size_t q = 0;
+  for (size_t k = 0; k < list.size(); ++k)
+    for (const Piece &pc : pieces[k]) desc[q++].dst = g->stage_d + pc.off;
+  GCK(cudaMemcpyAsync(g->desc_d, desc.data(), dbytes, cudaMemcpyHostToDevice, st));
+  GCK(launch_copy_list(g->desc_d, (int)desc.size(), st));
+  GCK(cudaMemcpyAsync(g->stage_h, g->stage_d, off, cudaMemcpyDeviceToHost, st));
+  GCK(cudaStreamSynchronize(st));
+  for (size_t k = 0; k < list.size(); ++k) {
+    Member &m = *list[k];
+    const int r = m.r;
+    const std::vector<Piece> &pc = pieces[k];
+    const char *H = g->stage_h;
+    const int *status = reinterpret_cast<const int *>(H + pc[0].off);
+    const int *iters = reinterpret_cast<const int *>(H + pc[1].off);
+    const double *f = reinterpret_cast<const double *>(H + pc[2].off);
+    const double *ev = reinterpret_cast<const double *>(H + pc[3].off);
+    const double *gam = reinterpret_cast<const double *>(H + pc[4].off);
+    const double *F = reinterpret_cast<const double *>(H + pc[5].off);
+    const int best = *reinterpret_cast<const int *>(H + pc[6].off);
+    const int64_t nnz = *reinterpret_cast<const int64_t *>(H + pc[7].off);
+    spca_result *res = m.res;
+    if (res->x) memcpy(res->x, H + pc[8].off, (size_t)m.p * 4);
+    if (res->y) memcpy(res->y, H + pc[9].off, (size_t)m.n * 4);
+    if (res->support && nnz > 0) memcpy(res->support, H + pc[10].off, (size_t)nnz * 8);
+    if (res->start_x)
+      GCK(cudaMemcpy2DAsync(res->start_x, (size_t)m.p * 4, m.d.X, m.ldX * 4, (size_t)m.p * 4, r,
+                            cudaMemcpyDeviceToHost, st));
+    int64_t sweeps = 0;
+    int nconv = 0, ndeg = 0;
+    for (int c = 0; c < r; ++c) {
+      sweeps += iters[c];
+      nconv += status[c] == SPCA_ST_CONVERGED;
+      ndeg += status[c] == SPCA_ST_DEGENERATE;
+    }
+    const bool pen = is_pen(m.P.form);
+    res->objective = f[best];
+    res->explained_variance = ev[best];
+    res->gamma = pen ? gam[best] : 0.0;
+    res->best_start = best;
+    res->best_iters = iters[best];
+    res->best_status = status[best];
+    res->converged = nconv;
+    res->degenerate = ndeg;
+    res->sweeps_total = sweeps;
+    res->nnz = nnz;
+    for (int c = 0; c < r; ++c) {
+      if (res->start_objective) res->start_objective[c] = f[c];
+      if (res->start_explained) res->start_explained[c] = ev[c];
+      if (res->start_F) res->start_F[c] = F[c];
+      if (res->start_iters) res->start_iters[c] = iters[c];
+      if (res->start_status) res->start_status[c] = status[c];
+      if (res->start_gamma) res->start_gamma[c] = pen ? gam[c] : 0.0;
+    }
+  }
+  GCK(cudaStreamSynchronize(st));   // the start_x copies
   return SPCA_OK;
 }
 
 void release_member(spca_group *g, Member &m) {
   if (m.mem) cudaFreeAsync(m.mem, g->stream);
   m.mem = nullptr;
-}
-
-int check_device_err(spca_group *g) {
-  GCK(cudaMemcpyAsync(g->h_err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
-  GCK(cudaStreamSynchronize(g->stream));
-  if (*g->h_err) {
-    const int code = *g->h_err;
-    cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream);
-    return gfail(g, code, "a device-side wait timed out");
-  }
-  return SPCA_OK;
 }
 
 // run `sweeps` sweeps for the current members (captured into a graph when `capture`), then the
@@ -543,22 +609,30 @@ int run_segment(spca_group *g, int sweeps, bool capture, bool retire, int *finis
   }
   GCK(launch_g_ctrl(g->dP, np, (int)(g->k & 1), 0, g->d_active, st));
   GCK(cudaMemcpyAsync(g->h_active, g->d_active, sizeof(int) * np, cudaMemcpyDeviceToHost, st));
+  GCK(cudaMemcpyAsync(g->h_err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   GCK(cudaStreamSynchronize(st));
-  GRC(check_device_err(g));
+  if (*g->h_err) {
+    const int code = *g->h_err;
+    cudaMemsetAsync(g->d_err, 0, sizeof(int), st);
+    return gfail(g, code, "a device-side wait timed out");
+  }
   if (!retire) return SPCA_OK;
   std::vector<Member> keep;
+  std::vector<Member *> done;
   int nf = 0;
   const std::vector<int> active(g->h_active, g->h_active + np);
   for (int i = 0; i < np; ++i) {
     Member &m = g->members[i];
-    if (active[i] > 0) {
-      keep.push_back(m);
-      continue;
-    }
-    GRC(finish_member(g, m));
+    if (active[i] > 0) continue;
+    done.push_back(&m);
     if (finished && nf < cap) finished[nf] = m.tag;
     ++nf;
-    release_member(g, m);
+  }
+  GRC(finish_members(g, done));
+  for (int i = 0; i < np; ++i) {
+    Member &m = g->members[i];
+    if (active[i] > 0) keep.push_back(m);
+    else release_member(g, m);
   }
   if (nf > 0) {
     g->members.swap(keep);
@@ -600,6 +674,9 @@ void spca_group_destroy(spca_group *g) {
   for (GroupGraph &q : g->graphs)
     if (q.exec) cudaGraphExecDestroy(q.exec);
   if (g->tab) cudaFree(g->tab);
+  if (g->stage_d) cudaFree(g->stage_d);
+  if (g->stage_h) cudaFreeHost(g->stage_h);
+  if (g->desc_d) cudaFree(g->desc_d);
   if (g->d_err) cudaFree(g->d_err);
   if (g->h_active) cudaFreeHost(g->h_active);
   if (g->h_err) cudaFreeHost(g->h_err);
@@ -633,13 +710,28 @@ int spca_group_admit(spca_group *g, spca_problem *probs, int count, const int *t
   GCK(cudaEventRecord(g->order_ev, g->user));
   GCK(cudaStreamWaitEvent(g->stream, g->order_ev, 0));
   const size_t before = g->members.size();
+  auto undo = [&](int rc) {   // none of this call's problems stays admitted
+    for (size_t j = before; j < g->members.size(); ++j) release_member(g, g->members[j]);
+    g->members.resize(before);
+    g->tables_ok = false;
+    return rc;
+  };
+  bool given = false;
+  for (int i = 0; i < count; ++i) given = given || probs[i].x0;
+  // no grouped launch is in flight between segments, so the error word is free for the x0 checks
+  if (given && cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream) != cudaSuccess)
+    return gfail(g, SPCA_E_CUDA, "cudaMemsetAsync failed");
   for (int i = 0; i < count; ++i) {
     const int rc = admit_one(g, probs[i], tags ? tags[i] : i);
-    if (rc != SPCA_OK) {   // none of this call's problems stays admitted
-      for (size_t j = before; j < g->members.size(); ++j) release_member(g, g->members[j]);
-      g->members.resize(before);
-      g->tables_ok = false;
-      return rc;
+    if (rc != SPCA_OK) return undo(rc);
+  }
+  if (given) {   // one synchronisation for every given start of the call
+    if (cudaMemcpyAsync(g->h_err, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+        cudaStreamSynchronize(g->stream) != cudaSuccess)
+      return undo(gfail(g, SPCA_E_CUDA, "reading the x0 check failed"));
+    if (*g->h_err) {
+      cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream);
+      return undo(gfail(g, SPCA_E_INVALID, "x0 has a non-finite entry"));
     }
   }
   return SPCA_OK;
@@ -675,8 +767,9 @@ int spca_solve_group(spca_group *g, spca_problem *probs, int count, const spca_g
     if (active == 0) break;
   }
   if (rc == SPCA_OK) {
-    for (Member &m : g->members)
-      if ((rc = finish_member(g, m)) != SPCA_OK) break;
+    std::vector<Member *> all;
+    for (Member &m : g->members) all.push_back(&m);
+    rc = finish_members(g, all);
   }
   for (Member &m : g->members) release_member(g, m);
   g->members.clear();

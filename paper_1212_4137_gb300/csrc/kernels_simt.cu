@@ -730,6 +730,28 @@ cudaError_t launch_g_active(const GProb *P, int np, int parity, cudaStream_t st)
   return cudaGetLastError();
 }
 
+// many small device copies in one launch (block i copies list[i]): 16 bytes at a time where both
+// ends are 16-byte aligned, else byte by byte
+__global__ void k_copy_list(const CopyDesc *__restrict__ list) {
+  const CopyDesc d = list[blockIdx.x];
+  const char *src = static_cast<const char *>(d.src);
+  char *dst = static_cast<char *>(d.dst);
+  if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0) {
+    const int64_t n16 = d.bytes / 16;
+    for (int64_t i = threadIdx.x; i < n16; i += blockDim.x)
+      reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
+    for (int64_t i = 16 * n16 + threadIdx.x; i < d.bytes; i += blockDim.x) dst[i] = src[i];
+  } else {
+    for (int64_t i = threadIdx.x; i < d.bytes; i += blockDim.x) dst[i] = src[i];
+  }
+}
+
+cudaError_t launch_copy_list(const CopyDesc *list, int count, cudaStream_t st) {
+  if (count < 1) return cudaSuccess;
+  k_copy_list<<<count, 256, 0, st>>>(list);
+  return cudaGetLastError();
+}
+
 // the control words of one sweep parity: cleared before an x-step, and their active counts gathered
 // for the host (out[i] = problem i's count)
 __global__ void k_g_ctrl(const GProb *__restrict__ P, int np, int parity, int clear, int *__restrict__ out) {

@@ -412,6 +412,13 @@ struct GProb {
 // global start g, R starts in all)
 cudaError_t launch_g_start_init(const GProb *P, const int *prob, int R, cudaStream_t st);
 cudaError_t launch_g_active(const GProb *P, int np, int parity, cudaStream_t st);
+// many small device-to-device copies in one launch
+struct CopyDesc {
+  const void *src;
+  void *dst;
+  int64_t bytes;
+};
+cudaError_t launch_copy_list(const CopyDesc *list, int count, cudaStream_t st);
 // clear (clear != 0) the control words of one parity, or gather their active counts into out[np]
 cudaError_t launch_g_ctrl(const GProb *P, int np, int parity, int clear, int *out, cudaStream_t st);
 cudaError_t launch_g_xplanes(const GProb *P, const int *prob, int R, cudaStream_t st);
@@ -420,9 +427,11 @@ cudaError_t launch_g_ystep(const GProb *P, const int *prob, int R, cudaStream_t 
 cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p, int parity, int sms, cudaStream_t st);
 
 // Grouped contraction: one persistent launch over the tiles of many contractions (one per problem
-// of a group), each described by a task in device memory.  pmap / qmap are device addresses of
-// tensor maps (P: 128-row boxes over two FP16 planes; Q: 64-row boxes over nb planes), 64-byte
-// aligned.  Tile shapes: (bn, stages) in {64: 2, 3, 4; 128: 2, 3} (grouped_config_ok).
+// of a group), each described by a task in device memory, its tiles listed in tile_list (task,
+// local tile: M tile = local / nt, N tile = local % nt) in the order the CTAs take them.
+// pmap / qmap are device addresses of tensor maps (P: 128-row boxes over two FP16 planes; Q:
+// 64-row boxes over nb planes), 64-byte aligned.  Tile shapes: (bn, stages) in {64: 2, 3, 4;
+// 128: 2, 3} (grouped_config_ok).
 constexpr int kGroupMaxTasks = 1024;
 struct GTask {
   const CUtensorMap *pmap, *qmap;
@@ -434,11 +443,11 @@ struct GTask {
   const float *row_inv, *col_inv;
   float q_inv;
   TcPairs pairs;
-  int tile0, mt, nt;            // first tile in the launch's list; M and N tiles (N tiles of bn)
+  int mt, nt;                   // M and N tiles (N tiles of bn)
 };
 bool grouped_config_ok(int bn, int stages);
-cudaError_t launch_gemm_grouped(const GTask *tasks, int ntasks, int total_tiles, int bn, int stages, int sms, int *err,
-                                uint64_t wait_ns, cudaStream_t st);
+cudaError_t launch_gemm_grouped(const GTask *tasks, const int2 *tile_list, int total_tiles, int bn, int stages, int sms,
+                                int *err, uint64_t wait_ns, cudaStream_t st);
 
 // FP16 planes (hi, lo; the first nplanes) of a scaled FP32 matrix, plane t at dst + t *
 // plane_stride elements: destination row r is source row row_map[r] (identity when null) times

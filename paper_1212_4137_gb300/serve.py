@@ -1,6 +1,14 @@
 """A request loop over the C ABI: resident matrices, memory-bounded admission, and solves of
 different requests running at the same time on one GPU.
 
+Two modes.  In ``group`` mode (the default) each worker owns a group session (``spca.Group``):
+between segments of ``sweeps_per_step`` sweeps it admits the requests waiting in the queue into the
+group, whose members all sweep in the same launches (every phase of a sweep one launch over all
+members), and the requests whose starts have all stopped leave the group with their results --
+continuous batching at sweep boundaries.  Requests a group does not take (a sparse matrix,
+low-precision sweeps, on-the-fly replacement) are solved whole by the same worker between two
+segments.  In ``solve`` mode each request is one whole solve on a clone of its matrix (below).
+
 Matrices are registered once (``spca_create`` / ``spca_create_csr``: copied to the device and kept
 there).  Workers, each a host thread with its own CUDA stream, take requests in arrival order; a
 worker solves on a clone of the request's matrix (``spca_clone``: the matrix shared read-only,
@@ -14,7 +22,8 @@ does not fit evicts the worker's least recently used clones first, and a request
 worker's whole budget is refused.  The estimate is the handle's per-solve workspace for (n, p, r).
 
 Each solve is a deterministic function of its own inputs (fixed-order reductions, no schedule
-dependence), so a request's result is the same alone and in the mix.
+dependence), and a group member's result does not depend on the other members, so a request's
+result is the same alone and in the mix.
 """
 from __future__ import annotations
 
@@ -36,6 +45,20 @@ def workspace_bytes(n: int, p: int, r: int) -> int:
     return int(r * per_start + 2 * 2 * pn * 1024 + (1 << 20))
 
 
+def member_bytes(n: int, p: int, r: int) -> int:
+    """Device bytes of a group member's block (an upper estimate): x, v, u and their 16-bit planes,
+    support lists, per-start scalars, the finalisation's partial sums and outputs."""
+    pn, pp = (n + 7) // 8 * 8, (p + 7) // 8 * 8
+    per_start = 4 * (2 * pp + pn) + 2 * 2 * (pp + pn) + 8 * pp + 16 * ((n + 255) // 256) + 128
+    return int(r * per_start + 16 * (pp + pn) + 4096)
+
+
+def groupable(kwargs: dict, sparse: bool) -> bool:
+    """Whether a group session takes the request (dense matrix, FP32 sweeps from r starts)."""
+    return (not sparse and not kwargs.get("lowp_sweeps") and kwargs.get("total_starts", 0) <= 0
+            and kwargs.get("engine", spca.SPCA_ENGINE_AUTO) in (spca.SPCA_ENGINE_AUTO, spca.SPCA_ENGINE_TC))
+
+
 @dataclass
 class Request:
     name: str
@@ -46,6 +69,7 @@ class Request:
     t_submit: float = field(default_factory=time.perf_counter)
     t_start: float = 0.0
     t_end: float = 0.0
+    group_bytes: object = None   # a group member's bytes, or None for a whole solve
 
 
 class _Worker:
@@ -75,43 +99,122 @@ class _Worker:
         self.held += b
         return h
 
+    def _solve_whole(self, req: "Request"):
+        s = self.server
+        try:
+            n, p = s._shape[req.name]
+            h = self._clone(req.name, workspace_bytes(n, p, max(req.r, req.kwargs.get("total_starts", 0))))
+            req.t_start = time.perf_counter()
+            out = h.solve(req.form, req.r, **req.kwargs)
+            req.t_end = time.perf_counter()
+            self._deliver(req, out)
+        except Exception as e:   # reported through the request's future
+            req.future.set_exception(e)
+        finally:
+            s._done(req)
+
+    def _deliver(self, req: "Request", out: dict) -> None:
+        out["queue_ms"] = 1e3 * (req.t_start - req.t_submit)
+        out["service_ms"] = 1e3 * (req.t_end - req.t_start)
+        out["latency_ms"] = 1e3 * (req.t_end - req.t_submit)
+        out["worker"] = self.index
+        req.future.set_result(out)
+
     def _run(self):
         s = self.server
         self.stream, self.stream_ptr = s._stream_factory()
-        while True:
-            req = s._next()
-            if req is None:
-                break
-            try:
-                n, p = s._shape[req.name]
-                h = self._clone(req.name, workspace_bytes(n, p, max(req.r, req.kwargs.get("total_starts", 0))))
-                req.t_start = time.perf_counter()
-                out = h.solve(req.form, req.r, **req.kwargs)
-                req.t_end = time.perf_counter()
-                out["queue_ms"] = 1e3 * (req.t_start - req.t_submit)
-                out["service_ms"] = 1e3 * (req.t_end - req.t_start)
-                out["latency_ms"] = 1e3 * (req.t_end - req.t_submit)
-                out["worker"] = self.index
-                req.future.set_result(out)
-            except Exception as e:   # reported through the request's future
-                req.future.set_exception(e)
-            finally:
-                s._done(req)
+        if s.mode == "group":
+            self._run_group()
+        else:
+            while True:
+                req = s._next()
+                if req is None:
+                    break
+                self._solve_whole(req)
         for h, _ in self.clones.values():
             h.close()
         self.clones.clear()
+
+    def _run_group(self):
+        """Admit waiting requests between segments, step the group, deliver the finished ones."""
+        s = self.server
+        g = s._group_factory(self.stream_ptr)
+        if s.tiles:
+            g.set_tiles(s.tiles)
+        members = {}   # tag -> (request, bytes)
+        held = 0
+        tag = 0
+        try:
+            while True:
+                batch = s._take(block=not members, budget=s.worker_budget - held, have=len(members),
+                                max_members=s.max_members)
+                if batch is None:
+                    break
+                admit = []
+                for req in batch:
+                    if req.group_bytes is None:      # not for a group: a whole solve now
+                        self._solve_whole(req)
+                        continue
+                    req.t_start = time.perf_counter()
+                    tag += 1
+                    members[tag] = (req, req.group_bytes)
+                    held += req.group_bytes
+                    admit.append((tag, req))
+                if admit:
+                    try:
+                        g.admit([(s._base[r.name], r.form, r.r, r.kwargs) for _, r in admit], [t for t, _ in admit])
+                    except Exception as e:
+                        for t, r in admit:
+                            members.pop(t)
+                            held -= r.group_bytes
+                            r.future.set_exception(e)
+                            s._done(r)
+                if not members:
+                    continue
+                try:
+                    finished = g.step(s.sweeps_per_step)
+                except Exception as e:   # the whole group fails: report it to every member
+                    for t, (r, b) in list(members.items()):
+                        r.future.set_exception(e)
+                        s._done(r)
+                    members.clear()
+                    held = 0
+                    g.close()
+                    g = s._group_factory(self.stream_ptr)
+                    continue
+                now = time.perf_counter()
+                for t, out in finished:
+                    req, b = members.pop(t)
+                    held -= b
+                    req.t_end = now
+                    self._deliver(req, out)
+                    s._done(req)
+        finally:
+            g.close()
 
 
 class Server:
     """Resident matrices and `workers` concurrent solvers (see the module docstring)."""
 
     def __init__(self, workers: int = 4, budget_bytes: int = 32 << 30, device: int = 0, handle_factory=None,
-                 stream_factory=None):
+                 stream_factory=None, mode: str = "group", sweeps_per_step: int = 4, max_members: int = 1024,
+                 tiles=None, group_factory=None):
         """handle_factory(A, stream=...) makes a matrix's handle (spca.Handle); stream_factory() gives
         a worker (stream object, cudaStream_t as int) on the calling thread (a new CUDA stream on
-        `device`).  Both are replaceable for tests of the loop without a GPU."""
+        `device`); group_factory(stream) makes a worker's group session (spca.Group).  All three
+        are replaceable for tests of the loop without a GPU.  mode: "group" (sessions, continuous
+        batching at sweep boundaries) or "solve" (whole solves on clones).  tiles: the grouped
+        contraction's tile shape, (tile_n, stages) or None."""
         if workers < 1:
             raise ValueError("workers must be >= 1")
+        if mode not in ("group", "solve"):
+            raise ValueError("mode must be 'group' or 'solve'")
+        self.mode = mode
+        self.sweeps_per_step = sweeps_per_step
+        self.max_members = max_members
+        self.tiles = tiles
+        self._group_factory = group_factory or (lambda stream: spca.Group(stream=stream))
+        self._sparse = {}
         self.device = device
         self._handle_factory = handle_factory or spca.Handle
         self._stream_factory = stream_factory or self._cuda_stream
@@ -139,6 +242,7 @@ class Server:
         h = self._handle_factory(A, stream=stream)
         self._base[name] = h
         self._shape[name] = (h.n, h.p)
+        self._sparse[name] = isinstance(A, tuple) and len(A) == 4 or hasattr(A, "indptr") or hasattr(A, "tocsr")
 
     def submit(self, name: str, form: int, r: int, **kwargs) -> cf.Future:
         """Queue a solve (the arguments of Handle.solve); the future gives its result dict, with the
@@ -148,13 +252,21 @@ class Server:
         if name not in self._base:
             raise KeyError(f"no matrix {name!r}")
         n, p = self._shape[name]
-        if workspace_bytes(n, p, max(r, kwargs.get("total_starts", 0))) > self.worker_budget:
+        gb = None
+        if self.mode == "group" and groupable(kwargs, self._sparse.get(name, False)):
+            gb = member_bytes(n, p, r)
+            need = gb
+        else:
+            need = workspace_bytes(n, p, max(r, kwargs.get("total_starts", 0)))
+        if need > self.worker_budget:
             raise MemoryError(f"a solve of {r} starts on {name!r} exceeds a worker's memory budget")
         fut: cf.Future = cf.Future()
         with self._cv:
             if self._closing:
                 raise RuntimeError("the server is closed")
-            self._queue.append(Request(name, form, r, dict(kwargs), fut))
+            req = Request(name, form, r, dict(kwargs), fut)
+            req.group_bytes = gb
+            self._queue.append(req)
             self._cv.notify()
         return fut
 
@@ -166,6 +278,31 @@ class Server:
                 return None
             self._in_flight += 1
             return self._queue.popleft()
+
+    def _take(self, block: bool, budget: int, have: int, max_members: int):
+        """For a group worker: the waiting requests, in arrival order, that fit the worker's remaining
+        memory and member count (requests not for a group count nothing); blocks while the queue is
+        empty if `block`.  None when the server closes and the worker has nothing left."""
+        with self._cv:
+            while block and not self._queue and not self._closing:
+                self._cv.wait()
+            if not self._queue:
+                return None if (self._closing and block) else []
+            out = []
+            # at most an even share of the queue per worker, so that idle workers take the rest
+            share = max(1, -(-len(self._queue) // len(self._workers)))
+            while self._queue and len(out) < share:
+                req = self._queue[0]
+                gb = req.group_bytes or 0
+                if req.group_bytes is not None and (gb > budget or have + 1 > max_members):
+                    break
+                self._queue.popleft()
+                self._in_flight += 1
+                out.append(req)
+                if req.group_bytes is not None:
+                    budget -= gb
+                    have += 1
+            return out
 
     def _done(self, req: Request) -> None:
         with self._cv:

@@ -4,7 +4,9 @@ spca_clone shares a matrix read-only: a clone's solve matches the FP64 oracle li
 the matrix outlives the handle it came from, and deflation of a shared matrix is refused.  The
 request loop runs solves of different requests at the same time; each request's result must be
 the same alone (one worker, one request at a time) and in the mix (four workers, every request
-queued at once), bit for bit, since a solve depends only on its own inputs."""
+queued at once), bit for bit, since a solve depends only on its own inputs.  The same holds in
+group mode, where requests join running group sessions between sweep segments and sweep in the
+same launches as the other members."""
 import numpy as np
 import pytest
 
@@ -70,9 +72,9 @@ def test_requests_same_alone_and_in_the_mix(lib):
     shapes["bow"] = (700, 1500)
     reqs = _requests(rng, list(shapes), shapes, 24)
 
-    def run(workers, one_at_a_time):
+    def run(workers, one_at_a_time, mode):
         outs = []
-        with serve.Server(workers=workers, budget_bytes=8 << 30) as s:
+        with serve.Server(workers=workers, budget_bytes=8 << 30, mode=mode) as s:
             for name, A in mats.items():
                 s.register(name, A)
             s.register("bow", (ip, ix, v, (700, 1500)))
@@ -84,11 +86,18 @@ def test_requests_same_alone_and_in_the_mix(lib):
                 outs = [f.result() for f in futs]
         return outs
 
-    alone = run(1, True)
-    mixed = run(4, False)
-    assert len({o["worker"] for o in mixed}) > 1
-    for a, m in zip(alone, mixed):
-        assert a["objective"] == m["objective"]
-        assert a["best_start"] == m["best_start"] and a["sweeps_total"] == m["sweeps_total"]
-        assert np.array_equal(a["x"], m["x"]) and np.array_equal(a["start_x"], m["start_x"])
-        assert np.array_equal(a["start_objective"], m["start_objective"])
+    for mode in ("solve", "group"):
+        alone = run(1, True, mode)
+        mixed = run(4 if mode == "solve" else 2, False, mode)
+        assert len({o["worker"] for o in mixed}) > 1   # (group mode: each worker's group held several)
+        for a, m in zip(alone, mixed):
+            assert a["objective"] == m["objective"]
+            assert a["best_start"] == m["best_start"] and a["sweeps_total"] == m["sweeps_total"]
+            assert np.array_equal(a["x"], m["x"]) and np.array_equal(a["start_x"], m["start_x"])
+            assert np.array_equal(a["start_objective"], m["start_objective"])
+        if mode == "group":
+            # a group's results agree with whole solves at the parity tolerances
+            whole = run(1, True, "solve")
+            close = [abs(a["objective"] - w["objective"]) <= 1e-4 * max(1.0, abs(w["objective"]))
+                     for a, w in zip(alone, whole)]
+            assert np.mean(close) >= 0.9

@@ -1,7 +1,11 @@
-"""The request loop's host logic without a GPU: a fake handle stands in for the C ABI (its solve
-returns its arguments after a short sleep).  Every request gets its own result, requests run on
-several workers at once, a worker's clones stay within its memory budget (least recently used
-first out), an oversized request is refused, and drain / close finish cleanly."""
+"""The request loop's host logic without a GPU: a fake handle and a fake group session stand in for
+the C ABI (a solve returns its arguments after a short sleep; a group member finishes after as
+many steps as its request asks).  Whole-solve mode: every request gets its own result, requests
+run on several workers at once, a worker's clones stay within its memory budget (least recently
+used first out), an oversized request is refused, and drain / close finish cleanly.  Group mode:
+requests that arrive while a group runs are admitted between its steps, each member leaves with
+its own result when it finishes, the members' memory stays within the worker's budget, requests a
+group does not take are solved whole by the same worker, and a failed step reaches every member."""
 import threading
 import time
 
@@ -40,6 +44,7 @@ class FakeHandle:
 
 
 def _server(**kw):
+    kw.setdefault("mode", "solve")
     return serve.Server(handle_factory=FakeHandle, stream_factory=lambda: (None, 0), **kw)
 
 
@@ -86,7 +91,7 @@ def test_errors_reach_the_future():
         def solve(self, form, r, **kw):
             raise RuntimeError("solve failed")
 
-    s = serve.Server(workers=2, handle_factory=Bad, stream_factory=lambda: (None, 0))
+    s = serve.Server(workers=2, handle_factory=Bad, stream_factory=lambda: (None, 0), mode="solve")
     s.register("a", (10, 20))
     f = s.submit("a", 1, 4)
     with pytest.raises(RuntimeError):
@@ -108,3 +113,103 @@ def test_registration_and_configuration_errors():
         assert all(f.done() for f in futs)
         assert [f.result()["tag"] for f in futs] == list(range(5))
     assert FakeHandle.live == 0
+
+
+# ---------------------------------------------------------------- group mode
+class FakeGroup:
+    """A group session: a member admitted with kwargs {"steps": k} finishes after k steps."""
+    instances = []
+    lock = threading.Lock()
+    fail_at = None
+
+    def __init__(self, stream=0):
+        self.members = {}
+        self.steps = 0
+        self.admitted_at = {}
+        self.max_members = 0
+        self.closed = False
+        with FakeGroup.lock:
+            FakeGroup.instances.append(self)
+
+    def set_tiles(self, tiles):
+        self.tiles = tiles
+
+    def admit(self, problems, tags):
+        for (h, form, r, kw), tag in zip(problems, tags):
+            self.members[tag] = [kw.get("steps", 1), {"form": form, "r": r, "shape": (h.n, h.p), **kw}]
+            self.admitted_at[tag] = self.steps
+        self.max_members = max(self.max_members, len(self.members))
+
+    def step(self, sweeps):
+        time.sleep(0.005)
+        self.steps += 1
+        if FakeGroup.fail_at is not None and self.steps >= FakeGroup.fail_at:
+            raise RuntimeError("step failed")
+        done = []
+        for tag, m in list(self.members.items()):
+            m[0] -= 1
+            if m[0] <= 0:
+                done.append((tag, dict(m[1], admitted_at=self.admitted_at[tag], finished_at=self.steps)))
+                del self.members[tag]
+        return done
+
+    def pending(self):
+        return len(self.members)
+
+    def close(self):
+        self.closed = True
+
+
+def _gserver(**kw):
+    FakeGroup.instances = []
+    FakeGroup.fail_at = None
+    return serve.Server(handle_factory=FakeHandle, stream_factory=lambda: (None, 0), group_factory=FakeGroup,
+                        mode="group", **kw)
+
+
+def test_group_mode_admits_between_steps():
+    with _gserver(workers=1, budget_bytes=1 << 34) as s:
+        s.register("a", (100, 500))
+        s.register("b", (300, 900))
+        first = s.submit("a", 1, 16, steps=20, tag=0)        # a long request ...
+        time.sleep(0.03)
+        later = [s.submit("ab"[i % 2], 2, 8, steps=2, tag=1 + i) for i in range(6)]   # ... joined later
+        outs = [f.result(timeout=10) for f in later]
+        assert not first.done() or first.result()["finished_at"] >= 20
+        for i, o in enumerate(outs):
+            assert o["tag"] == 1 + i and o["r"] == 8 and o["form"] == 2
+            assert o["admitted_at"] >= 1               # admitted while the first request ran
+            assert o["finished_at"] - o["admitted_at"] == 2
+            assert o["latency_ms"] >= o["service_ms"] >= 0.0
+        assert first.result(timeout=10)["finished_at"] == 20
+        g = FakeGroup.instances[0]
+        assert g.max_members >= 2                      # members swept together
+    assert all(g.closed for g in FakeGroup.instances)
+    assert FakeHandle.live == 0
+
+
+def test_group_mode_budget_members_and_whole_solves():
+    one = serve.member_bytes(1000, 4000, 64)
+    with _gserver(workers=1, budget_bytes=int(2.5 * one), max_members=8) as s:
+        s.register("a", (1000, 4000))
+        futs = [s.submit("a", 1, 64, steps=3, tag=i) for i in range(5)]
+        whole = s.submit("a", 1, 16, lowp_sweeps=4, tag=99)    # not for a group: solved whole
+        for f in futs:
+            f.result(timeout=10)
+        assert whole.result(timeout=10)["tag"] == 99 and "finished_at" not in whole.result()
+        assert FakeGroup.instances[0].max_members <= 2      # within the memory budget
+        with pytest.raises(MemoryError):
+            s.submit("a", 1, 64 * 10)
+    assert FakeHandle.live == 0
+
+
+def test_group_mode_failed_step_reaches_every_member():
+    with _gserver(workers=1, budget_bytes=1 << 34) as s:
+        FakeGroup.fail_at = 2
+        s.register("a", (10, 20))
+        futs = [s.submit("a", 1, 4, steps=5, tag=i) for i in range(3)]
+        for f in futs:
+            with pytest.raises(RuntimeError):
+                f.result(timeout=10)
+        FakeGroup.fail_at = None
+        assert s.submit("a", 1, 4, steps=1, tag=7).result(timeout=10)["tag"] == 7   # the worker goes on
