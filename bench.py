@@ -868,43 +868,88 @@ def run_tune(args, count=64):
         json.dump(table, fh, indent=1)
 
 
-# The serving configuration: resident spiked matrices (5 spikes, theta = (40, 30, 20, 15, 10)
-# sqrt(n / p), 50 nonzeros each), n log-uniform in [1000, 25000], p log-uniform in [2000, 50000], one
-# of them pinned at 25000 x 50000 (half the stated sizes in each dimension: this library keeps four
-# 4-byte copies' worth of every matrix, FP32 A and A^T and two FP16 planes of each, so the stated
-# sizes would not fit the 150 GB admission cap; see DESIGN).  Requests: a uniform matrix,
-# formulation 1..8, s uniform in [10, 200] (at most p), r uniform in {1, 16, 256}, at most 100
-# sweeps, tol 1e-9.  The request loop in group mode: `workers` group sessions, each admitting the
-# waiting requests between segments of 4 sweeps (member memory capped at 150 GB less the resident
-# matrices).  A closed loop (every request queued at once) gives the capacity; then Poisson
-# arrivals at 0.8 x capacity give the latency (p50 / p99 from submission to result).
+def spiked_on_device(n, p, thetas, nnz, seed, dev):
+    """The spiked model A = sum_k theta_k u_k v_k^T + N(0,1) noise, built in FP32 on the device:
+    the spike components from the seeded host generator (inputs.spike_components), the noise from a
+    seeded torch generator (the serving configuration's matrices, 15 G entries in all, would take
+    minutes to draw on the host)."""
+    import torch
+
+    from paper_1212_4137_gb300 import inputs as I
+    U, V = I.spike_components(n, p, len(thetas), nnz, seed)
+    Ut = torch.from_numpy(U * np.asarray(thetas, np.float64)).to(dev)
+    Vt = torch.from_numpy(V).to(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    A = torch.empty((n, p), dtype=torch.float32, device=dev)
+    rows = max(1, (1 << 27) // p)
+    for r0 in range(0, n, rows):
+        r1 = min(n, r0 + rows)
+        blk = torch.randn((r1 - r0, p), generator=g, dtype=torch.float32, device=dev)
+        blk += (Ut[r0:r1] @ Vt.T).float()
+        A[r0:r1] = blk
+    return A
+
+
+class _Kept:
+    """A registered handle the scan reuses across request loops (their close() leaves it open)."""
+
+    def __init__(self, h):
+        self._h = h
+
+    def __getattr__(self, name):
+        return getattr(self._h, name)
+
+    def close(self):
+        pass
+
+
+# The serving configuration: 32 resident spiked matrices (5 spikes, theta = (40, 30, 20, 15, 10)
+# sqrt(n / p), 50 nonzeros each), n log-uniform in [1000, 50000], p log-uniform in [2000, 100000],
+# one of them pinned at 50000 x 100000, held in 16 bits (SPCA_FP16_RESIDENT: the leading FP16
+# planes of A and A^T, 4 bytes per entry; the largest matrix's copy of A is 10 GB).  Requests: a
+# uniform matrix, formulation 1..8, s uniform in [10, 200] (at most p), r uniform in {1, 16, 256},
+# at most 100 sweeps, tol 1e-9.  Admission: the requests' working memory capped at 150 GB.  The
+# request loop in group mode (`workers` group sessions, each admitting the waiting requests between
+# segments of 4 sweeps) and, beside it, whole solves on clones.  A closed loop (every request
+# queued at once) gives the capacity; then Poisson arrivals at 0.8 x capacity give the latency
+# (p50 / p99 from submission to result).
 def run_scan_serving(args, mats=32, closed=400, open_requests=2000, modes=(("group", 2), ("group", 4), ("solve", 8)),
                      cap_gb=150):
     import torch
 
-    from paper_1212_4137_gb300 import build, inputs as I, serve
+    from paper_1212_4137_gb300 import build, inputs as I, serve, spca
     build.build()
+    spca.load()
+    dev = torch.device("cuda", 0)
     rng = np.random.default_rng(5)
-    shapes = [(25000, 50000)] + [(_log_uniform(rng, 1000, 25000), _log_uniform(rng, 2000, 50000))
-                                 for _ in range(mats - 1)]
-    import concurrent.futures as cf
+    shapes = [(50000, 100000)] + [(_log_uniform(rng, 1000, 50000), _log_uniform(rng, 2000, 100000))
+                                  for _ in range(mats - 1)]
     t0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(max_workers=16) as ex:
-        As = list(ex.map(lambda q: I.spiked_matrix(q[1][0], q[1][1], I.spiked_thetas(*q[1]), 50, 7000 + q[0],
-                                                   dtype=np.float32), enumerate(shapes)))
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    kept = []
+    for q, (n, p) in enumerate(shapes):
+        A = spiked_on_device(n, p, I.spiked_thetas(n, p), 50, 7000 + q, dev)
+        torch.cuda.synchronize(dev)
+        kept.append(_Kept(spca.Handle(A, storage=spca.SPCA_FP16_RESIDENT)))
+        del A
+        torch.cuda.empty_cache()
+    torch.cuda.synchronize(dev)
     gen_s = time.perf_counter() - t0
-    resident = sum(16 * A.size for A in As)   # FP32 A and A^T, two FP16 planes of each
-    budget = max(1 << 30, (cap_gb << 30) - resident)
-    head0 = {"scan": "serving", "matrices": mats, "sum_n_p": int(sum(A.size for A in As)),
-             "resident_gb": round(resident / 2**30, 1), "member_budget_gb": round(budget / 2**30, 1),
-             "host_generation_s": round(gen_s, 1)}
+    resident = free0 - torch.cuda.mem_get_info(dev)[0]
+    budget = cap_gb << 30
+    head0 = {"scan": "serving", "matrices": mats, "sum_n_p": int(sum(n * p for n, p in shapes)),
+             "largest": list(shapes[0]), "storage": "SPCA_FP16_RESIDENT (leading FP16 planes of A and A^T)",
+             "resident_gb": round(resident / 2**30, 1), "member_budget_gb": cap_gb,
+             "device_generation_and_create_s": round(gen_s, 1)}
     for mode, workers in modes:
         head = dict(head0, workers=workers, mode="group sessions, 4 sweeps per segment" if mode == "group"
                       else "whole solves on clones")
         rq = np.random.default_rng(55)   # the same requests and arrival times in every mode
-        with serve.Server(workers=workers, budget_bytes=budget, mode=mode) as srv:
-            for q, A in enumerate(As):
-                srv.register(f"s{q}", A)
+        with serve.Server(workers=workers, budget_bytes=budget, mode=mode,
+                          handle_factory=lambda A, stream=0, **kw: A) as srv:
+            for q, h in enumerate(kept):
+                srv.register(f"s{q}", h)
 
             def request(i):
                 name = f"s{int(rq.integers(0, mats))}"
@@ -937,6 +982,7 @@ def run_scan_serving(args, mats=32, closed=400, open_requests=2000, modes=(("gro
                 while time.perf_counter() < t_next:
                     time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
                 futs.append(srv.submit(nm, f, r, **kw))
+            t_last = time.perf_counter()
             outs = [f.result() for f in futs]
             dt = time.perf_counter() - t0
             lat = np.array([o["latency_ms"] for o in outs])
@@ -944,13 +990,16 @@ def run_scan_serving(args, mats=32, closed=400, open_requests=2000, modes=(("gro
                              "p99": round(float(np.percentile([o["latency_ms"] for o, q in zip(outs, reqs) if q[2] == r], 99)), 2)}
                     for r in (1, 16, 256) if any(q[2] == r for q in reqs)}
             print(json.dumps(dict(head, run="Poisson arrivals at 0.8 x capacity", requests=open_requests,
-                                  offered_per_s=round(rate, 2), solves_per_s=round(open_requests / dt, 2),
+                                  offered_per_s=round(rate, 2), arrivals_s=round(t_last - t0, 2),
+                                  solves_per_s=round(open_requests / dt, 2),
                                   sweeps_starts_per_s=round(sum(o["sweeps_total"] for o in outs) / dt, 1),
                                   latency_ms={"p50": round(float(np.percentile(lat, 50)), 2),
                                               "p99": round(float(np.percentile(lat, 99)), 2)},
                                   latency_by_r_ms=by_r,
                                   queue_ms_p50=round(float(np.percentile([o["queue_ms"] for o in outs], 50)), 2))),
                   flush=True)
+    for h in kept:
+        h._h.close()
 
 
 def sps_csr(ip, ix, v, n, p):

@@ -50,7 +50,8 @@ typedef enum {
     SPCA_F32 = 0,
     SPCA_F64 = 1,
     SPCA_FP16 = 2,            /* storage only: a 16-bit FP16 copy of A, row-scaled (see spca_create) */
-    SPCA_FP8_E4M3_COLSCALED = 3
+    SPCA_FP8_E4M3_COLSCALED = 3,
+    SPCA_FP16_RESIDENT = 4    /* storage only: A held only in 16 bits (see spca_create)             */
 } spca_dtype;
 
 /* formulation numbers = Table 1 of the paper:
@@ -116,6 +117,17 @@ typedef enum {
  *                and an 8-bit support gather, accumulating in FP32 (a clone's low-precision
  *                sweeps read the FP16 leading plane instead).  Both 16- and 8-bit storage need
  *                tensor cores (sm_100+): SPCA_E_UNSUPPORTED otherwise.
+ *                SPCA_FP16_RESIDENT keeps nothing but the leading FP16 planes of A and of A^T
+ *                with their row scales: 4 bytes per entry of A on the device instead of 16 (the
+ *                FP32 copies and the second planes are freed once the planes are built).  The
+ *                matrix the solves see is that 16-bit copy: every sweep is a low-precision sweep
+ *                (one tensor-core product per tile on the leading planes of A and of x or y, the
+ *                FP16 support gather), the stopping rule applies from the second sweep on, and
+ *                the objective of the finalise is that of the copy of A^T (FP16 entries times
+ *                their column's power-of-two scale), accumulated as for SPCA_F32.  Such a handle
+ *                takes the tensor-core engine only and no low-precision options (spca_solve),
+ *                on-the-fly replacement or deflation, and spca_products only with
+ *                SPCA_ENGINE_TC_LOWP (SPCA_E_UNSUPPORTED / SPCA_E_INVALID otherwise).
  *   cuda_stream  the caller's cudaStream_t (NULL = the legacy default stream): every call on
  *                the handle starts after the work queued on it before the call and returns with
  *                its own work complete.  The handle runs its kernels on a stream of its own, so

@@ -1181,7 +1181,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tensormap_acquire(T.qmap);
         last_task = ti;
       }
-      const uint32_t bytes = NA * A_BYTES + (uint32_t)T.nb * B_BYTES;
+      const uint32_t bytes = (uint32_t)T.na * A_BYTES + (uint32_t)T.nb * B_BYTES;
       for (int kb = 0; kb < T.kblocks; ++kb, ++it) {
         const int s = (int)(it % STAGES);
         const uint32_t ph = (it / STAGES) & 1u;
@@ -1189,8 +1189,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t fb = smem_u32(&full_bar[s]);
         mbar_expect_tx(fb, bytes);
         uint8_t *st = tiles + (size_t)s * STAGE_BYTES;
-#pragma unroll
-        for (int a = 0; a < NA; ++a) tma_load_3d(smem_u32(st + a * A_BYTES), T.pmap, kb * 64, m0, a, fb);
+        for (int a = 0; a < T.na; ++a) tma_load_3d(smem_u32(st + a * A_BYTES), T.pmap, kb * 64, m0, a, fb);
         for (int b = 0; b < T.nb; ++b)
 #pragma unroll
           for (int h = 0; h < BN / 64; ++h)

@@ -50,7 +50,7 @@ struct Member {
   int64_t ldX = 0, ldU = 0;
   char *mem = nullptr;            // the member's device block
   GProb d{};                      // its table entry (start0 set when the table is built)
-  CUtensorMap *maps = nullptr;    // device: A planes, A^T planes, X planes, Y planes
+  CUtensorMap *maps = nullptr;    // device: A planes, A^T planes, X planes
   double *partials = nullptr;
   float *y_out = nullptr, *x_out = nullptr;
   int64_t *support_out = nullptr, *nnz_out = nullptr;
@@ -68,6 +68,9 @@ uint64_t fnv(uint64_t h, const void *p, size_t n) {
 
 struct spca_group {
   cudaStream_t stream = nullptr;   // the group's own non-blocking stream
+  // the group's own stream-ordered memory pool (member blocks, pool buffers): it keeps what is
+  // freed for the next admissions instead of returning it to the device at every synchronisation
+  cudaMemPool_t mempool = nullptr;
   cudaStream_t user = nullptr;     // the caller's stream: each call starts after its prior work
   cudaEvent_t order_ev = nullptr;
   int sms = 1;
@@ -80,8 +83,17 @@ struct spca_group {
   int *d_start_prob = nullptr, *d_active = nullptr;
   GTask *d_tasks = nullptr;
   int2 *d_tiles[3] = {nullptr, nullptr, nullptr};   // tile lists: u, v of parity 0, v of parity 1
-  int R = 0, total_u = 0, total_v = 0, n_u = 0, max_n = 1, max_p = 1;
+  int R = 0, total_u = 0, total_v = 0, n_u = 0, max_n = 1, max_p = 1, max_p_small = 0;
+  bool any_large_p = false;
   bool tables_ok = false;
+  // pools (members on one matrix that share v = A^T y): the table, its member list, and one
+  // device block with each pool's V rows and Y planes (scratch of a sweep, rebuilt with the
+  // tables; kept when the pools' shapes are unchanged)
+  GPool *d_pools = nullptr;
+  int *d_pool_members = nullptr;
+  int npool = 0;
+  char *pool_mem = nullptr;
+  std::vector<int64_t> pool_sig;
   int *h_active = nullptr;         // pinned: active counts at a segment's end
   int h_active_cap = 0;
   int *h_err = nullptr;            // pinned: the device error word
@@ -141,6 +153,8 @@ const char *check_problem(const spca_problem &q) {
   if (P.r < 1 || P.r > kMaxStarts || P.max_iter < 1) return "r must be in 1..65535 and max_iter >= 1";
   if (P.lowp_sweeps != 0 || P.total_starts > P.r || P.timeout_us < 0)
     return "a grouped solve runs FP32 sweeps from r starts (no lowp_sweeps, no total_starts)";
+  if (h->resident16 && (P.lowp_first != 0 || P.refine_sweeps != 0))
+    return "every sweep of a resident 16-bit handle is a low-precision sweep: lowp_first and refine_sweeps must be 0";
   if (P.engine != SPCA_ENGINE_AUTO && P.engine != SPCA_ENGINE_TC) return "a grouped solve runs on the tensor cores";
   return nullptr;
 }
@@ -159,10 +173,10 @@ size_t member_layout(Member &m, size_t *o) {
   Layout L;
   const size_t r = (size_t)m.r;
   o[0] = L.take(4 * r * m.ldX);              // X
-  o[1] = L.take(4 * r * m.ldX);              // V
+  o[1] = L.take(0);                          // (V: the pool's rows)
   o[2] = L.take(4 * r * m.ldU);              // U
   o[3] = L.take(2 * 2 * r * m.ldX);          // X planes
-  o[4] = L.take(2 * 2 * r * m.ldU);          // Y planes
+  o[4] = L.take(0);                          // (Y planes: the pool's rows)
   o[5] = L.off;                              // (end of the zeroed part: padded columns)
   o[6] = L.take(4 * r);                      // x_scale
   o[7] = L.take(4 * r);                      // x_inv
@@ -197,7 +211,7 @@ int admit_one(spca_group *g, const spca_problem &q, int tag) {
   m.ldU = pad_ld(m.n);
   size_t o[20];
   const size_t bytes = member_layout(m, o);
-  GCK(cudaMallocAsync((void **)&m.mem, bytes, st));
+  GCK(cudaMallocFromPoolAsync((void **)&m.mem, bytes, g->mempool, st));
   auto at = [&](int i) { return m.mem + o[i]; };
   GCK(cudaMemsetAsync(m.mem, 0, o[5], st));
   GProb &d = m.d;
@@ -209,13 +223,15 @@ int admit_one(spca_group *g, const spca_problem &q, int tag) {
   d.ldU = m.ldU;
   d.ldAT = m.h->ldAT;
   d.AT32 = m.h->AT32;
+  d.AT16 = m.h->resident16 ? static_cast<const __half *>(m.h->ATpl) : nullptr;
+  d.at_inv = m.h->at_inv;
   d.X = reinterpret_cast<float *>(at(0));
-  d.V = reinterpret_cast<float *>(at(1));
+  d.V = nullptr;      // set with the pools (build_tables)
   d.U = reinterpret_cast<float *>(at(2));
   d.Xpl = reinterpret_cast<__half *>(at(3));
-  d.Ypl = reinterpret_cast<__half *>(at(4));
+  d.Ypl = nullptr;
   d.xps = (int64_t)m.r * m.ldX;
-  d.yps = (int64_t)m.r * m.ldU;
+  d.yps = 0;
   d.x_scale = reinterpret_cast<float *>(at(6));
   d.x_inv = reinterpret_cast<float *>(at(7));
   d.sup_idx = reinterpret_cast<int *>(at(8));
@@ -275,12 +291,11 @@ int admit_one(spca_group *g, const spca_problem &q, int tag) {
     // the caller reads the error word once for all the problems of its call
     GCK(launch_check_finite(d.X, m.r, m.p, m.ldX, g->d_err, st));
   }
-  CUtensorMap maps[4];
+  CUtensorMap maps[3];
   maps[0] = m.h->pmA.m[0];
   maps[1] = m.h->pmAT.m[0];
   GCK(make_plane_map(&maps[2], d.Xpl, m.r, m.ldX, 2, 64, 64));
-  GCK(make_plane_map(&maps[3], d.Ypl, m.r, m.ldU, 2, 64, 64));
-  GCK(cudaMemcpyAsync(m.maps, maps, sizeof(maps), cudaMemcpyHostToDevice, st));
+  GCK(cudaMemcpyAsync(m.maps, maps, 3 * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
   GCK(launch_start_init(d.x0, d.ld0, m.P.seed, m.r, m.p, d.X, m.ldX, s, d.gamma0, nullptr, nullptr, nullptr, st));
   // the next sweep is k + 1: it reads the control words of parity k & 1
   GCK(launch_active_list(s.status, nullptr, m.r, d.act, d.rank, d.ctrl[g->k & 1], st));
@@ -295,88 +310,190 @@ int admit_one(spca_group *g, const spca_problem &q, int tag) {
 int build_tables(spca_group *g) {
   const int np = (int)g->members.size();
   cudaStream_t st = g->stream;
-  std::vector<GProb> P(np);
-  int R = 0, max_n = 1, max_p = 1;
+  // pools: the members on one matrix whose v = A^T y takes the same plane products (two general
+  // operands, y = +-1, or the leading planes of a resident 16-bit matrix) share one contraction,
+  // their active starts side by side in one Y operand, so the matrix is read once per sweep for
+  // all of them; member order within a pool is admission order
+  struct PoolH {
+    const void *mat;
+    int type;
+    std::vector<int> mem;
+    int R = 0;
+  };
+  std::vector<PoolH> pools;
+  std::vector<int> vbase(np), pool_of(np);
+  for (int i = 0; i < np; ++i) {
+    const Member &m = g->members[i];
+    const int type = m.h->resident16 ? 2 : is_l1_var(m.P.form) ? 1 : 0;
+    int q = 0;
+    while (q < (int)pools.size() && !(pools[q].mat == m.h->shared && pools[q].type == type)) ++q;
+    if (q == (int)pools.size()) {
+      pools.emplace_back();
+      pools[q].mat = m.h->shared;
+      pools[q].type = type;
+    }
+    pool_of[i] = q;
+    vbase[i] = pools[q].R;
+    pools[q].R += m.r;
+    pools[q].mem.push_back(i);
+  }
+  const int npool = (int)pools.size();
+  // the pools' V rows and Y planes: one block, zeroed when it is made (the planes' padded columns
+  // stay zero: the y-step writes the first n of a row), kept while the pools' shapes are the same
+  Layout PL;
+  std::vector<size_t> oV(npool), oY(npool);
+  std::vector<int64_t> sig;
+  for (int q = 0; q < npool; ++q) {
+    const Member &m0 = g->members[pools[q].mem[0]];
+    oV[q] = PL.take(4 * (size_t)pools[q].R * m0.ldX);
+    oY[q] = PL.take(2 * 2 * (size_t)pools[q].R * m0.ldU);
+    sig.insert(sig.end(), {(int64_t)pools[q].R, m0.ldX, m0.ldU});
+  }
+  if (sig != g->pool_sig || !g->pool_mem) {
+    if (g->pool_mem) GCK(cudaFreeAsync(g->pool_mem, st));
+    g->pool_mem = nullptr;
+    g->pool_sig.clear();
+    GCK(cudaMallocFromPoolAsync((void **)&g->pool_mem, std::max<size_t>(PL.off, 256), g->mempool, st));
+    GCK(cudaMemsetAsync(g->pool_mem, 0, std::max<size_t>(PL.off, 256), st));
+    g->pool_sig = sig;
+  }
+  int R = 0, max_n = 1, max_p = 1, max_p_small = 0;
+  bool any_large_p = false;
   for (int i = 0; i < np; ++i) {
     Member &m = g->members[i];
+    const int q = pool_of[i];
     m.d.start0 = R;
-    P[i] = m.d;
+    m.d.vbase = vbase[i];
+    m.d.V = reinterpret_cast<float *>(g->pool_mem + oV[q]) + (int64_t)vbase[i] * m.ldX;
+    m.d.Ypl = reinterpret_cast<__half *>(g->pool_mem + oY[q]);
+    m.d.yps = (int64_t)pools[q].R * m.ldU;
     R += m.r;
     max_n = std::max(max_n, m.n);
     max_p = std::max(max_p, m.p);
+    if (m.p <= kXstepSmemMaxP)
+      max_p_small = std::max(max_p_small, m.p);
+    else
+      any_large_p = true;
   }
+  // the device tables: problems, start -> problem, tasks (u of the pending members; v of the
+  // pools, one copy per parity), active counts, tile lists, pools, pool members, pool counts,
+  // column maps, Y row offsets, the pools' Y plane maps
+  Layout L;
+  const size_t oP = L.take(sizeof(GProb) * np), oS = L.take(sizeof(int) * R),
+               oT = L.take(sizeof(GTask) * (np + 2 * npool)), oA = L.take(sizeof(int) * np);
+  std::vector<int2> tl[3];
+  const size_t oPool = L.take(sizeof(GPool) * npool), oPM = L.take(sizeof(int) * np),
+               oPC = L.take(sizeof(int) * npool), oCM = L.take(sizeof(int) * R), oYO = L.take(sizeof(int) * np),
+               oMap = L.take(sizeof(CUtensorMap) * npool);
+  // (the tile lists go last: their sizes are known once the tasks are)
   std::vector<int> start_prob(R);
   for (int i = 0; i < np; ++i)
-    for (int c = 0; c < g->members[i].r; ++c) start_prob[P[i].start0 + c] = i;
-  std::vector<GTask> tasks(3 * np);
-  std::vector<int2> tl[3];
-  int n_u = 0;
-  // one task per member; the tile list orders the matrices by falling K and, within a matrix, walks
-  // its M tiles with the tiles of every member on it side by side (they read the same A tile)
-  auto build = [&](bool u, int parity, GTask *base, std::vector<int2> &tiles, int *count) -> int {
-    std::vector<int> order;
-    for (int i = 0; i < np; ++i)
-      if (!u || g->members[i].first_pending) order.push_back(i);
-    auto kb = [&](int i) { return u ? (g->members[i].p + 63) / 64 : (g->members[i].n + 63) / 64; };
-    auto mat = [&](int i) { return reinterpret_cast<uintptr_t>(g->members[i].h->shared); };
+    for (int c = 0; c < g->members[i].r; ++c) start_prob[g->members[i].d.start0 + c] = i;
+  std::vector<GProb> P(np);
+  for (int i = 0; i < np; ++i) P[i] = g->members[i].d;
+  std::vector<GTask> tasks(np + 2 * npool);
+  // the tile list of a set of tasks: by falling K, and the tasks on one matrix walked together by
+  // M tile (their tiles of a row tile side by side: they read the same A tile)
+  auto tiles_of = [&](GTask *base, std::vector<GTask> &T, std::vector<const void *> &mat, std::vector<int2> &tiles) {
+    std::vector<int> order(T.size());
+    std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-      if (kb(a) != kb(b)) return kb(a) > kb(b);
-      return mat(a) < mat(b);
+      if (T[a].kblocks != T[b].kblocks) return T[a].kblocks > T[b].kblocks;
+      return reinterpret_cast<uintptr_t>(mat[a]) < reinterpret_cast<uintptr_t>(mat[b]);
     });
-    for (size_t k = 0; k < order.size(); ++k) {
-      const int i = order[k];
-      const Member &m = g->members[i];
-      GTask &T = base[k];
-      T = GTask{};
-      T.pmap = m.maps + (u ? 0 : 1);
-      T.qmap = m.maps + (u ? 2 : 3);
-      T.M = u ? m.n : m.p;
-      T.kblocks = kb(i);
-      T.nmax = m.r;
-      T.nb = u || !is_l1_var(m.P.form) ? 2 : 1;
-      T.n_dev = &m.d.ctrl[parity]->active;
-      T.col_map = m.d.act;
-      T.out = u ? m.d.U : m.d.V;
-      T.ldo = u ? m.ldU : m.ldX;
-      T.row_inv = u ? m.h->a_inv : m.h->at_inv;
-      T.col_inv = u ? m.d.x_inv : nullptr;
-      T.q_inv = u ? 1.0f : kQInv;
-      T.pairs = u || !is_l1_var(m.P.form) ? pairs_general() : pairs_sign();
-      T.mt = (T.M + TC_BM_ROWS - 1) / TC_BM_ROWS;
-      T.nt = (m.r + g->bn - 1) / g->bn;
-    }
+    for (size_t k = 0; k < order.size(); ++k) base[k] = T[order[k]];
     tiles.clear();
-    for (size_t a = 0; a < order.size();) {   // a run of tasks on one matrix
+    for (size_t a = 0; a < order.size();) {
       size_t b = a + 1;
-      while (b < order.size() && mat(order[b]) == mat(order[a])) ++b;
-      const int mt = base[a].mt;
-      for (int tm = 0; tm < mt; ++tm)
+      while (b < order.size() && mat[order[b]] == mat[order[a]] && base[b].mt == base[a].mt) ++b;
+      for (int tm = 0; tm < base[a].mt; ++tm)
         for (size_t k = a; k < b; ++k)
           for (int tn = 0; tn < base[k].nt; ++tn) tiles.push_back(make_int2((int)k, tm * base[k].nt + tn));
       a = b;
     }
-    *count = (int)order.size();
     return (int)tiles.size();
   };
-  // the pending members' first sweep is the next one, k + 1: it reads parity k & 1
-  int nv = 0;
-  g->total_u = build(true, (int)(g->k & 1), tasks.data(), tl[0], &n_u);
-  g->total_v = build(false, 0, tasks.data() + np, tl[1], &nv);
-  build(false, 1, tasks.data() + 2 * np, tl[2], &nv);
-  Layout L;
-  const size_t oP = L.take(sizeof(GProb) * np), oS = L.take(sizeof(int) * R), oT = L.take(sizeof(GTask) * 3 * np),
-               oA = L.take(sizeof(int) * np), oL0 = L.take(sizeof(int2) * tl[0].size()),
-               oL1 = L.take(sizeof(int2) * tl[1].size()), oL2 = L.take(sizeof(int2) * tl[2].size());
+  // u = A x of the members whose first sweep is pending (it reads parity k & 1)
+  int n_u = 0;
+  {
+    std::vector<GTask> T;
+    std::vector<const void *> mat;
+    for (int i = 0; i < np; ++i) {
+      const Member &m = g->members[i];
+      if (!m.first_pending) continue;
+      const bool lowp = m.h->resident16;   // its A has the leading plane only
+      GTask t{};
+      t.pmap = m.maps + 0;
+      t.qmap = m.maps + 2;
+      t.M = m.n;
+      t.kblocks = (m.p + 63) / 64;
+      t.nmax = m.r;
+      t.na = lowp ? 1 : 2;
+      t.nb = lowp ? 1 : 2;
+      t.n_dev = &m.d.ctrl[g->k & 1]->active;
+      t.col_map = m.d.act;
+      t.out = m.d.U;
+      t.ldo = m.ldU;
+      t.row_inv = m.h->a_inv;
+      t.col_inv = m.d.x_inv;
+      t.q_inv = 1.0f;
+      t.pairs = lowp ? pairs_hi() : pairs_general();
+      t.mt = (t.M + TC_BM_ROWS - 1) / TC_BM_ROWS;
+      t.nt = (m.r + g->bn - 1) / g->bn;
+      T.push_back(t);
+      mat.push_back(m.h->shared);
+    }
+    n_u = (int)T.size();
+    g->total_u = tiles_of(tasks.data(), T, mat, tl[0]);
+  }
+  // v = A^T y of the pools (one task each; the pool kernel fills the counts and column maps of the
+  // sweep's parity, so both parities take the same tasks)
+  {
+    std::vector<GTask> T;
+    std::vector<const void *> mat;
+    int64_t cm = 0;
+    for (int q = 0; q < npool; ++q) {
+      const Member &m0 = g->members[pools[q].mem[0]];
+      const int type = pools[q].type;
+      GTask t{};
+      t.pmap = m0.maps + 1;
+      t.qmap = reinterpret_cast<const CUtensorMap *>(g->tab + oMap) + q;
+      t.M = m0.p;
+      t.kblocks = (m0.n + 63) / 64;
+      t.nmax = pools[q].R;
+      t.na = type == 2 ? 1 : 2;
+      t.nb = type == 0 ? 2 : 1;
+      t.n_dev = reinterpret_cast<int *>(g->tab + oPC) + q;
+      t.col_map = reinterpret_cast<int *>(g->tab + oCM) + cm;
+      t.out = reinterpret_cast<float *>(g->pool_mem + oV[q]);
+      t.ldo = m0.ldX;
+      t.row_inv = m0.h->at_inv;
+      t.col_inv = nullptr;
+      t.q_inv = kQInv;
+      t.pairs = type == 2 ? pairs_hi() : type == 1 ? pairs_sign() : pairs_general();
+      t.mt = (t.M + TC_BM_ROWS - 1) / TC_BM_ROWS;
+      t.nt = (pools[q].R + g->bn - 1) / g->bn;
+      T.push_back(t);
+      mat.push_back(pools[q].mat);
+      cm += pools[q].R;
+    }
+    g->total_v = tiles_of(tasks.data() + np, T, mat, tl[1]);
+    for (int q = 0; q < npool; ++q) tasks[np + npool + q] = tasks[np + q];
+    tl[2] = tl[1];
+  }
+  const size_t oL0 = L.take(sizeof(int2) * tl[0].size()), oL1 = L.take(sizeof(int2) * tl[1].size());
   if (L.off > g->tab_bytes) {
+    // (the tasks hold addresses inside the table: a new table means new tasks, built again)
     GCK(cudaStreamSynchronize(st));
     if (g->tab) cudaFree(g->tab);
     g->tab = nullptr;
     g->tab_bytes = 0;
-    GCK(cudaMalloc((void **)&g->tab, L.off));
-    g->tab_bytes = L.off;
+    GCK(cudaMalloc((void **)&g->tab, L.off + (L.off >> 2)));
+    g->tab_bytes = L.off + (L.off >> 2);
     for (GroupGraph &q : g->graphs)
       if (q.exec) cudaGraphExecDestroy(q.exec);
     g->graphs.clear();
+    return build_tables(g);
   }
   if (g->h_active_cap < np) {
     if (g->h_active) cudaFreeHost(g->h_active);
@@ -385,22 +502,52 @@ int build_tables(spca_group *g) {
     GCK(cudaMallocHost((void **)&g->h_active, sizeof(int) * np));
     g->h_active_cap = np;
   }
-  g->dP = reinterpret_cast<GProb *>(g->tab + oP);
-  g->d_start_prob = reinterpret_cast<int *>(g->tab + oS);
-  g->d_tasks = reinterpret_cast<GTask *>(g->tab + oT);
-  g->d_active = reinterpret_cast<int *>(g->tab + oA);
-  for (int q = 0; q < 3; ++q) g->d_tiles[q] = reinterpret_cast<int2 *>(g->tab + (q == 0 ? oL0 : q == 1 ? oL1 : oL2));
+  char *tab = g->tab;
+  g->dP = reinterpret_cast<GProb *>(tab + oP);
+  g->d_start_prob = reinterpret_cast<int *>(tab + oS);
+  g->d_tasks = reinterpret_cast<GTask *>(tab + oT);
+  g->d_active = reinterpret_cast<int *>(tab + oA);
+  g->d_tiles[0] = reinterpret_cast<int2 *>(tab + oL0);
+  g->d_tiles[1] = g->d_tiles[2] = reinterpret_cast<int2 *>(tab + oL1);
+  g->d_pools = reinterpret_cast<GPool *>(tab + oPool);
+  g->d_pool_members = reinterpret_cast<int *>(tab + oPM);
+  g->npool = npool;
+  // pools, their member lists and the members' Y row offset words
+  std::vector<GPool> GP(npool);
+  std::vector<int> pm;
+  int64_t cm = 0;
+  for (int q = 0; q < npool; ++q) {
+    GP[q].first = (int)pm.size();
+    GP[q].nmem = (int)pools[q].mem.size();
+    GP[q].count = reinterpret_cast<int *>(tab + oPC) + q;
+    GP[q].colmap = reinterpret_cast<int *>(tab + oCM) + cm;
+    pm.insert(pm.end(), pools[q].mem.begin(), pools[q].mem.end());
+    cm += pools[q].R;
+  }
+  for (int i = 0; i < np; ++i) {
+    P[i].yoff = reinterpret_cast<int *>(tab + oYO) + i;
+    g->members[i].d.yoff = P[i].yoff;
+  }
+  std::vector<CUtensorMap> maps(npool);
+  for (int q = 0; q < npool; ++q)
+    GCK(make_plane_map(&maps[q], g->pool_mem + oY[q], pools[q].R, g->members[pools[q].mem[0]].ldU, 2, 64, 64));
   // (pageable sources: each copy returns once its data are staged, so the vectors may go)
   GCK(cudaMemcpyAsync(g->dP, P.data(), sizeof(GProb) * np, cudaMemcpyHostToDevice, st));
   GCK(cudaMemcpyAsync(g->d_start_prob, start_prob.data(), sizeof(int) * R, cudaMemcpyHostToDevice, st));
-  GCK(cudaMemcpyAsync(g->d_tasks, tasks.data(), sizeof(GTask) * 3 * np, cudaMemcpyHostToDevice, st));
-  for (int q = 0; q < 3; ++q)
-    if (!tl[q].empty())
-      GCK(cudaMemcpyAsync(g->d_tiles[q], tl[q].data(), sizeof(int2) * tl[q].size(), cudaMemcpyHostToDevice, st));
+  GCK(cudaMemcpyAsync(g->d_tasks, tasks.data(), sizeof(GTask) * tasks.size(), cudaMemcpyHostToDevice, st));
+  if (!tl[0].empty())
+    GCK(cudaMemcpyAsync(g->d_tiles[0], tl[0].data(), sizeof(int2) * tl[0].size(), cudaMemcpyHostToDevice, st));
+  if (!tl[1].empty())
+    GCK(cudaMemcpyAsync(g->d_tiles[1], tl[1].data(), sizeof(int2) * tl[1].size(), cudaMemcpyHostToDevice, st));
+  GCK(cudaMemcpyAsync(g->d_pools, GP.data(), sizeof(GPool) * npool, cudaMemcpyHostToDevice, st));
+  GCK(cudaMemcpyAsync(g->d_pool_members, pm.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st));
+  GCK(cudaMemcpyAsync(tab + oMap, maps.data(), sizeof(CUtensorMap) * npool, cudaMemcpyHostToDevice, st));
   g->R = R;
   g->n_u = n_u;
   g->max_n = max_n;
   g->max_p = max_p;
+  g->max_p_small = max_p_small;
+  g->any_large_p = any_large_p;
   g->tables_ok = true;
   return SPCA_OK;
 }
@@ -418,13 +565,16 @@ cudaError_t enqueue_sweep(spca_group *g, int64_t k, bool first_of_segment) {
     if (e == cudaSuccess)
       e = launch_gemm_grouped(g->d_tasks, g->d_tiles[0], g->total_u, g->bn, g->stages, g->sms, g->d_err, wait_ns, st);
   }
+  // the pools' Y rows, counts and column maps for this sweep's active lists
+  if (e == cudaSuccess) e = launch_g_pools(g->d_pools, g->npool, g->dP, g->d_pool_members, cur, st);
   if (e == cudaSuccess) e = launch_g_gather(g->dP, g->d_start_prob, g->R, g->max_n, st);
   if (e == cudaSuccess) e = launch_g_ystep(g->dP, g->d_start_prob, g->R, st);
   if (e == cudaSuccess)
-    e = launch_gemm_grouped(g->d_tasks + (1 + cur) * np, g->d_tiles[1 + cur], g->total_v, g->bn, g->stages, g->sms,
-                            g->d_err, wait_ns, st);
+    e = launch_gemm_grouped(g->d_tasks + np + cur * g->npool, g->d_tiles[1 + cur], g->total_v, g->bn, g->stages,
+                            g->sms, g->d_err, wait_ns, st);
   if (e == cudaSuccess) e = launch_g_ctrl(g->dP, np, nxt, 1, nullptr, st);
-  if (e == cudaSuccess) e = launch_g_xstep(g->dP, g->d_start_prob, g->R, g->max_p, nxt, g->sms, st);
+  if (e == cudaSuccess)
+    e = launch_g_xstep(g->dP, g->d_start_prob, g->R, g->max_p_small, g->any_large_p, nxt, g->sms, st);
   if (e == cudaSuccess) e = launch_g_active(g->dP, np, nxt, st);
   return e;
 }
@@ -450,8 +600,12 @@ int finish_members(spca_group *g, const std::vector<Member *> &list) {
   for (size_t k = 0; k < list.size(); ++k) {
     Member &m = *list[k];
     const GProb &d = m.d;
-    GCK(launch_finalise(m.P.form, m.h->AT32, m.h->ldAT, m.n, m.p, d.X, m.ldX, d.st, m.r, d.U, m.ldU, d.sup_idx,
-                        d.sup_val, m.p, m.partials, st));
+    if (m.h->resident16)
+      GCK(launch_finalise_h(m.P.form, d.AT16, d.at_inv, m.h->ldAT, m.n, d.st, m.r, d.U, m.ldU, d.sup_idx, d.sup_val,
+                            m.p, m.partials, st));
+    else
+      GCK(launch_finalise(m.P.form, m.h->AT32, m.h->ldAT, m.n, m.p, d.X, m.ldX, d.st, m.r, d.U, m.ldU, d.sup_idx,
+                          d.sup_val, m.p, m.partials, st));
     GCK(launch_best(m.P.form, m.target, d.st, m.r, m.best, st));
     GCK(launch_best_outputs(m.P.form, m.best, d.U, m.ldU, m.n, d.X, m.ldX, m.p, m.y_out, m.x_out, m.support_out,
                             m.nnz_out, st));
@@ -662,6 +816,16 @@ int spca_group_create(spca_group **out, void *cuda_stream) {
     spca_group_destroy(g);
     return SPCA_E_CUDA;
   }
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  uint64_t keep = ~0ull;
+  if (cudaMemPoolCreate(&g->mempool, &props) != cudaSuccess ||
+      cudaMemPoolSetAttribute(g->mempool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+    spca_group_destroy(g);
+    return SPCA_E_CUDA;
+  }
   *out = g;
   return SPCA_OK;
 }
@@ -670,6 +834,7 @@ void spca_group_destroy(spca_group *g) {
   if (!g) return;
   for (Member &m : g->members) release_member(g, m);
   g->members.clear();
+  if (g->pool_mem && g->stream) cudaFreeAsync(g->pool_mem, g->stream);
   if (g->stream) cudaStreamSynchronize(g->stream);
   for (GroupGraph &q : g->graphs)
     if (q.exec) cudaGraphExecDestroy(q.exec);
@@ -682,6 +847,7 @@ void spca_group_destroy(spca_group *g) {
   if (g->h_err) cudaFreeHost(g->h_err);
   if (g->order_ev) cudaEventDestroy(g->order_ev);
   if (g->stream) cudaStreamDestroy(g->stream);
+  if (g->mempool) cudaMemPoolDestroy(g->mempool);   // (every block was freed and the stream drained)
   delete g;
 }
 

@@ -16,14 +16,18 @@ constexpr int FT = 256;
 // grid (r, ceil(n / FT)): u_i = sum_t x_{j_t} A[i, j_t] over the support (compensated FP32
 // pairs); per-CTA FP64 partial sums of |u_i| and u_i^2 go to partials (fixed order later).
 // Starts on x, row chunks on y: the CTAs in flight share row chunks, so a column slice used by
-// several starts' supports is read from DRAM about once.
-__global__ void __launch_bounds__(FT) k_fin_partial(const float *__restrict__ AT, int64_t ldat, int n,
-                                                    const int *__restrict__ sup_idx,
+// several starts' supports is read from DRAM about once.  The columns of A are the rows of A^T:
+// FP32 (row_inv null), or FP16 entries times their row's power-of-two inverse scale (the 16-bit
+// copy of a resident handle; the scaled entry is exact in FP32).
+template <typename T>
+__global__ void __launch_bounds__(FT) k_fin_partial(const T *__restrict__ AT, const float *__restrict__ row_inv,
+                                                    int64_t ldat, int n, const int *__restrict__ sup_idx,
                                                     const float *__restrict__ sup_val, int cap,
                                                     StartState st, float *__restrict__ U,
                                                     int64_t ldu, double *__restrict__ partials) {
   __shared__ int sidx[FT];
   __shared__ float sval[FT];
+  __shared__ float sinv[FT];
   __shared__ double red[32];
   const int c = blockIdx.x;
   const int i = blockIdx.y * FT + threadIdx.x;
@@ -34,13 +38,18 @@ __global__ void __launch_bounds__(FT) k_fin_partial(const float *__restrict__ AT
   for (int t0 = 0; t0 < nnz; t0 += FT) {
     __syncthreads();
     if (t0 + (int)threadIdx.x < nnz) {
-      sidx[threadIdx.x] = gi[t0 + threadIdx.x];
+      const int j = gi[t0 + threadIdx.x];
+      sidx[threadIdx.x] = j;
       sval[threadIdx.x] = gv[t0 + threadIdx.x];
+      sinv[threadIdx.x] = row_inv ? row_inv[j] : 1.0f;
     }
     __syncthreads();
     const int m = min(FT, nnz - t0);
     if (i < n)
-      for (int t = 0; t < m; ++t) f32pair_fma(acc2, sval[t], AT[(int64_t)sidx[t] * ldat + i]);
+      for (int t = 0; t < m; ++t) {
+        const float a = static_cast<float>(AT[(int64_t)sidx[t] * ldat + i]) * sinv[t];
+        f32pair_fma(acc2, sval[t], a);
+      }
   }
   const double acc = f32pair_value(acc2);
   if (i < n) U[(int64_t)c * ldu + i] = (float)acc;
@@ -90,8 +99,21 @@ cudaError_t launch_finalise(int form, const float *AT, int64_t ldat, int n, int 
   (void)p; (void)X; (void)ldX;
   const int nchunks = (n + FT - 1) / FT;
   if (nchunks > 65535) return cudaErrorInvalidValue;   // grid y limit: n above 16.7 million rows
-  k_fin_partial<<<dim3((unsigned)r, (unsigned)nchunks), FT, 0, st>>>(AT, ldat, n, sup_idx, sup_val,
-                                                                      cap, s, U, ldu, partials);
+  k_fin_partial<float><<<dim3((unsigned)r, (unsigned)nchunks), FT, 0, st>>>(AT, nullptr, ldat, n, sup_idx, sup_val,
+                                                                             cap, s, U, ldu, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_fin_reduce<<<r, FT, 0, st>>>(form, partials, nchunks, sup_val, cap, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalise_h(int form, const __half *AT16, const float *at_inv, int64_t ldat, int n, StartState s,
+                              int r, float *U, int64_t ldu, const int *sup_idx, const float *sup_val, int cap,
+                              double *partials, cudaStream_t st) {
+  const int nchunks = (n + FT - 1) / FT;
+  if (nchunks > 65535) return cudaErrorInvalidValue;
+  k_fin_partial<__half><<<dim3((unsigned)r, (unsigned)nchunks), FT, 0, st>>>(AT16, at_inv, ldat, n, sup_idx,
+                                                                              sup_val, cap, s, U, ldu, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_fin_reduce<<<r, FT, 0, st>>>(form, partials, nchunks, sup_val, cap, s);

@@ -25,6 +25,7 @@ namespace {
 constexpr int XT = 512;                        // threads per CTA
 constexpr int XW = XT / 32;                    // warps per CTA
 constexpr int XSTEP_SMEM_MAX = 200 * 1024;     // largest v staged in shared memory (bytes)
+static_assert(kXstepSmemMaxP * 4 == XSTEP_SMEM_MAX, "the grouped x-step's split");
 
 struct XShared {
   unsigned hist[256];
@@ -1025,7 +1026,8 @@ __global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int 
 }  // namespace
 
 // groups of problems: the full pass for every active start of every problem, persistent CTAs over
-// the global starts (v staged in shared memory when the longest v fits)
+// the global starts; the kSmem launch takes the problems whose v fits in shared memory (staged
+// there), the other launch the rest
 template <bool kSmem>
 __global__ void __launch_bounds__(XT) k_g_xstep(const GProb *__restrict__ P, const int *__restrict__ prob, int R,
                                                 int parity) {
@@ -1033,6 +1035,7 @@ __global__ void __launch_bounds__(XT) k_g_xstep(const GProb *__restrict__ P, con
   __shared__ XShared sh;
   for (int g = blockIdx.x; g < R; g += gridDim.x) {
     const GProb &q = P[prob[g]];
+    if (kSmem != ((size_t)q.p * sizeof(float) <= (size_t)XSTEP_SMEM_MAX)) continue;
     const int c = g - q.start0;
     StartState st = q.st;
     if (st.status[c] != ST_ACTIVE) continue;
@@ -1043,18 +1046,24 @@ __global__ void __launch_bounds__(XT) k_g_xstep(const GProb *__restrict__ P, con
   }
 }
 
-cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p, int parity, int sms, cudaStream_t st) {
-  const size_t bytes = (size_t)max_p * sizeof(float);
-  if (bytes <= (size_t)XSTEP_SMEM_MAX) {
+cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p_small, bool any_large, int parity,
+                           int sms, cudaStream_t st) {
+  if (max_p_small > 0) {   // the problems whose v fits in shared memory: staged there
+    const size_t bytes = (size_t)max_p_small * sizeof(float);
+    if (bytes > (size_t)XSTEP_SMEM_MAX) return cudaErrorInvalidValue;
     static const cudaError_t configured =
         cudaFuncSetAttribute(k_g_xstep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, XSTEP_SMEM_MAX);
     if (configured != cudaSuccess) return configured;
     const int per_sm = bytes <= 100u * 1024u ? 2 : 1;
     k_g_xstep<true><<<min(R, per_sm * sms), XT, bytes, st>>>(P, prob, R, parity);
-  } else {
-    k_g_xstep<false><<<min(R, 2 * sms), XT, 0, st>>>(P, prob, R, parity);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  return cudaGetLastError();
+  if (any_large) {
+    k_g_xstep<false><<<min(R, 2 * sms), XT, 0, st>>>(P, prob, R, parity);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,

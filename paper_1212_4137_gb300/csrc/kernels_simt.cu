@@ -543,6 +543,57 @@ __device__ void gather_body(const float *__restrict__ AT, int64_t ldat, int n, c
   if (i4 + 3 < n) u[i4 + 3] = acc.w;
 }
 
+// gather_body over the leading FP16 plane of A^T (a resident 16-bit handle): row j of the plane
+// is A[:, j] times its power-of-two scale, undone by folding at_inv[j] into x_j (exact); four rows
+// per thread as one 8-byte load, products and sums in FP32 in support order
+__device__ void gather_lowp_body(const __half *__restrict__ AT0, const float *__restrict__ at_inv, int64_t ldat,
+                                 int n, const int *__restrict__ sup_idx, const float *__restrict__ sup_val, int cap,
+                                 StartState s, float *__restrict__ U, int64_t ldu, int c, int yb, int *sidx,
+                                 float *sval) {
+  if (s.status[c] != ST_ACTIVE) return;
+  if (s.iters[c] == 0) return;   // a start not swept yet has a dense x: the dense contraction
+  const int nnz = s.nnz[c];
+  const int i4 = (yb * kGatherThreads + threadIdx.x) * 4;
+  const int *gi = sup_idx + (int64_t)c * cap;
+  const float *gv = sup_val + (int64_t)c * cap;
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  auto step = [&](float xv, uint2 raw) {
+    const __half2 *h2 = reinterpret_cast<const __half2 *>(&raw);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float2 f = __half22float2(h2[q]);
+      acc[2 * q] = fmaf(xv, f.x, acc[2 * q]);
+      acc[2 * q + 1] = fmaf(xv, f.y, acc[2 * q + 1]);
+    }
+  };
+  for (int t0 = 0; t0 < nnz; t0 += kGatherThreads) {
+    __syncthreads();
+    if (t0 + (int)threadIdx.x < nnz) {
+      const int j = gi[t0 + threadIdx.x];
+      sidx[threadIdx.x] = j;
+      sval[threadIdx.x] = gv[t0 + threadIdx.x] * at_inv[j];
+    }
+    __syncthreads();
+    const int m = min(kGatherThreads, nnz - t0);
+    if (i4 < n) {
+      const __half *base = AT0 + i4;
+      int t = 0;
+      for (; t + 8 <= m; t += 8) {
+        uint2 a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = __ldg(reinterpret_cast<const uint2 *>(base + (int64_t)sidx[t + q] * ldat));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) step(sval[t + q], a[q]);
+      }
+      for (; t < m; ++t) step(sval[t], __ldg(reinterpret_cast<const uint2 *>(base + (int64_t)sidx[t] * ldat)));
+    }
+  }
+  float *u = U + (int64_t)c * ldu;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (i4 + q < n) u[i4 + q] = acc[q];
+}
+
 // The same gather over the leading FP16 plane of A^T (the low-precision sweeps): row j of the
 // plane is A[:, j] times at_scale[j]; the inverse scale is folded into x_j.  8 rows per thread as
 // one 16-byte load, products and sums in FP32 in support order.
@@ -812,7 +863,11 @@ __global__ void __launch_bounds__(kGatherThreads) k_g_gather(const GProb *__rest
   const GProb &q = P[prob[blockIdx.x]];
   if ((int)blockIdx.y * 4 * kGatherThreads >= q.n) return;
   const int c = (int)blockIdx.x - q.start0;
-  gather_body(q.AT32, q.ldAT, q.n, q.sup_idx, q.sup_val, q.p, q.st, q.U, q.ldU, c, (int)blockIdx.y, sidx, sval);
+  if (q.AT16)
+    gather_lowp_body(q.AT16, q.at_inv, q.ldAT, q.n, q.sup_idx, q.sup_val, q.p, q.st, q.U, q.ldU, c, (int)blockIdx.y,
+                     sidx, sval);
+  else
+    gather_body(q.AT32, q.ldAT, q.n, q.sup_idx, q.sup_val, q.p, q.st, q.U, q.ldU, c, (int)blockIdx.y, sidx, sval);
 }
 
 cudaError_t launch_g_gather(const GProb *P, const int *prob, int R, int max_n, cudaStream_t st) {
@@ -826,7 +881,36 @@ __global__ void __launch_bounds__(256) k_g_ystep(const GProb *__restrict__ P, co
   __shared__ float redf[32];
   const GProb &q = P[prob[blockIdx.x]];
   const int c = (int)blockIdx.x - q.start0;
-  ystep_body(q.form, q.U, q.ldU, q.n, nullptr, q.Ypl, q.yps, q.rank, q.st, q.X, q.ldX, q.p, c, redf);
+  // the member's active starts sit at its pool's Y rows *yoff + rank
+  __half *ypl = q.Ypl + (q.yoff ? (int64_t)*q.yoff * q.ldU : 0);
+  ystep_body(q.form, q.U, q.ldU, q.n, nullptr, ypl, q.yps, q.rank, q.st, q.X, q.ldX, q.p, c, redf);
+}
+
+__global__ void __launch_bounds__(256) k_g_pools(const GPool *__restrict__ pools, const GProb *__restrict__ P,
+                                                 const int *__restrict__ members, int parity) {
+  const GPool q = pools[blockIdx.x];
+  if (threadIdx.x == 0) {   // Y row offsets in member order
+    int acc = 0;
+    for (int k = 0; k < q.nmem; ++k) {
+      const GProb &m = P[members[q.first + k]];
+      *m.yoff = acc;
+      acc += m.ctrl[parity]->active;
+    }
+    *q.count = acc;
+  }
+  __syncthreads();   // (the offsets are this block's own global writes)
+  for (int k = 0; k < q.nmem; ++k) {
+    const GProb &m = P[members[q.first + k]];
+    const int a = m.ctrl[parity]->active, o = *m.yoff;
+    for (int t = threadIdx.x; t < a; t += blockDim.x) q.colmap[o + t] = m.vbase + m.act[t];
+  }
+}
+
+cudaError_t launch_g_pools(const GPool *pools, int npool, const GProb *P, const int *members, int parity,
+                           cudaStream_t st) {
+  if (npool < 1) return cudaSuccess;
+  k_g_pools<<<npool, 256, 0, st>>>(pools, P, members, parity);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_g_ystep(const GProb *P, const int *prob, int R, cudaStream_t st) {

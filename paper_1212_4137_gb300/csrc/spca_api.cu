@@ -282,6 +282,8 @@ int resolve_engine(spca_handle *h, int engine, int r, bool lowp, int *out) {
     return fail(h, SPCA_E_UNSUPPORTED, "a sparse A runs on the CUDA-core engine%s");
   if (engine == SPCA_ENGINE_TC && !h->tc_ok)
     return fail(h, SPCA_E_UNSUPPORTED, "tensor-core engine needs an sm_100+ device%s");
+  if (h->resident16 && (!lowp || engine == SPCA_ENGINE_SIMT))
+    return fail(h, SPCA_E_UNSUPPORTED, "a resident 16-bit handle runs low-precision sweeps on the tensor cores only%s");
   if (engine == SPCA_ENGINE_AUTO) {
     // few starts: the streaming GEMV on the CUDA cores reads A once per product at HBM speed,
     // where the tensor-core tiles would pad the starts to 256 columns
@@ -577,11 +579,12 @@ int build_operands(spca_handle *h) {
                                       h->stream);
     if (e == cudaSuccess)
       e = launch_row_scales(h->AT32, p, n, h->ldAT, h->at_scale, h->at_inv, nullptr, nullptr, nullptr, h->stream);
+    const int planes = h->resident16 ? 1 : kPlanes;
     if (e == cudaSuccess)
-      e = launch_split_planes(h->A32, n, h->ldA, h->ldA, h->Apl, h->ldA, n * h->ldA, kPlanes, h->a_scale, 1.0f,
+      e = launch_split_planes(h->A32, n, h->ldA, h->ldA, h->Apl, h->ldA, n * h->ldA, planes, h->a_scale, 1.0f,
                               nullptr, nullptr, nullptr, h->stream);
     if (e == cudaSuccess)
-      e = launch_split_planes(h->AT32, p, h->ldAT, h->ldAT, h->ATpl, h->ldAT, p * h->ldAT, kPlanes, h->at_scale,
+      e = launch_split_planes(h->AT32, p, h->ldAT, h->ldAT, h->ATpl, h->ldAT, p * h->ldAT, planes, h->at_scale,
                               1.0f, nullptr, nullptr, nullptr, h->stream);
     return e;
   }));
@@ -624,6 +627,7 @@ int spca_deflate(spca_handle *h, const float *x, int x_is_device) {
   if (h->shared && h->shared->refs.load() > 1)
     return fail(h, SPCA_E_UNSUPPORTED, "the matrix is shared with another handle (spca_clone)%s");
   if (h->sparse) return deflate_sparse(h, x, x_is_device);
+  if (h->resident16) return fail(h, SPCA_E_UNSUPPORTED, "deflation of a resident 16-bit handle%s");
   RC(enter(h));
   const int64_t n = h->n, p = h->p;
   cudaStream_t st = h->stream;
@@ -725,7 +729,8 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
   if (n < 1 || p < 1 || lda < p || n > INT32_MAX || p > INT32_MAX) return SPCA_E_INVALID;
   if (n > kMaxDenseRows) return SPCA_E_UNSUPPORTED;
   if (in_dtype != SPCA_F32 && in_dtype != SPCA_F64) return SPCA_E_INVALID;
-  if (storage != SPCA_F32 && storage != SPCA_FP16 && storage != SPCA_FP8_E4M3_COLSCALED) {
+  if (storage != SPCA_F32 && storage != SPCA_FP16 && storage != SPCA_FP8_E4M3_COLSCALED &&
+      storage != SPCA_FP16_RESIDENT) {
     if (storage == SPCA_F64) return SPCA_E_UNSUPPORTED;
     return SPCA_E_INVALID;
   }
@@ -751,9 +756,11 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
     h->tc_ok = major >= 10;
     CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
-    if ((storage == SPCA_FP16 || storage == SPCA_FP8_E4M3_COLSCALED) && !h->tc_ok)
+    if ((storage == SPCA_FP16 || storage == SPCA_FP8_E4M3_COLSCALED || storage == SPCA_FP16_RESIDENT) && !h->tc_ok)
       return SPCA_E_UNSUPPORTED;   // the planes need tcgen05
     h->fp8 = storage == SPCA_FP8_E4M3_COLSCALED;
+    h->resident16 = storage == SPCA_FP16_RESIDENT;
+    const int planes = h->resident16 ? 1 : kPlanes;
     CK(cudaMallocHost((void **)&h->h_ctrl, 2 * sizeof(Ctrl)));
     CK(cudaMallocHost((void **)&h->h_flag, 2 * sizeof(int)));
     h->h_flag[0] = h->h_flag[1] = 0;
@@ -781,8 +788,8 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     CK(timed(h, SPCA_K_PREP, 1, [&] { return launch_check_finite(h->A32, n, p, h->ldA, h->flag, h->stream); }));
     CK(cudaMemcpyAsync(h->h_flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     if (h->tc_ok) {
-      CK(dalloc(&h->Apl, (size_t)kPlanes * n * h->ldA, 2));
-      CK(dalloc(&h->ATpl, (size_t)kPlanes * p * h->ldAT, 2));
+      CK(dalloc(&h->Apl, (size_t)planes * n * h->ldA, 2));
+      CK(dalloc(&h->ATpl, (size_t)planes * p * h->ldAT, 2));
       CK(dalloc(&h->a_scale, (size_t)n)); CK(dalloc(&h->a_inv, (size_t)n));
       CK(dalloc(&h->at_scale, (size_t)p)); CK(dalloc(&h->at_inv, (size_t)p));
     }
@@ -799,8 +806,8 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     }
     RC(build_operands(h));
     if (h->tc_ok) {
-      CK(make_p_maps(&h->pmA, h->Apl, n, h->ldA, kPlanes));
-      CK(make_p_maps(&h->pmAT, h->ATpl, p, h->ldAT, kPlanes));
+      CK(make_p_maps(&h->pmA, h->Apl, n, h->ldA, planes));
+      CK(make_p_maps(&h->pmAT, h->ATpl, p, h->ldAT, planes));
       h->sk.slots = h->sms / 2 > 0 ? h->sms / 2 : 1;
       CK(dalloc(&h->sk.ws, (size_t)h->sk.slots * tc_sk_floats_per_slot()));
       CK(dalloc(&h->sk.flags, (size_t)2 * h->sk.slots));
@@ -808,6 +815,12 @@ int spca_create(spca_handle **out, const void *A, int64_t n, int64_t p, int64_t 
     }
     CK(cudaStreamSynchronize(h->stream));
     if (*h->h_flag) return fail(h, SPCA_E_INVALID, "A has a non-finite entry%s");
+    if (h->resident16) {   // the planes are built: the FP32 copies go
+      CK(cudaFree(h->A32));
+      h->A32 = nullptr;
+      CK(cudaFree(h->AT32));
+      h->AT32 = nullptr;
+    }
     return SPCA_OK;
   }();
   if (rc != SPCA_OK) {
@@ -930,6 +943,7 @@ int spca_clone(spca_handle **out, spca_handle *src, void *cuda_stream) {
   h->defl_k = src->defl_k; h->defl_cap = src->defl_cap;
   h->Wd = src->Wd; h->Zd = src->Zd;
   h->tc_ok = src->tc_ok; h->sms = src->sms;
+  h->resident16 = src->resident16;
   h->Apl = src->Apl; h->ATpl = src->ATpl;
   h->a_scale = src->a_scale; h->a_inv = src->a_inv;
   h->at_scale = src->at_scale; h->at_inv = src->at_inv;
@@ -1029,20 +1043,27 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   if (target && P.gamma_calib_sweeps < 1) return fail(h, SPCA_E_INVALID, "gamma_calib_sweeps must be >= 1%s");
   if (P.lowp_sweeps < 0 || P.refine_sweeps < 0 || P.timeout_us < 0 || P.lowp_first < 0)
     return fail(h, SPCA_E_INVALID, "lowp_sweeps, lowp_first, refine_sweeps and timeout_us must be >= 0%s");
+  // a resident 16-bit handle: every sweep reads the 16-bit copy (no FP32 copy to refine on)
+  const bool all_lowp = h->resident16;
+  if (all_lowp && (P.lowp_sweeps > 0 || P.lowp_first > 0 || P.refine_sweeps > 0))
+    return fail(h, SPCA_E_INVALID,
+                "every sweep of a resident 16-bit handle is a low-precision sweep: lowp_sweeps, lowp_first and "
+                "refine_sweeps must be 0%s");
   int engine;
-  RC(resolve_engine(h, P.engine, P.r, P.lowp_sweeps > 0, &engine));
+  RC(resolve_engine(h, P.engine, P.r, P.lowp_sweeps > 0 || all_lowp, &engine));
   if (P.lowp_sweeps > 0 && engine != SPCA_ENGINE_TC)
     return fail(h, SPCA_E_UNSUPPORTED, "low-precision sweeps need the tensor-core engine%s");
   // on-the-fly replacement: l starts through the r slots
   const int l = P.total_starts > P.r ? P.total_starts : P.r;
   if (l > kMaxStarts) return fail(h, SPCA_E_UNSUPPORTED, "more than 65535 starts%s");
   const bool otf = l > P.r;
-  if (otf && P.lowp_sweeps > 0)
+  if (otf && (P.lowp_sweeps > 0 || all_lowp))
     return fail(h, SPCA_E_UNSUPPORTED, "low-precision sweeps with on-the-fly replacement%s");
   RC(enter(h));
   const auto t_start = std::chrono::steady_clock::now();
-  // low-precision sweeps: F0 FP32 sweeps first, then L low-precision ones, then FP32 again
-  const int L = P.lowp_sweeps, F0 = L > 0 ? P.lowp_first : 0;
+  // low-precision sweeps: F0 FP32 sweeps first, then L low-precision ones, then FP32 again (all
+  // of them for a resident 16-bit handle)
+  const int L = all_lowp ? P.max_iter : P.lowp_sweeps, F0 = P.lowp_sweeps > 0 ? P.lowp_first : 0;
   const int max_iter = P.refine_sweeps > 0 ? (int)std::min<int64_t>(P.max_iter, (int64_t)F0 + L + P.refine_sweeps)
                                            : P.max_iter;
 
@@ -1118,7 +1139,9 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   xa.schedule = 1;
   xa.target = target ? 1 : 0;
   xa.calib_sweeps = C;
-  xa.lowp_sweeps = F0 + L;   // the stopping rule compares FP32 sweeps after the window
+  // the stopping rule compares FP32 sweeps after the window (any two sweeps when all are
+  // low-precision ones)
+  xa.lowp_sweeps = all_lowp ? 0 : F0 + L;
   xa.stop_enabled = P.tol >= 0.0 ? 1 : 0;
   // the host queues this many sweeps before it reads the active count back; every path decision
   // inside a sweep is taken on the device from the control word
@@ -1238,7 +1261,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
       dense_queued = max_nnz > sparse_cap / 2;
       pl.sparse_cap = dense_queued ? sparse_cap : p;   // p: the gather for every support
       const bool next_lowp = k + 1 > F0 && k + 1 <= F0 + L;
-      union_built = engine == SPCA_ENGINE_TC && !otf && !next_lowp && sum_nnz <= (int64_t)kUnionTry * h->kcap &&
+      union_built = engine == SPCA_ENGINE_TC && !otf && !all_lowp && !next_lowp && sum_nnz <= (int64_t)kUnionTry * h->kcap &&
                     h->n * sum_nnz >= kUnionMinReads;
       pl.union_out = union_built;
       plans.push_back(pl);
@@ -1349,8 +1372,12 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
     }));
   } else {
     CK(timed(h, SPCA_K_FINALISE, 4, [&] {
-      cudaError_t e = launch_finalise(form, h->AT32, h->ldAT, n, p, h->X, h->ldX, S, r, h->U, h->ldU, h->sup_idx,
-                                      h->sup_val, p, h->partials, st);
+      cudaError_t e =
+          h->resident16
+              ? launch_finalise_h(form, static_cast<const __half *>(h->ATpl), h->at_inv, h->ldAT, n, S, r, h->U,
+                                  h->ldU, h->sup_idx, h->sup_val, p, h->partials, st)
+              : launch_finalise(form, h->AT32, h->ldAT, n, p, h->X, h->ldX, S, r, h->U, h->ldU, h->sup_idx,
+                                h->sup_val, p, h->partials, st);
       if (e == cudaSuccess) e = launch_best(form, target ? 1 : 0, S, r, h->best, st);
       if (e == cudaSuccess)
         e = launch_best_outputs(form, h->best, h->U, h->ldU, n, h->X, h->ldX, p, h->y_out, h->x_out,

@@ -60,6 +60,9 @@ struct spca_handle {
   int lr_rows = 0;
   XstepScratch xs{};                       // the candidate x-step's lists and counts
   bool tc_ok = false;                      // the device has tcgen05 tensor cores (sm_100+)
+  // SPCA_FP16_RESIDENT: only the leading FP16 planes of A and A^T (one plane each, A32 and AT32
+  // freed after create); every sweep is a low-precision sweep
+  bool resident16 = false;
   int sms = 1;                             // streaming multiprocessors of the device
   void *Apl = nullptr, *ATpl = nullptr;    // tensor-core planes (kPlanes FP16 each, row-scaled)
   float *a_scale = nullptr, *a_inv = nullptr;     // row scales of A (n) and their inverses

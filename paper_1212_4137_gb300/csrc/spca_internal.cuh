@@ -393,6 +393,12 @@ struct GProb {
   int n, p, r, start0, form;
   int64_t ldX, ldU, ldAT;
   const float *AT32;            // A^T (p x ldAT): the support gather reads columns of A as its rows
+  const __half *AT16;           // or its leading FP16 plane (a resident 16-bit handle; AT32 null)
+  const float *at_inv;          // with the inverse row scales of that plane
+  // the member's place in its pool (the members on one matrix that share v = A^T y): its starts
+  // are V's rows vbase .. vbase + r - 1, and its active starts the Y planes' rows from *yoff on
+  int vbase;
+  int *yoff;
   float *X, *V, *U;             // r x ldX, r x ldX, r x ldU
   __half *Xpl, *Ypl;            // two FP16 planes each (x row-scaled, y scaled by kQScale), packed rows
   int64_t xps, yps;             // plane strides (elements)
@@ -408,6 +414,17 @@ struct GProb {
   uint64_t key;
   double gamma0;
 };
+// a pool: members on one matrix whose v = A^T y has the same plane products, listed at
+// members[first .. first + nmem - 1]; one contraction over their active starts side by side
+struct GPool {
+  int first, nmem;
+  int *count;                   // active starts of all its members (device, per sweep)
+  int *colmap;                  // Y row -> V row (vbase + start) of each active start
+};
+// per sweep, before the y-step: the pools' Y row offsets, active counts and column maps from the
+// members' active lists of that parity (one CTA per pool)
+cudaError_t launch_g_pools(const GPool *pools, int npool, const GProb *P, const int *members, int parity,
+                           cudaStream_t st);
 // the phases of a sweep for every problem of a group, one launch each (prob[g] = the problem of
 // global start g, R starts in all)
 cudaError_t launch_g_start_init(const GProb *P, const int *prob, int R, cudaStream_t st);
@@ -424,7 +441,10 @@ cudaError_t launch_g_ctrl(const GProb *P, int np, int parity, int clear, int *ou
 cudaError_t launch_g_xplanes(const GProb *P, const int *prob, int R, cudaStream_t st);
 cudaError_t launch_g_gather(const GProb *P, const int *prob, int R, int max_n, cudaStream_t st);
 cudaError_t launch_g_ystep(const GProb *P, const int *prob, int R, cudaStream_t st);
-cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p, int parity, int sms, cudaStream_t st);
+// (max_p_small: the longest v that fits in shared memory, 0 if none; any_large: some v does not)
+cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p_small, bool any_large, int parity,
+                           int sms, cudaStream_t st);
+constexpr int kXstepSmemMaxP = 200 * 1024 / 4;   // the longest v the x-step stages in shared memory
 
 // Grouped contraction: one persistent launch over the tiles of many contractions (one per problem
 // of a group), each described by a task in device memory, its tiles listed in tile_list (task,
@@ -435,7 +455,7 @@ cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p, in
 constexpr int kGroupMaxTasks = 1024;
 struct GTask {
   const CUtensorMap *pmap, *qmap;
-  int M, kblocks, nmax, nb;     // output rows, K-blocks (of 64), column bound, Q planes loaded
+  int M, kblocks, nmax, na, nb; // output rows, K-blocks (of 64), column bound, P and Q planes loaded
   const int *n_dev;             // active columns (device; <= nmax), or null for nmax
   const int *col_map;           // output row of column c (null = c)
   float *out;
@@ -521,6 +541,10 @@ cudaError_t launch_finalise(int form, const float *AT, int64_t ldat, int n, int 
                             int64_t ldX, StartState s, int r, float *U, int64_t ldu,
                             const int *sup_idx, const float *sup_val, int cap, double *partials,
                             cudaStream_t st);
+// the same on a 16-bit copy of A^T: FP16 rows (ldat apart) times their power-of-two inverse scale
+cudaError_t launch_finalise_h(int form, const __half *AT16, const float *at_inv, int64_t ldat, int n, StartState s,
+                              int r, float *U, int64_t ldu, const int *sup_idx, const float *sup_val, int cap,
+                              double *partials, cudaStream_t st);
 // argmax over starts (ties: lower index), then y(x) and the support of the best start
 cudaError_t launch_best(int form, int use_ev, StartState s, int r, int *best, cudaStream_t st);
 cudaError_t launch_best_outputs(int form, const int *best, const float *U, int64_t ldu, int n,

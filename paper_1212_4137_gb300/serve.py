@@ -235,11 +235,13 @@ class Server:
         st = torch.cuda.Stream()
         return st, st.cuda_stream
 
-    def register(self, name: str, A, stream: int = 0) -> None:
-        """Copy a matrix to the device (dense array or tensor, or a sparse matrix / CSR tuple)."""
+    def register(self, name: str, A, stream: int = 0, **handle_kwargs) -> None:
+        """Copy a matrix to the device (dense array or tensor, or a sparse matrix / CSR tuple);
+        handle_kwargs go to the handle factory (e.g. storage=spca.SPCA_FP16_RESIDENT: the matrix
+        kept only in 16 bits)."""
         if name in self._base:
             raise ValueError(f"matrix {name!r} is already registered")
-        h = self._handle_factory(A, stream=stream)
+        h = self._handle_factory(A, stream=stream, **handle_kwargs)
         self._base[name] = h
         self._shape[name] = (h.n, h.p)
         self._sparse[name] = isinstance(A, tuple) and len(A) == 4 or hasattr(A, "indptr") or hasattr(A, "tocsr")

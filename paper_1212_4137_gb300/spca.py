@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libspca.so")
 
 SPCA_OK, SPCA_E_INVALID, SPCA_E_NOMEM, SPCA_E_CUDA, SPCA_E_TIMEOUT, SPCA_E_BUSY, SPCA_E_UNSUPPORTED = range(7)
-SPCA_F32, SPCA_F64, SPCA_FP16, SPCA_FP8_E4M3_COLSCALED = range(4)
+SPCA_F32, SPCA_F64, SPCA_FP16, SPCA_FP8_E4M3_COLSCALED, SPCA_FP16_RESIDENT = range(5)
 SPCA_GAMMA_FIXED, SPCA_GAMMA_TARGET_NNZ = 0, 1
 SPCA_ST_MAXITER, SPCA_ST_CONVERGED, SPCA_ST_DEGENERATE = 0, 1, 2
 SPCA_ENGINE_AUTO, SPCA_ENGINE_SIMT, SPCA_ENGINE_TC, SPCA_ENGINE_TC_LOWP = 0, 1, 2, 3

@@ -147,3 +147,48 @@ def test_group_session_admits_while_others_run(lib):
     g.close()
     for h in handles:
         h.close()
+
+
+def test_group_pools_match_alone(lib, oracle):
+    """Members on one matrix share v = A^T y (a pool: their active starts side by side in one
+    operand, the matrix read once per sweep for all of them).  Each member's results are still its
+    results alone, bit for bit, whatever the other members' active counts put its starts at, and
+    members of another plane type (y = +-1) on the same matrix take their own pool."""
+    n, p = 900, 3100
+    A = I.spiked_matrix(n, p, I.spiked_thetas(n, p, (40.0, 30.0, 20.0)), 20, 6100, dtype=np.float32)
+    h = lib.Handle(A)
+    reqs = [(h, 1, 16, dict(seed=11, s=20.0, max_iter=30, tol=1e-7)),
+            (h, 3, 40, dict(seed=12, s=20.0, max_iter=50, tol=-1)),
+            (h, 2, 24, dict(seed=13, s=20.0, max_iter=40, tol=1e-7)),
+            (h, 5, 7, dict(seed=14, s=20.0, gamma_target=True, calib=6, max_iter=45, tol=1e-7)),
+            (h, 4, 70, dict(seed=15, s=20.0, max_iter=25, tol=1e-7))]
+    g = lib.Group()
+    alone = [g.solve([q], want_starts=True)[0] for q in reqs]
+    together = g.solve(reqs, want_starts=True)
+    for i, (a, t) in enumerate(zip(alone, together)):
+        assert np.array_equal(a["start_x"], t["start_x"]), i
+        assert np.array_equal(a["start_iters"], t["start_iters"]), i
+        assert a["objective"] == t["objective"], i
+    # and admitted at different times into a running session
+    done = {}
+    for wave in ([0, 2], [1], [3, 4]):
+        g.admit([reqs[i] for i in wave], wave, want_starts=True)
+        for tag, out in g.step(4):
+            done[tag] = out
+    while g.pending():
+        for tag, out in g.step(4):
+            done[tag] = out
+    for i, out in done.items():
+        assert np.array_equal(out["start_x"], alone[i]["start_x"]), i
+    g.close()
+    # the pooled solve against the oracle on one member
+    A64 = A.astype(np.float64)
+    G = I.raw_starts(p, 40, 12)   # not the seeded starts: a fresh solve with given starts
+    g = lib.Group()
+    outs = g.solve([(h, 3, 40, dict(x0=G.astype(np.float32), s=20.0, max_iter=30, tol=-1)),
+                    (h, 1, 16, dict(seed=11, s=20.0, max_iter=30, tol=1e-7))], want_starts=True)
+    g.close()
+    ref = oracle.solve(A64, 3, G.astype(np.float32).astype(np.float64), s=20.0, max_iter=30, tol=-1)
+    close = np.abs(outs[0]["start_objective"] - ref.f) <= OBJ_RTOL * np.maximum(1.0, np.abs(ref.f))
+    assert np.mean(close) >= 0.95
+    h.close()
