@@ -828,16 +828,20 @@ def run_scan_many(args, count=256, workers=8):
     g.close()
     for h in handles:
         h.close()
-    # the previous design: whole solves on clones from concurrent workers
-    with serve.Server(workers=workers, budget_bytes=64 << 30) as s:
-        for name, A, _, _, _ in probs:
-            s.register(name, A)
-        for name, _, form, kw, r in probs[:workers]:
-            s.submit(name, form, r, **kw).result()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        outs = [f.result() for f in [s.submit(name, form, r, **kw) for name, _, form, kw, r in probs]]
-        report(f"{workers} workers, whole solves overlapping", time.perf_counter() - t0, outs)
+    # the request loop: concurrent group sessions (a worker's session takes its share of the queue;
+    # the sessions' launches overlap on the device), and whole solves on clones from concurrent
+    # workers (the previous design)
+    for mode, label in (("group", f"{workers} group sessions overlapping (request loop)"),
+                        ("solve", f"{workers} workers, whole solves overlapping (request loop)")):
+        with serve.Server(workers=workers, budget_bytes=64 << 30, mode=mode) as s:
+            for name, A, _, _, _ in probs:
+                s.register(name, A)
+            for name, _, form, kw, r in probs[:workers]:
+                s.submit(name, form, r, **kw).result()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            outs = [f.result() for f in [s.submit(name, form, r, **kw) for name, _, form, kw, r in probs]]
+            report(label, time.perf_counter() - t0, outs)
 
 
 # The tuning of the grouped contraction's tile shape (tuning.py): for each bucket of start counts a
@@ -913,9 +917,9 @@ class _Kept:
 # request loop in group mode (`workers` group sessions, each admitting the waiting requests between
 # segments of 4 sweeps) and, beside it, whole solves on clones.  A closed loop (every request
 # queued at once) gives the capacity; then Poisson arrivals at 0.8 x capacity give the latency
-# (p50 / p99 from submission to result).
-def run_scan_serving(args, mats=32, closed=400, open_requests=2000, modes=(("group", 2), ("group", 4), ("solve", 8)),
-                     cap_gb=150):
+# (p50 / p99 from submission to result).  Both runs of every mode take the same 2000 requests.
+def run_scan_serving(args, mats=32, open_requests=2000,
+                     modes=(("group", 2, 1), ("group", 4, 4), ("group", 4, 2), ("solve", 8, 1)), cap_gb=150):
     import torch
 
     from paper_1212_4137_gb300 import build, inputs as I, serve, spca
@@ -942,46 +946,58 @@ def run_scan_serving(args, mats=32, closed=400, open_requests=2000, modes=(("gro
              "largest": list(shapes[0]), "storage": "SPCA_FP16_RESIDENT (leading FP16 planes of A and A^T)",
              "resident_gb": round(resident / 2**30, 1), "member_budget_gb": cap_gb,
              "device_generation_and_create_s": round(gen_s, 1)}
-    for mode, workers in modes:
+    # one request list for every mode and for both runs of a mode, so that the Poisson rate is
+    # 0.8 x the capacity measured on the same mix
+    rq = np.random.default_rng(55)
+
+    def request(i):
+        name = f"s{int(rq.integers(0, mats))}"
+        form = int(rq.integers(1, 9))
+        s = float(min(int(rq.integers(10, 201)), shapes[int(name[1:])][1]))
+        r = int(rq.choice([1, 16, 256]))
+        kw = dict(s=s, seed=8000 + i, max_iter=100, tol=1e-9)
+        if form >= 5:
+            kw.update(gamma_target=True, calib=10)
+        return name, form, r, kw
+
+    warm = [request(i) for i in range(32)]
+    reqs = [request(10000 + i) for i in range(open_requests)]
+    unit_gaps = np.random.default_rng(56).exponential(1.0, open_requests)   # scaled by 1 / rate
+    # size classes: thresholds on serve.request_cost that split the requests' total cost evenly
+    costs = np.sort([serve.request_cost(*shapes[int(nm[1:])], r) for nm, _, r, _ in reqs])
+    cum = np.cumsum(costs) / costs.sum()
+
+    def thresholds(k):
+        return [float(costs[np.searchsorted(cum, j / k)]) for j in range(1, k)]
+
+    for mode, workers, nclass in modes:
         head = dict(head0, workers=workers, mode="group sessions, 4 sweeps per segment" if mode == "group"
                       else "whole solves on clones")
-        rq = np.random.default_rng(55)   # the same requests and arrival times in every mode
-        with serve.Server(workers=workers, budget_bytes=budget, mode=mode,
-                          handle_factory=lambda A, stream=0, **kw: A) as srv:
+        if nclass > 1:
+            head["size_classes"] = f"{nclass} (equal shares of the requests' total cost, one group per worker)"
+        with serve.Server(workers=workers, budget_bytes=budget, mode=mode, classes=thresholds(nclass) if nclass > 1
+                          else None, handle_factory=lambda A, stream=0, **kw: A) as srv:
             for q, h in enumerate(kept):
                 srv.register(f"s{q}", h)
-
-            def request(i):
-                name = f"s{int(rq.integers(0, mats))}"
-                form = int(rq.integers(1, 9))
-                s = float(min(int(rq.integers(10, 201)), shapes[int(name[1:])][1]))
-                r = int(rq.choice([1, 16, 256]))
-                kw = dict(s=s, seed=8000 + i, max_iter=100, tol=1e-9)
-                if form >= 5:
-                    kw.update(gamma_target=True, calib=10)
-                return name, form, r, kw
-
-            for f in [srv.submit(*request(i)[:3], **request(i)[3]) for i in range(32)]:   # warm-up
+            for f in [srv.submit(nm, fm, r, **kw) for nm, fm, r, kw in warm]:
                 f.result()
             torch.cuda.synchronize()
-            reqs = [request(100 + i) for i in range(closed)]
             t0 = time.perf_counter()
-            outs = [f.result() for f in [srv.submit(nm, f, r, **kw) for nm, f, r, kw in reqs]]
+            outs = [f.result() for f in [srv.submit(nm, fm, r, **kw) for nm, fm, r, kw in reqs]]
             dt = time.perf_counter() - t0
-            capacity = closed / dt
-            print(json.dumps(dict(head, run="closed loop (capacity)", requests=closed, solves_per_s=round(capacity, 2),
+            capacity = len(reqs) / dt
+            print(json.dumps(dict(head, run="closed loop (capacity)", requests=len(reqs),
+                                  solves_per_s=round(capacity, 2),
                                   sweeps_starts_per_s=round(sum(o["sweeps_total"] for o in outs) / dt, 1))), flush=True)
             rate = 0.8 * capacity
-            reqs = [request(10000 + i) for i in range(open_requests)]
-            gaps = rq.exponential(1.0 / rate, open_requests)
             futs = []
             t0 = time.perf_counter()
             t_next = t0
-            for (nm, f, r, kw), g in zip(reqs, gaps):
-                t_next += g
+            for (nm, fm, r, kw), g in zip(reqs, unit_gaps):
+                t_next += g / rate
                 while time.perf_counter() < t_next:
                     time.sleep(min(0.001, max(0.0, t_next - time.perf_counter())))
-                futs.append(srv.submit(nm, f, r, **kw))
+                futs.append(srv.submit(nm, fm, r, **kw))
             t_last = time.perf_counter()
             outs = [f.result() for f in futs]
             dt = time.perf_counter() - t0
@@ -989,9 +1005,9 @@ def run_scan_serving(args, mats=32, closed=400, open_requests=2000, modes=(("gro
             by_r = {int(r): {"p50": round(float(np.percentile([o["latency_ms"] for o, q in zip(outs, reqs) if q[2] == r], 50)), 2),
                              "p99": round(float(np.percentile([o["latency_ms"] for o, q in zip(outs, reqs) if q[2] == r], 99)), 2)}
                     for r in (1, 16, 256) if any(q[2] == r for q in reqs)}
-            print(json.dumps(dict(head, run="Poisson arrivals at 0.8 x capacity", requests=open_requests,
+            print(json.dumps(dict(head, run="Poisson arrivals at 0.8 x capacity (the same requests)", requests=len(reqs),
                                   offered_per_s=round(rate, 2), arrivals_s=round(t_last - t0, 2),
-                                  solves_per_s=round(open_requests / dt, 2),
+                                  solves_per_s=round(len(reqs) / dt, 2),
                                   sweeps_starts_per_s=round(sum(o["sweeps_total"] for o in outs) / dt, 1),
                                   latency_ms={"p50": round(float(np.percentile(lat, 50)), 2),
                                               "p99": round(float(np.percentile(lat, 99)), 2)},

@@ -441,7 +441,12 @@ int spca_set_waits(spca_handle *h, int64_t wait_limit_us, int unpublished_parts)
  * launch over the tiles of all problems, the support gather, y-step, x-step (full pass) and
  * active lists as one launch each over all starts or problems.  Each problem's results do not
  * depend on the other problems of the group (the same bits alone and in any mix) and agree with
- * spca_solve's for it up to the order of rounding in the contractions.
+ * spca_solve's for it up to the order of rounding in the contractions.  The problems on one
+ * matrix (one handle and its clones) whose v = A^T y takes the same plane products share one
+ * contraction (a pool): their active starts side by side in one operand, so the matrix is read
+ * once per sweep for all of them; a start's sums do not depend on where the others put it.
+ * A resident 16-bit handle (SPCA_FP16_RESIDENT) runs every sweep of its problems on its leading
+ * planes, as spca_solve does.
  *
  * A group is also a session: problems can be admitted between segments of sweeps while others
  * run (spca_group_admit), and spca_group_step runs the next sweeps of every member, finalising
@@ -449,7 +454,8 @@ int spca_set_waits(spca_handle *h, int64_t wait_limit_us, int unpublished_parts)
  * boundaries.  Problem i of a call:
  *   h     a handle from spca_create (dense A) on a device with tensor cores, or a clone of one;
  *         read only (several problems and groups may use one handle at once).
- *   prm   as for spca_solve, with lowp_sweeps = 0, total_starts <= r, engine AUTO or TC,
+ *   prm   as for spca_solve, with lowp_sweeps = 0 (and, on a resident 16-bit handle,
+ *         lowp_first = refine_sweeps = 0), total_starts <= r, engine AUTO or TC,
  *         r in 1 .. 65535; timeout_us is not checked; the support gather serves every support
  *         after the first sweep.
  *   x0    r x p starts (host or device per prm.x0_is_device; copied at admission), or NULL for
@@ -463,8 +469,10 @@ int spca_set_waits(spca_handle *h, int64_t wait_limit_us, int unpublished_parts)
  *                      NULL is a no-op.
  * spca_group_last_error  static text for the group's last failure ("" if none).
  * spca_group_set_tiles the tile shape of the grouped contraction: tile_n (64 or 128 columns)
- *                      and stages (2..4 for 64, 2..3 for 128); NULL or {0, 0} = 64 x 4.
- *                      bench.py --tune measures the shapes per bucket of start counts.
+ *                      and stages (2..4 for 64, 2..3 for 128); NULL or {0, 0} = chosen when the
+ *                      tables are built, from the widest pool (the most starts that share one
+ *                      contraction): 64 x 4 up to 64 starts, 128 x 3 above, the shapes bench.py
+ *                      --tune measured best for those start counts.
  * spca_group_admit     admit `count` problems (tags[i] identifies problem i in the finished
  *                      lists; NULL = 0 .. count - 1); a member's device memory is allocated here
  *                      (stream-ordered).  On failure none of the call's problems is admitted.

@@ -1104,17 +1104,20 @@ cudaError_t launch_gemm_tc_f8(const PMaps &P, const CUtensorMap &Q, int M, int N
 // TMEM: NBUF = 512 / (4 BN) buffers of four accumulators (BN = 64: two buffers, so a tile's
 // epilogue overlaps the next tile's MMAs).  The hi x hi product of K-block kb goes to accumulator
 // kb mod 3 and the correction products to the fourth (FP32-class accuracy, see k_gemm_tc).
-template <int BN, int STAGES>
+// LOWP: every task takes the leading planes only (one P plane, one Q plane, one product: the
+// sweeps of resident 16-bit matrices, whose inputs carry 11 significant bits); one accumulator per
+// tile, so tiles up to 256 columns wide still get two TMEM buffers.
+template <int BN, int STAGES, bool LOWP>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_grouped(const GTask *__restrict__ tasks, const int2 *__restrict__ tile_list, int total_tiles, int *err,
                    uint64_t wait_ns) {
-  constexpr int NA = 2, NBMAX = 2;
+  constexpr int NA = LOWP ? 1 : 2, NBMAX = LOWP ? 1 : 2, NACC = LOWP ? 1 : 4;
   constexpr uint32_t A_BYTES = TC_BM * 64 * 2;            // 16 KB per P plane tile
   constexpr uint32_t B_BYTES = BN * 64 * 2;               // one Q plane tile (BN rows)
   constexpr uint32_t STAGE_BYTES = NA * A_BYTES + NBMAX * B_BYTES;
-  constexpr int NBUF = 512 / (4 * BN);
+  constexpr int NBUF = 512 / (NACC * BN);
   constexpr uint32_t TMEM_COLS = 512;
-  static_assert(NBUF >= 1, "TMEM");
+  static_assert(NBUF >= 1 && NBUF * NACC * BN <= (int)TMEM_COLS, "TMEM");
 
   extern __shared__ __align__(1024) uint8_t dsmem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar[NBUF], tmem_empty_bar[NBUF],
@@ -1216,7 +1219,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t dbase = tmem + (uint32_t)(b * 4 * BN);
+      const uint32_t dbase = tmem + (uint32_t)(b * NACC * BN);
       for (int kb = 0; kb < T.kblocks; ++kb, ++it) {
         const int s = (int)(it % STAGES);
         const uint32_t ph = (it / STAGES) & 1u;
@@ -1227,8 +1230,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t a_base = st + pairs.a[q] * A_BYTES;
           const uint32_t b_base = st + NA * A_BYTES + pairs.b[q] * B_BYTES;
           const bool main = (pairs.a[q] | pairs.b[q]) == 0;
-          const uint32_t d = dbase + (uint32_t)BN * (main ? (uint32_t)(kb % 3) : 3u);
-          const bool first = main ? (kb < 3 && q == pairs.first_main) : (kb == 0 && q == pairs.first_corr);
+          // a leading-planes task (one product) accumulates in one accumulator in either variant,
+          // so that its sums are the same whichever variant the group runs
+          const bool one = LOWP || pairs.n == 1;
+          const uint32_t d = one ? dbase : dbase + (uint32_t)BN * (main ? (uint32_t)(kb % 3) : 3u);
+          const bool first = one ? (kb == 0 && q == 0)
+                                 : main ? (kb < 3 && q == pairs.first_main) : (kb == 0 && q == pairs.first_corr);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             mma_bf16(d, sw_desc<64>(a_base + kk * 32), sw_desc<64>(b_base + kk * 32), idesc,
@@ -1258,10 +1265,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                           !abort_flag);
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int nused = T.kblocks < 3 ? T.kblocks : 3;
-      const bool corr = T.pairs.first_corr >= 0;
+      const int nused = LOWP || T.pairs.n == 1 ? 1 : T.kblocks < 3 ? T.kblocks : 3;
+      const bool corr = !LOWP && T.pairs.first_corr >= 0;
       const int row = m0 + row_l;
-      const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * 4 * BN);
+      const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * NACC * BN);
 #pragma unroll 1
       for (int cb = 0; cb < BN / 32; ++cb) {
         float v[32], w[32];
@@ -1311,13 +1318,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 namespace {
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool LOWP>
 cudaError_t launch_grouped_impl(const GTask *tasks, const int2 *tile_list, int total_tiles, int grid, int *err,
                                 uint64_t wait_ns, cudaStream_t st) {
-  constexpr int STAGE_BYTES = 2 * TC_BM * 64 * 2 + 2 * BN * 64 * 2;
+  constexpr int NP = LOWP ? 1 : 2;   // planes of each operand a stage holds
+  constexpr int STAGE_BYTES = NP * TC_BM * 64 * 2 + NP * BN * 64 * 2;
   constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
   static_assert(SMEM <= 227 * 1024, "shared memory");
-  auto kern = k_gemm_grouped<BN, STAGES>;
+  auto kern = k_gemm_grouped<BN, STAGES, LOWP>;
   static const cudaError_t configured = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
   if (configured != cudaSuccess) return configured;
   kern<<<grid, TC_THREADS, SMEM, st>>>(tasks, tile_list, total_tiles, err, wait_ns);
@@ -1325,21 +1333,33 @@ cudaError_t launch_grouped_impl(const GTask *tasks, const int2 *tile_list, int t
 }
 }  // namespace
 
-bool grouped_config_ok(int bn, int stages) {
+bool grouped_config_ok(int bn, int stages, bool lowp) {
+  if (lowp) return (bn == 64 || bn == 128 || bn == 256) && stages >= 2 && stages <= 4;
   return (bn == 64 && (stages == 2 || stages == 3 || stages == 4)) || (bn == 128 && (stages == 2 || stages == 3));
 }
 
-cudaError_t launch_gemm_grouped(const GTask *tasks, const int2 *tile_list, int total_tiles, int bn, int stages, int sms,
-                                int *err, uint64_t wait_ns, cudaStream_t st) {
+cudaError_t launch_gemm_grouped(const GTask *tasks, const int2 *tile_list, int total_tiles, int bn, int stages,
+                                bool lowp, int sms, int *err, uint64_t wait_ns, cudaStream_t st) {
   if (total_tiles < 1) return cudaSuccess;   // nothing to contract
   const int grid = total_tiles < sms ? total_tiles : sms;
-  if (bn == 64 && stages == 2) return launch_grouped_impl<64, 2>(tasks, tile_list, total_tiles, grid, err, wait_ns, st);
-  if (bn == 64 && stages == 3) return launch_grouped_impl<64, 3>(tasks, tile_list, total_tiles, grid, err, wait_ns, st);
-  if (bn == 64 && stages == 4) return launch_grouped_impl<64, 4>(tasks, tile_list, total_tiles, grid, err, wait_ns, st);
-  if (bn == 128 && stages == 2)
-    return launch_grouped_impl<128, 2>(tasks, tile_list, total_tiles, grid, err, wait_ns, st);
-  if (bn == 128 && stages == 3)
-    return launch_grouped_impl<128, 3>(tasks, tile_list, total_tiles, grid, err, wait_ns, st);
+#define SPCA_GROUPED(B, S, L) \
+  if (bn == B && stages == S && lowp == L) \
+    return launch_grouped_impl<B, S, L>(tasks, tile_list, total_tiles, grid, err, wait_ns, st);
+  SPCA_GROUPED(64, 2, false)
+  SPCA_GROUPED(64, 3, false)
+  SPCA_GROUPED(64, 4, false)
+  SPCA_GROUPED(128, 2, false)
+  SPCA_GROUPED(128, 3, false)
+  SPCA_GROUPED(64, 2, true)
+  SPCA_GROUPED(64, 3, true)
+  SPCA_GROUPED(64, 4, true)
+  SPCA_GROUPED(128, 2, true)
+  SPCA_GROUPED(128, 3, true)
+  SPCA_GROUPED(128, 4, true)
+  SPCA_GROUPED(256, 2, true)
+  SPCA_GROUPED(256, 3, true)
+  SPCA_GROUPED(256, 4, true)
+#undef SPCA_GROUPED
   return cudaErrorInvalidValue;
 }
 

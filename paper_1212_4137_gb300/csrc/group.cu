@@ -99,6 +99,8 @@ struct spca_group {
   int *h_err = nullptr;            // pinned: the device error word
   int *d_err = nullptr;
   int bn = 64, stages = 4;
+  bool tiles_auto = true;          // the shape follows the widest pool (spca_group_set_tiles)
+  bool lowp_all = false;           // every member is a resident 16-bit matrix's (leading planes only)
   std::vector<GroupGraph> graphs;
   // staging of finished members' results: device buffer, pinned host mirror, copy descriptors
   char *stage_d = nullptr, *stage_h = nullptr;
@@ -338,6 +340,20 @@ int build_tables(spca_group *g) {
     pools[q].mem.push_back(i);
   }
   const int npool = (int)pools.size();
+  bool lowp_all = true;
+  for (const PoolH &q : pools) lowp_all = lowp_all && q.type == 2;
+  g->lowp_all = lowp_all;
+  if (g->tiles_auto) {   // the measured choices by start count (bench.py --tune), on the widest pool
+    int widest = 0;
+    for (const PoolH &q : pools) widest = std::max(widest, q.R);
+    if (lowp_all) {   // one accumulator per tile: up to 256 columns, four stages
+      g->bn = widest > 128 ? 256 : widest > 64 ? 128 : 64;
+      g->stages = 4;
+    } else {
+      g->bn = widest > 64 ? 128 : 64;
+      g->stages = widest > 64 ? 3 : 4;
+    }
+  }
   // the pools' V rows and Y planes: one block, zeroed when it is made (the planes' padded columns
   // stay zero: the y-step writes the first n of a row), kept while the pools' shapes are the same
   Layout PL;
@@ -563,7 +579,8 @@ cudaError_t enqueue_sweep(spca_group *g, int64_t k, bool first_of_segment) {
     // the first sweep of the members admitted before this segment: the dense u = A x
     e = launch_g_xplanes(g->dP, g->d_start_prob, g->R, st);
     if (e == cudaSuccess)
-      e = launch_gemm_grouped(g->d_tasks, g->d_tiles[0], g->total_u, g->bn, g->stages, g->sms, g->d_err, wait_ns, st);
+      e = launch_gemm_grouped(g->d_tasks, g->d_tiles[0], g->total_u, g->bn, g->stages, g->lowp_all, g->sms, g->d_err,
+                              wait_ns, st);
   }
   // the pools' Y rows, counts and column maps for this sweep's active lists
   if (e == cudaSuccess) e = launch_g_pools(g->d_pools, g->npool, g->dP, g->d_pool_members, cur, st);
@@ -571,7 +588,7 @@ cudaError_t enqueue_sweep(spca_group *g, int64_t k, bool first_of_segment) {
   if (e == cudaSuccess) e = launch_g_ystep(g->dP, g->d_start_prob, g->R, st);
   if (e == cudaSuccess)
     e = launch_gemm_grouped(g->d_tasks + np + cur * g->npool, g->d_tiles[1 + cur], g->total_v, g->bn, g->stages,
-                            g->sms, g->d_err, wait_ns, st);
+                            g->lowp_all, g->sms, g->d_err, wait_ns, st);
   if (e == cudaSuccess) e = launch_g_ctrl(g->dP, np, nxt, 1, nullptr, st);
   if (e == cudaSuccess)
     e = launch_g_xstep(g->dP, g->d_start_prob, g->R, g->max_p_small, g->any_large_p, nxt, g->sms, st);
@@ -723,6 +740,7 @@ int run_segment(spca_group *g, int sweeps, bool capture, bool retire, int *finis
     key = fnv(key, &pend, sizeof pend);
     key = fnv(key, &sweeps, sizeof sweeps);
     key = fnv(key, &g->bn, sizeof g->bn);
+    key = fnv(key, &g->lowp_all, sizeof g->lowp_all);
     key = fnv(key, &g->stages, sizeof g->stages);
     GroupGraph *gg = nullptr;
     for (GroupGraph &q : g->graphs)
@@ -855,13 +873,15 @@ const char *spca_group_last_error(const spca_group *g) { return g ? g->last_erro
 
 int spca_group_set_tiles(spca_group *g, const spca_group_tiles *tiles) {
   if (!g) return SPCA_E_INVALID;
-  int bn = 64, stages = 4;
-  if (tiles && (tiles->tile_n || tiles->stages)) {
-    bn = tiles->tile_n;
-    stages = tiles->stages;
-    if (!grouped_config_ok(bn, stages)) return gfail(g, SPCA_E_INVALID, "unknown tile shape (tile_n, stages)");
+  if (!tiles || (!tiles->tile_n && !tiles->stages)) {   // chosen with the tables
+    if (!g->tiles_auto) g->tables_ok = false;
+    g->tiles_auto = true;
+    return SPCA_OK;
   }
-  if (bn != g->bn) g->tables_ok = false;   // the N tiles of the tasks change
+  const int bn = tiles->tile_n, stages = tiles->stages;
+  if (!grouped_config_ok(bn, stages, false)) return gfail(g, SPCA_E_INVALID, "unknown tile shape (tile_n, stages)");
+  if (bn != g->bn || g->tiles_auto) g->tables_ok = false;   // the N tiles of the tasks change
+  g->tiles_auto = false;
   g->bn = bn;
   g->stages = stages;
   return SPCA_OK;

@@ -465,9 +465,10 @@ struct GTask {
   TcPairs pairs;
   int mt, nt;                   // M and N tiles (N tiles of bn)
 };
-bool grouped_config_ok(int bn, int stages);
-cudaError_t launch_gemm_grouped(const GTask *tasks, const int2 *tile_list, int total_tiles, int bn, int stages, int sms,
-                                int *err, uint64_t wait_ns, cudaStream_t st);
+// lowp: every task takes the leading planes only (one accumulator per tile; tiles up to 256 wide)
+bool grouped_config_ok(int bn, int stages, bool lowp);
+cudaError_t launch_gemm_grouped(const GTask *tasks, const int2 *tile_list, int total_tiles, int bn, int stages,
+                                bool lowp, int sms, int *err, uint64_t wait_ns, cudaStream_t st);
 
 // FP16 planes (hi, lo; the first nplanes) of a scaled FP32 matrix, plane t at dst + t *
 // plane_stride elements: destination row r is source row row_map[r] (identity when null) times

@@ -27,6 +27,7 @@ result is the same alone and in the mix.
 """
 from __future__ import annotations
 
+import bisect
 import collections
 import concurrent.futures as cf
 import threading
@@ -53,6 +54,12 @@ def member_bytes(n: int, p: int, r: int) -> int:
     return int(r * per_start + 16 * (pp + pn) + 4096)
 
 
+def request_cost(n: int, p: int, r: int) -> float:
+    """A request's size for the size classes: the multiply-adds of one sweep's v = A^T y with the
+    starts padded by one 64-wide tile (a contraction over few starts still reads all of A)."""
+    return float(n) * float(p) * float(r + 64)
+
+
 def groupable(kwargs: dict, sparse: bool) -> bool:
     """Whether a group session takes the request (dense matrix, FP32 sweeps from r starts)."""
     return (not sparse and not kwargs.get("lowp_sweeps") and kwargs.get("total_starts", 0) <= 0
@@ -70,6 +77,7 @@ class Request:
     t_start: float = 0.0
     t_end: float = 0.0
     group_bytes: object = None   # a group member's bytes, or None for a whole solve
+    cls: int = 0                 # its size class (group mode with classes)
 
 
 class _Worker:
@@ -147,7 +155,7 @@ class _Worker:
         try:
             while True:
                 batch = s._take(block=not members, budget=s.worker_budget - held, have=len(members),
-                                max_members=s.max_members)
+                                max_members=s.max_members, cls=self.index % (len(s.classes) + 1))
                 if batch is None:
                     break
                 admit = []
@@ -198,15 +206,22 @@ class Server:
 
     def __init__(self, workers: int = 4, budget_bytes: int = 32 << 30, device: int = 0, handle_factory=None,
                  stream_factory=None, mode: str = "group", sweeps_per_step: int = 4, max_members: int = 1024,
-                 tiles=None, group_factory=None):
+                 tiles=None, group_factory=None, classes=None):
         """handle_factory(A, stream=...) makes a matrix's handle (spca.Handle); stream_factory() gives
         a worker (stream object, cudaStream_t as int) on the calling thread (a new CUDA stream on
         `device`); group_factory(stream) makes a worker's group session (spca.Group).  All three
         are replaceable for tests of the loop without a GPU.  mode: "group" (sessions, continuous
         batching at sweep boundaries) or "solve" (whole solves on clones).  tiles: the grouped
-        contraction's tile shape, (tile_n, stages) or None."""
+        contraction's tile shape, (tile_n, stages) or None.  classes: in group mode, ascending
+        thresholds on a request's size (request_cost: n p (r + 64)) that split the requests into
+        len(classes) + 1 classes; worker i serves class i mod (len(classes) + 1) only, so that a
+        small request sweeps beside other small ones (a group's sweep lasts as long as all its
+        members' work).  Needs at least that many workers."""
         if workers < 1:
             raise ValueError("workers must be >= 1")
+        self.classes = sorted(float(c) for c in (classes or ()))
+        if mode == "group" and len(self.classes) + 1 > workers:
+            raise ValueError("need at least one worker per size class")
         if mode not in ("group", "solve"):
             raise ValueError("mode must be 'group' or 'solve'")
         self.mode = mode
@@ -268,6 +283,7 @@ class Server:
                 raise RuntimeError("the server is closed")
             req = Request(name, form, r, dict(kwargs), fut)
             req.group_bytes = gb
+            req.cls = bisect.bisect_left(self.classes, request_cost(n, p, r)) if self.mode == "group" else 0
             self._queue.append(req)
             self._cv.notify()
         return fut
@@ -281,29 +297,38 @@ class Server:
             self._in_flight += 1
             return self._queue.popleft()
 
-    def _take(self, block: bool, budget: int, have: int, max_members: int):
-        """For a group worker: the waiting requests, in arrival order, that fit the worker's remaining
-        memory and member count (requests not for a group count nothing); blocks while the queue is
-        empty if `block`.  None when the server closes and the worker has nothing left."""
+    def _take(self, block: bool, budget: int, have: int, max_members: int, cls: int = 0):
+        """For a group worker of size class `cls`: the waiting requests of that class, in arrival
+        order, that fit the worker's remaining memory and member count (requests not for a group
+        count nothing); blocks while there are none if `block`.  None when the server closes and
+        the worker has nothing left."""
+        nclass = len(self.classes) + 1
+        mine = (lambda q: q.cls == cls) if nclass > 1 else (lambda q: True)
         with self._cv:
-            while block and not self._queue and not self._closing:
+            while block and not self._closing and not any(mine(q) for q in self._queue):
                 self._cv.wait()
-            if not self._queue:
+            waiting = [q for q in self._queue if mine(q)]
+            if not waiting:
                 return None if (self._closing and block) else []
+            # at most an even share of the class's queue per worker of the class, so that idle
+            # workers take the rest
+            peers = sum(1 for w in self._workers if w.index % nclass == cls)
+            share = max(1, -(-len(waiting) // peers))
             out = []
-            # at most an even share of the queue per worker, so that idle workers take the rest
-            share = max(1, -(-len(self._queue) // len(self._workers)))
-            while self._queue and len(out) < share:
-                req = self._queue[0]
+            for req in waiting:
+                if len(out) >= share:
+                    break
                 gb = req.group_bytes or 0
                 if req.group_bytes is not None and (gb > budget or have + 1 > max_members):
                     break
-                self._queue.popleft()
-                self._in_flight += 1
                 out.append(req)
+                self._in_flight += 1
                 if req.group_bytes is not None:
                     budget -= gb
                     have += 1
+            if out:
+                taken = set(map(id, out))
+                self._queue = collections.deque(q for q in self._queue if id(q) not in taken)
             return out
 
     def _done(self, req: Request) -> None:

@@ -152,12 +152,19 @@ def test_resident_in_groups(lib, spiked):
     pa = (ha, 2, 48, dict(x0=G[:48], s=20.0, max_iter=40, tol=-1))
     pb = (hb, 5, 32, dict(x0=GB, s=15.0, gamma_target=True, calib=6, max_iter=40, tol=-1))
     pc = (hc, 1, 32, dict(x0=GB, s=15.0, max_iter=40, tol=-1))
+    # a wide resident pool on another matrix: the group's tiles become 256 columns wide
+    D = I.spiked_matrix(400, 1500, I.spiked_thetas(400, 1500), 15, 915, dtype=np.float32)
+    hd = lib.Handle(D, storage=lib.SPCA_FP16_RESIDENT)
+    pd = (hd, 1, 300, dict(seed=5, s=15.0, max_iter=40, tol=-1))
     g = lib.Group()
     alone = g.solve([pa], want_starts=True)[0]
-    mix = g.solve([pb, pa, pc], want_starts=True)
+    mix = g.solve([pb, pa, pc], want_starts=True)      # resident and FP32 members together
+    wide = g.solve([pa, pd], want_starts=True)         # resident members only, 256-wide tiles
     g.close()
-    assert np.array_equal(alone["start_x"], mix[1]["start_x"])
-    assert alone["objective"] == mix[1]["objective"]
+    hd.close()
+    for other in (mix[1], wide[0]):
+        assert np.array_equal(alone["start_x"], other["start_x"])
+        assert alone["objective"] == other["objective"]
     # against solo solves on the same handles (another contraction kernel: rounding order differs)
     for (hh, form, r, kw), o in zip((pb, pa, pc), mix):
         solo = hh.solve(form, r, want_starts=True, **kw)

@@ -136,6 +136,7 @@ class FakeGroup:
 
     def admit(self, problems, tags):
         for (h, form, r, kw), tag in zip(problems, tags):
+            self.sizes = getattr(self, "sizes", set()) | {serve.request_cost(h.n, h.p, r)}
             self.members[tag] = [kw.get("steps", 1), {"form": form, "r": r, "shape": (h.n, h.p), **kw}]
             self.admitted_at[tag] = self.steps
         self.max_members = max(self.max_members, len(self.members))
@@ -213,3 +214,22 @@ def test_group_mode_failed_step_reaches_every_member():
                 f.result(timeout=10)
         FakeGroup.fail_at = None
         assert s.submit("a", 1, 4, steps=1, tag=7).result(timeout=10)["tag"] == 7   # the worker goes on
+
+
+def test_group_mode_size_classes():
+    """With size classes each worker's group takes the requests of its class only, so a small
+    request never sweeps beside a large one; every request is still served."""
+    big = serve.request_cost(3000, 9000, 256)
+    with _gserver(workers=2, budget_bytes=1 << 40, classes=[big / 2]) as s:
+        s.register("small", (100, 500))
+        s.register("large", (3000, 9000))
+        futs = [s.submit("small" if i % 3 else "large", 1, 8 if i % 3 else 256, steps=1 + i % 4, tag=i)
+                for i in range(30)]
+        outs = [f.result(timeout=10) for f in futs]
+        assert [o["tag"] for o in outs] == list(range(30))
+        used = [g for g in FakeGroup.instances if getattr(g, "sizes", None)]
+        assert len(used) == 2
+        for g in used:   # one class per group
+            assert all(c < big / 2 for c in g.sizes) or all(c >= big / 2 for c in g.sizes)
+    with pytest.raises(ValueError):
+        _gserver(workers=1, budget_bytes=1 << 30, classes=[1.0])
