@@ -94,6 +94,11 @@ struct spca_group {
   int npool = 0;
   char *pool_mem = nullptr;
   std::vector<int64_t> pool_sig;
+  // the candidate x-step's scratch (per start: kXstepCand values and indices, one int4), grown
+  // with the number of starts; used when some member's v is long enough (kCandMinP)
+  char *cand_mem = nullptr;
+  int cand_cap = 0;
+  bool use_cand = false;
   int *h_active = nullptr;         // pinned: active counts at a segment's end
   int h_active_cap = 0;
   int *h_err = nullptr;            // pinned: the device error word
@@ -298,9 +303,8 @@ int admit_one(spca_group *g, const spca_problem &q, int tag) {
   maps[1] = m.h->pmAT.m[0];
   GCK(make_plane_map(&maps[2], d.Xpl, m.r, m.ldX, 2, 64, 64));
   GCK(cudaMemcpyAsync(m.maps, maps, 3 * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
-  GCK(launch_start_init(d.x0, d.ld0, m.P.seed, m.r, m.p, d.X, m.ldX, s, d.gamma0, nullptr, nullptr, nullptr, st));
-  // the next sweep is k + 1: it reads the control words of parity k & 1
-  GCK(launch_active_list(s.status, nullptr, m.r, d.act, d.rank, d.ctrl[g->k & 1], st));
+  // the starts (seeded, or x0 normalised) and the first active list are set up at the start of the
+  // member's first sweep, in one launch each with every other member admitted for that sweep
   m.first_pending = true;
   g->members.push_back(m);
   g->tables_ok = false;
@@ -373,12 +377,36 @@ int build_tables(spca_group *g) {
     GCK(cudaMemsetAsync(g->pool_mem, 0, std::max<size_t>(PL.off, 256), st));
     g->pool_sig = sig;
   }
+  int R_all = 0;
+  bool use_cand = false;
+  for (const Member &m : g->members) {
+    R_all += m.r;
+    use_cand = use_cand || m.p >= kCandMinPGroup;
+  }
+  const size_t cand_row = sizeof(float) * kXstepCand + sizeof(int) * kXstepCand;
+  if (use_cand && R_all > g->cand_cap) {
+    const int cap = std::max(R_all, g->cand_cap + g->cand_cap / 2);
+    if (g->cand_mem) GCK(cudaFreeAsync(g->cand_mem, st));
+    g->cand_mem = nullptr;
+    g->cand_cap = 0;
+    GCK(cudaMallocFromPoolAsync((void **)&g->cand_mem, (cand_row + sizeof(int4)) * (size_t)cap, g->mempool, st));
+    g->cand_cap = cap;
+  }
+  g->use_cand = use_cand;
+  float *cand_val = use_cand ? reinterpret_cast<float *>(g->cand_mem) : nullptr;
+  int *cand_idx = use_cand ? reinterpret_cast<int *>(g->cand_mem + sizeof(float) * kXstepCand * (size_t)g->cand_cap)
+                           : nullptr;
+  int4 *cand_meta = use_cand ? reinterpret_cast<int4 *>(g->cand_mem + cand_row * (size_t)g->cand_cap) : nullptr;
   int R = 0, max_n = 1, max_p = 1, max_p_small = 0;
   bool any_large_p = false;
   for (int i = 0; i < np; ++i) {
     Member &m = g->members[i];
     const int q = pool_of[i];
+    m.d.cand_val = use_cand ? cand_val + (int64_t)R * kXstepCand : nullptr;
+    m.d.cand_idx = use_cand ? cand_idx + (int64_t)R * kXstepCand : nullptr;
+    m.d.meta = use_cand ? cand_meta + R : nullptr;
     m.d.start0 = R;
+    m.d.first = m.first_pending ? 1 : 0;
     m.d.vbase = vbase[i];
     m.d.V = reinterpret_cast<float *>(g->pool_mem + oV[q]) + (int64_t)vbase[i] * m.ldX;
     m.d.Ypl = reinterpret_cast<__half *>(g->pool_mem + oY[q]);
@@ -576,8 +604,11 @@ cudaError_t enqueue_sweep(spca_group *g, int64_t k, bool first_of_segment) {
   const uint64_t wait_ns = 2000000000ull;
   cudaError_t e = cudaSuccess;
   if (first_of_segment && g->n_u > 0) {
-    // the first sweep of the members admitted before this segment: the dense u = A x
-    e = launch_g_xplanes(g->dP, g->d_start_prob, g->R, st);
+    // the first sweep of the members admitted before this segment: their starts and active lists
+    // (parity cur: the control words this sweep reads), then the dense u = A x
+    e = launch_g_start_init(g->dP, g->d_start_prob, g->R, st);
+    if (e == cudaSuccess) e = launch_g_active(g->dP, np, cur, true, st);
+    if (e == cudaSuccess) e = launch_g_xplanes(g->dP, g->d_start_prob, g->R, st);
     if (e == cudaSuccess)
       e = launch_gemm_grouped(g->d_tasks, g->d_tiles[0], g->total_u, g->bn, g->stages, g->lowp_all, g->sms, g->d_err,
                               wait_ns, st);
@@ -591,8 +622,8 @@ cudaError_t enqueue_sweep(spca_group *g, int64_t k, bool first_of_segment) {
                             g->lowp_all, g->sms, g->d_err, wait_ns, st);
   if (e == cudaSuccess) e = launch_g_ctrl(g->dP, np, nxt, 1, nullptr, st);
   if (e == cudaSuccess)
-    e = launch_g_xstep(g->dP, g->d_start_prob, g->R, g->max_p_small, g->any_large_p, nxt, g->sms, st);
-  if (e == cudaSuccess) e = launch_g_active(g->dP, np, nxt, st);
+    e = launch_g_xstep(g->dP, g->d_start_prob, g->R, g->max_p_small, g->any_large_p, g->use_cand, nxt, g->sms, st);
+  if (e == cudaSuccess) e = launch_g_active(g->dP, np, nxt, false, st);
   return e;
 }
 
@@ -853,6 +884,7 @@ void spca_group_destroy(spca_group *g) {
   for (Member &m : g->members) release_member(g, m);
   g->members.clear();
   if (g->pool_mem && g->stream) cudaFreeAsync(g->pool_mem, g->stream);
+  if (g->cand_mem && g->stream) cudaFreeAsync(g->cand_mem, g->stream);
   if (g->stream) cudaStreamSynchronize(g->stream);
   for (GroupGraph &q : g->graphs)
     if (q.exec) cudaGraphExecDestroy(q.exec);

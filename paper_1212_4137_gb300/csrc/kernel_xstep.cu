@@ -697,6 +697,7 @@ constexpr float kGuess = 0.85f;
 constexpr float kGuessLo = 0.6f;
 constexpr float kSteady = 0.05f;         // |t_new / t - 1| below this: one guess next sweep
 constexpr int kCandMinP = 4096;          // shorter v: the full pass only
+static_assert(kCandMinP == kCandMinPGroup, "the group's candidate scratch follows the same rule");
 constexpr int kMetaHi = 1, kMetaLo = 2;  // meta[c].w: the list holds the entries above G_hi / G_lo
 
 // the candidate x-step's per-start prelude: the guesses (exact: G_hi = G_lo = the threshold
@@ -771,21 +772,29 @@ __device__ __forceinline__ int warp_compact_above(float *val, int *idx, int len,
 // A start the filter cannot serve gets xfast[c] = 0 and meta[c].w = 0.
 constexpr int kFilterChunks = 4;      // 128-entry chunks per warp and step, loaded before use
 constexpr int kFilterMinBlocks = 2;   // resident CTAs per SM the register budget is set for
-__global__ void __launch_bounds__(XT, kFilterMinBlocks) k_xstep_filter(XstepArgs a_in, const float *__restrict__ V, int64_t ldv,
-                                                     float *__restrict__ X, int64_t ldx, StartState st,
-                                                     const int *__restrict__ sup_idx, float *__restrict__ cand_val,
-                                                     int *__restrict__ cand_idx, int4 *__restrict__ meta) {
-  __shared__ XShared sh;
-  __shared__ float wval_s[kCand];
-  __shared__ int widx_s[kCand];
-  __shared__ int fail_s, raised_s;
-  const int c = blockIdx.x;
+// shared memory of the filter (one CTA per start)
+struct FilterShared {
+  XShared sh;
+  float wval_s[kCand];
+  int widx_s[kCand];
+  int fail_s, raised_s;
+};
+// start c: its candidates go to gv / gi (kCand each) and its counts to *meta_c
+__device__ __forceinline__ void xstep_filter_one(const XstepArgs &a_in, int c, const float *__restrict__ V,
+                                                 int64_t ldv, float *__restrict__ X, int64_t ldx,
+                                                 const StartState &st, const int *__restrict__ sup_idx,
+                                                 float *__restrict__ gv, int *__restrict__ gi, int4 *meta_c,
+                                                 FilterShared &fs) {
+  XShared &sh = fs.sh;
+  float *wval_s = fs.wval_s;
+  int *widx_s = fs.widx_s;
+  int &fail_s = fs.fail_s, &raised_s = fs.raised_s;
   if (st.status[c] != ST_ACTIVE) return;
   const CandPlan q = cand_plan(a_in, st, c, sup_idx != nullptr);
   if (!q.usable) {
     if (threadIdx.x == 0) {
       st.xfast[c] = 0;
-      meta[c].w = 0;
+      meta_c->w = 0;
     }
     return;
   }
@@ -879,7 +888,7 @@ __global__ void __launch_bounds__(XT, kFilterMinBlocks) k_xstep_filter(XstepArgs
   if (fail_s) {
     if (threadIdx.x == 0) {
       st.xfast[c] = 0;
-      meta[c].w = 0;
+      meta_c->w = 0;
     }
     return;
   }
@@ -888,8 +897,6 @@ __global__ void __launch_bounds__(XT, kFilterMinBlocks) k_xstep_filter(XstepArgs
   if (at_hi && Gk != Ghi) wc = warp_compact_above(wv, wi, wc, Ghi);   // every warp on one guess
   const int ncand = warp_offsets(lane == 0 ? wc : 0, sh);
   const int off = sh.woff[w];
-  float *gv = cand_val + (int64_t)c * kCand;
-  int *gi = cand_idx + (int64_t)c * kCand;
   for (int t = lane; t < wc; t += 32) {
     gv[off + t] = wv[t];
     gi[off + t] = wi[t];
@@ -898,37 +905,42 @@ __global__ void __launch_bounds__(XT, kFilterMinBlocks) k_xstep_filter(XstepArgs
   const int *old = sup_idx + (int64_t)c * q.a.cap;
   for (int t = threadIdx.x; t < nnz_old; t += XT) x[old[t]] = 0.0f;
   if (threadIdx.x == 0)
-    meta[c] = make_int4(ncand, __float_as_int(f1), __float_as_int(f2), at_hi ? kMetaHi : kMetaLo);
+    *meta_c = make_int4(ncand, __float_as_int(f1), __float_as_int(f2), at_hi ? kMetaHi : kMetaLo);
+}
+
+__global__ void __launch_bounds__(XT, kFilterMinBlocks) k_xstep_filter(XstepArgs a_in, const float *__restrict__ V, int64_t ldv,
+                                                     float *__restrict__ X, int64_t ldx, StartState st,
+                                                     const int *__restrict__ sup_idx, float *__restrict__ cand_val,
+                                                     int *__restrict__ cand_idx, int4 *__restrict__ meta) {
+  __shared__ FilterShared fs;
+  const int c = blockIdx.x;
+  xstep_filter_one(a_in, c, V, ldv, X, ldx, st, sup_idx, cand_val + (int64_t)c * kCand, cand_idx + (int64_t)c * kCand,
+                   meta + c, fs);
 }
 
 // Operator: a warp per start on the filter's candidates (staged in the warp's shared memory).
 // A list above G_lo is first cut to the entries above G_hi when G_hi is valid; then the operator,
 // with the check that the guess lies below the operator's threshold, the new x, F and support.
 constexpr int kOpWarps = 4;
-__global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int r, float *__restrict__ X,
-                                                            int64_t ldx, StartState st, int *__restrict__ sup_idx,
-                                                            float *__restrict__ sup_val,
-                                                            const float *__restrict__ cand_val,
-                                                            const int *__restrict__ cand_idx,
-                                                            const int4 *__restrict__ meta, Ctrl *ctrl) {
-  __shared__ float cval_s[kOpWarps][kCand];
-  __shared__ int cidx_s[kOpWarps][kCand];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x * kOpWarps + w;
-  if (c >= r) return;
+// start c on one warp: its candidates at gv / gi, its counts at *meta_c; cval / cidx: the warp's
+// shared memory (kCand each)
+__device__ __forceinline__ void xstep_op_one(const XstepArgs &a_in, int c, float *__restrict__ X, int64_t ldx,
+                                             const StartState &st, int *__restrict__ sup_idx,
+                                             float *__restrict__ sup_val, const float *__restrict__ gv,
+                                             const int *__restrict__ gi, const int4 *meta_c, Ctrl *ctrl, float *cval,
+                                             int *cidx) {
+  const int lane = threadIdx.x & 31;
   if (st.status[c] != ST_ACTIVE) return;
-  const int4 m = meta[c];
+  const int4 m = *meta_c;
   if (m.w == 0) return;
   const CandPlan q = cand_plan(a_in, st, c, true);
   const XstepArgs &a = q.a;
   const int form = a.form, s_int = q.s_int;
   int ncand = m.x;
   const float f1 = __int_as_float(m.y), f2 = __int_as_float(m.z);
-  float *cval = cval_s[w];
-  int *cidx = cidx_s[w];
   for (int t = lane; t < ncand; t += 32) {
-    cval[t] = cand_val[(int64_t)c * kCand + t];
-    cidx[t] = cand_idx[(int64_t)c * kCand + t];
+    cval[t] = gv[t];
+    cidx[t] = gi[t];
   }
   __syncwarp();
   // phi(G) < 0 over the candidates above G (all of v's entries above G when the list holds them)
@@ -1023,6 +1035,21 @@ __global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int 
     st.xfast[c] = G == q.G && steady ? 1 : 2;
   }
 }
+
+__global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int r, float *__restrict__ X,
+                                                            int64_t ldx, StartState st, int *__restrict__ sup_idx,
+                                                            float *__restrict__ sup_val,
+                                                            const float *__restrict__ cand_val,
+                                                            const int *__restrict__ cand_idx,
+                                                            const int4 *__restrict__ meta, Ctrl *ctrl) {
+  __shared__ float cval_s[kOpWarps][kCand];
+  __shared__ int cidx_s[kOpWarps][kCand];
+  const int w = threadIdx.x >> 5;
+  const int c = blockIdx.x * kOpWarps + w;
+  if (c >= r) return;
+  xstep_op_one(a_in, c, X, ldx, st, sup_idx, sup_val, cand_val + (int64_t)c * kCand, cand_idx + (int64_t)c * kCand,
+               meta + c, ctrl, cval_s[w], cidx_s[w]);
+}
 }  // namespace
 
 // groups of problems: the full pass for every active start of every problem, persistent CTAs over
@@ -1030,7 +1057,7 @@ __global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int 
 // there), the other launch the rest
 template <bool kSmem>
 __global__ void __launch_bounds__(XT) k_g_xstep(const GProb *__restrict__ P, const int *__restrict__ prob, int R,
-                                                int parity) {
+                                                int parity, int cand) {
   extern __shared__ float vsm[];
   __shared__ XShared sh;
   for (int g = blockIdx.x; g < R; g += gridDim.x) {
@@ -1039,6 +1066,7 @@ __global__ void __launch_bounds__(XT) k_g_xstep(const GProb *__restrict__ P, con
     const int c = g - q.start0;
     StartState st = q.st;
     if (st.status[c] != ST_ACTIVE) continue;
+    if (cand && st.xfast[c]) continue;   // the candidate kernels finished it this sweep
     st.xfast = nullptr;
     xstep_full_one(q.xa, c, q.V, q.ldX, q.X, q.ldX, st, q.sup_idx, q.sup_val, q.ctrl[parity], kSmem ? vsm : nullptr,
                    sh);
@@ -1046,8 +1074,49 @@ __global__ void __launch_bounds__(XT) k_g_xstep(const GProb *__restrict__ P, con
   }
 }
 
-cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p_small, bool any_large, int parity,
-                           int sms, cudaStream_t st) {
+// groups of problems: the candidate kernels for every active start of every problem, as in
+// launch_xstep (a CTA per global start for the filter, a warp per global start for the operator);
+// a problem whose v is shorter than kCandMinP is left to the full pass (xfast = 0)
+__global__ void __launch_bounds__(XT, kFilterMinBlocks) k_g_xstep_filter(const GProb *__restrict__ P,
+                                                                         const int *__restrict__ prob) {
+  __shared__ FilterShared fs;
+  const GProb &q = P[prob[blockIdx.x]];
+  const int c = (int)blockIdx.x - q.start0;
+  if (q.p < kCandMinP) {
+    if (threadIdx.x == 0 && q.st.status[c] == ST_ACTIVE) {
+      q.st.xfast[c] = 0;
+      q.meta[c].w = 0;
+    }
+    return;
+  }
+  xstep_filter_one(q.xa, c, q.V, q.ldX, q.X, q.ldX, q.st, q.sup_idx, q.cand_val + (int64_t)c * kCand,
+                   q.cand_idx + (int64_t)c * kCand, q.meta + c, fs);
+}
+
+__global__ void __launch_bounds__(32 * kOpWarps) k_g_xstep_op(const GProb *__restrict__ P, const int *__restrict__ prob,
+                                                              int R, int parity) {
+  __shared__ float cval_s[kOpWarps][kCand];
+  __shared__ int cidx_s[kOpWarps][kCand];
+  const int w = threadIdx.x >> 5;
+  const int g = blockIdx.x * kOpWarps + w;
+  if (g >= R) return;
+  const GProb &q = P[prob[g]];
+  if (q.p < kCandMinP) return;
+  const int c = g - q.start0;
+  xstep_op_one(q.xa, c, q.X, q.ldX, q.st, q.sup_idx, q.sup_val, q.cand_val + (int64_t)c * kCand,
+               q.cand_idx + (int64_t)c * kCand, q.meta + c, q.ctrl[parity], cval_s[w], cidx_s[w]);
+}
+
+cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p_small, bool any_large, bool cand,
+                           int parity, int sms, cudaStream_t st) {
+  if (cand) {
+    k_g_xstep_filter<<<R, XT, 0, st>>>(P, prob);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_g_xstep_op<<<(R + kOpWarps - 1) / kOpWarps, 32 * kOpWarps, 0, st>>>(P, prob, R, parity);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (max_p_small > 0) {   // the problems whose v fits in shared memory: staged there
     const size_t bytes = (size_t)max_p_small * sizeof(float);
     if (bytes > (size_t)XSTEP_SMEM_MAX) return cudaErrorInvalidValue;
@@ -1055,12 +1124,12 @@ cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p_sma
         cudaFuncSetAttribute(k_g_xstep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, XSTEP_SMEM_MAX);
     if (configured != cudaSuccess) return configured;
     const int per_sm = bytes <= 100u * 1024u ? 2 : 1;
-    k_g_xstep<true><<<min(R, per_sm * sms), XT, bytes, st>>>(P, prob, R, parity);
+    k_g_xstep<true><<<min(R, per_sm * sms), XT, bytes, st>>>(P, prob, R, parity, cand ? 1 : 0);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (any_large) {
-    k_g_xstep<false><<<min(R, 2 * sms), XT, 0, st>>>(P, prob, R, parity);
+    k_g_xstep<false><<<min(R, 2 * sms), XT, 0, st>>>(P, prob, R, parity, cand ? 1 : 0);
     return cudaGetLastError();
   }
   return cudaSuccess;

@@ -762,6 +762,7 @@ cudaError_t launch_gemm1_sparse(const float *AT, int64_t ldat, int n, const int 
 __global__ void __launch_bounds__(256) k_g_start_init(const GProb *__restrict__ P, const int *__restrict__ prob) {
   __shared__ float redf[32];
   const GProb &q = P[prob[blockIdx.x]];
+  if (!q.first) return;   // only the members whose first sweep is next
   const int c = (int)blockIdx.x - q.start0;
   start_init_body(q.x0, q.ld0, q.key, q.p, q.X, q.ldX, q.st, q.gamma0, c, c, redf);
 }
@@ -771,13 +772,14 @@ cudaError_t launch_g_start_init(const GProb *P, const int *prob, int R, cudaStre
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(1024) k_g_active(const GProb *__restrict__ P, int parity) {
+__global__ void __launch_bounds__(1024) k_g_active(const GProb *__restrict__ P, int parity, int only_first) {
   const GProb &q = P[blockIdx.x];
+  if (only_first && !q.first) return;
   active_list_body(q.st.status, q.st.nnz, q.r, q.act, q.rank, q.ctrl[parity]);
 }
 
-cudaError_t launch_g_active(const GProb *P, int np, int parity, cudaStream_t st) {
-  k_g_active<<<np, 1024, 0, st>>>(P, parity);
+cudaError_t launch_g_active(const GProb *P, int np, int parity, bool only_first, cudaStream_t st) {
+  k_g_active<<<np, 1024, 0, st>>>(P, parity, only_first ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -399,6 +399,12 @@ struct GProb {
   // are V's rows vbase .. vbase + r - 1, and its active starts the Y planes' rows from *yoff on
   int vbase;
   int *yoff;
+  int first;                    // its first sweep is the next one (its starts are set up then)
+  // the candidate x-step's scratch of the member's starts (kXstepCand values and indices, one
+  // int4 of counts per start), or null
+  float *cand_val;
+  int *cand_idx;
+  int4 *meta;
   float *X, *V, *U;             // r x ldX, r x ldX, r x ldU
   __half *Xpl, *Ypl;            // two FP16 planes each (x row-scaled, y scaled by kQScale), packed rows
   int64_t xps, yps;             // plane strides (elements)
@@ -427,8 +433,9 @@ cudaError_t launch_g_pools(const GPool *pools, int npool, const GProb *P, const 
                            cudaStream_t st);
 // the phases of a sweep for every problem of a group, one launch each (prob[g] = the problem of
 // global start g, R starts in all)
+// (the start initialisation runs for the members whose first sweep is next, GProb.first)
 cudaError_t launch_g_start_init(const GProb *P, const int *prob, int R, cudaStream_t st);
-cudaError_t launch_g_active(const GProb *P, int np, int parity, cudaStream_t st);
+cudaError_t launch_g_active(const GProb *P, int np, int parity, bool only_first, cudaStream_t st);
 // many small device-to-device copies in one launch
 struct CopyDesc {
   const void *src;
@@ -441,10 +448,12 @@ cudaError_t launch_g_ctrl(const GProb *P, int np, int parity, int clear, int *ou
 cudaError_t launch_g_xplanes(const GProb *P, const int *prob, int R, cudaStream_t st);
 cudaError_t launch_g_gather(const GProb *P, const int *prob, int R, int max_n, cudaStream_t st);
 cudaError_t launch_g_ystep(const GProb *P, const int *prob, int R, cudaStream_t st);
-// (max_p_small: the longest v that fits in shared memory, 0 if none; any_large: some v does not)
-cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p_small, bool any_large, int parity,
-                           int sms, cudaStream_t st);
+// (max_p_small: the longest v that fits in shared memory, 0 if none; any_large: some v does not;
+// cand: the candidate kernels first, with the problems' scratch (GProb.cand_val ...))
+cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p_small, bool any_large, bool cand,
+                           int parity, int sms, cudaStream_t st);
 constexpr int kXstepSmemMaxP = 200 * 1024 / 4;   // the longest v the x-step stages in shared memory
+constexpr int kCandMinPGroup = 4096;             // shorter v: the grouped x-step's full pass only
 
 // Grouped contraction: one persistent launch over the tiles of many contractions (one per problem
 // of a group), each described by a task in device memory, its tiles listed in tile_list (task,

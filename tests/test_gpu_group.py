@@ -192,3 +192,23 @@ def test_group_pools_match_alone(lib, oracle):
     close = np.abs(outs[0]["start_objective"] - ref.f) <= OBJ_RTOL * np.maximum(1.0, np.abs(ref.f))
     assert np.mean(close) >= 0.95
     h.close()
+
+
+def test_group_seeded_starts_are_the_solo_starts(lib):
+    """A group sets up its members' starts in its own launch (in their first sweep): seeded starts
+    are the ones spca_solve draws for the same seed, and given starts are normalised the same way,
+    so after one sweep each start's x agrees with the solo solve's to the contraction's rounding."""
+    probs = _draw(4, 7)
+    r = 24
+    handles = [lib.Handle(A) for A, _, _ in probs]
+    g = lib.Group()
+    req = [(h, form, r, dict(kw, seed=900 + i, max_iter=1, tol=-1)) for i, (h, (A, form, kw)) in
+           enumerate(zip(handles, probs))]
+    outs = g.solve(req, want_starts=True)
+    g.close()
+    for (h, form, r_, kw), o in zip(req, outs):
+        solo = h.solve(form, r_, want_starts=True, engine=lib.SPCA_ENGINE_TC, **kw)
+        dx = np.abs(o["start_x"] - solo["start_x"]).max(axis=1)
+        assert np.mean(dx <= 1e-4) >= 0.95, (form, dx.max())
+    for h in handles:
+        h.close()
