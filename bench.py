@@ -822,8 +822,11 @@ def run_scan_many(args, count=256, workers=8):
         dt = time.perf_counter() - t0
         best = dt if best is None or dt < best else best
     rel = [abs(a["objective"] - b["objective"]) / max(1.0, abs(b["objective"])) for a, b in zip(grouped, solo)]
+    # signed: the grouped best objective above (a better stationary point) or below the solo one
+    sgn = [(a["objective"] - b["objective"]) / max(1.0, abs(b["objective"])) for a, b in zip(grouped, solo)]
     report(f"one grouped solve (tiles {shape[0]} x {shape[1]} stages)", best, grouped,
            {"max_rel_objective_diff_vs_one_after_another": float(max(rel)),
+            "largest_rel_gain": float(max(sgn)), "largest_rel_shortfall": float(-min(sgn)),
             "problems_within_1e-5": int(sum(x <= 1e-5 for x in rel))})
     g.close()
     for h in handles:
