@@ -14,10 +14,12 @@
 // (support compaction, ranking of tied magnitudes) needs only warp ballots plus one scan over
 // the 16 warps.  Reductions are in a fixed order: a start's result does not depend on the
 // other starts or on scheduling.
+#include <algorithm>
 #include <cstdint>
 
 #include "block_util.cuh"
 #include "spca_internal.cuh"
+#include "sweep_bodies.cuh"
 
 namespace spca {
 
@@ -697,7 +699,7 @@ constexpr float kGuess = 0.85f;
 constexpr float kGuessLo = 0.6f;
 constexpr float kSteady = 0.05f;         // |t_new / t - 1| below this: one guess next sweep
 constexpr int kCandMinP = 4096;          // shorter v: the full pass only
-static_assert(kCandMinP == kCandMinPGroup, "the group's candidate scratch follows the same rule");
+static_assert(kCandMinPGroup <= kCandMinP, "the group's candidate threshold");
 constexpr int kMetaHi = 1, kMetaLo = 2;  // meta[c].w: the list holds the entries above G_hi / G_lo
 
 // the candidate x-step's per-start prelude: the guesses (exact: G_hi = G_lo = the threshold
@@ -1056,8 +1058,8 @@ __global__ void __launch_bounds__(32 * kOpWarps) k_xstep_op(XstepArgs a_in, int 
 // the global starts; the kSmem launch takes the problems whose v fits in shared memory (staged
 // there), the other launch the rest
 template <bool kSmem>
-__global__ void __launch_bounds__(XT) k_g_xstep(const GProb *__restrict__ P, const int *__restrict__ prob, int R,
-                                                int parity, int cand) {
+__global__ void __launch_bounds__(XT, 2) k_g_xstep(const GProb *__restrict__ P, const int *__restrict__ prob, int R,
+                                                   int parity, int cand) {
   extern __shared__ float vsm[];
   __shared__ XShared sh;
   for (int g = blockIdx.x; g < R; g += gridDim.x) {
@@ -1076,13 +1078,15 @@ __global__ void __launch_bounds__(XT) k_g_xstep(const GProb *__restrict__ P, con
 
 // groups of problems: the candidate kernels for every active start of every problem, as in
 // launch_xstep (a CTA per global start for the filter, a warp per global start for the operator);
-// a problem whose v is shorter than kCandMinP is left to the full pass (xfast = 0)
+// a problem whose v is shorter than kCandMinPGroup is left to the full pass (xfast = 0).  The
+// threshold is lower than a single problem's kCandMinP: a group's launches are shared by all its
+// starts, so the filter and operator cost no launches of their own per problem.
 __global__ void __launch_bounds__(XT, kFilterMinBlocks) k_g_xstep_filter(const GProb *__restrict__ P,
                                                                          const int *__restrict__ prob) {
   __shared__ FilterShared fs;
   const GProb &q = P[prob[blockIdx.x]];
   const int c = (int)blockIdx.x - q.start0;
-  if (q.p < kCandMinP) {
+  if (q.p < kCandMinPGroup) {
     if (threadIdx.x == 0 && q.st.status[c] == ST_ACTIVE) {
       q.st.xfast[c] = 0;
       q.meta[c].w = 0;
@@ -1101,7 +1105,7 @@ __global__ void __launch_bounds__(32 * kOpWarps) k_g_xstep_op(const GProb *__res
   const int g = blockIdx.x * kOpWarps + w;
   if (g >= R) return;
   const GProb &q = P[prob[g]];
-  if (q.p < kCandMinP) return;
+  if (q.p < kCandMinPGroup) return;
   const int c = g - q.start0;
   xstep_op_one(q.xa, c, q.X, q.ldX, q.st, q.sup_idx, q.sup_val, q.cand_val + (int64_t)c * kCand,
                q.cand_idx + (int64_t)c * kCand, q.meta + c, q.ctrl[parity], cval_s[w], cidx_s[w]);
@@ -1133,6 +1137,76 @@ cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p_sma
     return cudaGetLastError();
   }
   return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- small problems in one launch
+// For a small matrix the chain of launches of a sweep, not its work, sets the time.  Here every
+// sweep of a start runs in one CTA, all starts at once (a CTA per start): u = A x as a warp per
+// row of A, v = A^T y as a thread per column of A (both on the CUDA cores, sums in a fixed order;
+// A stays in L2 across the sweeps), then the y-step and the full-pass x-step of the
+// single-problem path, until the start stops or `sweeps` sweeps have run.  x and y are staged in
+// shared memory; v too, for the x-step.
+__global__ void __launch_bounds__(XT) k_small_sweeps(XstepArgs xa, const float *__restrict__ A, int64_t lda, int n,
+                                                     int p, float *__restrict__ X, int64_t ldx, float *__restrict__ U,
+                                                     float *__restrict__ Y, int64_t ldu, float *__restrict__ V,
+                                                     StartState st, int *__restrict__ sup_idx,
+                                                     float *__restrict__ sup_val, int sweeps) {
+  extern __shared__ float4 sm4[];
+  float *sm = reinterpret_cast<float *>(sm4);
+  __shared__ XShared sh;
+  __shared__ float redf[32];
+  const int c = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p4 = (p + 3) & ~3, n4 = (n + 3) & ~3;
+  float *xs = sm;              // x (p), then y (n) in the same place
+  float *vsm = sm + max(p4, n4);
+  const float *x = X + (int64_t)c * ldx;
+  float *u = U + (int64_t)c * ldu;
+  const float *y = Y + (int64_t)c * ldu;
+  float *v = V + (int64_t)c * ldx;
+  for (int k = 0; k < sweeps; ++k) {
+    __syncthreads();   // (the status and x written by the last x-step)
+    if (st.status[c] != ST_ACTIVE) break;
+    for (int j = threadIdx.x; j < p; j += XT) xs[j] = x[j];
+    __syncthreads();
+    for (int i = warp; i < n; i += XW) {   // u = A x
+      const float *a = A + (int64_t)i * lda;
+      float acc = 0.0f;
+      for (int j = lane; j < p; j += 32) acc = fmaf(a[j], xs[j], acc);
+      acc = warp_sum_f(acc);
+      if (lane == 0) u[i] = acc;
+    }
+    __syncthreads();
+    ystep_body(xa.form, U, ldu, n, Y, nullptr, 0, nullptr, st, X, ldx, p, c, redf);
+    __syncthreads();
+    if (st.status[c] != ST_ACTIVE) break;   // u = 0 under L2 variance: degenerate
+    for (int i = threadIdx.x; i < n; i += XT) xs[i] = y[i];
+    __syncthreads();
+    for (int j = threadIdx.x; j < p; j += XT) {   // v = A^T y, a column of A per thread
+      float acc = 0.0f;
+      for (int i = 0; i < n; ++i) acc = fmaf(A[(int64_t)i * lda + j], xs[i], acc);
+      v[j] = acc;
+    }
+    __syncthreads();
+    xstep_full_one(xa, c, V, ldx, X, ldx, st, sup_idx, sup_val, nullptr, vsm, sh);
+  }
+}
+
+bool small_sweeps_fit(int64_t n, int64_t p) {
+  const int64_t words = ((std::max(n, p) + 3) & ~int64_t(3)) + ((p + 3) & ~int64_t(3));
+  return n * p <= kSmallMaxEntries && words * 4 <= (int64_t)XSTEP_SMEM_MAX;
+}
+
+cudaError_t launch_small_sweeps(XstepArgs xa, const float *A, int64_t lda, int n, int p, float *X, int64_t ldx,
+                                float *U, float *Y, int64_t ldu, float *V, StartState s, int *sup_idx, float *sup_val,
+                                int r, int sweeps, cudaStream_t st) {
+  if (!small_sweeps_fit(n, p)) return cudaErrorInvalidValue;
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(k_small_sweeps, cudaFuncAttributeMaxDynamicSharedMemorySize, XSTEP_SMEM_MAX);
+  if (configured != cudaSuccess) return configured;
+  const size_t bytes = 4 * (size_t)((((std::max(n, p) + 3) & ~3)) + ((p + 3) & ~3));
+  k_small_sweeps<<<r, XT, bytes, st>>>(xa, A, lda, n, p, X, ldx, U, Y, ldu, V, s, sup_idx, sup_val, sweeps);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,

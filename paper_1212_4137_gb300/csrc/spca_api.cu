@@ -1246,7 +1246,25 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   // every start runs at most max_iter sweeps and every sweep advances at least one start, so l
   // starts end within l * max_iter sweeps (the loop stops as soon as no slot is active)
   const int max_total = otf ? (int)std::min<int64_t>((int64_t)l * max_iter, INT32_MAX / 2) : max_iter;
-  for (int k0 = 1; k0 <= max_total && rc == SPCA_OK;) {
+  // a small dense matrix on the CUDA-core engine: every sweep of every start in one launch, since
+  // the chain of launches of a sweep, not its work, would set the time (AUTO only: an explicit
+  // engine keeps the per-sweep kernels)
+  const bool small = P.engine == SPCA_ENGINE_AUTO && engine == SPCA_ENGINE_SIMT && !h->sparse && !otf && L == 0 &&
+                     h->defl_k == 0 && h->A32 && small_sweeps_fit(h->n, h->p);
+  if (small) {
+    CK(timed(h, SPCA_K_XSTEP, 1, [&] {
+      return launch_small_sweeps(xa, h->A32, h->ldA, n, p, h->X, h->ldX, h->U, h->Y, h->ldU, h->V, S, h->sup_idx,
+                                 h->sup_val, r, max_iter, st);
+    }));
+    if (P.timeout_us > 0 && std::chrono::duration_cast<std::chrono::microseconds>(
+                                std::chrono::steady_clock::now() - t_start).count() > P.timeout_us) {
+      CK(cudaStreamSynchronize(st));
+      if (std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t_start).count() >
+          P.timeout_us)
+        return fail(h, SPCA_E_TIMEOUT, "the solve ran past timeout_us%s");
+    }
+  }
+  for (int k0 = 1; k0 <= max_total && rc == SPCA_OK && !small;) {
     const int k1 = std::min(max_total, (k0 + check_every - 1) / check_every * check_every);
     plans.clear();
     key = solve_key;

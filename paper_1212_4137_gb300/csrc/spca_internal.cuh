@@ -453,7 +453,7 @@ cudaError_t launch_g_ystep(const GProb *P, const int *prob, int R, cudaStream_t 
 cudaError_t launch_g_xstep(const GProb *P, const int *prob, int R, int max_p_small, bool any_large, bool cand,
                            int parity, int sms, cudaStream_t st);
 constexpr int kXstepSmemMaxP = 200 * 1024 / 4;   // the longest v the x-step stages in shared memory
-constexpr int kCandMinPGroup = 4096;             // shorter v: the grouped x-step's full pass only
+constexpr int kCandMinPGroup = 512;              // shorter v: the grouped x-step's full pass only
 
 // Grouped contraction: one persistent launch over the tiles of many contractions (one per problem
 // of a group), each described by a task in device memory, its tiles listed in tile_list (task,
@@ -541,6 +541,14 @@ struct XstepScratch {
   int *cand_idx = nullptr;     // r * kXstepCand
   int *meta = nullptr;         // r * 4 (16-byte aligned)
 };
+// small problems (n p <= kSmallMaxEntries, x, y and v in shared memory): every sweep of every
+// start in one launch, a CTA per start (u = A x and v = A^T y on the CUDA cores from A, the y-step
+// writing Y, the full-pass x-step); sweeps = the most sweeps a start may run
+constexpr int64_t kSmallMaxEntries = int64_t(1) << 21;
+bool small_sweeps_fit(int64_t n, int64_t p);
+cudaError_t launch_small_sweeps(XstepArgs xa, const float *A, int64_t lda, int n, int p, float *X, int64_t ldx,
+                                float *U, float *Y, int64_t ldu, float *V, StartState s, int *sup_idx, float *sup_val,
+                                int r, int sweeps, cudaStream_t st);
 cudaError_t launch_xstep(XstepArgs a, const float *V, int64_t ldv, int r, float *X, int64_t ldx,
                          StartState s, int *sup_idx, float *sup_val, Ctrl *ctrl_next, XstepScratch scratch,
                          cudaStream_t st);

@@ -39,11 +39,13 @@ def lib():
     return spca
 
 
-ENGINES = ("simt", "tc")
+ENGINES = ("simt", "tc", "auto")
 
 
 def _engine(lib, name):
-    return {"simt": lib.SPCA_ENGINE_SIMT, "tc": lib.SPCA_ENGINE_TC}[name]
+    # "auto" on these small matrices takes the one-launch solve of small problems (every sweep of a
+    # start in one CTA); "simt" and "tc" keep the per-sweep kernels
+    return {"simt": lib.SPCA_ENGINE_SIMT, "tc": lib.SPCA_ENGINE_TC, "auto": lib.SPCA_ENGINE_AUTO}[name]
 
 
 def _kw(form, s, gamma, target):
