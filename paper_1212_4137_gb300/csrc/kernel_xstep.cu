@@ -1192,15 +1192,19 @@ __global__ void __launch_bounds__(XT) k_small_sweeps(XstepArgs xa, const float *
   }
 }
 
-bool small_sweeps_fit(int64_t n, int64_t p) {
+// (measured on GB300: with one CTA per start, a start's sweep costs about as much as the launch
+// chain it replaces at n p ~ 4e5, so mid-sized matrices take this path only with enough starts
+// to fill the device)
+bool small_sweeps_fit(int64_t n, int64_t p, int r) {
   const int64_t words = ((std::max(n, p) + 3) & ~int64_t(3)) + ((p + 3) & ~int64_t(3));
-  return n * p <= kSmallMaxEntries && words * 4 <= (int64_t)XSTEP_SMEM_MAX;
+  if (words * 4 > (int64_t)XSTEP_SMEM_MAX) return false;
+  return n * p <= kSmallAlwaysEntries || (n * p <= kSmallMaxEntries && r >= kSmallMinStarts);
 }
 
 cudaError_t launch_small_sweeps(XstepArgs xa, const float *A, int64_t lda, int n, int p, float *X, int64_t ldx,
                                 float *U, float *Y, int64_t ldu, float *V, StartState s, int *sup_idx, float *sup_val,
                                 int r, int sweeps, cudaStream_t st) {
-  if (!small_sweeps_fit(n, p)) return cudaErrorInvalidValue;
+  if (!small_sweeps_fit(n, p, r)) return cudaErrorInvalidValue;
   static const cudaError_t configured =
       cudaFuncSetAttribute(k_small_sweeps, cudaFuncAttributeMaxDynamicSharedMemorySize, XSTEP_SMEM_MAX);
   if (configured != cudaSuccess) return configured;

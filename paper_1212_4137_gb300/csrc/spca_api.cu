@@ -1250,7 +1250,7 @@ int spca_solve(spca_handle *h, const spca_params *prm, const float *x0, spca_res
   // the chain of launches of a sweep, not its work, would set the time (AUTO only: an explicit
   // engine keeps the per-sweep kernels)
   const bool small = P.engine == SPCA_ENGINE_AUTO && engine == SPCA_ENGINE_SIMT && !h->sparse && !otf && L == 0 &&
-                     h->defl_k == 0 && h->A32 && small_sweeps_fit(h->n, h->p);
+                     h->defl_k == 0 && h->A32 && small_sweeps_fit(h->n, h->p, r);
   if (small) {
     CK(timed(h, SPCA_K_XSTEP, 1, [&] {
       return launch_small_sweeps(xa, h->A32, h->ldA, n, p, h->X, h->ldX, h->U, h->Y, h->ldU, h->V, S, h->sup_idx,

@@ -541,11 +541,14 @@ struct XstepScratch {
   int *cand_idx = nullptr;     // r * kXstepCand
   int *meta = nullptr;         // r * 4 (16-byte aligned)
 };
-// small problems (n p <= kSmallMaxEntries, x, y and v in shared memory): every sweep of every
-// start in one launch, a CTA per start (u = A x and v = A^T y on the CUDA cores from A, the y-step
-// writing Y, the full-pass x-step); sweeps = the most sweeps a start may run
-constexpr int64_t kSmallMaxEntries = int64_t(1) << 21;
-bool small_sweeps_fit(int64_t n, int64_t p);
+// small problems (n p <= kSmallAlwaysEntries, or <= kSmallMaxEntries with at least
+// kSmallMinStarts starts; x, y and v in shared memory): every sweep of every start in one launch,
+// a CTA per start (u = A x and v = A^T y on the CUDA cores from A, the y-step writing Y, the
+// full-pass x-step); sweeps = the most sweeps a start may run
+constexpr int64_t kSmallAlwaysEntries = int64_t(1) << 17;
+constexpr int64_t kSmallMaxEntries = int64_t(1) << 19;
+constexpr int kSmallMinStarts = 16;
+bool small_sweeps_fit(int64_t n, int64_t p, int r);
 cudaError_t launch_small_sweeps(XstepArgs xa, const float *A, int64_t lda, int n, int p, float *X, int64_t ldx,
                                 float *U, float *Y, int64_t ldu, float *V, StartState s, int *sup_idx, float *sup_val,
                                 int r, int sweeps, cudaStream_t st);

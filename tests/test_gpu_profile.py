@@ -25,7 +25,8 @@ def test_profiled_solve_matches_and_counts(lib, kernels):
     A = I.spiked_matrix(n, p, I.spiked_thetas(n, p), 20, 61, dtype=np.float32)
     G = I.raw_starts(p, r, 62).astype(np.float32)
     h = lib.Handle(A)
-    kw = dict(s=20.0, x0=G, max_iter=40, tol=1e-7, want_starts=True)
+    # the per-sweep kernels (AUTO would run this small matrix in one launch per solve)
+    kw = dict(s=20.0, x0=G, max_iter=40, tol=1e-7, want_starts=True, engine=lib.SPCA_ENGINE_SIMT)
     plain = h.solve(3, r, **kw)
     h.profile(True, kernels=None if kernels is None else (lib.SPCA_K_V,))
     prof = h.solve(3, r, **kw)
