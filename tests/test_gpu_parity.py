@@ -432,3 +432,19 @@ def test_tiny_and_ragged_shapes(lib, oracle):
             ref = oracle.solve(A.astype(np.float64), form, G.astype(np.float64), s=s, max_iter=15, tol=-1)
             np.testing.assert_allclose(out["start_objective"], ref.f, rtol=1e-5, atol=1e-6)
         h.close()
+
+
+def test_tall_matrix_past_the_grid_limits(lib, oracle):
+    """n above 32 x 65535 rows: every launch sized by n must stay within the grid limits (the
+    transpose walks its row blocks in a loop), so a create and a solve succeed and agree with the
+    oracle."""
+    n, p, r = 2_097_153, 2, 2
+    A = I.gaussian_matrix(n, p, 41).astype(np.float32)
+    G = I.raw_starts(p, r, 42).astype(np.float32)
+    h = lib.Handle(A)
+    for engine in (lib.SPCA_ENGINE_AUTO, lib.SPCA_ENGINE_SIMT):
+        out = h.solve(1, r, s=1, max_iter=3, tol=-1, x0=G, want_starts=True, engine=engine)
+        ref = oracle.solve(A.astype(np.float64), 1, G.astype(np.float64), s=1, max_iter=3, tol=-1)
+        assert np.array_equal(out["start_x"] != 0, ref.X != 0)
+        assert np.all(np.abs(out["start_objective"] - ref.f) <= 1e-5 * np.abs(ref.f))
+    h.close()
