@@ -35,8 +35,8 @@ static __device__ __forceinline__ double bm_normal(uint64_t key, uint64_t i) {
 // Algorithm 2, "select initial point": x^(0) = g / ||g||_2 for the start in row c of X, taking
 // start `start` (its row of x0, or normal numbers start * p + j of the seeded stream).
 static __device__ void start_init_body(const float *__restrict__ x0, int64_t ld0, uint64_t key, int p,
-                                float *__restrict__ X, int64_t ldX, StartState s, double gamma0, int c,
-                                int64_t start, float *redf) {
+                                       float *__restrict__ X, int64_t ldX, StartState s, double gamma0, int c,
+                                       int64_t start, float *redf) {
   float *x = X + (int64_t)c * ldX;
   const float *g = x0 ? x0 + start * ld0 : nullptr;
   float part = 0.0f;
@@ -64,9 +64,10 @@ static __device__ void start_init_body(const float *__restrict__ x0, int64_t ld0
 // Counts the sweep for every active start; L1 variance: y = sgn(u) with sgn(0) = +1;
 // L2 variance: y = u / ||u||_2, and ||u||_2 = 0 ends the start as degenerate (x = 0).
 // y goes to Y (FP32) and/or to the FP16 planes of kQScale y (hi, lo; one exact plane for +-1).
-static __device__ void ystep_body(int form, const float *__restrict__ U, int64_t ldu, int n, float *__restrict__ Y,
-                           __half *__restrict__ Ypl, int64_t pstride, const int *__restrict__ rank, StartState s,
-                           float *__restrict__ X, int64_t ldX, int p, int c, float *redf) {
+static __device__ void ystep_body(int form, const float *__restrict__ U, int64_t ldu, int n,
+                                  float *__restrict__ Y, __half *__restrict__ Ypl, int64_t pstride,
+                                  const int *__restrict__ rank, StartState s, float *__restrict__ X, int64_t ldX,
+                                  int p, int c, float *redf) {
   if (s.status[c] != ST_ACTIVE) return;
   const float *u = U + (int64_t)c * ldu;
   float *y = Y ? Y + (int64_t)c * ldu : nullptr;
