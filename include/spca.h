@@ -438,10 +438,11 @@ int spca_set_waits(spca_handle *h, int64_t wait_limit_us, int unpublished_parts)
  * matrix (a handle), formulation, s or gamma and starts (the batching of Section 4 carried across
  * problems).  Every phase of a sweep is one launch over all the group's problems: the dense
  * u = A x of a problem's first sweep and v = A^T y of every sweep as one persistent tensor-core
- * launch over the tiles of all problems, the support gather, y-step, x-step (full pass) and
- * active lists as one launch each over all starts or problems.  Each problem's results do not
- * depend on the other problems of the group (the same bits alone and in any mix) and agree with
- * spca_solve's for it up to the order of rounding in the contractions.  The problems on one
+ * launch over the tiles of all problems; the start set-up, support gather, y-step, x-step (the
+ * candidate filter and operator, then the full pass for the starts they leave) and active lists
+ * as one launch each over all starts or problems.  Each problem's results do not depend on the
+ * other problems of the group (the same bits alone and in any mix) and agree with spca_solve's
+ * for it up to the order of rounding in the contractions and the x-step's sums.  The problems on one
  * matrix (one handle and its clones) whose v = A^T y takes the same plane products share one
  * contraction (a pool): their active starts side by side in one operand, so the matrix is read
  * once per sweep for all of them; a start's sums do not depend on where the others put it.
