@@ -245,7 +245,8 @@ def spca_destroy(h) -> None:
 class Handle:
     """Owns an spca_handle; A is host numpy (float32/float64), a torch CUDA tensor, or a sparse
     matrix (scipy.sparse, or a tuple (indptr, indices, data, (n, p)) of host arrays) kept in
-    compressed sparse rows."""
+    compressed sparse rows.  storage (dense A): SPCA_F32, SPCA_FP16, SPCA_FP8_E4M3_COLSCALED, or
+    SPCA_FP16_RESIDENT (A kept only in 16 bits; every sweep a low-precision one)."""
 
     def __init__(self, A, stream: int = 0, storage: int = SPCA_F32):
         if isinstance(A, tuple) or hasattr(A, "indptr") or hasattr(A, "tocsr"):
