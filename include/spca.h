@@ -473,7 +473,8 @@ int spca_set_waits(spca_handle *h, int64_t wait_limit_us, int unpublished_parts)
  *                      and stages (2..4 for 64, 2..3 for 128); NULL or {0, 0} = chosen when the
  *                      tables are built, from the widest pool (the most starts that share one
  *                      contraction): 64 x 4 up to 64 starts, 128 x 3 above, the shapes bench.py
- *                      --tune measured best for those start counts.
+ *                      --tune measured best for those start counts; a group of resident 16-bit
+ *                      matrices only takes 64, 128 or 256 columns by the same widths, 4 stages.
  * spca_group_admit     admit `count` problems (tags[i] identifies problem i in the finished
  *                      lists; NULL = 0 .. count - 1); a member's device memory is allocated here
  *                      (stream-ordered).  On failure none of the call's problems is admitted.
