@@ -74,6 +74,18 @@ def test_constants_match_header(lib):
     assert m and int(m.group(1)) == 262144
 
 
+def test_enums_and_group_structs_match_header(lib):
+    names = ("SPCA_OK", "SPCA_E_INVALID", "SPCA_E_NOMEM", "SPCA_E_CUDA", "SPCA_E_TIMEOUT", "SPCA_E_BUSY",
+             "SPCA_E_UNSUPPORTED", "SPCA_F32", "SPCA_F64", "SPCA_FP16", "SPCA_FP8_E4M3_COLSCALED",
+             "SPCA_FP16_RESIDENT", "SPCA_ST_MAXITER", "SPCA_ST_CONVERGED", "SPCA_ST_DEGENERATE",
+             "SPCA_ENGINE_AUTO", "SPCA_ENGINE_SIMT", "SPCA_ENGINE_TC", "SPCA_ENGINE_TC_LOWP")
+    vals = _enum_values(names)
+    for name in names:
+        assert getattr(lib, name) == vals[name], name
+    assert [f for f, _ in lib.spca_problem._fields_] == _struct_fields("spca_problem")
+    assert [f for f, _ in lib.spca_group_tiles._fields_] == _struct_fields("spca_group_tiles")
+
+
 def test_strerror_is_static_text(lib):
     assert lib.spca_strerror(0) == "ok"
     assert lib.spca_strerror(1) == "invalid argument"
