@@ -205,7 +205,7 @@ def run_ours(args, w, rank, world, local_rank):
     clocks = clk.summary()
     # per-kernel shares of device time from one more (untimed) step with every launch timed
     h.profile(True)
-    one_step()
+    sweeps_one = one_step()   # (the sweeps of this step: the per-kernel times below are this step's)
     kern = {}
     for kid, name in spca.KERNEL_NAMES.items():
         kern[name] = h.profile_query(kid)
@@ -267,8 +267,18 @@ def run_ours(args, w, rank, world, local_rank):
                 "algorithmic_bytes_same_launch": V_ALG_BYTES,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; FP16 and BF16 dense rates are equal)",
                 "launches": vstats["launches"], "avg_launch_ms": round(vstats["ms"] / max(1, vstats["launches"]), 4)}
+    elif dom == "xstep" and kern["xstep"][1] > 0 and kern["v"][0] == 0:
+        # a small problem: every sweep of every start in one launch (k_small_sweeps, charged to the
+        # x-step's timer); its work is the two products on the CUDA cores, 4 n p flop per sweep*start
+        achieved = 4.0 * n * p * sweeps_one / (kern["xstep"][1] / 1e3) / 1e12
+        roof = {"kernel": "every sweep of a start in one launch (k_small_sweeps: u = A x, v = A^T y, y-step, x-step)",
+                "bound": "alu", "achieved": round(achieved, 4), "peak": round(SIMT_FP32_PEAK_TFLOPS, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / SIMT_FP32_PEAK_TFLOPS, 5), "traffic": None,
+                "per_unit": "4*n*p flop per sweep*start (the two products, FP32 FMA)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived)",
+                "launches": kern["xstep"][0]}
     elif dom == "xstep" and kern["xstep"][1] > 0:
-        achieved = 8.0 * p * sweeps / (kern["xstep"][1] / 1e3) / 1e9
+        achieved = 8.0 * p * sweeps_one / (kern["xstep"][1] / 1e3) / 1e9
         roof = {"kernel": "x-step (k_xstep)", "bound": "hbm", "achieved": round(achieved, 1),
                 "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                 "frac": round(achieved / peaks.get("hbm_gbs", 6701.5), 4), "traffic": None,
